@@ -1,0 +1,223 @@
+"""Plain FP64 CPU oracle of one GO-Surf optimisation step (test infrastructure only).
+
+Only the tests, ``__graft_entry__.smoke()`` and the CPU-baseline leg of ``bench.py`` may
+import this package.  The product (the CUDA library and its Python binding) never does,
+and this package never imports the product: the two share only the seeded inputs made by
+``scenegen``.
+
+The arithmetic lives in ``gosurf_oracle.c`` (compiled here with gcc, -O2,
+-ffp-contract=off, OpenMP); this module only marshals numpy arrays.  Every function cites
+the passage of the paper it follows in the C source.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import subprocess
+import threading
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_BUILD = os.path.join(_HERE, "_build")
+_LIB = None
+_LOCK = threading.Lock()
+
+LEVELS, FEAT, MLP_PARAMS = 4, 4, 1684
+CLS_NONE, CLS_TR, CLS_FS = 0, 1, 2
+
+
+class OcConfig(ctypes.Structure):
+    _fields_ = [("dims", (ctypes.c_int32 * 3) * 4), ("voxel", ctypes.c_float * 4), ("origin", ctypes.c_float * 3),
+                ("n_strat", ctypes.c_int32), ("n_guided", ctypes.c_int32), ("near_m", ctypes.c_float),
+                ("far_m", ctypes.c_float), ("guide_half", ctypes.c_float), ("trunc", ctypes.c_float),
+                ("kappa_fs", ctypes.c_float), ("lam", ctypes.c_float * 5), ("n_smooth", ctypes.c_int32),
+                ("delta_s", ctypes.c_float)]
+
+
+class OcFrames(ctypes.Structure):
+    _fields_ = [("F", ctypes.c_int32), ("H", ctypes.c_int32), ("W", ctypes.c_int32), ("rgb", ctypes.c_void_p),
+                ("depth", ctypes.c_void_p), ("c2w", ctypes.c_void_p), ("fx", ctypes.c_float), ("fy", ctypes.c_float),
+                ("cx", ctypes.c_float), ("cy", ctypes.c_float)]
+
+
+def build(force: bool = False) -> str:
+    """Compile the oracle into oracle/_build/liboracle.so (this builds the checker; it does not run it)."""
+    os.makedirs(_BUILD, exist_ok=True)
+    so = os.path.join(_BUILD, "liboracle.so")
+    src = os.path.join(_HERE, "gosurf_oracle.c")
+    if force or not os.path.exists(so) or os.path.getmtime(so) < os.path.getmtime(src):
+        tmp = so + f".{os.getpid()}.tmp"
+        subprocess.check_call(["gcc", "-O2", "-std=c11", "-fPIC", "-shared", "-fopenmp", "-ffp-contract=off",
+                               "-fno-fast-math", src, "-o", tmp, "-lm"])
+        os.replace(tmp, so)
+    return so
+
+
+def _p(a):
+    return None if a is None else ctypes.c_void_p(a.ctypes.data)
+
+
+def lib():
+    global _LIB
+    with _LOCK:
+        if _LIB is None:
+            L = ctypes.CDLL(build())
+            vp, i32, i64, u64, u32, dbl = (ctypes.c_void_p, ctypes.c_int, ctypes.c_int64, ctypes.c_uint64,
+                                          ctypes.c_uint32, ctypes.c_double)
+            L.oc_sm64.restype = u64
+            L.oc_sm64.argtypes = [u64]
+            L.oc_composite.restype = None
+            L.oc_composite.argtypes = [i32, vp, dbl, vp, vp, vp, vp, vp, vp]
+            L.oc_draw.restype = u64
+            L.oc_draw.argtypes = [u64, u64, u64, u64, u64]
+            L.oc_sample_rays.restype = None
+            L.oc_sample_rays.argtypes = [vp, vp, u64, u32, i32] + [vp] * 8
+            L.oc_sample_smooth.restype = None
+            L.oc_sample_smooth.argtypes = [vp, vp, u64, u32, i32, vp, vp, vp, vp]
+            L.oc_step.restype = i32
+            L.oc_step.argtypes = [vp, vp, i32, i32] + [vp] * 6 + [i32] + [vp] * 10
+            L.oc_query_sdf.restype = None
+            L.oc_query_sdf.argtypes = [vp, vp, vp, i32, vp, vp]
+            L.oc_voxel_index.restype = None
+            L.oc_voxel_index.argtypes = [vp, vp, i32, vp]
+            L.oc_trilinear_coeffs.restype = None
+            L.oc_trilinear_coeffs.argtypes = [vp, vp, vp]
+            L.oc_trilinear_hessian.restype = None
+            L.oc_trilinear_hessian.argtypes = [vp, vp, vp]
+            L.oc_adam.restype = None
+            L.oc_adam.argtypes = [vp, vp, vp, vp, i64, i64, i32, dbl, dbl, dbl, dbl, dbl]
+            L.oc_num_threads.restype = i32
+            _LIB = L
+    return _LIB
+
+
+def make_config(w) -> OcConfig:
+    """Oracle configuration from a scenegen.Workload."""
+    c = OcConfig()
+    for l, d in enumerate(w.dims):
+        for a in range(3):
+            c.dims[l][a] = d[a]
+        c.voxel[l] = w.voxels[l]
+    c.origin[:] = list(w.extent_min)
+    c.n_strat, c.n_guided = w.n_strat, w.n_guided
+    c.near_m, c.far_m, c.guide_half, c.trunc, c.kappa_fs = w.near, w.far, w.guide_half, w.trunc, w.kappa_fs
+    c.lam[:] = list(w.lambdas)
+    c.n_smooth, c.delta_s = w.n_smooth, w.delta_s
+    return c
+
+
+class OcFramesHolder:
+    """Keeps the numpy arrays alive next to the ctypes struct that points at them."""
+
+    def __init__(self, frames):
+        self.rgb = np.ascontiguousarray(frames.rgb, dtype=np.uint8)
+        self.depth = np.ascontiguousarray(frames.depth, dtype=np.float32)
+        self.c2w = np.ascontiguousarray(frames.c2w, dtype=np.float32)
+        F, H, W = self.depth.shape
+        self.s = OcFrames(F, H, W, self.rgb.ctypes.data, self.depth.ctypes.data, self.c2w.ctypes.data,
+                          frames.fx, frames.fy, frames.cx, frames.cy)
+
+
+def sm64(x: int) -> int:
+    return int(lib().oc_sm64(x))
+
+
+def composite(phi, s, d):
+    """NeuS compositing of one ray: returns alpha, T, w, d_hat, wsum."""
+    phi = np.ascontiguousarray(phi, dtype=np.float64)
+    d = np.ascontiguousarray(d, dtype=np.float32)
+    N = len(phi)
+    alpha, T, w = np.empty(N), np.empty(N), np.empty(N)
+    dh, ws = np.empty(1), np.empty(1)
+    lib().oc_composite(N, _p(phi), s, _p(d), _p(alpha), _p(T), _p(w), _p(dh), _p(ws))
+    return alpha, T, w, float(dh[0]), float(ws[0])
+
+
+def draw(seed, stream, step, index, slot) -> int:
+    return int(lib().oc_draw(seed, stream, step, index, slot))
+
+
+def sample_rays(cfg: OcConfig, frames: OcFramesHolder, seed: int, step: int, R: int) -> dict:
+    N = cfg.n_strat + cfg.n_guided
+    out = dict(pix=np.empty(R, np.int64), o=np.empty((R, 3), np.float32), r=np.empty((R, 3), np.float32),
+               rgb=np.empty((R, 3), np.float32), D=np.empty(R, np.float32), t=np.empty((R, N), np.float32),
+               cls=np.empty((R, N), np.uint8), counts=np.empty(4, np.int64))
+    lib().oc_sample_rays(ctypes.byref(cfg), ctypes.byref(frames.s), seed, step, R, *[_p(out[k]) for k in
+                                                                                     ("pix", "o", "r", "rgb", "D", "t",
+                                                                                      "cls", "counts")])
+    return out
+
+
+def sample_smooth(cfg: OcConfig, frames: OcFramesHolder, seed: int, step: int, P: int) -> dict:
+    out = dict(xs=np.empty((P, 3), np.float32), eps=np.empty((P, 3), np.float32), valid=np.empty(P, np.uint8),
+               n_valid=np.empty(1, np.int64))
+    lib().oc_sample_smooth(ctypes.byref(cfg), ctypes.byref(frames.s), seed, step, P,
+                           *[_p(out[k]) for k in ("xs", "eps", "valid", "n_valid")])
+    return out
+
+
+def step(cfg: OcConfig, theta, batch: dict, smooth: dict | None, dloss=None, want_grad=True, want_margins=False):
+    """Losses (and gradients) of one step.  theta: flat parameters (promoted to FP64)."""
+    th = np.ascontiguousarray(theta, dtype=np.float64)
+    R, N = batch["t"].shape
+    if smooth is None:
+        P = 0
+        xs = eps = np.zeros((1, 3), np.float32)
+        valid = np.zeros(1, np.uint8)
+    else:
+        P = len(smooth["valid"])
+        xs, eps, valid = smooth["xs"], smooth["eps"], smooth["valid"]
+    loss = np.zeros(6)
+    rgb_hat, d_hat, wsum = np.zeros((R, 3)), np.zeros(R), np.zeros(R)
+    grad = np.zeros_like(th) if want_grad else None
+    margins = np.zeros(8) if want_margins else None
+    dl = None if dloss is None else np.ascontiguousarray(dloss, dtype=np.float64)
+    rc = lib().oc_step(ctypes.byref(cfg), _p(th), R, N, _p(batch["o"]), _p(batch["r"]), _p(batch["rgb"]),
+                       _p(batch["D"]), _p(batch["t"]), _p(batch["cls"]), P, _p(xs), _p(eps), _p(valid), _p(dl),
+                       _p(loss), _p(rgb_hat), _p(d_hat), _p(wsum), _p(grad), _p(margins))
+    if rc != 0:
+        raise ValueError("oc_step rejected its arguments")
+    return dict(loss=loss, rgb_hat=rgb_hat, d_hat=d_hat, wsum=wsum, grad=grad, margins=margins)
+
+
+def query_sdf(cfg: OcConfig, theta, x, want_grad=True):
+    th = np.ascontiguousarray(theta, dtype=np.float64)
+    x = np.ascontiguousarray(x, dtype=np.float32).reshape(-1, 3)
+    sdf = np.empty(len(x))
+    grad = np.empty((len(x), 3)) if want_grad else None
+    lib().oc_query_sdf(ctypes.byref(cfg), _p(th), _p(x), len(x), _p(sdf), _p(grad))
+    return sdf, grad
+
+
+def voxel_index(cfg: OcConfig, x) -> np.ndarray:
+    x = np.ascontiguousarray(x, dtype=np.float32).reshape(-1, 3)
+    out = np.empty((len(x), LEVELS), np.int64)
+    lib().oc_voxel_index(ctypes.byref(cfg), _p(x), len(x), _p(out))
+    return out
+
+
+def trilinear_coeffs(f):
+    f = np.ascontiguousarray(f, dtype=np.float64)
+    w, J = np.empty(8), np.empty((8, 3))
+    lib().oc_trilinear_coeffs(_p(f), _p(w), _p(J))
+    return w, J
+
+
+def trilinear_hessian(theta8, f):
+    th = np.ascontiguousarray(theta8, dtype=np.float64)
+    f = np.ascontiguousarray(f, dtype=np.float64)
+    h = np.empty(3)
+    lib().oc_trilinear_hessian(_p(th), _p(f), _p(h))
+    return h  # h12, h13, h23
+
+
+def adam(p, g, m, v, n_grid, t, lr_grid, lr_mlp, b1=0.9, b2=0.999, eps=1e-8):
+    """In-place FP64 Adam on float64 arrays (g is zeroed)."""
+    for a in (p, g, m, v):
+        assert a.dtype == np.float64 and a.flags.c_contiguous
+    lib().oc_adam(_p(p), _p(g), _p(m), _p(v), len(p), n_grid, t, lr_grid, lr_mlp, b1, b2, eps)
+
+
+def num_threads() -> int:
+    return int(lib().oc_num_threads())

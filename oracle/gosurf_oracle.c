@@ -1,0 +1,938 @@
+/*
+ * GO-Surf (arXiv 2206.14735) -- plain FP64 CPU oracle of one optimisation step.
+ *
+ * TEST INFRASTRUCTURE ONLY.  Only the tests, the smoke check and the benchmark's CPU
+ * baseline may load this file's library.  It shares no code, header or table with the
+ * CUDA library; both read the same seeded inputs.
+ *
+ * What it computes, in the paper's order:
+ *   ray batch sampling over all pixels of all frames ............ Sec. 3.4 (Optimization)
+ *   ray generation x_i = o + d_i r ............................... Sec. 3.2, Eq. (volume rendering)
+ *   per-ray samples (stratified + depth-guided, see below) ....... Sec. 3.2 (sampler reading)
+ *   bound b = D - d, near-surface / free-space split at t ........ Sec. 3.3
+ *   multi-level trilinear features, concatenated coarse->fine .... Sec. 3.1, Eq. (SDF_MLP); Supp. Sec. 1 Eq. (trilinear, coefficient vector)
+ *   geometry decoder phi = f_w(z), colour decoder ................ Sec. 3.1
+ *   NeuS opacity alpha_i, transmittance T_i, weights w_i ......... Sec. 3.2, Eq. (volume_rendering_alpha)
+ *   rendered colour / depth ...................................... Sec. 3.2, Eq. (volume_rendering)
+ *   l_rgb, l_d, l_sdf, l_fs and their batch normalisations ....... Sec. 3.2-3.4
+ *   l_smooth on near-surface points, grad_x phi .................. Sec. 3.3 Eq. (smoothness_loss); Supp. Sec. 1 Eq. (sdf_first_grad, jacobian)
+ *   gradients (hand reverse mode, incl. d/dtheta of grad_x phi) .. Supp. Sec. 1 Eq. (second_order_theta)
+ *   Adam ......................................................... Sec. 4 (Implementation Details)
+ *
+ * Precision: every quantity that decides an integer (pixel index, sample depths and their
+ * order, sample class, voxel cell, clamp flags, smoothness-point positions) is computed in
+ * IEEE binary32 with round-to-nearest and no contraction, exactly as the CUDA path does,
+ * so those results are comparable bit for bit.  Everything after the FP32 sample position
+ * is FP64.  Build with -ffp-contract=off and without fast-math.
+ *
+ * Readings where the paper is silent or ambiguous (each also listed in the design notes):
+ *   - l_rgb is the squared Euclidean norm, averaged over all rays; l_d is |D - d_hat|
+ *     averaged over rays with D > 0; L_sdf / L_fs / L_smooth are means over all points of
+ *     their set in the batch (an empty set contributes 0).
+ *   - S_tr = {|D-d| <= t}, S_fs = {D-d > t} (free space in front of the surface only);
+ *     rays with D = 0 supervise no sample.
+ *   - alpha_N = 0 (the last sample has no successor); the denominator is max(Phi_i, 1e-6).
+ *   - s = exp(kappa) with kappa learnable.
+ *   - Sub-gradients: 0 at every tie (ReLU at 0, max(.,0) at 0, |.| at 0); the free-space
+ *     max picks the first maximal entry of (0, exp term, linear term).
+ *   - Samples outside the grid box are clamped to it; the clamped axes get zero x-derivative.
+ *   - Sampling: N_s stratified samples over [near, far] plus N_g samples stratified over
+ *     [D - g, D + g] when D > 0 (all N_s + N_g stratified otherwise), merged by depth
+ *     with ties resolved stratified-first.
+ *   - Geometry decoder 16 -> 32 (ReLU) -> 16 linear outputs [phi, h_1..h_15]; colour decoder
+ *     15 -> 32 (ReLU) -> 3 with a sigmoid, fed by h.
+ */
+#include <math.h>
+#include <stdint.h>
+#include <stdlib.h>
+#include <string.h>
+#ifdef _OPENMP
+#include <omp.h>
+#endif
+
+#define OC_LEVELS 4
+#define OC_FEAT 4
+#define OC_Z (OC_LEVELS * OC_FEAT) /* 16 */
+#define OC_H1 32
+#define OC_OUT 16
+#define OC_HF 15
+#define OC_H2 32
+#define OC_RGB 3
+#define OC_MLP 1684
+
+enum { CLS_NONE = 0, CLS_TR = 1, CLS_FS = 2 };
+
+typedef struct {
+  int32_t dims[OC_LEVELS][3]; /* vertex counts (nx, ny, nz), level 0 = coarsest */
+  float voxel[OC_LEVELS];     /* voxel edge length (m) */
+  float origin[3];            /* position of vertex (0,0,0) */
+  int32_t n_strat, n_guided;
+  float near_m, far_m;
+  float guide_half; /* g: half width of the depth-guided band */
+  float trunc;      /* t: truncation distance of the SDF bound */
+  float kappa_fs;   /* exponent scale of the free-space penalty (5) */
+  float lam[5];     /* rgb, depth, sdf, fs, smooth */
+  int32_t n_smooth;
+  float delta_s;
+} oc_config;
+
+typedef struct {
+  int32_t F, H, W;
+  const uint8_t* rgb;
+  const float* depth;
+  const float* c2w; /* [F][3][4] row-major */
+  float fx, fy, cx, cy;
+} oc_frames;
+
+/* ------------------------------------------------------------------------------------ */
+/* counter-based random numbers: SplitMix64 (Steele, Lea & Flood, OOPSLA 2014)            */
+/* ------------------------------------------------------------------------------------ */
+static uint64_t sm64(uint64_t x) {
+  x += 0x9E3779B97F4A7C15ULL;
+  x = (x ^ (x >> 30)) * 0xBF58476D1CE4E5B9ULL;
+  x = (x ^ (x >> 27)) * 0x94D049BB133111EBULL;
+  return x ^ (x >> 31);
+}
+/* one SplitMix64 output: the generator seeded with x returns oc_sm64(x + (k-1) * golden gamma) as its k-th value */
+uint64_t oc_sm64(uint64_t x) { return sm64(x); }
+/* key chain (seed, stream, step, index, slot) -> 64 random bits */
+uint64_t oc_draw(uint64_t seed, uint64_t stream, uint64_t step, uint64_t index, uint64_t slot) {
+  uint64_t h = sm64(seed);
+  h = sm64(h ^ stream);
+  h = sm64(h ^ step);
+  h = sm64(h ^ index);
+  return sm64(h ^ slot);
+}
+/* uniform in [0,1): top 24 bits scaled by 2^-24 (exact in binary32) */
+static float unif24(uint64_t h) { return (float)(h >> 40) * 0x1p-24f; }
+
+/* ------------------------------------------------------------------------------------ */
+/* ray sampling (binary32)                                                                */
+/* ------------------------------------------------------------------------------------ */
+/* pixel -> camera ray with unit camera-z direction, so the ray parameter is z-depth */
+static void pixel_ray(const oc_frames* fr, int64_t pix, float o[3], float r[3], float rgb[3], float* D) {
+  int64_t hw = (int64_t)fr->H * fr->W;
+  int64_t f = pix / hw, rem = pix % hw;
+  int v = (int)(rem / fr->W), u = (int)(rem % fr->W);
+  float dx = (((float)u + 0.5f) - fr->cx) / fr->fx;
+  float dy = (((float)v + 0.5f) - fr->cy) / fr->fy;
+  const float* P = fr->c2w + 12 * f;
+  for (int a = 0; a < 3; ++a) {
+    float t0 = P[4 * a + 0] * dx;
+    float t1 = P[4 * a + 1] * dy;
+    r[a] = (t0 + t1) + P[4 * a + 2];
+    o[a] = P[4 * a + 3];
+  }
+  for (int j = 0; j < 3; ++j) rgb[j] = (float)fr->rgb[3 * pix + j] / 255.0f;
+  *D = fr->depth[pix];
+}
+
+static int sample_class(float D, float t, float trunc) {
+  if (!(D > 0.0f)) return CLS_NONE;
+  float b = D - t;
+  if (fabsf(b) <= trunc) return CLS_TR;
+  if (b > trunc) return CLS_FS;
+  return CLS_NONE;
+}
+
+/*
+ * Draw R rays uniformly (with replacement) over all F*H*W pixels, including pixels with
+ * missing depth, and N = n_strat + n_guided sorted sample depths per ray.
+ * Outputs: pix[R], o[R,3], r[R,3], rgb[R,3], D[R], t[R,N], cls[R,N], counts[4] =
+ * (rays with D>0, |S_tr|, |S_fs|, 0).
+ */
+void oc_sample_rays(const oc_config* c, const oc_frames* fr, uint64_t seed, uint32_t step, int R, int64_t* pix,
+                    float* o, float* r, float* rgb, float* D, float* t, uint8_t* cls, int64_t* counts) {
+  const int Ns = c->n_strat, Ng = c->n_guided, N = Ns + Ng;
+  const int64_t npix = (int64_t)fr->F * fr->H * fr->W;
+  float* ts = (float*)malloc(sizeof(float) * N);
+  float* tg = (float*)malloc(sizeof(float) * (Ng > 0 ? Ng : 1));
+  int64_t nd = 0, ntr = 0, nfs = 0;
+  for (int i = 0; i < R; ++i) {
+    uint64_t h = oc_draw(seed, 0, step, (uint64_t)i, 0);
+    int64_t p = (int64_t)(h % (uint64_t)npix);
+    pix[i] = p;
+    float Di;
+    pixel_ray(fr, p, o + 3 * i, r + 3 * i, rgb + 3 * i, &Di);
+    D[i] = Di;
+    float* ti = t + (size_t)i * N;
+    if (Di > 0.0f) {
+      ++nd;
+      float delta = (c->far_m - c->near_m) / (float)Ns;
+      for (int k = 0; k < Ns; ++k) {
+        float u = unif24(oc_draw(seed, 0, step, (uint64_t)i, 1 + (uint64_t)k));
+        ts[k] = c->near_m + ((float)k + u) * delta;
+      }
+      float g = c->guide_half;
+      float gstep = (2.0f * g) / (float)Ng;
+      float g0 = Di - g;
+      for (int k = 0; k < Ng; ++k) {
+        float u = unif24(oc_draw(seed, 0, step, (uint64_t)i, 1 + (uint64_t)Ns + (uint64_t)k));
+        tg[k] = g0 + ((float)k + u) * gstep;
+      }
+      /* merge two ascending lists; ties keep the stratified sample first */
+      int a = 0, b = 0;
+      for (int k = 0; k < N; ++k) {
+        if (b >= Ng || (a < Ns && ts[a] <= tg[b])) ti[k] = ts[a++];
+        else ti[k] = tg[b++];
+      }
+    } else {
+      float delta = (c->far_m - c->near_m) / (float)N;
+      for (int k = 0; k < N; ++k) {
+        float u = unif24(oc_draw(seed, 0, step, (uint64_t)i, 1 + (uint64_t)k));
+        ti[k] = c->near_m + ((float)k + u) * delta;
+      }
+    }
+    for (int k = 0; k < N; ++k) {
+      int cl = sample_class(Di, ti[k], c->trunc);
+      cls[(size_t)i * N + k] = (uint8_t)cl;
+      ntr += cl == CLS_TR;
+      nfs += cl == CLS_FS;
+    }
+  }
+  counts[0] = nd;
+  counts[1] = ntr;
+  counts[2] = nfs;
+  counts[3] = 0;
+  free(ts);
+  free(tg);
+}
+
+/*
+ * Near-surface points S_g for the smoothness term: back-projected observed depth of a
+ * random valid pixel (up to 8 draws), jittered uniformly by +-t per axis; perturbation
+ * eps of length delta_s with a direction drawn by rejection in [-1,1]^3 (up to 16 draws,
+ * x axis otherwise).  valid[p] = 0 when no valid pixel was drawn.
+ */
+void oc_sample_smooth(const oc_config* c, const oc_frames* fr, uint64_t seed, uint32_t step, int P, float* xs,
+                      float* eps, uint8_t* valid, int64_t* n_valid) {
+  const int64_t npix = (int64_t)fr->F * fr->H * fr->W;
+  int64_t nv = 0;
+  for (int p = 0; p < P; ++p) {
+    int64_t px = -1;
+    for (int tr = 0; tr < 8; ++tr) {
+      uint64_t h = oc_draw(seed, 1, step, (uint64_t)p, (uint64_t)tr);
+      int64_t q = (int64_t)(h % (uint64_t)npix);
+      if (fr->depth[q] > 0.0f) { px = q; break; }
+    }
+    if (px < 0) {
+      valid[p] = 0;
+      for (int a = 0; a < 3; ++a) xs[3 * p + a] = eps[3 * p + a] = 0.0f;
+      continue;
+    }
+    valid[p] = 1;
+    ++nv;
+    float o[3], r[3], rgb[3], D;
+    pixel_ray(fr, px, o, r, rgb, &D);
+    for (int a = 0; a < 3; ++a) {
+      float u = unif24(oc_draw(seed, 1, step, (uint64_t)p, 16 + (uint64_t)a));
+      float base = o[a] + D * r[a];
+      float jit = c->trunc * (2.0f * u - 1.0f);
+      xs[3 * p + a] = base + jit;
+    }
+    float v[3] = {1.0f, 0.0f, 0.0f}, n2 = 1.0f;
+    for (int tr = 0; tr < 16; ++tr) {
+      float w[3];
+      for (int a = 0; a < 3; ++a) w[a] = 2.0f * unif24(oc_draw(seed, 1, step, (uint64_t)p, 32 + 3 * (uint64_t)tr + a)) - 1.0f;
+      float q = (w[0] * w[0] + w[1] * w[1]) + w[2] * w[2];
+      if (q >= 0.01f && q <= 1.0f) {
+        v[0] = w[0]; v[1] = w[1]; v[2] = w[2];
+        n2 = q;
+        break;
+      }
+    }
+    float sc = c->delta_s / sqrtf(n2);
+    for (int a = 0; a < 3; ++a) eps[3 * p + a] = v[a] * sc;
+  }
+  *n_valid = nv;
+}
+
+/* ------------------------------------------------------------------------------------ */
+/* multi-level trilinear interpolation (Sec. 3.1; Supp. Sec. 1)                           */
+/* ------------------------------------------------------------------------------------ */
+static int64_t level_offset(const oc_config* c, int l) {
+  int64_t o = 0;
+  for (int k = 0; k < l; ++k) o += (int64_t)c->dims[k][0] * c->dims[k][1] * c->dims[k][2] * OC_FEAT;
+  return o;
+}
+static int64_t grid_size(const oc_config* c) { return level_offset(c, OC_LEVELS); }
+
+typedef struct {
+  int64_t corner[8];  /* flat float index of feature 0 of corner c = 4*bx + 2*by + bz */
+  double w[8];        /* w_c(f), Supp. Eq. (coefficient vector) */
+  double dw[8][3];    /* d w_c / d f_a (zero on clamped axes), Supp. Eq. (coeff_jacobian) */
+  double inv_v;       /* 1 / v_l  (d f / d x) */
+} cell_t;
+
+/* Cell and in-cell coordinates of x at level l.  The cell and the clamp flags are decided
+ * in binary32; the fractional coordinate is then taken in FP64. */
+static void locate(const oc_config* c, int l, const float x[3], cell_t* cl, int32_t base_out[3]) {
+  double f[3];
+  int idx[3], clamped[3];
+  for (int a = 0; a < 3; ++a) {
+    int n = c->dims[l][a];
+    float u = (x[a] - c->origin[a]) / c->voxel[l];
+    clamped[a] = 0;
+    if (u < 0.0f) { u = 0.0f; clamped[a] = 1; }
+    else if (u > (float)(n - 1)) { u = (float)(n - 1); clamped[a] = 1; }
+    int i = (int)floorf(u);
+    if (i > n - 2) i = n - 2;
+    idx[a] = i;
+    if (clamped[a]) f[a] = (double)u - (double)i;
+    else f[a] = ((double)x[a] - (double)c->origin[a]) / (double)c->voxel[l] - (double)i;
+    if (base_out) base_out[a] = i;
+  }
+  int nx = c->dims[l][0], ny = c->dims[l][1];
+  int64_t off = level_offset(c, l);
+  for (int cc = 0; cc < 8; ++cc) {
+    int bx = (cc >> 2) & 1, by = (cc >> 1) & 1, bz = cc & 1;
+    int64_t vtx = ((int64_t)(idx[2] + bz) * ny + (idx[1] + by)) * nx + (idx[0] + bx);
+    cl->corner[cc] = off + vtx * OC_FEAT;
+    double wx = bx ? f[0] : 1.0 - f[0], wy = by ? f[1] : 1.0 - f[1], wz = bz ? f[2] : 1.0 - f[2];
+    double sx = bx ? 1.0 : -1.0, sy = by ? 1.0 : -1.0, sz = bz ? 1.0 : -1.0;
+    cl->w[cc] = wx * wy * wz;
+    cl->dw[cc][0] = clamped[0] ? 0.0 : sx * wy * wz;
+    cl->dw[cc][1] = clamped[1] ? 0.0 : wx * sy * wz;
+    cl->dw[cc][2] = clamped[2] ? 0.0 : wx * wy * sz;
+  }
+  cl->inv_v = 1.0 / (double)c->voxel[l];
+}
+
+/* z[16] = [V^0(x), V^1(x), V^2(x), V^3(x)]; optional dz/dx [16][3] */
+static void features(const oc_config* c, const double* theta, const float x[3], cell_t cells[OC_LEVELS],
+                     double z[OC_Z], double dzdx[OC_Z][3]) {
+  for (int l = 0; l < OC_LEVELS; ++l) {
+    locate(c, l, x, &cells[l], NULL);
+    for (int k = 0; k < OC_FEAT; ++k) {
+      double s = 0, g[3] = {0, 0, 0};
+      for (int cc = 0; cc < 8; ++cc) {
+        double th = theta[cells[l].corner[cc] + k];
+        s += cells[l].w[cc] * th;
+        for (int a = 0; a < 3; ++a) g[a] += cells[l].dw[cc][a] * th;
+      }
+      z[OC_FEAT * l + k] = s;
+      if (dzdx)
+        for (int a = 0; a < 3; ++a) dzdx[OC_FEAT * l + k][a] = g[a] * cells[l].inv_v;
+    }
+  }
+}
+
+/* ------------------------------------------------------------------------------------ */
+/* decoders                                                                               */
+/* ------------------------------------------------------------------------------------ */
+typedef struct {
+  const double *W1, *b1, *W2, *b2, *W3, *b3, *W4, *b4, *kappa;
+} mlp_t;
+
+static mlp_t mlp_view(const double* base) {
+  mlp_t m;
+  m.W1 = base;
+  m.b1 = m.W1 + OC_H1 * OC_Z;
+  m.W2 = m.b1 + OC_H1;
+  m.b2 = m.W2 + OC_OUT * OC_H1;
+  m.W3 = m.b2 + OC_OUT;
+  m.b3 = m.W3 + OC_H2 * OC_HF;
+  m.W4 = m.b3 + OC_H2;
+  m.b4 = m.W4 + OC_RGB * OC_H2;
+  m.kappa = m.b4 + OC_RGB;
+  return m;
+}
+
+typedef struct {
+  double z[OC_Z];
+  double y1[OC_H1], a1[OC_H1];
+  double out[OC_OUT]; /* out[0] = phi, out[1..15] = h */
+  double y2[OC_H2], a2[OC_H2];
+  double pre[OC_RGB], c[OC_RGB];
+} act_t;
+
+static double sigm(double x) { return 1.0 / (1.0 + exp(-x)); }
+
+static void decode(const mlp_t* m, act_t* A) {
+  for (int j = 0; j < OC_H1; ++j) {
+    double s = m->b1[j];
+    for (int k = 0; k < OC_Z; ++k) s += m->W1[j * OC_Z + k] * A->z[k];
+    A->y1[j] = s;
+    A->a1[j] = s > 0 ? s : 0;
+  }
+  for (int j = 0; j < OC_OUT; ++j) {
+    double s = m->b2[j];
+    for (int k = 0; k < OC_H1; ++k) s += m->W2[j * OC_H1 + k] * A->a1[k];
+    A->out[j] = s;
+  }
+  for (int j = 0; j < OC_H2; ++j) {
+    double s = m->b3[j];
+    for (int k = 0; k < OC_HF; ++k) s += m->W3[j * OC_HF + k] * A->out[1 + k];
+    A->y2[j] = s;
+    A->a2[j] = s > 0 ? s : 0;
+  }
+  for (int j = 0; j < OC_RGB; ++j) {
+    double s = m->b4[j];
+    for (int k = 0; k < OC_H2; ++k) s += m->W4[j * OC_H2 + k] * A->a2[k];
+    A->pre[j] = s;
+    A->c[j] = sigm(s);
+  }
+}
+
+/* reverse mode of decode(): given dphi and dc, accumulate parameter grads into gm (MLP
+ * block) and return dz */
+static void decode_backward(const mlp_t* m, const act_t* A, double dphi, const double dc[OC_RGB], double* gm,
+                            double dz[OC_Z]) {
+  double* gW1 = gm;
+  double* gb1 = gW1 + OC_H1 * OC_Z;
+  double* gW2 = gb1 + OC_H1;
+  double* gb2 = gW2 + OC_OUT * OC_H1;
+  double* gW3 = gb2 + OC_OUT;
+  double* gb3 = gW3 + OC_H2 * OC_HF;
+  double* gW4 = gb3 + OC_H2;
+  double* gb4 = gW4 + OC_RGB * OC_H2;
+  double dpre[OC_RGB], da2[OC_H2], dy2[OC_H2], dout[OC_OUT], da1[OC_H1], dy1[OC_H1];
+  for (int j = 0; j < OC_RGB; ++j) dpre[j] = dc[j] * A->c[j] * (1.0 - A->c[j]);
+  for (int j = 0; j < OC_RGB; ++j) {
+    gb4[j] += dpre[j];
+    for (int k = 0; k < OC_H2; ++k) gW4[j * OC_H2 + k] += dpre[j] * A->a2[k];
+  }
+  for (int k = 0; k < OC_H2; ++k) {
+    double s = 0;
+    for (int j = 0; j < OC_RGB; ++j) s += m->W4[j * OC_H2 + k] * dpre[j];
+    da2[k] = s;
+    dy2[k] = A->y2[k] > 0 ? s : 0;
+  }
+  for (int j = 0; j < OC_H2; ++j) {
+    gb3[j] += dy2[j];
+    for (int k = 0; k < OC_HF; ++k) gW3[j * OC_HF + k] += dy2[j] * A->out[1 + k];
+  }
+  dout[0] = dphi;
+  for (int k = 0; k < OC_HF; ++k) {
+    double s = 0;
+    for (int j = 0; j < OC_H2; ++j) s += m->W3[j * OC_HF + k] * dy2[j];
+    dout[1 + k] = s;
+  }
+  for (int j = 0; j < OC_OUT; ++j) {
+    gb2[j] += dout[j];
+    for (int k = 0; k < OC_H1; ++k) gW2[j * OC_H1 + k] += dout[j] * A->a1[k];
+  }
+  for (int k = 0; k < OC_H1; ++k) {
+    double s = 0;
+    for (int j = 0; j < OC_OUT; ++j) s += m->W2[j * OC_H1 + k] * dout[j];
+    da1[k] = s;
+    dy1[k] = A->y1[k] > 0 ? s : 0;
+  }
+  for (int j = 0; j < OC_H1; ++j) {
+    gb1[j] += dy1[j];
+    for (int k = 0; k < OC_Z; ++k) gW1[j * OC_Z + k] += dy1[j] * A->z[k];
+  }
+  for (int k = 0; k < OC_Z; ++k) {
+    double s = 0;
+    for (int j = 0; j < OC_H1; ++j) s += m->W1[j * OC_Z + k] * dy1[j];
+    dz[k] = s;
+  }
+  (void)da2;
+  (void)da1;
+}
+
+/* p = d phi / d z = W1^T (m (.) W2[0,:]^T), m = 1[y1 > 0] (ReLU => piecewise linear) */
+static void dphi_dz(const mlp_t* m, const act_t* A, double p[OC_Z], double mw2[OC_H1]) {
+  for (int j = 0; j < OC_H1; ++j) mw2[j] = A->y1[j] > 0 ? m->W2[j] : 0.0; /* row 0 of W2 */
+  for (int k = 0; k < OC_Z; ++k) {
+    double s = 0;
+    for (int j = 0; j < OC_H1; ++j) s += m->W1[j * OC_Z + k] * mw2[j];
+    p[k] = s;
+  }
+}
+
+/* ------------------------------------------------------------------------------------ */
+/* query: phi(x) and grad_x phi(x) (Supp. Eq. sdf_first_grad)                            */
+/* ------------------------------------------------------------------------------------ */
+void oc_query_sdf(const oc_config* c, const double* theta, const float* x, int P, double* sdf, double* grad) {
+  mlp_t m = mlp_view(theta + grid_size(c));
+#pragma omp parallel for schedule(static)
+  for (int i = 0; i < P; ++i) {
+    cell_t cells[OC_LEVELS];
+    act_t A;
+    double dzdx[OC_Z][3];
+    features(c, theta, x + 3 * i, cells, A.z, dzdx);
+    decode(&m, &A);
+    sdf[i] = A.out[0];
+    if (grad) {
+      double p[OC_Z], mw2[OC_H1];
+      dphi_dz(&m, &A, p, mw2);
+      for (int a = 0; a < 3; ++a) {
+        double s = 0;
+        for (int k = 0; k < OC_Z; ++k) s += p[k] * dzdx[k][a];
+        grad[3 * i + a] = s;
+      }
+    }
+  }
+}
+
+/* base vertex (cell) index per level, binary32 decision; out [P][4] flat vertex ids */
+void oc_voxel_index(const oc_config* c, const float* x, int P, int64_t* out) {
+  for (int i = 0; i < P; ++i)
+    for (int l = 0; l < OC_LEVELS; ++l) {
+      cell_t cl;
+      int32_t b[3];
+      locate(c, l, x + 3 * i, &cl, b);
+      out[(size_t)OC_LEVELS * i + l] = ((int64_t)b[2] * c->dims[l][1] + b[1]) * c->dims[l][0] + b[0];
+    }
+}
+
+/* trilinear pieces of one cell, for tests of Supp. Sec. 1: w[8], J[8][3] at f */
+void oc_trilinear_coeffs(const double f[3], double w[8], double J[8][3]) {
+  for (int cc = 0; cc < 8; ++cc) {
+    int bx = (cc >> 2) & 1, by = (cc >> 1) & 1, bz = cc & 1;
+    double wx = bx ? f[0] : 1 - f[0], wy = by ? f[1] : 1 - f[1], wz = bz ? f[2] : 1 - f[2];
+    w[cc] = wx * wy * wz;
+    J[cc][0] = (bx ? 1.0 : -1.0) * wy * wz;
+    J[cc][1] = wx * (by ? 1.0 : -1.0) * wz;
+    J[cc][2] = wx * wy * (bz ? 1.0 : -1.0);
+  }
+}
+
+/* second x-derivatives of f = theta^T w(x) in cell coordinates: the off-diagonal entries
+ * h12, h13, h23 (the diagonal is zero), obtained by differentiating each column of J
+ * once more; used by the pose-refinement path and by tests */
+void oc_trilinear_hessian(const double theta8[8], const double f[3], double h[3]) {
+  double H[3][3] = {{0}};
+  for (int cc = 0; cc < 8; ++cc) {
+    int b[3] = {(cc >> 2) & 1, (cc >> 1) & 1, cc & 1};
+    double lin[3], sgn[3];
+    for (int a = 0; a < 3; ++a) {
+      lin[a] = b[a] ? f[a] : 1 - f[a];
+      sgn[a] = b[a] ? 1.0 : -1.0;
+    }
+    for (int a = 0; a < 3; ++a)
+      for (int d = 0; d < 3; ++d) {
+        if (a == d) continue;
+        int e = 3 - a - d;
+        H[a][d] += theta8[cc] * sgn[a] * sgn[d] * lin[e];
+      }
+  }
+  h[0] = H[0][1];
+  h[1] = H[0][2];
+  h[2] = H[1][2];
+}
+
+/* ------------------------------------------------------------------------------------ */
+/* volume rendering along one ray (Sec. 3.2, Eq. volume_rendering / volume_rendering_alpha) */
+/* ------------------------------------------------------------------------------------ */
+/* Phi_i = sigma_s(phi_i) = 1/(1+exp(-s phi_i));
+ * alpha_i = max((Phi_i - Phi_{i+1}) / max(Phi_i, 1e-6), 0) for i < N, alpha_N = 0;
+ * T_i = prod_{j<i} (1 - alpha_j);  w_i = T_i alpha_i;
+ * c_hat = sum_i w_i c_i;  d_hat = sum_i w_i d_i;  wsum = sum_i w_i. */
+static void composite(int N, const double* phi, double s, const act_t* A, const float* d, double* Phi,
+                      double* alpha, double* T, double* w, double ch[3], double* dh, double* ws) {
+  for (int k = 0; k < N; ++k) Phi[k] = sigm(s * phi[k]);
+  for (int k = 0; k < N; ++k) {
+    if (k == N - 1) {
+      alpha[k] = 0;
+      continue;
+    }
+    double den = Phi[k] > 1e-6 ? Phi[k] : 1e-6;
+    double q = (Phi[k] - Phi[k + 1]) / den;
+    alpha[k] = q > 0 ? q : 0;
+  }
+  double Tk = 1.0;
+  ch[0] = ch[1] = ch[2] = 0;
+  *dh = 0;
+  *ws = 0;
+  for (int k = 0; k < N; ++k) {
+    T[k] = Tk;
+    w[k] = Tk * alpha[k];
+    if (A)
+      for (int j = 0; j < 3; ++j) ch[j] += w[k] * A[k].c[j];
+    *dh += w[k] * (double)d[k];
+    *ws += w[k];
+    Tk *= 1.0 - alpha[k];
+  }
+}
+
+/* test access to the renderer alone: phi[N], d[N] -> alpha[N], T[N], w[N], d_hat, wsum */
+void oc_composite(int N, const double* phi, double s, const float* d, double* alpha, double* T, double* w,
+                  double* d_hat, double* wsum) {
+  double* Phi = (double*)malloc(sizeof(double) * N);
+  double ch[3];
+  composite(N, phi, s, NULL, d, Phi, alpha, T, w, ch, d_hat, wsum);
+  free(Phi);
+}
+
+/* ------------------------------------------------------------------------------------ */
+/* one optimisation step: losses (Sec. 3.2-3.4) and their gradients                     */
+/* ------------------------------------------------------------------------------------ */
+static double sgn(double v) { return v > 0 ? 1.0 : (v < 0 ? -1.0 : 0.0); }
+
+/* margins[8]: distance of this evaluation from every branch point, for gradient tests:
+ *  0 min |hidden pre-activation| (both decoders, main samples and smoothness points)
+ *  1 min |Phi_i - Phi_{i+1}| / max(Phi_i,1e-6) over i < N
+ *  2 min |Phi_i - 1e-6|
+ *  3 min |phi - b| over S_tr
+ *  4 min gap between the largest and second largest entry of the free-space max over S_fs
+ *  5 min |d_hat - D| over rays with D > 0
+ *  6 min |hidden pre-activation| at smoothness points (also folded into 0)
+ *  7 signature of every branch decision taken (52-bit hash, as a double): two
+ *    evaluations with equal signatures lie on the same smooth piece of the loss */
+typedef struct {
+  double m[8];
+  uint64_t sig;
+} margins_t;
+static void sigmix(uint64_t* sig, uint64_t id, uint64_t val) { *sig ^= sm64(id * 0x9E3779B97F4A7C15ULL + val); }
+static uint64_t relu_mask(const double* y, int n) {
+  uint64_t b = 0;
+  for (int j = 0; j < n; ++j) b |= (uint64_t)(y[j] > 0) << j;
+  return b;
+}
+static void mmin(double* a, double v) {
+  v = fabs(v);
+  if (v < *a) *a = v;
+}
+
+/*
+ * Forward (and, if grad != NULL, backward) of one step on a given batch.
+ * theta: flat parameters (grid levels 0..3 as [nz][ny][nx][4], then the 1684-entry
+ * decoder block W1,b1,W2,b2,W3,b3,W4,b4,kappa).  Batch arrays as produced by the samplers.
+ * dloss[6]: upstream derivative of each output (rgb, depth, sdf, fs, smooth, total); the
+ * effective weight of term k is dloss[k] + lam[k] * dloss[5].  NULL means (0,..,0,1).
+ * loss[6]: L_rgb, L_d, L_sdf, L_fs, L_smooth, total.  rgb_hat[R,3], d_hat[R], wsum[R] may be
+ * NULL.  grad: same layout as theta, overwritten.  margins[8] may be NULL.
+ * Returns 0, or -1 on a bad argument.
+ */
+int oc_step(const oc_config* c, const double* theta, int R, int N, const float* o, const float* r,
+            const float* rgb, const float* D, const float* t, const uint8_t* cls, int P, const float* xs,
+            const float* eps, const uint8_t* valid, const double* dloss, double* loss, double* rgb_hat,
+            double* d_hat, double* wsum, double* grad, double* margins) {
+  if (R < 0 || N < 2 || P < 0) return -1;
+  const int64_t ng = grid_size(c);
+  mlp_t m = mlp_view(theta + ng);
+  const double s = exp(*m.kappa);
+
+  /* set sizes for the batch normalisations */
+  int64_t n_d = 0, n_tr = 0, n_fs = 0, n_g = 0;
+  for (int i = 0; i < R; ++i) {
+    n_d += D[i] > 0.0f;
+    for (int k = 0; k < N; ++k) {
+      n_tr += cls[(size_t)i * N + k] == CLS_TR;
+      n_fs += cls[(size_t)i * N + k] == CLS_FS;
+    }
+  }
+  for (int p = 0; p < P; ++p) n_g += valid[p] != 0;
+
+  double wt[5];
+  for (int k = 0; k < 5; ++k) wt[k] = dloss ? dloss[k] + (double)c->lam[k] * dloss[5] : (double)c->lam[k];
+  const int do_grad = grad != NULL;
+
+  int nthreads = 1;
+#ifdef _OPENMP
+  nthreads = omp_get_max_threads();
+#endif
+  double* gm_all = (double*)calloc((size_t)nthreads * OC_MLP, sizeof(double));
+  double* lsum_all = (double*)calloc((size_t)nthreads * 5, sizeof(double));
+  margins_t* mg_all = (margins_t*)malloc(sizeof(margins_t) * nthreads);
+  for (int th = 0; th < nthreads; ++th) {
+    for (int k = 0; k < 8; ++k) mg_all[th].m[k] = INFINITY;
+    mg_all[th].sig = 0;
+  }
+  /* per-sample dL/dz, scattered into the grid afterwards in sample order */
+  double* dz_all = do_grad ? (double*)malloc(sizeof(double) * (size_t)R * N * OC_Z) : NULL;
+  double* dzs_all = do_grad ? (double*)malloc(sizeof(double) * (size_t)(P > 0 ? P : 1) * 2 * 8 * OC_LEVELS * OC_FEAT) : NULL;
+
+#pragma omp parallel
+  {
+    int th = 0;
+#ifdef _OPENMP
+    th = omp_get_thread_num();
+#endif
+    double* gm = gm_all + (size_t)th * OC_MLP;
+    double* lsum = lsum_all + (size_t)th * 5;
+    margins_t* mg = mg_all + th;
+    act_t* A = (act_t*)malloc(sizeof(act_t) * N);
+    cell_t* cells = (cell_t*)malloc(sizeof(cell_t) * N * OC_LEVELS);
+    double *phi = malloc(sizeof(double) * N), *Phi = malloc(sizeof(double) * N), *alpha = malloc(sizeof(double) * N),
+           *T = malloc(sizeof(double) * N), *w = malloc(sizeof(double) * N), *U = malloc(sizeof(double) * N),
+           *dPhi = malloc(sizeof(double) * N);
+
+#pragma omp for schedule(static)
+    for (int i = 0; i < R; ++i) {
+      const float* ti = t + (size_t)i * N;
+      /* samples x_i = o + d_i r (binary32), features, decoders */
+      for (int k = 0; k < N; ++k) {
+        float x[3];
+        for (int a = 0; a < 3; ++a) {
+          float step_ = ti[k] * r[3 * i + a];
+          x[a] = o[3 * i + a] + step_;
+        }
+        features(c, theta, x, cells + (size_t)k * OC_LEVELS, A[k].z, NULL);
+        decode(&m, &A[k]);
+        phi[k] = A[k].out[0];
+        for (int j = 0; j < OC_H1; ++j) mmin(&mg->m[0], A[k].y1[j]);
+        for (int j = 0; j < OC_H2; ++j) mmin(&mg->m[0], A[k].y2[j]);
+        uint64_t sid = ((uint64_t)i * (uint64_t)N + (uint64_t)k) * 8;
+        sigmix(&mg->sig, sid + 0, relu_mask(A[k].y1, OC_H1));
+        sigmix(&mg->sig, sid + 1, relu_mask(A[k].y2, OC_H2));
+      }
+      /* NeuS weights and expected colour / depth (Sec. 3.2) */
+      double ch[3], dh, ws;
+      composite(N, phi, s, A, ti, Phi, alpha, T, w, ch, &dh, &ws);
+      for (int k = 0; k + 1 < N; ++k) {
+        double den = Phi[k] > 1e-6 ? Phi[k] : 1e-6;
+        if (phi[k] != phi[k + 1]) mmin(&mg->m[1], (Phi[k] - Phi[k + 1]) / den);
+        mmin(&mg->m[2], Phi[k] - 1e-6);
+        uint64_t sid = ((uint64_t)i * (uint64_t)N + (uint64_t)k) * 8;
+        sigmix(&mg->sig, sid + 2, (uint64_t)(alpha[k] > 0) | (uint64_t)(Phi[k] > 1e-6) << 1);
+      }
+      if (rgb_hat)
+        for (int j = 0; j < 3; ++j) rgb_hat[3 * i + j] = ch[j];
+      if (d_hat) d_hat[i] = dh;
+      if (wsum) wsum[i] = ws;
+      /* rendering losses */
+      double lr = 0;
+      for (int j = 0; j < 3; ++j) {
+        double e = (double)rgb[3 * i + j] - ch[j];
+        lr += e * e;
+      }
+      lsum[0] += lr;
+      const double Di = (double)D[i];
+      if (D[i] > 0.0f) {
+        lsum[1] += fabs(Di - dh);
+        mmin(&mg->m[5], dh - Di);
+        sigmix(&mg->sig, ((uint64_t)i * (uint64_t)N) * 8 + 7, (uint64_t)(dh > Di));
+      }
+      /* approximate SDF supervision (Sec. 3.3) */
+      for (int k = 0; k < N; ++k) {
+        int cl = cls[(size_t)i * N + k];
+        double b = Di - (double)ti[k];
+        if (cl == CLS_TR) {
+          lsum[2] += fabs(phi[k] - b);
+          mmin(&mg->m[3], phi[k] - b);
+          sigmix(&mg->sig, ((uint64_t)i * (uint64_t)N + (uint64_t)k) * 8 + 3, (uint64_t)(phi[k] > b));
+        } else if (cl == CLS_FS) {
+          double e = exp(-(double)c->kappa_fs * phi[k]) - 1.0, lin = phi[k] - b;
+          double v[3] = {0.0, e, lin};
+          int arg = 0;
+          for (int q = 1; q < 3; ++q)
+            if (v[q] > v[arg]) arg = q;
+          double top = v[arg], second = -INFINITY;
+          for (int q = 0; q < 3; ++q)
+            if (q != arg && v[q] > second) second = v[q];
+          mmin(&mg->m[4], top - second);
+          sigmix(&mg->sig, ((uint64_t)i * (uint64_t)N + (uint64_t)k) * 8 + 4, (uint64_t)arg);
+          lsum[3] += top;
+        }
+      }
+      if (!do_grad) continue;
+
+      /* ---------------- backward ---------------- */
+      double gc[3], gd = 0;
+      for (int j = 0; j < 3; ++j) gc[j] = wt[0] / (double)R * 2.0 * (ch[j] - (double)rgb[3 * i + j]);
+      if (D[i] > 0.0f && n_d > 0) gd = wt[1] / (double)n_d * sgn(dh - Di);
+      /* dL/dalpha_k = T_k (e_k - U_k), U_{N-1} = 0, U_{k-1} = alpha_k e_k + (1 - alpha_k) U_k */
+      U[N - 1] = 0;
+      for (int k = N - 1; k >= 1; --k) {
+        double ek = gc[0] * A[k].c[0] + gc[1] * A[k].c[1] + gc[2] * A[k].c[2] + gd * (double)ti[k];
+        U[k - 1] = alpha[k] * ek + (1.0 - alpha[k]) * U[k];
+      }
+      for (int k = 0; k < N; ++k) dPhi[k] = 0;
+      for (int k = 0; k < N - 1; ++k) {
+        double ek = gc[0] * A[k].c[0] + gc[1] * A[k].c[1] + gc[2] * A[k].c[2] + gd * (double)ti[k];
+        double dalpha = T[k] * (ek - U[k]);
+        double den = Phi[k] > 1e-6 ? Phi[k] : 1e-6;
+        double q = (Phi[k] - Phi[k + 1]) / den;
+        if (q > 0) {
+          dPhi[k + 1] += dalpha * (-1.0 / den);
+          if (Phi[k] > 1e-6) dPhi[k] += dalpha * (Phi[k + 1] / (Phi[k] * Phi[k]));
+          else dPhi[k] += dalpha * (1.0 / 1e-6);
+        }
+      }
+      double* gkappa = gm + (OC_MLP - 1);
+      for (int k = 0; k < N; ++k) {
+        double dsig = Phi[k] * (1.0 - Phi[k]);
+        double dphi = dPhi[k] * s * dsig;
+        *gkappa += dPhi[k] * dsig * s * phi[k];
+        int cl = cls[(size_t)i * N + k];
+        double b = Di - (double)ti[k];
+        if (cl == CLS_TR && n_tr > 0) dphi += wt[2] / (double)n_tr * sgn(phi[k] - b);
+        if (cl == CLS_FS && n_fs > 0) {
+          double e = exp(-(double)c->kappa_fs * phi[k]) - 1.0, lin = phi[k] - b;
+          int arg = 0;
+          double top = 0;
+          if (e > top) { top = e; arg = 1; }
+          if (lin > top) { arg = 2; }
+          double dd = arg == 1 ? -(double)c->kappa_fs * (e + 1.0) : (arg == 2 ? 1.0 : 0.0);
+          dphi += wt[3] / (double)n_fs * dd;
+        }
+        double dc[3];
+        for (int j = 0; j < 3; ++j) dc[j] = w[k] * gc[j];
+        double* dz = dz_all + ((size_t)i * N + k) * OC_Z;
+        decode_backward(&m, &A[k], dphi, dc, gm, dz);
+      }
+    }
+
+    /* ------------- smoothness on S_g (Sec. 3.3, Supp. Sec. 1) ------------- */
+#pragma omp for schedule(static)
+    for (int p = 0; p < P; ++p) {
+      if (!valid[p]) continue;
+      float y[2][3];
+      for (int a = 0; a < 3; ++a) {
+        y[0][a] = xs[3 * p + a];
+        y[1][a] = xs[3 * p + a] + eps[3 * p + a];
+      }
+      cell_t cl[2][OC_LEVELS];
+      act_t Ay[2];
+      double dzdx[2][OC_Z][3], pz[2][OC_Z], mw2[2][OC_H1], g[2][3];
+      for (int e = 0; e < 2; ++e) {
+        features(c, theta, y[e], cl[e], Ay[e].z, dzdx[e]);
+        decode(&m, &Ay[e]);
+        for (int j = 0; j < OC_H1; ++j) {
+          mmin(&mg->m[6], Ay[e].y1[j]);
+          mmin(&mg->m[0], Ay[e].y1[j]);
+        }
+        sigmix(&mg->sig, ((uint64_t)1 << 60) + (uint64_t)p * 2 + e, relu_mask(Ay[e].y1, OC_H1));
+        dphi_dz(&m, &Ay[e], pz[e], mw2[e]);
+        for (int a = 0; a < 3; ++a) {
+          double sacc = 0;
+          for (int k = 0; k < OC_Z; ++k) sacc += pz[e][k] * dzdx[e][k][a];
+          g[e][a] = sacc;
+        }
+      }
+      double dg[3], l2 = 0;
+      for (int a = 0; a < 3; ++a) {
+        dg[a] = g[0][a] - g[1][a];
+        l2 += dg[a] * dg[a];
+      }
+      lsum[4] += l2;
+      if (!do_grad || n_g == 0) continue;
+      double* gW1 = gm;
+      double* gW2 = gm + OC_H1 * OC_Z + OC_H1;
+      for (int e = 0; e < 2; ++e) {
+        /* adjoint of g at this point: a = dL/dg */
+        double av[3];
+        for (int a = 0; a < 3; ++a) av[a] = (e == 0 ? 1.0 : -1.0) * wt[4] / (double)n_g * 2.0 * dg[a];
+        /* j_k = a . dz_k/dx ; direct theta term p_k (1/v) (a . dw_c/df) */
+        double jv[OC_Z];
+        for (int k = 0; k < OC_Z; ++k) jv[k] = av[0] * dzdx[e][k][0] + av[1] * dzdx[e][k][1] + av[2] * dzdx[e][k][2];
+        double* dzs = dzs_all + ((size_t)p * 2 + e) * 8 * OC_LEVELS * OC_FEAT;
+        for (int l = 0; l < OC_LEVELS; ++l)
+          for (int cc = 0; cc < 8; ++cc) {
+            double ad = (av[0] * cl[e][l].dw[cc][0] + av[1] * cl[e][l].dw[cc][1] + av[2] * cl[e][l].dw[cc][2]) *
+                        cl[e][l].inv_v;
+            for (int k = 0; k < OC_FEAT; ++k) dzs[(l * 8 + cc) * OC_FEAT + k] = pz[e][OC_FEAT * l + k] * ad;
+          }
+        /* decoder terms: a.g = w2^T (m (.) (W1 j)) */
+        double W1j[OC_H1];
+        for (int h = 0; h < OC_H1; ++h) {
+          double sacc = 0;
+          for (int k = 0; k < OC_Z; ++k) sacc += m.W1[h * OC_Z + k] * jv[k];
+          W1j[h] = sacc;
+        }
+        for (int h = 0; h < OC_H1; ++h) {
+          if (!(Ay[e].y1[h] > 0)) continue;
+          for (int k = 0; k < OC_Z; ++k) gW1[h * OC_Z + k] += m.W2[h] * jv[k];
+          gW2[h] += W1j[h];
+        }
+      }
+    }
+    free(A);
+    free(cells);
+    free(phi);
+    free(Phi);
+    free(alpha);
+    free(T);
+    free(w);
+    free(U);
+    free(dPhi);
+  }
+
+  double lsum[5] = {0, 0, 0, 0, 0};
+  for (int th = 0; th < nthreads; ++th)
+    for (int k = 0; k < 5; ++k) lsum[k] += lsum_all[(size_t)th * 5 + k];
+  loss[0] = R > 0 ? lsum[0] / (double)R : 0.0;
+  loss[1] = n_d > 0 ? lsum[1] / (double)n_d : 0.0;
+  loss[2] = n_tr > 0 ? lsum[2] / (double)n_tr : 0.0;
+  loss[3] = n_fs > 0 ? lsum[3] / (double)n_fs : 0.0;
+  loss[4] = n_g > 0 ? lsum[4] / (double)n_g : 0.0;
+  loss[5] = 0;
+  for (int k = 0; k < 5; ++k) loss[5] += (double)c->lam[k] * loss[k];
+
+  if (margins) {
+    uint64_t sig = 0;
+    for (int k = 0; k < 8; ++k) margins[k] = INFINITY;
+    for (int th = 0; th < nthreads; ++th) {
+      for (int k = 0; k < 7; ++k)
+        if (mg_all[th].m[k] < margins[k]) margins[k] = mg_all[th].m[k];
+      sig ^= mg_all[th].sig;
+    }
+    margins[7] = (double)(sig & ((1ULL << 52) - 1));
+  }
+
+  if (do_grad) {
+    const int64_t ntot = ng + OC_MLP;
+    memset(grad, 0, sizeof(double) * (size_t)ntot);
+    for (int th = 0; th < nthreads; ++th)
+      for (int k = 0; k < OC_MLP; ++k) grad[ng + k] += gm_all[(size_t)th * OC_MLP + k];
+    /* scatter dL/dz of every main sample into the 8 corners of its cell at each level */
+    for (int i = 0; i < R; ++i) {
+      const float* ti = t + (size_t)i * N;
+      for (int k = 0; k < N; ++k) {
+        float x[3];
+        for (int a = 0; a < 3; ++a) {
+          float step_ = ti[k] * r[3 * i + a];
+          x[a] = o[3 * i + a] + step_;
+        }
+        const double* dz = dz_all + ((size_t)i * N + k) * OC_Z;
+        for (int l = 0; l < OC_LEVELS; ++l) {
+          cell_t cl;
+          locate(c, l, x, &cl, NULL);
+          for (int cc = 0; cc < 8; ++cc)
+            for (int f = 0; f < OC_FEAT; ++f) grad[cl.corner[cc] + f] += cl.w[cc] * dz[OC_FEAT * l + f];
+        }
+      }
+    }
+    /* smoothness: direct d/dtheta of grad_x phi */
+    if (n_g > 0)
+      for (int p = 0; p < P; ++p) {
+        if (!valid[p]) continue;
+        for (int e = 0; e < 2; ++e) {
+          float y[3];
+          for (int a = 0; a < 3; ++a) y[a] = e == 0 ? xs[3 * p + a] : xs[3 * p + a] + eps[3 * p + a];
+          const double* dzs = dzs_all + ((size_t)p * 2 + e) * 8 * OC_LEVELS * OC_FEAT;
+          for (int l = 0; l < OC_LEVELS; ++l) {
+            cell_t cl;
+            locate(c, l, y, &cl, NULL);
+            for (int cc = 0; cc < 8; ++cc)
+              for (int f = 0; f < OC_FEAT; ++f) grad[cl.corner[cc] + f] += dzs[(l * 8 + cc) * OC_FEAT + f];
+          }
+        }
+      }
+  }
+  free(gm_all);
+  free(lsum_all);
+  free(mg_all);
+  free(dz_all);
+  free(dzs_all);
+  return 0;
+}
+
+/* ------------------------------------------------------------------------------------ */
+/* Adam (Kingma & Ba 2015), per-group learning rates (Sec. 4 Implementation Details)     */
+/* ------------------------------------------------------------------------------------ */
+/* entries [0, n_grid) use lr_grid, the rest lr_mlp; t >= 1 is the step count; g is zeroed */
+void oc_adam(double* p, double* g, double* mom, double* vel, int64_t n, int64_t n_grid, int t, double lr_grid,
+             double lr_mlp, double b1, double b2, double eps) {
+  double bc1 = 1.0 - pow(b1, (double)t), bc2 = 1.0 - pow(b2, (double)t);
+#pragma omp parallel for schedule(static)
+  for (int64_t i = 0; i < n; ++i) {
+    double lr = i < n_grid ? lr_grid : lr_mlp;
+    mom[i] = b1 * mom[i] + (1.0 - b1) * g[i];
+    vel[i] = b2 * vel[i] + (1.0 - b2) * g[i] * g[i];
+    double mh = mom[i] / bc1, vh = vel[i] / bc2;
+    p[i] -= lr * mh / (sqrt(vh) + eps);
+    g[i] = 0.0;
+  }
+}
+
+int oc_num_threads(void) {
+#ifdef _OPENMP
+  return omp_get_max_threads();
+#else
+  return 1;
+#endif
+}

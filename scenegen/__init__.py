@@ -1,0 +1,387 @@
+"""Seeded synthetic inputs shared by the CUDA path's tests, the bench and the CPU oracle.
+
+This package makes inputs only: scene primitives, posed RGB-D frames rendered by exact
+ray casting of those primitives, workload configurations and seeded parameter
+initialisations.  It contains no step of the reconstruction method (no feature-grid
+interpolation, decoding, volume rendering, loss or update), so the CUDA library and the
+oracle stay independent of each other while reading identical inputs.
+
+Workloads stand in for the paper's datasets (ScanNet and the Neural RGB-D synthetic
+scenes are not available here): a 2.56 m cube with a sphere and a box seen by one
+160x120 camera, and an 8x6x3 m room built from seeded primitives seen along a smooth
+1000-pose trajectory at 640x480, the room scale of the paper's performance table.
+"""
+from __future__ import annotations
+
+import ctypes
+import math
+import os
+import subprocess
+import threading
+from dataclasses import dataclass, field
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_BUILD = os.path.join(_HERE, "_build")
+_LIB = None
+_LOCK = threading.Lock()
+
+SEED_SCENE, SEED_TRAJ, SEED_RAYS, SEED_INIT = 1, 2, 3, 4
+
+MLP_SHAPES = [("W1", (32, 16)), ("b1", (32,)), ("W2", (16, 32)), ("b2", (16,)),
+              ("W3", (32, 15)), ("b3", (32,)), ("W4", (3, 32)), ("b4", (3,)), ("kappa", (1,))]
+MLP_PARAMS = sum(int(np.prod(s)) for _, s in MLP_SHAPES)  # 1684
+FEAT = 4
+LEVELS = 4
+
+
+class _Prim(ctypes.Structure):
+    _fields_ = [("kind", ctypes.c_int32), ("pad", ctypes.c_int32), ("a", ctypes.c_double * 3),
+                ("b", ctypes.c_double * 3), ("r", ctypes.c_double), ("col", ctypes.c_double * 3)]
+
+
+def build(force: bool = False) -> str:
+    """Compile the frame renderer (gcc, OpenMP) into scenegen/_build/; returns the .so path."""
+    os.makedirs(_BUILD, exist_ok=True)
+    so = os.path.join(_BUILD, "libscenegen.so")
+    src = os.path.join(_HERE, "raycast.c")
+    if force or not os.path.exists(so) or os.path.getmtime(so) < os.path.getmtime(src):
+        tmp = so + f".{os.getpid()}.tmp"
+        subprocess.check_call(["gcc", "-O2", "-std=c11", "-fPIC", "-shared", "-fopenmp",
+                               "-ffp-contract=off", src, "-o", tmp, "-lm"])
+        os.replace(tmp, so)
+    return so
+
+
+def _lib():
+    global _LIB
+    with _LOCK:
+        if _LIB is None:
+            lib = ctypes.CDLL(build())
+            lib.sg_render.restype = None
+            lib.sg_render.argtypes = [ctypes.POINTER(_Prim), ctypes.c_int, ctypes.c_int, ctypes.c_void_p,
+                                      ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_double, ctypes.c_double,
+                                      ctypes.c_double, ctypes.c_double, ctypes.c_double, ctypes.c_double,
+                                      ctypes.c_double, ctypes.c_uint64, ctypes.c_void_p, ctypes.c_void_p,
+                                      ctypes.c_void_p]
+            lib.sg_sdf.restype = ctypes.c_double
+            lib.sg_sdf.argtypes = [ctypes.POINTER(_Prim), ctypes.c_int, ctypes.POINTER(ctypes.c_double)]
+            _LIB = lib
+    return _LIB
+
+
+# --------------------------------------------------------------------------------------
+# scenes
+# --------------------------------------------------------------------------------------
+@dataclass
+class Scene:
+    prims: list  # (kind, a, b, r, col)
+    shade_mode: int
+
+    def _array(self):
+        arr = (_Prim * len(self.prims))()
+        for i, (kind, a, b, r, col) in enumerate(self.prims):
+            arr[i].kind = kind
+            arr[i].a[:] = list(a)
+            arr[i].b[:] = list(b)
+            arr[i].r = r
+            arr[i].col[:] = list(col)
+        return arr
+
+    def sdf(self, x) -> np.ndarray:
+        """Exact scene SDF at points x [P,3] (float64)."""
+        x = np.ascontiguousarray(np.asarray(x, dtype=np.float64).reshape(-1, 3))
+        arr = self._array()
+        lib = _lib()
+        out = np.empty(len(x))
+        for i in range(len(x)):
+            out[i] = lib.sg_sdf(arr, len(self.prims), x[i].ctypes.data_as(ctypes.POINTER(ctypes.c_double)))
+        return out
+
+
+def cube_scene() -> Scene:
+    """Sphere r=0.5 m at (-0.4,0,0) and an axis-aligned box (centre (0.55,0,0), half extent 0.3 m)."""
+    return Scene(prims=[(2, (-0.4, 0.0, 0.0), (0, 0, 0), 0.5, (1, 1, 1)),
+                        (1, (0.55, 0.0, 0.0), (0.3, 0.3, 0.3), 0.0, (1, 1, 1))], shade_mode=0)
+
+
+def _ellipse_path(n=256):
+    a = np.linspace(0, 2 * np.pi, n, endpoint=False)
+    return np.stack([4 + 3 * np.cos(a), 3 + 2 * np.sin(a), 1.55 + 0.15 * np.sin(3 * a)], 1)
+
+
+def room_scene(seed: int = SEED_SCENE, size=(8.0, 6.0, 3.0)) -> Scene:
+    """Room interior (floor, ceiling, four walls) plus 20 boxes, 10 spheres and 5 capsules.
+
+    Objects rest on the floor or against a wall and keep clear of the camera trajectory.
+    """
+    rng = np.random.default_rng(seed)
+    sx, sy, sz = size
+    prims = [(0, (sx / 2, sy / 2, sz / 2), (sx / 2, sy / 2, sz / 2), 0.0, (0.8, 0.78, 0.72))]
+    path = _ellipse_path()
+
+    def clear(c, rad):
+        return np.min(np.linalg.norm(path - np.asarray(c)[None], axis=1)) > rad + 0.45
+
+    def colour():
+        return tuple(0.25 + 0.7 * rng.random(3))
+
+    n_box = 0
+    while n_box < 20:
+        h = rng.uniform(0.2, 1.5, 3) / 2
+        if rng.random() < 0.7:  # on the floor
+            c = (rng.uniform(h[0], sx - h[0]), rng.uniform(h[1], sy - h[1]), h[2])
+        else:  # against a wall (x=0 or x=sx), at a seeded height
+            wx = h[0] if rng.random() < 0.5 else sx - h[0]
+            c = (wx, rng.uniform(h[1], sy - h[1]), rng.uniform(h[2], sz - h[2]))
+        if clear(c, float(np.linalg.norm(h))):
+            prims.append((1, c, tuple(h), 0.0, colour()))
+            n_box += 1
+    n_sph = 0
+    while n_sph < 10:
+        r = rng.uniform(0.15, 0.5)
+        c = (rng.uniform(r, sx - r), rng.uniform(r, sy - r), r if rng.random() < 0.6 else rng.uniform(r, sz - r))
+        if clear(c, r):
+            prims.append((2, c, (0, 0, 0), r, colour()))
+            n_sph += 1
+    n_cap = 0
+    while n_cap < 5:
+        r = rng.uniform(0.05, 0.2)
+        L = rng.uniform(0.3, 1.5)
+        if rng.random() < 0.5:  # standing on the floor
+            x, y = rng.uniform(r, sx - r), rng.uniform(r, sy - r)
+            a, b = (x, y, r), (x, y, r + L)
+        else:  # lying on the floor along x or y
+            if rng.random() < 0.5:
+                x, y = rng.uniform(r, sx - r - L), rng.uniform(r, sy - r)
+                a, b = (x, y, r), (x + L, y, r)
+            else:
+                x, y = rng.uniform(r, sx - r), rng.uniform(r, sy - r - L)
+                a, b = (x, y, r), (x, y + L, r)
+        mid = tuple((np.asarray(a) + np.asarray(b)) / 2)
+        if clear(mid, L / 2 + r):
+            prims.append((3, a, b, r, colour()))
+            n_cap += 1
+    return Scene(prims=prims, shade_mode=1)
+
+
+# --------------------------------------------------------------------------------------
+# cameras
+# --------------------------------------------------------------------------------------
+def look_at(pos, target, up=(0.0, 0.0, 1.0)) -> np.ndarray:
+    """c2w [3,4] for an OpenCV camera (x right, y down, z forward) at pos looking at target."""
+    pos, target, up = (np.asarray(v, dtype=np.float64) for v in (pos, target, up))
+    fwd = target - pos
+    fwd /= np.linalg.norm(fwd)
+    right = np.cross(fwd, up)
+    if np.linalg.norm(right) < 1e-9:
+        right = np.cross(fwd, np.array([0.0, 1.0, 0.0]))
+    right /= np.linalg.norm(right)
+    down = np.cross(fwd, right)
+    return np.concatenate([np.stack([right, down, fwd], 1), pos[:, None]], 1)
+
+
+def cube_poses(seed: int = SEED_TRAJ, n: int = 1) -> np.ndarray:
+    """Seeded camera positions on the radius-1.1 m sphere, looking at the origin."""
+    rng = np.random.default_rng(seed)
+    out = []
+    for _ in range(n):
+        v = rng.normal(size=3)
+        v /= np.linalg.norm(v)
+        out.append(look_at(1.1 * v, (0, 0, 0), up=(0, 0, 1) if abs(v[2]) < 0.95 else (0, 1, 0)))
+    return np.stack(out)
+
+
+def room_poses(n: int = 1000, seed: int = SEED_TRAJ) -> np.ndarray:
+    """Smooth closed trajectory: ellipse of radii 3x2 m at 1.4-1.7 m height, look-at point
+    orbiting the room centre, plus seeded low-frequency jitter."""
+    rng = np.random.default_rng(seed)
+    amp = rng.uniform(0.01, 0.04, (3, 3))
+    ph = rng.uniform(0, 2 * np.pi, (3, 3))
+    ps = rng.uniform(0, 2 * np.pi, 2)
+    out = []
+    for k in range(n):
+        a = 2 * np.pi * k / n
+        jit = np.array([sum(amp[m, ax] * np.sin((m + 1) * 2 * a + ph[m, ax]) for m in range(3)) for ax in range(3)])
+        pos = np.array([4 + 3 * np.cos(a), 3 + 2 * np.sin(a), 1.55 + 0.15 * np.sin(3 * a)]) + jit
+        tgt = np.array([4 + 1.2 * np.cos(2 * a + ps[0]), 3 + 0.8 * np.sin(2 * a + ps[1]), 0.8 + 0.2 * np.sin(a)])
+        out.append(look_at(pos, tgt))
+    return np.stack(out)
+
+
+# --------------------------------------------------------------------------------------
+# workloads
+# --------------------------------------------------------------------------------------
+def grid_dims(extent_min, extent_max, voxels):
+    """Vertex counts per level (nx, ny, nz): ceil(E / v) + 1 per axis, vertex-aligned grid."""
+    dims = []
+    for v in voxels:
+        dims.append(tuple(int(math.ceil((hi - lo) / v - 1e-6)) + 1 for lo, hi in zip(extent_min, extent_max)))
+    return dims
+
+
+@dataclass
+class Workload:
+    name: str
+    extent_min: tuple
+    extent_max: tuple
+    voxels: tuple           # level 0 (coarsest) .. 3 (finest), metres
+    rays: int
+    n_strat: int
+    n_guided: int
+    near: float
+    far: float
+    frames: int
+    height: int
+    width: int
+    fx: float
+    fy: float
+    cx: float
+    cy: float
+    scene: str              # "cube" | "room"
+    noise_k: float = 0.0
+    drop_p: float = 0.0
+    blob_frac: float = 0.0
+    trunc: float = 0.10
+    guide_half: float = 0.10
+    kappa_fs: float = 5.0
+    lambdas: tuple = (10.0, 1.0, 10.0, 1.0, 1.0)  # rgb, depth, sdf, fs, smooth
+    n_smooth: int = 4096
+    delta_s: float = 0.004
+    lr_grid: float = 1e-2
+    lr_mlp: float = 1e-3
+    betas: tuple = (0.9, 0.999)
+    adam_eps: float = 1e-8
+    precision: str = "fp32"
+    extra: dict = field(default_factory=dict)
+
+    @property
+    def n_samples(self) -> int:
+        return self.n_strat + self.n_guided
+
+    @property
+    def dims(self):
+        return grid_dims(self.extent_min, self.extent_max, self.voxels)
+
+    def layout(self):
+        """Flat parameter vector: grid levels 0..3 as [nz][ny][nx][4] float32, then the MLP block."""
+        offs, o = [], 0
+        for (nx, ny, nz) in self.dims:
+            offs.append(o)
+            o += nx * ny * nz * FEAT
+        n_grid = o
+        return offs, n_grid, n_grid + MLP_PARAMS
+
+    def with_(self, **kw) -> "Workload":
+        d = dict(self.__dict__)
+        d.update(kw)
+        return Workload(**d)
+
+
+WORKLOADS = {
+    # 2.56 m cube, 1 camera 160x120, 1024 rays x (48 stratified + 16 depth-guided)
+    "cube-1024x64": Workload(
+        name="cube-1024x64", extent_min=(-1.28, -1.28, -1.28), extent_max=(1.28, 1.28, 1.28),
+        voxels=(0.64, 0.32, 0.16, 0.08), rays=1024, n_strat=48, n_guided=16, near=0.1, far=4.0,
+        frames=1, height=120, width=160, fx=130.0, fy=130.0, cx=80.0, cy=60.0, scene="cube"),
+    # 8x6x3 m room, 1000 poses at 640x480, 8192 rays x (64 + 32), FP32
+    "room-8192x96": Workload(
+        name="room-8192x96", extent_min=(0.0, 0.0, 0.0), extent_max=(8.0, 6.0, 3.0),
+        voxels=(0.96, 0.24, 0.06, 0.02), rays=8192, n_strat=64, n_guided=32, near=0.1, far=6.0,
+        frames=1000, height=480, width=640, fx=525.0, fy=525.0, cx=320.0, cy=240.0, scene="room",
+        noise_k=0.001, drop_p=0.05),
+}
+WORKLOADS["room-bf16-32768x96"] = WORKLOADS["room-8192x96"].with_(name="room-bf16-32768x96", rays=32768,
+                                                                   precision="bf16")
+WORKLOADS["room-diff-65536x96"] = WORKLOADS["room-8192x96"].with_(name="room-diff-65536x96", rays=65536)
+
+
+@dataclass
+class Frames:
+    rgb: np.ndarray    # uint8 [F,H,W,3]
+    depth: np.ndarray  # float32 [F,H,W], 0 = missing
+    c2w: np.ndarray    # float32 [F,3,4]
+    fx: float
+    fy: float
+    cx: float
+    cy: float
+    gt_depth: np.ndarray | None = None
+
+
+def make_frames(w: Workload, n_frames: int | None = None, with_gt: bool = False) -> Frames:
+    """Render the workload's frames (optionally only the first n_frames poses)."""
+    F = w.frames if n_frames is None else n_frames
+    if w.scene == "cube":
+        scene, poses = cube_scene(), cube_poses(n=F)
+    else:
+        scene, poses = room_scene(), room_poses(n=w.frames)[:F]
+    poses = np.ascontiguousarray(poses, dtype=np.float64)
+    H, W = w.height, w.width
+    rgb = np.empty((F, H, W, 3), np.uint8)
+    depth = np.empty((F, H, W), np.float32)
+    gt = np.empty((F, H, W), np.float32) if with_gt else None
+    arr = scene._array()
+    _lib().sg_render(arr, len(scene.prims), scene.shade_mode, poses.ctypes.data, F, H, W, w.fx, w.fy, w.cx, w.cy,
+                     w.noise_k, w.drop_p, w.blob_frac, SEED_SCENE, rgb.ctypes.data, depth.ctypes.data,
+                     gt.ctypes.data if gt is not None else None)
+    return Frames(rgb=rgb, depth=depth, c2w=poses.astype(np.float32), fx=w.fx, fy=w.fy, cx=w.cx, cy=w.cy,
+                  gt_depth=gt)
+
+
+def init_params(w: Workload, seed: int = SEED_INIT) -> np.ndarray:
+    """Default initialisation: grid features N(0, 1e-4^2); MLP weights U(+-1/sqrt(fan_in)),
+    biases 0; kappa = ln 20 (s = 20 1/m)."""
+    rng = np.random.default_rng(seed)
+    offs, n_grid, n_total = w.layout()
+    theta = np.empty(n_total, np.float32)
+    theta[:n_grid] = rng.normal(0.0, 1e-4, n_grid).astype(np.float32)
+    o = n_grid
+    for name, shape in MLP_SHAPES:
+        n = int(np.prod(shape))
+        if name.startswith("W"):
+            bound = 1.0 / math.sqrt(shape[1])
+            theta[o:o + n] = rng.uniform(-bound, bound, n).astype(np.float32)
+        elif name == "kappa":
+            theta[o] = np.float32(math.log(20.0))
+        else:
+            theta[o:o + n] = 0.0
+        o += n
+    return theta
+
+
+def parity_params(w: Workload, seed: int = 11, grid_std: float = 0.05, bias: float = 0.25,
+                  kappa: float = math.log(20.0)) -> np.ndarray:
+    """Parameters for element-wise parity tests.
+
+    Grid features are N(0, grid_std^2) so that decoded values vary along every ray; the two
+    hidden layers get biases of alternating sign and magnitude `bias`, which keeps every
+    hidden pre-activation far from the ReLU kink (units are always on or always off), so an
+    FP32 and an FP64 evaluation take the same branch at every sample.
+    """
+    rng = np.random.default_rng(seed)
+    theta = init_params(w, seed)
+    offs, n_grid, n_total = w.layout()
+    theta[:n_grid] = rng.normal(0.0, grid_std, n_grid).astype(np.float32)
+    o = n_grid
+    for name, shape in MLP_SHAPES:
+        n = int(np.prod(shape))
+        if name in ("b1", "b3"):
+            sign = np.where(np.arange(n) % 2 == 0, 1.0, -1.0)
+            theta[o:o + n] = (sign * bias).astype(np.float32)
+        elif name in ("b2", "b4"):
+            theta[o:o + n] = rng.uniform(-0.1, 0.1, n).astype(np.float32)
+        elif name == "kappa":
+            theta[o] = np.float32(kappa)
+        o += n
+    return theta
+
+
+def mlp_views(theta: np.ndarray, n_grid: int) -> dict:
+    """Named views of the MLP block of a flat parameter vector."""
+    out, o = {}, n_grid
+    for name, shape in MLP_SHAPES:
+        n = int(np.prod(shape))
+        out[name] = theta[o:o + n].reshape(shape)
+        o += n
+    return out
