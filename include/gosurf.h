@@ -1,0 +1,170 @@
+/*
+ * gosurf.h -- C ABI of the GB300 (sm_103a) implementation of one GO-Surf optimisation step
+ * (Wang, Bleja, Agapito: "GO-Surf: Neural Feature Grid Optimization for Fast, High-Fidelity
+ * RGB-D Surface Reconstruction", arXiv 2206.14735).
+ *
+ * One step samples a batch of rays from posed RGB-D frames, decodes an SDF and a colour at
+ * every sample from a four-level dense feature grid and two small decoders, renders colour
+ * and depth with NeuS weights, evaluates the rgb / depth / truncated-SDF / free-space losses
+ * and the SDF-gradient smoothness term, back-propagates to every grid feature and decoder
+ * weight, and applies Adam.
+ *
+ * Conventions common to every entry point
+ *   - Every pointer argument is a DEVICE pointer unless its comment says "host".  The caller
+ *     owns all of them; the library never frees or keeps them past the call.
+ *   - Device arrays of float / float4 data must be 16-byte aligned (GS_ERR_ALIGN otherwise).
+ *   - `stream` is a cudaStream_t passed as void* (NULL = legacy default stream).  Calls only
+ *     enqueue work and return; argument errors are detected on the host and returned before
+ *     anything is enqueued.  Errors raised on the device (bounds checks of debug builds) are
+ *     recorded in the context and reported by gs_sync_status().
+ *   - No call allocates device memory except gs_create (which sizes its workspace once).
+ *   - A context serves one stream at a time and is not thread-safe.
+ *
+ * Parameter vector (one flat float32 array, "theta"), in this order:
+ *   grid level l = 0 (coarsest) .. 3 (finest): dims[l][2] x dims[l][1] x dims[l][0] vertices
+ *     stored z-major, x fastest, 4 features per vertex (one 16-byte vector per vertex);
+ *   decoder block of GS_MLP_PARAMS floats: W1[32][16], b1[32], W2[16][32], b2[16],
+ *     W3[32][15], b3[32], W4[3][32], b4[3], kappa (sharpness s = exp(kappa)).
+ *   The gradient vector and the Adam moments use the same layout.
+ */
+#ifndef GOSURF_H
+#define GOSURF_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define GS_LEVELS 4
+#define GS_FEAT 4
+#define GS_MLP_PARAMS 1684
+#define GS_MAX_SAMPLES 128 /* n_strat + n_guided per ray */
+#define GS_NUM_LOSS 6      /* rgb, depth, sdf, fs, smooth, total */
+
+typedef enum {
+  GS_OK = 0,
+  GS_ERR_INVALID_ARG = 1, /* NULL pointer or out-of-range scalar */
+  GS_ERR_SHAPE = 2,       /* sizes inconsistent with the context's configuration */
+  GS_ERR_ALIGN = 3,       /* a device array is not 16-byte aligned */
+  GS_ERR_CUDA = 4,        /* a CUDA runtime call failed (see gs_last_error) */
+  GS_ERR_DEVICE = 5,      /* a device-side check failed in an earlier call */
+  GS_ERR_UNSUPPORTED = 6  /* configuration outside what this build supports */
+} gs_status;
+
+/* Sample classes written by gs_sample_rays (Sec. 3.3): */
+#define GS_CLS_NONE 0 /* no SDF supervision (behind the surface, or the ray has no depth) */
+#define GS_CLS_TR 1   /* near surface, |D - d| <= t: truncated-SDF loss */
+#define GS_CLS_FS 2   /* free space in front of the surface, D - d > t: free-space loss */
+
+/* Scene and optimisation settings (host struct; values copied by gs_create). */
+typedef struct gs_config {
+  int32_t dims[GS_LEVELS][3]; /* vertex counts (nx, ny, nz) per level, level 0 coarsest (Sec. 3.1) */
+  float voxel[GS_LEVELS];     /* voxel edge length per level, metres */
+  float origin[3];            /* world position of vertex (0,0,0) of every level */
+  int32_t n_strat;            /* stratified samples per ray over [near, far] */
+  int32_t n_guided;           /* samples stratified over [D - g, D + g] when D > 0 */
+  float near_m, far_m;        /* stratified range, metres */
+  float guide_half;           /* g, metres */
+  float trunc;                /* truncation distance t of the SDF bound, metres (Sec. 3.3) */
+  float kappa_fs;             /* exponent scale of the free-space penalty (Sec. 3.3: 5) */
+  float lam[5];               /* loss weights: rgb, depth, sdf, fs, smooth (Sec. 3.4) */
+  int32_t max_rays;           /* largest ray batch any call will see (workspace sizing) */
+  int32_t max_smooth;         /* largest smoothness point batch */
+  float delta_s;              /* smoothness perturbation length, metres (Sec. 3.3) */
+} gs_config;
+
+/* Posed RGB-D frames resident in device memory (Sec. 3: {I_t, D_t}, xi_t). */
+typedef struct gs_frames {
+  int32_t F, H, W;
+  const uint8_t* rgb;  /* [F][H][W][3] */
+  const float* depth;  /* [F][H][W], metres of z-depth, 0 = missing */
+  const float* c2w;    /* [F][3][4] camera-to-world, OpenCV axes (x right, y down, z forward) */
+  float fx, fy, cx, cy;
+} gs_frames;
+
+/* A ray batch; all arrays caller-allocated on the device. */
+typedef struct gs_batch {
+  int32_t R;       /* rays */
+  int32_t N;       /* samples per ray = n_strat + n_guided */
+  int32_t P;       /* smoothness points (may be 0) */
+  int64_t* pix;    /* [R] flat pixel id f*H*W + v*W + u */
+  float* origin;   /* [R][3] ray origin o */
+  float* dir;      /* [R][3] ray direction r with unit camera-z (ray parameter = z-depth) */
+  float* rgb;      /* [R][3] observed colour I[u,v] in [0,1] */
+  float* depth;    /* [R] observed depth D[u,v] (0 = missing) */
+  float* t;        /* [R][N] sample depths d_i, ascending */
+  uint8_t* cls;    /* [R][N] GS_CLS_* */
+  float* xs;       /* [P][3] smoothness points x */
+  float* eps;      /* [P][3] perturbations (|eps| = delta_s) */
+  uint8_t* valid;  /* [P] 1 if the point is used */
+  int32_t* counts; /* [4] rays with D > 0, |S_tr|, |S_fs|, valid smoothness points */
+} gs_batch;
+
+typedef struct gs_ctx gs_ctx;
+
+/* Creates a context for the current CUDA device and sizes its workspace for cfg->max_rays.
+ * Returns GS_ERR_INVALID_ARG / GS_ERR_UNSUPPORTED for a bad configuration. */
+gs_status gs_create(const gs_config* cfg, gs_ctx** out);
+void gs_destroy(gs_ctx* ctx);
+
+/* Host: number of floats in the flat parameter vector; *n_grid (may be NULL) receives the
+ * number of grid floats that precede the decoder block. */
+int64_t gs_param_count(const gs_config* cfg, int64_t* n_grid);
+
+/* Ray batch sampling (Sec. 3.4 "we sample a batch of R rays from all pixels across all
+ * images, including pixels that have missing depth"), sample placement and the bound
+ * classes of Sec. 3.3, plus the near-surface smoothness points S_g (Sec. 3.3, Eq.
+ * smoothness_loss).  Pixels, jitters and perturbation directions come from SplitMix64 keyed
+ * by (seed, stream, step, index, slot); every quantity is computed in binary32 with
+ * round-to-nearest and no contraction, so results are reproducible bit for bit.
+ * batch->R, N, P select the sizes; N must equal n_strat + n_guided. */
+gs_status gs_sample_rays(gs_ctx* ctx, const gs_frames* frames, uint64_t seed, uint32_t step, gs_batch* batch,
+                         void* stream);
+
+/* Forward pass (Sec. 3.1-3.4): loss[6] = L_rgb, L_d, L_sdf, L_fs, L_smooth and the weighted
+ * total sum_k lam_k L_k (device floats; per-CTA partial sums are combined in FP64).
+ * rgb_hat [R][3], d_hat [R], wsum [R] (sum of weights) may each be NULL. */
+gs_status gs_forward(gs_ctx* ctx, const float* theta, const gs_batch* batch, float* loss, float* rgb_hat,
+                     float* d_hat, float* wsum, void* stream);
+
+/* Backward pass: grad += d(sum_k dloss_k * out_k)/d theta, with out = the six outputs of
+ * gs_forward and dloss [6] device floats (NULL = (0,0,0,0,0,1), the gradient of the total).
+ * Activations are recomputed from theta (nothing is stored between the two calls).  Grid
+ * gradients are accumulated with FP32 atomics (summation order not deterministic); decoder
+ * gradients are reduced in a fixed order. */
+gs_status gs_backward(gs_ctx* ctx, const float* theta, const gs_batch* batch, const float* dloss, float* grad,
+                      void* stream);
+
+/* Forward and backward in one pass over the batch (loss and grad as above). */
+gs_status gs_forward_backward(gs_ctx* ctx, const float* theta, const gs_batch* batch, const float* dloss,
+                              float* loss, float* grad, void* stream);
+
+/* Adam (Kingma & Ba) over the n-entry flat vectors theta, grad, m, v with bias correction
+ * for step t >= 1; entries [0, n_grid) use lr_grid, the rest lr_mlp (Sec. 4: 1e-2 for
+ * grids, 1e-3 for decoders).  grad is set to zero.  theta_bf16 (may be NULL) receives a
+ * round-to-nearest-even bfloat16 copy of the first n_grid entries. */
+gs_status gs_adam_step(gs_ctx* ctx, float* theta, float* grad, float* m, float* v, int64_t n, int64_t n_grid,
+                       int32_t t, float lr_grid, float lr_mlp, float beta1, float beta2, float eps,
+                       uint16_t* theta_bf16, void* stream);
+
+/* SDF query (Sec. 3.1 Eq. SDF_MLP; gradient per Supp. Eq. sdf_first_grad): sdf[P] and, if
+ * grad != NULL, grad_x phi [P][3] at points x [P][3]. */
+gs_status gs_query_sdf(gs_ctx* ctx, const float* theta, const float* x, int32_t P, float* sdf, float* grad,
+                       void* stream);
+
+/* Cell lookup used by every gather: out [P][4] = flat base-vertex index of the cell holding
+ * x (clamped to the grid box) at each level, decided in binary32. */
+gs_status gs_voxel_index(gs_ctx* ctx, const float* x, int32_t P, int64_t* out, void* stream);
+
+/* Synchronises the context's last stream and reports device-side check failures. */
+gs_status gs_sync_status(gs_ctx* ctx);
+
+/* Host: message of the last error raised through this context ("" if none). */
+const char* gs_last_error(gs_ctx* ctx);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* GOSURF_H */

@@ -171,7 +171,7 @@ def step(cfg: OcConfig, theta, batch: dict, smooth: dict | None, dloss=None, wan
     loss = np.zeros(6)
     rgb_hat, d_hat, wsum = np.zeros((R, 3)), np.zeros(R), np.zeros(R)
     grad = np.zeros_like(th) if want_grad else None
-    margins = np.zeros(8) if want_margins else None
+    margins = np.zeros(10) if want_margins else None
     dl = None if dloss is None else np.ascontiguousarray(dloss, dtype=np.float64)
     rc = lib().oc_step(ctypes.byref(cfg), _p(th), R, N, _p(batch["o"]), _p(batch["r"]), _p(batch["rgb"]),
                        _p(batch["D"]), _p(batch["t"]), _p(batch["cls"]), P, _p(xs), _p(eps), _p(valid), _p(dl),

@@ -561,18 +561,21 @@ void oc_composite(int N, const double* phi, double s, const float* d, double* al
 /* ------------------------------------------------------------------------------------ */
 static double sgn(double v) { return v > 0 ? 1.0 : (v < 0 ? -1.0 : 0.0); }
 
-/* margins[8]: distance of this evaluation from every branch point, for gradient tests:
+/* margins[10]: distance of this evaluation from every branch point, for gradient tests:
  *  0 min |hidden pre-activation| (both decoders, main samples and smoothness points)
- *  1 min |Phi_i - Phi_{i+1}| / max(Phi_i,1e-6) over i < N
+ *  1 min |Phi_i - Phi_{i+1}| / max(Phi_i,1e-6) over i < N (unsaturated, untied samples)
  *  2 min |Phi_i - 1e-6|
  *  3 min |phi - b| over S_tr
  *  4 min gap between the largest and second largest entry of the free-space max over S_fs
  *  5 min |d_hat - D| over rays with D > 0
  *  6 min |hidden pre-activation| at smoothness points (also folded into 0)
  *  7 signature of every branch decision taken (52-bit hash, as a double): two
- *    evaluations with equal signatures lie on the same smooth piece of the loss */
+ *    evaluations with equal signatures lie on the same smooth piece of the loss
+ *  8 largest change of dL/dphi that flipping an ambiguous alpha > 0 decision would cause,
+ *    over samples with |q| < 1e-6 (a binary32 evaluation may decide those either way)
+ *  9 unused (0) */
 typedef struct {
-  double m[8];
+  double m[10];
   uint64_t sig;
 } margins_t;
 static void sigmix(uint64_t* sig, uint64_t id, uint64_t val) { *sig ^= sm64(id * 0x9E3779B97F4A7C15ULL + val); }
@@ -628,7 +631,9 @@ int oc_step(const oc_config* c, const double* theta, int R, int N, const float* 
   double* lsum_all = (double*)calloc((size_t)nthreads * 5, sizeof(double));
   margins_t* mg_all = (margins_t*)malloc(sizeof(margins_t) * nthreads);
   for (int th = 0; th < nthreads; ++th) {
-    for (int k = 0; k < 8; ++k) mg_all[th].m[k] = INFINITY;
+    for (int k = 0; k < 10; ++k) mg_all[th].m[k] = INFINITY;
+    mg_all[th].m[8] = 0.0;
+    mg_all[th].m[9] = 0.0;
     mg_all[th].sig = 0;
   }
   /* per-sample dL/dz, scattered into the grid afterwards in sample order */
@@ -674,7 +679,9 @@ int oc_step(const oc_config* c, const double* theta, int R, int N, const float* 
       composite(N, phi, s, A, ti, Phi, alpha, T, w, ch, &dh, &ws);
       for (int k = 0; k + 1 < N; ++k) {
         double den = Phi[k] > 1e-6 ? Phi[k] : 1e-6;
-        if (phi[k] != phi[k + 1]) mmin(&mg->m[1], (Phi[k] - Phi[k + 1]) / den);
+        /* a flip of the alpha > 0 branch changes dphi by about s (1 - Phi_k) |dL/dalpha|, so
+         * saturated samples (1 - Phi_k < 1e-5) and exact ties (equal phi) are not counted */
+        if (phi[k] != phi[k + 1] && 1.0 - Phi[k] > 1e-5) mmin(&mg->m[1], (Phi[k] - Phi[k + 1]) / den);
         mmin(&mg->m[2], Phi[k] - 1e-6);
         uint64_t sid = ((uint64_t)i * (uint64_t)N + (uint64_t)k) * 8;
         sigmix(&mg->sig, sid + 2, (uint64_t)(alpha[k] > 0) | (uint64_t)(Phi[k] > 1e-6) << 1);
@@ -736,6 +743,12 @@ int oc_step(const oc_config* c, const double* theta, int R, int N, const float* 
         double dalpha = T[k] * (ek - U[k]);
         double den = Phi[k] > 1e-6 ? Phi[k] : 1e-6;
         double q = (Phi[k] - Phi[k + 1]) / den;
+        if (fabs(q) < 1e-6 && phi[k] != phi[k + 1]) {
+          double self = fabs(dalpha) * s * Phi[k] * (1.0 - Phi[k]) / den;
+          double next = fabs(dalpha) * s * Phi[k + 1] * (1.0 - Phi[k + 1]) / den;
+          double imp = self > next ? self : next;
+          if (imp > mg->m[8]) mg->m[8] = imp;
+        }
         if (q > 0) {
           dPhi[k + 1] += dalpha * (-1.0 / den);
           if (Phi[k] > 1e-6) dPhi[k] += dalpha * (Phi[k + 1] / (Phi[k] * Phi[k]));
@@ -854,10 +867,12 @@ int oc_step(const oc_config* c, const double* theta, int R, int N, const float* 
 
   if (margins) {
     uint64_t sig = 0;
-    for (int k = 0; k < 8; ++k) margins[k] = INFINITY;
+    for (int k = 0; k < 10; ++k) margins[k] = INFINITY;
+    margins[8] = margins[9] = 0.0;
     for (int th = 0; th < nthreads; ++th) {
       for (int k = 0; k < 7; ++k)
         if (mg_all[th].m[k] < margins[k]) margins[k] = mg_all[th].m[k];
+      if (mg_all[th].m[8] > margins[8]) margins[8] = mg_all[th].m[8];
       sig ^= mg_all[th].sig;
     }
     margins[7] = (double)(sig & ((1ULL << 52) - 1));

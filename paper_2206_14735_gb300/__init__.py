@@ -1,0 +1,176 @@
+"""GB300-native GO-Surf optimisation step (arXiv 2206.14735): Python binding.
+
+The computation lives in ``libgosurf.so`` (hand-written sm_103a CUDA behind the C ABI of
+``include/gosurf.h``).  This package allocates device buffers with PyTorch, passes their
+pointers to the library's entry points (same names as the C functions) on the caller's
+current CUDA stream, and wraps forward/backward in a ``torch.autograd.Function``.
+"""
+from __future__ import annotations
+
+import ctypes
+from dataclasses import dataclass
+
+import torch
+
+from ._lib import (GS_FEAT, GS_LEVELS, GS_MLP_PARAMS, GS_NUM_LOSS, EXPORTS, GoSurfError, GsBatch, GsConfig,
+                   GsFrames, lib, library_path)
+
+__all__ = ["Context", "Batch", "DeviceFrames", "GoSurfStep", "make_config", "GS_MLP_PARAMS", "GS_NUM_LOSS",
+           "library_path", "EXPORTS"]
+
+
+def make_config(workload, max_rays=None, max_smooth=None) -> GsConfig:
+    """gs_config from any object with the workload attributes (dims, voxels, extent_min,
+    n_strat, n_guided, near, far, guide_half, trunc, kappa_fs, lambdas, n_smooth, delta_s, rays)."""
+    c = GsConfig()
+    for l, d in enumerate(workload.dims):
+        for a in range(3):
+            c.dims[l][a] = int(d[a])
+        c.voxel[l] = float(workload.voxels[l])
+    c.origin[:] = [float(v) for v in workload.extent_min]
+    c.n_strat, c.n_guided = int(workload.n_strat), int(workload.n_guided)
+    c.near_m, c.far_m = float(workload.near), float(workload.far)
+    c.guide_half, c.trunc, c.kappa_fs = float(workload.guide_half), float(workload.trunc), float(workload.kappa_fs)
+    c.lam[:] = [float(v) for v in workload.lambdas]
+    c.max_rays = int(max_rays if max_rays is not None else workload.rays)
+    c.max_smooth = int(max_smooth if max_smooth is not None else workload.n_smooth)
+    c.delta_s = float(workload.delta_s)
+    return c
+
+
+def _ptr(t):
+    return None if t is None else ctypes.c_void_p(t.data_ptr())
+
+
+def _stream():
+    return ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+
+
+class DeviceFrames:
+    """Posed RGB-D frames copied to the device once (they stay resident)."""
+
+    def __init__(self, rgb, depth, c2w, fx, fy, cx, cy, device="cuda"):
+        self.rgb = torch.as_tensor(rgb).to(device=device, dtype=torch.uint8).contiguous()
+        self.depth = torch.as_tensor(depth).to(device=device, dtype=torch.float32).contiguous()
+        self.c2w = torch.as_tensor(c2w).to(device=device, dtype=torch.float32).contiguous()
+        F, H, W = self.depth.shape
+        self.s = GsFrames(F, H, W, self.rgb.data_ptr(), self.depth.data_ptr(), self.c2w.data_ptr(), fx, fy, cx, cy)
+
+
+@dataclass
+class Batch:
+    """Device buffers of one ray batch (gs_batch)."""
+    R: int
+    N: int
+    P: int
+    pix: torch.Tensor
+    origin: torch.Tensor
+    dir: torch.Tensor
+    rgb: torch.Tensor
+    depth: torch.Tensor
+    t: torch.Tensor
+    cls: torch.Tensor
+    xs: torch.Tensor
+    eps: torch.Tensor
+    valid: torch.Tensor
+    counts: torch.Tensor
+
+    @staticmethod
+    def allocate(R: int, N: int, P: int, device="cuda") -> "Batch":
+        f = dict(device=device, dtype=torch.float32)
+        return Batch(R=R, N=N, P=P, pix=torch.empty(R, device=device, dtype=torch.int64),
+                     origin=torch.empty(R, 3, **f), dir=torch.empty(R, 3, **f), rgb=torch.empty(R, 3, **f),
+                     depth=torch.empty(R, **f), t=torch.empty(R, N, **f),
+                     cls=torch.empty(R, N, device=device, dtype=torch.uint8), xs=torch.empty(max(P, 1), 3, **f),
+                     eps=torch.empty(max(P, 1), 3, **f), valid=torch.empty(max(P, 1), device=device, dtype=torch.uint8),
+                     counts=torch.zeros(4, device=device, dtype=torch.int32))
+
+    def struct(self) -> GsBatch:
+        return GsBatch(self.R, self.N, self.P, self.pix.data_ptr(), self.origin.data_ptr(), self.dir.data_ptr(),
+                       self.rgb.data_ptr(), self.depth.data_ptr(), self.t.data_ptr(), self.cls.data_ptr(),
+                       self.xs.data_ptr(), self.eps.data_ptr(), self.valid.data_ptr(), self.counts.data_ptr())
+
+
+class Context:
+    """One gs_ctx (workspace sized at creation) on the current CUDA device."""
+
+    def __init__(self, workload, max_rays=None, max_smooth=None):
+        self.L = lib()
+        self.cfg = make_config(workload, max_rays, max_smooth)
+        h = ctypes.c_void_p()
+        self._check(self.L.gs_create(ctypes.byref(self.cfg), ctypes.byref(h)), None)
+        self.h = h
+        ng = ctypes.c_int64()
+        self.n_params = int(self.L.gs_param_count(ctypes.byref(self.cfg), ctypes.byref(ng)))
+        self.n_grid = int(ng.value)
+
+    def _check(self, st, h=...):
+        if st != 0:
+            handle = self.h if h is ... else h
+            raise GoSurfError(st, self.L.gs_last_error(handle).decode())
+
+    def close(self):
+        if getattr(self, "h", None):
+            self.L.gs_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    # --- entry points (same names as the C ABI, minus the gs_ prefix) ---
+    def sample_rays(self, frames: DeviceFrames, seed: int, step: int, batch: Batch):
+        b = batch.struct()
+        self._check(self.L.gs_sample_rays(self.h, ctypes.byref(frames.s), seed, step, ctypes.byref(b), _stream()))
+
+    def forward(self, theta, batch: Batch, loss, rgb_hat=None, d_hat=None, wsum=None):
+        b = batch.struct()
+        self._check(self.L.gs_forward(self.h, _ptr(theta), ctypes.byref(b), _ptr(loss), _ptr(rgb_hat), _ptr(d_hat),
+                                      _ptr(wsum), _stream()))
+
+    def backward(self, theta, batch: Batch, dloss, grad):
+        b = batch.struct()
+        self._check(self.L.gs_backward(self.h, _ptr(theta), ctypes.byref(b), _ptr(dloss), _ptr(grad), _stream()))
+
+    def forward_backward(self, theta, batch: Batch, dloss, loss, grad):
+        b = batch.struct()
+        self._check(self.L.gs_forward_backward(self.h, _ptr(theta), ctypes.byref(b), _ptr(dloss), _ptr(loss),
+                                               _ptr(grad), _stream()))
+
+    def adam_step(self, theta, grad, m, v, t, lr_grid, lr_mlp, beta1=0.9, beta2=0.999, eps=1e-8, theta_bf16=None):
+        n = theta.numel()
+        self._check(self.L.gs_adam_step(self.h, _ptr(theta), _ptr(grad), _ptr(m), _ptr(v), n, self.n_grid, t,
+                                        lr_grid, lr_mlp, beta1, beta2, eps, _ptr(theta_bf16), _stream()))
+
+    def query_sdf(self, theta, x, sdf, grad=None):
+        self._check(self.L.gs_query_sdf(self.h, _ptr(theta), _ptr(x), x.shape[0], _ptr(sdf), _ptr(grad), _stream()))
+
+    def voxel_index(self, x, out):
+        self._check(self.L.gs_voxel_index(self.h, _ptr(x), x.shape[0], _ptr(out), _stream()))
+
+    def sync_status(self):
+        self._check(self.L.gs_sync_status(self.h))
+
+
+class GoSurfStep(torch.autograd.Function):
+    """losses = GoSurfStep.apply(theta, ctx, batch): the six outputs of gs_forward
+    (L_rgb, L_d, L_sdf, L_fs, L_smooth, total) as a differentiable function of the flat
+    parameter vector; backward runs gs_backward with the incoming gradient as dloss."""
+
+    @staticmethod
+    def forward(fctx, theta, ctx: Context, batch: Batch):
+        loss = torch.empty(GS_NUM_LOSS, device=theta.device, dtype=torch.float32)
+        ctx.forward(theta.detach(), batch, loss)
+        fctx.save_for_backward(theta)
+        fctx.gs = (ctx, batch)
+        return loss
+
+    @staticmethod
+    def backward(fctx, dloss):
+        (theta,) = fctx.saved_tensors
+        ctx, batch = fctx.gs
+        grad = torch.zeros_like(theta)
+        ctx.backward(theta.detach(), batch, dloss.contiguous().float(), grad)
+        return grad, None, None

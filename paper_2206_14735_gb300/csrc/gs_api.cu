@@ -1,0 +1,235 @@
+// C ABI entry points (include/gosurf.h): argument validation, context and workspace.
+#include <cstdio>
+#include <cstring>
+#include <new>
+
+#include "gs_internal.h"
+
+namespace {
+
+thread_local std::string g_err;  // errors raised before a context exists
+
+gs_status fail(gs_ctx* ctx, gs_status s, const char* msg) {
+  if (ctx) ctx->last_error = msg;
+  else g_err = msg;
+  return s;
+}
+
+gs_status cuda_fail(gs_ctx* ctx, const char* where) {
+  const cudaError_t e = cudaGetLastError();
+  char buf[256];
+  snprintf(buf, sizeof(buf), "%s: %s", where, cudaGetErrorString(e));
+  return fail(ctx, GS_ERR_CUDA, buf);
+}
+
+bool aligned16(const void* p) { return (reinterpret_cast<uintptr_t>(p) & 15u) == 0; }
+
+long long level_floats(const gs_config* c, int l) {
+  return (long long)c->dims[l][0] * c->dims[l][1] * c->dims[l][2] * GS_FEAT;
+}
+
+gs_status check_batch(gs_ctx* ctx, const gs_batch* b, bool need_smooth_arrays) {
+  if (!b) return fail(ctx, GS_ERR_INVALID_ARG, "batch is NULL");
+  if (b->R < 0 || b->R > ctx->cfg.max_rays) return fail(ctx, GS_ERR_SHAPE, "batch R outside [0, max_rays]");
+  if (b->N != ctx->cfg.n_strat + ctx->cfg.n_guided) return fail(ctx, GS_ERR_SHAPE, "batch N != n_strat + n_guided");
+  if (b->P < 0 || b->P > ctx->cfg.max_smooth) return fail(ctx, GS_ERR_SHAPE, "batch P outside [0, max_smooth]");
+  if (!b->counts) return fail(ctx, GS_ERR_INVALID_ARG, "batch counts is NULL");
+  if (b->R > 0 && (!b->origin || !b->dir || !b->rgb || !b->depth || !b->t || !b->cls))
+    return fail(ctx, GS_ERR_INVALID_ARG, "batch ray array is NULL");
+  if (b->R > 0 && need_smooth_arrays && !b->pix) return fail(ctx, GS_ERR_INVALID_ARG, "batch pix is NULL");
+  if (b->P > 0 && (!b->xs || !b->eps || !b->valid)) return fail(ctx, GS_ERR_INVALID_ARG, "batch smoothness array is NULL");
+  return GS_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int64_t gs_param_count(const gs_config* cfg, int64_t* n_grid) {
+  if (!cfg) return -1;
+  long long g = 0;
+  for (int l = 0; l < GS_LEVELS; ++l) g += level_floats(cfg, l);
+  if (n_grid) *n_grid = g;
+  return g + GS_MLP_PARAMS;
+}
+
+gs_status gs_create(const gs_config* cfg, gs_ctx** out) {
+  if (!cfg || !out) return fail(nullptr, GS_ERR_INVALID_ARG, "gs_create: NULL argument");
+  *out = nullptr;
+  for (int l = 0; l < GS_LEVELS; ++l) {
+    for (int a = 0; a < 3; ++a)
+      if (cfg->dims[l][a] < 2) return fail(nullptr, GS_ERR_INVALID_ARG, "gs_create: every level needs >= 2 vertices per axis");
+    if (!(cfg->voxel[l] > 0.0f)) return fail(nullptr, GS_ERR_INVALID_ARG, "gs_create: voxel size must be > 0");
+  }
+  const int N = cfg->n_strat + cfg->n_guided;
+  if (cfg->n_strat < 1 || cfg->n_guided < 0 || N < 2) return fail(nullptr, GS_ERR_INVALID_ARG, "gs_create: need n_strat >= 1 and N >= 2");
+  if (N > 128) return fail(nullptr, GS_ERR_UNSUPPORTED, "gs_create: this build renders at most 128 samples per ray");
+  if (!(cfg->far_m > cfg->near_m) || !(cfg->trunc > 0.0f) || !(cfg->guide_half >= 0.0f))
+    return fail(nullptr, GS_ERR_INVALID_ARG, "gs_create: bad near/far/trunc/guide_half");
+  if (cfg->max_rays < 0 || cfg->max_smooth < 0) return fail(nullptr, GS_ERR_INVALID_ARG, "gs_create: negative batch bound");
+
+  gs_ctx* c = new (std::nothrow) gs_ctx();
+  if (!c) return fail(nullptr, GS_ERR_INVALID_ARG, "gs_create: out of host memory");
+  c->cfg = *cfg;
+  if (cudaGetDevice(&c->device) != cudaSuccess ||
+      cudaDeviceGetAttribute(&c->num_sms, cudaDevAttrMultiProcessorCount, c->device) != cudaSuccess) {
+    delete c;
+    return cuda_fail(nullptr, "gs_create: no CUDA device");
+  }
+  gs::GridDesc& g = c->grid;
+  long long off = 0;
+  for (int l = 0; l < GS_LEVELS; ++l) {
+    for (int a = 0; a < 3; ++a) g.dims[l][a] = cfg->dims[l][a];
+    g.voxel[l] = cfg->voxel[l];
+    g.inv_voxel[l] = 1.0f / cfg->voxel[l];
+    g.off[l] = off;
+    off += level_floats(cfg, l);
+  }
+  for (int a = 0; a < 3; ++a) g.origin[a] = cfg->origin[a];
+  g.n_grid = off;
+  c->render_ctas = c->num_sms;
+  c->n_parts = c->render_ctas + kSmoothCtas;
+  const float dl[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 1.f};
+  if (cudaMalloc(&c->loss_part, sizeof(float) * kLossPad * c->n_parts) != cudaSuccess ||
+      cudaMalloc(&c->mlp_part, sizeof(float) * kMlpPad * c->n_parts) != cudaSuccess ||
+      cudaMalloc(&c->default_dloss, sizeof(float) * 8) != cudaSuccess ||
+      cudaMalloc(&c->status, sizeof(int)) != cudaSuccess ||
+      cudaMemcpy(c->default_dloss, dl, sizeof(dl), cudaMemcpyHostToDevice) != cudaSuccess ||
+      cudaMemset(c->status, 0, sizeof(int)) != cudaSuccess) {
+    gs_status s = cuda_fail(nullptr, "gs_create: workspace allocation");
+    gs_destroy(c);
+    return s;
+  }
+  *out = c;
+  return GS_OK;
+}
+
+void gs_destroy(gs_ctx* ctx) {
+  if (!ctx) return;
+  cudaFree(ctx->loss_part);
+  cudaFree(ctx->mlp_part);
+  cudaFree(ctx->default_dloss);
+  cudaFree(ctx->status);
+  delete ctx;
+}
+
+gs_status gs_sample_rays(gs_ctx* ctx, const gs_frames* frames, uint64_t seed, uint32_t step, gs_batch* batch,
+                         void* stream) {
+  if (!ctx) return fail(nullptr, GS_ERR_INVALID_ARG, "gs_sample_rays: ctx is NULL");
+  if (!frames || !frames->rgb || !frames->depth || !frames->c2w)
+    return fail(ctx, GS_ERR_INVALID_ARG, "gs_sample_rays: frames or a frame array is NULL");
+  if (frames->F < 1 || frames->H < 1 || frames->W < 1) return fail(ctx, GS_ERR_SHAPE, "gs_sample_rays: empty frames");
+  if (!(frames->fx != 0.0f) || !(frames->fy != 0.0f)) return fail(ctx, GS_ERR_INVALID_ARG, "gs_sample_rays: zero focal length");
+  gs_status s = check_batch(ctx, batch, true);
+  if (s != GS_OK) return s;
+  cudaStream_t st = (cudaStream_t)stream;
+  ctx->last_stream = st;
+  s = gs_launch_sample(ctx, frames, seed, step, batch, st);
+  return s == GS_OK ? s : cuda_fail(ctx, "gs_sample_rays");
+}
+
+static gs_status render_common(gs_ctx* ctx, const char* who, const float* theta, const gs_batch* batch,
+                               const float* dloss, float* loss, float* grad, float* rgb_hat, float* d_hat, float* wsum,
+                               int mode, void* stream) {
+  if (!ctx) return fail(nullptr, GS_ERR_INVALID_ARG, "ctx is NULL");
+  if (!theta) return fail(ctx, GS_ERR_INVALID_ARG, "theta is NULL");
+  if (!aligned16(theta)) return fail(ctx, GS_ERR_ALIGN, "theta is not 16-byte aligned");
+  if ((mode & 1) && !loss) return fail(ctx, GS_ERR_INVALID_ARG, "loss is NULL");
+  if ((mode & 2) && !grad) return fail(ctx, GS_ERR_INVALID_ARG, "grad is NULL");
+  if ((mode & 2) && !aligned16(grad)) return fail(ctx, GS_ERR_ALIGN, "grad is not 16-byte aligned");
+  gs_status s = check_batch(ctx, batch, false);
+  if (s != GS_OK) return s;
+  cudaStream_t st = (cudaStream_t)stream;
+  ctx->last_stream = st;
+  const float* dl = dloss ? dloss : ctx->default_dloss;
+  if (batch->R > 0 && gs_launch_render(ctx, theta, batch, dl, grad, rgb_hat, d_hat, wsum, mode, st) != GS_OK)
+    return cuda_fail(ctx, who);
+  if (gs_launch_smooth(ctx, theta, batch, dl, grad, mode, st) != GS_OK) return cuda_fail(ctx, who);
+  // partial rows: render CTAs (if any rays) then smoothness CTAs (if any points)
+  gs_ctx tmp = *ctx;
+  if (batch->R == 0 || batch->P == 0) {
+    // only rows that this call wrote are combined
+    tmp.n_parts = (batch->R > 0 ? ctx->render_ctas : 0) + (batch->P > 0 ? kSmoothCtas : 0);
+    if (batch->R == 0) {
+      tmp.loss_part = ctx->loss_part + (size_t)ctx->render_ctas * kLossPad;
+      tmp.mlp_part = ctx->mlp_part + (size_t)ctx->render_ctas * kMlpPad;
+    }
+  }
+  if (gs_launch_finalize(&tmp, batch, loss, grad, mode, st) != GS_OK) return cuda_fail(ctx, who);
+  tmp.last_error.clear();
+  return GS_OK;
+}
+
+gs_status gs_forward(gs_ctx* ctx, const float* theta, const gs_batch* batch, float* loss, float* rgb_hat,
+                     float* d_hat, float* wsum, void* stream) {
+  return render_common(ctx, "gs_forward", theta, batch, nullptr, loss, nullptr, rgb_hat, d_hat, wsum, 1, stream);
+}
+
+gs_status gs_backward(gs_ctx* ctx, const float* theta, const gs_batch* batch, const float* dloss, float* grad,
+                      void* stream) {
+  return render_common(ctx, "gs_backward", theta, batch, dloss, nullptr, grad, nullptr, nullptr, nullptr, 2, stream);
+}
+
+gs_status gs_forward_backward(gs_ctx* ctx, const float* theta, const gs_batch* batch, const float* dloss,
+                              float* loss, float* grad, void* stream) {
+  return render_common(ctx, "gs_forward_backward", theta, batch, dloss, loss, grad, nullptr, nullptr, nullptr, 3,
+                       stream);
+}
+
+gs_status gs_adam_step(gs_ctx* ctx, float* theta, float* grad, float* m, float* v, int64_t n, int64_t n_grid,
+                       int32_t t, float lr_grid, float lr_mlp, float beta1, float beta2, float eps,
+                       uint16_t* theta_bf16, void* stream) {
+  if (!ctx) return fail(nullptr, GS_ERR_INVALID_ARG, "gs_adam_step: ctx is NULL");
+  if (!theta || !grad || !m || !v) return fail(ctx, GS_ERR_INVALID_ARG, "gs_adam_step: NULL array");
+  if (!aligned16(theta) || !aligned16(grad) || !aligned16(m) || !aligned16(v) ||
+      (theta_bf16 && (reinterpret_cast<uintptr_t>(theta_bf16) & 7u)))
+    return fail(ctx, GS_ERR_ALIGN, "gs_adam_step: arrays must be 16-byte aligned (bf16 copy 8-byte)");
+  if (n < 0 || n_grid < 0 || n_grid > n || (n & 3) || (n_grid & 3))
+    return fail(ctx, GS_ERR_SHAPE, "gs_adam_step: n and n_grid must be multiples of 4 with n_grid <= n");
+  if (t < 1) return fail(ctx, GS_ERR_INVALID_ARG, "gs_adam_step: step count t must be >= 1");
+  if (!(beta1 >= 0.f && beta1 < 1.f && beta2 >= 0.f && beta2 < 1.f && eps > 0.f))
+    return fail(ctx, GS_ERR_INVALID_ARG, "gs_adam_step: bad beta or eps");
+  cudaStream_t st = (cudaStream_t)stream;
+  ctx->last_stream = st;
+  if (n == 0) return GS_OK;
+  if (gs_launch_adam(theta, grad, m, v, n, n_grid, t, lr_grid, lr_mlp, beta1, beta2, eps, theta_bf16, ctx->num_sms,
+                     st) != GS_OK)
+    return cuda_fail(ctx, "gs_adam_step");
+  return GS_OK;
+}
+
+gs_status gs_query_sdf(gs_ctx* ctx, const float* theta, const float* x, int32_t P, float* sdf, float* grad,
+                       void* stream) {
+  if (!ctx) return fail(nullptr, GS_ERR_INVALID_ARG, "gs_query_sdf: ctx is NULL");
+  if (P < 0) return fail(ctx, GS_ERR_SHAPE, "gs_query_sdf: P < 0");
+  if (P > 0 && (!theta || !x || !sdf)) return fail(ctx, GS_ERR_INVALID_ARG, "gs_query_sdf: NULL array");
+  if (P > 0 && !aligned16(theta)) return fail(ctx, GS_ERR_ALIGN, "gs_query_sdf: theta is not 16-byte aligned");
+  cudaStream_t st = (cudaStream_t)stream;
+  ctx->last_stream = st;
+  if (gs_launch_query(ctx, theta, x, P, sdf, grad, st) != GS_OK) return cuda_fail(ctx, "gs_query_sdf");
+  return GS_OK;
+}
+
+gs_status gs_voxel_index(gs_ctx* ctx, const float* x, int32_t P, int64_t* out, void* stream) {
+  if (!ctx) return fail(nullptr, GS_ERR_INVALID_ARG, "gs_voxel_index: ctx is NULL");
+  if (P < 0) return fail(ctx, GS_ERR_SHAPE, "gs_voxel_index: P < 0");
+  if (P > 0 && (!x || !out)) return fail(ctx, GS_ERR_INVALID_ARG, "gs_voxel_index: NULL array");
+  cudaStream_t st = (cudaStream_t)stream;
+  ctx->last_stream = st;
+  if (gs_launch_voxel_index(ctx, x, P, (long long*)out, st) != GS_OK) return cuda_fail(ctx, "gs_voxel_index");
+  return GS_OK;
+}
+
+gs_status gs_sync_status(gs_ctx* ctx) {
+  if (!ctx) return fail(nullptr, GS_ERR_INVALID_ARG, "gs_sync_status: ctx is NULL");
+  if (cudaStreamSynchronize(ctx->last_stream) != cudaSuccess) return cuda_fail(ctx, "gs_sync_status");
+  int h = 0;
+  if (cudaMemcpy(&h, ctx->status, sizeof(int), cudaMemcpyDeviceToHost) != cudaSuccess)
+    return cuda_fail(ctx, "gs_sync_status");
+  if (h != 0) return fail(ctx, GS_ERR_DEVICE, "a device-side check failed");
+  return GS_OK;
+}
+
+const char* gs_last_error(gs_ctx* ctx) { return ctx ? ctx->last_error.c_str() : g_err.c_str(); }
+
+}  // extern "C"

@@ -1,0 +1,43 @@
+// Library-internal declarations: the context object and the kernel launchers.
+#pragma once
+#include <cuda_runtime.h>
+
+#include <string>
+
+#include "gosurf.h"
+#include "gs_device.cuh"
+
+constexpr int kMlpPad = 1688;     // per-CTA decoder-gradient partial row (>= GS_MLP_PARAMS, 16-B multiple)
+constexpr int kLossPad = 8;       // per-CTA loss partial row
+constexpr int kSmoothCtas = 64;   // CTAs of the smoothness kernel (fixed, so partial rows are known)
+
+struct gs_ctx {
+  gs_config cfg;
+  gs::GridDesc grid;
+  int device = 0;
+  int num_sms = 0;
+  int render_ctas = 0;  // persistent CTAs of the fused render kernel
+  int n_parts = 0;      // render_ctas + kSmoothCtas
+  float* loss_part = nullptr;
+  float* mlp_part = nullptr;
+  float* default_dloss = nullptr;  // (0,0,0,0,0,1)
+  int* status = nullptr;
+  cudaStream_t last_stream = nullptr;
+  std::string last_error;
+};
+
+gs_status gs_launch_sample(const gs_ctx* ctx, const gs_frames* f, uint64_t seed, uint32_t step, const gs_batch* b,
+                           cudaStream_t st);
+// mode bit 1: forward outputs (loss partials, per-ray outputs), bit 2: backward (grad)
+gs_status gs_launch_render(const gs_ctx* ctx, const float* theta, const gs_batch* b, const float* dloss, float* grad,
+                           float* rgb_hat, float* d_hat, float* wsum, int mode, cudaStream_t st);
+gs_status gs_launch_smooth(const gs_ctx* ctx, const float* theta, const gs_batch* b, const float* dloss, float* grad,
+                           int mode, cudaStream_t st);
+gs_status gs_launch_finalize(const gs_ctx* ctx, const gs_batch* b, float* loss, float* grad, int mode,
+                             cudaStream_t st);
+gs_status gs_launch_adam(float* theta, float* grad, float* m, float* v, long long n, long long n_grid, int t,
+                         float lr_grid, float lr_mlp, float b1, float b2, float eps, uint16_t* bf16, int num_sms,
+                         cudaStream_t st);
+gs_status gs_launch_query(const gs_ctx* ctx, const float* theta, const float* x, int P, float* sdf, float* grad,
+                          cudaStream_t st);
+gs_status gs_launch_voxel_index(const gs_ctx* ctx, const float* x, int P, long long* out, cudaStream_t st);

@@ -1,0 +1,184 @@
+// Loss / decoder-gradient combination, SDF query and cell lookup, and the dispatch of the
+// fused render kernel over samples-per-ray (its instantiations live in gs_render_n*.cu).
+#include "gs_render_kernel.cuh"
+
+namespace gs {
+
+extern template gs_status launch_n<1>(const gs_ctx*, RenderArgs&, int, cudaStream_t);
+extern template gs_status launch_n<2>(const gs_ctx*, RenderArgs&, int, cudaStream_t);
+extern template gs_status launch_n<3>(const gs_ctx*, RenderArgs&, int, cudaStream_t);
+extern template gs_status launch_n<4>(const gs_ctx*, RenderArgs&, int, cudaStream_t);
+
+// ------------------------------------------------------------------------------------
+// combine per-CTA partials: losses in FP64, decoder gradients in a fixed order
+// ------------------------------------------------------------------------------------
+__global__ void finalize_kernel(const float* loss_part, const float* mlp_part, int nparts, const int* counts, int R,
+                                float l0, float l1, float l2, float l3, float l4, float* loss, float* gmlp) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (gmlp && i < GS_MLP_PARAMS) {
+    float s = 0.f;
+    for (int p = 0; p < nparts; ++p) s += mlp_part[(size_t)p * kMlpPad + i];
+    gmlp[i] += s;
+  }
+  if (loss && blockIdx.x == 0 && threadIdx.x < 32) {
+    const int k = threadIdx.x;
+    double s = 0.0;
+    if (k < 5)
+      for (int p = 0; p < nparts; ++p) s += (double)loss_part[(size_t)p * kLossPad + k];
+    const double den[5] = {(double)R, (double)counts[0], (double)counts[1], (double)counts[2], (double)counts[3]};
+    double v = (k < 5 && den[k < 5 ? k : 0] > 0) ? s / den[k < 5 ? k : 0] : 0.0;
+    const double lam[5] = {l0, l1, l2, l3, l4};
+    double tot = (k < 5) ? lam[k] * v : 0.0;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) tot += __shfl_xor_sync(0xffffffffu, tot, o);
+    if (k < 5) loss[k] = (float)v;
+    if (k == 5) loss[5] = (float)tot;
+  }
+}
+
+// ------------------------------------------------------------------------------------
+// SDF query and cell lookup
+// ------------------------------------------------------------------------------------
+__global__ void query_kernel(GridDesc g, const float* __restrict__ theta, const float* __restrict__ xq, int P,
+                             float* sdf, float* grad) {
+  __shared__ __align__(16) float sm[kSmemMlp];
+  const float* mlp = theta + g.n_grid;
+  for (int i = threadIdx.x; i < kSmemMlp; i += blockDim.x) {
+    float v = 0.0f;
+    if (i < sb1) v = mlp[oW1 + i];
+    else if (i < sW2) v = mlp[ob1 + i - sb1];
+    else if (i < sb2) v = mlp[oW2 + i - sW2];
+    else if (i < sW3) v = mlp[ob2 + i - sb2];
+    else if (i < sb3) {
+      const int j = (i - sW3) >> 4, k = (i - sW3) & 15;
+      v = k < kHF ? mlp[oW3 + j * kHF + k] : 0.0f;
+    }
+    sm[i] = v;
+  }
+  __syncthreads();
+  const int p = blockIdx.x * blockDim.x + threadIdx.x;
+  if (p >= P) return;
+  const float x[3] = {xq[3 * p], xq[3 * p + 1], xq[3 * p + 2]};
+  float z[kZ], dzdx[kZ][3];
+#pragma unroll
+  for (int l = 0; l < kLevels; ++l) {
+    const Cell c = locate(g, l, x);
+    float w[8], dw[8][3];
+    corner_weights(c.f, w);
+    corner_weight_grads(c.f, c.clamped, dw);
+    const float4* base = reinterpret_cast<const float4*>(theta + g.off[l]);
+    float4 acc = make_float4(0.f, 0.f, 0.f, 0.f), ax = acc, ay = acc, az = acc;
+#pragma unroll
+    for (int k = 0; k < 8; ++k) {
+      const float4 v = __ldg(base + c.vtx + corner_offset(g, l, k));
+      f4fma(acc, w[k], v);
+      f4fma(ax, dw[k][0], v);
+      f4fma(ay, dw[k][1], v);
+      f4fma(az, dw[k][2], v);
+    }
+    const float iv = g.inv_voxel[l];
+    const float zz[4] = {acc.x, acc.y, acc.z, acc.w}, gx[4] = {ax.x, ax.y, ax.z, ax.w},
+                gy[4] = {ay.x, ay.y, ay.z, ay.w}, gz[4] = {az.x, az.y, az.z, az.w};
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+      z[4 * l + k] = zz[k];
+      dzdx[4 * l + k][0] = gx[k] * iv;
+      dzdx[4 * l + k][1] = gy[k] * iv;
+      dzdx[4 * l + k][2] = gz[k] * iv;
+    }
+  }
+  float y1[kH1];
+  float phi = sm[sb2];
+#pragma unroll
+  for (int j = 0; j < kH1; ++j) {
+    float s = sm[sb1 + j];
+#pragma unroll
+    for (int k = 0; k < kZ; ++k) s = fmaf(sm[sW1 + j * 16 + k], z[k], s);
+    y1[j] = s;
+    phi = fmaf(sm[sW2 + j], fmaxf(s, 0.f), phi);
+  }
+  sdf[p] = phi;
+  if (grad) {
+    float gxyz[3] = {0.f, 0.f, 0.f};
+#pragma unroll
+    for (int k = 0; k < kZ; ++k) {
+      float pk = 0.f;  // d phi / d z_k = sum_j W1[j][k] [y1_j > 0] W2[0][j]
+#pragma unroll
+      for (int j = 0; j < kH1; ++j) pk = fmaf(sm[sW1 + j * 16 + k], y1[j] > 0.f ? sm[sW2 + j] : 0.f, pk);
+#pragma unroll
+      for (int q = 0; q < 3; ++q) gxyz[q] = fmaf(pk, dzdx[k][q], gxyz[q]);
+    }
+    grad[3 * p] = gxyz[0];
+    grad[3 * p + 1] = gxyz[1];
+    grad[3 * p + 2] = gxyz[2];
+  }
+}
+
+__global__ void voxel_index_kernel(GridDesc g, const float* __restrict__ xq, int P, long long* out) {
+  const int p = blockIdx.x * blockDim.x + threadIdx.x;
+  if (p >= P) return;
+  const float x[3] = {xq[3 * p], xq[3 * p + 1], xq[3 * p + 2]};
+#pragma unroll
+  for (int l = 0; l < kLevels; ++l) out[(size_t)kLevels * p + l] = locate(g, l, x).vtx;
+}
+
+}  // namespace gs
+
+using namespace gs;
+
+gs_status gs_launch_render(const gs_ctx* ctx, const float* theta, const gs_batch* b, const float* dloss, float* grad,
+                           float* rgb_hat, float* d_hat, float* wsum, int mode, cudaStream_t st) {
+  RenderArgs a;
+  a.g = ctx->grid;
+  a.theta = theta;
+  a.R = b->R;
+  a.N = b->N;
+  a.o = b->origin;
+  a.r = b->dir;
+  a.rgb = b->rgb;
+  a.D = b->depth;
+  a.t = b->t;
+  a.cls = b->cls;
+  a.counts = b->counts;
+  a.dloss = dloss;
+  for (int k = 0; k < 5; ++k) a.lam[k] = ctx->cfg.lam[k];
+  a.kappa_fs = ctx->cfg.kappa_fs;
+  a.grad = grad;
+  a.loss_part = ctx->loss_part;
+  a.mlp_part = ctx->mlp_part;
+  a.rgb_hat = rgb_hat;
+  a.d_hat = d_hat;
+  a.wsum = wsum;
+  const int n0 = ctx->grid.dims[0][0] * ctx->grid.dims[0][1] * ctx->grid.dims[0][2];
+  a.lvl0_staged = n0 <= kLvl0MaxVerts;
+  const int nch = (b->N + 31) / 32;
+  switch (nch) {
+    case 1: return launch_n<1>(ctx, a, mode, st);
+    case 2: return launch_n<2>(ctx, a, mode, st);
+    case 3: return launch_n<3>(ctx, a, mode, st);
+    case 4: return launch_n<4>(ctx, a, mode, st);
+    default: return GS_ERR_UNSUPPORTED;
+  }
+}
+
+gs_status gs_launch_finalize(const gs_ctx* ctx, const gs_batch* b, float* loss, float* grad, int mode,
+                             cudaStream_t st) {
+  const float* l = ctx->cfg.lam;
+  float* gmlp = (mode & 2) ? grad + ctx->grid.n_grid : nullptr;
+  float* lo = (mode & 1) ? loss : nullptr;
+  finalize_kernel<<<(GS_MLP_PARAMS + 255) / 256, 256, 0, st>>>(ctx->loss_part, ctx->mlp_part, ctx->n_parts,
+                                                                b->counts, b->R, l[0], l[1], l[2], l[3], l[4], lo,
+                                                                gmlp);
+  return cudaPeekAtLastError() == cudaSuccess ? GS_OK : GS_ERR_CUDA;
+}
+
+gs_status gs_launch_query(const gs_ctx* ctx, const float* theta, const float* x, int P, float* sdf, float* grad,
+                          cudaStream_t st) {
+  if (P > 0) query_kernel<<<(P + 127) / 128, 128, 0, st>>>(ctx->grid, theta, x, P, sdf, grad);
+  return cudaPeekAtLastError() == cudaSuccess ? GS_OK : GS_ERR_CUDA;
+}
+
+gs_status gs_launch_voxel_index(const gs_ctx* ctx, const float* x, int P, long long* out, cudaStream_t st) {
+  if (P > 0) voxel_index_kernel<<<(P + 127) / 128, 128, 0, st>>>(ctx->grid, x, P, out);
+  return cudaPeekAtLastError() == cudaSuccess ? GS_OK : GS_ERR_CUDA;
+}

@@ -1,0 +1,6 @@
+// Fused render kernel instantiated for rays of up to 64 samples.
+#include "gs_render_kernel.cuh"
+
+namespace gs {
+template gs_status launch_n<2>(const gs_ctx*, RenderArgs&, int, cudaStream_t);
+}  // namespace gs

@@ -1,0 +1,238 @@
+// SDF-gradient smoothness term (Sec. 3.3, Eq. smoothness_loss) and its second-order adjoint
+// (Supp. Sec. 1): L_smooth = mean_p || grad phi(x_p) - grad phi(x_p + eps_p) ||^2 over S_g.
+//
+// grad_x phi = sum_l (1/v_l) J_l(x)^T p_l with p = d phi/d z = W1^T (m (.) W2[0,:]^T), m the
+// ReLU mask (the decoder is piecewise linear, so p does not depend on z almost everywhere).
+// For an adjoint a = dL/d(grad phi) at a point y:
+//   d/d theta_{l,c,k} = p_{l,k} (1/v_l) (a . dw_c/df)       (Supp. Eq. second_order_theta)
+//   d/d W1 = (m (.) W2[0,:]) j^T,  d/d W2[0,:] = m (.) (W1 j), j_k = a . d z_k / d x.
+// One lane per point; a warp stages its 32 points' vectors and reduces the decoder
+// gradients as 4x4 tiles, as the render kernel does.
+#include "gs_internal.h"
+
+namespace gs {
+
+constexpr int kSmoothWarps = 2;  // static shared memory stays under 48 KB
+constexpr int kSt = 84;  // staged row: mw2[32] | j[16] | u[32] (+4 pad), stride = 20 mod 32 banks
+constexpr int sMw2 = 0, sJ = 32, sU = 48;
+
+struct SmoothRunArgs {
+  GridDesc g;
+  const float* theta;
+  int P;
+  const float *xs, *eps;
+  const uint8_t* valid;
+  const int* counts;
+  const float* dloss;
+  float lam4;
+  float* grad;
+  float* loss_part;  // rows for this kernel's CTAs
+  float* mlp_part;
+};
+
+__device__ __forceinline__ float4 ldv(const float* p) { return *reinterpret_cast<const float4*>(p); }
+
+// z, dz/dx (metric) and the cells at point y
+__device__ __forceinline__ void features_with_jacobian(const GridDesc& g, const float* __restrict__ theta,
+                                                       const float y[3], float z[kZ], float dzdx[kZ][3]) {
+#pragma unroll
+  for (int l = 0; l < kLevels; ++l) {
+    const Cell c = locate(g, l, y);
+    float w[8], dw[8][3];
+    corner_weights(c.f, w);
+    corner_weight_grads(c.f, c.clamped, dw);
+    const float4* base = reinterpret_cast<const float4*>(theta + g.off[l]);
+    float4 acc = make_float4(0.f, 0.f, 0.f, 0.f), ax = acc, ay = acc, az = acc;
+#pragma unroll
+    for (int k = 0; k < 8; ++k) {
+      const float4 v = __ldg(base + c.vtx + corner_offset(g, l, k));
+      f4fma(acc, w[k], v);
+      f4fma(ax, dw[k][0], v);
+      f4fma(ay, dw[k][1], v);
+      f4fma(az, dw[k][2], v);
+    }
+    const float iv = g.inv_voxel[l];
+    const float zz[4] = {acc.x, acc.y, acc.z, acc.w}, gx[4] = {ax.x, ax.y, ax.z, ax.w},
+                gy[4] = {ay.x, ay.y, ay.z, ay.w}, gz[4] = {az.x, az.y, az.z, az.w};
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+      z[4 * l + k] = zz[k];
+      dzdx[4 * l + k][0] = gx[k] * iv;
+      dzdx[4 * l + k][1] = gy[k] * iv;
+      dzdx[4 * l + k][2] = gz[k] * iv;
+    }
+  }
+}
+
+// ReLU mask m (bit j = unit j on), m (.) W2[0,:], and p = d phi / d z
+__device__ __forceinline__ unsigned phi_sensitivity(const float* sm, const float z[kZ], float mw2[kH1], float p[kZ]) {
+  unsigned mask = 0;
+#pragma unroll
+  for (int j = 0; j < kH1; ++j) {
+    float s = sm[sb1 + j];
+#pragma unroll
+    for (int k = 0; k < kZ; ++k) s = fmaf(sm[sW1 + j * 16 + k], z[k], s);
+    mw2[j] = s > 0.f ? sm[sW2 + j] : 0.f;
+    mask |= (s > 0.f ? 1u : 0u) << j;
+  }
+#pragma unroll
+  for (int k = 0; k < kZ; ++k) {
+    float s = 0.f;
+#pragma unroll
+    for (int j = 0; j < kH1; ++j) s = fmaf(sm[sW1 + j * 16 + k], mw2[j], s);
+    p[k] = s;
+  }
+  return mask;
+}
+
+template <bool FWD, bool BWD>
+__global__ void __launch_bounds__(kSmoothWarps * 32) smooth_kernel(SmoothRunArgs a) {
+  __shared__ __align__(16) float sm[kSmemMlp];
+  __shared__ __align__(16) float acc[kMlpPad + kLossPad];
+  __shared__ __align__(16) float stage[kSmoothWarps][32 * kSt];
+  const float* mlp = a.theta + a.g.n_grid;
+  for (int i = threadIdx.x; i < kSmemMlp; i += blockDim.x) {
+    float v = 0.0f;
+    if (i < sb1) v = mlp[oW1 + i];
+    else if (i < sW2) v = mlp[ob1 + i - sb1];
+    else if (i < sb2) v = mlp[oW2 + i - sW2];
+    sm[i] = v;
+  }
+  for (int i = threadIdx.x; i < kMlpPad + kLossPad; i += blockDim.x) acc[i] = 0.0f;
+  __syncthreads();
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  float* st = stage[warp];
+  const int n_g = a.counts[3];
+  const float k_sm = n_g > 0 ? (a.dloss[4] + a.lam4 * a.dloss[5]) * 2.0f / (float)n_g : 0.0f;
+  float l_sm = 0.f;
+
+  for (int base = (blockIdx.x * kSmoothWarps + warp) * 32; base < a.P; base += gridDim.x * kSmoothWarps * 32) {
+    const int p = base + lane;
+    const bool valid = p < a.P && a.valid[p];
+    float y[2][3], g[2][3];
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+      y[0][k] = valid ? a.xs[3 * p + k] : 0.f;
+      y[1][k] = valid ? __fadd_rn(a.xs[3 * p + k], a.eps[3 * p + k]) : 0.f;
+    }
+#pragma unroll
+    for (int e = 0; e < 2; ++e) {
+      float z[kZ], dzdx[kZ][3], mw2[kH1], pz[kZ];
+      features_with_jacobian(a.g, a.theta, y[e], z, dzdx);
+      phi_sensitivity(sm, z, mw2, pz);
+#pragma unroll
+      for (int q = 0; q < 3; ++q) {
+        float s = 0.f;
+#pragma unroll
+        for (int k = 0; k < kZ; ++k) s = fmaf(pz[k], dzdx[k][q], s);
+        g[e][q] = s;
+      }
+    }
+    const float dg[3] = {g[0][0] - g[1][0], g[0][1] - g[1][1], g[0][2] - g[1][2]};
+    if (FWD && valid) l_sm += dg[0] * dg[0] + dg[1] * dg[1] + dg[2] * dg[2];
+    if constexpr (!BWD) continue;
+#pragma unroll 1
+    for (int e = 0; e < 2; ++e) {
+      const float sgn = e == 0 ? 1.f : -1.f;
+      const float av[3] = {valid ? sgn * k_sm * dg[0] : 0.f, valid ? sgn * k_sm * dg[1] : 0.f,
+                           valid ? sgn * k_sm * dg[2] : 0.f};
+      float z[kZ], dzdx[kZ][3], mw2[kH1], pz[kZ];
+      const float ye[3] = {e == 0 ? y[0][0] : y[1][0], e == 0 ? y[0][1] : y[1][1], e == 0 ? y[0][2] : y[1][2]};
+      features_with_jacobian(a.g, a.theta, ye, z, dzdx);
+      const unsigned mask = phi_sensitivity(sm, z, mw2, pz);
+      float jv[kZ];
+#pragma unroll
+      for (int k = 0; k < kZ; ++k) jv[k] = av[0] * dzdx[k][0] + av[1] * dzdx[k][1] + av[2] * dzdx[k][2];
+      float* row = st + lane * kSt;
+#pragma unroll
+      for (int q = 0; q < 8; ++q)
+        *reinterpret_cast<float4*>(row + sMw2 + 4 * q) = make_float4(mw2[4 * q], mw2[4 * q + 1], mw2[4 * q + 2], mw2[4 * q + 3]);
+#pragma unroll
+      for (int q = 0; q < 4; ++q)
+        *reinterpret_cast<float4*>(row + sJ + 4 * q) = make_float4(jv[4 * q], jv[4 * q + 1], jv[4 * q + 2], jv[4 * q + 3]);
+      // d/d W2[0][j] = m_j (W1 j)_j
+#pragma unroll
+      for (int j = 0; j < kH1; ++j) {
+        float u = 0.f;
+        if ((mask >> j) & 1u) {
+#pragma unroll
+          for (int k = 0; k < kZ; ++k) u = fmaf(sm[sW1 + j * 16 + k], jv[k], u);
+        }
+        row[sU + j] = u;
+      }
+      // direct term: d/d theta_{l,c,k} = p_{l,k} (1/v_l) (a . dw_c/df)
+      if (valid) {
+#pragma unroll
+        for (int l = 0; l < kLevels; ++l) {
+          const Cell c = locate(a.g, l, ye);
+          float dw[8][3];
+          corner_weight_grads(c.f, c.clamped, dw);
+          const float iv = a.g.inv_voxel[l];
+          const float4 p4 = make_float4(pz[4 * l], pz[4 * l + 1], pz[4 * l + 2], pz[4 * l + 3]);
+#pragma unroll
+          for (int k = 0; k < 8; ++k) {
+            const float ad = (av[0] * dw[k][0] + av[1] * dw[k][1] + av[2] * dw[k][2]) * iv;
+            atomicAdd(reinterpret_cast<float4*>(a.grad + a.g.off[l]) + c.vtx + corner_offset(a.g, l, k),
+                      f4scale(p4, ad));
+          }
+        }
+      }
+      __syncwarp();
+      {  // dW1[32][16] += mw2 (x) j over the warp's 32 points
+        const int i0 = 4 * (lane >> 2), j0 = 4 * (lane & 3);
+        float t[4][4] = {};
+#pragma unroll 4
+        for (int s = 0; s < 32; ++s) {
+          const float4 av4 = ldv(st + s * kSt + sMw2 + i0), bv4 = ldv(st + s * kSt + sJ + j0);
+          const float ar[4] = {av4.x, av4.y, av4.z, av4.w}, br[4] = {bv4.x, bv4.y, bv4.z, bv4.w};
+#pragma unroll
+          for (int x = 0; x < 4; ++x)
+#pragma unroll
+            for (int q = 0; q < 4; ++q) t[x][q] = fmaf(ar[x], br[q], t[x][q]);
+        }
+#pragma unroll
+        for (int x = 0; x < 4; ++x)
+#pragma unroll
+          for (int q = 0; q < 4; ++q) atomicAdd(acc + oW1 + (i0 + x) * kZ + j0 + q, t[x][q]);
+        float u = 0.f;  // dW2[0][lane] += sum_s u_s[lane]
+#pragma unroll 4
+        for (int s = 0; s < 32; ++s) u += st[s * kSt + sU + lane];
+        atomicAdd(acc + oW2 + lane, u);
+      }
+      __syncwarp();
+    }
+  }
+  if (FWD) {
+    l_sm = warp_sum(l_sm);
+    if (lane == 0) atomicAdd(acc + kMlpPad + 4, l_sm);
+  }
+  __syncthreads();
+  if (threadIdx.x < kLossPad) a.loss_part[(size_t)blockIdx.x * kLossPad + threadIdx.x] = acc[kMlpPad + threadIdx.x];
+  for (int i = threadIdx.x; i < kMlpPad; i += blockDim.x) a.mlp_part[(size_t)blockIdx.x * kMlpPad + i] = acc[i];
+}
+
+}  // namespace gs
+
+using namespace gs;
+
+gs_status gs_launch_smooth(const gs_ctx* ctx, const float* theta, const gs_batch* b, const float* dloss, float* grad,
+                           int mode, cudaStream_t st) {
+  if (b->P <= 0) return GS_OK;
+  SmoothRunArgs a;
+  a.g = ctx->grid;
+  a.theta = theta;
+  a.P = b->P;
+  a.xs = b->xs;
+  a.eps = b->eps;
+  a.valid = b->valid;
+  a.counts = b->counts;
+  a.dloss = dloss;
+  a.lam4 = ctx->cfg.lam[4];
+  a.grad = grad;
+  a.loss_part = ctx->loss_part + (size_t)ctx->render_ctas * kLossPad;
+  a.mlp_part = ctx->mlp_part + (size_t)ctx->render_ctas * kMlpPad;
+  if (mode == 1) smooth_kernel<true, false><<<kSmoothCtas, kSmoothWarps * 32, 0, st>>>(a);
+  else if (mode == 2) smooth_kernel<false, true><<<kSmoothCtas, kSmoothWarps * 32, 0, st>>>(a);
+  else smooth_kernel<true, true><<<kSmoothCtas, kSmoothWarps * 32, 0, st>>>(a);
+  return cudaPeekAtLastError() == cudaSuccess ? GS_OK : GS_ERR_CUDA;
+}

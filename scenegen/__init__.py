@@ -67,6 +67,9 @@ def _lib():
                                       ctypes.c_void_p]
             lib.sg_sdf.restype = ctypes.c_double
             lib.sg_sdf.argtypes = [ctypes.POINTER(_Prim), ctypes.c_int, ctypes.POINTER(ctypes.c_double)]
+            lib.sg_sdf_batch.restype = None
+            lib.sg_sdf_batch.argtypes = [ctypes.POINTER(_Prim), ctypes.c_int, ctypes.c_void_p, ctypes.c_longlong,
+                                         ctypes.c_void_p]
             _LIB = lib
     return _LIB
 
@@ -92,11 +95,8 @@ class Scene:
     def sdf(self, x) -> np.ndarray:
         """Exact scene SDF at points x [P,3] (float64)."""
         x = np.ascontiguousarray(np.asarray(x, dtype=np.float64).reshape(-1, 3))
-        arr = self._array()
-        lib = _lib()
         out = np.empty(len(x))
-        for i in range(len(x)):
-            out[i] = lib.sg_sdf(arr, len(self.prims), x[i].ctypes.data_as(ctypes.POINTER(ctypes.c_double)))
+        _lib().sg_sdf_batch(self._array(), len(self.prims), x.ctypes.data, len(x), out.ctypes.data)
         return out
 
 

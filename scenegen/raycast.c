@@ -237,3 +237,9 @@ double sg_sdf(const sg_prim* prims, int n_prims, const double x[3]) {
   }
   return best;
 }
+
+/* Scene SDF at P points x [P][3] (OpenMP). */
+void sg_sdf_batch(const sg_prim* prims, int n_prims, const double* x, long long P, double* out) {
+#pragma omp parallel for schedule(static)
+  for (long long i = 0; i < P; ++i) out[i] = sg_sdf(prims, n_prims, x + 3 * i);
+}

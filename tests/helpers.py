@@ -62,3 +62,46 @@ def hand_batch(o, r, t, D, rgb=None, trunc=0.1):
     cls = np.where(D[:, None] > 0, np.where(np.abs(b) <= np.float32(trunc), 1, np.where(b > np.float32(trunc), 2, 0)),
                    0).astype(np.uint8)
     return dict(o=o, r=r, t=t, D=D, rgb=rgb, cls=cls)
+
+
+def sdf_parity_params(w, scene, seed=21, grid_std=0.05, bias=0.25, pass_offset=3.0, mix=0.1):
+    """Parameters for element-wise GPU-vs-oracle parity: the scene's exact SDF baked into
+    feature 0 of the finest level, random features elsewhere, and decoders whose every
+    hidden unit stays far from its ReLU kink.
+
+    Hidden units 0 and 1 carry phi = z[12] exactly through two always-on units
+    (0.5 relu(v + B) - 0.5 relu(B - v) = v for |v| < B); the other units get biases of
+    alternating sign and magnitude `bias`, and add a small nonlinear term (weight `mix`).
+    A realistic SDF makes adjacent samples' opacities differ, so the alpha > 0 decisions are
+    clear-cut in binary32 as well as in FP64.
+    """
+    import math
+    rng = np.random.default_rng(seed)
+    offs, n_grid, n_tot = w.layout()
+    theta = np.zeros(n_tot, np.float32)
+    theta[:n_grid] = rng.normal(0.0, grid_std, n_grid).astype(np.float32)
+    nx, ny, nz = w.dims[3]
+    X = vertex_positions(w, 3)
+    sdf = scene.sdf(X.reshape(-1, 3)).reshape(nz, ny, nx)
+    set_level_field(w, theta, 3, 0, lambda _: sdf)
+    m = sg.mlp_views(theta, n_grid)
+    m["W1"][:] = rng.uniform(-0.25, 0.25, m["W1"].shape)
+    m["W1"][:, 12] = 0.0  # the SDF feature reaches phi only through the pass-through units
+    m["b1"][:] = np.where(np.arange(32) % 2 == 0, bias, -bias)
+    m["W1"][0, :] = 0.0
+    m["W1"][1, :] = 0.0
+    m["W1"][0, 12] = 1.0
+    m["W1"][1, 12] = -1.0
+    m["b1"][0] = m["b1"][1] = pass_offset
+    m["W2"][:] = rng.uniform(-0.18, 0.18, m["W2"].shape)
+    m["W2"][0, :] = rng.uniform(-mix, mix, 32)
+    m["W2"][1:, :2] = 0.0  # the colour features do not see the pass-through units
+    m["W2"][0, 0], m["W2"][0, 1] = 0.5, -0.5
+    m["b2"][:] = rng.uniform(-0.1, 0.1, 16)
+    m["b2"][0] = 0.0
+    m["W3"][:] = rng.uniform(-0.2, 0.2, m["W3"].shape)
+    m["b3"][:] = np.where(np.arange(32) % 2 == 0, bias, -bias)
+    m["W4"][:] = rng.uniform(-0.5, 0.5, m["W4"].shape)
+    m["b4"][:] = rng.uniform(-0.2, 0.2, 3)
+    m["kappa"][0] = math.log(20.0)
+    return theta
