@@ -76,7 +76,7 @@ def lib():
             L.oc_sample_smooth.restype = None
             L.oc_sample_smooth.argtypes = [vp, vp, u64, u32, i32, vp, vp, vp, vp]
             L.oc_step.restype = i32
-            L.oc_step.argtypes = [vp, vp, i32, i32] + [vp] * 6 + [i32] + [vp] * 10
+            L.oc_step.argtypes = [vp, vp, i32, i32] + [vp] * 6 + [i32] + [vp] * 11
             L.oc_query_sdf.restype = None
             L.oc_query_sdf.argtypes = [vp, vp, vp, i32, vp, vp]
             L.oc_voxel_index.restype = None
@@ -172,13 +172,14 @@ def step(cfg: OcConfig, theta, batch: dict, smooth: dict | None, dloss=None, wan
     rgb_hat, d_hat, wsum = np.zeros((R, 3)), np.zeros(R), np.zeros(R)
     grad = np.zeros_like(th) if want_grad else None
     margins = np.zeros(10) if want_margins else None
+    amb = np.zeros((R, N), np.uint8) if want_margins else None
     dl = None if dloss is None else np.ascontiguousarray(dloss, dtype=np.float64)
     rc = lib().oc_step(ctypes.byref(cfg), _p(th), R, N, _p(batch["o"]), _p(batch["r"]), _p(batch["rgb"]),
                        _p(batch["D"]), _p(batch["t"]), _p(batch["cls"]), P, _p(xs), _p(eps), _p(valid), _p(dl),
-                       _p(loss), _p(rgb_hat), _p(d_hat), _p(wsum), _p(grad), _p(margins))
+                       _p(loss), _p(rgb_hat), _p(d_hat), _p(wsum), _p(grad), _p(margins), _p(amb))
     if rc != 0:
         raise ValueError("oc_step rejected its arguments")
-    return dict(loss=loss, rgb_hat=rgb_hat, d_hat=d_hat, wsum=wsum, grad=grad, margins=margins)
+    return dict(loss=loss, rgb_hat=rgb_hat, d_hat=d_hat, wsum=wsum, grad=grad, margins=margins, amb=amb)
 
 
 def query_sdf(cfg: OcConfig, theta, x, want_grad=True):

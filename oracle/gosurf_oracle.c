@@ -596,13 +596,18 @@ static void mmin(double* a, double v) {
  * dloss[6]: upstream derivative of each output (rgb, depth, sdf, fs, smooth, total); the
  * effective weight of term k is dloss[k] + lam[k] * dloss[5].  NULL means (0,..,0,1).
  * loss[6]: L_rgb, L_d, L_sdf, L_fs, L_smooth, total.  rgb_hat[R,3], d_hat[R], wsum[R] may be
- * NULL.  grad: same layout as theta, overwritten.  margins[8] may be NULL.
+ * NULL.  grad: same layout as theta, overwritten.  margins[10] may be NULL.
+ * amb [R,N] (may be NULL) flags the samples whose branch decisions lie within binary32
+ * rounding of a tie: bit 0 the alpha_k > 0 decision (|q_k| < 1e-5, unsaturated, untied),
+ * bit 1 the sign of phi - b on S_tr (|phi - b| < 2e-5), bit 2 the free-space max (gap < 2e-5).
+ * Bit 0 is set only when gradients are requested and a flip would change dL/dphi by more
+ * than 1e-7.
  * Returns 0, or -1 on a bad argument.
  */
 int oc_step(const oc_config* c, const double* theta, int R, int N, const float* o, const float* r,
             const float* rgb, const float* D, const float* t, const uint8_t* cls, int P, const float* xs,
             const float* eps, const uint8_t* valid, const double* dloss, double* loss, double* rgb_hat,
-            double* d_hat, double* wsum, double* grad, double* margins) {
+            double* d_hat, double* wsum, double* grad, double* margins, uint8_t* amb) {
   if (R < 0 || N < 2 || P < 0) return -1;
   const int64_t ng = grid_size(c);
   mlp_t m = mlp_view(theta + ng);
@@ -621,6 +626,7 @@ int oc_step(const oc_config* c, const double* theta, int R, int N, const float* 
 
   double wt[5];
   for (int k = 0; k < 5; ++k) wt[k] = dloss ? dloss[k] + (double)c->lam[k] * dloss[5] : (double)c->lam[k];
+  if (amb) memset(amb, 0, (size_t)R * N);
   const int do_grad = grad != NULL;
 
   int nthreads = 1;
@@ -681,7 +687,11 @@ int oc_step(const oc_config* c, const double* theta, int R, int N, const float* 
         double den = Phi[k] > 1e-6 ? Phi[k] : 1e-6;
         /* a flip of the alpha > 0 branch changes dphi by about s (1 - Phi_k) |dL/dalpha|, so
          * saturated samples (1 - Phi_k < 1e-5) and exact ties (equal phi) are not counted */
-        if (phi[k] != phi[k + 1] && 1.0 - Phi[k] > 1e-5) mmin(&mg->m[1], (Phi[k] - Phi[k + 1]) / den);
+        if (phi[k] != phi[k + 1] && 1.0 - Phi[k] > 1e-5) {
+          double q = (Phi[k] - Phi[k + 1]) / den;
+          mmin(&mg->m[1], q);
+
+        }
         mmin(&mg->m[2], Phi[k] - 1e-6);
         uint64_t sid = ((uint64_t)i * (uint64_t)N + (uint64_t)k) * 8;
         sigmix(&mg->sig, sid + 2, (uint64_t)(alpha[k] > 0) | (uint64_t)(Phi[k] > 1e-6) << 1);
@@ -710,6 +720,7 @@ int oc_step(const oc_config* c, const double* theta, int R, int N, const float* 
         if (cl == CLS_TR) {
           lsum[2] += fabs(phi[k] - b);
           mmin(&mg->m[3], phi[k] - b);
+          if (amb && fabs(phi[k] - b) < 2e-5) amb[(size_t)i * N + k] |= 2;
           sigmix(&mg->sig, ((uint64_t)i * (uint64_t)N + (uint64_t)k) * 8 + 3, (uint64_t)(phi[k] > b));
         } else if (cl == CLS_FS) {
           double e = exp(-(double)c->kappa_fs * phi[k]) - 1.0, lin = phi[k] - b;
@@ -721,6 +732,7 @@ int oc_step(const oc_config* c, const double* theta, int R, int N, const float* 
           for (int q = 0; q < 3; ++q)
             if (q != arg && v[q] > second) second = v[q];
           mmin(&mg->m[4], top - second);
+          if (amb && top - second < 2e-5) amb[(size_t)i * N + k] |= 4;
           sigmix(&mg->sig, ((uint64_t)i * (uint64_t)N + (uint64_t)k) * 8 + 4, (uint64_t)arg);
           lsum[3] += top;
         }
@@ -743,11 +755,15 @@ int oc_step(const oc_config* c, const double* theta, int R, int N, const float* 
         double dalpha = T[k] * (ek - U[k]);
         double den = Phi[k] > 1e-6 ? Phi[k] : 1e-6;
         double q = (Phi[k] - Phi[k + 1]) / den;
-        if (fabs(q) < 1e-6 && phi[k] != phi[k + 1]) {
+        if (fabs(q) < 1e-5 && phi[k] != phi[k + 1] && 1.0 - Phi[k] > 1e-5) {
           double self = fabs(dalpha) * s * Phi[k] * (1.0 - Phi[k]) / den;
           double next = fabs(dalpha) * s * Phi[k + 1] * (1.0 - Phi[k + 1]) / den;
           double imp = self > next ? self : next;
-          if (imp > mg->m[8]) mg->m[8] = imp;
+          if (fabs(q) < 1e-6 && imp > mg->m[8]) mg->m[8] = imp;
+          /* binary32 decides sign(Phi_k - Phi_k+1) = sign(phi_k - phi_k+1) reliably once the
+           * two SDF values differ by more than a few ulps */
+          double dphi_rel = fabs(phi[k] - phi[k + 1]) / (fabs(phi[k]) > 1.0 ? fabs(phi[k]) : 1.0);
+          if (amb && imp > 1e-7 && dphi_rel < 2e-6) amb[(size_t)i * N + k] |= 1;
         }
         if (q > 0) {
           dPhi[k + 1] += dalpha * (-1.0 / den);

@@ -68,28 +68,37 @@ def sample_positions(bt):
     return (bt["o"][:, None, :] + (t[..., None] * bt["r"][:, None, :]).astype(np.float32)).astype(np.float32)
 
 
-def scrub_ambiguous(p: Problem, theta, bt, tol=2e-5):
-    """Remove from supervision the samples whose class decision is within binary32 rounding
-    of a tie (|phi - b| ~ 0 for the truncated-SDF sign, equal entries of the free-space max),
-    on a copy of the oracle batch.  Returns the new cls [R,N] and counts [4]."""
-    x = sample_positions(bt)
-    R, N = bt["t"].shape
-    phi, _ = oc.query_sdf(p.cfg, np.asarray(theta, np.float64), x.reshape(-1, 3), want_grad=False)
-    phi = phi.reshape(R, N)
-    b = bt["D"].astype(np.float64)[:, None] - bt["t"].astype(np.float64)
-    cls = bt["cls"].copy()
-    amb_tr = (cls == oc.CLS_TR) & (np.abs(phi - b) < tol)
-    e = np.exp(-p.w.kappa_fs * phi) - 1.0
-    lin = phi - b
-    vals = np.stack([np.zeros_like(phi), e, lin], -1)
-    srt = np.sort(vals, -1)
-    amb_fs = (cls == oc.CLS_FS) & (srt[..., 2] - srt[..., 1] < tol)
-    cls[amb_tr | amb_fs] = oc.CLS_NONE
-    counts = np.array([(bt["D"] > 0).sum(), (cls == 1).sum(), (cls == 2).sum(), 0], np.int64)
-    return cls, counts, int(amb_tr.sum() + amb_fs.sum())
+def _classes(D, t, trunc):
+    """Sample classes by the bound b = D - t (binary32), as the sampler assigns them."""
+    b = (D[:, None] - t).astype(np.float32)
+    tr = np.float32(trunc)
+    return np.where(D[:, None] > 0, np.where(np.abs(b) <= tr, 1, np.where(b > tr, 2, 0)), 0).astype(np.uint8)
 
 
-def upload_oracle_batch(bt, sm, counts_smooth, cls=None, counts=None, device="cuda"):
+def prepare_parity_batch(p: Problem, theta, bt, sm, max_iter=6, max_drop=0.1):
+    """Subset of the oracle batch on which no branch decision lies within binary32 rounding
+    of a tie, so that the FP32 kernels and the FP64 oracle take every branch the same way.
+
+    The oracle flags the samples whose alpha > 0 decision (when a flip would move dL/dphi by
+    more than 1e-7), truncated-SDF sign or free-space maximum is that close to a tie; the rays
+    holding them are left out and both sides run on the remaining rays.  Returns (batch,
+    reference step, number of rays left out)."""
+    keep = np.ones(len(bt["D"]), bool)
+    for _ in range(max_iter):
+        sub = {k: (v[keep] if k != "counts" else v) for k, v in bt.items()}
+        sub["counts"] = np.array([(sub["D"] > 0).sum(), (sub["cls"] == 1).sum(), (sub["cls"] == 2).sum(), 0],
+                                 np.int64)
+        ref = oc.step(p.cfg, theta, sub, sm, want_margins=True)
+        bad = ref["amb"].any(axis=1)
+        if not bad.any():
+            dropped = int((~keep).sum())
+            assert dropped <= max_drop * len(keep), dropped
+            return sub, ref, dropped
+        keep[np.nonzero(keep)[0][bad]] = False
+    raise AssertionError("could not move the parity batch away from binary32 ties")
+
+
+def upload_oracle_batch(bt, sm, counts_smooth, device="cuda"):
     """Device batch holding exactly the oracle's sampled inputs (for tests that modify them)."""
     R, N = bt["t"].shape
     P = 0 if sm is None else len(sm["valid"])
@@ -100,12 +109,12 @@ def upload_oracle_batch(bt, sm, counts_smooth, cls=None, counts=None, device="cu
     b.rgb.copy_(torch.from_numpy(bt["rgb"]))
     b.depth.copy_(torch.from_numpy(bt["D"]))
     b.t.copy_(torch.from_numpy(bt["t"]))
-    b.cls.copy_(torch.from_numpy(bt["cls"] if cls is None else cls))
+    b.cls.copy_(torch.from_numpy(bt["cls"]))
     if P > 0:
         b.xs[:P].copy_(torch.from_numpy(sm["xs"]))
         b.eps[:P].copy_(torch.from_numpy(sm["eps"]))
         b.valid[:P].copy_(torch.from_numpy(sm["valid"]))
-    c = bt["counts"] if counts is None else counts
+    c = bt["counts"]
     b.counts.copy_(torch.tensor([int(c[0]), int(c[1]), int(c[2]), int(counts_smooth)], dtype=torch.int32))
     return b
 
