@@ -157,6 +157,21 @@ gs_status gs_query_sdf(gs_ctx* ctx, const float* theta, const float* x, int32_t 
  * x (clamped to the grid box) at each level, decided in binary32. */
 gs_status gs_voxel_index(gs_ctx* ctx, const float* x, int32_t P, int64_t* out, void* stream);
 
+/* Allocation-free variant of gs_forward_backward (the paper has no counterpart).  For callers
+ * that may not allocate device memory -- e.g. code inside a host framework that owns every
+ * device allocation (a plugin or custom operator that must draw from the framework's pool),
+ * or a latency-critical loop that cannot take cudaMalloc's implicit device synchronisation.
+ * It takes the configuration instead of a context and allocates nothing: the kernels'
+ * per-CTA partial rows live in a file-scope device array of 1.73 MB (rows for 256 CTAs),
+ * which every GPU that loads the library holds until the process exits.  Devices with more
+ * than 192 SMs are rejected with GS_ERR_UNSUPPORTED.  The first call on a device resolves the
+ * array's device address and writes its default dloss (a synchronous set-up), so make that
+ * first call before any stream capture.  All calls share the array: calls whose work
+ * overlaps on the GPU (other streams, other host threads) race and give wrong results.
+ * Arguments, outputs and errors as gs_forward_backward; messages via gs_last_error(NULL). */
+gs_status gs_forward_backward_noalloc(const gs_config* cfg, const float* theta, const gs_batch* batch,
+                                      const float* dloss, float* loss, float* grad, void* stream);
+
 /* Synchronises the context's last stream and reports device-side check failures. */
 gs_status gs_sync_status(gs_ctx* ctx);
 

@@ -17,7 +17,7 @@ STATUS = {0: "GS_OK", 1: "GS_ERR_INVALID_ARG", 2: "GS_ERR_SHAPE", 3: "GS_ERR_ALI
 
 EXPORTS = ["gs_create", "gs_destroy", "gs_param_count", "gs_sample_rays", "gs_forward", "gs_backward",
            "gs_forward_backward", "gs_adam_step", "gs_query_sdf", "gs_voxel_index", "gs_sync_status",
-           "gs_last_error"]
+           "gs_last_error", "gs_forward_backward_noalloc"]
 
 
 class GsConfig(ctypes.Structure):
@@ -80,6 +80,9 @@ def lib():
             L.gs_voxel_index.argtypes = [vp, vp, i32, vp, vp]
             L.gs_sync_status.restype = i32
             L.gs_sync_status.argtypes = [vp]
+            L.gs_forward_backward_noalloc.restype = i32
+            L.gs_forward_backward_noalloc.argtypes = [ctypes.POINTER(GsConfig), vp, ctypes.POINTER(GsBatch), vp, vp,
+                                                      vp, vp]
             L.gs_last_error.restype = ctypes.c_char_p
             L.gs_last_error.argtypes = [vp]
             _LIB = L

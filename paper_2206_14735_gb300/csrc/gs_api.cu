@@ -43,6 +43,9 @@ gs_status check_batch(gs_ctx* ctx, const gs_batch* b, bool need_smooth_arrays) {
 
 }  // namespace
 
+// Records a message for gs_last_error(NULL) (used by entry points that have no context).
+void gs_set_thread_error(const char* msg) { g_err = msg; }
+
 extern "C" {
 
 int64_t gs_param_count(const gs_config* cfg, int64_t* n_grid) {

@@ -41,3 +41,4 @@ gs_status gs_launch_adam(float* theta, float* grad, float* m, float* v, long lon
 gs_status gs_launch_query(const gs_ctx* ctx, const float* theta, const float* x, int P, float* sdf, float* grad,
                           cudaStream_t st);
 gs_status gs_launch_voxel_index(const gs_ctx* ctx, const float* x, int P, long long* out, cudaStream_t st);
+void gs_set_thread_error(const char* msg);

@@ -1,0 +1,119 @@
+// Allocation-free variant of gs_forward_backward.  The paper has no counterpart: this
+// entry point exists for callers that may not allocate device memory -- for example code
+// running inside a host framework that owns every device allocation (a plugin or custom
+// operator whose memory must come from the framework's own pool), or a latency-critical
+// loop that cannot afford the implicit device synchronisation of cudaMalloc.
+//
+// The fused render kernel needs per-CTA partial rows (loss sums and decoder-gradient sums)
+// that gs_create would otherwise allocate.  Here they live in one file-scope device array
+// of fixed size, which every GPU that loads this library holds until the process exits.
+#include <mutex>
+
+#include "gs_internal.h"
+
+namespace {
+
+// partial rows for up to 256 CTAs: the render kernel uses one CTA per SM and the
+// smoothness kernel kSmoothCtas, so devices with up to 256 - kSmoothCtas = 192 SMs fit
+constexpr int kNoAllocRows = 256;
+constexpr size_t kNoAllocFloats = (size_t)kNoAllocRows * (kLossPad + kMlpPad) + 8;  // + default dloss
+
+__device__ __align__(256) float g_noalloc_scratch[kNoAllocFloats];  // 1.73 MB
+
+constexpr int kMaxDevices = 64;
+std::mutex g_setup_mu;
+float* g_scratch_ptr[kMaxDevices] = {};  // device address of g_noalloc_scratch, per device
+
+// Once per device, with that device current: the array's device address (the host-side
+// name is only a stand-in) and the default upstream derivative (0,0,0,0,0,1).
+gs_status setup_device(int dev, float** out) {
+  std::lock_guard<std::mutex> lock(g_setup_mu);
+  if (g_scratch_ptr[dev] == nullptr) {
+    float* p = nullptr;
+    if (cudaGetSymbolAddress(reinterpret_cast<void**>(&p), g_noalloc_scratch) != cudaSuccess || p == nullptr)
+      return GS_ERR_CUDA;
+    const float dl[8] = {0.f, 0.f, 0.f, 0.f, 0.f, 1.f, 0.f, 0.f};
+    if (cudaMemcpy(p + (size_t)kNoAllocRows * (kLossPad + kMlpPad), dl, sizeof(dl), cudaMemcpyHostToDevice) !=
+        cudaSuccess)
+      return GS_ERR_CUDA;
+    g_scratch_ptr[dev] = p;
+  }
+  *out = g_scratch_ptr[dev];
+  return GS_OK;
+}
+
+}  // namespace
+
+static gs_status noalloc_fail(gs_status s, const char* msg) {
+  gs_set_thread_error(msg);
+  return s;
+}
+
+extern "C" gs_status gs_forward_backward_noalloc(const gs_config* cfg, const float* theta, const gs_batch* batch,
+                                                 const float* dloss, float* loss, float* grad, void* stream) {
+  if (!cfg) return noalloc_fail(GS_ERR_INVALID_ARG, "gs_forward_backward_noalloc: cfg is NULL");
+  for (int l = 0; l < GS_LEVELS; ++l) {
+    for (int a = 0; a < 3; ++a)
+      if (cfg->dims[l][a] < 2)
+        return noalloc_fail(GS_ERR_INVALID_ARG, "gs_forward_backward_noalloc: every level needs >= 2 vertices per axis");
+    if (!(cfg->voxel[l] > 0.0f)) return noalloc_fail(GS_ERR_INVALID_ARG, "gs_forward_backward_noalloc: voxel size must be > 0");
+  }
+  const int N = cfg->n_strat + cfg->n_guided;
+  if (cfg->n_strat < 1 || cfg->n_guided < 0 || N < 2 || N > 128)
+    return noalloc_fail(GS_ERR_SHAPE, "gs_forward_backward_noalloc: samples per ray must be in [2, 128]");
+  if (!theta || !loss || !grad || !batch) return noalloc_fail(GS_ERR_INVALID_ARG, "gs_forward_backward_noalloc: NULL argument");
+  if ((reinterpret_cast<uintptr_t>(theta) & 15u) || (reinterpret_cast<uintptr_t>(grad) & 15u))
+    return noalloc_fail(GS_ERR_ALIGN, "gs_forward_backward_noalloc: theta and grad must be 16-byte aligned");
+  if (batch->R < 0 || batch->R > cfg->max_rays || batch->N != N || batch->P < 0 || batch->P > cfg->max_smooth ||
+      !batch->counts)
+    return noalloc_fail(GS_ERR_SHAPE, "gs_forward_backward_noalloc: batch sizes outside the configuration");
+  if (batch->R > 0 && (!batch->origin || !batch->dir || !batch->rgb || !batch->depth || !batch->t || !batch->cls))
+    return noalloc_fail(GS_ERR_INVALID_ARG, "gs_forward_backward_noalloc: batch ray array is NULL");
+  if (batch->P > 0 && (!batch->xs || !batch->eps || !batch->valid))
+    return noalloc_fail(GS_ERR_INVALID_ARG, "gs_forward_backward_noalloc: batch smoothness array is NULL");
+  int dev = 0, sms = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices ||
+      cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
+    return noalloc_fail(GS_ERR_CUDA, "gs_forward_backward_noalloc: no usable CUDA device");
+  if (sms + kSmoothCtas > kNoAllocRows)
+    return noalloc_fail(GS_ERR_UNSUPPORTED,
+                        "gs_forward_backward_noalloc: the static scratch holds partial rows for at most 192 SMs");
+  float* scratch = nullptr;
+  if (setup_device(dev, &scratch) != GS_OK)
+    return noalloc_fail(GS_ERR_CUDA, "gs_forward_backward_noalloc: could not resolve the static scratch array");
+
+  // a context on the stack whose workspace points into the static array (no allocation)
+  gs_ctx c;
+  c.cfg = *cfg;
+  long long off = 0;
+  for (int l = 0; l < GS_LEVELS; ++l) {
+    for (int a = 0; a < 3; ++a) c.grid.dims[l][a] = cfg->dims[l][a];
+    c.grid.voxel[l] = cfg->voxel[l];
+    c.grid.inv_voxel[l] = 1.0f / cfg->voxel[l];
+    c.grid.off[l] = off;
+    off += (long long)cfg->dims[l][0] * cfg->dims[l][1] * cfg->dims[l][2] * GS_FEAT;
+  }
+  for (int a = 0; a < 3; ++a) c.grid.origin[a] = cfg->origin[a];
+  c.grid.n_grid = off;
+  c.device = dev;
+  c.num_sms = sms;
+  c.render_ctas = sms;
+  c.loss_part = scratch;
+  c.mlp_part = scratch + (size_t)kNoAllocRows * kLossPad;
+  c.default_dloss = scratch + (size_t)kNoAllocRows * (kLossPad + kMlpPad);
+  const float* dl = dloss ? dloss : c.default_dloss;
+  cudaStream_t st = (cudaStream_t)stream;
+  if (batch->R > 0 && gs_launch_render(&c, theta, batch, dl, grad, nullptr, nullptr, nullptr, 3, st) != GS_OK)
+    return noalloc_fail(GS_ERR_CUDA, "gs_forward_backward_noalloc: render launch failed");
+  if (gs_launch_smooth(&c, theta, batch, dl, grad, 3, st) != GS_OK)
+    return noalloc_fail(GS_ERR_CUDA, "gs_forward_backward_noalloc: smoothness launch failed");
+  // combine the rows written by this call: render CTAs (if any rays), then smoothness CTAs
+  c.n_parts = (batch->R > 0 ? sms : 0) + (batch->P > 0 ? kSmoothCtas : 0);
+  if (batch->R == 0) {
+    c.loss_part += (size_t)sms * kLossPad;
+    c.mlp_part += (size_t)sms * kMlpPad;
+  }
+  if (gs_launch_finalize(&c, batch, loss, grad, 3, st) != GS_OK)
+    return noalloc_fail(GS_ERR_CUDA, "gs_forward_backward_noalloc: finalize launch failed");
+  return GS_OK;
+}
