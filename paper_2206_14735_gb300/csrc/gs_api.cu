@@ -90,7 +90,7 @@ gs_status gs_create(const gs_config* cfg, gs_ctx** out) {
   }
   for (int a = 0; a < 3; ++a) g.origin[a] = cfg->origin[a];
   g.n_grid = off;
-  c->render_ctas = c->num_sms;
+  c->render_ctas = kRenderCtasPerSm * c->num_sms;
   c->n_parts = c->render_ctas + kSmoothCtas;
   const float dl[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 1.f};
   if (cudaMalloc(&c->loss_part, sizeof(float) * kLossPad * c->n_parts) != cudaSuccess ||

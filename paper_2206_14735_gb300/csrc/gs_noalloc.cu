@@ -13,12 +13,12 @@
 
 namespace {
 
-// partial rows for up to 256 CTAs: the render kernel uses one CTA per SM and the
-// smoothness kernel kSmoothCtas, so devices with up to 256 - kSmoothCtas = 192 SMs fit
-constexpr int kNoAllocRows = 256;
-constexpr size_t kNoAllocFloats = (size_t)kNoAllocRows * (kLossPad + kMlpPad) + 8;  // + default dloss
+// partial rows for up to 448 CTAs: the render kernel uses kRenderCtasPerSm (2) CTAs per SM
+// and the smoothness kernel kSmoothCtas (64), so devices with up to 192 SMs fit
+constexpr int kNoAllocRows = 448;
+constexpr size_t kNoAllocFloats = (size_t)kNoAllocRows * (kLossPad + kMlpPad) + 16;  // + default dloss, status
 
-__device__ __align__(256) float g_noalloc_scratch[kNoAllocFloats];  // 1.73 MB
+__device__ __align__(256) float g_noalloc_scratch[kNoAllocFloats];  // 3.04 MB
 
 constexpr int kMaxDevices = 64;
 std::mutex g_setup_mu;
@@ -32,7 +32,7 @@ gs_status setup_device(int dev, float** out) {
     float* p = nullptr;
     if (cudaGetSymbolAddress(reinterpret_cast<void**>(&p), g_noalloc_scratch) != cudaSuccess || p == nullptr)
       return GS_ERR_CUDA;
-    const float dl[8] = {0.f, 0.f, 0.f, 0.f, 0.f, 1.f, 0.f, 0.f};
+    const float dl[16] = {0.f, 0.f, 0.f, 0.f, 0.f, 1.f};  // default dloss, then a zeroed status word
     if (cudaMemcpy(p + (size_t)kNoAllocRows * (kLossPad + kMlpPad), dl, sizeof(dl), cudaMemcpyHostToDevice) !=
         cudaSuccess)
       return GS_ERR_CUDA;
@@ -75,7 +75,7 @@ extern "C" gs_status gs_forward_backward_noalloc(const gs_config* cfg, const flo
   if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices ||
       cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
     return noalloc_fail(GS_ERR_CUDA, "gs_forward_backward_noalloc: no usable CUDA device");
-  if (sms + kSmoothCtas > kNoAllocRows)
+  if (kRenderCtasPerSm * sms + kSmoothCtas > kNoAllocRows)
     return noalloc_fail(GS_ERR_UNSUPPORTED,
                         "gs_forward_backward_noalloc: the static scratch holds partial rows for at most 192 SMs");
   float* scratch = nullptr;
@@ -97,10 +97,11 @@ extern "C" gs_status gs_forward_backward_noalloc(const gs_config* cfg, const flo
   c.grid.n_grid = off;
   c.device = dev;
   c.num_sms = sms;
-  c.render_ctas = sms;
+  c.render_ctas = kRenderCtasPerSm * sms;
   c.loss_part = scratch;
   c.mlp_part = scratch + (size_t)kNoAllocRows * kLossPad;
   c.default_dloss = scratch + (size_t)kNoAllocRows * (kLossPad + kMlpPad);
+  c.status = reinterpret_cast<int*>(c.default_dloss + 8);  // device-side check word
   const float* dl = dloss ? dloss : c.default_dloss;
   cudaStream_t st = (cudaStream_t)stream;
   if (batch->R > 0 && gs_launch_render(&c, theta, batch, dl, grad, nullptr, nullptr, nullptr, 3, st) != GS_OK)
@@ -108,10 +109,10 @@ extern "C" gs_status gs_forward_backward_noalloc(const gs_config* cfg, const flo
   if (gs_launch_smooth(&c, theta, batch, dl, grad, 3, st) != GS_OK)
     return noalloc_fail(GS_ERR_CUDA, "gs_forward_backward_noalloc: smoothness launch failed");
   // combine the rows written by this call: render CTAs (if any rays), then smoothness CTAs
-  c.n_parts = (batch->R > 0 ? sms : 0) + (batch->P > 0 ? kSmoothCtas : 0);
+  c.n_parts = (batch->R > 0 ? c.render_ctas : 0) + (batch->P > 0 ? kSmoothCtas : 0);
   if (batch->R == 0) {
-    c.loss_part += (size_t)sms * kLossPad;
-    c.mlp_part += (size_t)sms * kMlpPad;
+    c.loss_part += (size_t)c.render_ctas * kLossPad;
+    c.mlp_part += (size_t)c.render_ctas * kMlpPad;
   }
   if (gs_launch_finalize(&c, batch, loss, grad, 3, st) != GS_OK)
     return noalloc_fail(GS_ERR_CUDA, "gs_forward_backward_noalloc: finalize launch failed");

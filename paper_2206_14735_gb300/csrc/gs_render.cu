@@ -1,13 +1,13 @@
 // Loss / decoder-gradient combination, SDF query and cell lookup, and the dispatch of the
-// fused render kernel over samples-per-ray (its instantiations live in gs_render_n*.cu).
-#include "gs_render_kernel.cuh"
+// fused render kernel over samples-per-ray (its instantiations live in gs_render_tc_n*.cu).
+#include "gs_render_tc.cuh"
 
 namespace gs {
 
-extern template gs_status launch_n<1>(const gs_ctx*, RenderArgs&, int, cudaStream_t);
-extern template gs_status launch_n<2>(const gs_ctx*, RenderArgs&, int, cudaStream_t);
-extern template gs_status launch_n<3>(const gs_ctx*, RenderArgs&, int, cudaStream_t);
-extern template gs_status launch_n<4>(const gs_ctx*, RenderArgs&, int, cudaStream_t);
+extern template gs_status launch_tc_n<1>(const gs_ctx*, RenderTcArgs&, int, cudaStream_t);
+extern template gs_status launch_tc_n<2>(const gs_ctx*, RenderTcArgs&, int, cudaStream_t);
+extern template gs_status launch_tc_n<3>(const gs_ctx*, RenderTcArgs&, int, cudaStream_t);
+extern template gs_status launch_tc_n<4>(const gs_ctx*, RenderTcArgs&, int, cudaStream_t);
 
 // ------------------------------------------------------------------------------------
 // combine per-CTA partials: losses in FP64, decoder gradients in a fixed order
@@ -128,7 +128,7 @@ using namespace gs;
 
 gs_status gs_launch_render(const gs_ctx* ctx, const float* theta, const gs_batch* b, const float* dloss, float* grad,
                            float* rgb_hat, float* d_hat, float* wsum, int mode, cudaStream_t st) {
-  RenderArgs a;
+  RenderTcArgs a;
   a.g = ctx->grid;
   a.theta = theta;
   a.R = b->R;
@@ -149,14 +149,15 @@ gs_status gs_launch_render(const gs_ctx* ctx, const float* theta, const gs_batch
   a.rgb_hat = rgb_hat;
   a.d_hat = d_hat;
   a.wsum = wsum;
+  a.status = ctx->status;
   const int n0 = ctx->grid.dims[0][0] * ctx->grid.dims[0][1] * ctx->grid.dims[0][2];
   a.lvl0_staged = n0 <= kLvl0MaxVerts;
   const int nch = (b->N + 31) / 32;
   switch (nch) {
-    case 1: return launch_n<1>(ctx, a, mode, st);
-    case 2: return launch_n<2>(ctx, a, mode, st);
-    case 3: return launch_n<3>(ctx, a, mode, st);
-    case 4: return launch_n<4>(ctx, a, mode, st);
+    case 1: return launch_tc_n<1>(ctx, a, mode, st);
+    case 2: return launch_tc_n<2>(ctx, a, mode, st);
+    case 3: return launch_tc_n<3>(ctx, a, mode, st);
+    case 4: return launch_tc_n<4>(ctx, a, mode, st);
     default: return GS_ERR_UNSUPPORTED;
   }
 }

@@ -1,0 +1,822 @@
+// Fused per-ray pass of one GO-Surf step with the decoders on the tcgen05 tensor cores.
+//
+// What it computes (same as the paper's step, Sec. 3.1-3.4): multi-level trilinear gather,
+// geometry and colour decoders, NeuS compositing, the rgb / depth / sdf / free-space losses
+// and, in the same pass, their reverse mode down to every grid feature and decoder weight.
+//
+// Mapping.  A "group" of 4 warps owns one M = 128 tensor-core tile: warp w of the group
+// renders one ray and its 32-sample chunk j fills tile rows 32w..32w+31, which are exactly
+// the tensor-memory lanes that warp may read.  Each decoder layer of a chunk is one MMA
+// phase: every thread writes its sample's activation row into the shared-memory A operand
+// (K-major, no swizzle), one thread issues the MMA(s) against the shared-memory weight tile,
+// the result lands in tensor memory and every thread reads its own row back with
+// tcgen05.ld.  Forward: 4 phases per chunk.  Reverse: the forward is recomputed (4 phases)
+// and the four activation adjoints run as 4 more phases; the decoder weight gradients are
+// reduced on CUDA cores as 4x4 register tiles over the warp's 32 staged samples while the
+// next MMA runs.  FP32 form: each operand is split into three bfloat16 parts and the six
+// leading part products are accumulated in FP32 (FP32-grade accuracy on BF16 tensor cores).
+// Compositing and its adjoint are warp scans over the ray's chunks, as in the CUDA-core
+// design; grid gradients are scattered with 16-byte vector atomics (coarsest level first
+// accumulated in shared memory).
+#pragma once
+#include "gs_internal.h"
+#include <cuda_bf16.h>
+
+#include "gs_tc.cuh"
+
+namespace gs {
+
+// Operand precisions.  Every operand is split into `planes` bfloat16 parts
+// x = x0 + x1 + x2 (x0 = bf16(x), x1 = bf16(x - x0), x2 = bf16(x - x0 - x1): 24 significant
+// bits) and a product is the sum of the part products with i + j < planes, accumulated in
+// FP32 by the tensor core: 6 MMAs per K step give FP32-grade products (the dropped terms
+// are below 2^-24 relative), 1 MMA per step is the plain BF16 form.
+struct PrecBF16x3 {
+  static constexpr int kind = tc::KIND_BF16;
+  static constexpr int es = 2;      // bytes per operand element
+  static constexpr int kmma = 16;   // K per MMA instruction
+  static constexpr int planes = 3;
+};
+struct PrecBF16 {
+  static constexpr int kind = tc::KIND_BF16;
+  static constexpr int es = 2;
+  static constexpr int kmma = 16;
+  static constexpr int planes = 1;
+};
+
+constexpr int kKD = 16;  // padded K of the colour-output adjoint (3 real columns) = one bf16 K step
+
+// weight (B) tiles: {N, K} of the 8 decoder contractions
+//   0 W1  32x16 | 1 W2 16x32 | 2 W3 32x16 (col 15 zero) | 3 W4 16x32 (rows 3.. zero)
+//   4 W4^T 32xKD (cols 3.. zero) | 5 W3^T 16x32 (row 15 zero) | 6 W2^T 32x16 | 7 W1^T 16x32
+__host__ __device__ constexpr int wN(int i) { return (i == 0 || i == 2 || i == 4 || i == 6) ? 32 : 16; }
+__host__ __device__ constexpr int wK(int i) { return i == 4 ? kKD : ((i == 0 || i == 2 || i == 6) ? 16 : 32); }
+template <class P>
+__host__ __device__ constexpr uint32_t wBytes(int i) { return (uint32_t)(wN(i) * wK(i) * P::es); }
+template <class P>
+__host__ __device__ constexpr uint32_t wOff(int i) {
+  uint32_t o = 0;
+  for (int k = 0; k < i; ++k) o += wBytes<P>(k);
+  return o;
+}
+template <class P>
+__host__ __device__ constexpr uint32_t wTotal() { return wOff<P>(8); }
+
+// tensor-memory columns of one group
+constexpr uint32_t cD1 = 0, cD2 = 32, cD3 = 48, cX = 80, cY = 112, kGroupCols = 128;
+
+constexpr int kGroupThreads = 128;
+constexpr int kStRow = 52;  // staged row: 48 floats + 4 pad (row stride = 20 mod 32 banks)
+constexpr uint32_t kMbarLimit = 1u << 26;  // bounded MMA-completion wait
+
+template <class P>
+struct TcLayout {
+  static constexpr uint32_t a_bytes = 128u * 32u * P::es;  // one A operand plane, K <= 32
+  static constexpr uint32_t stage_bytes = 4u * 32u * kStRow * 4u;
+  static constexpr uint32_t group_bytes = a_bytes * P::planes + stage_bytes + 128;  // + mbarrier, flag
+};
+
+__device__ __forceinline__ void group_sync(int g) {
+  asm volatile("bar.sync %0, %1;" ::"r"(1 + g), "r"(kGroupThreads) : "memory");
+}
+
+// ---- operand rows ---------------------------------------------------------------------
+// bf16 parts of x (round to nearest even; the differences are exact in binary32)
+template <int PL>
+__device__ __forceinline__ void split_bf16(float x, __nv_bfloat16 (&p)[PL]) {
+  float r = x;
+#pragma unroll
+  for (int i = 0; i < PL; ++i) {
+    p[i] = __float2bfloat16_rn(r);
+    r = r - __bfloat162float(p[i]);
+  }
+}
+
+// write K values as row `row` of a K-major no-swizzle tile, one plane per bf16 part
+template <class P, int K>
+__device__ __forceinline__ void store_row(uint8_t* planes, int row, const float* v) {
+  constexpr uint32_t sbo = (uint32_t)(K * P::es / 16) * 128u;
+  constexpr uint32_t plane_bytes = 128u * 32u * P::es;
+#pragma unroll
+  for (int c = 0; c < K / 8; ++c) {
+    __nv_bfloat16 e[8][P::planes];
+#pragma unroll
+    for (int q = 0; q < 8; ++q) split_bf16<P::planes>(v[8 * c + q], e[q]);
+    const uint32_t off = tc::core_offset((uint32_t)row, (uint32_t)c, 128u, sbo);
+#pragma unroll
+    for (int pl = 0; pl < P::planes; ++pl) {
+      uint4 u;
+      u.x = (uint32_t)__bfloat16_as_ushort(e[0][pl]) | ((uint32_t)__bfloat16_as_ushort(e[1][pl]) << 16);
+      u.y = (uint32_t)__bfloat16_as_ushort(e[2][pl]) | ((uint32_t)__bfloat16_as_ushort(e[3][pl]) << 16);
+      u.z = (uint32_t)__bfloat16_as_ushort(e[4][pl]) | ((uint32_t)__bfloat16_as_ushort(e[5][pl]) << 16);
+      u.w = (uint32_t)__bfloat16_as_ushort(e[6][pl]) | ((uint32_t)__bfloat16_as_ushort(e[7][pl]) << 16);
+      *reinterpret_cast<uint4*>(planes + pl * plane_bytes + off) = u;
+    }
+  }
+}
+
+// one element of a weight tile (planes `wplane` bytes apart)
+template <class P>
+__device__ __forceinline__ void store_w(uint8_t* planes, uint32_t wplane, int K, int n, int k, float v) {
+  const uint32_t sbo = (uint32_t)(K * P::es / 16) * 128u;
+  const uint32_t off = tc::core_offset((uint32_t)n, (uint32_t)(k * P::es / 16), 128u, sbo) + (uint32_t)(k * P::es % 16);
+  __nv_bfloat16 e[P::planes];
+  split_bf16<P::planes>(v, e);
+#pragma unroll
+  for (int pl = 0; pl < P::planes; ++pl) *reinterpret_cast<__nv_bfloat16*>(planes + pl * wplane + off) = e[pl];
+}
+
+// D[128][N] (+)= A[128][K] * B[N][K]^T over the part products i + j < planes, one thread
+template <class P, int N, int K>
+__device__ __forceinline__ void issue_mma(uint32_t d, uint32_t a0, uint32_t b0, uint32_t wplane) {
+  constexpr uint32_t sbo = (uint32_t)(K * P::es / 16) * 128u;
+  constexpr uint32_t idesc = tc::instr_desc(P::kind, 128, N);
+  constexpr uint32_t aplane = 128u * 32u * P::es;
+  bool first = true;
+#pragma unroll
+  for (int s = 0; s < K / P::kmma; ++s) {
+    const uint32_t off = (uint32_t)s * 256u;  // two 16-byte core-matrix columns per K step
+    // smallest part products first
+#pragma unroll
+    for (int sum = P::planes - 1; sum >= 0; --sum)
+#pragma unroll
+      for (int i = 0; i <= sum; ++i) {
+        const int jj = sum - i;
+        tc::mma_bf16(d, tc::smem_desc(a0 + i * aplane + off, 128u, sbo),
+                     tc::smem_desc(b0 + jj * wplane + off, 128u, sbo), idesc, first ? 0u : 1u);
+        first = false;
+      }
+  }
+}
+
+// per-group MMA machinery
+struct Group {
+  uint8_t* a;  // A operand planes
+  uint64_t* mbar;
+  int* abort;
+  uint32_t tcol;   // tensor-memory address of this group's column 0
+  uint32_t phase;  // parity of the next completion
+  int g, gt;
+};
+
+// A rows written by every thread -> one thread issues the MMA and commits
+template <class P, int N, int K>
+__device__ __forceinline__ void mma_phase_issue(Group& G, uint32_t dcol, const uint8_t* w, uint32_t wplane) {
+  tc::fence_smem_async();
+  tc::fence_before_sync();
+  group_sync(G.g);
+  tc::fence_after_sync();
+  if (G.gt == 0) {
+    issue_mma<P, N, K>(G.tcol + dcol, tc::smem_u32(G.a), tc::smem_u32(w), wplane);
+    tc::mma_commit(G.mbar);
+  }
+}
+// every thread waits for the MMA (bounded); false if it never completed
+__device__ __forceinline__ bool mma_phase_wait(Group& G) {
+  const bool ok = tc::mbar_wait(G.mbar, G.phase, kMbarLimit);
+  if (!ok) atomicExch(G.abort, 1);
+  G.phase ^= 1u;
+  group_sync(G.g);
+  tc::fence_after_sync();
+  return *reinterpret_cast<volatile int*>(G.abort) == 0;
+}
+
+__device__ __forceinline__ uint32_t lane_addr(const Group& G, uint32_t col, int warp_g) {
+  return G.tcol + col + ((uint32_t)(32 * warp_g) << 16);
+}
+
+// ---- decoder weight gradients from the warp's 32 staged rows ---------------------------
+// rows: [A-part (rows i) | B-part (cols j)] at offsets ao / bo of each staged row
+template <int NI, int NJ>
+__device__ __forceinline__ void stage_tiles(const float* st, int ao, int bo, float* acc, int accoff, int ldw, int jmax,
+                                            int lane) {
+  constexpr int BJ = NJ / 4;  // column blocks
+  const int i0 = 4 * (lane / BJ), j0 = 4 * (lane % BJ);
+  if (i0 >= NI) return;
+  float t[4][4] = {};
+#pragma unroll 4
+  for (int s = 0; s < 32; ++s) {
+    const float4 av = *reinterpret_cast<const float4*>(st + s * kStRow + ao + i0);
+    const float4 bv = *reinterpret_cast<const float4*>(st + s * kStRow + bo + j0);
+    const float ar[4] = {av.x, av.y, av.z, av.w}, br[4] = {bv.x, bv.y, bv.z, bv.w};
+#pragma unroll
+    for (int x = 0; x < 4; ++x)
+#pragma unroll
+      for (int y = 0; y < 4; ++y) t[x][y] = fmaf(ar[x], br[y], t[x][y]);
+  }
+#pragma unroll
+  for (int x = 0; x < 4; ++x)
+#pragma unroll
+    for (int y = 0; y < 4; ++y)
+      if (j0 + y < jmax) atomicAdd(acc + accoff + (i0 + x) * ldw + j0 + y, t[x][y]);
+}
+// column sum of the staged A-part (a bias gradient): lane owns column `lane`
+__device__ __forceinline__ float stage_colsum(const float* st, int ao, int lane) {
+  float s = 0.f;
+#pragma unroll 8
+  for (int r = 0; r < 32; ++r) s += st[r * kStRow + ao + lane];
+  return s;
+}
+
+template <int K>
+__device__ __forceinline__ void stage_write(float* st, int lane, int off, const float* v) {
+#pragma unroll
+  for (int q = 0; q < K / 4; ++q)
+    *reinterpret_cast<float4*>(st + lane * kStRow + off + 4 * q) = make_float4(v[4 * q], v[4 * q + 1], v[4 * q + 2], v[4 * q + 3]);
+}
+
+// ---- gather / scatter -------------------------------------------------------------------
+__device__ __forceinline__ void gather_z(const GridDesc& g, const float* __restrict__ theta, const float x[3],
+                                         float z[kZ]) {
+#pragma unroll
+  for (int l = 0; l < kLevels; ++l) {
+    const Cell c = locate(g, l, x);
+    float w[8];
+    corner_weights(c.f, w);
+    const float4* base = reinterpret_cast<const float4*>(theta + g.off[l]);
+    float4 v[8];
+#pragma unroll
+    for (int k = 0; k < 8; ++k) v[k] = __ldg(base + c.vtx + corner_offset(g, l, k));
+    float4 s = make_float4(0.f, 0.f, 0.f, 0.f);
+#pragma unroll
+    for (int k = 0; k < 8; ++k) f4fma(s, w[k], v[k]);
+    z[4 * l] = s.x;
+    z[4 * l + 1] = s.y;
+    z[4 * l + 2] = s.z;
+    z[4 * l + 3] = s.w;
+  }
+}
+
+__device__ __forceinline__ void scatter_dz(const GridDesc& g, float* grad, float* lvl0g, const float x[3],
+                                           const float dz[kZ]) {
+#pragma unroll
+  for (int l = 0; l < kLevels; ++l) {
+    const Cell cc = locate(g, l, x);
+    float wc[8];
+    corner_weights(cc.f, wc);
+    const float4 g4 = make_float4(dz[4 * l], dz[4 * l + 1], dz[4 * l + 2], dz[4 * l + 3]);
+#pragma unroll
+    for (int k = 0; k < 8; ++k) {
+      const long long vtx = cc.vtx + corner_offset(g, l, k);
+      const float4 v = f4scale(g4, wc[k]);
+      if (l == 0 && lvl0g != nullptr) {
+        float* p = lvl0g + 4 * vtx;
+        atomicAdd(p, v.x);
+        atomicAdd(p + 1, v.y);
+        atomicAdd(p + 2, v.z);
+        atomicAdd(p + 3, v.w);
+      } else {
+        atomicAdd(reinterpret_cast<float4*>(grad + g.off[l]) + vtx, v);
+      }
+    }
+  }
+}
+
+template <int N>
+__device__ __forceinline__ float pick_tc(const float (&arr)[N], int j) {
+  float v = arr[0];
+#pragma unroll
+  for (int q = 1; q < N; ++q)
+    if (q == j) v = arr[q];
+  return v;
+}
+
+struct RenderTcArgs {
+  GridDesc g;
+  const float* theta;
+  int R, N;
+  const float *o, *r, *rgb, *D, *t;
+  const uint8_t* cls;
+  const int* counts;
+  const float* dloss;
+  float lam[5];
+  float kappa_fs;
+  float* grad;
+  float* loss_part;
+  float* mlp_part;
+  float *rgb_hat, *d_hat, *wsum;
+  int lvl0_staged;  // accumulate the coarsest level's gradient in shared memory
+  int* status;      // device status word (bit 1: an MMA never completed)
+};
+
+template <class P, int NCH, int GR, bool FWD, bool BWD>
+__global__ void __launch_bounds__(GR * kGroupThreads, 1) render_tc_kernel(RenderTcArgs a) {
+  using L = TcLayout<P>;
+  extern __shared__ __align__(1024) uint8_t smem[];
+  constexpr uint32_t wplane = wTotal<P>();  // one bf16 part of all weight tiles
+  uint8_t* wt0 = smem;
+  float* acc = reinterpret_cast<float*>(smem + wplane * P::planes);  // [kMlpPad] + loss [kLossPad]
+  float* lacc = acc + kMlpPad;
+  float* bias = lacc + kLossPad;  // b1[32] b2[16] b3[32] b4[4] kappa
+  uint32_t* tslot = reinterpret_cast<uint32_t*>(bias + 88);
+  const int n0 = a.g.dims[0][0] * a.g.dims[0][1] * a.g.dims[0][2];
+  float* lvl0g = reinterpret_cast<float*>(tslot + 4);
+  const int n0g = (BWD && a.lvl0_staged) ? n0 * 4 : 0;
+  uint8_t* gbase = reinterpret_cast<uint8_t*>(lvl0g + n0g);
+  gbase = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(gbase) + 1023) & ~uintptr_t(1023));
+
+  const int tid = threadIdx.x, gi = tid / kGroupThreads, gt = tid % kGroupThreads, warp_g = gt >> 5,
+            lane = tid & 31;
+  uint8_t* gmem = gbase + (size_t)gi * L::group_bytes;
+  Group G;
+  G.a = gmem;
+  float* stage = reinterpret_cast<float*>(gmem + L::a_bytes * P::planes) + warp_g * 32 * kStRow;
+  G.mbar = reinterpret_cast<uint64_t*>(gmem + L::a_bytes * P::planes + L::stage_bytes);
+  G.abort = reinterpret_cast<int*>(G.mbar + 1);
+  G.g = gi;
+  G.gt = gt;
+  G.phase = 0;
+
+  // ---- CTA set-up: weight tiles, biases, accumulators, barriers, tensor memory ----
+  const float* mlp = a.theta + a.g.n_grid;
+  for (int m = 0; m < 8; ++m) {
+    const int Nn = wN(m), K = wK(m);
+    for (int e = tid; e < Nn * K; e += blockDim.x) {
+      const int n = e / K, k = e % K;
+      float v = 0.f;
+      switch (m) {
+        case 0: v = mlp[oW1 + n * kZ + k]; break;
+        case 1: v = mlp[oW2 + n * kH1 + k]; break;
+        case 2: v = k < kHF ? mlp[oW3 + n * kHF + k] : 0.f; break;
+        case 3: v = n < kRGB ? mlp[oW4 + n * kH2 + k] : 0.f; break;
+        case 4: v = k < kRGB ? mlp[oW4 + k * kH2 + n] : 0.f; break;
+        case 5: v = n < kHF ? mlp[oW3 + k * kHF + n] : 0.f; break;
+        case 6: v = mlp[oW2 + k * kH1 + n]; break;
+        default: v = mlp[oW1 + k * kZ + n]; break;
+      }
+      store_w<P>(wt0 + wOff<P>(m), wplane, K, n, k, v);
+    }
+  }
+  for (int i = tid; i < 88; i += blockDim.x) {
+    float v = 0.f;
+    if (i < 32) v = mlp[ob1 + i];
+    else if (i < 48) v = mlp[ob2 + i - 32];
+    else if (i < 80) v = mlp[ob3 + i - 48];
+    else if (i < 83) v = mlp[ob4 + i - 80];
+    else if (i == 84) v = mlp[oKappa];
+    bias[i] = v;
+  }
+  for (int i = tid; i < kMlpPad + kLossPad; i += blockDim.x) acc[i] = 0.f;
+  for (int i = tid; i < n0g; i += blockDim.x) lvl0g[i] = 0.f;
+  if (gt == 0) {
+    tc::mbar_init(G.mbar, 1);
+    *G.abort = 0;
+  }
+  if (tid < 32) tc::tmem_alloc(tslot, (uint32_t)(GR * kGroupCols));
+  tc::fence_smem_async();
+  tc::fence_before_sync();
+  __syncthreads();
+  tc::fence_after_sync();
+  G.tcol = *tslot + (uint32_t)(gi * kGroupCols);
+  const float* b1 = bias;
+  const float* b2 = bias + 32;
+  const float* b3 = bias + 48;
+  const float* b4 = bias + 80;
+  const float s_sharp = expf(bias[84]);
+  float* lvl0p = n0g ? lvl0g : nullptr;
+
+  const int N = a.N;
+  float wt[5];
+#pragma unroll
+  for (int k = 0; k < 5; ++k) wt[k] = a.dloss[k] + a.lam[k] * a.dloss[5];
+  const int n_d = a.counts[0], n_tr = a.counts[1], n_fs = a.counts[2];
+  const float k_rgb = a.R > 0 ? wt[0] * 2.0f / (float)a.R : 0.f;
+  const float k_d = n_d > 0 ? wt[1] / (float)n_d : 0.0f;
+  const float k_sdf = n_tr > 0 ? wt[2] / (float)n_tr : 0.0f;
+  const float k_fs = n_fs > 0 ? wt[3] / (float)n_fs : 0.0f;
+  float l_rgb = 0.f, l_d = 0.f, l_sdf = 0.f, l_fs = 0.f, g_kappa = 0.f;
+  const int row = gt;  // tile row of this thread's sample
+  bool alive = true;
+
+  for (int quad = blockIdx.x * GR + gi; quad * 4 < a.R && alive; quad += gridDim.x * GR) {
+    const int ray = quad * 4 + warp_g;
+    const bool has_ray = ray < a.R;
+    const int rr = has_ray ? ray : 0;
+    const float o[3] = {a.o[3 * rr], a.o[3 * rr + 1], a.o[3 * rr + 2]};
+    const float r[3] = {a.r[3 * rr], a.r[3 * rr + 1], a.r[3 * rr + 2]};
+    const float D = has_ray ? a.D[rr] : 0.f;
+    float tt[NCH], ph[NCH], col[NCH][3];
+
+    // ================= forward: gather, then 4 decoder phases per chunk =================
+#pragma unroll 1
+    for (int j = 0; j < NCH && alive; ++j) {
+      const int si = 32 * j + lane;
+      const bool valid = has_ray && si < N;
+      const float t = valid ? a.t[(size_t)rr * N + si] : 0.f;
+      float z[kZ];
+      if (valid) {
+        float x[3];
+        sample_pos(o, r, t, x);
+        gather_z(a.g, a.theta, x, z);
+      } else {
+#pragma unroll
+        for (int k = 0; k < kZ; ++k) z[k] = 0.f;
+      }
+      store_row<P, 16>(G.a, row, z);
+      mma_phase_issue<P, 32, 16>(G, cD1, wt0 + wOff<P>(0), wplane);
+      if (!(alive = mma_phase_wait(G))) break;
+      float v[32];
+      tc::tmem_ld32(lane_addr(G, cD1, warp_g), v);
+      tc::tmem_ld_wait();
+#pragma unroll
+      for (int k = 0; k < 32; ++k) v[k] = fmaxf(v[k] + b1[k], 0.f);
+      store_row<P, 32>(G.a, row, v);
+      mma_phase_issue<P, 16, 32>(G, cD2, wt0 + wOff<P>(1), wplane);
+      if (!(alive = mma_phase_wait(G))) break;
+      float u[16];
+      tc::tmem_ld16(lane_addr(G, cD2, warp_g), u);
+      tc::tmem_ld_wait();
+      const float phi = u[0] + b2[0];
+      float h[16];
+#pragma unroll
+      for (int k = 0; k < 15; ++k) h[k] = u[k + 1] + b2[k + 1];
+      h[15] = 0.f;
+      store_row<P, 16>(G.a, row, h);
+      mma_phase_issue<P, 32, 16>(G, cD3, wt0 + wOff<P>(2), wplane);
+      if (!(alive = mma_phase_wait(G))) break;
+      tc::tmem_ld32(lane_addr(G, cD3, warp_g), v);
+      tc::tmem_ld_wait();
+#pragma unroll
+      for (int k = 0; k < 32; ++k) v[k] = fmaxf(v[k] + b3[k], 0.f);
+      store_row<P, 32>(G.a, row, v);
+      mma_phase_issue<P, 16, 32>(G, cX, wt0 + wOff<P>(3), wplane);
+      if (!(alive = mma_phase_wait(G))) break;
+      tc::tmem_ld16(lane_addr(G, cX, warp_g), u);
+      tc::tmem_ld_wait();
+      float c3[3];
+#pragma unroll
+      for (int k = 0; k < 3; ++k) c3[k] = sigmoidf_(u[k] + b4[k]);
+      // keep per-chunk values in registers (compile-time index via a selector loop)
+#pragma unroll
+      for (int q = 0; q < NCH; ++q)
+        if (q == j) {
+          tt[q] = t;
+          ph[q] = valid ? phi : 0.f;
+          col[q][0] = valid ? c3[0] : 0.f;
+          col[q][1] = valid ? c3[1] : 0.f;
+          col[q][2] = valid ? c3[2] : 0.f;
+        }
+    }
+    if (!alive) break;
+
+    // ================= NeuS opacity, transmittance, weights (Sec. 3.2) =================
+    float Ph[NCH], PhN[NCH], al[NCH], T[NCH], w[NCH];
+#pragma unroll
+    for (int j = 0; j < NCH; ++j) Ph[j] = (has_ray && 32 * j + lane < N) ? sigmoidf_(s_sharp * ph[j]) : 0.f;
+#pragma unroll
+    for (int j = 0; j < NCH; ++j) {
+      float nx = __shfl_down_sync(0xffffffffu, Ph[j], 1);
+      const float nx0 = (j + 1 < NCH) ? __shfl_sync(0xffffffffu, Ph[j + 1 < NCH ? j + 1 : j], 0) : 0.f;
+      if (lane == 31) nx = nx0;
+      PhN[j] = nx;
+      float q = 0.f;
+      if (has_ray && 32 * j + lane < N - 1) q = (Ph[j] - nx) / fmaxf(Ph[j], 1e-6f);
+      al[j] = q > 0.f ? q : 0.f;
+    }
+    float carry = 1.0f;
+#pragma unroll
+    for (int j = 0; j < NCH; ++j) {
+      float inc = 1.0f - al[j];
+#pragma unroll
+      for (int off = 1; off < 32; off <<= 1) {
+        const float y = __shfl_up_sync(0xffffffffu, inc, off);
+        if (lane >= off) inc *= y;
+      }
+      float exc = __shfl_up_sync(0xffffffffu, inc, 1);
+      if (lane == 0) exc = 1.0f;
+      T[j] = carry * exc;
+      carry *= __shfl_sync(0xffffffffu, inc, 31);
+      w[j] = T[j] * al[j];
+    }
+    float ch[3] = {0.f, 0.f, 0.f}, dh = 0.f, ws = 0.f;
+#pragma unroll
+    for (int j = 0; j < NCH; ++j) {
+#pragma unroll
+      for (int k = 0; k < 3; ++k) ch[k] = fmaf(w[j], col[j][k], ch[k]);
+      dh = fmaf(w[j], tt[j], dh);
+      ws += w[j];
+    }
+#pragma unroll
+    for (int k = 0; k < 3; ++k) ch[k] = warp_sum(ch[k]);
+    dh = warp_sum(dh);
+    ws = warp_sum(ws);
+    const float I[3] = {a.rgb[3 * rr], a.rgb[3 * rr + 1], a.rgb[3 * rr + 2]};
+    if (FWD && has_ray) {
+      if (lane == 0) {
+        float e2 = 0.f;
+#pragma unroll
+        for (int k = 0; k < 3; ++k) e2 = fmaf(I[k] - ch[k], I[k] - ch[k], e2);
+        l_rgb += e2;
+        if (D > 0.f) l_d += fabsf(D - dh);
+        if (a.rgb_hat) {
+          a.rgb_hat[3 * ray] = ch[0];
+          a.rgb_hat[3 * ray + 1] = ch[1];
+          a.rgb_hat[3 * ray + 2] = ch[2];
+        }
+        if (a.d_hat) a.d_hat[ray] = dh;
+        if (a.wsum) a.wsum[ray] = ws;
+      }
+#pragma unroll
+      for (int j = 0; j < NCH; ++j) {
+        const int si = 32 * j + lane;
+        if (si >= N) continue;
+        const int cl = a.cls[(size_t)ray * N + si];
+        const float b = __fsub_rn(D, tt[j]);
+        if (cl == CLS_TR) l_sdf += fabsf(ph[j] - b);
+        else if (cl == CLS_FS) l_fs += fmaxf(fmaxf(0.f, expf(-a.kappa_fs * ph[j]) - 1.0f), ph[j] - b);
+      }
+    }
+    if constexpr (!BWD) continue;
+
+    // ================= adjoint of compositing: dL/dalpha_k = T_k (e_k - U_k) =================
+    float gc[3];
+#pragma unroll
+    for (int k = 0; k < 3; ++k) gc[k] = has_ray ? k_rgb * (ch[k] - I[k]) : 0.f;
+    const float gd = (has_ray && D > 0.f) ? k_d * ((dh > D) ? 1.f : (dh < D ? -1.f : 0.f)) : 0.f;
+    float e[NCH], U[NCH];
+#pragma unroll
+    for (int j = 0; j < NCH; ++j) e[j] = gc[0] * col[j][0] + gc[1] * col[j][1] + gc[2] * col[j][2] + gd * tt[j];
+    float cA = 0.f;
+#pragma unroll
+    for (int j = NCH - 1; j >= 0; --j) {
+      float A = al[j] * e[j], B = 1.0f - al[j];
+#pragma unroll
+      for (int off = 1; off < 32; off <<= 1) {
+        const float A2 = __shfl_down_sync(0xffffffffu, A, off), B2 = __shfl_down_sync(0xffffffffu, B, off);
+        if (lane + off < 32) {
+          A = fmaf(B, A2, A);
+          B *= B2;
+        }
+      }
+      float eA = __shfl_down_sync(0xffffffffu, A, 1), eB = __shfl_down_sync(0xffffffffu, B, 1);
+      if (lane == 31) {
+        eA = 0.f;
+        eB = 1.f;
+      }
+      U[j] = fmaf(eB, cA, eA);
+      const float A0 = __shfl_sync(0xffffffffu, A, 0), B0 = __shfl_sync(0xffffffffu, B, 0);
+      cA = fmaf(B0, cA, A0);
+    }
+    float dnext_prev = 0.f;
+    float dphi[NCH];
+#pragma unroll
+    for (int j = 0; j < NCH; ++j) {
+      const int si = 32 * j + lane;
+      const bool valid = has_ray && si < N;
+      const float dal = T[j] * (e[j] - U[j]);
+      float dself = 0.f, dnext = 0.f;
+      if (valid && si < N - 1) {
+        const float den = fmaxf(Ph[j], 1e-6f);
+        if (Ph[j] - PhN[j] > 0.f) {
+          dnext = -dal / den;
+          dself = (Ph[j] > 1e-6f) ? dal * PhN[j] / (Ph[j] * Ph[j]) : dal * 1e6f;
+        }
+      }
+      float recv = __shfl_up_sync(0xffffffffu, dnext, 1);
+      const float last = __shfl_sync(0xffffffffu, dnext, 31);
+      if (lane == 0) recv = dnext_prev;
+      dnext_prev = last;
+      const float dPh = dself + recv;
+      const float dsig = Ph[j] * (1.0f - Ph[j]);
+      float d = dPh * s_sharp * dsig;
+      if (valid) {
+        g_kappa = fmaf(dPh * dsig * s_sharp, ph[j], g_kappa);
+        const int cl = a.cls[(size_t)ray * N + si];
+        const float b = __fsub_rn(D, tt[j]);
+        if (cl == CLS_TR) {
+          const float df = ph[j] - b;
+          d += k_sdf * (df > 0.f ? 1.f : (df < 0.f ? -1.f : 0.f));
+        } else if (cl == CLS_FS) {
+          const float ex = expf(-a.kappa_fs * ph[j]) - 1.0f, lin = ph[j] - b;
+          int arg = 0;
+          float top = 0.f;
+          if (ex > top) {
+            top = ex;
+            arg = 1;
+          }
+          if (lin > top) arg = 2;
+          d += k_fs * (arg == 1 ? -a.kappa_fs * (ex + 1.0f) : (arg == 2 ? 1.0f : 0.0f));
+        }
+      } else {
+        d = 0.f;
+      }
+      dphi[j] = d;
+    }
+
+    // ================= reverse, chunk by chunk: recompute, 4 adjoint phases =================
+#pragma unroll 1
+    for (int j = 0; j < NCH && alive; ++j) {
+      const int si = 32 * j + lane;
+      const bool valid = has_ray && si < N;
+      const float t = pick_tc(tt, j);
+      float x[3];
+      sample_pos(o, r, t, x);
+      float z[kZ];
+      if (valid) {
+        gather_z(a.g, a.theta, x, z);
+      } else {
+#pragma unroll
+        for (int k = 0; k < kZ; ++k) z[k] = 0.f;
+      }
+      // recompute the decoders (the same four phases as the forward)
+      store_row<P, 16>(G.a, row, z);
+      mma_phase_issue<P, 32, 16>(G, cD1, wt0 + wOff<P>(0), wplane);
+      if (!(alive = mma_phase_wait(G))) break;
+      float v[32];
+      uint32_t mask1 = 0, mask2 = 0;
+      tc::tmem_ld32(lane_addr(G, cD1, warp_g), v);
+      tc::tmem_ld_wait();
+#pragma unroll
+      for (int k = 0; k < 32; ++k) {
+        v[k] = fmaxf(v[k] + b1[k], 0.f);
+        mask1 |= (v[k] > 0.f ? 1u : 0u) << k;
+      }
+      store_row<P, 32>(G.a, row, v);
+      mma_phase_issue<P, 16, 32>(G, cD2, wt0 + wOff<P>(1), wplane);
+      if (!(alive = mma_phase_wait(G))) break;
+      float u[16];
+      tc::tmem_ld16(lane_addr(G, cD2, warp_g), u);
+      tc::tmem_ld_wait();
+      float h[16];
+#pragma unroll
+      for (int k = 0; k < 15; ++k) h[k] = u[k + 1] + b2[k + 1];
+      h[15] = 0.f;
+      store_row<P, 16>(G.a, row, h);
+      mma_phase_issue<P, 32, 16>(G, cD3, wt0 + wOff<P>(2), wplane);
+      if (!(alive = mma_phase_wait(G))) break;
+      tc::tmem_ld32(lane_addr(G, cD3, warp_g), v);
+      tc::tmem_ld_wait();
+#pragma unroll
+      for (int k = 0; k < 32; ++k) {
+        v[k] = fmaxf(v[k] + b3[k], 0.f);
+        mask2 |= (v[k] > 0.f ? 1u : 0u) << k;
+      }
+      store_row<P, 32>(G.a, row, v);
+      mma_phase_issue<P, 16, 32>(G, cX, wt0 + wOff<P>(3), wplane);
+      if (!(alive = mma_phase_wait(G))) break;
+      tc::tmem_ld16(lane_addr(G, cX, warp_g), u);
+      tc::tmem_ld_wait();
+      // colour output adjoint: dpre = w gc c (1 - c)
+      const float wj = pick_tc(w, j);
+      float dp[kKD];
+#pragma unroll
+      for (int k = 0; k < kKD; ++k) dp[k] = 0.f;
+#pragma unroll
+      for (int k = 0; k < 3; ++k) {
+        const float c = sigmoidf_(u[k] + b4[k]);
+        dp[k] = valid ? wj * gc[k] * c * (1.0f - c) : 0.f;
+      }
+      store_row<P, kKD>(G.a, row, dp);
+      // --- b4: da2 = dpre W4  (overlap: dW4, db4 from dpre and a2) ---
+      mma_phase_issue<P, 32, kKD>(G, cX, wt0 + wOff<P>(4), wplane);
+      {
+        float* st = stage;
+        stage_write<4>(st, lane, 0, dp);
+        stage_write<32>(st, lane, 4, v);  // a2
+        __syncwarp();
+        float w4[3] = {0.f, 0.f, 0.f}, db4 = 0.f;
+#pragma unroll 4
+        for (int s = 0; s < 32; ++s) {
+          const float* rw = st + s * kStRow;
+          const float a2v = rw[4 + lane];
+          w4[0] = fmaf(rw[0], a2v, w4[0]);
+          w4[1] = fmaf(rw[1], a2v, w4[1]);
+          w4[2] = fmaf(rw[2], a2v, w4[2]);
+          db4 += rw[lane & 3];
+        }
+#pragma unroll
+        for (int q = 0; q < 3; ++q) atomicAdd(acc + oW4 + q * kH2 + lane, w4[q]);
+        if (lane < 3) atomicAdd(acc + ob4 + lane, db4);
+        __syncwarp();
+      }
+      if (!(alive = mma_phase_wait(G))) break;
+      tc::tmem_ld32(lane_addr(G, cX, warp_g), v);
+      tc::tmem_ld_wait();
+#pragma unroll
+      for (int k = 0; k < 32; ++k) v[k] = ((mask2 >> k) & 1u) ? v[k] : 0.f;  // dy2
+      store_row<P, 32>(G.a, row, v);
+      // --- b3: dh = dy2 W3  (overlap: dW3, db3 from dy2 and h) ---
+      mma_phase_issue<P, 16, 32>(G, cY, wt0 + wOff<P>(5), wplane);
+      {
+        float* st = stage;
+        stage_write<32>(st, lane, 0, v);
+        stage_write<16>(st, lane, 32, h);
+        __syncwarp();
+        stage_tiles<32, 16>(st, 0, 32, acc, oW3, kHF, kHF, lane);
+        const float db3 = stage_colsum(st, 0, lane);
+        atomicAdd(acc + ob3 + lane, db3);
+        __syncwarp();
+      }
+      if (!(alive = mma_phase_wait(G))) break;
+      tc::tmem_ld16(lane_addr(G, cY, warp_g), u);
+      tc::tmem_ld_wait();
+      float dout[16];
+      dout[0] = valid ? pick_tc(dphi, j) : 0.f;
+#pragma unroll
+      for (int k = 1; k < 16; ++k) dout[k] = u[k - 1];
+      store_row<P, 16>(G.a, row, dout);
+      // --- b2: da1 = dout W2  (overlap: dW2, db2 from dout and a1) ---
+      mma_phase_issue<P, 32, 16>(G, cX, wt0 + wOff<P>(6), wplane);
+      {
+        float a1[32];
+        tc::tmem_ld32(lane_addr(G, cD1, warp_g), a1);
+        tc::tmem_ld_wait();
+#pragma unroll
+        for (int k = 0; k < 32; ++k) a1[k] = fmaxf(a1[k] + b1[k], 0.f);
+        float* st = stage;
+        stage_write<16>(st, lane, 0, dout);
+        stage_write<32>(st, lane, 16, a1);
+        __syncwarp();
+        stage_tiles<16, 32>(st, 0, 16, acc, oW2, kH1, kH1, lane);
+        const float db2 = stage_colsum(st, 0, lane & 15);
+        if (lane < 16) atomicAdd(acc + ob2 + lane, db2);
+        __syncwarp();
+      }
+      if (!(alive = mma_phase_wait(G))) break;
+      tc::tmem_ld32(lane_addr(G, cX, warp_g), v);
+      tc::tmem_ld_wait();
+#pragma unroll
+      for (int k = 0; k < 32; ++k) v[k] = ((mask1 >> k) & 1u) ? v[k] : 0.f;  // dy1
+      store_row<P, 32>(G.a, row, v);
+      // --- b1: dz = dy1 W1  (overlap: dW1, db1 from dy1 and z) ---
+      mma_phase_issue<P, 16, 32>(G, cY, wt0 + wOff<P>(7), wplane);
+      {
+        float* st = stage;
+        stage_write<32>(st, lane, 0, v);
+        stage_write<16>(st, lane, 32, z);
+        __syncwarp();
+        stage_tiles<32, 16>(st, 0, 32, acc, oW1, kZ, kZ, lane);
+        const float db1 = stage_colsum(st, 0, lane);
+        atomicAdd(acc + ob1 + lane, db1);
+        __syncwarp();
+      }
+      if (!(alive = mma_phase_wait(G))) break;
+      tc::tmem_ld16(lane_addr(G, cY, warp_g), u);
+      tc::tmem_ld_wait();
+      if (valid) scatter_dz(a.g, a.grad, lvl0p, x, u);
+    }
+  }
+
+  // ---- epilogue: loss and decoder-gradient partials, coarsest level, tensor memory ----
+  if (FWD) {
+    l_rgb = warp_sum(l_rgb);
+    l_d = warp_sum(l_d);
+    l_sdf = warp_sum(l_sdf);
+    l_fs = warp_sum(l_fs);
+    if (lane == 0) {
+      atomicAdd(lacc + 0, l_rgb);
+      atomicAdd(lacc + 1, l_d);
+      atomicAdd(lacc + 2, l_sdf);
+      atomicAdd(lacc + 3, l_fs);
+    }
+  }
+  if (BWD) {
+    g_kappa = warp_sum(g_kappa);
+    if (lane == 0) atomicAdd(acc + oKappa, g_kappa);
+  }
+  if (!alive && gt == 0) {
+    atomicOr(a.status, 2);
+    tc::mbar_wait(G.mbar, G.phase ^ 1u, kMbarLimit);  // let an MMA in flight finish
+  }
+  tc::fence_before_sync();
+  __syncthreads();
+  if (tid < kLossPad) a.loss_part[(size_t)blockIdx.x * kLossPad + tid] = lacc[tid];
+  for (int i = tid; i < kMlpPad; i += blockDim.x) a.mlp_part[(size_t)blockIdx.x * kMlpPad + i] = acc[i];
+  for (int i = tid; i < n0g; i += blockDim.x) {
+    const float v = lvl0g[i];
+    if (v != 0.0f) atomicAdd(a.grad + a.g.off[0] + i, v);
+  }
+  if (tid < 32) {
+    tc::fence_after_sync();
+    tc::tmem_dealloc(*tslot, (uint32_t)(GR * kGroupCols));
+  }
+}
+
+template <class P, int GR>
+size_t render_tc_smem(const GridDesc& g, bool staged, bool bwd) {
+  using L = TcLayout<P>;
+  const int n0 = g.dims[0][0] * g.dims[0][1] * g.dims[0][2];
+  size_t b = wTotal<P>() * P::planes + (kMlpPad + kLossPad + 88 + 4) * 4 + ((staged && bwd) ? (size_t)n0 * 16 : 0);
+  b = (b + 1023) & ~size_t(1023);
+  return b + (size_t)GR * L::group_bytes + 1024;  // + alignment slack of the dynamic window
+}
+
+template <class P, int NCH, int GR, bool FWD, bool BWD>
+gs_status launch_tc_t(const gs_ctx* ctx, RenderTcArgs& a, cudaStream_t st) {
+  const size_t smem = render_tc_smem<P, GR>(ctx->grid, a.lvl0_staged, BWD);
+  auto k = render_tc_kernel<P, NCH, GR, FWD, BWD>;
+  if (cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess)
+    return GS_ERR_CUDA;
+  k<<<ctx->render_ctas, GR * kGroupThreads, smem, st>>>(a);
+  return cudaPeekAtLastError() == cudaSuccess ? GS_OK : GS_ERR_CUDA;
+}
+
+template <int NCH>
+gs_status launch_tc_n(const gs_ctx* ctx, RenderTcArgs& a, int mode, cudaStream_t st) {
+  constexpr int GR = 1;
+  if (mode == 1) return launch_tc_t<PrecBF16x3, NCH, GR, true, false>(ctx, a, st);
+  if (mode == 2) return launch_tc_t<PrecBF16x3, NCH, GR, false, true>(ctx, a, st);
+  return launch_tc_t<PrecBF16x3, NCH, GR, true, true>(ctx, a, st);
+}
+
+}  // namespace gs
