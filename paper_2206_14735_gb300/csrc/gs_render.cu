@@ -12,13 +12,25 @@ extern template gs_status launch_tc_n<4>(const gs_ctx*, RenderTcArgs&, int, cuda
 // ------------------------------------------------------------------------------------
 // combine per-CTA partials: losses in FP64, decoder gradients in a fixed order
 // ------------------------------------------------------------------------------------
-__global__ void finalize_kernel(const float* loss_part, const float* mlp_part, int nparts, const int* counts, int R,
-                                float l0, float l1, float l2, float l3, float l4, float* loss, float* gmlp) {
-  const int i = blockIdx.x * blockDim.x + threadIdx.x;
-  if (gmlp && i < GS_MLP_PARAMS) {
+__global__ void __launch_bounds__(256) finalize_kernel(const float* loss_part, const float* mlp_part, int nparts,
+                                                       const int* counts, int R, float l0, float l1, float l2,
+                                                       float l3, float l4, float* loss, float* gmlp) {
+  // decoder gradients: block b owns entries [32b, 32b + 32); warp w sums rows w, w + 8, ...
+  __shared__ float part[8][33];
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  const int i = blockIdx.x * 32 + lane;
+  if (gmlp) {
     float s = 0.f;
-    for (int p = 0; p < nparts; ++p) s += mlp_part[(size_t)p * kMlpPad + i];
-    gmlp[i] += s;
+    if (i < GS_MLP_PARAMS)
+      for (int p = wid; p < nparts; p += 8) s += mlp_part[(size_t)p * kMlpPad + i];
+    part[wid][lane] = s;
+    __syncthreads();
+    if (wid == 0 && i < GS_MLP_PARAMS) {
+      float t = 0.f;
+#pragma unroll
+      for (int k = 0; k < 8; ++k) t += part[k][lane];
+      gmlp[i] += t;
+    }
   }
   if (loss && blockIdx.x == 0 && threadIdx.x < 32) {
     const int k = threadIdx.x;
@@ -167,7 +179,7 @@ gs_status gs_launch_finalize(const gs_ctx* ctx, const gs_batch* b, float* loss, 
   const float* l = ctx->cfg.lam;
   float* gmlp = (mode & 2) ? grad + ctx->grid.n_grid : nullptr;
   float* lo = (mode & 1) ? loss : nullptr;
-  finalize_kernel<<<(GS_MLP_PARAMS + 255) / 256, 256, 0, st>>>(ctx->loss_part, ctx->mlp_part, ctx->n_parts,
+  finalize_kernel<<<(GS_MLP_PARAMS + 31) / 32, 256, 0, st>>>(ctx->loss_part, ctx->mlp_part, ctx->n_parts,
                                                                 b->counts, b->R, l[0], l[1], l[2], l[3], l[4], lo,
                                                                 gmlp);
   return cudaPeekAtLastError() == cudaSuccess ? GS_OK : GS_ERR_CUDA;

@@ -72,7 +72,7 @@ constexpr uint32_t kMbarLimit = 1u << 26;  // bounded MMA-completion wait
 template <class P>
 struct TcLayout {
   static constexpr uint32_t a_bytes = 128u * 32u * P::es;  // one A operand plane, K <= 32
-  static constexpr uint32_t stage_bytes = 4u * 32u * kStRow * 4u;
+  static constexpr uint32_t stage_bytes = 4u * 16u * kStRow * 4u;  // 16 staged rows per warp
   static constexpr uint32_t group_bytes = a_bytes * P::planes + stage_bytes + 128;  // + mbarrier, flag
 };
 
@@ -92,25 +92,31 @@ __device__ __forceinline__ void split_bf16(float x, __nv_bfloat16 (&p)[PL]) {
   }
 }
 
-// write K values as row `row` of a K-major no-swizzle tile, one plane per bf16 part
+// write K values as row `row` of a K-major no-swizzle tile, one plane per bf16 part; pairs
+// of values are rounded together (one cvt.rn.bf16x2 per pair and part)
 template <class P, int K>
 __device__ __forceinline__ void store_row(uint8_t* planes, int row, const float* v) {
   constexpr uint32_t sbo = (uint32_t)(K * P::es / 16) * 128u;
   constexpr uint32_t plane_bytes = 128u * 32u * P::es;
 #pragma unroll
   for (int c = 0; c < K / 8; ++c) {
-    __nv_bfloat16 e[8][P::planes];
+    float r[8];
 #pragma unroll
-    for (int q = 0; q < 8; ++q) split_bf16<P::planes>(v[8 * c + q], e[q]);
+    for (int q = 0; q < 8; ++q) r[q] = v[8 * c + q];
     const uint32_t off = tc::core_offset((uint32_t)row, (uint32_t)c, 128u, sbo);
 #pragma unroll
     for (int pl = 0; pl < P::planes; ++pl) {
-      uint4 u;
-      u.x = (uint32_t)__bfloat16_as_ushort(e[0][pl]) | ((uint32_t)__bfloat16_as_ushort(e[1][pl]) << 16);
-      u.y = (uint32_t)__bfloat16_as_ushort(e[2][pl]) | ((uint32_t)__bfloat16_as_ushort(e[3][pl]) << 16);
-      u.z = (uint32_t)__bfloat16_as_ushort(e[4][pl]) | ((uint32_t)__bfloat16_as_ushort(e[5][pl]) << 16);
-      u.w = (uint32_t)__bfloat16_as_ushort(e[6][pl]) | ((uint32_t)__bfloat16_as_ushort(e[7][pl]) << 16);
-      *reinterpret_cast<uint4*>(planes + pl * plane_bytes + off) = u;
+      uint32_t w[4];
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        const __nv_bfloat162 b = __floats2bfloat162_rn(r[2 * q], r[2 * q + 1]);
+        w[q] = *reinterpret_cast<const uint32_t*>(&b);
+        if (pl + 1 < P::planes) {
+          r[2 * q] -= __uint_as_float(w[q] << 16);
+          r[2 * q + 1] -= __uint_as_float(w[q] & 0xFFFF0000u);
+        }
+      }
+      *reinterpret_cast<uint4*>(planes + pl * plane_bytes + off) = make_uint4(w[0], w[1], w[2], w[3]);
     }
   }
 }
@@ -185,17 +191,16 @@ __device__ __forceinline__ uint32_t lane_addr(const Group& G, uint32_t col, int 
   return G.tcol + col + ((uint32_t)(32 * warp_g) << 16);
 }
 
-// ---- decoder weight gradients from the warp's 32 staged rows ---------------------------
-// rows: [A-part (rows i) | B-part (cols j)] at offsets ao / bo of each staged row
+// ---- decoder weight gradients from the warp's staged rows ---------------------------
+// The warp's 32 samples are staged 16 at a time; rows: [A-part (rows i) | B-part (cols j)]
+// at offsets ao / bo.  t accumulates the lane's 4x4 tile over both halves.
 template <int NI, int NJ>
-__device__ __forceinline__ void stage_tiles(const float* st, int ao, int bo, float* acc, int accoff, int ldw, int jmax,
-                                            int lane) {
+__device__ __forceinline__ void stage_tiles(const float* st, int ao, int bo, float (&t)[4][4], int lane) {
   constexpr int BJ = NJ / 4;  // column blocks
   const int i0 = 4 * (lane / BJ), j0 = 4 * (lane % BJ);
   if (i0 >= NI) return;
-  float t[4][4] = {};
 #pragma unroll 4
-  for (int s = 0; s < 32; ++s) {
+  for (int s = 0; s < 16; ++s) {
     const float4 av = *reinterpret_cast<const float4*>(st + s * kStRow + ao + i0);
     const float4 bv = *reinterpret_cast<const float4*>(st + s * kStRow + bo + j0);
     const float ar[4] = {av.x, av.y, av.z, av.w}, br[4] = {bv.x, bv.y, bv.z, bv.w};
@@ -204,25 +209,56 @@ __device__ __forceinline__ void stage_tiles(const float* st, int ao, int bo, flo
 #pragma unroll
       for (int y = 0; y < 4; ++y) t[x][y] = fmaf(ar[x], br[y], t[x][y]);
   }
+}
+template <int NI, int NJ>
+__device__ __forceinline__ void flush_tiles(const float (&t)[4][4], float* acc, int accoff, int ldw, int jmax,
+                                            int lane) {
+  constexpr int BJ = NJ / 4;
+  const int i0 = 4 * (lane / BJ), j0 = 4 * (lane % BJ);
+  if (i0 >= NI) return;
 #pragma unroll
   for (int x = 0; x < 4; ++x)
 #pragma unroll
     for (int y = 0; y < 4; ++y)
       if (j0 + y < jmax) atomicAdd(acc + accoff + (i0 + x) * ldw + j0 + y, t[x][y]);
 }
-// column sum of the staged A-part (a bias gradient): lane owns column `lane`
-__device__ __forceinline__ float stage_colsum(const float* st, int ao, int lane) {
+// column sum of the staged A-part (a bias gradient): lane owns column `col`
+__device__ __forceinline__ float stage_colsum(const float* st, int ao, int col) {
   float s = 0.f;
 #pragma unroll 8
-  for (int r = 0; r < 32; ++r) s += st[r * kStRow + ao + lane];
+  for (int r = 0; r < 16; ++r) s += st[r * kStRow + ao + col];
   return s;
 }
 
-template <int K>
-__device__ __forceinline__ void stage_write(float* st, int lane, int off, const float* v) {
+// lanes [16h, 16h+16) write their rows (KA values at 0, KB values at KA)
+template <int KA, int KB>
+__device__ __forceinline__ void stage_pair(float* st, int lane, int half, const float* va, const float* vb) {
+  if ((lane >> 4) != half) return;
+  float* rw = st + (lane & 15) * kStRow;
 #pragma unroll
-  for (int q = 0; q < K / 4; ++q)
-    *reinterpret_cast<float4*>(st + lane * kStRow + off + 4 * q) = make_float4(v[4 * q], v[4 * q + 1], v[4 * q + 2], v[4 * q + 3]);
+  for (int q = 0; q < KA / 4; ++q)
+    *reinterpret_cast<float4*>(rw + 4 * q) = make_float4(va[4 * q], va[4 * q + 1], va[4 * q + 2], va[4 * q + 3]);
+#pragma unroll
+  for (int q = 0; q < KB / 4; ++q)
+    *reinterpret_cast<float4*>(rw + KA + 4 * q) = make_float4(vb[4 * q], vb[4 * q + 1], vb[4 * q + 2], vb[4 * q + 3]);
+}
+
+// dW (+)= sum over the warp's 32 samples of a (x) b, plus the column sums of a (bias)
+template <int KA, int KB, int NI, int NJ>
+__device__ __forceinline__ void warp_weight_grad(float* st, int lane, const float* va, const float* vb, float* acc,
+                                                 int woff, int ldw, int jmax, int boff, int bcols) {
+  float t[4][4] = {};
+  float bsum = 0.f;
+#pragma unroll 1
+  for (int half = 0; half < 2; ++half) {
+    stage_pair<KA, KB>(st, lane, half, va, vb);
+    __syncwarp();
+    stage_tiles<NI, NJ>(st, 0, KA, t, lane);
+    bsum += stage_colsum(st, 0, lane % bcols);
+    __syncwarp();
+  }
+  flush_tiles<NI, NJ>(t, acc, woff, ldw, jmax, lane);
+  if (lane < bcols) atomicAdd(acc + boff + lane, bsum);
 }
 
 // ---- gather / scatter -------------------------------------------------------------------
@@ -320,7 +356,7 @@ __global__ void __launch_bounds__(GR * kGroupThreads, 1) render_tc_kernel(Render
   uint8_t* gmem = gbase + (size_t)gi * L::group_bytes;
   Group G;
   G.a = gmem;
-  float* stage = reinterpret_cast<float*>(gmem + L::a_bytes * P::planes) + warp_g * 32 * kStRow;
+  float* stage = reinterpret_cast<float*>(gmem + L::a_bytes * P::planes) + warp_g * 16 * kStRow;
   G.mbar = reinterpret_cast<uint64_t*>(gmem + L::a_bytes * P::planes + L::stage_bytes);
   G.abort = reinterpret_cast<int*>(G.mbar + 1);
   G.g = gi;
@@ -669,25 +705,26 @@ __global__ void __launch_bounds__(GR * kGroupThreads, 1) render_tc_kernel(Render
       store_row<P, kKD>(G.a, row, dp);
       // --- b4: da2 = dpre W4  (overlap: dW4, db4 from dpre and a2) ---
       mma_phase_issue<P, 32, kKD>(G, cX, wt0 + wOff<P>(4), wplane);
-      {
-        float* st = stage;
-        stage_write<4>(st, lane, 0, dp);
-        stage_write<32>(st, lane, 4, v);  // a2
-        __syncwarp();
+      {  // dW4[3][32] (+)= dpre (x) a2 (column `lane`), db4
         float w4[3] = {0.f, 0.f, 0.f}, db4 = 0.f;
+#pragma unroll 1
+        for (int half = 0; half < 2; ++half) {
+          stage_pair<4, 32>(stage, lane, half, dp, v);
+          __syncwarp();
 #pragma unroll 4
-        for (int s = 0; s < 32; ++s) {
-          const float* rw = st + s * kStRow;
-          const float a2v = rw[4 + lane];
-          w4[0] = fmaf(rw[0], a2v, w4[0]);
-          w4[1] = fmaf(rw[1], a2v, w4[1]);
-          w4[2] = fmaf(rw[2], a2v, w4[2]);
-          db4 += rw[lane & 3];
+          for (int s2 = 0; s2 < 16; ++s2) {
+            const float* rw = stage + s2 * kStRow;
+            const float a2v = rw[4 + lane];
+            w4[0] = fmaf(rw[0], a2v, w4[0]);
+            w4[1] = fmaf(rw[1], a2v, w4[1]);
+            w4[2] = fmaf(rw[2], a2v, w4[2]);
+            db4 += rw[lane & 3];
+          }
+          __syncwarp();
         }
 #pragma unroll
         for (int q = 0; q < 3; ++q) atomicAdd(acc + oW4 + q * kH2 + lane, w4[q]);
         if (lane < 3) atomicAdd(acc + ob4 + lane, db4);
-        __syncwarp();
       }
       if (!(alive = mma_phase_wait(G))) break;
       tc::tmem_ld32(lane_addr(G, cX, warp_g), v);
@@ -697,16 +734,7 @@ __global__ void __launch_bounds__(GR * kGroupThreads, 1) render_tc_kernel(Render
       store_row<P, 32>(G.a, row, v);
       // --- b3: dh = dy2 W3  (overlap: dW3, db3 from dy2 and h) ---
       mma_phase_issue<P, 16, 32>(G, cY, wt0 + wOff<P>(5), wplane);
-      {
-        float* st = stage;
-        stage_write<32>(st, lane, 0, v);
-        stage_write<16>(st, lane, 32, h);
-        __syncwarp();
-        stage_tiles<32, 16>(st, 0, 32, acc, oW3, kHF, kHF, lane);
-        const float db3 = stage_colsum(st, 0, lane);
-        atomicAdd(acc + ob3 + lane, db3);
-        __syncwarp();
-      }
+      warp_weight_grad<32, 16, 32, 16>(stage, lane, v, h, acc, oW3, kHF, kHF, ob3, 32);  // dW3, db3
       if (!(alive = mma_phase_wait(G))) break;
       tc::tmem_ld16(lane_addr(G, cY, warp_g), u);
       tc::tmem_ld_wait();
@@ -723,14 +751,7 @@ __global__ void __launch_bounds__(GR * kGroupThreads, 1) render_tc_kernel(Render
         tc::tmem_ld_wait();
 #pragma unroll
         for (int k = 0; k < 32; ++k) a1[k] = fmaxf(a1[k] + b1[k], 0.f);
-        float* st = stage;
-        stage_write<16>(st, lane, 0, dout);
-        stage_write<32>(st, lane, 16, a1);
-        __syncwarp();
-        stage_tiles<16, 32>(st, 0, 16, acc, oW2, kH1, kH1, lane);
-        const float db2 = stage_colsum(st, 0, lane & 15);
-        if (lane < 16) atomicAdd(acc + ob2 + lane, db2);
-        __syncwarp();
+        warp_weight_grad<16, 32, 16, 32>(stage, lane, dout, a1, acc, oW2, kH1, kH1, ob2, 16);  // dW2, db2
       }
       if (!(alive = mma_phase_wait(G))) break;
       tc::tmem_ld32(lane_addr(G, cX, warp_g), v);
@@ -740,16 +761,7 @@ __global__ void __launch_bounds__(GR * kGroupThreads, 1) render_tc_kernel(Render
       store_row<P, 32>(G.a, row, v);
       // --- b1: dz = dy1 W1  (overlap: dW1, db1 from dy1 and z) ---
       mma_phase_issue<P, 16, 32>(G, cY, wt0 + wOff<P>(7), wplane);
-      {
-        float* st = stage;
-        stage_write<32>(st, lane, 0, v);
-        stage_write<16>(st, lane, 32, z);
-        __syncwarp();
-        stage_tiles<32, 16>(st, 0, 32, acc, oW1, kZ, kZ, lane);
-        const float db1 = stage_colsum(st, 0, lane);
-        atomicAdd(acc + ob1 + lane, db1);
-        __syncwarp();
-      }
+      warp_weight_grad<32, 16, 32, 16>(stage, lane, v, z, acc, oW1, kZ, kZ, ob1, 32);  // dW1, db1
       if (!(alive = mma_phase_wait(G))) break;
       tc::tmem_ld16(lane_addr(G, cY, warp_g), u);
       tc::tmem_ld_wait();
@@ -813,7 +825,7 @@ gs_status launch_tc_t(const gs_ctx* ctx, RenderTcArgs& a, cudaStream_t st) {
 
 template <int NCH>
 gs_status launch_tc_n(const gs_ctx* ctx, RenderTcArgs& a, int mode, cudaStream_t st) {
-  constexpr int GR = 1;
+  constexpr int GR = kRenderGroups;  // 4 groups x 128 tensor-memory columns: one CTA per SM
   if (mode == 1) return launch_tc_t<PrecBF16x3, NCH, GR, true, false>(ctx, a, st);
   if (mode == 2) return launch_tc_t<PrecBF16x3, NCH, GR, false, true>(ctx, a, st);
   return launch_tc_t<PrecBF16x3, NCH, GR, true, true>(ctx, a, st);
