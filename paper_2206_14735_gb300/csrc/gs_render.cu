@@ -162,8 +162,6 @@ gs_status gs_launch_render(const gs_ctx* ctx, const float* theta, const gs_batch
   a.d_hat = d_hat;
   a.wsum = wsum;
   a.status = ctx->status;
-  const int n0 = ctx->grid.dims[0][0] * ctx->grid.dims[0][1] * ctx->grid.dims[0][2];
-  a.lvl0_staged = n0 <= kLvl0MaxVerts;
   const int nch = (b->N + 31) / 32;
   switch (nch) {
     case 1: return launch_tc_n<1>(ctx, a, mode, st);

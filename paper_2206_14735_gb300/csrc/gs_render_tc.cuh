@@ -67,7 +67,7 @@ constexpr uint32_t cD1 = 0, cD2 = 32, cD3 = 48, cX = 80, cY = 112, kGroupCols = 
 
 constexpr int kGroupThreads = 128;
 constexpr int kStRow = 52;  // staged row: 48 floats + 4 pad (row stride = 20 mod 32 banks)
-constexpr uint32_t kMbarLimit = 1u << 26;  // bounded MMA-completion wait
+constexpr uint32_t kMbarLimit = 1u << 20;  // bounded MMA-completion wait (tries of up to 2 us: ~2 s)
 
 template <class P>
 struct TcLayout {
@@ -177,10 +177,10 @@ __device__ __forceinline__ void mma_phase_issue(Group& G, uint32_t dcol, const u
     tc::mma_commit(G.mbar);
   }
 }
-// every thread waits for the MMA (bounded); false if it never completed
+// the issuing thread waits for the MMA (bounded) while the other threads of the group park on
+// the hardware barrier; false (for every thread) if it never completed
 __device__ __forceinline__ bool mma_phase_wait(Group& G) {
-  const bool ok = tc::mbar_wait(G.mbar, G.phase, kMbarLimit);
-  if (!ok) atomicExch(G.abort, 1);
+  if (G.gt == 0 && !tc::mbar_wait(G.mbar, G.phase, kMbarLimit)) *reinterpret_cast<volatile int*>(G.abort) = 1;
   G.phase ^= 1u;
   group_sync(G.g);
   tc::fence_after_sync();
@@ -216,11 +216,14 @@ __device__ __forceinline__ void flush_tiles(const float (&t)[4][4], float* acc, 
   constexpr int BJ = NJ / 4;
   const int i0 = 4 * (lane / BJ), j0 = 4 * (lane % BJ);
   if (i0 >= NI) return;
+  const int rot = (threadIdx.x >> 5) & 3;  // the group's warps flush in rotated order
 #pragma unroll
-  for (int x = 0; x < 4; ++x)
+  for (int q = 0; q < 4; ++q) {
+    const int x = (q + rot) & 3;
 #pragma unroll
     for (int y = 0; y < 4; ++y)
       if (j0 + y < jmax) atomicAdd(acc + accoff + (i0 + x) * ldw + j0 + y, t[x][y]);
+  }
 }
 // column sum of the staged A-part (a bias gradient): lane owns column `col`
 __device__ __forceinline__ float stage_colsum(const float* st, int ao, int col) {
@@ -283,27 +286,54 @@ __device__ __forceinline__ void gather_z(const GridDesc& g, const float* __restr
   }
 }
 
-__device__ __forceinline__ void scatter_dz(const GridDesc& g, float* grad, float* lvl0g, const float x[3],
-                                           const float dz[kZ]) {
+// Adjoint of the gather: dtheta_l[corner] += w_c dz_l.  A warp's lanes hold consecutive
+// samples of one ray, so the cells they fall in are visited monotonically and equal cells
+// form contiguous runs of lanes.  At the two coarse levels (where runs are long) the 8
+// weighted corner vectors are first summed over each run with a segmented shuffle scan and
+// only the run's first lane issues the 16-byte atomics; at the fine levels every lane
+// issues its own.
+__device__ __forceinline__ void scatter_dz(const GridDesc& g, float* grad, const float x[3], const float dz[kZ],
+                                           bool valid) {
+  const unsigned active = __ballot_sync(0xffffffffu, valid);
+  if (active == 0) return;
+  const int lane = threadIdx.x & 31;
 #pragma unroll
   for (int l = 0; l < kLevels; ++l) {
     const Cell cc = locate(g, l, x);
     float wc[8];
     corner_weights(cc.f, wc);
-    const float4 g4 = make_float4(dz[4 * l], dz[4 * l + 1], dz[4 * l + 2], dz[4 * l + 3]);
+    const float4 g4 = valid ? make_float4(dz[4 * l], dz[4 * l + 1], dz[4 * l + 2], dz[4 * l + 3])
+                            : make_float4(0.f, 0.f, 0.f, 0.f);
+    float4* gl = reinterpret_cast<float4*>(grad + g.off[l]);
+    if (l < 2) {
+      const long long key = valid ? cc.vtx : -1 - (long long)lane;  // invalid lanes: singleton runs
+      float4 v[8];
 #pragma unroll
-    for (int k = 0; k < 8; ++k) {
-      const long long vtx = cc.vtx + corner_offset(g, l, k);
-      const float4 v = f4scale(g4, wc[k]);
-      if (l == 0 && lvl0g != nullptr) {
-        float* p = lvl0g + 4 * vtx;
-        atomicAdd(p, v.x);
-        atomicAdd(p + 1, v.y);
-        atomicAdd(p + 2, v.z);
-        atomicAdd(p + 3, v.w);
-      } else {
-        atomicAdd(reinterpret_cast<float4*>(grad + g.off[l]) + vtx, v);
+      for (int k = 0; k < 8; ++k) v[k] = f4scale(g4, wc[k]);
+#pragma unroll
+      for (int o = 1; o < 32; o <<= 1) {
+        const long long kk = __shfl_down_sync(0xffffffffu, key, o);
+        const bool take = (lane + o < 32) && kk == key;
+#pragma unroll
+        for (int k = 0; k < 8; ++k) {
+          const float tx = __shfl_down_sync(0xffffffffu, v[k].x, o), ty = __shfl_down_sync(0xffffffffu, v[k].y, o);
+          const float tz = __shfl_down_sync(0xffffffffu, v[k].z, o), tw = __shfl_down_sync(0xffffffffu, v[k].w, o);
+          if (take) {
+            v[k].x += tx;
+            v[k].y += ty;
+            v[k].z += tz;
+            v[k].w += tw;
+          }
+        }
       }
+      const long long prev = __shfl_up_sync(0xffffffffu, key, 1);
+      if (valid && (lane == 0 || prev != key)) {
+#pragma unroll
+        for (int k = 0; k < 8; ++k) atomicAdd(gl + cc.vtx + corner_offset(g, l, k), v[k]);
+      }
+    } else if (valid) {
+#pragma unroll
+      for (int k = 0; k < 8; ++k) atomicAdd(gl + cc.vtx + corner_offset(g, l, k), f4scale(g4, wc[k]));
     }
   }
 }
@@ -331,7 +361,6 @@ struct RenderTcArgs {
   float* loss_part;
   float* mlp_part;
   float *rgb_hat, *d_hat, *wsum;
-  int lvl0_staged;  // accumulate the coarsest level's gradient in shared memory
   int* status;      // device status word (bit 1: an MMA never completed)
 };
 
@@ -345,10 +374,8 @@ __global__ void __launch_bounds__(GR * kGroupThreads, 1) render_tc_kernel(Render
   float* lacc = acc + kMlpPad;
   float* bias = lacc + kLossPad;  // b1[32] b2[16] b3[32] b4[4] kappa
   uint32_t* tslot = reinterpret_cast<uint32_t*>(bias + 88);
-  const int n0 = a.g.dims[0][0] * a.g.dims[0][1] * a.g.dims[0][2];
-  float* lvl0g = reinterpret_cast<float*>(tslot + 4);
-  const int n0g = (BWD && a.lvl0_staged) ? n0 * 4 : 0;
-  uint8_t* gbase = reinterpret_cast<uint8_t*>(lvl0g + n0g);
+  float* gacc = reinterpret_cast<float*>(tslot + 4);  // per-group decoder-gradient accumulators [GR][kMlpPad]
+  uint8_t* gbase = reinterpret_cast<uint8_t*>(gacc + GR * kMlpPad);
   gbase = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(gbase) + 1023) & ~uintptr_t(1023));
 
   const int tid = threadIdx.x, gi = tid / kGroupThreads, gt = tid % kGroupThreads, warp_g = gt >> 5,
@@ -393,7 +420,7 @@ __global__ void __launch_bounds__(GR * kGroupThreads, 1) render_tc_kernel(Render
     bias[i] = v;
   }
   for (int i = tid; i < kMlpPad + kLossPad; i += blockDim.x) acc[i] = 0.f;
-  for (int i = tid; i < n0g; i += blockDim.x) lvl0g[i] = 0.f;
+  for (int i = tid; i < GR * kMlpPad; i += blockDim.x) gacc[i] = 0.f;
   if (gt == 0) {
     tc::mbar_init(G.mbar, 1);
     *G.abort = 0;
@@ -409,7 +436,7 @@ __global__ void __launch_bounds__(GR * kGroupThreads, 1) render_tc_kernel(Render
   const float* b3 = bias + 48;
   const float* b4 = bias + 80;
   const float s_sharp = expf(bias[84]);
-  float* lvl0p = n0g ? lvl0g : nullptr;
+  float* macc = gacc + gi * kMlpPad;  // this group's decoder-gradient accumulator
 
   const int N = a.N;
   float wt[5];
@@ -723,8 +750,8 @@ __global__ void __launch_bounds__(GR * kGroupThreads, 1) render_tc_kernel(Render
           __syncwarp();
         }
 #pragma unroll
-        for (int q = 0; q < 3; ++q) atomicAdd(acc + oW4 + q * kH2 + lane, w4[q]);
-        if (lane < 3) atomicAdd(acc + ob4 + lane, db4);
+        for (int q = 0; q < 3; ++q) atomicAdd(macc + oW4 + q * kH2 + lane, w4[q]);
+        if (lane < 3) atomicAdd(macc + ob4 + lane, db4);
       }
       if (!(alive = mma_phase_wait(G))) break;
       tc::tmem_ld32(lane_addr(G, cX, warp_g), v);
@@ -734,7 +761,7 @@ __global__ void __launch_bounds__(GR * kGroupThreads, 1) render_tc_kernel(Render
       store_row<P, 32>(G.a, row, v);
       // --- b3: dh = dy2 W3  (overlap: dW3, db3 from dy2 and h) ---
       mma_phase_issue<P, 16, 32>(G, cY, wt0 + wOff<P>(5), wplane);
-      warp_weight_grad<32, 16, 32, 16>(stage, lane, v, h, acc, oW3, kHF, kHF, ob3, 32);  // dW3, db3
+      warp_weight_grad<32, 16, 32, 16>(stage, lane, v, h, macc, oW3, kHF, kHF, ob3, 32);  // dW3, db3
       if (!(alive = mma_phase_wait(G))) break;
       tc::tmem_ld16(lane_addr(G, cY, warp_g), u);
       tc::tmem_ld_wait();
@@ -751,7 +778,7 @@ __global__ void __launch_bounds__(GR * kGroupThreads, 1) render_tc_kernel(Render
         tc::tmem_ld_wait();
 #pragma unroll
         for (int k = 0; k < 32; ++k) a1[k] = fmaxf(a1[k] + b1[k], 0.f);
-        warp_weight_grad<16, 32, 16, 32>(stage, lane, dout, a1, acc, oW2, kH1, kH1, ob2, 16);  // dW2, db2
+        warp_weight_grad<16, 32, 16, 32>(stage, lane, dout, a1, macc, oW2, kH1, kH1, ob2, 16);  // dW2, db2
       }
       if (!(alive = mma_phase_wait(G))) break;
       tc::tmem_ld32(lane_addr(G, cX, warp_g), v);
@@ -761,11 +788,11 @@ __global__ void __launch_bounds__(GR * kGroupThreads, 1) render_tc_kernel(Render
       store_row<P, 32>(G.a, row, v);
       // --- b1: dz = dy1 W1  (overlap: dW1, db1 from dy1 and z) ---
       mma_phase_issue<P, 16, 32>(G, cY, wt0 + wOff<P>(7), wplane);
-      warp_weight_grad<32, 16, 32, 16>(stage, lane, v, z, acc, oW1, kZ, kZ, ob1, 32);  // dW1, db1
+      warp_weight_grad<32, 16, 32, 16>(stage, lane, v, z, macc, oW1, kZ, kZ, ob1, 32);  // dW1, db1
       if (!(alive = mma_phase_wait(G))) break;
       tc::tmem_ld16(lane_addr(G, cY, warp_g), u);
       tc::tmem_ld_wait();
-      if (valid) scatter_dz(a.g, a.grad, lvl0p, x, u);
+      scatter_dz(a.g, a.grad, x, u, valid);
     }
   }
 
@@ -793,10 +820,11 @@ __global__ void __launch_bounds__(GR * kGroupThreads, 1) render_tc_kernel(Render
   tc::fence_before_sync();
   __syncthreads();
   if (tid < kLossPad) a.loss_part[(size_t)blockIdx.x * kLossPad + tid] = lacc[tid];
-  for (int i = tid; i < kMlpPad; i += blockDim.x) a.mlp_part[(size_t)blockIdx.x * kMlpPad + i] = acc[i];
-  for (int i = tid; i < n0g; i += blockDim.x) {
-    const float v = lvl0g[i];
-    if (v != 0.0f) atomicAdd(a.grad + a.g.off[0] + i, v);
+  for (int i = tid; i < kMlpPad; i += blockDim.x) {
+    float v = acc[i];
+#pragma unroll
+    for (int q = 0; q < GR; ++q) v += gacc[q * kMlpPad + i];
+    a.mlp_part[(size_t)blockIdx.x * kMlpPad + i] = v;
   }
   if (tid < 32) {
     tc::fence_after_sync();
@@ -805,17 +833,16 @@ __global__ void __launch_bounds__(GR * kGroupThreads, 1) render_tc_kernel(Render
 }
 
 template <class P, int GR>
-size_t render_tc_smem(const GridDesc& g, bool staged, bool bwd) {
+size_t render_tc_smem() {
   using L = TcLayout<P>;
-  const int n0 = g.dims[0][0] * g.dims[0][1] * g.dims[0][2];
-  size_t b = wTotal<P>() * P::planes + (kMlpPad + kLossPad + 88 + 4) * 4 + ((staged && bwd) ? (size_t)n0 * 16 : 0);
+  size_t b = wTotal<P>() * P::planes + (kMlpPad + kLossPad + 88 + 4 + GR * kMlpPad) * 4;
   b = (b + 1023) & ~size_t(1023);
   return b + (size_t)GR * L::group_bytes + 1024;  // + alignment slack of the dynamic window
 }
 
 template <class P, int NCH, int GR, bool FWD, bool BWD>
 gs_status launch_tc_t(const gs_ctx* ctx, RenderTcArgs& a, cudaStream_t st) {
-  const size_t smem = render_tc_smem<P, GR>(ctx->grid, a.lvl0_staged, BWD);
+  const size_t smem = render_tc_smem<P, GR>();
   auto k = render_tc_kernel<P, NCH, GR, FWD, BWD>;
   if (cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess)
     return GS_ERR_CUDA;

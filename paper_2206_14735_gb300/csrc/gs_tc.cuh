@@ -88,19 +88,21 @@ __device__ __forceinline__ void fence_smem_async() { asm volatile("fence.proxy.a
 __device__ __forceinline__ void mbar_init(uint64_t* mbar, uint32_t count) {
   asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(mbar)), "r"(count) : "memory");
 }
-__device__ __forceinline__ bool mbar_try_wait(uint64_t* mbar, uint32_t parity) {
+// try_wait with a suspend-time hint: the thread sleeps until the phase completes or the
+// hint (ns) elapses, instead of spinning on issue slots
+__device__ __forceinline__ bool mbar_try_wait(uint64_t* mbar, uint32_t parity, uint32_t hint_ns) {
   uint32_t ok;
   asm volatile(
-      "{\n.reg .pred p;\nmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\nselp.u32 %0, 1, 0, p;\n}\n"
+      "{\n.reg .pred p;\nmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2, %3;\nselp.u32 %0, 1, 0, p;\n}\n"
       : "=r"(ok)
-      : "r"(smem_u32(mbar)), "r"(parity)
+      : "r"(smem_u32(mbar)), "r"(parity), "r"(hint_ns)
       : "memory");
   return ok != 0;
 }
-// bounded wait: false after `limit` polls (the caller records an error and leaves)
+// bounded wait: false after `limit` tries of up to 2 us each (the caller records an error and leaves)
 __device__ __forceinline__ bool mbar_wait(uint64_t* mbar, uint32_t parity, uint32_t limit) {
   for (uint32_t i = 0; i < limit; ++i)
-    if (mbar_try_wait(mbar, parity)) return true;
+    if (mbar_try_wait(mbar, parity, 2000u)) return true;
   return false;
 }
 
