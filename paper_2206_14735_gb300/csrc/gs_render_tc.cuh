@@ -64,6 +64,12 @@ __host__ __device__ constexpr uint32_t wTotal() { return wOff<P>(8); }
 
 // tensor-memory columns of one group
 constexpr uint32_t cD1 = 0, cD2 = 32, cD3 = 48, cX = 80, cY = 112, kGroupCols = 128;
+// tcgen05.alloc takes a power of two >= 32 columns
+__host__ __device__ constexpr uint32_t tmem_cols(int groups) {
+  uint32_t c = 32;
+  while (c < (uint32_t)groups * kGroupCols) c <<= 1;
+  return c;
+}
 
 constexpr int kGroupThreads = 128;
 constexpr int kStRow = 52;  // staged row: 48 floats + 4 pad (row stride = 20 mod 32 banks)
@@ -425,7 +431,8 @@ __global__ void __launch_bounds__(GR * kGroupThreads, 1) render_tc_kernel(Render
     tc::mbar_init(G.mbar, 1);
     *G.abort = 0;
   }
-  if (tid < 32) tc::tmem_alloc(tslot, (uint32_t)(GR * kGroupCols));
+  static_assert(tmem_cols(GR) <= 512, "tensor memory holds 512 columns");
+  if (tid < 32) tc::tmem_alloc(tslot, tmem_cols(GR));
   tc::fence_smem_async();
   tc::fence_before_sync();
   __syncthreads();
@@ -828,7 +835,7 @@ __global__ void __launch_bounds__(GR * kGroupThreads, 1) render_tc_kernel(Render
   }
   if (tid < 32) {
     tc::fence_after_sync();
-    tc::tmem_dealloc(*tslot, (uint32_t)(GR * kGroupCols));
+    tc::tmem_dealloc(*tslot, tmem_cols(GR));
   }
 }
 
