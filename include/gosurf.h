@@ -162,9 +162,9 @@ gs_status gs_voxel_index(gs_ctx* ctx, const float* x, int32_t P, int64_t* out, v
  * device allocation (a plugin or custom operator that must draw from the framework's pool),
  * or a latency-critical loop that cannot take cudaMalloc's implicit device synchronisation.
  * It takes the configuration instead of a context and allocates nothing: the kernels'
- * per-CTA partial rows live in a file-scope device array of 1.73 MB (rows for 256 CTAs),
+ * per-CTA partial rows live in a file-scope device array of 3.04 MB (rows for 448 CTAs),
  * which every GPU that loads the library holds until the process exits.  Devices with more
- * than 192 SMs are rejected with GS_ERR_UNSUPPORTED.  The first call on a device resolves the
+ * than 320 SMs are rejected with GS_ERR_UNSUPPORTED.  The first call on a device resolves the
  * array's device address and writes its default dloss (a synchronous set-up), so make that
  * first call before any stream capture.  All calls share the array: calls whose work
  * overlaps on the GPU (other streams, other host threads) race and give wrong results.

@@ -9,7 +9,7 @@
 
 constexpr int kMlpPad = 1688;     // per-CTA decoder-gradient partial row (>= GS_MLP_PARAMS, 16-B multiple)
 constexpr int kLossPad = 8;       // per-CTA loss partial row
-constexpr int kSmoothCtas = 64;   // CTAs of the smoothness kernel (fixed, so partial rows are known)
+constexpr int kSmoothCtas = 128;  // CTAs of the smoothness kernel (fixed, so partial rows are known)
 constexpr int kRenderCtasPerSm = 1;  // persistent render CTAs per SM
 constexpr int kRenderGroups = 3;     // tile groups (4 warps, 128 tensor-memory columns each) per render CTA
 

@@ -13,8 +13,8 @@
 
 namespace {
 
-// partial rows for up to 448 CTAs: the render kernel uses kRenderCtasPerSm (2) CTAs per SM
-// and the smoothness kernel kSmoothCtas (64), so devices with up to 192 SMs fit
+// partial rows for up to 448 CTAs: the render kernel uses kRenderCtasPerSm (1) CTA per SM
+// and the smoothness kernel kSmoothCtas (128), so devices with up to 320 SMs fit
 constexpr int kNoAllocRows = 448;
 constexpr size_t kNoAllocFloats = (size_t)kNoAllocRows * (kLossPad + kMlpPad) + 16;  // + default dloss, status
 
@@ -77,7 +77,7 @@ extern "C" gs_status gs_forward_backward_noalloc(const gs_config* cfg, const flo
     return noalloc_fail(GS_ERR_CUDA, "gs_forward_backward_noalloc: no usable CUDA device");
   if (kRenderCtasPerSm * sms + kSmoothCtas > kNoAllocRows)
     return noalloc_fail(GS_ERR_UNSUPPORTED,
-                        "gs_forward_backward_noalloc: the static scratch holds partial rows for at most 192 SMs");
+                        "gs_forward_backward_noalloc: the static scratch holds partial rows for at most 320 SMs");
   float* scratch = nullptr;
   if (setup_device(dev, &scratch) != GS_OK)
     return noalloc_fail(GS_ERR_CUDA, "gs_forward_backward_noalloc: could not resolve the static scratch array");

@@ -64,6 +64,44 @@ __device__ __forceinline__ void features_with_jacobian(const GridDesc& g, const 
   }
 }
 
+// z at y (all levels), values only
+__device__ __forceinline__ void features_only(const GridDesc& g, const float* __restrict__ theta, const float y[3],
+                                              float z[kZ]) {
+#pragma unroll
+  for (int l = 0; l < kLevels; ++l) {
+    const Cell c = locate(g, l, y);
+    float w[8];
+    corner_weights(c.f, w);
+    const float4* base = reinterpret_cast<const float4*>(theta + g.off[l]);
+    float4 acc = make_float4(0.f, 0.f, 0.f, 0.f);
+#pragma unroll
+    for (int k = 0; k < 8; ++k) f4fma(acc, w[k], __ldg(base + c.vtx + corner_offset(g, l, k)));
+    z[4 * l] = acc.x;
+    z[4 * l + 1] = acc.y;
+    z[4 * l + 2] = acc.z;
+    z[4 * l + 3] = acc.w;
+  }
+}
+// d z_l / d x (4 features x 3 axes) at level l, and the cell (for the scatter)
+__device__ __forceinline__ Cell level_jacobian(const GridDesc& g, const float* __restrict__ theta, int l,
+                                               const float y[3], float4 (&dl)[3], float (&dw)[8][3]) {
+  const Cell c = locate(g, l, y);
+  corner_weight_grads(c.f, c.clamped, dw);
+  const float4* base = reinterpret_cast<const float4*>(theta + g.off[l]);
+  dl[0] = dl[1] = dl[2] = make_float4(0.f, 0.f, 0.f, 0.f);
+#pragma unroll
+  for (int k = 0; k < 8; ++k) {
+    const float4 v = __ldg(base + c.vtx + corner_offset(g, l, k));
+    f4fma(dl[0], dw[k][0], v);
+    f4fma(dl[1], dw[k][1], v);
+    f4fma(dl[2], dw[k][2], v);
+  }
+  const float iv = g.inv_voxel[l];
+#pragma unroll
+  for (int a = 0; a < 3; ++a) dl[a] = f4scale(dl[a], iv);
+  return c;
+}
+
 // ReLU mask m (bit j = unit j on), m (.) W2[0,:], and p = d phi / d z
 __device__ __forceinline__ unsigned phi_sensitivity(const float* sm, const float z[kZ], float mw2[kH1], float p[kZ]) {
   unsigned mask = 0;
@@ -86,7 +124,7 @@ __device__ __forceinline__ unsigned phi_sensitivity(const float* sm, const float
 }
 
 template <bool FWD, bool BWD>
-__global__ void __launch_bounds__(kSmoothWarps * 32) smooth_kernel(SmoothRunArgs a) {
+__global__ void __launch_bounds__(kSmoothWarps * 32, 1) smooth_kernel(SmoothRunArgs a) {
   __shared__ __align__(16) float sm[kSmemMlp];
   __shared__ __align__(16) float acc[kMlpPad + kLossPad];
   __shared__ __align__(16) float stage[kSmoothWarps][32 * kSt];
@@ -106,101 +144,102 @@ __global__ void __launch_bounds__(kSmoothWarps * 32) smooth_kernel(SmoothRunArgs
   const float k_sm = n_g > 0 ? (a.dloss[4] + a.lam4 * a.dloss[5]) * 2.0f / (float)n_g : 0.0f;
   float l_sm = 0.f;
 
-  for (int base = (blockIdx.x * kSmoothWarps + warp) * 32; base < a.P; base += gridDim.x * kSmoothWarps * 32) {
-    const int p = base + lane;
+  // one lane per gradient evaluation: lanes 2q and 2q+1 evaluate point q at x and x + eps
+  for (int base = (blockIdx.x * kSmoothWarps + warp) * 16; base < a.P; base += gridDim.x * kSmoothWarps * 16) {
+    const int p = base + (lane >> 1), e = lane & 1;
     const bool valid = p < a.P && a.valid[p];
-    float y[2][3], g[2][3];
+    float y[3];
 #pragma unroll
-    for (int k = 0; k < 3; ++k) {
-      y[0][k] = valid ? a.xs[3 * p + k] : 0.f;
-      y[1][k] = valid ? __fadd_rn(a.xs[3 * p + k], a.eps[3 * p + k]) : 0.f;
+    for (int k = 0; k < 3; ++k) y[k] = valid ? (e == 0 ? a.xs[3 * p + k] : __fadd_rn(a.xs[3 * p + k], a.eps[3 * p + k])) : 0.f;
+    float pz[kZ], mw2[kH1];
+    unsigned mask;
+    {
+      float z[kZ];
+      features_only(a.g, a.theta, y, z);
+      mask = phi_sensitivity(sm, z, mw2, pz);
     }
+    float gq[3] = {0.f, 0.f, 0.f};  // grad_x phi = sum_l (dz_l/dx)^T p_l
 #pragma unroll
-    for (int e = 0; e < 2; ++e) {
-      float z[kZ], dzdx[kZ][3], mw2[kH1], pz[kZ];
-      features_with_jacobian(a.g, a.theta, y[e], z, dzdx);
-      phi_sensitivity(sm, z, mw2, pz);
+    for (int l = 0; l < kLevels; ++l) {
+      float4 dl[3];
+      float dw[8][3];
+      level_jacobian(a.g, a.theta, l, y, dl, dw);
 #pragma unroll
-      for (int q = 0; q < 3; ++q) {
-        float s = 0.f;
-#pragma unroll
-        for (int k = 0; k < kZ; ++k) s = fmaf(pz[k], dzdx[k][q], s);
-        g[e][q] = s;
-      }
+      for (int q = 0; q < 3; ++q)
+        gq[q] += pz[4 * l] * dl[q].x + pz[4 * l + 1] * dl[q].y + pz[4 * l + 2] * dl[q].z + pz[4 * l + 3] * dl[q].w;
     }
-    const float dg[3] = {g[0][0] - g[1][0], g[0][1] - g[1][1], g[0][2] - g[1][2]};
-    if (FWD && valid) l_sm += dg[0] * dg[0] + dg[1] * dg[1] + dg[2] * dg[2];
+    float dg[3];  // g(x) - g(x + eps), on both lanes of the pair
+#pragma unroll
+    for (int q = 0; q < 3; ++q) {
+      const float other = __shfl_xor_sync(0xffffffffu, gq[q], 1);
+      dg[q] = e == 0 ? gq[q] - other : other - gq[q];
+    }
+    if (FWD && valid && e == 0) l_sm += dg[0] * dg[0] + dg[1] * dg[1] + dg[2] * dg[2];
     if constexpr (!BWD) continue;
-#pragma unroll 1
-    for (int e = 0; e < 2; ++e) {
-      const float sgn = e == 0 ? 1.f : -1.f;
-      const float av[3] = {valid ? sgn * k_sm * dg[0] : 0.f, valid ? sgn * k_sm * dg[1] : 0.f,
-                           valid ? sgn * k_sm * dg[2] : 0.f};
-      float z[kZ], dzdx[kZ][3], mw2[kH1], pz[kZ];
-      const float ye[3] = {e == 0 ? y[0][0] : y[1][0], e == 0 ? y[0][1] : y[1][1], e == 0 ? y[0][2] : y[1][2]};
-      features_with_jacobian(a.g, a.theta, ye, z, dzdx);
-      const unsigned mask = phi_sensitivity(sm, z, mw2, pz);
-      float jv[kZ];
+    const float sgn = e == 0 ? 1.f : -1.f;
+    const float av[3] = {valid ? sgn * k_sm * dg[0] : 0.f, valid ? sgn * k_sm * dg[1] : 0.f,
+                         valid ? sgn * k_sm * dg[2] : 0.f};
+    // per level: j_l = a . dz_l/dx, and the direct term d/d theta_{l,c,k} = p_{l,k} (1/v_l) (a . dw_c/df)
+    float jv[kZ];
 #pragma unroll
-      for (int k = 0; k < kZ; ++k) jv[k] = av[0] * dzdx[k][0] + av[1] * dzdx[k][1] + av[2] * dzdx[k][2];
-      float* row = st + lane * kSt;
-#pragma unroll
-      for (int q = 0; q < 8; ++q)
-        *reinterpret_cast<float4*>(row + sMw2 + 4 * q) = make_float4(mw2[4 * q], mw2[4 * q + 1], mw2[4 * q + 2], mw2[4 * q + 3]);
-#pragma unroll
-      for (int q = 0; q < 4; ++q)
-        *reinterpret_cast<float4*>(row + sJ + 4 * q) = make_float4(jv[4 * q], jv[4 * q + 1], jv[4 * q + 2], jv[4 * q + 3]);
-      // d/d W2[0][j] = m_j (W1 j)_j
-#pragma unroll
-      for (int j = 0; j < kH1; ++j) {
-        float u = 0.f;
-        if ((mask >> j) & 1u) {
-#pragma unroll
-          for (int k = 0; k < kZ; ++k) u = fmaf(sm[sW1 + j * 16 + k], jv[k], u);
-        }
-        row[sU + j] = u;
-      }
-      // direct term: d/d theta_{l,c,k} = p_{l,k} (1/v_l) (a . dw_c/df)
+    for (int l = 0; l < kLevels; ++l) {
+      float4 dl[3];
+      float dw[8][3];
+      const Cell c = level_jacobian(a.g, a.theta, l, y, dl, dw);
+      jv[4 * l] = av[0] * dl[0].x + av[1] * dl[1].x + av[2] * dl[2].x;
+      jv[4 * l + 1] = av[0] * dl[0].y + av[1] * dl[1].y + av[2] * dl[2].y;
+      jv[4 * l + 2] = av[0] * dl[0].z + av[1] * dl[1].z + av[2] * dl[2].z;
+      jv[4 * l + 3] = av[0] * dl[0].w + av[1] * dl[1].w + av[2] * dl[2].w;
       if (valid) {
+        const float iv = a.g.inv_voxel[l];
+        const float4 p4 = make_float4(pz[4 * l], pz[4 * l + 1], pz[4 * l + 2], pz[4 * l + 3]);
 #pragma unroll
-        for (int l = 0; l < kLevels; ++l) {
-          const Cell c = locate(a.g, l, ye);
-          float dw[8][3];
-          corner_weight_grads(c.f, c.clamped, dw);
-          const float iv = a.g.inv_voxel[l];
-          const float4 p4 = make_float4(pz[4 * l], pz[4 * l + 1], pz[4 * l + 2], pz[4 * l + 3]);
-#pragma unroll
-          for (int k = 0; k < 8; ++k) {
-            const float ad = (av[0] * dw[k][0] + av[1] * dw[k][1] + av[2] * dw[k][2]) * iv;
-            atomicAdd(reinterpret_cast<float4*>(a.grad + a.g.off[l]) + c.vtx + corner_offset(a.g, l, k),
-                      f4scale(p4, ad));
-          }
+        for (int k = 0; k < 8; ++k) {
+          const float ad = (av[0] * dw[k][0] + av[1] * dw[k][1] + av[2] * dw[k][2]) * iv;
+          atomicAdd(reinterpret_cast<float4*>(a.grad + a.g.off[l]) + c.vtx + corner_offset(a.g, l, k), f4scale(p4, ad));
         }
       }
-      __syncwarp();
-      {  // dW1[32][16] += mw2 (x) j over the warp's 32 points
-        const int i0 = 4 * (lane >> 2), j0 = 4 * (lane & 3);
-        float t[4][4] = {};
+    }
+    float* row = st + lane * kSt;
+#pragma unroll
+    for (int q = 0; q < 8; ++q)
+      *reinterpret_cast<float4*>(row + sMw2 + 4 * q) = make_float4(mw2[4 * q], mw2[4 * q + 1], mw2[4 * q + 2], mw2[4 * q + 3]);
+#pragma unroll
+    for (int q = 0; q < 4; ++q)
+      *reinterpret_cast<float4*>(row + sJ + 4 * q) = make_float4(jv[4 * q], jv[4 * q + 1], jv[4 * q + 2], jv[4 * q + 3]);
+    // d/d W2[0][j] = m_j (W1 j)_j
+#pragma unroll
+    for (int j = 0; j < kH1; ++j) {
+      float u = 0.f;
+      if ((mask >> j) & 1u) {
+#pragma unroll
+        for (int k = 0; k < kZ; ++k) u = fmaf(sm[sW1 + j * 16 + k], jv[k], u);
+      }
+      row[sU + j] = u;
+    }
+    __syncwarp();
+    {  // dW1[32][16] += mw2 (x) j over the warp's 32 evaluations
+      const int i0 = 4 * (lane >> 2), j0 = 4 * (lane & 3);
+      float t[4][4] = {};
 #pragma unroll 4
-        for (int s = 0; s < 32; ++s) {
-          const float4 av4 = ldv(st + s * kSt + sMw2 + i0), bv4 = ldv(st + s * kSt + sJ + j0);
-          const float ar[4] = {av4.x, av4.y, av4.z, av4.w}, br[4] = {bv4.x, bv4.y, bv4.z, bv4.w};
-#pragma unroll
-          for (int x = 0; x < 4; ++x)
-#pragma unroll
-            for (int q = 0; q < 4; ++q) t[x][q] = fmaf(ar[x], br[q], t[x][q]);
-        }
+      for (int s2 = 0; s2 < 32; ++s2) {
+        const float4 av4 = ldv(st + s2 * kSt + sMw2 + i0), bv4 = ldv(st + s2 * kSt + sJ + j0);
+        const float ar[4] = {av4.x, av4.y, av4.z, av4.w}, br[4] = {bv4.x, bv4.y, bv4.z, bv4.w};
 #pragma unroll
         for (int x = 0; x < 4; ++x)
 #pragma unroll
-          for (int q = 0; q < 4; ++q) atomicAdd(acc + oW1 + (i0 + x) * kZ + j0 + q, t[x][q]);
-        float u = 0.f;  // dW2[0][lane] += sum_s u_s[lane]
-#pragma unroll 4
-        for (int s = 0; s < 32; ++s) u += st[s * kSt + sU + lane];
-        atomicAdd(acc + oW2 + lane, u);
+          for (int q = 0; q < 4; ++q) t[x][q] = fmaf(ar[x], br[q], t[x][q]);
       }
-      __syncwarp();
+#pragma unroll
+      for (int x = 0; x < 4; ++x)
+#pragma unroll
+        for (int q = 0; q < 4; ++q) atomicAdd(acc + oW1 + (i0 + x) * kZ + j0 + q, t[x][q]);
+      float u = 0.f;  // dW2[0][lane] += sum_s u_s[lane]
+#pragma unroll 4
+      for (int s2 = 0; s2 < 32; ++s2) u += st[s2 * kSt + sU + lane];
+      atomicAdd(acc + oW2 + lane, u);
     }
+    __syncwarp();
   }
   if (FWD) {
     l_sm = warp_sum(l_sm);
