@@ -99,6 +99,9 @@ def run_ours(args):
     dfr = gs.DeviceFrames(fr.rgb, fr.depth, fr.c2w, fr.fx, fr.fy, fr.cx, fr.cy)
     theta = torch.from_numpy(sg.init_params(w)).cuda()
     grad, m, v = torch.zeros_like(theta), torch.zeros_like(theta), torch.zeros_like(theta)
+    n_grid_ = w.layout()[1]
+    # BF16 form: the grid copy the gathers read, refreshed by every Adam step
+    mirror = theta[:n_grid_].to(torch.bfloat16).view(torch.int16).contiguous() if ctx.bf16 else None
     batch = gs.Batch.allocate(w.rays, w.n_samples, w.n_smooth)
     loss = torch.empty(6, device="cuda")
     stream = torch.cuda.current_stream()
@@ -111,10 +114,10 @@ def run_ours(args):
         ctx.sample_rays(dfr, seed, k, batch)
         if ev is not None:
             ev[1].record(stream)
-        ctx.forward_backward(theta, batch, None, loss, grad)
+        ctx.forward_backward(theta, batch, None, loss, grad, theta_bf16=mirror)
         if ev is not None:
             ev[2].record(stream)
-        ctx.adam_step(theta, grad, m, v, k + 1, w.lr_grid, w.lr_mlp, b1, b2, w.adam_eps)
+        ctx.adam_step(theta, grad, m, v, k + 1, w.lr_grid, w.lr_mlp, b1, b2, w.adam_eps, theta_bf16=mirror)
         if ev is not None:
             ev[3].record(stream)
 
@@ -160,8 +163,8 @@ def run_ours(args):
     for k in range(e2e_steps):
         dl_dev.copy_(dl_host, non_blocking=True)
         ctx.sample_rays(dfr, seed, base + k, batch)
-        ctx.forward_backward(theta, batch, dl_dev, loss, grad)
-        ctx.adam_step(theta, grad, m, v, base + k + 1, w.lr_grid, w.lr_mlp, b1, b2, w.adam_eps)
+        ctx.forward_backward(theta, batch, dl_dev, loss, grad, theta_bf16=mirror)
+        ctx.adam_step(theta, grad, m, v, base + k + 1, w.lr_grid, w.lr_mlp, b1, b2, w.adam_eps, theta_bf16=mirror)
         out_host.copy_(loss, non_blocking=True)
         cnt_host.copy_(batch.counts, non_blocking=True)
         torch.cuda.current_stream().synchronize()
@@ -179,9 +182,10 @@ def run_ours(args):
     peaks, kind = _peaks()
     S = w.rays * w.n_samples
     n_grid = w.layout()[1]
-    # algorithmic bytes: gather 4 levels x 8 corners x 16 B and as many scattered per sample
-    render_bytes = S * (512 + 512)
-    adam_bytes = w.layout()[2] * 32
+    # algorithmic bytes: gather 4 levels x 8 corners x 16 B (8 B from the BF16 copy) and 512 B
+    # of FP32 gradient scattered per sample; Adam 32 B per parameter (+2 B per grid entry copied)
+    render_bytes = S * ((256 if ctx.bf16 else 512) + 512)
+    adam_bytes = w.layout()[2] * 32 + (2 * n_grid_ if ctx.bf16 else 0)
     dom = max(("render", "adam"), key=lambda k: avg[k])
     dom_bytes = render_bytes if dom == "render" else adam_bytes
     achieved = dom_bytes / (avg[dom] / 1e3) / 1e9
@@ -190,7 +194,7 @@ def run_ours(args):
     line = {
         "metric": METRIC, "value": round(value, 1), "unit": "rays/s", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": round(ms / args.steps, 4), "higher_is_better": True,
-        "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "scaling": "weak", "vs_baseline": None, "dtype": "bf16" if ctx.bf16 else "f32", "data": "synthetic",
         "config": {"workload": w.name, "rays": w.rays, "samples_per_ray": w.n_samples,
                    "samples_per_s": round(value * w.n_samples, 1), "smooth_points": w.n_smooth,
                    "params": w.layout()[2], "grid_params": n_grid, "frames": fr.depth.shape[0],

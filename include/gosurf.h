@@ -52,6 +52,10 @@ typedef enum {
   GS_ERR_UNSUPPORTED = 6  /* configuration outside what this build supports */
 } gs_status;
 
+/* Arithmetic forms of the render pass (gs_config.precision): */
+#define GS_PREC_FP32 0 /* FP32 grid gathers; decoders on tensor cores with FP32-grade products */
+#define GS_PREC_BF16 1 /* gathers from the bfloat16 grid copy; decoders in BF16 with FP32 accumulation */
+
 /* Sample classes written by gs_sample_rays (Sec. 3.3): */
 #define GS_CLS_NONE 0 /* no SDF supervision (behind the surface, or the ray has no depth) */
 #define GS_CLS_TR 1   /* near surface, |D - d| <= t: truncated-SDF loss */
@@ -72,6 +76,7 @@ typedef struct gs_config {
   int32_t max_rays;           /* largest ray batch any call will see (workspace sizing) */
   int32_t max_smooth;         /* largest smoothness point batch */
   float delta_s;              /* smoothness perturbation length, metres (Sec. 3.3) */
+  int32_t precision;          /* GS_PREC_FP32 or GS_PREC_BF16 */
 } gs_config;
 
 /* Posed RGB-D frames resident in device memory (Sec. 3: {I_t, D_t}, xi_t). */
@@ -124,21 +129,23 @@ gs_status gs_sample_rays(gs_ctx* ctx, const gs_frames* frames, uint64_t seed, ui
 
 /* Forward pass (Sec. 3.1-3.4): loss[6] = L_rgb, L_d, L_sdf, L_fs, L_smooth and the weighted
  * total sum_k lam_k L_k (device floats; per-CTA partial sums are combined in FP64).
- * rgb_hat [R][3], d_hat [R], wsum [R] (sum of weights) may each be NULL. */
-gs_status gs_forward(gs_ctx* ctx, const float* theta, const gs_batch* batch, float* loss, float* rgb_hat,
-                     float* d_hat, float* wsum, void* stream);
+ * theta_bf16: the bfloat16 copy of the grid that gs_adam_step writes; read by the gathers of
+ * the BF16 form (required there), ignored (may be NULL) in the FP32 form.  The decoders always
+ * read theta.  rgb_hat [R][3], d_hat [R], wsum [R] (sum of weights) may each be NULL. */
+gs_status gs_forward(gs_ctx* ctx, const float* theta, const uint16_t* theta_bf16, const gs_batch* batch, float* loss,
+                     float* rgb_hat, float* d_hat, float* wsum, void* stream);
 
 /* Backward pass: grad += d(sum_k dloss_k * out_k)/d theta, with out = the six outputs of
  * gs_forward and dloss [6] device floats (NULL = (0,0,0,0,0,1), the gradient of the total).
  * Activations are recomputed from theta (nothing is stored between the two calls).  Grid
  * gradients are accumulated with FP32 atomics (summation order not deterministic); decoder
  * gradients are reduced in a fixed order. */
-gs_status gs_backward(gs_ctx* ctx, const float* theta, const gs_batch* batch, const float* dloss, float* grad,
-                      void* stream);
+gs_status gs_backward(gs_ctx* ctx, const float* theta, const uint16_t* theta_bf16, const gs_batch* batch,
+                      const float* dloss, float* grad, void* stream);
 
 /* Forward and backward in one pass over the batch (loss and grad as above). */
-gs_status gs_forward_backward(gs_ctx* ctx, const float* theta, const gs_batch* batch, const float* dloss,
-                              float* loss, float* grad, void* stream);
+gs_status gs_forward_backward(gs_ctx* ctx, const float* theta, const uint16_t* theta_bf16, const gs_batch* batch,
+                              const float* dloss, float* loss, float* grad, void* stream);
 
 /* Adam (Kingma & Ba) over the n-entry flat vectors theta, grad, m, v with bias correction
  * for step t >= 1; entries [0, n_grid) use lr_grid, the rest lr_mlp (Sec. 4: 1e-2 for
@@ -168,7 +175,8 @@ gs_status gs_voxel_index(gs_ctx* ctx, const float* x, int32_t P, int64_t* out, v
  * array's device address and writes its default dloss (a synchronous set-up), so make that
  * first call before any stream capture.  All calls share the array: calls whose work
  * overlaps on the GPU (other streams, other host threads) race and give wrong results.
- * Arguments, outputs and errors as gs_forward_backward; messages via gs_last_error(NULL). */
+ * FP32 form only (cfg->precision must be GS_PREC_FP32).  Arguments, outputs and errors as
+ * gs_forward_backward; messages via gs_last_error(NULL). */
 gs_status gs_forward_backward_noalloc(const gs_config* cfg, const float* theta, const gs_batch* batch,
                                       const float* dloss, float* loss, float* grad, void* stream);
 

@@ -12,8 +12,8 @@ from dataclasses import dataclass
 
 import torch
 
-from ._lib import (GS_FEAT, GS_LEVELS, GS_MLP_PARAMS, GS_NUM_LOSS, EXPORTS, GoSurfError, GsBatch, GsConfig,
-                   GsFrames, lib, library_path)
+from ._lib import (GS_FEAT, GS_LEVELS, GS_MLP_PARAMS, GS_NUM_LOSS, GS_PREC_BF16, GS_PREC_FP32, EXPORTS, GoSurfError,
+                   GsBatch, GsConfig, GsFrames, lib, library_path)
 
 __all__ = ["Context", "Batch", "DeviceFrames", "GoSurfStep", "make_config", "GS_MLP_PARAMS", "GS_NUM_LOSS",
            "library_path", "EXPORTS"]
@@ -35,6 +35,7 @@ def make_config(workload, max_rays=None, max_smooth=None) -> GsConfig:
     c.max_rays = int(max_rays if max_rays is not None else workload.rays)
     c.max_smooth = int(max_smooth if max_smooth is not None else workload.n_smooth)
     c.delta_s = float(workload.delta_s)
+    c.precision = GS_PREC_BF16 if getattr(workload, "precision", "fp32") == "bf16" else GS_PREC_FP32
     return c
 
 
@@ -125,19 +126,24 @@ class Context:
         b = batch.struct()
         self._check(self.L.gs_sample_rays(self.h, ctypes.byref(frames.s), seed, step, ctypes.byref(b), _stream()))
 
-    def forward(self, theta, batch: Batch, loss, rgb_hat=None, d_hat=None, wsum=None):
+    def forward(self, theta, batch: Batch, loss, rgb_hat=None, d_hat=None, wsum=None, theta_bf16=None):
         b = batch.struct()
-        self._check(self.L.gs_forward(self.h, _ptr(theta), ctypes.byref(b), _ptr(loss), _ptr(rgb_hat), _ptr(d_hat),
-                                      _ptr(wsum), _stream()))
+        self._check(self.L.gs_forward(self.h, _ptr(theta), _ptr(theta_bf16), ctypes.byref(b), _ptr(loss),
+                                      _ptr(rgb_hat), _ptr(d_hat), _ptr(wsum), _stream()))
 
-    def backward(self, theta, batch: Batch, dloss, grad):
+    def backward(self, theta, batch: Batch, dloss, grad, theta_bf16=None):
         b = batch.struct()
-        self._check(self.L.gs_backward(self.h, _ptr(theta), ctypes.byref(b), _ptr(dloss), _ptr(grad), _stream()))
+        self._check(self.L.gs_backward(self.h, _ptr(theta), _ptr(theta_bf16), ctypes.byref(b), _ptr(dloss),
+                                       _ptr(grad), _stream()))
 
-    def forward_backward(self, theta, batch: Batch, dloss, loss, grad):
+    def forward_backward(self, theta, batch: Batch, dloss, loss, grad, theta_bf16=None):
         b = batch.struct()
-        self._check(self.L.gs_forward_backward(self.h, _ptr(theta), ctypes.byref(b), _ptr(dloss), _ptr(loss),
-                                               _ptr(grad), _stream()))
+        self._check(self.L.gs_forward_backward(self.h, _ptr(theta), _ptr(theta_bf16), ctypes.byref(b), _ptr(dloss),
+                                               _ptr(loss), _ptr(grad), _stream()))
+
+    @property
+    def bf16(self) -> bool:
+        return self.cfg.precision == GS_PREC_BF16
 
     def adam_step(self, theta, grad, m, v, t, lr_grid, lr_mlp, beta1=0.9, beta2=0.999, eps=1e-8, theta_bf16=None):
         n = theta.numel()
@@ -160,17 +166,17 @@ class GoSurfStep(torch.autograd.Function):
     parameter vector; backward runs gs_backward with the incoming gradient as dloss."""
 
     @staticmethod
-    def forward(fctx, theta, ctx: Context, batch: Batch):
+    def forward(fctx, theta, ctx: Context, batch: Batch, theta_bf16=None):
         loss = torch.empty(GS_NUM_LOSS, device=theta.device, dtype=torch.float32)
-        ctx.forward(theta.detach(), batch, loss)
+        ctx.forward(theta.detach(), batch, loss, theta_bf16=theta_bf16)
         fctx.save_for_backward(theta)
-        fctx.gs = (ctx, batch)
+        fctx.gs = (ctx, batch, theta_bf16)
         return loss
 
     @staticmethod
     def backward(fctx, dloss):
         (theta,) = fctx.saved_tensors
-        ctx, batch = fctx.gs
+        ctx, batch, theta_bf16 = fctx.gs
         grad = torch.zeros_like(theta)
-        ctx.backward(theta.detach(), batch, dloss.contiguous().float(), grad)
-        return grad, None, None
+        ctx.backward(theta.detach(), batch, dloss.contiguous().float(), grad, theta_bf16=theta_bf16)
+        return grad, None, None, None

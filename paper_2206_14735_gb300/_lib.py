@@ -12,6 +12,7 @@ _LIB = None
 _LOCK = threading.Lock()
 
 GS_LEVELS, GS_FEAT, GS_MLP_PARAMS, GS_NUM_LOSS = 4, 4, 1684, 6
+GS_PREC_FP32, GS_PREC_BF16 = 0, 1
 STATUS = {0: "GS_OK", 1: "GS_ERR_INVALID_ARG", 2: "GS_ERR_SHAPE", 3: "GS_ERR_ALIGN", 4: "GS_ERR_CUDA",
           5: "GS_ERR_DEVICE", 6: "GS_ERR_UNSUPPORTED"}
 
@@ -25,7 +26,7 @@ class GsConfig(ctypes.Structure):
                 ("n_strat", ctypes.c_int32), ("n_guided", ctypes.c_int32), ("near_m", ctypes.c_float),
                 ("far_m", ctypes.c_float), ("guide_half", ctypes.c_float), ("trunc", ctypes.c_float),
                 ("kappa_fs", ctypes.c_float), ("lam", ctypes.c_float * 5), ("max_rays", ctypes.c_int32),
-                ("max_smooth", ctypes.c_int32), ("delta_s", ctypes.c_float)]
+                ("max_smooth", ctypes.c_int32), ("delta_s", ctypes.c_float), ("precision", ctypes.c_int32)]
 
 
 class GsFrames(ctypes.Structure):
@@ -67,11 +68,11 @@ def lib():
             L.gs_sample_rays.restype = i32
             L.gs_sample_rays.argtypes = [vp, ctypes.POINTER(GsFrames), u64, u32, ctypes.POINTER(GsBatch), vp]
             L.gs_forward.restype = i32
-            L.gs_forward.argtypes = [vp, vp, ctypes.POINTER(GsBatch), vp, vp, vp, vp, vp]
+            L.gs_forward.argtypes = [vp, vp, vp, ctypes.POINTER(GsBatch), vp, vp, vp, vp, vp]
             L.gs_backward.restype = i32
-            L.gs_backward.argtypes = [vp, vp, ctypes.POINTER(GsBatch), vp, vp, vp]
+            L.gs_backward.argtypes = [vp, vp, vp, ctypes.POINTER(GsBatch), vp, vp, vp]
             L.gs_forward_backward.restype = i32
-            L.gs_forward_backward.argtypes = [vp, vp, ctypes.POINTER(GsBatch), vp, vp, vp, vp]
+            L.gs_forward_backward.argtypes = [vp, vp, vp, ctypes.POINTER(GsBatch), vp, vp, vp, vp]
             L.gs_adam_step.restype = i32
             L.gs_adam_step.argtypes = [vp, vp, vp, vp, vp, i64, i64, i32, f32, f32, f32, f32, f32, vp, vp]
             L.gs_query_sdf.restype = i32

@@ -131,12 +131,16 @@ gs_status gs_sample_rays(gs_ctx* ctx, const gs_frames* frames, uint64_t seed, ui
   return s == GS_OK ? s : cuda_fail(ctx, "gs_sample_rays");
 }
 
-static gs_status render_common(gs_ctx* ctx, const char* who, const float* theta, const gs_batch* batch,
-                               const float* dloss, float* loss, float* grad, float* rgb_hat, float* d_hat, float* wsum,
-                               int mode, void* stream) {
+static gs_status render_common(gs_ctx* ctx, const char* who, const float* theta, const uint16_t* theta_bf16,
+                               const gs_batch* batch, const float* dloss, float* loss, float* grad, float* rgb_hat,
+                               float* d_hat, float* wsum, int mode, void* stream) {
   if (!ctx) return fail(nullptr, GS_ERR_INVALID_ARG, "ctx is NULL");
   if (!theta) return fail(ctx, GS_ERR_INVALID_ARG, "theta is NULL");
   if (!aligned16(theta)) return fail(ctx, GS_ERR_ALIGN, "theta is not 16-byte aligned");
+  if (ctx->cfg.precision == GS_PREC_BF16 && !theta_bf16)
+    return fail(ctx, GS_ERR_INVALID_ARG, "the BF16 form needs theta_bf16 (the grid copy written by gs_adam_step)");
+  if (ctx->cfg.precision == GS_PREC_BF16 && (reinterpret_cast<uintptr_t>(theta_bf16) & 7u))
+    return fail(ctx, GS_ERR_ALIGN, "theta_bf16 is not 8-byte aligned");
   if ((mode & 1) && !loss) return fail(ctx, GS_ERR_INVALID_ARG, "loss is NULL");
   if ((mode & 2) && !grad) return fail(ctx, GS_ERR_INVALID_ARG, "grad is NULL");
   if ((mode & 2) && !aligned16(grad)) return fail(ctx, GS_ERR_ALIGN, "grad is not 16-byte aligned");
@@ -145,7 +149,8 @@ static gs_status render_common(gs_ctx* ctx, const char* who, const float* theta,
   cudaStream_t st = (cudaStream_t)stream;
   ctx->last_stream = st;
   const float* dl = dloss ? dloss : ctx->default_dloss;
-  if (batch->R > 0 && gs_launch_render(ctx, theta, batch, dl, grad, rgb_hat, d_hat, wsum, mode, st) != GS_OK)
+  if (batch->R > 0 &&
+      gs_launch_render(ctx, theta, theta_bf16, batch, dl, grad, rgb_hat, d_hat, wsum, mode, st) != GS_OK)
     return cuda_fail(ctx, who);
   if (gs_launch_smooth(ctx, theta, batch, dl, grad, mode, st) != GS_OK) return cuda_fail(ctx, who);
   // partial rows: render CTAs (if any rays) then smoothness CTAs (if any points)
@@ -163,20 +168,22 @@ static gs_status render_common(gs_ctx* ctx, const char* who, const float* theta,
   return GS_OK;
 }
 
-gs_status gs_forward(gs_ctx* ctx, const float* theta, const gs_batch* batch, float* loss, float* rgb_hat,
-                     float* d_hat, float* wsum, void* stream) {
-  return render_common(ctx, "gs_forward", theta, batch, nullptr, loss, nullptr, rgb_hat, d_hat, wsum, 1, stream);
-}
-
-gs_status gs_backward(gs_ctx* ctx, const float* theta, const gs_batch* batch, const float* dloss, float* grad,
-                      void* stream) {
-  return render_common(ctx, "gs_backward", theta, batch, dloss, nullptr, grad, nullptr, nullptr, nullptr, 2, stream);
-}
-
-gs_status gs_forward_backward(gs_ctx* ctx, const float* theta, const gs_batch* batch, const float* dloss,
-                              float* loss, float* grad, void* stream) {
-  return render_common(ctx, "gs_forward_backward", theta, batch, dloss, loss, grad, nullptr, nullptr, nullptr, 3,
+gs_status gs_forward(gs_ctx* ctx, const float* theta, const uint16_t* theta_bf16, const gs_batch* batch, float* loss,
+                     float* rgb_hat, float* d_hat, float* wsum, void* stream) {
+  return render_common(ctx, "gs_forward", theta, theta_bf16, batch, nullptr, loss, nullptr, rgb_hat, d_hat, wsum, 1,
                        stream);
+}
+
+gs_status gs_backward(gs_ctx* ctx, const float* theta, const uint16_t* theta_bf16, const gs_batch* batch,
+                      const float* dloss, float* grad, void* stream) {
+  return render_common(ctx, "gs_backward", theta, theta_bf16, batch, dloss, nullptr, grad, nullptr, nullptr, nullptr,
+                       2, stream);
+}
+
+gs_status gs_forward_backward(gs_ctx* ctx, const float* theta, const uint16_t* theta_bf16, const gs_batch* batch,
+                              const float* dloss, float* loss, float* grad, void* stream) {
+  return render_common(ctx, "gs_forward_backward", theta, theta_bf16, batch, dloss, loss, grad, nullptr, nullptr,
+                       nullptr, 3, stream);
 }
 
 gs_status gs_adam_step(gs_ctx* ctx, float* theta, float* grad, float* m, float* v, int64_t n, int64_t n_grid,

@@ -31,8 +31,9 @@ struct gs_ctx {
 gs_status gs_launch_sample(const gs_ctx* ctx, const gs_frames* f, uint64_t seed, uint32_t step, const gs_batch* b,
                            cudaStream_t st);
 // mode bit 1: forward outputs (loss partials, per-ray outputs), bit 2: backward (grad)
-gs_status gs_launch_render(const gs_ctx* ctx, const float* theta, const gs_batch* b, const float* dloss, float* grad,
-                           float* rgb_hat, float* d_hat, float* wsum, int mode, cudaStream_t st);
+gs_status gs_launch_render(const gs_ctx* ctx, const float* theta, const uint16_t* theta_bf16, const gs_batch* b,
+                           const float* dloss, float* grad, float* rgb_hat, float* d_hat, float* wsum, int mode,
+                           cudaStream_t st);
 gs_status gs_launch_smooth(const gs_ctx* ctx, const float* theta, const gs_batch* b, const float* dloss, float* grad,
                            int mode, cudaStream_t st);
 gs_status gs_launch_finalize(const gs_ctx* ctx, const gs_batch* b, float* loss, float* grad, int mode,

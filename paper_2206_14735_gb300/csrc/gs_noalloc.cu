@@ -58,6 +58,8 @@ extern "C" gs_status gs_forward_backward_noalloc(const gs_config* cfg, const flo
         return noalloc_fail(GS_ERR_INVALID_ARG, "gs_forward_backward_noalloc: every level needs >= 2 vertices per axis");
     if (!(cfg->voxel[l] > 0.0f)) return noalloc_fail(GS_ERR_INVALID_ARG, "gs_forward_backward_noalloc: voxel size must be > 0");
   }
+  if (cfg->precision != GS_PREC_FP32)
+    return noalloc_fail(GS_ERR_UNSUPPORTED, "gs_forward_backward_noalloc: FP32 form only");
   const int N = cfg->n_strat + cfg->n_guided;
   if (cfg->n_strat < 1 || cfg->n_guided < 0 || N < 2 || N > 128)
     return noalloc_fail(GS_ERR_SHAPE, "gs_forward_backward_noalloc: samples per ray must be in [2, 128]");
@@ -104,7 +106,7 @@ extern "C" gs_status gs_forward_backward_noalloc(const gs_config* cfg, const flo
   c.status = reinterpret_cast<int*>(c.default_dloss + 8);  // device-side check word
   const float* dl = dloss ? dloss : c.default_dloss;
   cudaStream_t st = (cudaStream_t)stream;
-  if (batch->R > 0 && gs_launch_render(&c, theta, batch, dl, grad, nullptr, nullptr, nullptr, 3, st) != GS_OK)
+  if (batch->R > 0 && gs_launch_render(&c, theta, nullptr, batch, dl, grad, nullptr, nullptr, nullptr, 3, st) != GS_OK)
     return noalloc_fail(GS_ERR_CUDA, "gs_forward_backward_noalloc: render launch failed");
   if (gs_launch_smooth(&c, theta, batch, dl, grad, 3, st) != GS_OK)
     return noalloc_fail(GS_ERR_CUDA, "gs_forward_backward_noalloc: smoothness launch failed");

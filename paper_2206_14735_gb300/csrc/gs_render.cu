@@ -4,10 +4,14 @@
 
 namespace gs {
 
-extern template gs_status launch_tc_n<1>(const gs_ctx*, RenderTcArgs&, int, cudaStream_t);
-extern template gs_status launch_tc_n<2>(const gs_ctx*, RenderTcArgs&, int, cudaStream_t);
-extern template gs_status launch_tc_n<3>(const gs_ctx*, RenderTcArgs&, int, cudaStream_t);
-extern template gs_status launch_tc_n<4>(const gs_ctx*, RenderTcArgs&, int, cudaStream_t);
+extern template gs_status launch_tc_n<PrecBF16x3, 1>(const gs_ctx*, RenderTcArgs&, int, cudaStream_t);
+extern template gs_status launch_tc_n<PrecBF16x3, 2>(const gs_ctx*, RenderTcArgs&, int, cudaStream_t);
+extern template gs_status launch_tc_n<PrecBF16x3, 3>(const gs_ctx*, RenderTcArgs&, int, cudaStream_t);
+extern template gs_status launch_tc_n<PrecBF16x3, 4>(const gs_ctx*, RenderTcArgs&, int, cudaStream_t);
+extern template gs_status launch_tc_n<PrecBF16, 1>(const gs_ctx*, RenderTcArgs&, int, cudaStream_t);
+extern template gs_status launch_tc_n<PrecBF16, 2>(const gs_ctx*, RenderTcArgs&, int, cudaStream_t);
+extern template gs_status launch_tc_n<PrecBF16, 3>(const gs_ctx*, RenderTcArgs&, int, cudaStream_t);
+extern template gs_status launch_tc_n<PrecBF16, 4>(const gs_ctx*, RenderTcArgs&, int, cudaStream_t);
 
 // ------------------------------------------------------------------------------------
 // combine per-CTA partials: losses in FP64, decoder gradients in a fixed order
@@ -138,11 +142,13 @@ __global__ void voxel_index_kernel(GridDesc g, const float* __restrict__ xq, int
 
 using namespace gs;
 
-gs_status gs_launch_render(const gs_ctx* ctx, const float* theta, const gs_batch* b, const float* dloss, float* grad,
-                           float* rgb_hat, float* d_hat, float* wsum, int mode, cudaStream_t st) {
+gs_status gs_launch_render(const gs_ctx* ctx, const float* theta, const uint16_t* theta_bf16, const gs_batch* b,
+                           const float* dloss, float* grad, float* rgb_hat, float* d_hat, float* wsum, int mode,
+                           cudaStream_t st) {
   RenderTcArgs a;
   a.g = ctx->grid;
   a.theta = theta;
+  a.theta_bf16 = theta_bf16;
   a.R = b->R;
   a.N = b->N;
   a.o = b->origin;
@@ -163,11 +169,20 @@ gs_status gs_launch_render(const gs_ctx* ctx, const float* theta, const gs_batch
   a.wsum = wsum;
   a.status = ctx->status;
   const int nch = (b->N + 31) / 32;
+  if (ctx->cfg.precision == GS_PREC_BF16) {
+    switch (nch) {
+      case 1: return launch_tc_n<PrecBF16, 1>(ctx, a, mode, st);
+      case 2: return launch_tc_n<PrecBF16, 2>(ctx, a, mode, st);
+      case 3: return launch_tc_n<PrecBF16, 3>(ctx, a, mode, st);
+      case 4: return launch_tc_n<PrecBF16, 4>(ctx, a, mode, st);
+      default: return GS_ERR_UNSUPPORTED;
+    }
+  }
   switch (nch) {
-    case 1: return launch_tc_n<1>(ctx, a, mode, st);
-    case 2: return launch_tc_n<2>(ctx, a, mode, st);
-    case 3: return launch_tc_n<3>(ctx, a, mode, st);
-    case 4: return launch_tc_n<4>(ctx, a, mode, st);
+    case 1: return launch_tc_n<PrecBF16x3, 1>(ctx, a, mode, st);
+    case 2: return launch_tc_n<PrecBF16x3, 2>(ctx, a, mode, st);
+    case 3: return launch_tc_n<PrecBF16x3, 3>(ctx, a, mode, st);
+    case 4: return launch_tc_n<PrecBF16x3, 4>(ctx, a, mode, st);
     default: return GS_ERR_UNSUPPORTED;
   }
 }

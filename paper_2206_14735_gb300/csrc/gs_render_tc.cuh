@@ -271,17 +271,29 @@ __device__ __forceinline__ void warp_weight_grad(float* st, int lane, const floa
 }
 
 // ---- gather / scatter -------------------------------------------------------------------
-__device__ __forceinline__ void gather_z(const GridDesc& g, const float* __restrict__ theta, const float x[3],
-                                         float z[kZ]) {
+// z = [V^0(x), .., V^3(x)] from the FP32 grid, or (BF16 form) from its bfloat16 copy
+template <bool BF16GRID>
+__device__ __forceinline__ void gather_z(const GridDesc& g, const float* __restrict__ theta,
+                                         const uint16_t* __restrict__ theta_bf16, const float x[3], float z[kZ]) {
 #pragma unroll
   for (int l = 0; l < kLevels; ++l) {
     const Cell c = locate(g, l, x);
     float w[8];
     corner_weights(c.f, w);
-    const float4* base = reinterpret_cast<const float4*>(theta + g.off[l]);
     float4 v[8];
+    if constexpr (BF16GRID) {
+      const uint2* base = reinterpret_cast<const uint2*>(theta_bf16 + g.off[l]);
 #pragma unroll
-    for (int k = 0; k < 8; ++k) v[k] = __ldg(base + c.vtx + corner_offset(g, l, k));
+      for (int k = 0; k < 8; ++k) {
+        const uint2 u = __ldg(base + c.vtx + corner_offset(g, l, k));
+        v[k] = make_float4(__uint_as_float(u.x << 16), __uint_as_float(u.x & 0xFFFF0000u),
+                           __uint_as_float(u.y << 16), __uint_as_float(u.y & 0xFFFF0000u));
+      }
+    } else {
+      const float4* base = reinterpret_cast<const float4*>(theta + g.off[l]);
+#pragma unroll
+      for (int k = 0; k < 8; ++k) v[k] = __ldg(base + c.vtx + corner_offset(g, l, k));
+    }
     float4 s = make_float4(0.f, 0.f, 0.f, 0.f);
 #pragma unroll
     for (int k = 0; k < 8; ++k) f4fma(s, w[k], v[k]);
@@ -356,6 +368,7 @@ __device__ __forceinline__ float pick_tc(const float (&arr)[N], int j) {
 struct RenderTcArgs {
   GridDesc g;
   const float* theta;
+  const uint16_t* theta_bf16;  // BF16 form: grid copy read by the gathers
   int R, N;
   const float *o, *r, *rgb, *D, *t;
   const uint8_t* cls;
@@ -477,7 +490,7 @@ __global__ void __launch_bounds__(GR * kGroupThreads, 1) render_tc_kernel(Render
       if (valid) {
         float x[3];
         sample_pos(o, r, t, x);
-        gather_z(a.g, a.theta, x, z);
+        gather_z<(P::planes == 1)>(a.g, a.theta, a.theta_bf16, x, z);
       } else {
 #pragma unroll
         for (int k = 0; k < kZ; ++k) z[k] = 0.f;
@@ -683,7 +696,7 @@ __global__ void __launch_bounds__(GR * kGroupThreads, 1) render_tc_kernel(Render
       sample_pos(o, r, t, x);
       float z[kZ];
       if (valid) {
-        gather_z(a.g, a.theta, x, z);
+        gather_z<(P::planes == 1)>(a.g, a.theta, a.theta_bf16, x, z);
       } else {
 #pragma unroll
         for (int k = 0; k < kZ; ++k) z[k] = 0.f;
@@ -857,12 +870,12 @@ gs_status launch_tc_t(const gs_ctx* ctx, RenderTcArgs& a, cudaStream_t st) {
   return cudaPeekAtLastError() == cudaSuccess ? GS_OK : GS_ERR_CUDA;
 }
 
-template <int NCH>
+template <class P, int NCH>
 gs_status launch_tc_n(const gs_ctx* ctx, RenderTcArgs& a, int mode, cudaStream_t st) {
-  constexpr int GR = kRenderGroups;  // 4 groups x 128 tensor-memory columns: one CTA per SM
-  if (mode == 1) return launch_tc_t<PrecBF16x3, NCH, GR, true, false>(ctx, a, st);
-  if (mode == 2) return launch_tc_t<PrecBF16x3, NCH, GR, false, true>(ctx, a, st);
-  return launch_tc_t<PrecBF16x3, NCH, GR, true, true>(ctx, a, st);
+  constexpr int GR = kRenderGroups;  // tile groups of 128 tensor-memory columns in one CTA per SM
+  if (mode == 1) return launch_tc_t<P, NCH, GR, true, false>(ctx, a, st);
+  if (mode == 2) return launch_tc_t<P, NCH, GR, false, true>(ctx, a, st);
+  return launch_tc_t<P, NCH, GR, true, true>(ctx, a, st);
 }
 
 }  // namespace gs

@@ -70,8 +70,8 @@ def test_create_rejects_bad_configs_on_host(L):
 
 def test_entry_points_reject_null_context(L):
     assert L.gs_sample_rays(None, None, 0, 0, None, None) == 1
-    assert L.gs_forward(None, None, None, None, None, None, None, None) == 1
-    assert L.gs_backward(None, None, None, None, None, None) == 1
+    assert L.gs_forward(None, None, None, None, None, None, None, None, None) == 1
+    assert L.gs_backward(None, None, None, None, None, None, None) == 1
     assert L.gs_adam_step(None, None, None, None, None, 0, 0, 1, 0.0, 0.0, 0.9, 0.999, 1e-8, None, None) == 1
     assert L.gs_query_sdf(None, None, None, 0, None, None, None) == 1
     assert L.gs_sync_status(None) == 1
