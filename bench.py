@@ -95,7 +95,7 @@ def run_ours(args):
     t0 = time.time()
     fr = sg.make_frames(w, n_frames=args.frames)
     t_frames = time.time() - t0
-    ctx = gs.Context(w)
+    ctx = gs.Context(w, store_activations=args.store)
     dfr = gs.DeviceFrames(fr.rgb, fr.depth, fr.c2w, fr.fx, fr.fy, fr.cx, fr.cy)
     theta = torch.from_numpy(sg.init_params(w)).cuda()
     grad, m, v = torch.zeros_like(theta), torch.zeros_like(theta), torch.zeros_like(theta)
@@ -199,6 +199,7 @@ def run_ours(args):
                    "samples_per_s": round(value * w.n_samples, 1), "smooth_points": w.n_smooth,
                    "params": w.layout()[2], "grid_params": n_grid, "frames": fr.depth.shape[0],
                    "resolution": [w.width, w.height], "parallelism": f"replicas{world}",
+                   "activations": "stored" if args.store else "recomputed",
                    "l2": "inputs larger than L2: 1.2 GB of parameter/gradient/moment state streamed per step",
                    "frame_render_s": round(t_frames, 1)},
         "kernels_ms": {k: round(vv, 4) for k, vv in avg.items()},
@@ -217,9 +218,54 @@ def run_ours(args):
         "clocks": clk,
         "loss_last": [round(x, 6) for x in lossv],
     }
+    if args.diff_report:
+        line["differentiation"] = differentiation_report(w, dfr, theta, mirror)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(w, fr, args.cpu_rays)
     return line
+
+
+def differentiation_report(w, dfr, theta, mirror, reps=20):
+    """Forward + backward of one sampled batch with the decoder activations recomputed in the
+    backward pass versus stored by the forward pass: device time per call (CUDA events) for
+    the split calls (gs_forward then gs_backward, as the autograd Function runs them) and the
+    fused call, and the memory the store takes."""
+    import torch
+
+    import paper_2206_14735_gb300 as gs
+    out = {}
+    stream = torch.cuda.current_stream()
+    for name, store in (("recompute", False), ("store", True)):
+        c = gs.Context(w, store_activations=store)
+        b = gs.Batch.allocate(w.rays, w.n_samples, w.n_smooth)
+        c.sample_rays(dfr, 11, 0, b)
+        loss = torch.empty(6, device="cuda")
+        grad = torch.zeros_like(theta)
+        ms = {"forward": 0.0, "backward": 0.0, "fused": 0.0}
+        for it in range(reps + 3):
+            ev = [torch.cuda.Event(enable_timing=True) for _ in range(4)]
+            ev[0].record(stream)
+            c.forward(theta, b, loss, theta_bf16=mirror)
+            ev[1].record(stream)
+            c.backward(theta, b, None, grad, theta_bf16=mirror)
+            ev[2].record(stream)
+            c.forward_backward(theta, b, None, loss, grad, theta_bf16=mirror)
+            ev[3].record(stream)
+            torch.cuda.synchronize()
+            if it >= 3:
+                ms["forward"] += ev[0].elapsed_time(ev[1]) / reps
+                ms["backward"] += ev[1].elapsed_time(ev[2]) / reps
+                ms["fused"] += ev[2].elapsed_time(ev[3]) / reps
+        c.sync_status()
+        extra = w.rays * w.n_samples * 99 * 4 if store else 0
+        out[name] = {"forward_ms": round(ms["forward"], 4), "backward_ms": round(ms["backward"], 4),
+                     "split_ms": round(ms["forward"] + ms["backward"], 4), "fused_ms": round(ms["fused"], 4),
+                     "extra_device_bytes": extra}
+        c.close()
+    out["what"] = (f"{w.rays} rays x {w.n_samples} samples + {w.n_smooth} smoothness points; "
+                   f"store keeps 99 floats per sample (z, both ReLU layers, SDF and geometric feature, colour); "
+                   f"mean of {reps} calls each")
+    return out
 
 
 def _oracle_sample_step(w, fr, R, P, n_adam, reps_min_s, reps_max):
@@ -304,6 +350,9 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--traffic-render", type=float, default=None)
     ap.add_argument("--traffic-adam", type=float, default=None)
+    ap.add_argument("--diff-report", action="store_true",
+                    help="also time forward/backward with stored versus recomputed decoder activations")
+    ap.add_argument("--store", action="store_true", help="keep decoder activations between forward and backward")
     args = ap.parse_args()
     line = run_reference(args) if args.impl == "reference" else run_ours(args)
     if line is not None:

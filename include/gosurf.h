@@ -77,6 +77,12 @@ typedef struct gs_config {
   int32_t max_smooth;         /* largest smoothness point batch */
   float delta_s;              /* smoothness perturbation length, metres (Sec. 3.3) */
   int32_t precision;          /* GS_PREC_FP32 or GS_PREC_BF16 */
+  int32_t store_activations;  /* 1: every forward pass writes each sample's decoder inputs and
+                                 activations (z, ReLU outputs, SDF, geometric feature, colour:
+                                 99 floats = 396 bytes per sample, max_rays x N samples, one
+                                 plane per field, allocated by gs_create) and every backward
+                                 pass reads them instead of gathering again and recomputing the
+                                 decoders; 0: the backward pass recomputes them (no memory) */
 } gs_config;
 
 /* Posed RGB-D frames resident in device memory (Sec. 3: {I_t, D_t}, xi_t). */
@@ -137,7 +143,10 @@ gs_status gs_forward(gs_ctx* ctx, const float* theta, const uint16_t* theta_bf16
 
 /* Backward pass: grad += d(sum_k dloss_k * out_k)/d theta, with out = the six outputs of
  * gs_forward and dloss [6] device floats (NULL = (0,0,0,0,0,1), the gradient of the total).
- * Activations are recomputed from theta (nothing is stored between the two calls).  Grid
+ * With store_activations the activations kept by the last gs_forward (or
+ * gs_forward_backward) are read: that call must have seen the same theta and batch, and
+ * GS_ERR_INVALID_ARG is returned when no forward pass of a batch with this R, N and t
+ * pointer came first.  Otherwise everything is recomputed from theta.  Grid
  * gradients are accumulated with FP32 atomics (summation order not deterministic); decoder
  * gradients are reduced in a fixed order. */
 gs_status gs_backward(gs_ctx* ctx, const float* theta, const uint16_t* theta_bf16, const gs_batch* batch,
@@ -159,6 +168,14 @@ gs_status gs_adam_step(gs_ctx* ctx, float* theta, float* grad, float* m, float* 
  * grad != NULL, grad_x phi [P][3] at points x [P][3]. */
 gs_status gs_query_sdf(gs_ctx* ctx, const float* theta, const float* x, int32_t P, float* sdf, float* grad,
                        void* stream);
+
+/* Reverse mode of gs_query_sdf with respect to the parameters (the double backward of the
+ * SDF gradient, Supp. Sec. 1): grad [n_params] += sum_p dsdf[p] d phi(x_p)/d theta
+ * + dgrad[p] . d grad_x phi(x_p)/d theta, for device arrays x [P][3], dsdf [P] and dgrad
+ * [P][3] (either may be NULL = zero).  theta and grad 16-byte aligned.  The points x are
+ * constants (no gradient with respect to x).  Accumulates with atomics (order not fixed). */
+gs_status gs_query_sdf_backward(gs_ctx* ctx, const float* theta, const float* x, int32_t P, const float* dsdf,
+                                const float* dgrad, float* grad, void* stream);
 
 /* Cell lookup used by every gather: out [P][4] = flat base-vertex index of the cell holding
  * x (clamped to the grid box) at each level, decided in binary32. */

@@ -79,6 +79,8 @@ def lib():
             L.oc_step.argtypes = [vp, vp, i32, i32] + [vp] * 6 + [i32] + [vp] * 11
             L.oc_query_sdf.restype = None
             L.oc_query_sdf.argtypes = [vp, vp, vp, i32, vp, vp]
+            L.oc_query_sdf_backward.restype = None
+            L.oc_query_sdf_backward.argtypes = [vp, vp, vp, i32, vp, vp, vp]
             L.oc_voxel_index.restype = None
             L.oc_voxel_index.argtypes = [vp, vp, i32, vp]
             L.oc_trilinear_coeffs.restype = None
@@ -189,6 +191,17 @@ def query_sdf(cfg: OcConfig, theta, x, want_grad=True):
     grad = np.empty((len(x), 3)) if want_grad else None
     lib().oc_query_sdf(ctypes.byref(cfg), _p(th), _p(x), len(x), _p(sdf), _p(grad))
     return sdf, grad
+
+
+def query_sdf_backward(cfg: OcConfig, theta, x, dsdf=None, dgrad=None) -> np.ndarray:
+    """d/dtheta of sum_i dsdf_i phi(x_i) + dgrad_i . grad_x phi(x_i) (flat, FP64)."""
+    th = np.ascontiguousarray(theta, dtype=np.float64)
+    x = np.ascontiguousarray(x, dtype=np.float32).reshape(-1, 3)
+    ds = None if dsdf is None else np.ascontiguousarray(dsdf, dtype=np.float64).reshape(len(x))
+    dg = None if dgrad is None else np.ascontiguousarray(dgrad, dtype=np.float64).reshape(len(x), 3)
+    grad = np.zeros(len(th))
+    lib().oc_query_sdf_backward(ctypes.byref(cfg), _p(th), _p(x), len(x), _p(ds), _p(dg), _p(grad))
+    return grad
 
 
 def voxel_index(cfg: OcConfig, x) -> np.ndarray:

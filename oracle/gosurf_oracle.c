@@ -466,6 +466,60 @@ void oc_query_sdf(const oc_config* c, const double* theta, const float* x, int P
   }
 }
 
+/* Reverse mode of oc_query_sdf with respect to theta (grid and decoders):
+ *   grad += sum_i dsdf_i d phi(x_i)/d theta + dgrad_i . d grad_x phi(x_i)/d theta.
+ * The first term is the ordinary backward pass of the SDF decoder and the trilinear gather
+ * (Sec. 3.1).  The second is the second-order path of Supp. Sec. 1: with p = d phi/d z and
+ * a = dgrad_i, a . grad_x phi = sum_k p_k j_k where j_k = a . d z_k / d x, so
+ *   d/d theta_{l,c,f} = p_{l,f} (1/v_l) (a . d w_c / d f)      (grid, through d z / d x),
+ *   d/d W1[h][k] = m_h W2[0][h] j_k,   d/d W2[0][h] = m_h (W1 j)_h  (decoder, through p),
+ * with m the layer-1 ReLU mask; p does not otherwise depend on theta (the decoder is
+ * piecewise linear in z).  dsdf or dgrad may be NULL (zero).  x is not differentiated. */
+void oc_query_sdf_backward(const oc_config* c, const double* theta, const float* x, int P, const double* dsdf,
+                           const double* dgrad, double* grad) {
+  const int64_t ng = grid_size(c);
+  mlp_t m = mlp_view(theta + ng);
+  double* gm = grad + ng;
+  for (int i = 0; i < P; ++i) {
+    cell_t cells[OC_LEVELS];
+    act_t A;
+    double dzdx[OC_Z][3];
+    features(c, theta, x + 3 * i, cells, A.z, dzdx);
+    decode(&m, &A);
+    if (dsdf && dsdf[i] != 0.0) {
+      const double dc[OC_RGB] = {0, 0, 0};
+      double dz[OC_Z];
+      decode_backward(&m, &A, dsdf[i], dc, gm, dz);
+      for (int l = 0; l < OC_LEVELS; ++l)
+        for (int cc = 0; cc < 8; ++cc)
+          for (int f = 0; f < OC_FEAT; ++f) grad[cells[l].corner[cc] + f] += cells[l].w[cc] * dz[OC_FEAT * l + f];
+    }
+    if (dgrad) {
+      const double* av = dgrad + 3 * i;
+      double p[OC_Z], mw2[OC_H1], jv[OC_Z];
+      dphi_dz(&m, &A, p, mw2);
+      for (int k = 0; k < OC_Z; ++k) jv[k] = av[0] * dzdx[k][0] + av[1] * dzdx[k][1] + av[2] * dzdx[k][2];
+      for (int l = 0; l < OC_LEVELS; ++l)
+        for (int cc = 0; cc < 8; ++cc) {
+          const double ad =
+              (av[0] * cells[l].dw[cc][0] + av[1] * cells[l].dw[cc][1] + av[2] * cells[l].dw[cc][2]) * cells[l].inv_v;
+          for (int f = 0; f < OC_FEAT; ++f) grad[cells[l].corner[cc] + f] += p[OC_FEAT * l + f] * ad;
+        }
+      double* gW1 = gm;
+      double* gW2 = gm + OC_H1 * OC_Z + OC_H1; /* row 0 of W2 */
+      for (int h = 0; h < OC_H1; ++h) {
+        if (!(A.y1[h] > 0)) continue;
+        double w1j = 0;
+        for (int k = 0; k < OC_Z; ++k) {
+          gW1[h * OC_Z + k] += m.W2[h] * jv[k];
+          w1j += m.W1[h * OC_Z + k] * jv[k];
+        }
+        gW2[h] += w1j;
+      }
+    }
+  }
+}
+
 /* base vertex (cell) index per level, binary32 decision; out [P][4] flat vertex ids */
 void oc_voxel_index(const oc_config* c, const float* x, int P, int64_t* out) {
   for (int i = 0; i < P; ++i)

@@ -15,11 +15,11 @@ import torch
 from ._lib import (GS_FEAT, GS_LEVELS, GS_MLP_PARAMS, GS_NUM_LOSS, GS_PREC_BF16, GS_PREC_FP32, EXPORTS, GoSurfError,
                    GsBatch, GsConfig, GsFrames, lib, library_path)
 
-__all__ = ["Context", "Batch", "DeviceFrames", "GoSurfStep", "make_config", "GS_MLP_PARAMS", "GS_NUM_LOSS",
+__all__ = ["Context", "Batch", "DeviceFrames", "GoSurfStep", "SdfGrad", "GoSurfError", "make_config", "GS_MLP_PARAMS", "GS_NUM_LOSS",
            "library_path", "EXPORTS"]
 
 
-def make_config(workload, max_rays=None, max_smooth=None) -> GsConfig:
+def make_config(workload, max_rays=None, max_smooth=None, store_activations=False) -> GsConfig:
     """gs_config from any object with the workload attributes (dims, voxels, extent_min,
     n_strat, n_guided, near, far, guide_half, trunc, kappa_fs, lambdas, n_smooth, delta_s, rays)."""
     c = GsConfig()
@@ -36,6 +36,7 @@ def make_config(workload, max_rays=None, max_smooth=None) -> GsConfig:
     c.max_smooth = int(max_smooth if max_smooth is not None else workload.n_smooth)
     c.delta_s = float(workload.delta_s)
     c.precision = GS_PREC_BF16 if getattr(workload, "precision", "fp32") == "bf16" else GS_PREC_FP32
+    c.store_activations = 1 if store_activations else 0
     return c
 
 
@@ -95,9 +96,9 @@ class Batch:
 class Context:
     """One gs_ctx (workspace sized at creation) on the current CUDA device."""
 
-    def __init__(self, workload, max_rays=None, max_smooth=None):
+    def __init__(self, workload, max_rays=None, max_smooth=None, store_activations=False):
         self.L = lib()
-        self.cfg = make_config(workload, max_rays, max_smooth)
+        self.cfg = make_config(workload, max_rays, max_smooth, store_activations)
         h = ctypes.c_void_p()
         self._check(self.L.gs_create(ctypes.byref(self.cfg), ctypes.byref(h)), None)
         self.h = h
@@ -153,6 +154,10 @@ class Context:
     def query_sdf(self, theta, x, sdf, grad=None):
         self._check(self.L.gs_query_sdf(self.h, _ptr(theta), _ptr(x), x.shape[0], _ptr(sdf), _ptr(grad), _stream()))
 
+    def query_sdf_backward(self, theta, x, dsdf, dgrad, grad):
+        self._check(self.L.gs_query_sdf_backward(self.h, _ptr(theta), _ptr(x), x.shape[0], _ptr(dsdf), _ptr(dgrad),
+                                                 _ptr(grad), _stream()))
+
     def voxel_index(self, x, out):
         self._check(self.L.gs_voxel_index(self.h, _ptr(x), x.shape[0], _ptr(out), _stream()))
 
@@ -180,3 +185,30 @@ class GoSurfStep(torch.autograd.Function):
         grad = torch.zeros_like(theta)
         ctx.backward(theta.detach(), batch, dloss.contiguous().float(), grad, theta_bf16=theta_bf16)
         return grad, None, None, None
+
+
+class SdfGrad(torch.autograd.Function):
+    """sdf, grad_x = SdfGrad.apply(theta, ctx, x): the SDF phi(x) [P] and its spatial gradient
+    [P][3] (gs_query_sdf) as differentiable functions of the flat parameter vector.  The
+    backward pass runs gs_query_sdf_backward, so a loss on grad_x (an eikonal or smoothness
+    term) reaches the grid and the decoder through the second-order path.  The points x are
+    treated as constants."""
+
+    @staticmethod
+    def forward(fctx, theta, ctx: Context, x):
+        x = x.detach().float().contiguous()
+        sdf = torch.empty(x.shape[0], device=x.device, dtype=torch.float32)
+        g = torch.empty(x.shape[0], 3, device=x.device, dtype=torch.float32)
+        ctx.query_sdf(theta.detach(), x, sdf, g)
+        fctx.save_for_backward(theta, x)
+        fctx.gs = ctx
+        return sdf, g
+
+    @staticmethod
+    def backward(fctx, dsdf, dgrad):
+        theta, x = fctx.saved_tensors
+        grad = torch.zeros_like(theta)
+        ds = None if dsdf is None else dsdf.contiguous().float()
+        dg = None if dgrad is None else dgrad.contiguous().float()
+        fctx.gs.query_sdf_backward(theta.detach(), x, ds, dg, grad)
+        return grad, None, None

@@ -17,7 +17,7 @@ STATUS = {0: "GS_OK", 1: "GS_ERR_INVALID_ARG", 2: "GS_ERR_SHAPE", 3: "GS_ERR_ALI
           5: "GS_ERR_DEVICE", 6: "GS_ERR_UNSUPPORTED"}
 
 EXPORTS = ["gs_create", "gs_destroy", "gs_param_count", "gs_sample_rays", "gs_forward", "gs_backward",
-           "gs_forward_backward", "gs_adam_step", "gs_query_sdf", "gs_voxel_index", "gs_sync_status",
+           "gs_forward_backward", "gs_adam_step", "gs_query_sdf", "gs_query_sdf_backward", "gs_voxel_index", "gs_sync_status",
            "gs_last_error", "gs_forward_backward_noalloc"]
 
 
@@ -26,7 +26,8 @@ class GsConfig(ctypes.Structure):
                 ("n_strat", ctypes.c_int32), ("n_guided", ctypes.c_int32), ("near_m", ctypes.c_float),
                 ("far_m", ctypes.c_float), ("guide_half", ctypes.c_float), ("trunc", ctypes.c_float),
                 ("kappa_fs", ctypes.c_float), ("lam", ctypes.c_float * 5), ("max_rays", ctypes.c_int32),
-                ("max_smooth", ctypes.c_int32), ("delta_s", ctypes.c_float), ("precision", ctypes.c_int32)]
+                ("max_smooth", ctypes.c_int32), ("delta_s", ctypes.c_float), ("precision", ctypes.c_int32),
+                ("store_activations", ctypes.c_int32)]
 
 
 class GsFrames(ctypes.Structure):
@@ -77,6 +78,8 @@ def lib():
             L.gs_adam_step.argtypes = [vp, vp, vp, vp, vp, i64, i64, i32, f32, f32, f32, f32, f32, vp, vp]
             L.gs_query_sdf.restype = i32
             L.gs_query_sdf.argtypes = [vp, vp, vp, i32, vp, vp, vp]
+            L.gs_query_sdf_backward.restype = i32
+            L.gs_query_sdf_backward.argtypes = [vp, vp, vp, i32, vp, vp, vp, vp]
             L.gs_voxel_index.restype = i32
             L.gs_voxel_index.argtypes = [vp, vp, i32, vp, vp]
             L.gs_sync_status.restype = i32

@@ -98,7 +98,10 @@ gs_status gs_create(const gs_config* cfg, gs_ctx** out) {
       cudaMalloc(&c->default_dloss, sizeof(float) * 8) != cudaSuccess ||
       cudaMalloc(&c->status, sizeof(int)) != cudaSuccess ||
       cudaMemcpy(c->default_dloss, dl, sizeof(dl), cudaMemcpyHostToDevice) != cudaSuccess ||
-      cudaMemset(c->status, 0, sizeof(int)) != cudaSuccess) {
+      cudaMemset(c->status, 0, sizeof(int)) != cudaSuccess ||
+      (cfg->store_activations &&
+       cudaMalloc(&c->store, c->store_bytes = (size_t)cfg->max_rays * N * kStoreFloatsPerSample * sizeof(float)) !=
+           cudaSuccess)) {
     gs_status s = cuda_fail(nullptr, "gs_create: workspace allocation");
     gs_destroy(c);
     return s;
@@ -113,6 +116,7 @@ void gs_destroy(gs_ctx* ctx) {
   cudaFree(ctx->mlp_part);
   cudaFree(ctx->default_dloss);
   cudaFree(ctx->status);
+  cudaFree(ctx->store);
   delete ctx;
 }
 
@@ -146,6 +150,10 @@ static gs_status render_common(gs_ctx* ctx, const char* who, const float* theta,
   if ((mode & 2) && !aligned16(grad)) return fail(ctx, GS_ERR_ALIGN, "grad is not 16-byte aligned");
   gs_status s = check_batch(ctx, batch, false);
   if (s != GS_OK) return s;
+  if (ctx->store && mode == 2 && batch->R > 0 &&
+      (ctx->store_R != batch->R || ctx->store_N != batch->N || ctx->store_t != batch->t))
+    return fail(ctx, GS_ERR_INVALID_ARG,
+                "store_activations: gs_backward needs a gs_forward of the same batch first (none, or another batch)");
   cudaStream_t st = (cudaStream_t)stream;
   ctx->last_stream = st;
   const float* dl = dloss ? dloss : ctx->default_dloss;
@@ -165,6 +173,11 @@ static gs_status render_common(gs_ctx* ctx, const char* who, const float* theta,
   }
   if (gs_launch_finalize(&tmp, batch, loss, grad, mode, st) != GS_OK) return cuda_fail(ctx, who);
   tmp.last_error.clear();
+  if (ctx->store && (mode & 1)) {
+    ctx->store_R = batch->R;
+    ctx->store_N = batch->N;
+    ctx->store_t = batch->t;
+  }
   return GS_OK;
 }
 
@@ -217,6 +230,20 @@ gs_status gs_query_sdf(gs_ctx* ctx, const float* theta, const float* x, int32_t 
   cudaStream_t st = (cudaStream_t)stream;
   ctx->last_stream = st;
   if (gs_launch_query(ctx, theta, x, P, sdf, grad, st) != GS_OK) return cuda_fail(ctx, "gs_query_sdf");
+  return GS_OK;
+}
+
+gs_status gs_query_sdf_backward(gs_ctx* ctx, const float* theta, const float* x, int32_t P, const float* dsdf,
+                                const float* dgrad, float* grad, void* stream) {
+  if (!ctx) return fail(nullptr, GS_ERR_INVALID_ARG, "gs_query_sdf_backward: ctx is NULL");
+  if (P < 0) return fail(ctx, GS_ERR_SHAPE, "gs_query_sdf_backward: P < 0");
+  if (P > 0 && (!theta || !x || !grad)) return fail(ctx, GS_ERR_INVALID_ARG, "gs_query_sdf_backward: NULL array");
+  if (P > 0 && (!aligned16(theta) || !aligned16(grad)))
+    return fail(ctx, GS_ERR_ALIGN, "gs_query_sdf_backward: theta or grad is not 16-byte aligned");
+  cudaStream_t st = (cudaStream_t)stream;
+  ctx->last_stream = st;
+  if (gs_launch_query_backward(ctx, theta, x, P, dsdf, dgrad, grad, st) != GS_OK)
+    return cuda_fail(ctx, "gs_query_sdf_backward");
   return GS_OK;
 }
 

@@ -11,6 +11,7 @@ constexpr int kMlpPad = 1688;     // per-CTA decoder-gradient partial row (>= GS
 constexpr int kLossPad = 8;       // per-CTA loss partial row
 constexpr int kSmoothCtas = 128;  // CTAs of the smoothness kernel (fixed, so partial rows are known)
 constexpr int kRenderCtasPerSm = 1;  // persistent render CTAs per SM
+constexpr int kStoreFloatsPerSample = 99;  // stored activations: z 16, a1 32, (phi, h) 16, a2 32, c 3
 constexpr int kRenderGroups = 3;     // tile groups (4 warps, 128 tensor-memory columns each) per render CTA
 
 struct gs_ctx {
@@ -24,6 +25,10 @@ struct gs_ctx {
   float* mlp_part = nullptr;
   float* default_dloss = nullptr;  // (0,0,0,0,0,1)
   int* status = nullptr;
+  float* store = nullptr;    // decoder activations kept by the forward pass (store_activations)
+  size_t store_bytes = 0;
+  int store_R = -1, store_N = -1;     // batch shape and depths pointer of the gs_forward that filled it
+  const float* store_t = nullptr;
   cudaStream_t last_stream = nullptr;
   std::string last_error;
 };
@@ -41,6 +46,8 @@ gs_status gs_launch_finalize(const gs_ctx* ctx, const gs_batch* b, float* loss, 
 gs_status gs_launch_adam(float* theta, float* grad, float* m, float* v, long long n, long long n_grid, int t,
                          float lr_grid, float lr_mlp, float b1, float b2, float eps, uint16_t* bf16, int num_sms,
                          cudaStream_t st);
+gs_status gs_launch_query_backward(const gs_ctx* ctx, const float* theta, const float* x, int P, const float* dsdf,
+                                   const float* dgrad, float* grad, cudaStream_t st);
 gs_status gs_launch_query(const gs_ctx* ctx, const float* theta, const float* x, int P, float* sdf, float* grad,
                           cudaStream_t st);
 gs_status gs_launch_voxel_index(const gs_ctx* ctx, const float* x, int P, long long* out, cudaStream_t st);

@@ -168,6 +168,8 @@ gs_status gs_launch_render(const gs_ctx* ctx, const float* theta, const uint16_t
   a.d_hat = d_hat;
   a.wsum = wsum;
   a.status = ctx->status;
+  a.store = ctx->store;
+  a.store_stride = (long long)ctx->cfg.max_rays * (ctx->cfg.n_strat + ctx->cfg.n_guided);
   const int nch = (b->N + 31) / 32;
   if (ctx->cfg.precision == GS_PREC_BF16) {
     switch (nch) {

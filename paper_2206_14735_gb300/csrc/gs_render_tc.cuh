@@ -365,6 +365,17 @@ __device__ __forceinline__ float pick_tc(const float (&arr)[N], int j) {
   return v;
 }
 
+template <int F0, int NF, int M>
+__device__ __forceinline__ void put_fields(float* sp, long long ss, const float (&v)[M]) {
+#pragma unroll
+  for (int k = 0; k < NF; ++k) sp[(F0 + k) * ss] = v[k];
+}
+template <int F0, int NF, int M>
+__device__ __forceinline__ void get_fields(const float* sp, long long ss, bool get, float (&v)[M]) {
+#pragma unroll
+  for (int k = 0; k < NF; ++k) v[k] = get ? __ldg(sp + (F0 + k) * ss) : 0.f;
+}
+
 struct RenderTcArgs {
   GridDesc g;
   const float* theta;
@@ -381,7 +392,16 @@ struct RenderTcArgs {
   float* mlp_part;
   float *rgb_hat, *d_hat, *wsum;
   int* status;      // device status word (bit 1: an MMA never completed)
+  // Stored activations (store mode): field f of sample s = rr * N + si at store[f * store_stride + s],
+  // one coalesced plane per field.  Written by every forward pass, read by every backward pass
+  // in place of the gather and the four recomputed decoder phases.  nullptr: recompute.
+  float* store;
+  long long store_stride;
 };
+
+// fields of one stored sample: z[16] | a1 = ReLU layer-1 output [32] | (phi, h[15]) | a2 [32] | c[3]
+constexpr int kFz = 0, kFa1 = 16, kFout = 48, kFa2 = 64, kFc = 96, kStoreFields = 99;
+static_assert(kStoreFields == kStoreFloatsPerSample, "the store holds every field");
 
 template <class P, int NCH, int GR, bool FWD, bool BWD>
 __global__ void __launch_bounds__(GR * kGroupThreads, 1) render_tc_kernel(RenderTcArgs a) {
@@ -486,6 +506,21 @@ __global__ void __launch_bounds__(GR * kGroupThreads, 1) render_tc_kernel(Render
       const int si = 32 * j + lane;
       const bool valid = has_ray && si < N;
       const float t = valid ? a.t[(size_t)rr * N + si] : 0.f;
+      float* sp = a.store != nullptr ? a.store + (size_t)rr * N + si : nullptr;  // this sample's field 0
+      const long long ss = a.store_stride;
+      if (!FWD && sp != nullptr) {  // stored by the forward pass: no decoder phases here
+#pragma unroll
+        for (int q = 0; q < NCH; ++q)
+          if (q == j) {
+            tt[q] = t;
+            ph[q] = valid ? sp[kFout * ss] : 0.f;
+            col[q][0] = valid ? sp[kFc * ss] : 0.f;
+            col[q][1] = valid ? sp[(kFc + 1) * ss] : 0.f;
+            col[q][2] = valid ? sp[(kFc + 2) * ss] : 0.f;
+          }
+        continue;
+      }
+      const bool put = FWD && sp != nullptr && valid;
       float z[kZ];
       if (valid) {
         float x[3];
@@ -497,6 +532,7 @@ __global__ void __launch_bounds__(GR * kGroupThreads, 1) render_tc_kernel(Render
       }
       store_row<P, 16>(G.a, row, z);
       mma_phase_issue<P, 32, 16>(G, cD1, wt0 + wOff<P>(0), wplane);
+      if (put) put_fields<kFz, 16>(sp, ss, z);
       if (!(alive = mma_phase_wait(G))) break;
       float v[32];
       tc::tmem_ld32(lane_addr(G, cD1, warp_g), v);
@@ -505,6 +541,7 @@ __global__ void __launch_bounds__(GR * kGroupThreads, 1) render_tc_kernel(Render
       for (int k = 0; k < 32; ++k) v[k] = fmaxf(v[k] + b1[k], 0.f);
       store_row<P, 32>(G.a, row, v);
       mma_phase_issue<P, 16, 32>(G, cD2, wt0 + wOff<P>(1), wplane);
+      if (put) put_fields<kFa1, 32>(sp, ss, v);
       if (!(alive = mma_phase_wait(G))) break;
       float u[16];
       tc::tmem_ld16(lane_addr(G, cD2, warp_g), u);
@@ -516,6 +553,10 @@ __global__ void __launch_bounds__(GR * kGroupThreads, 1) render_tc_kernel(Render
       h[15] = 0.f;
       store_row<P, 16>(G.a, row, h);
       mma_phase_issue<P, 32, 16>(G, cD3, wt0 + wOff<P>(2), wplane);
+      if (put) {
+        sp[kFout * ss] = phi;
+        put_fields<kFout + 1, 15>(sp, ss, h);
+      }
       if (!(alive = mma_phase_wait(G))) break;
       tc::tmem_ld32(lane_addr(G, cD3, warp_g), v);
       tc::tmem_ld_wait();
@@ -523,12 +564,14 @@ __global__ void __launch_bounds__(GR * kGroupThreads, 1) render_tc_kernel(Render
       for (int k = 0; k < 32; ++k) v[k] = fmaxf(v[k] + b3[k], 0.f);
       store_row<P, 32>(G.a, row, v);
       mma_phase_issue<P, 16, 32>(G, cX, wt0 + wOff<P>(3), wplane);
+      if (put) put_fields<kFa2, 32>(sp, ss, v);
       if (!(alive = mma_phase_wait(G))) break;
       tc::tmem_ld16(lane_addr(G, cX, warp_g), u);
       tc::tmem_ld_wait();
       float c3[3];
 #pragma unroll
       for (int k = 0; k < 3; ++k) c3[k] = sigmoidf_(u[k] + b4[k]);
+      if (put) put_fields<kFc, 3>(sp, ss, c3);
       // keep per-chunk values in registers (compile-time index via a selector loop)
 #pragma unroll
       for (int q = 0; q < NCH; ++q)
@@ -694,61 +737,64 @@ __global__ void __launch_bounds__(GR * kGroupThreads, 1) render_tc_kernel(Render
       const float t = pick_tc(tt, j);
       float x[3];
       sample_pos(o, r, t, x);
-      float z[kZ];
-      if (valid) {
-        gather_z<(P::planes == 1)>(a.g, a.theta, a.theta_bf16, x, z);
+      const float* sp = a.store != nullptr ? a.store + (size_t)rr * N + si : nullptr;
+      const long long ss = a.store_stride;
+      const bool get = sp != nullptr && valid;
+      float z[kZ], v[32], h[16], u[16], c3[3];
+      uint32_t mask2 = 0;
+      if (sp != nullptr) {  // stored activations: z, a2, h and c now, a1 where it is used
+        get_fields<kFz, 16>(sp, ss, get, z);
+        get_fields<kFa2, 32>(sp, ss, get, v);
+        get_fields<kFout + 1, 15>(sp, ss, get, h);
+        h[15] = 0.f;
+        get_fields<kFc, 3>(sp, ss, get, c3);
       } else {
+        if (valid) {
+          gather_z<(P::planes == 1)>(a.g, a.theta, a.theta_bf16, x, z);
+        } else {
 #pragma unroll
-        for (int k = 0; k < kZ; ++k) z[k] = 0.f;
+          for (int k = 0; k < kZ; ++k) z[k] = 0.f;
+        }
+        // recompute the decoders (the same four phases as the forward)
+        store_row<P, 16>(G.a, row, z);
+        mma_phase_issue<P, 32, 16>(G, cD1, wt0 + wOff<P>(0), wplane);
+        if (!(alive = mma_phase_wait(G))) break;
+        tc::tmem_ld32(lane_addr(G, cD1, warp_g), v);
+        tc::tmem_ld_wait();
+#pragma unroll
+        for (int k = 0; k < 32; ++k) v[k] = fmaxf(v[k] + b1[k], 0.f);
+        store_row<P, 32>(G.a, row, v);
+        mma_phase_issue<P, 16, 32>(G, cD2, wt0 + wOff<P>(1), wplane);
+        if (!(alive = mma_phase_wait(G))) break;
+        tc::tmem_ld16(lane_addr(G, cD2, warp_g), u);
+        tc::tmem_ld_wait();
+#pragma unroll
+        for (int k = 0; k < 15; ++k) h[k] = u[k + 1] + b2[k + 1];
+        h[15] = 0.f;
+        store_row<P, 16>(G.a, row, h);
+        mma_phase_issue<P, 32, 16>(G, cD3, wt0 + wOff<P>(2), wplane);
+        if (!(alive = mma_phase_wait(G))) break;
+        tc::tmem_ld32(lane_addr(G, cD3, warp_g), v);
+        tc::tmem_ld_wait();
+#pragma unroll
+        for (int k = 0; k < 32; ++k) v[k] = fmaxf(v[k] + b3[k], 0.f);
+        store_row<P, 32>(G.a, row, v);
+        mma_phase_issue<P, 16, 32>(G, cX, wt0 + wOff<P>(3), wplane);
+        if (!(alive = mma_phase_wait(G))) break;
+        tc::tmem_ld16(lane_addr(G, cX, warp_g), u);
+        tc::tmem_ld_wait();
+#pragma unroll
+        for (int k = 0; k < 3; ++k) c3[k] = sigmoidf_(u[k] + b4[k]);
       }
-      // recompute the decoders (the same four phases as the forward)
-      store_row<P, 16>(G.a, row, z);
-      mma_phase_issue<P, 32, 16>(G, cD1, wt0 + wOff<P>(0), wplane);
-      if (!(alive = mma_phase_wait(G))) break;
-      float v[32];
-      uint32_t mask1 = 0, mask2 = 0;
-      tc::tmem_ld32(lane_addr(G, cD1, warp_g), v);
-      tc::tmem_ld_wait();
 #pragma unroll
-      for (int k = 0; k < 32; ++k) {
-        v[k] = fmaxf(v[k] + b1[k], 0.f);
-        mask1 |= (v[k] > 0.f ? 1u : 0u) << k;
-      }
-      store_row<P, 32>(G.a, row, v);
-      mma_phase_issue<P, 16, 32>(G, cD2, wt0 + wOff<P>(1), wplane);
-      if (!(alive = mma_phase_wait(G))) break;
-      float u[16];
-      tc::tmem_ld16(lane_addr(G, cD2, warp_g), u);
-      tc::tmem_ld_wait();
-      float h[16];
-#pragma unroll
-      for (int k = 0; k < 15; ++k) h[k] = u[k + 1] + b2[k + 1];
-      h[15] = 0.f;
-      store_row<P, 16>(G.a, row, h);
-      mma_phase_issue<P, 32, 16>(G, cD3, wt0 + wOff<P>(2), wplane);
-      if (!(alive = mma_phase_wait(G))) break;
-      tc::tmem_ld32(lane_addr(G, cD3, warp_g), v);
-      tc::tmem_ld_wait();
-#pragma unroll
-      for (int k = 0; k < 32; ++k) {
-        v[k] = fmaxf(v[k] + b3[k], 0.f);
-        mask2 |= (v[k] > 0.f ? 1u : 0u) << k;
-      }
-      store_row<P, 32>(G.a, row, v);
-      mma_phase_issue<P, 16, 32>(G, cX, wt0 + wOff<P>(3), wplane);
-      if (!(alive = mma_phase_wait(G))) break;
-      tc::tmem_ld16(lane_addr(G, cX, warp_g), u);
-      tc::tmem_ld_wait();
+      for (int k = 0; k < 32; ++k) mask2 |= (v[k] > 0.f ? 1u : 0u) << k;
       // colour output adjoint: dpre = w gc c (1 - c)
       const float wj = pick_tc(w, j);
       float dp[kKD];
 #pragma unroll
       for (int k = 0; k < kKD; ++k) dp[k] = 0.f;
 #pragma unroll
-      for (int k = 0; k < 3; ++k) {
-        const float c = sigmoidf_(u[k] + b4[k]);
-        dp[k] = valid ? wj * gc[k] * c * (1.0f - c) : 0.f;
-      }
+      for (int k = 0; k < 3; ++k) dp[k] = valid ? wj * gc[k] * c3[k] * (1.0f - c3[k]) : 0.f;
       store_row<P, kKD>(G.a, row, dp);
       // --- b4: da2 = dpre W4  (overlap: dW4, db4 from dpre and a2) ---
       mma_phase_issue<P, 32, kKD>(G, cX, wt0 + wOff<P>(4), wplane);
@@ -792,12 +838,19 @@ __global__ void __launch_bounds__(GR * kGroupThreads, 1) render_tc_kernel(Render
       store_row<P, 16>(G.a, row, dout);
       // --- b2: da1 = dout W2  (overlap: dW2, db2 from dout and a1) ---
       mma_phase_issue<P, 32, 16>(G, cX, wt0 + wOff<P>(6), wplane);
+      uint32_t mask1 = 0;
       {
         float a1[32];
-        tc::tmem_ld32(lane_addr(G, cD1, warp_g), a1);
-        tc::tmem_ld_wait();
+        if (sp != nullptr) {
+          get_fields<kFa1, 32>(sp, ss, get, a1);
+        } else {
+          tc::tmem_ld32(lane_addr(G, cD1, warp_g), a1);
+          tc::tmem_ld_wait();
 #pragma unroll
-        for (int k = 0; k < 32; ++k) a1[k] = fmaxf(a1[k] + b1[k], 0.f);
+          for (int k = 0; k < 32; ++k) a1[k] = fmaxf(a1[k] + b1[k], 0.f);
+        }
+#pragma unroll
+        for (int k = 0; k < 32; ++k) mask1 |= (a1[k] > 0.f ? 1u : 0u) << k;
         warp_weight_grad<16, 32, 16, 32>(stage, lane, dout, a1, macc, oW2, kH1, kH1, ob2, 16);  // dW2, db2
       }
       if (!(alive = mma_phase_wait(G))) break;

@@ -462,6 +462,79 @@ def test_gradients_match_central_differences_h1e3(tiny_problem):
 
 
 # ----------------------------------------------------------------------------------------
+# SDF query backward (phi and grad_x phi as differentiable outputs, Supp. Sec. 1)
+# ----------------------------------------------------------------------------------------
+def _query_objective(cfg, th, x, dsdf, dgrad):
+    phi, g = oc.query_sdf(cfg, th, x)
+    return float(np.dot(dsdf, phi) + np.sum(dgrad * g))
+
+
+@pytest.mark.parametrize("h,tol", [(1e-6, 1e-6), (1e-3, 1e-4)])
+def test_query_sdf_backward_matches_central_differences(tiny_problem, h, tol):
+    cfg, _, _, th = tiny_problem
+    _, n_grid, n_tot = TINY.layout()
+    rng = np.random.default_rng(4)
+    x = rng.uniform(-1.2, 1.2, (40, 3)).astype(np.float32)
+    dsdf, dgrad = rng.normal(size=40), rng.normal(size=(40, 3))
+    g = oc.query_sdf_backward(cfg, th, x, dsdf, dgrad)
+    touched = np.nonzero(g[:n_grid])[0]
+    assert len(touched) > 100
+    idx = np.r_[touched[::2], np.arange(n_grid, n_tot)]
+    fd = np.empty(len(idx))
+    for j, i in enumerate(idx):
+        xp, xm = th.copy(), th.copy()
+        xp[i] += h
+        xm[i] -= h
+        fd[j] = (_query_objective(cfg, xp, x, dsdf, dgrad) - _query_objective(cfg, xm, x, dsdf, dgrad)) / (2 * h)
+    err = np.abs(fd - g[idx]) / np.abs(g[idx]).max()
+    # at h = 1e-3 a ReLU unit of some point may switch inside [theta - h, theta + h]
+    assert (np.median(err) < tol and np.mean(err < tol) > 0.98) if h > 1e-5 else err.max() < tol, err.max()
+
+
+def test_query_sdf_backward_terms_separate_and_add(tiny_problem):
+    """The two upstream seeds act linearly and independently; kappa and the colour decoder
+    get no gradient from an SDF query."""
+    cfg, _, _, th = tiny_problem
+    _, n_grid, n_tot = TINY.layout()
+    rng = np.random.default_rng(5)
+    x = rng.uniform(-1.0, 1.0, (16, 3)).astype(np.float32)
+    ds, dg = rng.normal(size=16), rng.normal(size=(16, 3))
+    g1 = oc.query_sdf_backward(cfg, th, x, ds, None)
+    g2 = oc.query_sdf_backward(cfg, th, x, None, dg)
+    g12 = oc.query_sdf_backward(cfg, th, x, 2 * ds, -dg)
+    np.testing.assert_allclose(g12, 2 * g1 - g2, rtol=1e-12, atol=1e-14)
+    offs = dict(zip([n for n, _ in sg.MLP_SHAPES], np.cumsum([0] + [int(np.prod(s)) for _, s in sg.MLP_SHAPES])))
+    colour = slice(n_grid + offs["W3"], n_tot)
+    assert not np.any(g1[colour]) and not np.any(g2[colour])
+    # d phi / d b2 = (1, 0, ..., 0): the SDF seeds sum into b2[0]
+    assert abs(g1[n_grid + offs["b2"]] - ds.sum()) < 1e-12
+
+
+def test_query_sdf_backward_affine_field_closed_form():
+    """phi = z_k (pass-through decoder) on an affine field: grad_x phi = c is constant and
+    a . grad_x phi is linear in the level's vertex values, with d/d theta_v = a . d w_v / d x
+    summed over the points; its total over the vertices is 0 (the weights' gradients
+    sum to zero in every cell)."""
+    th = zero_params(CUBE)
+    set_level_field(CUBE, th, 2, 1, lambda X: X @ np.array([0.3, -0.7, 0.2]) + 0.1)
+    passthrough_decoder(CUBE, th, 9)
+    cfg = oc.make_config(CUBE)
+    rng = np.random.default_rng(6)
+    x = rng.uniform(-0.9, 0.9, (12, 3)).astype(np.float32)
+    a = rng.normal(size=(12, 3))
+    g = oc.query_sdf_backward(cfg, th, x, None, a)
+    offs, n_grid, _ = CUBE.layout()
+    n2 = int(np.prod(CUBE.dims[2])) * 4
+    lvl = g[offs[2]:offs[2] + n2].reshape(-1, 4)
+    assert np.abs(lvl[:, 1]).max() > 0
+    assert abs(lvl[:, 1].sum()) < 1e-9 * np.abs(lvl[:, 1]).max() * len(x)
+    # and the SDF seed alone puts the trilinear weights (summing to 1 per point) on feature 1
+    g1 = oc.query_sdf_backward(cfg, th, x, np.ones(12), None)
+    lv1 = g1[offs[2]:offs[2] + n2].reshape(-1, 4)
+    assert abs(lv1[:, 1].sum() - 12.0) < 1e-9
+
+
+# ----------------------------------------------------------------------------------------
 # Adam (Kingma & Ba 2015) with the paper's per-group learning rates
 # ----------------------------------------------------------------------------------------
 def test_adam_first_two_steps_closed_form():
