@@ -76,7 +76,13 @@ def lib():
             L.oc_sample_smooth.restype = None
             L.oc_sample_smooth.argtypes = [vp, vp, u64, u32, i32, vp, vp, vp, vp]
             L.oc_step.restype = i32
-            L.oc_step.argtypes = [vp, vp, i32, i32] + [vp] * 6 + [i32] + [vp] * 11
+            L.oc_step.argtypes = [vp, vp, i32, i32] + [vp] * 6 + [i32] + [vp] * 12
+            L.oc_prop_forward.restype = None
+            L.oc_prop_forward.argtypes = [vp, vp, vp, i32, vp, vp, vp]
+            L.oc_prop_ce.restype = dbl
+            L.oc_prop_ce.argtypes = [vp, vp, vp, i32, i32, vp, vp, vp, vp, vp, vp]
+            L.oc_prop_sample.restype = None
+            L.oc_prop_sample.argtypes = [vp, i32, i32, i32, vp, vp, ctypes.c_uint64, ctypes.c_uint32, vp, vp, vp]
             L.oc_query_sdf.restype = None
             L.oc_query_sdf.argtypes = [vp, vp, vp, i32, vp, vp]
             L.oc_query_sdf_backward.restype = None
@@ -159,7 +165,8 @@ def sample_smooth(cfg: OcConfig, frames: OcFramesHolder, seed: int, step: int, P
     return out
 
 
-def step(cfg: OcConfig, theta, batch: dict, smooth: dict | None, dloss=None, want_grad=True, want_margins=False):
+def step(cfg: OcConfig, theta, batch: dict, smooth: dict | None, dloss=None, want_grad=True, want_margins=False,
+         want_weights=False):
     """Losses (and gradients) of one step.  theta: flat parameters (promoted to FP64)."""
     th = np.ascontiguousarray(theta, dtype=np.float64)
     R, N = batch["t"].shape
@@ -176,12 +183,57 @@ def step(cfg: OcConfig, theta, batch: dict, smooth: dict | None, dloss=None, wan
     margins = np.zeros(10) if want_margins else None
     amb = np.zeros((R, N), np.uint8) if want_margins else None
     dl = None if dloss is None else np.ascontiguousarray(dloss, dtype=np.float64)
+    w = np.zeros((R, N)) if want_weights else None
     rc = lib().oc_step(ctypes.byref(cfg), _p(th), R, N, _p(batch["o"]), _p(batch["r"]), _p(batch["rgb"]),
                        _p(batch["D"]), _p(batch["t"]), _p(batch["cls"]), P, _p(xs), _p(eps), _p(valid), _p(dl),
-                       _p(loss), _p(rgb_hat), _p(d_hat), _p(wsum), _p(grad), _p(margins), _p(amb))
+                       _p(loss), _p(rgb_hat), _p(d_hat), _p(wsum), _p(grad), _p(margins), _p(amb), _p(w))
     if rc != 0:
         raise ValueError("oc_step rejected its arguments")
-    return dict(loss=loss, rgb_hat=rgb_hat, d_hat=d_hat, wsum=wsum, grad=grad, margins=margins, amb=amb)
+    return dict(loss=loss, rgb_hat=rgb_hat, d_hat=d_hat, wsum=wsum, grad=grad, margins=margins, amb=amb, w=w)
+
+
+# ---- learned proposal sampler (a sample-count reduction; not part of the paper) ----
+PROP_BINS = 32
+PROP_PARAMS = 32 * 11 + 32 + 32 * 32 + 32 + 32 + 1  # 1473
+
+
+def prop_forward(cfg: OcConfig, theta, q, o, r) -> np.ndarray:
+    """Proposal distribution p [R][32] (FP64)."""
+    th = np.ascontiguousarray(theta, dtype=np.float64)
+    qq = np.ascontiguousarray(q, dtype=np.float64)
+    o = np.ascontiguousarray(o, dtype=np.float32).reshape(-1, 3)
+    r = np.ascontiguousarray(r, dtype=np.float32).reshape(-1, 3)
+    p = np.empty((len(o), PROP_BINS))
+    lib().oc_prop_forward(ctypes.byref(cfg), _p(th), _p(qq), len(o), _p(o), _p(r), _p(p))
+    return p
+
+
+def prop_ce(cfg: OcConfig, theta, q, o, r, t, w, want_grad=True):
+    """Cross-entropy training loss of the proposal against the binned weights w [R][N]
+    at depths t [R][N]; returns (loss, gradient w.r.t. q or None, rays used)."""
+    th = np.ascontiguousarray(theta, dtype=np.float64)
+    qq = np.ascontiguousarray(q, dtype=np.float64)
+    o = np.ascontiguousarray(o, dtype=np.float32).reshape(-1, 3)
+    r = np.ascontiguousarray(r, dtype=np.float32).reshape(-1, 3)
+    t = np.ascontiguousarray(t, dtype=np.float32)
+    w = np.ascontiguousarray(w, dtype=np.float64)
+    R, N = t.shape
+    g = np.zeros(PROP_PARAMS) if want_grad else None
+    n = np.zeros(1, np.int64)
+    ce = lib().oc_prop_ce(ctypes.byref(cfg), _p(th), _p(qq), R, N, _p(o), _p(r), _p(t), _p(w), _p(g), _p(n))
+    return ce, g, int(n[0])
+
+
+def prop_sample(cfg: OcConfig, D, p, N: int, n_guided: int, seed: int, step: int) -> dict:
+    """Depths drawn from the proposal p [R][32] (binary32, bit-exact), sorted, with classes."""
+    D = np.ascontiguousarray(D, dtype=np.float32)
+    p = np.ascontiguousarray(p, dtype=np.float32)
+    R = len(D)
+    t = np.empty((R, N), np.float32)
+    cls = np.empty((R, N), np.uint8)
+    counts = np.zeros(4, np.int64)
+    lib().oc_prop_sample(ctypes.byref(cfg), R, N, n_guided, _p(D), _p(p), seed, step, _p(t), _p(cls), _p(counts))
+    return dict(t=t, cls=cls, counts=counts)
 
 
 def query_sdf(cfg: OcConfig, theta, x, want_grad=True):

@@ -655,13 +655,13 @@ static void mmin(double* a, double v) {
  * rounding of a tie: bit 0 the alpha_k > 0 decision (|q_k| < 1e-5, unsaturated, untied),
  * bit 1 the sign of phi - b on S_tr (|phi - b| < 2e-5), bit 2 the free-space max (gap < 2e-5).
  * Bit 0 is set only when gradients are requested and a flip would change dL/dphi by more
- * than 1e-7.
+ * than 1e-7.  w_out [R,N] (may be NULL) receives the rendering weights w_i = T_i alpha_i.
  * Returns 0, or -1 on a bad argument.
  */
 int oc_step(const oc_config* c, const double* theta, int R, int N, const float* o, const float* r,
             const float* rgb, const float* D, const float* t, const uint8_t* cls, int P, const float* xs,
             const float* eps, const uint8_t* valid, const double* dloss, double* loss, double* rgb_hat,
-            double* d_hat, double* wsum, double* grad, double* margins, uint8_t* amb) {
+            double* d_hat, double* wsum, double* grad, double* margins, uint8_t* amb, double* w_out) {
   if (R < 0 || N < 2 || P < 0) return -1;
   const int64_t ng = grid_size(c);
   mlp_t m = mlp_view(theta + ng);
@@ -754,6 +754,8 @@ int oc_step(const oc_config* c, const double* theta, int R, int N, const float* 
         for (int j = 0; j < 3; ++j) rgb_hat[3 * i + j] = ch[j];
       if (d_hat) d_hat[i] = dh;
       if (wsum) wsum[i] = ws;
+      if (w_out)
+        for (int k = 0; k < N; ++k) w_out[(size_t)i * N + k] = w[k];
       /* rendering losses */
       double lr = 0;
       for (int j = 0; j < 3; ++j) {
@@ -994,6 +996,221 @@ int oc_step(const oc_config* c, const double* theta, int R, int N, const float* 
   free(dz_all);
   free(dzs_all);
   return 0;
+}
+
+/* ------------------------------------------------------------------------------------ */
+/* learned proposal sampler (not part of the paper: a sample-count reduction trained       */
+/* online on the main model's rendering weights)                                         */
+/* ------------------------------------------------------------------------------------ */
+/* The interval [near, far] is cut into OC_PB equal bins.  For every bin centre x_b the
+ * network reads the two coarsest grid levels' features z_0(x_b), z_1(x_b) and the unit ray
+ * direction, u = [z_0, z_1, r/|r|] (11 values), and returns one logit:
+ *   l_b = w3 . relu(W2 relu(W1 u + b1) + b2) + b3,    p = softmax_b(l).
+ * Parameters (OC_PROP floats): W1[32][11], b1[32], W2[32][32], b2[32], w3[32], b3. */
+#define OC_PB 32
+#define OC_PIN 11
+#define OC_PH 32
+#define OC_PROP (OC_PH * OC_PIN + OC_PH + OC_PH * OC_PH + OC_PH + OC_PH + 1) /* 1473 */
+
+typedef struct {
+  double u[OC_PIN], y1[OC_PH], a1[OC_PH], y2[OC_PH], a2[OC_PH], logit;
+} prop_act_t;
+
+/* binary32 bin geometry: width and left edge of bin b */
+static float prop_width(const oc_config* c) { return (c->far_m - c->near_m) / (float)OC_PB; }
+static float prop_edge(const oc_config* c, int b) { return c->near_m + (float)b * prop_width(c); }
+
+static void prop_eval(const oc_config* c, const double* theta, const double* q, const float o[3], const float r[3],
+                      int b, prop_act_t* A) {
+  const double *W1 = q, *b1 = W1 + OC_PH * OC_PIN, *W2 = b1 + OC_PH, *b2 = W2 + OC_PH * OC_PH, *w3 = b2 + OC_PH,
+               *b3 = w3 + OC_PH;
+  const float tc = c->near_m + ((float)b + 0.5f) * prop_width(c); /* bin centre (binary32) */
+  float x[3];
+  for (int a = 0; a < 3; ++a) {
+    float step_ = tc * r[a];
+    x[a] = o[a] + step_;
+  }
+  cell_t cells[OC_LEVELS];
+  double z[OC_Z];
+  features(c, theta, x, cells, z, NULL);
+  for (int k = 0; k < 8; ++k) A->u[k] = z[k]; /* levels 0 and 1 */
+  const double n = sqrt((double)r[0] * r[0] + (double)r[1] * r[1] + (double)r[2] * r[2]);
+  for (int a = 0; a < 3; ++a) A->u[8 + a] = (double)r[a] / n;
+  for (int j = 0; j < OC_PH; ++j) {
+    double s = b1[j];
+    for (int k = 0; k < OC_PIN; ++k) s += W1[j * OC_PIN + k] * A->u[k];
+    A->y1[j] = s;
+    A->a1[j] = s > 0 ? s : 0;
+  }
+  for (int j = 0; j < OC_PH; ++j) {
+    double s = b2[j];
+    for (int k = 0; k < OC_PH; ++k) s += W2[j * OC_PH + k] * A->a1[k];
+    A->y2[j] = s;
+    A->a2[j] = s > 0 ? s : 0;
+  }
+  double l = b3[0];
+  for (int k = 0; k < OC_PH; ++k) l += w3[k] * A->a2[k];
+  A->logit = l;
+}
+
+/* p [R][OC_PB]: the proposal distribution of every ray (FP64) */
+void oc_prop_forward(const oc_config* c, const double* theta, const double* q, int R, const float* o, const float* r,
+                     double* p) {
+#pragma omp parallel for schedule(static)
+  for (int i = 0; i < R; ++i) {
+    prop_act_t A;
+    double l[OC_PB], mx = -INFINITY, s = 0;
+    for (int b = 0; b < OC_PB; ++b) {
+      prop_eval(c, theta, q, o + 3 * i, r + 3 * i, b, &A);
+      l[b] = A.logit;
+      if (l[b] > mx) mx = l[b];
+    }
+    for (int b = 0; b < OC_PB; ++b) s += exp(l[b] - mx);
+    for (int b = 0; b < OC_PB; ++b) p[(size_t)i * OC_PB + b] = exp(l[b] - mx) / s;
+  }
+}
+
+/* bin of a sample depth (binary32 decision), clamped to [0, OC_PB) */
+static int prop_bin(const oc_config* c, float t) {
+  float f = (t - c->near_m) / prop_width(c);
+  int b = (int)floorf(f);
+  return b < 0 ? 0 : (b >= OC_PB ? OC_PB - 1 : b);
+}
+
+/*
+ * Training loss of the proposal: for every ray, the main model's weights w [R][N] at its
+ * samples t [R][N] are summed per bin, h_b = sum_{t_i in bin b} w_i, and normalised,
+ * hh = h / sum(h); rays with sum(h) < 1e-3 are skipped.  The loss is the mean over the used
+ * rays of the cross entropy -sum_b hh_b log p_b; the target is a constant (no gradient
+ * reaches the main model or the grid).  Returns the loss; gq (+=, may be NULL) receives
+ * its gradient with respect to the proposal parameters, d/d l_b = (p_b - hh_b) / n_used.
+ */
+double oc_prop_ce(const oc_config* c, const double* theta, const double* q, int R, int N, const float* o,
+                  const float* r, const float* t, const double* w, double* gq, int64_t* n_used_out) {
+  int64_t n_used = 0;
+  double ce = 0;
+  double* gtmp = (double*)calloc(OC_PROP, sizeof(double));
+  const double *W2 = q + OC_PH * OC_PIN + OC_PH, *w3 = W2 + OC_PH * OC_PH + OC_PH;
+  for (int i = 0; i < R; ++i) {
+    double h[OC_PB] = {0}, S = 0;
+    for (int k = 0; k < N; ++k) h[prop_bin(c, t[(size_t)i * N + k])] += w[(size_t)i * N + k];
+    for (int b = 0; b < OC_PB; ++b) S += h[b];
+    if (!(S >= 1e-3)) continue;
+    ++n_used;
+    prop_act_t A[OC_PB];
+    double mx = -INFINITY, se = 0;
+    for (int b = 0; b < OC_PB; ++b) {
+      prop_eval(c, theta, q, o + 3 * i, r + 3 * i, b, &A[b]);
+      if (A[b].logit > mx) mx = A[b].logit;
+    }
+    for (int b = 0; b < OC_PB; ++b) se += exp(A[b].logit - mx);
+    const double lse = mx + log(se);
+    for (int b = 0; b < OC_PB; ++b) {
+      const double hh = h[b] / S, pb = exp(A[b].logit - lse);
+      ce -= hh * (A[b].logit - lse);
+      /* reverse mode through the bin's network, seed dl = p_b - hh_b (scaled later) */
+      const double dl = pb - hh;
+      double* gW1 = gtmp;
+      double* gb1 = gW1 + OC_PH * OC_PIN;
+      double* gW2 = gb1 + OC_PH;
+      double* gb2 = gW2 + OC_PH * OC_PH;
+      double* gw3 = gb2 + OC_PH;
+      double* gb3 = gw3 + OC_PH;
+      double dy2[OC_PH], dy1[OC_PH];
+      gb3[0] += dl;
+      for (int k = 0; k < OC_PH; ++k) {
+        gw3[k] += dl * A[b].a2[k];
+        dy2[k] = A[b].y2[k] > 0 ? dl * w3[k] : 0.0;
+      }
+      for (int j = 0; j < OC_PH; ++j) {
+        gb2[j] += dy2[j];
+        for (int k = 0; k < OC_PH; ++k) gW2[j * OC_PH + k] += dy2[j] * A[b].a1[k];
+      }
+      for (int k = 0; k < OC_PH; ++k) {
+        double s = 0;
+        for (int j = 0; j < OC_PH; ++j) s += W2[j * OC_PH + k] * dy2[j];
+        dy1[k] = A[b].y1[k] > 0 ? s : 0.0;
+      }
+      for (int j = 0; j < OC_PH; ++j) {
+        gb1[j] += dy1[j];
+        for (int k = 0; k < OC_PIN; ++k) gW1[j * OC_PIN + k] += dy1[j] * A[b].u[k];
+      }
+    }
+  }
+  if (gq && n_used > 0)
+    for (int k = 0; k < OC_PROP; ++k) gq[k] += gtmp[k] / (double)n_used;
+  free(gtmp);
+  if (n_used_out) *n_used_out = n_used;
+  return n_used > 0 ? ce / (double)n_used : 0.0;
+}
+
+static int cmp_float(const void* a, const void* b) {
+  float x = *(const float*)a, y = *(const float*)b;
+  return (x > y) - (x < y);
+}
+
+/*
+ * Sample depths from the proposal (binary32, bit-exact given p): the mixture
+ * pp = 0.95 p + 0.05 / OC_PB keeps every bin reachable; its running sums C_b (added in bin
+ * order) form the inverse CDF.  K = N - n_guided stratified draws u_k = (k + xi_k) / K
+ * (K = N when D <= 0: no depth to guide) land at target = u_k C_{last}; the bin is the
+ * first with C_b > target and the depth is placed linearly inside it.  When D > 0 the
+ * n_guided samples are stratified over [D - g, D + g] as in the plain sampler.  The N
+ * depths are sorted ascending and classified like the plain sampler's.  Random numbers:
+ * stream 2, slot 1 + k for draw k (the rays themselves are the plain sampler's).
+ * p [R][OC_PB] binary32; t [R][N], cls [R][N]; counts[3] = (rays with D>0, |S_tr|, |S_fs|).
+ */
+void oc_prop_sample(const oc_config* c, int R, int N, int n_guided, const float* D, const float* p, uint64_t seed,
+                    uint32_t step, float* t, uint8_t* cls, int64_t* counts) {
+  const float width = prop_width(c);
+  const float mixw = 0.05f / (float)OC_PB;
+  int64_t nd = 0, ntr = 0, nfs = 0;
+  for (int i = 0; i < R; ++i) {
+    float pp[OC_PB], C[OC_PB], acc = 0.0f;
+    for (int b = 0; b < OC_PB; ++b) {
+      pp[b] = 0.95f * p[(size_t)i * OC_PB + b] + mixw;
+      acc = acc + pp[b];
+      C[b] = acc;
+    }
+    const float total = C[OC_PB - 1];
+    const float Di = D[i];
+    const int ng = (Di > 0.0f) ? n_guided : 0;
+    const int K = N - ng;
+    float* ti = t + (size_t)i * N;
+    for (int k = 0; k < K; ++k) {
+      float u = unif24(oc_draw(seed, 2, step, (uint64_t)i, 1 + (uint64_t)k));
+      float target = (((float)k + u) / (float)K) * total;
+      int b = 0;
+      while (b < OC_PB && C[b] <= target) ++b;
+      if (b > OC_PB - 1) b = OC_PB - 1;
+      float lo = b > 0 ? C[b - 1] : 0.0f;
+      float e0 = prop_edge(c, b), e1 = prop_edge(c, b + 1);
+      float x = e0 + ((target - lo) / pp[b]) * width;
+      ti[k] = x < e0 ? e0 : (x > e1 ? e1 : x);
+    }
+    if (ng > 0) {
+      ++nd;
+      float g = c->guide_half;
+      float gstep = (2.0f * g) / (float)ng;
+      float g0 = Di - g;
+      for (int j = 0; j < ng; ++j) {
+        float u = unif24(oc_draw(seed, 2, step, (uint64_t)i, 1 + (uint64_t)K + (uint64_t)j));
+        ti[K + j] = g0 + ((float)j + u) * gstep;
+      }
+    } else if (Di > 0.0f) {
+      ++nd;
+    }
+    qsort(ti, (size_t)N, sizeof(float), cmp_float);
+    for (int k = 0; k < N; ++k) {
+      int cl = sample_class(Di, ti[k], c->trunc);
+      cls[(size_t)i * N + k] = (uint8_t)cl;
+      ntr += cl == CLS_TR;
+      nfs += cl == CLS_FS;
+    }
+  }
+  counts[0] = nd;
+  counts[1] = ntr;
+  counts[2] = nfs;
 }
 
 /* ------------------------------------------------------------------------------------ */
