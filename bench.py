@@ -95,7 +95,7 @@ def run_ours(args):
     t0 = time.time()
     fr = sg.make_frames(w, n_frames=args.frames)
     t_frames = time.time() - t0
-    ctx = gs.Context(w, store_activations=args.store)
+    ctx = gs.Context(w, store_activations=not args.recompute)
     dfr = gs.DeviceFrames(fr.rgb, fr.depth, fr.c2w, fr.fx, fr.fy, fr.cx, fr.cy)
     theta = torch.from_numpy(sg.init_params(w)).cuda()
     grad, m, v = torch.zeros_like(theta), torch.zeros_like(theta), torch.zeros_like(theta)
@@ -114,7 +114,11 @@ def run_ours(args):
         ctx.sample_rays(dfr, seed, k, batch)
         if ev is not None:
             ev[1].record(stream)
-        ctx.forward_backward(theta, batch, None, loss, grad, theta_bf16=mirror)
+        if args.split:
+            ctx.forward(theta, batch, loss, theta_bf16=mirror)
+            ctx.backward(theta, batch, None, grad, theta_bf16=mirror)
+        else:
+            ctx.forward_backward(theta, batch, None, loss, grad, theta_bf16=mirror)
         if ev is not None:
             ev[2].record(stream)
         ctx.adam_step(theta, grad, m, v, k + 1, w.lr_grid, w.lr_mlp, b1, b2, w.adam_eps, theta_bf16=mirror)
@@ -163,7 +167,11 @@ def run_ours(args):
     for k in range(e2e_steps):
         dl_dev.copy_(dl_host, non_blocking=True)
         ctx.sample_rays(dfr, seed, base + k, batch)
-        ctx.forward_backward(theta, batch, dl_dev, loss, grad, theta_bf16=mirror)
+        if args.split:
+            ctx.forward(theta, batch, loss, theta_bf16=mirror)
+            ctx.backward(theta, batch, dl_dev, grad, theta_bf16=mirror)
+        else:
+            ctx.forward_backward(theta, batch, dl_dev, loss, grad, theta_bf16=mirror)
         ctx.adam_step(theta, grad, m, v, base + k + 1, w.lr_grid, w.lr_mlp, b1, b2, w.adam_eps, theta_bf16=mirror)
         out_host.copy_(loss, non_blocking=True)
         cnt_host.copy_(batch.counts, non_blocking=True)
@@ -199,7 +207,8 @@ def run_ours(args):
                    "samples_per_s": round(value * w.n_samples, 1), "smooth_points": w.n_smooth,
                    "params": w.layout()[2], "grid_params": n_grid, "frames": fr.depth.shape[0],
                    "resolution": [w.width, w.height], "parallelism": f"replicas{world}",
-                   "activations": "stored" if args.store else "recomputed",
+                   "activations": "recomputed" if args.recompute else "stored (396 B/sample)",
+                   "calls": "gs_forward + gs_backward" if args.split else "gs_forward_backward",
                    "l2": "inputs larger than L2: 1.2 GB of parameter/gradient/moment state streamed per step",
                    "frame_render_s": round(t_frames, 1)},
         "kernels_ms": {k: round(vv, 4) for k, vv in avg.items()},
@@ -214,7 +223,7 @@ def run_ours(args):
                 "h2d_bytes_per_step": 24, "d2h_bytes_per_step": 40, "steps": e2e_steps,
                 "what": "per step: H2D dloss seed (pinned), the three C-ABI calls, D2H loss and counts, host sync; "
                         "frames resident on the device"},
-        "gpu_launches": 6 * args.steps,
+        "gpu_launches": (9 if args.split else 6) * args.steps,
         "clocks": clk,
         "loss_last": [round(x, 6) for x in lossv],
     }
@@ -222,6 +231,158 @@ def run_ours(args):
         line["differentiation"] = differentiation_report(w, dfr, theta, mirror)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(w, fr, args.cpu_rays)
+    return line
+
+
+def _eval_depth(ctx, w, dfr, gt, theta, sampler, q=None, R=65536, seed=99):
+    """Rendered depth of R fresh rays against the noise-free depth: mean |d_hat - D_gt| over
+    rays with D_gt > 0, and over those whose observed depth was dropped (D = 0)."""
+    import numpy as np
+    import torch
+
+    import paper_2206_14735_gb300 as gs
+    R = min(R, w.rays)
+    if sampler == "plain":
+        b = gs.Batch.allocate(R, w.n_samples, 0)
+        ctx.sample_rays(dfr, seed, 0, b)
+    else:
+        b = gs.Batch.allocate(R, w.prop_samples, 0)
+        ctx.proposal_sample(dfr, seed, 0, b, theta=theta, prop=q)
+    loss = torch.empty(6, device="cuda")
+    dh = torch.empty(R, device="cuda")
+    ctx.forward(theta, b, loss, d_hat=dh)
+    d_hat = dh.cpu().numpy().astype(np.float64)
+    pix = b.pix.cpu().numpy()
+    D = b.depth.cpu().numpy()
+    g = gt.reshape(-1)[pix].astype(np.float64)
+    ok = g > 0
+    drop = ok & (D <= 0)
+    return {"depth_l1_gt_m": round(float(np.abs(d_hat - g)[ok].mean()), 5),
+            "depth_l1_gt_dropped_m": round(float(np.abs(d_hat - g)[drop].mean()), 5) if drop.any() else None,
+            "rays": int(R), "dropped_rays": int(drop.sum())}
+
+
+def proposal_report(w, fr, dfr, steps):
+    """Trains the plain form (n_strat + n_guided samples) and the learned-proposal form
+    (prop_samples, plain as the fallback) from the same initial parameters for `steps`
+    steps; reports rays/s of each and the final rendered-depth error against the
+    noise-free depth (overall and on rays whose observed depth was dropped)."""
+    import numpy as np
+    import torch
+
+    import paper_2206_14735_gb300 as gs
+    import scenegen as sg
+    from paper_2206_14735_gb300.proposal import ProposalTrainer
+    out = {}
+    for form in ("plain", "proposal"):
+        ctx = gs.Context(w, store_activations=True)
+        theta = torch.from_numpy(sg.init_params(w)).cuda()
+        grad, m, v = torch.zeros_like(theta), torch.zeros_like(theta), torch.zeros_like(theta)
+        loss = torch.empty(6, device="cuda")
+        trainer = ProposalTrainer(ctx, w, dfr, seed=5) if form == "proposal" else None
+        batch = gs.Batch.allocate(w.rays, w.n_samples, w.n_smooth) if form == "plain" else None
+        n_prop = 0
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for k in range(steps):
+            if trainer is None:
+                ctx.sample_rays(dfr, 5, k, batch)
+                ctx.forward_backward(theta, batch, None, loss, grad)
+                ctx.adam_step(theta, grad, m, v, k + 1, w.lr_grid, w.lr_mlp, w.betas[0], w.betas[1], w.adam_eps)
+            else:
+                n_prop += int(trainer.controller.use_proposal)
+                trainer.step(k, theta, grad, m, v, loss)
+        torch.cuda.synchronize()
+        dt = time.perf_counter() - t0
+        ctx.sync_status()
+        res = {"steps": steps, "ms_per_step": round(1e3 * dt / steps, 3), "rays_per_s": round(w.rays * steps / dt, 1)}
+        if trainer is None:
+            res.update(_eval_depth(ctx, w, dfr, fr.gt_depth, theta, "plain"))
+            res["samples_per_ray"] = w.n_samples
+        else:
+            res["proposal_steps"] = n_prop
+            hist = trainer.controller.history
+            res["controller_trace"] = [[round(a, 4), round(b, 4), c] for a, b, c in hist[::max(1, len(hist) // 12)]]
+            res["ce_last"] = round(float(trainer.ce[0].item()), 5)
+            res["with_proposal"] = _eval_depth(ctx, w, dfr, fr.gt_depth, theta, "proposal", q=trainer.q)
+            res["with_plain"] = _eval_depth(ctx, w, dfr, fr.gt_depth, theta, "plain")
+            res["samples_per_ray"] = w.prop_samples
+        out[form] = res
+        ctx.close()
+    out["what"] = ("both forms trained from the same initial parameters on the same frames; depth error of the "
+                   "rendered depth against the noise-free depth on 65536 fresh rays; rays_per_s includes the "
+                   "proposal's training step and its held-out fallback checks (host wall clock)")
+    return out
+
+
+def run_proposal(args):
+    """The learned-proposal form as the timed step: sampler (proposal, or the plain
+    fallback), fused forward/backward, proposal training, Adam on both, periodic fallback
+    check."""
+    import torch
+
+    import paper_2206_14735_gb300 as gs
+    import scenegen as sg
+    from paper_2206_14735_gb300 import build as gbuild
+    from paper_2206_14735_gb300.proposal import ProposalTrainer
+
+    rank, world, local = dist_env()
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
+    torch.cuda.set_device(local)
+    gbuild.build()
+    w = sg.WORKLOADS[args.workload]
+    fr = sg.make_frames(w, n_frames=args.frames, with_gt=args.prop_report > 0)
+    dfr = gs.DeviceFrames(fr.rgb, fr.depth, fr.c2w, fr.fx, fr.fy, fr.cx, fr.cy)
+    ctx = gs.Context(w, store_activations=not args.recompute)
+    theta = torch.from_numpy(sg.init_params(w)).cuda()
+    grad, m, v = torch.zeros_like(theta), torch.zeros_like(theta), torch.zeros_like(theta)
+    loss = torch.empty(6, device="cuda")
+    trainer = ProposalTrainer(ctx, w, dfr, seed=3 + 1000 * rank)
+    for k in range(args.warmup + args.prop_pretrain):
+        trainer.step(k, theta, grad, m, v, loss)
+    torch.cuda.synchronize()
+    ctx.sync_status()
+    stream = torch.cuda.current_stream()
+    start, stop = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    if world > 1:
+        torch.distributed.barrier()
+    clocks = ClockSampler(local)
+    base = args.warmup + args.prop_pretrain
+    n_prop = 0
+    start.record(stream)
+    for k in range(args.steps):
+        n_prop += int(trainer.controller.use_proposal)
+        trainer.step(base + k, theta, grad, m, v, loss)
+    stop.record(stream)
+    torch.cuda.synchronize()
+    if world > 1:
+        torch.distributed.barrier()
+    clk = clocks.stop()
+    ms = start.elapsed_time(stop)
+    ctx.sync_status()
+    if world > 1:
+        t = torch.tensor([ms], device="cuda", dtype=torch.float64)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        ms = float(t[0])
+    if rank != 0:
+        return None
+    value = w.rays * args.steps * world / (ms / 1e3)
+    line = {
+        "metric": METRIC, "value": round(value, 1), "unit": "rays/s", "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": round(ms / args.steps, 4), "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": w.name, "rays": w.rays, "samples_per_ray": w.prop_samples,
+                   "fallback_samples_per_ray": w.n_samples, "pretrain_steps": args.prop_pretrain,
+                   "parallelism": f"replicas{world}"},
+        "proposal": {"timed_steps_on_proposal": n_prop, "controller_last": trainer.controller.history[-3:],
+                     "ce_last": round(float(trainer.ce[0].item()), 5)},
+        "clocks": clk,
+        "loss_last": [round(x, 6) for x in loss.cpu().numpy().tolist()],
+    }
+    if args.prop_report > 0:
+        line["proposal_report"] = proposal_report(w, fr, dfr, args.prop_report)
     return line
 
 
@@ -352,9 +513,19 @@ def main():
     ap.add_argument("--traffic-adam", type=float, default=None)
     ap.add_argument("--diff-report", action="store_true",
                     help="also time forward/backward with stored versus recomputed decoder activations")
-    ap.add_argument("--store", action="store_true", help="keep decoder activations between forward and backward")
+    ap.add_argument("--recompute", action="store_true",
+                    help="recompute the decoder activations in the backward pass instead of storing them")
+    ap.add_argument("--split", action="store_true", help="gs_forward then gs_backward instead of the fused call")
+    ap.add_argument("--prop-pretrain", type=int, default=300,
+                    help="proposal workloads: untimed steps before the timed region (controller settles)")
+    ap.add_argument("--prop-report", type=int, default=0,
+                    help="proposal workloads: train plain and proposal forms this many steps and compare depth")
     args = ap.parse_args()
-    line = run_reference(args) if args.impl == "reference" else run_ours(args)
+    if args.impl == "reference":
+        line = run_reference(args)
+    else:
+        import scenegen as sg
+        line = run_proposal(args) if sg.WORKLOADS[args.workload].prop_samples > 0 else run_ours(args)
     if line is not None:
         print(json.dumps(line), flush=True)
 

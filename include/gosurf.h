@@ -41,6 +41,8 @@ extern "C" {
 #define GS_MLP_PARAMS 1684
 #define GS_MAX_SAMPLES 128 /* n_strat + n_guided per ray */
 #define GS_NUM_LOSS 6      /* rgb, depth, sdf, fs, smooth, total */
+#define GS_PROP_BINS 32    /* bins of the learned proposal over [near_m, far_m] */
+#define GS_PROP_PARAMS 1473 /* proposal network: W1[32][11], b1[32], W2[32][32], b2[32], w3[32], b3 */
 
 typedef enum {
   GS_OK = 0,
@@ -83,6 +85,9 @@ typedef struct gs_config {
                                  plane per field, allocated by gs_create) and every backward
                                  pass reads them instead of gathering again and recomputing the
                                  decoders; 0: the backward pass recomputes them (no memory) */
+  int32_t prop_samples;       /* learned proposal sampler (not part of the paper): samples per
+                                 ray of a proposal batch, 2..32; 0 disables gs_proposal_* */
+  int32_t prop_guided;        /* of those, samples stratified over [D - g, D + g] when D > 0 */
 } gs_config;
 
 /* Posed RGB-D frames resident in device memory (Sec. 3: {I_t, D_t}, xi_t). */
@@ -110,6 +115,8 @@ typedef struct gs_batch {
   float* eps;      /* [P][3] perturbations (|eps| = delta_s) */
   uint8_t* valid;  /* [P] 1 if the point is used */
   int32_t* counts; /* [4] rays with D > 0, |S_tr|, |S_fs|, valid smoothness points */
+  float* w;        /* [R][N] rendering weights w_i = T_i alpha_i, written by the forward passes
+                      when not NULL; read by gs_proposal_backward */
 } gs_batch;
 
 typedef struct gs_ctx gs_ctx;
@@ -129,7 +136,8 @@ int64_t gs_param_count(const gs_config* cfg, int64_t* n_grid);
  * smoothness_loss).  Pixels, jitters and perturbation directions come from SplitMix64 keyed
  * by (seed, stream, step, index, slot); every quantity is computed in binary32 with
  * round-to-nearest and no contraction, so results are reproducible bit for bit.
- * batch->R, N, P select the sizes; N must equal n_strat + n_guided. */
+ * batch->R, N, P select the sizes; N must equal n_strat + n_guided.  The render entry
+ * points also accept batches of N = prop_samples made by gs_proposal_sample. */
 gs_status gs_sample_rays(gs_ctx* ctx, const gs_frames* frames, uint64_t seed, uint32_t step, gs_batch* batch,
                          void* stream);
 
@@ -168,6 +176,34 @@ gs_status gs_adam_step(gs_ctx* ctx, float* theta, float* grad, float* m, float* 
  * grad != NULL, grad_x phi [P][3] at points x [P][3]. */
 gs_status gs_query_sdf(gs_ctx* ctx, const float* theta, const float* x, int32_t P, float* sdf, float* grad,
                        void* stream);
+
+/* Learned proposal sampler (an addition to the paper's method: it reduces the samples per
+ * ray).  [near_m, far_m] is cut into GS_PROP_BINS equal bins; for the centre x_b of bin b a
+ * network reads the features of the two coarsest grid levels and the unit ray direction,
+ * u = [z_0(x_b), z_1(x_b), r/|r|], and gives one logit
+ *   l_b = w3 . relu(W2 relu(W1 u + b1) + b2) + b3;   p = softmax_b(l).
+ * prop: the GS_PROP_PARAMS floats in the order of the GS_PROP_PARAMS comment.
+ *
+ * gs_proposal_sample draws the same rays as gs_sample_rays for the same (seed, step) (and
+ * the same smoothness points), then batch->N = prop_samples depths per ray from the
+ * mixture pp = 0.95 p + 0.05 / GS_PROP_BINS: K = N - prop_guided inverse-CDF draws
+ * u_k = (k + xi_k) / K (K = N when D <= 0), placed linearly inside their bin, plus
+ * prop_guided samples stratified over [D - g, D + g] when D > 0; sorted ascending and
+ * classified as in gs_sample_rays.  Binary32 with explicit rounding (bit-reproducible for a
+ * given p).  pdf_in [R][GS_PROP_BINS] (may be NULL) replaces the network's p (then theta and
+ * prop may be NULL); pdf_out (may be NULL) receives the p that was used. */
+gs_status gs_proposal_sample(gs_ctx* ctx, const float* theta, const float* prop, const gs_frames* frames,
+                             uint64_t seed, uint32_t step, const float* pdf_in, float* pdf_out, gs_batch* batch,
+                             void* stream);
+
+/* Training step of the proposal: for every ray the weights batch->w at the depths batch->t
+ * (from a forward pass of the main model on this batch, any sampler) are summed per bin,
+ * h_b, and normalised; rays with sum(h) < 1e-3 are skipped.  The loss is the mean over the
+ * used rays of -sum_b (h_b / sum h) log p_b; the target is constant (no gradient reaches
+ * theta).  prop_grad [GS_PROP_PARAMS] += the gradient w.r.t. prop; ce [2] (may be NULL)
+ * receives (loss, rays used).  Needs prop_samples > 0 in the configuration. */
+gs_status gs_proposal_backward(gs_ctx* ctx, const float* theta, const float* prop, const gs_batch* batch,
+                               float* prop_grad, float* ce, void* stream);
 
 /* Reverse mode of gs_query_sdf with respect to the parameters (the double backward of the
  * SDF gradient, Supp. Sec. 1): grad [n_params] += sum_p dsdf[p] d phi(x_p)/d theta

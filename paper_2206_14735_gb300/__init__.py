@@ -12,7 +12,8 @@ from dataclasses import dataclass
 
 import torch
 
-from ._lib import (GS_FEAT, GS_LEVELS, GS_MLP_PARAMS, GS_NUM_LOSS, GS_PREC_BF16, GS_PREC_FP32, EXPORTS, GoSurfError,
+from ._lib import (GS_FEAT, GS_LEVELS, GS_MLP_PARAMS, GS_NUM_LOSS, GS_PREC_BF16, GS_PREC_FP32, GS_PROP_BINS,
+                   GS_PROP_PARAMS, EXPORTS, GoSurfError,
                    GsBatch, GsConfig, GsFrames, lib, library_path)
 
 __all__ = ["Context", "Batch", "DeviceFrames", "GoSurfStep", "SdfGrad", "GoSurfError", "make_config", "GS_MLP_PARAMS", "GS_NUM_LOSS",
@@ -37,6 +38,8 @@ def make_config(workload, max_rays=None, max_smooth=None, store_activations=Fals
     c.delta_s = float(workload.delta_s)
     c.precision = GS_PREC_BF16 if getattr(workload, "precision", "fp32") == "bf16" else GS_PREC_FP32
     c.store_activations = 1 if store_activations else 0
+    c.prop_samples = int(getattr(workload, "prop_samples", 0))
+    c.prop_guided = int(getattr(workload, "prop_guided", 0))
     return c
 
 
@@ -76,21 +79,24 @@ class Batch:
     eps: torch.Tensor
     valid: torch.Tensor
     counts: torch.Tensor
+    w: torch.Tensor | None = None  # [R][N] rendering weights (written by forward passes when present)
 
     @staticmethod
-    def allocate(R: int, N: int, P: int, device="cuda") -> "Batch":
+    def allocate(R: int, N: int, P: int, device="cuda", weights=False) -> "Batch":
         f = dict(device=device, dtype=torch.float32)
         return Batch(R=R, N=N, P=P, pix=torch.empty(R, device=device, dtype=torch.int64),
                      origin=torch.empty(R, 3, **f), dir=torch.empty(R, 3, **f), rgb=torch.empty(R, 3, **f),
                      depth=torch.empty(R, **f), t=torch.empty(R, N, **f),
                      cls=torch.empty(R, N, device=device, dtype=torch.uint8), xs=torch.empty(max(P, 1), 3, **f),
                      eps=torch.empty(max(P, 1), 3, **f), valid=torch.empty(max(P, 1), device=device, dtype=torch.uint8),
-                     counts=torch.zeros(4, device=device, dtype=torch.int32))
+                     counts=torch.zeros(4, device=device, dtype=torch.int32),
+                     w=torch.zeros(R, N, **f) if weights else None)
 
     def struct(self) -> GsBatch:
         return GsBatch(self.R, self.N, self.P, self.pix.data_ptr(), self.origin.data_ptr(), self.dir.data_ptr(),
                        self.rgb.data_ptr(), self.depth.data_ptr(), self.t.data_ptr(), self.cls.data_ptr(),
-                       self.xs.data_ptr(), self.eps.data_ptr(), self.valid.data_ptr(), self.counts.data_ptr())
+                       self.xs.data_ptr(), self.eps.data_ptr(), self.valid.data_ptr(), self.counts.data_ptr(),
+                       None if self.w is None else self.w.data_ptr())
 
 
 class Context:
@@ -146,13 +152,28 @@ class Context:
     def bf16(self) -> bool:
         return self.cfg.precision == GS_PREC_BF16
 
-    def adam_step(self, theta, grad, m, v, t, lr_grid, lr_mlp, beta1=0.9, beta2=0.999, eps=1e-8, theta_bf16=None):
+    def adam_step(self, theta, grad, m, v, t, lr_grid, lr_mlp, beta1=0.9, beta2=0.999, eps=1e-8, theta_bf16=None,
+                  n_grid=None):
+        """n_grid: entries taking lr_grid (default: this context's grid size; 0 for a vector
+        that is not the main parameter vector, e.g. the proposal network's)."""
         n = theta.numel()
-        self._check(self.L.gs_adam_step(self.h, _ptr(theta), _ptr(grad), _ptr(m), _ptr(v), n, self.n_grid, t,
+        ng = self.n_grid if n_grid is None else n_grid
+        self._check(self.L.gs_adam_step(self.h, _ptr(theta), _ptr(grad), _ptr(m), _ptr(v), n, ng, t,
                                         lr_grid, lr_mlp, beta1, beta2, eps, _ptr(theta_bf16), _stream()))
 
     def query_sdf(self, theta, x, sdf, grad=None):
         self._check(self.L.gs_query_sdf(self.h, _ptr(theta), _ptr(x), x.shape[0], _ptr(sdf), _ptr(grad), _stream()))
+
+    def proposal_sample(self, frames: DeviceFrames, seed: int, step: int, batch: Batch, theta=None, prop=None,
+                        pdf_in=None, pdf_out=None):
+        b = batch.struct()
+        self._check(self.L.gs_proposal_sample(self.h, _ptr(theta), _ptr(prop), ctypes.byref(frames.s), seed, step,
+                                              _ptr(pdf_in), _ptr(pdf_out), ctypes.byref(b), _stream()))
+
+    def proposal_backward(self, theta, prop, batch: Batch, prop_grad, ce=None):
+        b = batch.struct()
+        self._check(self.L.gs_proposal_backward(self.h, _ptr(theta), _ptr(prop), ctypes.byref(b), _ptr(prop_grad),
+                                                _ptr(ce), _stream()))
 
     def query_sdf_backward(self, theta, x, dsdf, dgrad, grad):
         self._check(self.L.gs_query_sdf_backward(self.h, _ptr(theta), _ptr(x), x.shape[0], _ptr(dsdf), _ptr(dgrad),

@@ -13,11 +13,12 @@ _LOCK = threading.Lock()
 
 GS_LEVELS, GS_FEAT, GS_MLP_PARAMS, GS_NUM_LOSS = 4, 4, 1684, 6
 GS_PREC_FP32, GS_PREC_BF16 = 0, 1
+GS_PROP_BINS, GS_PROP_PARAMS = 32, 1473
 STATUS = {0: "GS_OK", 1: "GS_ERR_INVALID_ARG", 2: "GS_ERR_SHAPE", 3: "GS_ERR_ALIGN", 4: "GS_ERR_CUDA",
           5: "GS_ERR_DEVICE", 6: "GS_ERR_UNSUPPORTED"}
 
 EXPORTS = ["gs_create", "gs_destroy", "gs_param_count", "gs_sample_rays", "gs_forward", "gs_backward",
-           "gs_forward_backward", "gs_adam_step", "gs_query_sdf", "gs_query_sdf_backward", "gs_voxel_index", "gs_sync_status",
+           "gs_forward_backward", "gs_adam_step", "gs_query_sdf", "gs_query_sdf_backward", "gs_proposal_sample", "gs_proposal_backward", "gs_voxel_index", "gs_sync_status",
            "gs_last_error", "gs_forward_backward_noalloc"]
 
 
@@ -27,7 +28,8 @@ class GsConfig(ctypes.Structure):
                 ("far_m", ctypes.c_float), ("guide_half", ctypes.c_float), ("trunc", ctypes.c_float),
                 ("kappa_fs", ctypes.c_float), ("lam", ctypes.c_float * 5), ("max_rays", ctypes.c_int32),
                 ("max_smooth", ctypes.c_int32), ("delta_s", ctypes.c_float), ("precision", ctypes.c_int32),
-                ("store_activations", ctypes.c_int32)]
+                ("store_activations", ctypes.c_int32), ("prop_samples", ctypes.c_int32),
+                ("prop_guided", ctypes.c_int32)]
 
 
 class GsFrames(ctypes.Structure):
@@ -41,7 +43,7 @@ class GsBatch(ctypes.Structure):
                 ("origin", ctypes.c_void_p), ("dir", ctypes.c_void_p), ("rgb", ctypes.c_void_p),
                 ("depth", ctypes.c_void_p), ("t", ctypes.c_void_p), ("cls", ctypes.c_void_p),
                 ("xs", ctypes.c_void_p), ("eps", ctypes.c_void_p), ("valid", ctypes.c_void_p),
-                ("counts", ctypes.c_void_p)]
+                ("counts", ctypes.c_void_p), ("w", ctypes.c_void_p)]
 
 
 def library_path() -> str:
@@ -78,6 +80,10 @@ def lib():
             L.gs_adam_step.argtypes = [vp, vp, vp, vp, vp, i64, i64, i32, f32, f32, f32, f32, f32, vp, vp]
             L.gs_query_sdf.restype = i32
             L.gs_query_sdf.argtypes = [vp, vp, vp, i32, vp, vp, vp]
+            L.gs_proposal_sample.restype = i32
+            L.gs_proposal_sample.argtypes = [vp, vp, vp, vp, ctypes.c_uint64, ctypes.c_uint32, vp, vp, vp, vp]
+            L.gs_proposal_backward.restype = i32
+            L.gs_proposal_backward.argtypes = [vp, vp, vp, vp, vp, vp, vp]
             L.gs_query_sdf_backward.restype = i32
             L.gs_query_sdf_backward.argtypes = [vp, vp, vp, i32, vp, vp, vp, vp]
             L.gs_voxel_index.restype = i32

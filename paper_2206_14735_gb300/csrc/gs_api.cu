@@ -31,13 +31,24 @@ long long level_floats(const gs_config* c, int l) {
 gs_status check_batch(gs_ctx* ctx, const gs_batch* b, bool need_smooth_arrays) {
   if (!b) return fail(ctx, GS_ERR_INVALID_ARG, "batch is NULL");
   if (b->R < 0 || b->R > ctx->cfg.max_rays) return fail(ctx, GS_ERR_SHAPE, "batch R outside [0, max_rays]");
-  if (b->N != ctx->cfg.n_strat + ctx->cfg.n_guided) return fail(ctx, GS_ERR_SHAPE, "batch N != n_strat + n_guided");
+  if (b->N != ctx->cfg.n_strat + ctx->cfg.n_guided && !(ctx->cfg.prop_samples > 0 && b->N == ctx->cfg.prop_samples))
+    return fail(ctx, GS_ERR_SHAPE, "batch N is neither n_strat + n_guided nor prop_samples");
   if (b->P < 0 || b->P > ctx->cfg.max_smooth) return fail(ctx, GS_ERR_SHAPE, "batch P outside [0, max_smooth]");
   if (!b->counts) return fail(ctx, GS_ERR_INVALID_ARG, "batch counts is NULL");
   if (b->R > 0 && (!b->origin || !b->dir || !b->rgb || !b->depth || !b->t || !b->cls))
     return fail(ctx, GS_ERR_INVALID_ARG, "batch ray array is NULL");
   if (b->R > 0 && need_smooth_arrays && !b->pix) return fail(ctx, GS_ERR_INVALID_ARG, "batch pix is NULL");
   if (b->P > 0 && (!b->xs || !b->eps || !b->valid)) return fail(ctx, GS_ERR_INVALID_ARG, "batch smoothness array is NULL");
+  return GS_OK;
+}
+
+gs_status check_frames(gs_ctx* ctx, const gs_frames* frames, const char* who) {
+  std::string w(who);
+  if (!frames || !frames->rgb || !frames->depth || !frames->c2w)
+    return fail(ctx, GS_ERR_INVALID_ARG, (w + ": frames or a frame array is NULL").c_str());
+  if (frames->F < 1 || frames->H < 1 || frames->W < 1) return fail(ctx, GS_ERR_SHAPE, (w + ": empty frames").c_str());
+  if (!(frames->fx != 0.0f) || !(frames->fy != 0.0f))
+    return fail(ctx, GS_ERR_INVALID_ARG, (w + ": zero focal length").c_str());
   return GS_OK;
 }
 
@@ -70,6 +81,10 @@ gs_status gs_create(const gs_config* cfg, gs_ctx** out) {
   if (!(cfg->far_m > cfg->near_m) || !(cfg->trunc > 0.0f) || !(cfg->guide_half >= 0.0f))
     return fail(nullptr, GS_ERR_INVALID_ARG, "gs_create: bad near/far/trunc/guide_half");
   if (cfg->max_rays < 0 || cfg->max_smooth < 0) return fail(nullptr, GS_ERR_INVALID_ARG, "gs_create: negative batch bound");
+  if (cfg->prop_samples != 0 &&
+      (cfg->prop_samples < 2 || cfg->prop_samples > GS_PROP_BINS || cfg->prop_guided < 0 ||
+       cfg->prop_guided >= cfg->prop_samples))
+    return fail(nullptr, GS_ERR_INVALID_ARG, "gs_create: need 2 <= prop_samples <= 32 and 0 <= prop_guided < prop_samples");
 
   gs_ctx* c = new (std::nothrow) gs_ctx();
   if (!c) return fail(nullptr, GS_ERR_INVALID_ARG, "gs_create: out of host memory");
@@ -99,6 +114,8 @@ gs_status gs_create(const gs_config* cfg, gs_ctx** out) {
       cudaMalloc(&c->status, sizeof(int)) != cudaSuccess ||
       cudaMemcpy(c->default_dloss, dl, sizeof(dl), cudaMemcpyHostToDevice) != cudaSuccess ||
       cudaMemset(c->status, 0, sizeof(int)) != cudaSuccess ||
+      (cfg->prop_samples > 0 &&
+       cudaMalloc(&c->prop_part, sizeof(float) * gs_prop_part_floats(c->num_sms)) != cudaSuccess) ||
       (cfg->store_activations &&
        cudaMalloc(&c->store, c->store_bytes = (size_t)cfg->max_rays * N * kStoreFloatsPerSample * sizeof(float)) !=
            cudaSuccess)) {
@@ -117,18 +134,19 @@ void gs_destroy(gs_ctx* ctx) {
   cudaFree(ctx->default_dloss);
   cudaFree(ctx->status);
   cudaFree(ctx->store);
+  cudaFree(ctx->prop_part);
   delete ctx;
 }
 
 gs_status gs_sample_rays(gs_ctx* ctx, const gs_frames* frames, uint64_t seed, uint32_t step, gs_batch* batch,
                          void* stream) {
   if (!ctx) return fail(nullptr, GS_ERR_INVALID_ARG, "gs_sample_rays: ctx is NULL");
-  if (!frames || !frames->rgb || !frames->depth || !frames->c2w)
-    return fail(ctx, GS_ERR_INVALID_ARG, "gs_sample_rays: frames or a frame array is NULL");
-  if (frames->F < 1 || frames->H < 1 || frames->W < 1) return fail(ctx, GS_ERR_SHAPE, "gs_sample_rays: empty frames");
-  if (!(frames->fx != 0.0f) || !(frames->fy != 0.0f)) return fail(ctx, GS_ERR_INVALID_ARG, "gs_sample_rays: zero focal length");
+  gs_status fs = check_frames(ctx, frames, "gs_sample_rays");
+  if (fs != GS_OK) return fs;
   gs_status s = check_batch(ctx, batch, true);
   if (s != GS_OK) return s;
+  if (batch->N != ctx->cfg.n_strat + ctx->cfg.n_guided)
+    return fail(ctx, GS_ERR_SHAPE, "gs_sample_rays: batch N != n_strat + n_guided");
   cudaStream_t st = (cudaStream_t)stream;
   ctx->last_stream = st;
   s = gs_launch_sample(ctx, frames, seed, step, batch, st);
@@ -231,6 +249,40 @@ gs_status gs_query_sdf(gs_ctx* ctx, const float* theta, const float* x, int32_t 
   ctx->last_stream = st;
   if (gs_launch_query(ctx, theta, x, P, sdf, grad, st) != GS_OK) return cuda_fail(ctx, "gs_query_sdf");
   return GS_OK;
+}
+
+gs_status gs_proposal_sample(gs_ctx* ctx, const float* theta, const float* prop, const gs_frames* frames,
+                             uint64_t seed, uint32_t step, const float* pdf_in, float* pdf_out, gs_batch* batch,
+                             void* stream) {
+  if (!ctx) return fail(nullptr, GS_ERR_INVALID_ARG, "gs_proposal_sample: ctx is NULL");
+  if (ctx->cfg.prop_samples <= 0) return fail(ctx, GS_ERR_UNSUPPORTED, "gs_proposal_sample: prop_samples is 0");
+  gs_status s = check_frames(ctx, frames, "gs_proposal_sample");
+  if (s != GS_OK) return s;
+  s = check_batch(ctx, batch, true);
+  if (s != GS_OK) return s;
+  if (batch->N != ctx->cfg.prop_samples) return fail(ctx, GS_ERR_SHAPE, "gs_proposal_sample: batch N != prop_samples");
+  if (batch->R > 0 && !pdf_in && (!theta || !prop))
+    return fail(ctx, GS_ERR_INVALID_ARG, "gs_proposal_sample: theta and prop are needed without pdf_in");
+  if (batch->R > 0 && !pdf_in && !aligned16(theta)) return fail(ctx, GS_ERR_ALIGN, "gs_proposal_sample: theta is not 16-byte aligned");
+  cudaStream_t st = (cudaStream_t)stream;
+  ctx->last_stream = st;
+  s = gs_launch_prop_sample(ctx, theta, prop, frames, seed, step, pdf_in, pdf_out, batch, st);
+  return s == GS_OK ? s : cuda_fail(ctx, "gs_proposal_sample");
+}
+
+gs_status gs_proposal_backward(gs_ctx* ctx, const float* theta, const float* prop, const gs_batch* batch,
+                               float* prop_grad, float* ce, void* stream) {
+  if (!ctx) return fail(nullptr, GS_ERR_INVALID_ARG, "gs_proposal_backward: ctx is NULL");
+  if (ctx->cfg.prop_samples <= 0) return fail(ctx, GS_ERR_UNSUPPORTED, "gs_proposal_backward: prop_samples is 0");
+  gs_status s = check_batch(ctx, batch, false);
+  if (s != GS_OK) return s;
+  if (!theta || !prop || !prop_grad) return fail(ctx, GS_ERR_INVALID_ARG, "gs_proposal_backward: NULL array");
+  if (batch->R > 0 && !batch->w) return fail(ctx, GS_ERR_INVALID_ARG, "gs_proposal_backward: batch w is NULL");
+  if (!aligned16(theta)) return fail(ctx, GS_ERR_ALIGN, "gs_proposal_backward: theta is not 16-byte aligned");
+  cudaStream_t st = (cudaStream_t)stream;
+  ctx->last_stream = st;
+  s = gs_launch_prop_backward(ctx, theta, prop, batch, prop_grad, ce, st);
+  return s == GS_OK ? s : cuda_fail(ctx, "gs_proposal_backward");
 }
 
 gs_status gs_query_sdf_backward(gs_ctx* ctx, const float* theta, const float* x, int32_t P, const float* dsdf,

@@ -29,6 +29,7 @@ struct gs_ctx {
   size_t store_bytes = 0;
   int store_R = -1, store_N = -1;     // batch shape and depths pointer of the gs_forward that filled it
   const float* store_t = nullptr;
+  float* prop_part = nullptr;        // proposal training partial rows (prop_samples > 0)
   cudaStream_t last_stream = nullptr;
   std::string last_error;
 };
@@ -46,6 +47,15 @@ gs_status gs_launch_finalize(const gs_ctx* ctx, const gs_batch* b, float* loss, 
 gs_status gs_launch_adam(float* theta, float* grad, float* m, float* v, long long n, long long n_grid, int t,
                          float lr_grid, float lr_mlp, float b1, float b2, float eps, uint16_t* bf16, int num_sms,
                          cudaStream_t st);
+gs_status gs_launch_sample_smooth(const gs_ctx* ctx, const gs_frames* f, uint64_t seed, uint32_t step,
+                                  const gs_batch* b, cudaStream_t st);
+int gs_prop_part_rows(int num_sms);
+size_t gs_prop_part_floats(int num_sms);
+gs_status gs_launch_prop_sample(const gs_ctx* ctx, const float* theta, const float* q, const gs_frames* f,
+                                uint64_t seed, uint32_t step, const float* pdf_in, float* pdf_out, const gs_batch* b,
+                                cudaStream_t st);
+gs_status gs_launch_prop_backward(const gs_ctx* ctx, const float* theta, const float* q, const gs_batch* b,
+                                  float* grad, float* ce, cudaStream_t st);
 gs_status gs_launch_query_backward(const gs_ctx* ctx, const float* theta, const float* x, int P, const float* dsdf,
                                    const float* dgrad, float* grad, cudaStream_t st);
 gs_status gs_launch_query(const gs_ctx* ctx, const float* theta, const float* x, int P, float* sdf, float* grad,

@@ -169,6 +169,7 @@ gs_status gs_launch_render(const gs_ctx* ctx, const float* theta, const uint16_t
   a.wsum = wsum;
   a.status = ctx->status;
   a.store = ctx->store;
+  a.w_out = b->w;
   a.store_stride = (long long)ctx->cfg.max_rays * (ctx->cfg.n_strat + ctx->cfg.n_guided);
   const int nch = (b->N + 31) / 32;
   if (ctx->cfg.precision == GS_PREC_BF16) {

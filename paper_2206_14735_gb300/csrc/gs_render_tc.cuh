@@ -397,6 +397,7 @@ struct RenderTcArgs {
   // in place of the gather and the four recomputed decoder phases.  nullptr: recompute.
   float* store;
   long long store_stride;
+  float* w_out;  // [R][N] rendering weights, written by forward passes when not nullptr
 };
 
 // fields of one stored sample: z[16] | a1 = ReLU layer-1 output [32] | (phi, h[15]) | a2 [32] | c[3]
@@ -613,6 +614,11 @@ __global__ void __launch_bounds__(GR * kGroupThreads, 1) render_tc_kernel(Render
       T[j] = carry * exc;
       carry *= __shfl_sync(0xffffffffu, inc, 31);
       w[j] = T[j] * al[j];
+    }
+    if (FWD && a.w_out != nullptr && has_ray) {
+#pragma unroll
+      for (int j = 0; j < NCH; ++j)
+        if (32 * j + lane < N) a.w_out[(size_t)ray * N + 32 * j + lane] = w[j];
     }
     float ch[3] = {0.f, 0.f, 0.f}, dh = 0.f, ws = 0.f;
 #pragma unroll

@@ -1,44 +1,9 @@
 // Ray batch sampling, sample placement and bound classes (Sec. 3.2-3.4), and the
 // near-surface smoothness points S_g (Sec. 3.3).  Every value here is computed with
 // explicitly rounded binary32 operations so that it is reproducible bit for bit.
-#include "gs_internal.h"
+#include "gs_sample.cuh"
 
 namespace gs {
-
-struct FramesDev {
-  int F, H, W;
-  const uint8_t* rgb;
-  const float* depth;
-  const float* c2w;
-  float fx, fy, cx, cy;
-};
-
-// pixel -> (o, r, I, D); r has unit camera-z so the ray parameter is z-depth
-__device__ __forceinline__ void pixel_ray(const FramesDev& fr, long long pix, float o[3], float r[3], float rgb[3],
-                                          float* D) {
-  const long long hw = (long long)fr.H * fr.W;
-  const long long f = pix / hw, rem = pix - f * hw;
-  const int v = (int)(rem / fr.W), u = (int)(rem - (long long)v * fr.W);
-  const float dx = __fdiv_rn(__fsub_rn(__fadd_rn((float)u, 0.5f), fr.cx), fr.fx);
-  const float dy = __fdiv_rn(__fsub_rn(__fadd_rn((float)v, 0.5f), fr.cy), fr.fy);
-  const float* P = fr.c2w + 12 * f;
-#pragma unroll
-  for (int a = 0; a < 3; ++a) {
-    r[a] = __fadd_rn(__fadd_rn(__fmul_rn(P[4 * a + 0], dx), __fmul_rn(P[4 * a + 1], dy)), P[4 * a + 2]);
-    o[a] = P[4 * a + 3];
-  }
-#pragma unroll
-  for (int j = 0; j < 3; ++j) rgb[j] = __fdiv_rn((float)fr.rgb[3 * pix + j], 255.0f);
-  *D = fr.depth[pix];
-}
-
-__device__ __forceinline__ int sample_class(float D, float t, float trunc) {
-  if (!(D > 0.0f)) return CLS_NONE;
-  const float b = __fsub_rn(D, t);
-  if (fabsf(b) <= trunc) return CLS_TR;
-  if (b > trunc) return CLS_FS;
-  return CLS_NONE;
-}
 
 struct SampleArgs {
   FramesDev fr;
@@ -51,17 +16,6 @@ struct SampleArgs {
   uint8_t* cls;
   int* counts;
 };
-
-__device__ __forceinline__ void block_add_counts(int* counts, int a, int b, int c) {
-  a = __reduce_add_sync(0xffffffffu, a);
-  b = __reduce_add_sync(0xffffffffu, b);
-  c = __reduce_add_sync(0xffffffffu, c);
-  if ((threadIdx.x & 31) == 0) {
-    if (a) atomicAdd(counts + 0, a);
-    if (b) atomicAdd(counts + 1, b);
-    if (c) atomicAdd(counts + 2, c);
-  }
-}
 
 __global__ void __launch_bounds__(128) sample_rays_kernel(SampleArgs a) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
@@ -199,6 +153,16 @@ __global__ void __launch_bounds__(128) sample_smooth_kernel(SmoothArgs a) {
 
 using namespace gs;
 
+gs_status gs_launch_sample_smooth(const gs_ctx* ctx, const gs_frames* f, uint64_t seed, uint32_t step,
+                                  const gs_batch* b, cudaStream_t st) {
+  FramesDev fr{f->F, f->H, f->W, f->rgb, f->depth, f->c2w, f->fx, f->fy, f->cx, f->cy};
+  if (b->P > 0) {
+    SmoothArgs s{fr, seed, step, b->P, ctx->cfg.trunc, ctx->cfg.delta_s, b->xs, b->eps, b->valid, b->counts};
+    sample_smooth_kernel<<<(b->P + 127) / 128, 128, 0, st>>>(s);
+  }
+  return cudaPeekAtLastError() == cudaSuccess ? GS_OK : GS_ERR_CUDA;
+}
+
 gs_status gs_launch_sample(const gs_ctx* ctx, const gs_frames* f, uint64_t seed, uint32_t step, const gs_batch* b,
                            cudaStream_t st) {
   FramesDev fr{f->F, f->H, f->W, f->rgb, f->depth, f->c2w, f->fx, f->fy, f->cx, f->cy};
@@ -209,9 +173,5 @@ gs_status gs_launch_sample(const gs_ctx* ctx, const gs_frames* f, uint64_t seed,
                  b->rgb, b->depth, b->t, b->cls, b->counts};
     sample_rays_kernel<<<(b->R + 127) / 128, 128, 0, st>>>(a);
   }
-  if (b->P > 0) {
-    SmoothArgs s{fr, seed, step, b->P, ctx->cfg.trunc, ctx->cfg.delta_s, b->xs, b->eps, b->valid, b->counts};
-    sample_smooth_kernel<<<(b->P + 127) / 128, 128, 0, st>>>(s);
-  }
-  return cudaPeekAtLastError() == cudaSuccess ? GS_OK : GS_ERR_CUDA;
+  return gs_launch_sample_smooth(ctx, f, seed, step, b, st);
 }

@@ -254,6 +254,9 @@ class Workload:
     betas: tuple = (0.9, 0.999)
     adam_eps: float = 1e-8
     precision: str = "fp32"
+    prop_samples: int = 0   # learned proposal: samples per ray of a proposal batch (0 = off)
+    prop_guided: int = 8    # of those, depth-guided when D > 0
+    lr_prop: float = 1e-3
     extra: dict = field(default_factory=dict)
 
     @property
@@ -295,6 +298,10 @@ WORKLOADS = {
 WORKLOADS["room-bf16-32768x96"] = WORKLOADS["room-8192x96"].with_(name="room-bf16-32768x96", rays=32768,
                                                                    precision="bf16")
 WORKLOADS["room-diff-65536x96"] = WORKLOADS["room-8192x96"].with_(name="room-diff-65536x96", rays=65536)
+# learned-proposal form: 30% of every depth frame zeroed in contiguous blobs, 65536 rays,
+# 32 samples per ray (24 drawn from the proposal + 8 depth-guided), plain 64 + 32 as fallback
+WORKLOADS["room-prop-65536x32"] = WORKLOADS["room-8192x96"].with_(name="room-prop-65536x32", rays=65536,
+                                                                   blob_frac=0.3, prop_samples=32, prop_guided=8)
 
 
 @dataclass

@@ -1,0 +1,138 @@
+"""Learned proposal sampler (an addition to the method) on the GPU versus the oracle:
+ray selection and the inverse-CDF sampler bit for bit given the same PDF, the network's PDF
+within FP32 rounding, the rendering weights the forward pass writes, and the cross-entropy
+gradient of the proposal network."""
+import numpy as np
+import pytest
+import torch
+
+import oracle as oc
+import paper_2206_14735_gb300 as gs
+import scenegen as sg
+from gpu_common import Problem, prepare_parity_batch, upload_oracle_batch
+from helpers import CUBE, sdf_parity_params
+
+pytestmark = pytest.mark.gpu
+
+CUBE_P = CUBE.with_(name="cube-prop", prop_samples=32, prop_guided=8)
+SEED, STEP = 4, 7
+
+
+def _q(seed=3, scale=0.3):
+    return np.random.default_rng(seed).normal(0.0, scale, oc.PROP_PARAMS).astype(np.float32)
+
+
+@pytest.fixture(scope="module")
+def prob():
+    p = Problem(CUBE_P, max_rays=4096)
+    theta = sdf_parity_params(CUBE_P, sg.cube_scene(), seed=21)
+    theta[:p.n_grid] += np.random.default_rng(5).normal(0, 0.2, p.n_grid).astype(np.float32)  # coarse features vary
+    return dict(p=p, theta=theta, q=_q())
+
+
+def _bits(a):
+    return np.ascontiguousarray(a).view(np.uint32)
+
+
+def _gpu_prop_sample(pr, R, P, pdf_in=None, with_net=True):
+    p = pr["p"]
+    b = gs.Batch.allocate(R, CUBE_P.prop_samples, P, weights=True)
+    th = torch.from_numpy(pr["theta"]).cuda()
+    q = torch.from_numpy(pr["q"]).cuda()
+    pdf_out = torch.empty(max(R, 1), oc.PROP_BINS, device="cuda")
+    pin = None if pdf_in is None else torch.from_numpy(np.ascontiguousarray(pdf_in, np.float32)).cuda()
+    p.ctx.proposal_sample(p.dfr, SEED, STEP, b, theta=th if with_net else None, prop=q if with_net else None,
+                          pdf_in=pin, pdf_out=pdf_out)
+    torch.cuda.synchronize()
+    return b, pdf_out[:R].cpu().numpy()
+
+
+@pytest.mark.parametrize("R", [1000, 33, 1, 0])
+def test_rays_and_inverse_cdf_bit_exact_given_the_pdf(prob, R):
+    p = prob["p"]
+    bt, sm = p.oracle_sample(SEED, STEP, R, 64)
+    # the PDF both sides sample from: the oracle network's, rounded to binary32
+    pdf = oc.prop_forward(p.cfg, prob["theta"], prob["q"], bt["o"], bt["r"]).astype(np.float32)
+    b, used = _gpu_prop_sample(prob, R, 64, pdf_in=pdf, with_net=False)
+    assert np.array_equal(b.pix.cpu().numpy(), bt["pix"])
+    for gk, ok in (("origin", "o"), ("dir", "r"), ("rgb", "rgb"), ("depth", "D")):
+        assert np.array_equal(_bits(getattr(b, gk).cpu().numpy()), _bits(bt[ok])), gk
+    assert np.array_equal(_bits(used), _bits(pdf))
+    ref = oc.prop_sample(p.cfg, bt["D"], pdf, CUBE_P.prop_samples, CUBE_P.prop_guided, SEED, STEP)
+    assert np.array_equal(_bits(b.t.cpu().numpy()), _bits(ref["t"]))
+    assert np.array_equal(b.cls.cpu().numpy(), ref["cls"])
+    assert list(b.counts.cpu().numpy()[:3]) == list(ref["counts"][:3])
+    # smoothness points are the plain sampler's
+    assert np.array_equal(_bits(b.xs[:64].cpu().numpy()), _bits(sm["xs"]))
+
+
+def test_network_pdf_parity(prob):
+    p = prob["p"]
+    bt, _ = p.oracle_sample(SEED, STEP, 2000, 0)
+    _, pdf = _gpu_prop_sample(prob, 2000, 0)
+    ref = oc.prop_forward(p.cfg, prob["theta"], prob["q"], bt["o"], bt["r"])
+    np.testing.assert_allclose(pdf, ref, rtol=2e-5, atol=1e-7)
+    np.testing.assert_allclose(pdf.sum(1), 1.0, atol=2e-6)
+
+
+def test_forward_writes_rendering_weights(prob):
+    """batch.w after gs_forward equals the oracle's w_i = T_i alpha_i on a parity batch."""
+    p = prob["p"]
+    theta = sdf_parity_params(CUBE, sg.cube_scene(), seed=21)
+    bt, sm = p.oracle_sample(3, 5)
+    bt_s, _, _ = prepare_parity_batch(p, theta, bt, sm)
+    ref = oc.step(p.cfg, theta, bt_s, sm, want_grad=False, want_weights=True)
+    b = upload_oracle_batch(bt_s, sm, sm["n_valid"][0])
+    b.w = torch.zeros_like(b.t)
+    loss = torch.empty(6, device="cuda")
+    p.ctx.forward(torch.from_numpy(theta).cuda(), b, loss)
+    torch.cuda.synchronize()
+    # alpha = (Phi_i - Phi_i+1) / Phi_i loses relative precision in binary32 when the two
+    # opacities are close, so the bound is relative as well as absolute
+    np.testing.assert_allclose(b.w.cpu().numpy(), ref["w"], rtol=1e-4, atol=2e-6)
+
+
+def test_cross_entropy_gradient_parity(prob):
+    p = prob["p"]
+    R = 3000
+    bt, _ = p.oracle_sample(SEED, STEP, R, 0)
+    pdf = oc.prop_forward(p.cfg, prob["theta"], prob["q"], bt["o"], bt["r"]).astype(np.float32)
+    b, _ = _gpu_prop_sample(prob, R, 0, pdf_in=pdf, with_net=False)
+    ref_s = oc.prop_sample(p.cfg, bt["D"], pdf, CUBE_P.prop_samples, CUBE_P.prop_guided, SEED, STEP)
+    # target weights: peaked per ray, some rays below the 1e-3 threshold (skipped)
+    rng = np.random.default_rng(9)
+    w = rng.dirichlet(np.full(CUBE_P.prop_samples, 0.2), R) * rng.uniform(0.2, 1.0, (R, 1))
+    w[::17] *= 1e-4
+    w = w.astype(np.float32)
+    b.w.copy_(torch.from_numpy(w))
+    grad = torch.zeros(oc.PROP_PARAMS, device="cuda")
+    ce = torch.zeros(2, device="cuda")
+    th = torch.from_numpy(prob["theta"]).cuda()
+    q = torch.from_numpy(prob["q"]).cuda()
+    p.ctx.proposal_backward(th, q, b, grad, ce)
+    torch.cuda.synchronize()
+    loss, g_ref, n_used = oc.prop_ce(p.cfg, prob["theta"], prob["q"], bt["o"], bt["r"], ref_s["t"], w)
+    ce_h = ce.cpu().numpy()
+    assert int(ce_h[1]) == n_used
+    assert abs(ce_h[0] - loss) <= 1e-5 * abs(loss)
+    g = grad.cpu().numpy().astype(np.float64)
+    blocks = [("W1", 0, 352), ("b1", 352, 384), ("W2", 384, 1408), ("b2", 1408, 1440), ("w3", 1440, 1472)]
+    for name, a, e in blocks:
+        scale = np.abs(g_ref[a:e]).max()
+        assert np.abs(g[a:e] - g_ref[a:e]).max() <= 1e-4 * scale, name
+    # d/d b3 = sum_b (p_b - hh_b) / n = 0 for every ray (both distributions sum to one)
+    assert abs(g_ref[1472]) < 1e-12 and abs(g[1472]) < 1e-6
+
+
+def test_proposal_entry_points_reject_bad_shapes(prob):
+    p = prob["p"]
+    b = gs.Batch.allocate(8, CUBE_P.n_samples, 0)  # plain N, not prop_samples
+    with pytest.raises(gs.GoSurfError):
+        p.ctx.proposal_sample(p.dfr, 1, 1, b, theta=torch.from_numpy(prob["theta"]).cuda(),
+                              prop=torch.from_numpy(prob["q"]).cuda())
+    bp = gs.Batch.allocate(8, CUBE_P.prop_samples, 0)
+    with pytest.raises(gs.GoSurfError):
+        p.ctx.sample_rays(p.dfr, 1, 1, bp)  # the plain sampler writes n_strat + n_guided samples
+    with pytest.raises(gs.GoSurfError):  # no weights to learn from
+        p.ctx.proposal_backward(torch.from_numpy(prob["theta"]).cuda(), torch.from_numpy(prob["q"]).cuda(), bp,
+                                torch.zeros(oc.PROP_PARAMS, device="cuda"))
