@@ -333,6 +333,10 @@ def run_proposal(args):
     torch.cuda.set_device(local)
     gbuild.build()
     w = sg.WORKLOADS[args.workload]
+    if args.prop_guided is not None:
+        w = w.with_(prop_guided=args.prop_guided)
+    if args.lr_prop is not None:
+        w = w.with_(lr_prop=args.lr_prop)
     fr = sg.make_frames(w, n_frames=args.frames, with_gt=args.prop_report > 0)
     dfr = gs.DeviceFrames(fr.rgb, fr.depth, fr.c2w, fr.fx, fr.fy, fr.cx, fr.cy)
     ctx = gs.Context(w, store_activations=not args.recompute)
@@ -374,6 +378,7 @@ def run_proposal(args):
         "warmup": args.warmup, "ms_per_step": round(ms / args.steps, 4), "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
         "config": {"workload": w.name, "rays": w.rays, "samples_per_ray": w.prop_samples,
+                   "guided_of_those": w.prop_guided, "lr_prop": w.lr_prop,
                    "fallback_samples_per_ray": w.n_samples, "pretrain_steps": args.prop_pretrain,
                    "parallelism": f"replicas{world}"},
         "proposal": {"timed_steps_on_proposal": n_prop, "controller_last": trainer.controller.history[-3:],
@@ -518,6 +523,8 @@ def main():
     ap.add_argument("--split", action="store_true", help="gs_forward then gs_backward instead of the fused call")
     ap.add_argument("--prop-pretrain", type=int, default=300,
                     help="proposal workloads: untimed steps before the timed region (controller settles)")
+    ap.add_argument("--prop-guided", type=int, default=None, help="proposal workloads: override prop_guided")
+    ap.add_argument("--lr-prop", type=float, default=None, help="proposal workloads: override the proposal's lr")
     ap.add_argument("--prop-report", type=int, default=0,
                     help="proposal workloads: train plain and proposal forms this many steps and compare depth")
     args = ap.parse_args()

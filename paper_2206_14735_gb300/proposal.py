@@ -52,7 +52,7 @@ class ProposalTrainer:
     fallback), the proposal's own training step, and the periodic fallback decision."""
 
     def __init__(self, ctx, workload, frames, *, seed: int = 3, eval_every: int = 25, holdout: int | None = None,
-                 tolerance: float = 1.05, q0: np.ndarray | None = None):
+                 tolerance: float = 1.05, q0: np.ndarray | None = None, train_rays: int | None = 16384):
         from . import Batch  # local import: the package imports this module lazily
         w = workload
         self.ctx, self.w, self.frames, self.seed = ctx, w, frames, seed
@@ -71,6 +71,8 @@ class ProposalTrainer:
         self.hold_loss = torch.zeros(2, GS_NUM_LOSS, device="cuda")
         self.controller = FallbackController(tolerance=tolerance)
         self.t_q = 0
+        # the proposal learns from the first train_rays rays of each batch (rays are i.i.d.)
+        self.train_rays = R if train_rays is None else min(R, train_rays)
 
     def batch(self, step: int, theta):
         """Sample this step's batch with the current sampler choice."""
@@ -81,8 +83,11 @@ class ProposalTrainer:
         return self.batch_plain
 
     def train_proposal(self, theta, batch):
-        """Cross-entropy step of the proposal on the weights the last forward pass wrote."""
-        self.ctx.proposal_backward(theta, self.q, batch, self.gq, self.ce)
+        """Cross-entropy step of the proposal on the weights the last forward pass wrote
+        (first train_rays rays of the batch)."""
+        from dataclasses import replace
+        sub = batch if self.train_rays >= batch.R else replace(batch, R=self.train_rays)
+        self.ctx.proposal_backward(theta, self.q, sub, self.gq, self.ce)
         self.t_q += 1
         self.ctx.adam_step(self.q, self.gq, self.mq, self.vq, self.t_q, 0.0, self.w.lr_prop, self.w.betas[0],
                            self.w.betas[1], self.w.adam_eps, n_grid=0)
