@@ -62,8 +62,12 @@ __host__ __device__ constexpr uint32_t wOff(int i) {
 template <class P>
 __host__ __device__ constexpr uint32_t wTotal() { return wOff<P>(8); }
 
-// tensor-memory columns of one group
-constexpr uint32_t cD1 = 0, cD2 = 32, cD3 = 48, cX = 80, cY = 112, kGroupCols = 128;
+// tensor-memory columns of one group: forward accumulators D1..D3 and the colour output X;
+// the backward phases reuse D3 (N = 32) and D2 (N = 16) once those are consumed; the decoder
+// weight gradients accumulate over all of the group's tiles in W1..W4 (M = 64 layout: row m
+// in lane 32 (m / 16) + m % 16)
+constexpr uint32_t cD1 = 0, cD2 = 32, cD3 = 48, cX = 80, cXb = cD3, cYb = cD2;
+constexpr uint32_t cW1 = 96, cW2 = 120, cW3 = 136, cW4 = 152, kGroupCols = 160;
 // tcgen05.alloc takes a power of two >= 32 columns
 __host__ __device__ constexpr uint32_t tmem_cols(int groups) {
   uint32_t c = 32;
@@ -72,14 +76,16 @@ __host__ __device__ constexpr uint32_t tmem_cols(int groups) {
 }
 
 constexpr int kGroupThreads = 128;
-constexpr int kStRow = 52;  // staged row: 48 floats + 4 pad (row stride = 20 mod 32 banks)
 constexpr uint32_t kMbarLimit = 1u << 20;  // bounded MMA-completion wait (tries of up to 2 us: ~2 s)
 
 template <class P>
 struct TcLayout {
   static constexpr uint32_t a_bytes = 128u * 32u * P::es;  // one A operand plane, K <= 32
-  static constexpr uint32_t stage_bytes = 4u * 16u * kStRow * 4u;  // 16 staged rows per warp
-  static constexpr uint32_t group_bytes = a_bytes * P::planes + stage_bytes + 128;  // + mbarrier, flag
+  // partner operand of the weight-gradient products (an activation tile of up to 40 columns);
+  // 12 KB per plane keeps every M = 64 operand read inside the plane
+  static constexpr uint32_t b_bytes = 12288u;
+  static constexpr int b_planes = P::planes < 2 ? P::planes : 2;
+  static constexpr uint32_t group_bytes = a_bytes * P::planes + b_bytes * b_planes + 128;  // + mbarrier, flag
 };
 
 __device__ __forceinline__ void group_sync(int g) {
@@ -100,10 +106,11 @@ __device__ __forceinline__ void split_bf16(float x, __nv_bfloat16 (&p)[PL]) {
 
 // write K values as row `row` of a K-major no-swizzle tile, one plane per bf16 part; pairs
 // of values are rounded together (one cvt.rn.bf16x2 per pair and part)
-template <class P, int K>
-__device__ __forceinline__ void store_row(uint8_t* planes, int row, const float* v) {
-  constexpr uint32_t sbo = (uint32_t)(K * P::es / 16) * 128u;
-  constexpr uint32_t plane_bytes = 128u * 32u * P::es;
+template <int NPL, int K, uint32_t PLANE_BYTES>
+__device__ __forceinline__ void store_row_planes(uint8_t* planes, int row, const float* v) {
+  constexpr uint32_t sbo = (uint32_t)(K * 2 / 16) * 128u;
+  constexpr uint32_t plane_bytes = PLANE_BYTES;
+  constexpr int kPl = NPL;
 #pragma unroll
   for (int c = 0; c < K / 8; ++c) {
     float r[8];
@@ -111,13 +118,13 @@ __device__ __forceinline__ void store_row(uint8_t* planes, int row, const float*
     for (int q = 0; q < 8; ++q) r[q] = v[8 * c + q];
     const uint32_t off = tc::core_offset((uint32_t)row, (uint32_t)c, 128u, sbo);
 #pragma unroll
-    for (int pl = 0; pl < P::planes; ++pl) {
+    for (int pl = 0; pl < kPl; ++pl) {
       uint32_t w[4];
 #pragma unroll
       for (int q = 0; q < 4; ++q) {
         const __nv_bfloat162 b = __floats2bfloat162_rn(r[2 * q], r[2 * q + 1]);
         w[q] = *reinterpret_cast<const uint32_t*>(&b);
-        if (pl + 1 < P::planes) {
+        if (pl + 1 < kPl) {
           r[2 * q] -= __uint_as_float(w[q] << 16);
           r[2 * q + 1] -= __uint_as_float(w[q] & 0xFFFF0000u);
         }
@@ -125,6 +132,12 @@ __device__ __forceinline__ void store_row(uint8_t* planes, int row, const float*
       *reinterpret_cast<uint4*>(planes + pl * plane_bytes + off) = make_uint4(w[0], w[1], w[2], w[3]);
     }
   }
+}
+// a row of the A operand tile of the decoder phases
+template <class P, int K>
+__device__ __forceinline__ void store_row(uint8_t* planes, int row, const float* v) {
+  static_assert(P::es == 2, "bf16 parts");
+  store_row_planes<P::planes, K, 128u * 32u * P::es>(planes, row, v);
 }
 
 // one element of a weight tile (planes `wplane` bytes apart)
@@ -161,13 +174,41 @@ __device__ __forceinline__ void issue_mma(uint32_t d, uint32_t a0, uint32_t b0, 
   }
 }
 
+// Decoder weight gradients on the tensor core: D[64][N] (+)= sum over the tile's 128 samples
+// of A[s][m] B[s][n], both operands read MN-major from the sample-row tiles the phases write
+// (core-matrix stride along K = the tile's row-group stride, along M/N = 128 bytes).  Part
+// products i + j < SUM, i < APL, j < BPL, smallest first; `acc` false on the first tile.
+template <int APL, int BPL, int SUM, int N>
+__device__ __forceinline__ void issue_mma_dw(uint32_t d, uint32_t a0, uint32_t a_plane, uint32_t a_kstride,
+                                             uint32_t b0, uint32_t b_plane, uint32_t b_kstride, bool acc) {
+  constexpr uint32_t idesc = tc::instr_desc(tc::KIND_BF16, 64, N) | (1u << 15) | (1u << 16);
+#pragma unroll 1
+  for (int s = 0; s < 8; ++s) {  // K = 128 samples, 16 per MMA
+    const uint32_t oa = (uint32_t)s * 2u * a_kstride, ob = (uint32_t)s * 2u * b_kstride;
+#pragma unroll
+    for (int sum = SUM - 1; sum >= 0; --sum)
+#pragma unroll
+      for (int i = 0; i <= sum; ++i) {
+        const int j = sum - i;
+        if (i >= APL || j >= BPL) continue;
+        tc::mma_bf16(d, tc::smem_desc(a0 + i * a_plane + oa, a_kstride, 128u),
+                     tc::smem_desc(b0 + j * b_plane + ob, b_kstride, 128u), idesc, acc ? 1u : 0u);
+        acc = true;
+      }
+  }
+}
+
 // per-group MMA machinery
 struct Group {
   uint8_t* a;  // A operand planes
-  uint64_t* mbar;
+  uint8_t* b;  // partner planes of the weight-gradient products
+  uint64_t* mbar;     // completion of the phase MMAs (issued by thread 0 of the group)
+  uint64_t* mbar_dw;  // completion of the weight-gradient MMAs (issued by thread 32)
   int* abort;
-  uint32_t tcol;   // tensor-memory address of this group's column 0
-  uint32_t phase;  // parity of the next completion
+  uint32_t tcol;      // tensor-memory address of this group's column 0
+  uint32_t phase;     // parity of the next completion on mbar
+  uint32_t phase_dw;  // ... on mbar_dw
+  bool dw_pending;    // weight-gradient MMAs may still read the operand tiles
   int g, gt;
 };
 
@@ -183,6 +224,33 @@ __device__ __forceinline__ void mma_phase_issue(Group& G, uint32_t dcol, const u
     tc::mma_commit(G.mbar);
   }
 }
+// the same, and a second thread issues the weight-gradient products that read the same tiles
+// and commits them to mbar_dw: the phase's result does not wait for them, and the operand
+// tiles are rewritten only after dw_wait
+template <class P, int N, int K, class Extra>
+__device__ __forceinline__ void mma_phase_issue_dw(Group& G, uint32_t dcol, const uint8_t* w, uint32_t wplane,
+                                                   Extra extra) {
+  tc::fence_smem_async();
+  tc::fence_before_sync();
+  group_sync(G.g);
+  tc::fence_after_sync();
+  if (G.gt == 0) {
+    issue_mma<P, N, K>(G.tcol + dcol, tc::smem_u32(G.a), tc::smem_u32(w), wplane);
+    tc::mma_commit(G.mbar);
+  } else if (G.gt == 32) {
+    extra();
+    tc::mma_commit(G.mbar_dw);
+  }
+  G.dw_pending = true;
+}
+// every thread of the group: bounded wait until the weight-gradient MMAs are done with the tiles
+__device__ __forceinline__ void dw_wait(Group& G) {
+  if (!G.dw_pending) return;
+  if (!tc::mbar_wait(G.mbar_dw, G.phase_dw, kMbarLimit)) *reinterpret_cast<volatile int*>(G.abort) = 1;
+  G.phase_dw ^= 1u;
+  G.dw_pending = false;
+  tc::fence_after_sync();
+}
 // the issuing thread waits for the MMA (bounded) while the other threads of the group park on
 // the hardware barrier; false (for every thread) if it never completed
 __device__ __forceinline__ bool mma_phase_wait(Group& G) {
@@ -195,79 +263,6 @@ __device__ __forceinline__ bool mma_phase_wait(Group& G) {
 
 __device__ __forceinline__ uint32_t lane_addr(const Group& G, uint32_t col, int warp_g) {
   return G.tcol + col + ((uint32_t)(32 * warp_g) << 16);
-}
-
-// ---- decoder weight gradients from the warp's staged rows ---------------------------
-// The warp's 32 samples are staged 16 at a time; rows: [A-part (rows i) | B-part (cols j)]
-// at offsets ao / bo.  t accumulates the lane's 4x4 tile over both halves.
-template <int NI, int NJ>
-__device__ __forceinline__ void stage_tiles(const float* st, int ao, int bo, float (&t)[4][4], int lane) {
-  constexpr int BJ = NJ / 4;  // column blocks
-  const int i0 = 4 * (lane / BJ), j0 = 4 * (lane % BJ);
-  if (i0 >= NI) return;
-#pragma unroll 4
-  for (int s = 0; s < 16; ++s) {
-    const float4 av = *reinterpret_cast<const float4*>(st + s * kStRow + ao + i0);
-    const float4 bv = *reinterpret_cast<const float4*>(st + s * kStRow + bo + j0);
-    const float ar[4] = {av.x, av.y, av.z, av.w}, br[4] = {bv.x, bv.y, bv.z, bv.w};
-#pragma unroll
-    for (int x = 0; x < 4; ++x)
-#pragma unroll
-      for (int y = 0; y < 4; ++y) t[x][y] = fmaf(ar[x], br[y], t[x][y]);
-  }
-}
-template <int NI, int NJ>
-__device__ __forceinline__ void flush_tiles(const float (&t)[4][4], float* acc, int accoff, int ldw, int jmax,
-                                            int lane) {
-  constexpr int BJ = NJ / 4;
-  const int i0 = 4 * (lane / BJ), j0 = 4 * (lane % BJ);
-  if (i0 >= NI) return;
-  const int rot = (threadIdx.x >> 5) & 3;  // the group's warps flush in rotated order
-#pragma unroll
-  for (int q = 0; q < 4; ++q) {
-    const int x = (q + rot) & 3;
-#pragma unroll
-    for (int y = 0; y < 4; ++y)
-      if (j0 + y < jmax) atomicAdd(acc + accoff + (i0 + x) * ldw + j0 + y, t[x][y]);
-  }
-}
-// column sum of the staged A-part (a bias gradient): lane owns column `col`
-__device__ __forceinline__ float stage_colsum(const float* st, int ao, int col) {
-  float s = 0.f;
-#pragma unroll 8
-  for (int r = 0; r < 16; ++r) s += st[r * kStRow + ao + col];
-  return s;
-}
-
-// lanes [16h, 16h+16) write their rows (KA values at 0, KB values at KA)
-template <int KA, int KB>
-__device__ __forceinline__ void stage_pair(float* st, int lane, int half, const float* va, const float* vb) {
-  if ((lane >> 4) != half) return;
-  float* rw = st + (lane & 15) * kStRow;
-#pragma unroll
-  for (int q = 0; q < KA / 4; ++q)
-    *reinterpret_cast<float4*>(rw + 4 * q) = make_float4(va[4 * q], va[4 * q + 1], va[4 * q + 2], va[4 * q + 3]);
-#pragma unroll
-  for (int q = 0; q < KB / 4; ++q)
-    *reinterpret_cast<float4*>(rw + KA + 4 * q) = make_float4(vb[4 * q], vb[4 * q + 1], vb[4 * q + 2], vb[4 * q + 3]);
-}
-
-// dW (+)= sum over the warp's 32 samples of a (x) b, plus the column sums of a (bias)
-template <int KA, int KB, int NI, int NJ>
-__device__ __forceinline__ void warp_weight_grad(float* st, int lane, const float* va, const float* vb, float* acc,
-                                                 int woff, int ldw, int jmax, int boff, int bcols) {
-  float t[4][4] = {};
-  float bsum = 0.f;
-#pragma unroll 1
-  for (int half = 0; half < 2; ++half) {
-    stage_pair<KA, KB>(st, lane, half, va, vb);
-    __syncwarp();
-    stage_tiles<NI, NJ>(st, 0, KA, t, lane);
-    bsum += stage_colsum(st, 0, lane % bcols);
-    __syncwarp();
-  }
-  flush_tiles<NI, NJ>(t, acc, woff, ldw, jmax, lane);
-  if (lane < bcols) atomicAdd(acc + boff + lane, bsum);
 }
 
 // ---- gather / scatter -------------------------------------------------------------------
@@ -423,9 +418,12 @@ __global__ void __launch_bounds__(GR * kGroupThreads, 1) render_tc_kernel(Render
   uint8_t* gmem = gbase + (size_t)gi * L::group_bytes;
   Group G;
   G.a = gmem;
-  float* stage = reinterpret_cast<float*>(gmem + L::a_bytes * P::planes) + warp_g * 16 * kStRow;
-  G.mbar = reinterpret_cast<uint64_t*>(gmem + L::a_bytes * P::planes + L::stage_bytes);
-  G.abort = reinterpret_cast<int*>(G.mbar + 1);
+  G.b = gmem + L::a_bytes * P::planes;
+  G.mbar = reinterpret_cast<uint64_t*>(gmem + L::a_bytes * P::planes + L::b_bytes * L::b_planes);
+  G.mbar_dw = G.mbar + 1;
+  G.abort = reinterpret_cast<int*>(G.mbar + 2);
+  G.phase_dw = 0;
+  G.dw_pending = false;
   G.g = gi;
   G.gt = gt;
   G.phase = 0;
@@ -463,6 +461,7 @@ __global__ void __launch_bounds__(GR * kGroupThreads, 1) render_tc_kernel(Render
   for (int i = tid; i < GR * kMlpPad; i += blockDim.x) gacc[i] = 0.f;
   if (gt == 0) {
     tc::mbar_init(G.mbar, 1);
+    tc::mbar_init(G.mbar_dw, 1);
     *G.abort = 0;
   }
   static_assert(tmem_cols(GR) <= 512, "tensor memory holds 512 columns");
@@ -491,6 +490,7 @@ __global__ void __launch_bounds__(GR * kGroupThreads, 1) render_tc_kernel(Render
   float l_rgb = 0.f, l_d = 0.f, l_sdf = 0.f, l_fs = 0.f, g_kappa = 0.f;
   const int row = gt;  // tile row of this thread's sample
   bool alive = true;
+  bool dw_acc = false;  // the weight-gradient accumulators hold a first tile (accumulate from then on)
 
   for (int quad = blockIdx.x * GR + gi; quad * 4 < a.R && alive; quad += gridDim.x * GR) {
     const int ray = quad * 4 + warp_g;
@@ -531,6 +531,7 @@ __global__ void __launch_bounds__(GR * kGroupThreads, 1) render_tc_kernel(Render
 #pragma unroll
         for (int k = 0; k < kZ; ++k) z[k] = 0.f;
       }
+      dw_wait(G);
       store_row<P, 16>(G.a, row, z);
       mma_phase_issue<P, 32, 16>(G, cD1, wt0 + wOff<P>(0), wplane);
       if (put) put_fields<kFz, 16>(sp, ss, z);
@@ -762,6 +763,7 @@ __global__ void __launch_bounds__(GR * kGroupThreads, 1) render_tc_kernel(Render
           for (int k = 0; k < kZ; ++k) z[k] = 0.f;
         }
         // recompute the decoders (the same four phases as the forward)
+        dw_wait(G);
         store_row<P, 16>(G.a, row, z);
         mma_phase_issue<P, 32, 16>(G, cD1, wt0 + wOff<P>(0), wplane);
         if (!(alive = mma_phase_wait(G))) break;
@@ -801,75 +803,93 @@ __global__ void __launch_bounds__(GR * kGroupThreads, 1) render_tc_kernel(Render
       for (int k = 0; k < kKD; ++k) dp[k] = 0.f;
 #pragma unroll
       for (int k = 0; k < 3; ++k) dp[k] = valid ? wj * gc[k] * c3[k] * (1.0f - c3[k]) : 0.f;
+      dw_wait(G);
       store_row<P, kKD>(G.a, row, dp);
-      // --- b4: da2 = dpre W4  (overlap: dW4, db4 from dpre and a2) ---
-      mma_phase_issue<P, 32, kKD>(G, cX, wt0 + wOff<P>(4), wplane);
-      {  // dW4[3][32] (+)= dpre (x) a2 (column `lane`), db4
-        float w4[3] = {0.f, 0.f, 0.f}, db4 = 0.f;
-#pragma unroll 1
-        for (int half = 0; half < 2; ++half) {
-          stage_pair<4, 32>(stage, lane, half, dp, v);
-          __syncwarp();
-#pragma unroll 4
-          for (int s2 = 0; s2 < 16; ++s2) {
-            const float* rw = stage + s2 * kStRow;
-            const float a2v = rw[4 + lane];
-            w4[0] = fmaf(rw[0], a2v, w4[0]);
-            w4[1] = fmaf(rw[1], a2v, w4[1]);
-            w4[2] = fmaf(rw[2], a2v, w4[2]);
-            db4 += rw[lane & 3];
-          }
-          __syncwarp();
-        }
+      // --- b4: da2 = dpre W4;  dW4^T, db4 (+)= [a2 | 1]^T dpre on the tensor core ---
+      {
+        float ab[40];
 #pragma unroll
-        for (int q = 0; q < 3; ++q) atomicAdd(macc + oW4 + q * kH2 + lane, w4[q]);
-        if (lane < 3) atomicAdd(macc + ob4 + lane, db4);
+        for (int k = 0; k < 32; ++k) ab[k] = v[k];
+        ab[32] = 1.f;
+#pragma unroll
+        for (int k = 33; k < 40; ++k) ab[k] = 0.f;
+        store_row_planes<L::b_planes, 40, L::b_bytes>(G.b, row, ab);
       }
+      mma_phase_issue_dw<P, 32, kKD>(G, cXb, wt0 + wOff<P>(4), wplane, [&] {
+        issue_mma_dw<L::b_planes, P::planes, P::planes, 8>(G.tcol + cW4, tc::smem_u32(G.b), L::b_bytes, 5u * 128u,
+                                                           tc::smem_u32(G.a), L::a_bytes, 2u * 128u, dw_acc);
+      });
       if (!(alive = mma_phase_wait(G))) break;
-      tc::tmem_ld32(lane_addr(G, cX, warp_g), v);
+      tc::tmem_ld32(lane_addr(G, cXb, warp_g), v);
       tc::tmem_ld_wait();
 #pragma unroll
       for (int k = 0; k < 32; ++k) v[k] = ((mask2 >> k) & 1u) ? v[k] : 0.f;  // dy2
+      dw_wait(G);
       store_row<P, 32>(G.a, row, v);
-      // --- b3: dh = dy2 W3  (overlap: dW3, db3 from dy2 and h) ---
-      mma_phase_issue<P, 16, 32>(G, cY, wt0 + wOff<P>(5), wplane);
-      warp_weight_grad<32, 16, 32, 16>(stage, lane, v, h, macc, oW3, kHF, kHF, ob3, 32);  // dW3, db3
+      h[15] = 1.f;  // ones column: the bias gradient db3 lands in column 15 of dW3
+      store_row_planes<L::b_planes, 16, L::b_bytes>(G.b, row, h);
+      // --- b3: dh = dy2 W3;  dW3, db3 (+)= dy2^T [h | 1] ---
+      mma_phase_issue_dw<P, 16, 32>(G, cYb, wt0 + wOff<P>(5), wplane, [&] {
+        issue_mma_dw<P::planes, L::b_planes, P::planes, 16>(G.tcol + cW3, tc::smem_u32(G.a), L::a_bytes, 4u * 128u,
+                                                            tc::smem_u32(G.b), L::b_bytes, 2u * 128u, dw_acc);
+      });
       if (!(alive = mma_phase_wait(G))) break;
-      tc::tmem_ld16(lane_addr(G, cY, warp_g), u);
+      tc::tmem_ld16(lane_addr(G, cYb, warp_g), u);
       tc::tmem_ld_wait();
       float dout[16];
       dout[0] = valid ? pick_tc(dphi, j) : 0.f;
 #pragma unroll
       for (int k = 1; k < 16; ++k) dout[k] = u[k - 1];
+      dw_wait(G);
       store_row<P, 16>(G.a, row, dout);
-      // --- b2: da1 = dout W2  (overlap: dW2, db2 from dout and a1) ---
-      mma_phase_issue<P, 32, 16>(G, cX, wt0 + wOff<P>(6), wplane);
       uint32_t mask1 = 0;
       {
-        float a1[32];
+        float ab[40];
         if (sp != nullptr) {
-          get_fields<kFa1, 32>(sp, ss, get, a1);
+          get_fields<kFa1, 32>(sp, ss, get, ab);
         } else {
+          float a1[32];
           tc::tmem_ld32(lane_addr(G, cD1, warp_g), a1);
           tc::tmem_ld_wait();
 #pragma unroll
-          for (int k = 0; k < 32; ++k) a1[k] = fmaxf(a1[k] + b1[k], 0.f);
+          for (int k = 0; k < 32; ++k) ab[k] = fmaxf(a1[k] + b1[k], 0.f);
         }
 #pragma unroll
-        for (int k = 0; k < 32; ++k) mask1 |= (a1[k] > 0.f ? 1u : 0u) << k;
-        warp_weight_grad<16, 32, 16, 32>(stage, lane, dout, a1, macc, oW2, kH1, kH1, ob2, 16);  // dW2, db2
+        for (int k = 0; k < 32; ++k) mask1 |= (ab[k] > 0.f ? 1u : 0u) << k;
+        ab[32] = 1.f;
+#pragma unroll
+        for (int k = 33; k < 40; ++k) ab[k] = 0.f;
+        store_row_planes<L::b_planes, 40, L::b_bytes>(G.b, row, ab);
       }
+      // --- b2: da1 = dout W2;  dW2^T, db2 (+)= [a1 | 1]^T dout ---
+      mma_phase_issue_dw<P, 32, 16>(G, cXb, wt0 + wOff<P>(6), wplane, [&] {
+        issue_mma_dw<L::b_planes, P::planes, P::planes, 16>(G.tcol + cW2, tc::smem_u32(G.b), L::b_bytes, 5u * 128u,
+                                                            tc::smem_u32(G.a), L::a_bytes, 2u * 128u, dw_acc);
+      });
       if (!(alive = mma_phase_wait(G))) break;
-      tc::tmem_ld32(lane_addr(G, cX, warp_g), v);
+      tc::tmem_ld32(lane_addr(G, cXb, warp_g), v);
       tc::tmem_ld_wait();
 #pragma unroll
       for (int k = 0; k < 32; ++k) v[k] = ((mask1 >> k) & 1u) ? v[k] : 0.f;  // dy1
+      dw_wait(G);
       store_row<P, 32>(G.a, row, v);
-      // --- b1: dz = dy1 W1  (overlap: dW1, db1 from dy1 and z) ---
-      mma_phase_issue<P, 16, 32>(G, cY, wt0 + wOff<P>(7), wplane);
-      warp_weight_grad<32, 16, 32, 16>(stage, lane, v, z, macc, oW1, kZ, kZ, ob1, 32);  // dW1, db1
+      {
+        float zb[24];
+#pragma unroll
+        for (int k = 0; k < 16; ++k) zb[k] = z[k];
+        zb[16] = 1.f;
+#pragma unroll
+        for (int k = 17; k < 24; ++k) zb[k] = 0.f;
+        store_row_planes<L::b_planes, 24, L::b_bytes>(G.b, row, zb);
+      }
+      // --- b1: dz = dy1 W1;  dW1, db1 (+)= dy1^T [z | 1] ---
+      mma_phase_issue_dw<P, 16, 32>(G, cYb, wt0 + wOff<P>(7), wplane, [&] {
+        issue_mma_dw<P::planes, L::b_planes, P::planes, 24>(G.tcol + cW1, tc::smem_u32(G.a), L::a_bytes, 4u * 128u,
+                                                            tc::smem_u32(G.b), L::b_bytes, 3u * 128u, dw_acc);
+      });
       if (!(alive = mma_phase_wait(G))) break;
-      tc::tmem_ld16(lane_addr(G, cY, warp_g), u);
+      dw_acc = true;
+      tc::tmem_ld16(lane_addr(G, cYb, warp_g), u);
       tc::tmem_ld_wait();
       scatter_dz(a.g, a.grad, x, u, valid);
     }
@@ -891,6 +911,33 @@ __global__ void __launch_bounds__(GR * kGroupThreads, 1) render_tc_kernel(Render
   if (BWD) {
     g_kappa = warp_sum(g_kappa);
     if (lane == 0) atomicAdd(acc + oKappa, g_kappa);
+    dw_wait(G);
+    if (alive && dw_acc && *reinterpret_cast<volatile int*>(G.abort) == 0) {
+      // the group's weight-gradient accumulators: warp w holds rows 16 w .. 16 w + 15 of every
+      // M = 64 product in its lanes 0..15 (rows 32.. are the bias rows or unused)
+      float d1[32], d2[32];
+      tc::tmem_ld32(lane_addr(G, cW1, warp_g), d1);  // cW1 .. cW1 + 31: dW1 (24) | dW2^T (first 8)
+      tc::tmem_ld32(lane_addr(G, cW1 + 32, warp_g), d2);  // dW2^T (last 8) | dW3 (16) | dW4^T (8)
+      tc::tmem_ld_wait();
+      const int m = 16 * warp_g + lane;  // D row held by this lane
+      if (lane < 16 && m < 32) {
+#pragma unroll
+        for (int n = 0; n < 16; ++n) macc[oW1 + m * kZ + n] += d1[n];  // dW1[m][n]
+        macc[ob1 + m] += d1[16];                                       // db1[m]
+#pragma unroll
+        for (int n = 0; n < 16; ++n) macc[oW2 + n * kH1 + m] += (n < 8 ? d1[24 + n] : d2[n - 8]);  // dW2[n][m]
+#pragma unroll
+        for (int n = 0; n < 15; ++n) macc[oW3 + m * kHF + n] += d2[8 + n];  // dW3[m][n]
+        macc[ob3 + m] += d2[8 + 15];                                      // db3[m]
+#pragma unroll
+        for (int n = 0; n < 3; ++n) macc[oW4 + n * kH2 + m] += d2[24 + n];  // dW4[n][m]
+      } else if (lane == 0 && m == 32) {  // bias rows of the transposed products
+#pragma unroll
+        for (int n = 0; n < 16; ++n) macc[ob2 + n] += (n < 8 ? d1[24 + n] : d2[n - 8]);
+#pragma unroll
+        for (int n = 0; n < 3; ++n) macc[ob4 + n] += d2[24 + n];
+      }
+    }
   }
   if (!alive && gt == 0) {
     atomicOr(a.status, 2);
