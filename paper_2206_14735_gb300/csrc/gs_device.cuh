@@ -55,6 +55,7 @@ struct Cell {
   long long vtx;  // flat index of the base vertex (x fastest)
   float f[3];     // in-cell coordinates
   unsigned clamped;  // bit a set when axis a was clamped to the grid box
+  int idx[3];     // base vertex per axis
 };
 
 // Cell of x at level l: u = (x - origin) / v decided in binary32 (round-to-nearest),
@@ -80,6 +81,8 @@ __device__ __forceinline__ Cell locate(const GridDesc& g, int l, const float x[3
     c.f[a] = __fsub_rn(u, (float)i);
   }
   c.vtx = ((long long)idx[2] * g.dims[l][1] + idx[1]) * g.dims[l][0] + idx[0];
+#pragma unroll
+  for (int a = 0; a < 3; ++a) c.idx[a] = idx[a];
   return c;
 }
 

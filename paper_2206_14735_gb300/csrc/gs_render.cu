@@ -142,6 +142,36 @@ __global__ void voxel_index_kernel(GridDesc g, const float* __restrict__ xq, int
 
 using namespace gs;
 
+// cuTensorMapEncodeTiled from the driver (the library links only the runtime)
+typedef CUresult (*EncodeTiledFn)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
+                                  const cuuint64_t*, const cuuint32_t*, const cuuint32_t*, CUtensorMapInterleave,
+                                  CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+static EncodeTiledFn encode_tiled() {
+  static EncodeTiledFn fn = [] {
+    void* p = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) != cudaSuccess ||
+        q != cudaDriverEntryPointSuccess)
+      p = nullptr;
+    return reinterpret_cast<EncodeTiledFn>(p);
+  }();
+  return fn;
+}
+
+// 2D view [nz * ny][nx * 4] of grid level l with a box of 2 vertices x 4 features, one row high
+static bool encode_level_map(const gs_ctx* ctx, const float* theta, int l, CUtensorMap* m) {
+  EncodeTiledFn fn = encode_tiled();
+  if (!fn) return false;
+  const GridDesc& g = ctx->grid;
+  const cuuint64_t dims[2] = {(cuuint64_t)g.dims[l][0] * 4, (cuuint64_t)g.dims[l][1] * g.dims[l][2]};
+  const cuuint64_t strides[1] = {(cuuint64_t)g.dims[l][0] * 16};
+  const cuuint32_t box[2] = {8, 1};
+  const cuuint32_t es[2] = {1, 1};
+  return fn(m, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, const_cast<float*>(theta + g.off[l]), dims, strides, box, es,
+            CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+            CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
 gs_status gs_launch_render(const gs_ctx* ctx, const float* theta, const uint16_t* theta_bf16, const gs_batch* b,
                            const float* dloss, float* grad, float* rgb_hat, float* d_hat, float* wsum, int mode,
                            cudaStream_t st) {
@@ -168,6 +198,9 @@ gs_status gs_launch_render(const gs_ctx* ctx, const float* theta, const uint16_t
   a.d_hat = d_hat;
   a.wsum = wsum;
   a.status = ctx->status;
+  if (ctx->cfg.precision != GS_PREC_BF16)
+    for (int q = 0; q < 2; ++q)
+      if (!encode_level_map(ctx, theta, 2 + q, &a.tmap[q])) return GS_ERR_CUDA;
   a.store = ctx->store;
   a.w_out = b->w;
   a.store_stride = (long long)ctx->cfg.max_rays * (ctx->cfg.n_strat + ctx->cfg.n_guided);

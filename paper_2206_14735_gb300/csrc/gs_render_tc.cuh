@@ -20,6 +20,7 @@
 // accumulated in shared memory).
 #pragma once
 #include "gs_internal.h"
+#include <cuda.h>
 #include <cuda_bf16.h>
 
 #include "gs_tc.cuh"
@@ -204,10 +205,12 @@ struct Group {
   uint8_t* b;  // partner planes of the weight-gradient products
   uint64_t* mbar;     // completion of the phase MMAs (issued by thread 0 of the group)
   uint64_t* mbar_dw;  // completion of the weight-gradient MMAs (issued by thread 32)
+  uint64_t* mbar_tma; // completion of the fine-level TMA gathers (armed by thread 0)
   int* abort;
   uint32_t tcol;      // tensor-memory address of this group's column 0
   uint32_t phase;     // parity of the next completion on mbar
   uint32_t phase_dw;  // ... on mbar_dw
+  uint32_t phase_tma; // ... on mbar_tma
   bool dw_pending;    // weight-gradient MMAs may still read the operand tiles
   int g, gt;
 };
@@ -270,9 +273,22 @@ __device__ __forceinline__ uint32_t lane_addr(const Group& G, uint32_t col, int 
 template <bool BF16GRID>
 __device__ __forceinline__ void gather_z(const GridDesc& g, const float* __restrict__ theta,
                                          const uint16_t* __restrict__ theta_bf16, const float x[3], float z[kZ]) {
+  // cells of every level first, and an L2 prefetch of each x-adjacent corner pair, so that the
+  // four levels' loads below overlap instead of taking four memory round trips in sequence
+  Cell cs[kLevels];
 #pragma unroll
   for (int l = 0; l < kLevels; ++l) {
-    const Cell c = locate(g, l, x);
+    cs[l] = locate(g, l, x);
+    const char* base = BF16GRID ? reinterpret_cast<const char*>(theta_bf16 + g.off[l])
+                                : reinterpret_cast<const char*>(theta + g.off[l]);
+    const int es = BF16GRID ? 8 : 16;  // bytes per vertex
+#pragma unroll
+    for (int k = 0; k < 4; ++k)  // corners k and k + 4 differ only in x
+      asm volatile("prefetch.global.L2 [%0];" ::"l"(base + (cs[l].vtx + corner_offset(g, l, k)) * es));
+  }
+#pragma unroll
+  for (int l = 0; l < kLevels; ++l) {
+    const Cell c = cs[l];
     float w[8];
     corner_weights(c.f, w);
     float4 v[8];
@@ -305,6 +321,75 @@ __device__ __forceinline__ void gather_z(const GridDesc& g, const float* __restr
 // weighted corner vectors are first summed over each run with a segmented shuffle scan and
 // only the run's first lane issues the 16-byte atomics; at the fine levels every lane
 // issues its own.
+// Fine levels (2, 3) through the TMA: every thread of the group issues one tile::gather4 per
+// level for its sample (rows (y,z), (y+1,z), (y,z+1), (y+1,z+1) of the level's 2D view, 2
+// vertices each) into a 128-byte slot.  The slots sit where the group's tiles are not written
+// before the first decoder phase: level 2 in the partner tile, level 3 in the rest of it and in
+// the gaps of the A planes that the 16-column z tile leaves free.
+__device__ __forceinline__ uint32_t fine_slot(uint8_t* ga, uint8_t* gb, int lvl, int gt) {
+  if (lvl == 0) return tc::smem_u32(gb + gt * 128);
+  if (gt < 64) return tc::smem_u32(gb + 16384 + gt * 128);
+  if (gt < 96) return tc::smem_u32(ga + 4096 + (gt - 64) * 128);
+  return tc::smem_u32(ga + 12288 + (gt - 96) * 128);
+}
+constexpr uint32_t kFineTmaBytes = 128u * 2u * 128u;  // per group and round: 128 samples x 2 levels x 128 B
+
+// issue both fine-level gathers of this thread's sample; returns the cells (for the weights)
+__device__ __forceinline__ void fine_gather_issue(const GridDesc& g, const CUtensorMap* tmap, uint8_t* ga, uint8_t* gb,
+                                                  int gt, uint64_t* mbar, const float x[3], Cell (&cs)[2]) {
+  tc::fence_smem_async();  // earlier generic accesses to the slots before the asynchronous writes
+#pragma unroll
+  for (int q = 0; q < 2; ++q) {
+    const int l = 2 + q;
+    cs[q] = locate(g, l, x);
+    const int ny = g.dims[l][1];
+    const int r0 = cs[q].idx[2] * ny + cs[q].idx[1];
+    tc::tma_gather4(fine_slot(ga, gb, q, gt), &tmap[q], 4 * cs[q].idx[0], r0, r0 + 1, r0 + ny, r0 + ny + 1, mbar);
+  }
+}
+// z of the fine levels from this thread's slots (chunk order rotated by lane: no bank conflicts)
+__device__ __forceinline__ void fine_gather_read(const uint8_t* ga, const uint8_t* gb, int gt, const Cell (&cs)[2],
+                                                 float z[kZ]) {
+  const int lane = gt & 31;
+#pragma unroll
+  for (int q = 0; q < 2; ++q) {
+    const uint8_t* slot = q == 0 ? gb + gt * 128
+                                 : (gt < 64 ? gb + 16384 + gt * 128
+                                            : (gt < 96 ? ga + 4096 + (gt - 64) * 128 : ga + 12288 + (gt - 96) * 128));
+    const float f0 = cs[q].f[0], f1 = cs[q].f[1], f2 = cs[q].f[2];
+    float4 s = make_float4(0.f, 0.f, 0.f, 0.f);
+#pragma unroll
+    for (int k = 0; k < 8; ++k) {
+      const int c = (k + lane) & 7;  // 16-byte chunk: row c >> 1 = (by, bz), x-vertex c & 1
+      const int bx = c & 1, by = (c >> 1) & 1, bz = c >> 2;
+      const float w = ((bx ? f0 : 1.0f - f0) * (by ? f1 : 1.0f - f1)) * (bz ? f2 : 1.0f - f2);
+      f4fma(s, w, *reinterpret_cast<const float4*>(slot + c * 16));
+    }
+    z[8 + 4 * q] = s.x;
+    z[9 + 4 * q] = s.y;
+    z[10 + 4 * q] = s.z;
+    z[11 + 4 * q] = s.w;
+  }
+}
+// coarse levels (0, 1) by plain loads (a warp's samples share these cells)
+__device__ __forceinline__ void coarse_gather(const GridDesc& g, const float* __restrict__ theta, const float x[3],
+                                              float z[kZ]) {
+#pragma unroll
+  for (int l = 0; l < 2; ++l) {
+    const Cell c = locate(g, l, x);
+    float w[8];
+    corner_weights(c.f, w);
+    const float4* base = reinterpret_cast<const float4*>(theta + g.off[l]);
+    float4 s = make_float4(0.f, 0.f, 0.f, 0.f);
+#pragma unroll
+    for (int k = 0; k < 8; ++k) f4fma(s, w[k], __ldg(base + c.vtx + corner_offset(g, l, k)));
+    z[4 * l] = s.x;
+    z[4 * l + 1] = s.y;
+    z[4 * l + 2] = s.z;
+    z[4 * l + 3] = s.w;
+  }
+}
+
 __device__ __forceinline__ void scatter_dz(const GridDesc& g, float* grad, const float x[3], const float dz[kZ],
                                            bool valid) {
   const unsigned active = __ballot_sync(0xffffffffu, valid);
@@ -393,14 +478,39 @@ struct RenderTcArgs {
   float* store;
   long long store_stride;
   float* w_out;  // [R][N] rendering weights, written by forward passes when not nullptr
+  // FP32 form: 2D views [nz * ny][nx * 4] of grid levels 2 and 3 for the TMA gathers (a box of
+  // 2 vertices x 4 features; one tile::gather4 brings a cell's 8 corners)
+  CUtensorMap tmap[2];
 };
 
 // fields of one stored sample: z[16] | a1 = ReLU layer-1 output [32] | (phi, h[15]) | a2 [32] | c[3]
 constexpr int kFz = 0, kFa1 = 16, kFout = 48, kFa2 = 64, kFc = 96, kStoreFields = 99;
 static_assert(kStoreFields == kStoreFloatsPerSample, "the store holds every field");
 
+// z of one chunk: every thread of the group takes part (the TMA round counts all 128 slots);
+// invalid samples get z = 0
+template <class P>
+__device__ __forceinline__ void gather_chunk(Group& G, const RenderTcArgs& a, const float x[3], bool valid,
+                                             float z[kZ]) {
+  if constexpr (P::planes > 1) {  // FP32 form: fine levels through the TMA, coarse by plain loads
+    Cell cs[2];
+    fine_gather_issue(a.g, a.tmap, G.a, G.b, G.gt, G.mbar_tma, x, cs);
+    if (valid) coarse_gather(a.g, a.theta, x, z);
+    if (!tc::mbar_wait(G.mbar_tma, G.phase_tma, kMbarLimit)) *reinterpret_cast<volatile int*>(G.abort) = 1;
+    G.phase_tma ^= 1u;
+    if (G.gt == 0) tc::mbar_arrive_expect_tx(G.mbar_tma, kFineTmaBytes);  // armed for the next round
+    fine_gather_read(G.a, G.b, G.gt, cs, z);
+  } else if (valid) {
+    gather_z<true>(a.g, a.theta, a.theta_bf16, x, z);
+  }
+  if (!valid) {
+#pragma unroll
+    for (int k = 0; k < kZ; ++k) z[k] = 0.f;
+  }
+}
+
 template <class P, int NCH, int GR, bool FWD, bool BWD>
-__global__ void __launch_bounds__(GR * kGroupThreads, 1) render_tc_kernel(RenderTcArgs a) {
+__global__ void __launch_bounds__(GR * kGroupThreads, 1) render_tc_kernel(const __grid_constant__ RenderTcArgs a) {
   using L = TcLayout<P>;
   extern __shared__ __align__(1024) uint8_t smem[];
   constexpr uint32_t wplane = wTotal<P>();  // one bf16 part of all weight tiles
@@ -421,8 +531,10 @@ __global__ void __launch_bounds__(GR * kGroupThreads, 1) render_tc_kernel(Render
   G.b = gmem + L::a_bytes * P::planes;
   G.mbar = reinterpret_cast<uint64_t*>(gmem + L::a_bytes * P::planes + L::b_bytes * L::b_planes);
   G.mbar_dw = G.mbar + 1;
-  G.abort = reinterpret_cast<int*>(G.mbar + 2);
+  G.mbar_tma = G.mbar + 2;
+  G.abort = reinterpret_cast<int*>(G.mbar + 3);
   G.phase_dw = 0;
+  G.phase_tma = 0;
   G.dw_pending = false;
   G.g = gi;
   G.gt = gt;
@@ -462,6 +574,9 @@ __global__ void __launch_bounds__(GR * kGroupThreads, 1) render_tc_kernel(Render
   if (gt == 0) {
     tc::mbar_init(G.mbar, 1);
     tc::mbar_init(G.mbar_dw, 1);
+    tc::mbar_init(G.mbar_tma, 1);
+    tc::fence_mbar_init();
+    if (P::planes > 1) tc::mbar_arrive_expect_tx(G.mbar_tma, kFineTmaBytes);  // armed for the first round
     *G.abort = 0;
   }
   static_assert(tmem_cols(GR) <= 512, "tensor memory holds 512 columns");
@@ -523,15 +638,12 @@ __global__ void __launch_bounds__(GR * kGroupThreads, 1) render_tc_kernel(Render
       }
       const bool put = FWD && sp != nullptr && valid;
       float z[kZ];
-      if (valid) {
+      {
         float x[3];
         sample_pos(o, r, t, x);
-        gather_z<(P::planes == 1)>(a.g, a.theta, a.theta_bf16, x, z);
-      } else {
-#pragma unroll
-        for (int k = 0; k < kZ; ++k) z[k] = 0.f;
+        dw_wait(G);  // the TMA slots overlap the partner tile and the A planes
+        gather_chunk<P>(G, a, x, valid, z);
       }
-      dw_wait(G);
       store_row<P, 16>(G.a, row, z);
       mma_phase_issue<P, 32, 16>(G, cD1, wt0 + wOff<P>(0), wplane);
       if (put) put_fields<kFz, 16>(sp, ss, z);
@@ -756,14 +868,9 @@ __global__ void __launch_bounds__(GR * kGroupThreads, 1) render_tc_kernel(Render
         h[15] = 0.f;
         get_fields<kFc, 3>(sp, ss, get, c3);
       } else {
-        if (valid) {
-          gather_z<(P::planes == 1)>(a.g, a.theta, a.theta_bf16, x, z);
-        } else {
-#pragma unroll
-          for (int k = 0; k < kZ; ++k) z[k] = 0.f;
-        }
-        // recompute the decoders (the same four phases as the forward)
         dw_wait(G);
+        gather_chunk<P>(G, a, x, valid, z);
+        // recompute the decoders (the same four phases as the forward)
         store_row<P, 16>(G.a, row, z);
         mma_phase_issue<P, 32, 16>(G, cD1, wt0 + wOff<P>(0), wplane);
         if (!(alive = mma_phase_wait(G))) break;

@@ -106,6 +106,25 @@ __device__ __forceinline__ bool mbar_wait(uint64_t* mbar, uint32_t parity, uint3
   return false;
 }
 
+// arrival of the calling thread that also announces `bytes` of asynchronous copies on this phase
+__device__ __forceinline__ void mbar_arrive_expect_tx(uint64_t* mbar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(mbar)), "r"(bytes) : "memory");
+}
+// mbarrier initialisation visible to the asynchronous (TMA) proxy
+__device__ __forceinline__ void fence_mbar_init() { asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory"); }
+
+// ---- TMA ----------------------------------------------------------------------------------
+// 4 rows (row0..row3) x the tensor map's box width, starting at column `col` (a multiple of
+// 16 bytes), from a 2D tensor map into 4 consecutive box rows at `dst`; completes `bytes` on mbar
+__device__ __forceinline__ void tma_gather4(uint32_t dst, const void* tmap, int col, int row0, int row1, int row2,
+                                            int row3, uint64_t* mbar) {
+  asm volatile(
+      "cp.async.bulk.tensor.2d.shared::cluster.global.tile::gather4.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, "
+      "%4, %5, %6}], [%7];" ::"r"(dst),
+      "l"(reinterpret_cast<uint64_t>(tmap)), "r"(col), "r"(row0), "r"(row1), "r"(row2), "r"(row3), "r"(smem_u32(mbar))
+      : "memory");
+}
+
 // ---- tensor memory -> registers: warp reads its 32 lanes, 16 / 32 consecutive columns ----
 __device__ __forceinline__ void tmem_ld16(uint32_t taddr, float (&v)[16]) {
   uint32_t r[16];
