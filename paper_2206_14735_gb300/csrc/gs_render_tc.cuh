@@ -614,14 +614,24 @@ __global__ void __launch_bounds__(GR * kGroupThreads, 1) render_tc_kernel(const 
     const float o[3] = {a.o[3 * rr], a.o[3 * rr + 1], a.o[3 * rr + 2]};
     const float r[3] = {a.r[3 * rr], a.r[3 * rr + 1], a.r[3 * rr + 2]};
     const float D = has_ray ? a.D[rr] : 0.f;
+    const float I[3] = {a.rgb[3 * rr], a.rgb[3 * rr + 1], a.rgb[3 * rr + 2]};
     float tt[NCH], ph[NCH], col[NCH][3];
+    int clv[NCH];  // sample classes
+    // every per-sample input of the ray up front: one memory round trip instead of one per chunk
+#pragma unroll
+    for (int q = 0; q < NCH; ++q) {
+      const int si = 32 * q + lane;
+      const bool in = has_ray && si < N;
+      tt[q] = in ? a.t[(size_t)rr * N + si] : 0.f;
+      clv[q] = in ? (int)a.cls[(size_t)rr * N + si] : 0;
+    }
 
     // ================= forward: gather, then 4 decoder phases per chunk =================
 #pragma unroll 1
     for (int j = 0; j < NCH && alive; ++j) {
       const int si = 32 * j + lane;
       const bool valid = has_ray && si < N;
-      const float t = valid ? a.t[(size_t)rr * N + si] : 0.f;
+      const float t = pick_tc(tt, j);
       float* sp = a.store != nullptr ? a.store + (size_t)rr * N + si : nullptr;  // this sample's field 0
       const long long ss = a.store_stride;
       if (!FWD && sp != nullptr) {  // stored by the forward pass: no decoder phases here
@@ -745,7 +755,6 @@ __global__ void __launch_bounds__(GR * kGroupThreads, 1) render_tc_kernel(const 
     for (int k = 0; k < 3; ++k) ch[k] = warp_sum(ch[k]);
     dh = warp_sum(dh);
     ws = warp_sum(ws);
-    const float I[3] = {a.rgb[3 * rr], a.rgb[3 * rr + 1], a.rgb[3 * rr + 2]};
     if (FWD && has_ray) {
       if (lane == 0) {
         float e2 = 0.f;
@@ -765,7 +774,7 @@ __global__ void __launch_bounds__(GR * kGroupThreads, 1) render_tc_kernel(const 
       for (int j = 0; j < NCH; ++j) {
         const int si = 32 * j + lane;
         if (si >= N) continue;
-        const int cl = a.cls[(size_t)ray * N + si];
+        const int cl = clv[j];
         const float b = __fsub_rn(D, tt[j]);
         if (cl == CLS_TR) l_sdf += fabsf(ph[j] - b);
         else if (cl == CLS_FS) l_fs += fmaxf(fmaxf(0.f, expf(-a.kappa_fs * ph[j]) - 1.0f), ph[j] - b);
@@ -826,7 +835,7 @@ __global__ void __launch_bounds__(GR * kGroupThreads, 1) render_tc_kernel(const 
       float d = dPh * s_sharp * dsig;
       if (valid) {
         g_kappa = fmaf(dPh * dsig * s_sharp, ph[j], g_kappa);
-        const int cl = a.cls[(size_t)ray * N + si];
+        const int cl = clv[j];
         const float b = __fsub_rn(D, tt[j]);
         if (cl == CLS_TR) {
           const float df = ph[j] - b;
