@@ -199,6 +199,11 @@ __device__ __forceinline__ void issue_mma_dw(uint32_t d, uint32_t a0, uint32_t a
   }
 }
 
+// Part products kept in the weight-gradient MMAs: i + j < 2 in the FP32 form (relative error
+// of a product below 2^-15, against the 1e-4 gradient tolerance), the single product in BF16.
+template <class P>
+constexpr int kDwSum = P::planes > 1 ? 2 : 1;
+
 // per-group MMA machinery
 struct Group {
   uint8_t* a;  // A operand planes
@@ -932,7 +937,7 @@ __global__ void __launch_bounds__(GR * kGroupThreads, 1) render_tc_kernel(const 
         store_row_planes<L::b_planes, 40, L::b_bytes>(G.b, row, ab);
       }
       mma_phase_issue_dw<P, 32, kKD>(G, cXb, wt0 + wOff<P>(4), wplane, [&] {
-        issue_mma_dw<L::b_planes, P::planes, P::planes, 8>(G.tcol + cW4, tc::smem_u32(G.b), L::b_bytes, 5u * 128u,
+        issue_mma_dw<L::b_planes, P::planes, kDwSum<P>, 8>(G.tcol + cW4, tc::smem_u32(G.b), L::b_bytes, 5u * 128u,
                                                            tc::smem_u32(G.a), L::a_bytes, 2u * 128u, dw_acc);
       });
       if (!(alive = mma_phase_wait(G))) break;
@@ -946,7 +951,7 @@ __global__ void __launch_bounds__(GR * kGroupThreads, 1) render_tc_kernel(const 
       store_row_planes<L::b_planes, 16, L::b_bytes>(G.b, row, h);
       // --- b3: dh = dy2 W3;  dW3, db3 (+)= dy2^T [h | 1] ---
       mma_phase_issue_dw<P, 16, 32>(G, cYb, wt0 + wOff<P>(5), wplane, [&] {
-        issue_mma_dw<P::planes, L::b_planes, P::planes, 16>(G.tcol + cW3, tc::smem_u32(G.a), L::a_bytes, 4u * 128u,
+        issue_mma_dw<P::planes, L::b_planes, kDwSum<P>, 16>(G.tcol + cW3, tc::smem_u32(G.a), L::a_bytes, 4u * 128u,
                                                             tc::smem_u32(G.b), L::b_bytes, 2u * 128u, dw_acc);
       });
       if (!(alive = mma_phase_wait(G))) break;
@@ -979,7 +984,7 @@ __global__ void __launch_bounds__(GR * kGroupThreads, 1) render_tc_kernel(const 
       }
       // --- b2: da1 = dout W2;  dW2^T, db2 (+)= [a1 | 1]^T dout ---
       mma_phase_issue_dw<P, 32, 16>(G, cXb, wt0 + wOff<P>(6), wplane, [&] {
-        issue_mma_dw<L::b_planes, P::planes, P::planes, 16>(G.tcol + cW2, tc::smem_u32(G.b), L::b_bytes, 5u * 128u,
+        issue_mma_dw<L::b_planes, P::planes, kDwSum<P>, 16>(G.tcol + cW2, tc::smem_u32(G.b), L::b_bytes, 5u * 128u,
                                                             tc::smem_u32(G.a), L::a_bytes, 2u * 128u, dw_acc);
       });
       if (!(alive = mma_phase_wait(G))) break;
@@ -1000,7 +1005,7 @@ __global__ void __launch_bounds__(GR * kGroupThreads, 1) render_tc_kernel(const 
       }
       // --- b1: dz = dy1 W1;  dW1, db1 (+)= dy1^T [z | 1] ---
       mma_phase_issue_dw<P, 16, 32>(G, cYb, wt0 + wOff<P>(7), wplane, [&] {
-        issue_mma_dw<P::planes, L::b_planes, P::planes, 24>(G.tcol + cW1, tc::smem_u32(G.a), L::a_bytes, 4u * 128u,
+        issue_mma_dw<P::planes, L::b_planes, kDwSum<P>, 24>(G.tcol + cW1, tc::smem_u32(G.a), L::a_bytes, 4u * 128u,
                                                             tc::smem_u32(G.b), L::b_bytes, 3u * 128u, dw_acc);
       });
       if (!(alive = mma_phase_wait(G))) break;
