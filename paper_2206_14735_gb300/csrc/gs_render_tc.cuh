@@ -337,15 +337,16 @@ __device__ __forceinline__ uint32_t fine_slot(uint8_t* ga, uint8_t* gb, int lvl,
   if (gt < 96) return tc::smem_u32(ga + 4096 + (gt - 64) * 128);
   return tc::smem_u32(ga + 12288 + (gt - 96) * 128);
 }
-constexpr uint32_t kFineTmaBytes = 128u * 2u * 128u;  // per group and round: 128 samples x 2 levels x 128 B
+constexpr int kTmaLevels = 1;  // the finest levels that go through the TMA (the rest: plain loads)
+constexpr uint32_t kFineTmaBytes = 128u * kTmaLevels * 128u;  // per group and round: 128 samples x levels x 128 B
 
 // issue both fine-level gathers of this thread's sample; returns the cells (for the weights)
 __device__ __forceinline__ void fine_gather_issue(const GridDesc& g, const CUtensorMap* tmap, uint8_t* ga, uint8_t* gb,
-                                                  int gt, uint64_t* mbar, const float x[3], Cell (&cs)[2]) {
+                                                  int gt, uint64_t* mbar, const float x[3], Cell (&cs)[kTmaLevels]) {
   tc::fence_smem_async();  // earlier generic accesses to the slots before the asynchronous writes
 #pragma unroll
-  for (int q = 0; q < 2; ++q) {
-    const int l = 2 + q;
+  for (int q = 0; q < kTmaLevels; ++q) {
+    const int l = kLevels - kTmaLevels + q;
     cs[q] = locate(g, l, x);
     const int ny = g.dims[l][1];
     const int r0 = cs[q].idx[2] * ny + cs[q].idx[1];
@@ -353,11 +354,12 @@ __device__ __forceinline__ void fine_gather_issue(const GridDesc& g, const CUten
   }
 }
 // z of the fine levels from this thread's slots (chunk order rotated by lane: no bank conflicts)
-__device__ __forceinline__ void fine_gather_read(const uint8_t* ga, const uint8_t* gb, int gt, const Cell (&cs)[2],
-                                                 float z[kZ]) {
+__device__ __forceinline__ void fine_gather_read(const uint8_t* ga, const uint8_t* gb, int gt,
+                                                 const Cell (&cs)[kTmaLevels], float z[kZ]) {
   const int lane = gt & 31;
 #pragma unroll
-  for (int q = 0; q < 2; ++q) {
+  for (int q = 0; q < kTmaLevels; ++q) {
+    const int l = kLevels - kTmaLevels + q;
     const uint8_t* slot = q == 0 ? gb + gt * 128
                                  : (gt < 64 ? gb + 16384 + gt * 128
                                             : (gt < 96 ? ga + 4096 + (gt - 64) * 128 : ga + 12288 + (gt - 96) * 128));
@@ -370,17 +372,17 @@ __device__ __forceinline__ void fine_gather_read(const uint8_t* ga, const uint8_
       const float w = ((bx ? f0 : 1.0f - f0) * (by ? f1 : 1.0f - f1)) * (bz ? f2 : 1.0f - f2);
       f4fma(s, w, *reinterpret_cast<const float4*>(slot + c * 16));
     }
-    z[8 + 4 * q] = s.x;
-    z[9 + 4 * q] = s.y;
-    z[10 + 4 * q] = s.z;
-    z[11 + 4 * q] = s.w;
+    z[4 * l] = s.x;
+    z[4 * l + 1] = s.y;
+    z[4 * l + 2] = s.z;
+    z[4 * l + 3] = s.w;
   }
 }
-// coarse levels (0, 1) by plain loads (a warp's samples share these cells)
+// the other levels by plain loads (a warp's samples share the coarse cells)
 __device__ __forceinline__ void coarse_gather(const GridDesc& g, const float* __restrict__ theta, const float x[3],
                                               float z[kZ]) {
 #pragma unroll
-  for (int l = 0; l < 2; ++l) {
+  for (int l = 0; l < kLevels - kTmaLevels; ++l) {
     const Cell c = locate(g, l, x);
     float w[8];
     corner_weights(c.f, w);
@@ -498,8 +500,8 @@ template <class P>
 __device__ __forceinline__ void gather_chunk(Group& G, const RenderTcArgs& a, const float x[3], bool valid,
                                              float z[kZ]) {
   if constexpr (P::planes > 1) {  // FP32 form: fine levels through the TMA, coarse by plain loads
-    Cell cs[2];
-    fine_gather_issue(a.g, a.tmap, G.a, G.b, G.gt, G.mbar_tma, x, cs);
+    Cell cs[kTmaLevels];
+    fine_gather_issue(a.g, a.tmap + (2 - kTmaLevels), G.a, G.b, G.gt, G.mbar_tma, x, cs);
     if (valid) coarse_gather(a.g, a.theta, x, z);
     if (!tc::mbar_wait(G.mbar_tma, G.phase_tma, kMbarLimit)) *reinterpret_cast<volatile int*>(G.abort) = 1;
     G.phase_tma ^= 1u;
