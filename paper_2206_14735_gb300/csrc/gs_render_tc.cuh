@@ -494,6 +494,17 @@ struct RenderTcArgs {
 constexpr int kFz = 0, kFa1 = 16, kFout = 48, kFa2 = 64, kFc = 96, kStoreFields = 99;
 static_assert(kStoreFields == kStoreFloatsPerSample, "the store holds every field");
 
+// colour c = sigmoid(W4 a2 + b4) on CUDA cores (3 outputs: too narrow for a tensor-core phase)
+__device__ __forceinline__ void colour_out(const float* w4f, const float* b4, const float (&a2)[32], float (&c3)[3]) {
+#pragma unroll
+  for (int n = 0; n < 3; ++n) {
+    float s = b4[n];
+#pragma unroll
+    for (int k = 0; k < 32; ++k) s = fmaf(w4f[32 * n + k], a2[k], s);
+    c3[n] = sigmoidf_(s);
+  }
+}
+
 // z of one chunk: every thread of the group takes part (the TMA round counts all 128 slots);
 // invalid samples get z = 0
 template <class P>
@@ -525,7 +536,8 @@ __global__ void __launch_bounds__(GR * kGroupThreads, 1) render_tc_kernel(const 
   float* acc = reinterpret_cast<float*>(smem + wplane * P::planes);  // [kMlpPad] + loss [kLossPad]
   float* lacc = acc + kMlpPad;
   float* bias = lacc + kLossPad;  // b1[32] b2[16] b3[32] b4[4] kappa
-  uint32_t* tslot = reinterpret_cast<uint32_t*>(bias + 88);
+  float* w4f = bias + 88;         // W4 [3][32] in FP32: the colour output layer runs on CUDA cores
+  uint32_t* tslot = reinterpret_cast<uint32_t*>(w4f + 96);
   float* gacc = reinterpret_cast<float*>(tslot + 4);  // per-group decoder-gradient accumulators [GR][kMlpPad]
   uint8_t* gbase = reinterpret_cast<uint8_t*>(gacc + GR * kMlpPad);
   gbase = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(gbase) + 1023) & ~uintptr_t(1023));
@@ -567,6 +579,7 @@ __global__ void __launch_bounds__(GR * kGroupThreads, 1) render_tc_kernel(const 
       store_w<P>(wt0 + wOff<P>(m), wplane, K, n, k, v);
     }
   }
+  for (int i = tid; i < 96; i += blockDim.x) w4f[i] = mlp[oW4 + i];
   for (int i = tid; i < 88; i += blockDim.x) {
     float v = 0.f;
     if (i < 32) v = mlp[ob1 + i];
@@ -613,6 +626,7 @@ __global__ void __launch_bounds__(GR * kGroupThreads, 1) render_tc_kernel(const 
   const int row = gt;  // tile row of this thread's sample
   bool alive = true;
   bool dw_acc = false;  // the weight-gradient accumulators hold a first tile (accumulate from then on)
+  float w4acc[3] = {0.f, 0.f, 0.f}, b4acc = 0.f;  // this warp's dW4[.][lane] and (lanes < 3) db4[lane]
 
   for (int quad = blockIdx.x * GR + gi; quad * 4 < a.R && alive; quad += gridDim.x * GR) {
     const int ray = quad * 4 + warp_g;
@@ -693,15 +707,9 @@ __global__ void __launch_bounds__(GR * kGroupThreads, 1) render_tc_kernel(const 
       tc::tmem_ld_wait();
 #pragma unroll
       for (int k = 0; k < 32; ++k) v[k] = fmaxf(v[k] + b3[k], 0.f);
-      store_row<P, 32>(G.a, row, v);
-      mma_phase_issue<P, 16, 32>(G, cX, wt0 + wOff<P>(3), wplane);
       if (put) put_fields<kFa2, 32>(sp, ss, v);
-      if (!(alive = mma_phase_wait(G))) break;
-      tc::tmem_ld16(lane_addr(G, cX, warp_g), u);
-      tc::tmem_ld_wait();
       float c3[3];
-#pragma unroll
-      for (int k = 0; k < 3; ++k) c3[k] = sigmoidf_(u[k] + b4[k]);
+      colour_out(w4f, b4, v, c3);
       if (put) put_fields<kFc, 3>(sp, ss, c3);
       // keep per-chunk values in registers (compile-time index via a selector loop)
 #pragma unroll
@@ -909,13 +917,7 @@ __global__ void __launch_bounds__(GR * kGroupThreads, 1) render_tc_kernel(const 
         tc::tmem_ld_wait();
 #pragma unroll
         for (int k = 0; k < 32; ++k) v[k] = fmaxf(v[k] + b3[k], 0.f);
-        store_row<P, 32>(G.a, row, v);
-        mma_phase_issue<P, 16, 32>(G, cX, wt0 + wOff<P>(3), wplane);
-        if (!(alive = mma_phase_wait(G))) break;
-        tc::tmem_ld16(lane_addr(G, cX, warp_g), u);
-        tc::tmem_ld_wait();
-#pragma unroll
-        for (int k = 0; k < 3; ++k) c3[k] = sigmoidf_(u[k] + b4[k]);
+        colour_out(w4f, b4, v, c3);
       }
 #pragma unroll
       for (int k = 0; k < 32; ++k) mask2 |= (v[k] > 0.f ? 1u : 0u) << k;
@@ -926,28 +928,36 @@ __global__ void __launch_bounds__(GR * kGroupThreads, 1) render_tc_kernel(const 
       for (int k = 0; k < kKD; ++k) dp[k] = 0.f;
 #pragma unroll
       for (int k = 0; k < 3; ++k) dp[k] = valid ? wj * gc[k] * c3[k] * (1.0f - c3[k]) : 0.f;
-      dw_wait(G);
-      store_row<P, kKD>(G.a, row, dp);
-      // --- b4: da2 = dpre W4;  dW4^T, db4 (+)= [a2 | 1]^T dpre on the tensor core ---
+      dw_wait(G);  // no tensor-core product reads the tiles now: stage the colour layer's rows there
+      // --- b4 on CUDA cores: da2 = dpre W4 (3 x 32); dW4, db4 (+)= sum over the warp's samples ---
       {
-        float ab[40];
+        // 4 warps x 32 rows x 36 floats = 18 KB from the A planes on (the A and partner planes
+        // are contiguous and hold at least 20 KB in both forms)
+        static_assert(L::a_bytes * P::planes + L::b_bytes * L::b_planes >= 4u * 32u * 36u * 4u, "staging space");
+        float* st = reinterpret_cast<float*>(G.a) + warp_g * (32 * 36);  // row: dpre[3] | 0 | a2[32]
+        float* rw = st + lane * 36;
+        *reinterpret_cast<float4*>(rw) = make_float4(dp[0], dp[1], dp[2], 0.f);
 #pragma unroll
-        for (int k = 0; k < 32; ++k) ab[k] = v[k];
-        ab[32] = 1.f;
+        for (int q = 0; q < 8; ++q)
+          *reinterpret_cast<float4*>(rw + 4 + 4 * q) = make_float4(v[4 * q], v[4 * q + 1], v[4 * q + 2], v[4 * q + 3]);
+        __syncwarp();
+#pragma unroll 4
+        for (int s2 = 0; s2 < 32; ++s2) {
+          const float* r2 = st + s2 * 36;
+          const float a2v = r2[4 + lane];
+          w4acc[0] = fmaf(r2[0], a2v, w4acc[0]);
+          w4acc[1] = fmaf(r2[1], a2v, w4acc[1]);
+          w4acc[2] = fmaf(r2[2], a2v, w4acc[2]);
+          b4acc += r2[lane & 3];
+        }
+        __syncwarp();
 #pragma unroll
-        for (int k = 33; k < 40; ++k) ab[k] = 0.f;
-        store_row_planes<L::b_planes, 40, L::b_bytes>(G.b, row, ab);
+        for (int k = 0; k < 32; ++k) {  // dy2 = mask2 (.) (dpre W4)
+          const float d = fmaf(dp[0], w4f[k], fmaf(dp[1], w4f[32 + k], dp[2] * w4f[64 + k]));
+          v[k] = ((mask2 >> k) & 1u) ? d : 0.f;
+        }
+        group_sync(G.g);  // every warp has read its staged rows before the tiles are rewritten
       }
-      mma_phase_issue_dw<P, 32, kKD>(G, cXb, wt0 + wOff<P>(4), wplane, [&] {
-        issue_mma_dw<L::b_planes, P::planes, kDwSum<P>, 8>(G.tcol + cW4, tc::smem_u32(G.b), L::b_bytes, 5u * 128u,
-                                                           tc::smem_u32(G.a), L::a_bytes, 2u * 128u, dw_acc);
-      });
-      if (!(alive = mma_phase_wait(G))) break;
-      tc::tmem_ld32(lane_addr(G, cXb, warp_g), v);
-      tc::tmem_ld_wait();
-#pragma unroll
-      for (int k = 0; k < 32; ++k) v[k] = ((mask2 >> k) & 1u) ? v[k] : 0.f;  // dy2
-      dw_wait(G);
       store_row<P, 32>(G.a, row, v);
       h[15] = 1.f;  // ones column: the bias gradient db3 lands in column 15 of dW3
       store_row_planes<L::b_planes, 16, L::b_bytes>(G.b, row, h);
@@ -1052,15 +1062,15 @@ __global__ void __launch_bounds__(GR * kGroupThreads, 1) render_tc_kernel(const 
 #pragma unroll
         for (int n = 0; n < 15; ++n) macc[oW3 + m * kHF + n] += d2[8 + n];  // dW3[m][n]
         macc[ob3 + m] += d2[8 + 15];                                      // db3[m]
-#pragma unroll
-        for (int n = 0; n < 3; ++n) macc[oW4 + n * kH2 + m] += d2[24 + n];  // dW4[n][m]
-      } else if (lane == 0 && m == 32) {  // bias rows of the transposed products
+      } else if (lane == 0 && m == 32) {  // bias row of the transposed product
 #pragma unroll
         for (int n = 0; n < 16; ++n) macc[ob2 + n] += (n < 8 ? d1[24 + n] : d2[n - 8]);
-#pragma unroll
-        for (int n = 0; n < 3; ++n) macc[ob4 + n] += d2[24 + n];
       }
     }
+    // the colour layer's gradient, accumulated per warp on CUDA cores
+#pragma unroll
+    for (int n = 0; n < 3; ++n) atomicAdd(macc + oW4 + n * kH2 + lane, w4acc[n]);
+    if (lane < 3) atomicAdd(macc + ob4 + lane, b4acc);
   }
   if (!alive && gt == 0) {
     atomicOr(a.status, 2);
@@ -1084,7 +1094,7 @@ __global__ void __launch_bounds__(GR * kGroupThreads, 1) render_tc_kernel(const 
 template <class P, int GR>
 size_t render_tc_smem() {
   using L = TcLayout<P>;
-  size_t b = wTotal<P>() * P::planes + (kMlpPad + kLossPad + 88 + 4 + GR * kMlpPad) * 4;
+  size_t b = wTotal<P>() * P::planes + (kMlpPad + kLossPad + 88 + 96 + 4 + GR * kMlpPad) * 4;
   b = (b + 1023) & ~size_t(1023);
   return b + (size_t)GR * L::group_bytes + 1024;  // + alignment slack of the dynamic window
 }
