@@ -320,17 +320,11 @@ __device__ __forceinline__ void gather_z(const GridDesc& g, const float* __restr
   }
 }
 
-// Adjoint of the gather: dtheta_l[corner] += w_c dz_l.  A warp's lanes hold consecutive
-// samples of one ray, so the cells they fall in are visited monotonically and equal cells
-// form contiguous runs of lanes.  At the two coarse levels (where runs are long) the 8
-// weighted corner vectors are first summed over each run with a segmented shuffle scan and
-// only the run's first lane issues the 16-byte atomics; at the fine levels every lane
-// issues its own.
-// Fine levels (2, 3) through the TMA: every thread of the group issues one tile::gather4 per
-// level for its sample (rows (y,z), (y+1,z), (y,z+1), (y+1,z+1) of the level's 2D view, 2
-// vertices each) into a 128-byte slot.  The slots sit where the group's tiles are not written
-// before the first decoder phase: level 2 in the partner tile, level 3 in the rest of it and in
-// the gaps of the A planes that the 16-column z tile leaves free.
+// The finest kTmaLevels levels through the TMA: every thread of the group issues one
+// tile::gather4 per level for its sample (rows (y,z), (y+1,z), (y,z+1), (y+1,z+1) of the
+// level's 2D view, 2 vertices each) into a 128-byte slot.  The slots sit where the group's
+// tiles are not written before the first decoder phase: the partner tile, then the gaps of the
+// A planes that the 16-column z tile leaves free.
 __device__ __forceinline__ uint32_t fine_slot(uint8_t* ga, uint8_t* gb, int lvl, int gt) {
   if (lvl == 0) return tc::smem_u32(gb + gt * 128);
   if (gt < 64) return tc::smem_u32(gb + 16384 + gt * 128);
@@ -397,8 +391,15 @@ __device__ __forceinline__ void coarse_gather(const GridDesc& g, const float* __
   }
 }
 
+// Adjoint of the gather: dtheta_l[corner] += w_c dz_l.  A warp's lanes hold consecutive
+// samples of one ray, so the cells they fall in are visited monotonically and equal cells
+// form contiguous runs of lanes.  At the two coarse levels (long runs) the 8 weighted corner
+// vectors are summed over each run through shared memory: every lane stages its 32 values as
+// a row, then lane c walks the 32 rows summing component c (corner c / 4, feature c % 4) and
+// issues one atomic at the end of each run.  At the fine levels every lane issues its own
+// 16-byte atomics.  `st`: this warp's 33 x 36 floats of staging space.
 __device__ __forceinline__ void scatter_dz(const GridDesc& g, float* grad, const float x[3], const float dz[kZ],
-                                           bool valid) {
+                                           bool valid, float* st) {
   const unsigned active = __ballot_sync(0xffffffffu, valid);
   if (active == 0) return;
   const int lane = threadIdx.x & 31;
@@ -409,34 +410,30 @@ __device__ __forceinline__ void scatter_dz(const GridDesc& g, float* grad, const
     corner_weights(cc.f, wc);
     const float4 g4 = valid ? make_float4(dz[4 * l], dz[4 * l + 1], dz[4 * l + 2], dz[4 * l + 3])
                             : make_float4(0.f, 0.f, 0.f, 0.f);
-    float4* gl = reinterpret_cast<float4*>(grad + g.off[l]);
     if (l < 2) {
-      const long long key = valid ? cc.vtx : -1 - (long long)lane;  // invalid lanes: singleton runs
-      float4 v[8];
+      const int key = valid ? (int)cc.vtx : -1;  // the coarse levels have fewer than 2^31 vertices
+      const int next = __shfl_down_sync(0xffffffffu, key, 1);
+      const unsigned ends = __ballot_sync(0xffffffffu, lane == 31 || next != key || key < 0);  // a run's last lane
+      float* rw = st + lane * 36;
 #pragma unroll
-      for (int k = 0; k < 8; ++k) v[k] = f4scale(g4, wc[k]);
-#pragma unroll
-      for (int o = 1; o < 32; o <<= 1) {
-        const long long kk = __shfl_down_sync(0xffffffffu, key, o);
-        const bool take = (lane + o < 32) && kk == key;
-#pragma unroll
-        for (int k = 0; k < 8; ++k) {
-          const float tx = __shfl_down_sync(0xffffffffu, v[k].x, o), ty = __shfl_down_sync(0xffffffffu, v[k].y, o);
-          const float tz = __shfl_down_sync(0xffffffffu, v[k].z, o), tw = __shfl_down_sync(0xffffffffu, v[k].w, o);
-          if (take) {
-            v[k].x += tx;
-            v[k].y += ty;
-            v[k].z += tz;
-            v[k].w += tw;
-          }
+      for (int k = 0; k < 8; ++k) *reinterpret_cast<float4*>(rw + 4 * k) = f4scale(g4, wc[k]);
+      st[32 * 36 + lane] = __int_as_float(key);  // the keys after the rows
+      __syncwarp();
+      float* gl = grad + g.off[l];
+      const long long coff = corner_offset(g, l, lane >> 2);
+      float acc = 0.f;
+#pragma unroll 4
+      for (int i = 0; i < 32; ++i) {
+        acc += st[i * 36 + lane];
+        if ((ends >> i) & 1u) {  // uniform: the run holding row i ends at row i
+          const int ki = __float_as_int(st[32 * 36 + i]);
+          if (ki >= 0) atomicAdd(gl + 4 * ((long long)ki + coff) + (lane & 3), acc);
+          acc = 0.f;
         }
       }
-      const long long prev = __shfl_up_sync(0xffffffffu, key, 1);
-      if (valid && (lane == 0 || prev != key)) {
-#pragma unroll
-        for (int k = 0; k < 8; ++k) atomicAdd(gl + cc.vtx + corner_offset(g, l, k), v[k]);
-      }
+      __syncwarp();
     } else if (valid) {
+      float4* gl = reinterpret_cast<float4*>(grad + g.off[l]);
 #pragma unroll
       for (int k = 0; k < 8; ++k) atomicAdd(gl + cc.vtx + corner_offset(g, l, k), f4scale(g4, wc[k]));
     }
@@ -1024,7 +1021,9 @@ __global__ void __launch_bounds__(GR * kGroupThreads, 1) render_tc_kernel(const 
       dw_acc = true;
       tc::tmem_ld16(lane_addr(G, cYb, warp_g), u);
       tc::tmem_ld_wait();
-      scatter_dz(a.g, a.grad, x, u, valid);
+      dw_wait(G);  // the tiles' space holds the scatter's staging rows
+      scatter_dz(a.g, a.grad, x, u, valid, reinterpret_cast<float*>(G.a) + warp_g * (33 * 36));
+      group_sync(G.g);  // every warp is done with its rows before the tiles are rewritten
     }
   }
 
