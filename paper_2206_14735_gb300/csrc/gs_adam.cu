@@ -37,6 +37,7 @@ __global__ void __launch_bounds__(256) adam_kernel(AdamArgs a) {
     a.p[i] = p;
     __stcs(a.m + i, m);
     __stcs(a.v + i, v);
+    // the gradient is left zero for the next step; entries no sample touched are zero already
     if (g.x != 0.f || g.y != 0.f || g.z != 0.f || g.w != 0.f) __stcs(a.g + i, zero);
     if (a.bf16 != nullptr && grid) {
       const __nv_bfloat162 lo = __floats2bfloat162_rn(p.x, p.y), hi = __floats2bfloat162_rn(p.z, p.w);
