@@ -20,14 +20,21 @@ __global__ void __launch_bounds__(256) finalize_kernel(const float* loss_part, c
                                                        const int* counts, int R, float l0, float l1, float l2,
                                                        float l3, float l4, float* loss, float* gmlp) {
   // decoder gradients: block b owns entries [32b, 32b + 32); warp w sums rows w, w + 8, ...
+  // with four independent partial sums (the loads of a warp overlap), combined in a fixed order
   __shared__ float part[8][33];
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
   const int i = blockIdx.x * 32 + lane;
   if (gmlp) {
-    float s = 0.f;
-    if (i < GS_MLP_PARAMS)
-      for (int p = wid; p < nparts; p += 8) s += mlp_part[(size_t)p * kMlpPad + i];
-    part[wid][lane] = s;
+    float s[4] = {0.f, 0.f, 0.f, 0.f};
+    if (i < GS_MLP_PARAMS) {
+      int p = wid;
+      for (; p + 24 < nparts; p += 32) {
+#pragma unroll
+        for (int q = 0; q < 4; ++q) s[q] += mlp_part[(size_t)(p + 8 * q) * kMlpPad + i];
+      }
+      for (int q = 0; p < nparts; p += 8, q = (q + 1) & 3) s[q] += mlp_part[(size_t)p * kMlpPad + i];
+    }
+    part[wid][lane] = (s[0] + s[1]) + (s[2] + s[3]);
     __syncthreads();
     if (wid == 0 && i < GS_MLP_PARAMS) {
       float t = 0.f;
@@ -36,19 +43,28 @@ __global__ void __launch_bounds__(256) finalize_kernel(const float* loss_part, c
       gmlp[i] += t;
     }
   }
+  // losses (FP64): lane l of warp 0 sums rows l, l + 32, ... of every term, then a warp sum
   if (loss && blockIdx.x == 0 && threadIdx.x < 32) {
-    const int k = threadIdx.x;
-    double s = 0.0;
-    if (k < 5)
-      for (int p = 0; p < nparts; ++p) s += (double)loss_part[(size_t)p * kLossPad + k];
-    const double den[5] = {(double)R, (double)counts[0], (double)counts[1], (double)counts[2], (double)counts[3]};
-    double v = (k < 5 && den[k < 5 ? k : 0] > 0) ? s / den[k < 5 ? k : 0] : 0.0;
-    const double lam[5] = {l0, l1, l2, l3, l4};
-    double tot = (k < 5) ? lam[k] * v : 0.0;
+    double s[5] = {0.0, 0.0, 0.0, 0.0, 0.0};
+    for (int p = lane; p < nparts; p += 32)
 #pragma unroll
-    for (int o = 16; o > 0; o >>= 1) tot += __shfl_xor_sync(0xffffffffu, tot, o);
-    if (k < 5) loss[k] = (float)v;
-    if (k == 5) loss[5] = (float)tot;
+      for (int k = 0; k < 5; ++k) s[k] += (double)loss_part[(size_t)p * kLossPad + k];
+#pragma unroll
+    for (int k = 0; k < 5; ++k)
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) s[k] += __shfl_xor_sync(0xffffffffu, s[k], o);
+    if (lane == 0) {
+      const double den[5] = {(double)R, (double)counts[0], (double)counts[1], (double)counts[2], (double)counts[3]};
+      const double lam[5] = {l0, l1, l2, l3, l4};
+      double tot = 0.0;
+#pragma unroll
+      for (int k = 0; k < 5; ++k) {
+        const double v = den[k] > 0 ? s[k] / den[k] : 0.0;
+        loss[k] = (float)v;
+        tot += lam[k] * v;
+      }
+      loss[5] = (float)tot;
+    }
   }
 }
 
