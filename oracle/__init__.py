@@ -87,6 +87,8 @@ def lib():
             L.oc_query_sdf.argtypes = [vp, vp, vp, i32, vp, vp]
             L.oc_query_sdf_backward.restype = None
             L.oc_query_sdf_backward.argtypes = [vp, vp, vp, i32, vp, vp, vp]
+            L.oc_eikonal.restype = i64
+            L.oc_eikonal.argtypes = [vp, vp, i32, i32, vp, vp, vp, vp, dbl, vp, vp, vp]
             L.oc_voxel_index.restype = None
             L.oc_voxel_index.argtypes = [vp, vp, i32, vp]
             L.oc_trilinear_coeffs.restype = None
@@ -254,6 +256,25 @@ def query_sdf_backward(cfg: OcConfig, theta, x, dsdf=None, dgrad=None) -> np.nda
     grad = np.zeros(len(th))
     lib().oc_query_sdf_backward(ctypes.byref(cfg), _p(th), _p(x), len(x), _p(ds), _p(dg), _p(grad))
     return grad
+
+
+def eikonal(cfg: OcConfig, theta, batch: dict, dscale: float = 1.0, want_grad=True):
+    """Eikonal term over the batch's free-space samples: (L_eik, dscale * dL_eik/dtheta or
+    None, |S_fs|, |grad_x phi| per sample [R][N] (-1 outside S_fs))."""
+    th = np.ascontiguousarray(theta, dtype=np.float64)
+    t = np.ascontiguousarray(batch["t"], dtype=np.float32)
+    R, N = t.shape
+    o = np.ascontiguousarray(batch["o"], dtype=np.float32).reshape(R, 3)
+    r = np.ascontiguousarray(batch["r"], dtype=np.float32).reshape(R, 3)
+    cls = np.ascontiguousarray(batch["cls"], dtype=np.uint8).reshape(R, N)
+    loss = np.zeros(1)
+    grad = np.zeros(len(th)) if want_grad else None
+    gnorm = np.empty((R, N))
+    n = lib().oc_eikonal(ctypes.byref(cfg), _p(th), R, N, _p(o), _p(r), _p(t), _p(cls), ctypes.c_double(dscale),
+                         _p(loss), _p(grad), _p(gnorm))
+    if n < 0:
+        raise ValueError("oc_eikonal rejected its arguments")
+    return float(loss[0]), grad, int(n), gnorm
 
 
 def voxel_index(cfg: OcConfig, x) -> np.ndarray:

@@ -17,6 +17,7 @@
  *   l_rgb, l_d, l_sdf, l_fs and their batch normalisations ....... Sec. 3.2-3.4
  *   l_smooth on near-surface points, grad_x phi .................. Sec. 3.3 Eq. (smoothness_loss); Supp. Sec. 1 Eq. (sdf_first_grad, jacobian)
  *   gradients (hand reverse mode, incl. d/dtheta of grad_x phi) .. Supp. Sec. 1 Eq. (second_order_theta)
+ *   l_eik on the free-space samples (separate entry) ............. Sec. 3.3 Eq. (eikonal_loss), Sec. 3.4
  *   Adam ......................................................... Sec. 4 (Implementation Details)
  *
  * Precision: every quantity that decides an integer (pixel index, sample depths and their
@@ -35,6 +36,8 @@
  *   - s = exp(kappa) with kappa learnable.
  *   - Sub-gradients: 0 at every tie (ReLU at 0, max(.,0) at 0, |.| at 0); the free-space
  *     max picks the first maximal entry of (0, exp term, linear term).
+ *   - L_eik is normalised like L_fs (mean over all free-space samples of the batch); its
+ *     sub-gradient at grad_x phi = 0 is 0.
  *   - Samples outside the grid box are clamped to it; the clamped axes get zero x-derivative.
  *   - Sampling: N_s stratified samples over [near, far] plus N_g samples stratified over
  *     [D - g, D + g] when D > 0 (all N_s + N_g stratified otherwise), merged by depth
@@ -518,6 +521,60 @@ void oc_query_sdf_backward(const oc_config* c, const double* theta, const float*
       }
     }
   }
+}
+
+/* ------------------------------------------------------------------------------------ */
+/* Eikonal term (Sec. 3.3 Eq. eikonal_loss; batch normalisation Sec. 3.4)                */
+/* ------------------------------------------------------------------------------------ */
+/* L_eik = mean over the free-space samples S_fs of the batch of (1 - |grad_x phi(x_s)|)^2,
+ * the same set and the same normalisation as L_fs (0 when S_fs is empty).  The points are
+ * the main samples x_s = o + d_s r, formed in binary32 exactly as in oc_step.
+ * With grad != NULL: grad += dscale dL_eik/dtheta.  For one point, with g = grad_x phi,
+ *   d l / d g = -2 (1 - |g|) g / |g|        (taken as 0 where |g| = 0),
+ * and the rest is the reverse mode of grad_x phi with respect to theta (oc_query_sdf_backward
+ * with that adjoint; x carries no gradient).  gnorm [R][N] (may be NULL) receives |g| at the
+ * free-space samples and -1 elsewhere.  Returns |S_fs|, or -1 on a bad argument. */
+int64_t oc_eikonal(const oc_config* c, const double* theta, int R, int N, const float* o, const float* r,
+                   const float* t, const uint8_t* cls, double dscale, double* loss, double* grad, double* gnorm) {
+  if (R < 0 || N < 1 || !loss) return -1;
+  int64_t n_fs = 0;
+  for (int64_t s = 0; s < (int64_t)R * N; ++s) n_fs += cls[s] == CLS_FS;
+  *loss = 0.0;
+  if (gnorm)
+    for (int64_t s = 0; s < (int64_t)R * N; ++s) gnorm[s] = -1.0;
+  if (n_fs == 0) return 0;
+  float* x = (float*)malloc(sizeof(float) * 3 * (size_t)n_fs);
+  int64_t* at = (int64_t*)malloc(sizeof(int64_t) * (size_t)n_fs);
+  double* sdf = (double*)malloc(sizeof(double) * (size_t)n_fs);
+  double* g = (double*)malloc(sizeof(double) * 3 * (size_t)n_fs);
+  int64_t q = 0;
+  for (int i = 0; i < R; ++i)
+    for (int k = 0; k < N; ++k) {
+      const int64_t s = (int64_t)i * N + k;
+      if (cls[s] != CLS_FS) continue;
+      for (int a = 0; a < 3; ++a) {
+        float step_ = t[s] * r[3 * i + a];
+        x[3 * q + a] = o[3 * i + a] + step_;
+      }
+      at[q++] = s;
+    }
+  oc_query_sdf(c, theta, x, (int)n_fs, sdf, g);
+  double sum = 0.0;
+  for (int64_t p = 0; p < n_fs; ++p) {
+    const double nrm = sqrt(g[3 * p] * g[3 * p] + g[3 * p + 1] * g[3 * p + 1] + g[3 * p + 2] * g[3 * p + 2]);
+    sum += (1.0 - nrm) * (1.0 - nrm);
+    if (gnorm) gnorm[at[p]] = nrm;
+    /* the adjoint of g, kept in g */
+    const double k = nrm > 0.0 ? dscale * (-2.0 / (double)n_fs) * (1.0 - nrm) / nrm : 0.0;
+    for (int a = 0; a < 3; ++a) g[3 * p + a] *= k;
+  }
+  *loss = sum / (double)n_fs;
+  if (grad) oc_query_sdf_backward(c, theta, x, (int)n_fs, NULL, g, grad);
+  free(x);
+  free(at);
+  free(sdf);
+  free(g);
+  return n_fs;
 }
 
 /* base vertex (cell) index per level, binary32 decision; out [P][4] flat vertex ids */
