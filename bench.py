@@ -104,6 +104,7 @@ def run_ours(args):
     mirror = theta[:n_grid_].to(torch.bfloat16).view(torch.int16).contiguous() if ctx.bf16 else None
     batch = gs.Batch.allocate(w.rays, w.n_samples, w.n_smooth)
     loss = torch.empty(6, device="cuda")
+    eik = torch.zeros(1, device="cuda")  # L_eik when --eikonal (Sec. 3.3, lam_eik = 1)
     stream = torch.cuda.current_stream()
     seed = 3 + 1000 * rank
     b1, b2 = w.betas
@@ -121,9 +122,13 @@ def run_ours(args):
             ctx.forward_backward(theta, batch, None, loss, grad, theta_bf16=mirror)
         if ev is not None:
             ev[2].record(stream)
-        ctx.adam_step(theta, grad, m, v, k + 1, w.lr_grid, w.lr_mlp, b1, b2, w.adam_eps, theta_bf16=mirror)
+        if args.eikonal:
+            ctx.eikonal(theta, batch, loss=eik, grad=grad)
         if ev is not None:
             ev[3].record(stream)
+        ctx.adam_step(theta, grad, m, v, k + 1, w.lr_grid, w.lr_mlp, b1, b2, w.adam_eps, theta_bf16=mirror)
+        if ev is not None:
+            ev[4].record(stream)
 
     for k in range(args.warmup):
         step(k)
@@ -131,7 +136,7 @@ def run_ours(args):
     ctx.sync_status()
 
     # ---- device-timed region: K full steps, inputs resident in HBM ----
-    evs = [[torch.cuda.Event(enable_timing=True) for _ in range(4)] for _ in range(args.steps)]
+    evs = [[torch.cuda.Event(enable_timing=True) for _ in range(5)] for _ in range(args.steps)]
     start, stop = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     if world > 1:
         torch.distributed.barrier()
@@ -147,13 +152,17 @@ def run_ours(args):
     clk = clocks.stop()
     ms = start.elapsed_time(stop)
     per = {"sample": [], "render": [], "adam": []}
+    if args.eikonal:
+        per["eikonal"] = []
     for e in evs:
         per["sample"].append(e[0].elapsed_time(e[1]))
         per["render"].append(e[1].elapsed_time(e[2]))
-        per["adam"].append(e[2].elapsed_time(e[3]))
+        if args.eikonal:
+            per["eikonal"].append(e[2].elapsed_time(e[3]))
+        per["adam"].append(e[3].elapsed_time(e[4]))
     avg = {k: sum(vv) / len(vv) for k, vv in per.items()}
     ctx.sync_status()
-    lossv = loss.cpu().numpy().tolist()
+    lossv = loss.cpu().numpy().tolist() + (eik.cpu().numpy().tolist() if args.eikonal else [])
 
     # ---- end-to-end region: the same steps through the public API with host round trips ----
     e2e_steps = max(1, min(args.steps, args.e2e_steps))
@@ -172,6 +181,8 @@ def run_ours(args):
             ctx.backward(theta, batch, dl_dev, grad, theta_bf16=mirror)
         else:
             ctx.forward_backward(theta, batch, dl_dev, loss, grad, theta_bf16=mirror)
+        if args.eikonal:
+            ctx.eikonal(theta, batch, loss=eik, grad=grad)
         ctx.adam_step(theta, grad, m, v, base + k + 1, w.lr_grid, w.lr_mlp, b1, b2, w.adam_eps, theta_bf16=mirror)
         out_host.copy_(loss, non_blocking=True)
         cnt_host.copy_(batch.counts, non_blocking=True)
@@ -199,7 +210,8 @@ def run_ours(args):
     achieved = dom_bytes / (avg[dom] / 1e3) / 1e9
     peak = peaks["hbm_gbs"]
     traffic = args.traffic_render if dom == "render" else args.traffic_adam
-    default_step = (w.name == WORKLOAD and not args.recompute and not args.split and args.frames in (None, 50))
+    default_step = (w.name == WORKLOAD and not args.recompute and not args.split and not args.eikonal and
+                    args.frames in (None, 50))
     if traffic is None and dom == "render" and default_step:
         traffic = _profiled_traffic("render_tc_kernel_room-8192x96.md",
                                     ("gs_render_tc.cuh", "gs_tc.cuh", "gs_device.cuh"))
@@ -212,7 +224,10 @@ def run_ours(args):
                    "params": w.layout()[2], "grid_params": n_grid, "frames": fr.depth.shape[0],
                    "resolution": [w.width, w.height], "parallelism": f"replicas{world}",
                    "activations": "recomputed" if args.recompute else "stored (396 B/sample)",
-                   "calls": "gs_forward + gs_backward" if args.split else "gs_forward_backward",
+                   "calls": ("gs_forward + gs_backward" if args.split else "gs_forward_backward") +
+                            (" + gs_eikonal" if args.eikonal else ""),
+                   "loss_terms": "rgb, depth, sdf, fs, smooth" + (", eikonal (lam 1, free-space samples)"
+                                                                  if args.eikonal else ""),
                    "l2": "inputs larger than L2: 1.2 GB of parameter/gradient/moment state streamed per step",
                    "frame_render_s": round(t_frames, 1)},
         "kernels_ms": {k: round(vv, 4) for k, vv in avg.items()},
@@ -226,9 +241,9 @@ def run_ours(args):
                  "frac_of_peak": round(adam_bytes / (avg['adam'] / 1e3) / 1e9 / peak, 4)},
         "e2e": {"value": round(w.rays * e2e_steps * world / e2e_s, 1), "unit": "rays/s",
                 "h2d_bytes_per_step": 24, "d2h_bytes_per_step": 40, "steps": e2e_steps,
-                "what": "per step: H2D dloss seed (pinned), the three C-ABI calls, D2H loss and counts, host sync; "
+                "what": "per step: H2D dloss seed (pinned), the C-ABI calls of the step, D2H loss and counts, host sync; "
                         "frames resident on the device"},
-        "gpu_launches": (9 if args.split else 6) * args.steps,
+        "gpu_launches": ((9 if args.split else 6) + (1 if args.eikonal else 0)) * args.steps,
         "clocks": clk,
         "loss_last": [round(x, 6) for x in lossv],
     }
@@ -544,6 +559,8 @@ def main():
     ap.add_argument("--recompute", action="store_true",
                     help="recompute the decoder activations in the backward pass instead of storing them")
     ap.add_argument("--split", action="store_true", help="gs_forward then gs_backward instead of the fused call")
+    ap.add_argument("--eikonal", action="store_true",
+                    help="add the Eikonal term on the free-space samples (gs_eikonal, lam_eik = 1) to every step")
     ap.add_argument("--prop-pretrain", type=int, default=300,
                     help="proposal workloads: untimed steps before the timed region (controller settles)")
     ap.add_argument("--prop-guided", type=int, default=None, help="proposal workloads: override prop_guided")

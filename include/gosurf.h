@@ -6,8 +6,8 @@
  * One step samples a batch of rays from posed RGB-D frames, decodes an SDF and a colour at
  * every sample from a four-level dense feature grid and two small decoders, renders colour
  * and depth with NeuS weights, evaluates the rgb / depth / truncated-SDF / free-space losses
- * and the SDF-gradient smoothness term, back-propagates to every grid feature and decoder
- * weight, and applies Adam.
+ * and the SDF-gradient smoothness term (the Eikonal term through its own entry point),
+ * back-propagates to every grid feature and decoder weight, and applies Adam.
  *
  * Conventions common to every entry point
  *   - Every pointer argument is a DEVICE pointer unless its comment says "host".  The caller
@@ -212,6 +212,20 @@ gs_status gs_proposal_backward(gs_ctx* ctx, const float* theta, const float* pro
  * constants (no gradient with respect to x).  Accumulates with atomics (order not fixed). */
 gs_status gs_query_sdf_backward(gs_ctx* ctx, const float* theta, const float* x, int32_t P, const float* dsdf,
                                 const float* dgrad, float* grad, void* stream);
+
+/* Eikonal term (Sec. 3.3 Eq. eikonal_loss, on the free-space samples as Sec. 3.4 states):
+ *   L_eik = (1 / |S_fs|) sum over the batch's samples of class GS_CLS_FS of (1 - |grad_x phi(x)|)^2,
+ * x = o + d r formed in binary32 as in gs_forward, |S_fs| = batch->counts[2] (written by the
+ * sampler); 0 when S_fs is empty.  The five losses of gs_forward do not include it: the
+ * caller adds lam_eik L_eik (Sec. 4: lam_eik = 1) to its objective.
+ * loss [1] (device, may be NULL) receives L_eik, reduced in FP64 over per-CTA partial sums.
+ * grad (may be NULL; not both NULL) += dloss[0] dL_eik/dtheta with dloss [1] a device float
+ * (NULL = 1): the second-order path of Supp. Sec. 1 (grid features through d z/d x, W1 and
+ * row 0 of W2 through d phi/d z; the sub-gradient at grad_x phi = 0 is 0), accumulated with
+ * atomics (order not fixed).  Reads the FP32 grid in every precision form.  Needs only the
+ * batch's ray arrays (origin, dir, t, cls, counts). */
+gs_status gs_eikonal(gs_ctx* ctx, const float* theta, const gs_batch* batch, const float* dloss, float* loss,
+                     float* grad, void* stream);
 
 /* Cell lookup used by every gather: out [P][4] = flat base-vertex index of the cell holding
  * x (clamped to the grid box) at each level, decided in binary32. */

@@ -179,6 +179,12 @@ class Context:
         self._check(self.L.gs_query_sdf_backward(self.h, _ptr(theta), _ptr(x), x.shape[0], _ptr(dsdf), _ptr(dgrad),
                                                  _ptr(grad), _stream()))
 
+    def eikonal(self, theta, batch: Batch, loss=None, grad=None, dloss=None):
+        """L_eik over the batch's free-space samples into loss [1]; grad += dloss * dL_eik/dtheta."""
+        bs = batch.struct()
+        self._check(self.L.gs_eikonal(self.h, _ptr(theta), ctypes.byref(bs), _ptr(dloss), _ptr(loss), _ptr(grad),
+                                      _stream()))
+
     def voxel_index(self, x, out):
         self._check(self.L.gs_voxel_index(self.h, _ptr(x), x.shape[0], _ptr(out), _stream()))
 

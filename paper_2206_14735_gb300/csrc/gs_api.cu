@@ -107,11 +107,15 @@ gs_status gs_create(const gs_config* cfg, gs_ctx** out) {
   g.n_grid = off;
   c->render_ctas = kRenderCtasPerSm * c->num_sms;
   c->n_parts = c->render_ctas + kSmoothCtas;
+  c->eik_ctas = kEikCtasPerSm * c->num_sms;
   const float dl[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 1.f};
   if (cudaMalloc(&c->loss_part, sizeof(float) * kLossPad * c->n_parts) != cudaSuccess ||
       cudaMalloc(&c->mlp_part, sizeof(float) * kMlpPad * c->n_parts) != cudaSuccess ||
       cudaMalloc(&c->default_dloss, sizeof(float) * 8) != cudaSuccess ||
       cudaMalloc(&c->status, sizeof(int)) != cudaSuccess ||
+      cudaMalloc(&c->eik_part, sizeof(float) * kEikCtasPerSm * c->num_sms) != cudaSuccess ||
+      cudaMalloc(&c->eik_ticket, sizeof(unsigned)) != cudaSuccess ||
+      cudaMemset(c->eik_ticket, 0, sizeof(unsigned)) != cudaSuccess ||
       cudaMemcpy(c->default_dloss, dl, sizeof(dl), cudaMemcpyHostToDevice) != cudaSuccess ||
       cudaMemset(c->status, 0, sizeof(int)) != cudaSuccess ||
       (cfg->prop_samples > 0 &&
@@ -135,6 +139,8 @@ void gs_destroy(gs_ctx* ctx) {
   cudaFree(ctx->status);
   cudaFree(ctx->store);
   cudaFree(ctx->prop_part);
+  cudaFree(ctx->eik_part);
+  cudaFree(ctx->eik_ticket);
   delete ctx;
 }
 
@@ -296,6 +302,22 @@ gs_status gs_query_sdf_backward(gs_ctx* ctx, const float* theta, const float* x,
   ctx->last_stream = st;
   if (gs_launch_query_backward(ctx, theta, x, P, dsdf, dgrad, grad, st) != GS_OK)
     return cuda_fail(ctx, "gs_query_sdf_backward");
+  return GS_OK;
+}
+
+gs_status gs_eikonal(gs_ctx* ctx, const float* theta, const gs_batch* batch, const float* dloss, float* loss,
+                     float* grad, void* stream) {
+  if (!ctx) return fail(nullptr, GS_ERR_INVALID_ARG, "gs_eikonal: ctx is NULL");
+  if (!theta) return fail(ctx, GS_ERR_INVALID_ARG, "gs_eikonal: theta is NULL");
+  if (!loss && !grad) return fail(ctx, GS_ERR_INVALID_ARG, "gs_eikonal: loss and grad are both NULL");
+  if (!aligned16(theta) || (grad && !aligned16(grad)))
+    return fail(ctx, GS_ERR_ALIGN, "gs_eikonal: theta or grad is not 16-byte aligned");
+  gs_status s = check_batch(ctx, batch, false);
+  if (s != GS_OK) return s;
+  cudaStream_t st = (cudaStream_t)stream;
+  ctx->last_stream = st;
+  const float* dl = dloss ? dloss : ctx->default_dloss + 5;  // 1.0
+  if (gs_launch_eikonal(ctx, theta, batch, dl, loss, grad, st) != GS_OK) return cuda_fail(ctx, "gs_eikonal");
   return GS_OK;
 }
 

@@ -13,6 +13,7 @@ constexpr int kSmoothCtas = 128;  // CTAs of the smoothness kernel (fixed, so pa
 constexpr int kRenderCtasPerSm = 1;  // persistent render CTAs per SM
 constexpr int kStoreFloatsPerSample = 99;  // stored activations: z 16, a1 32, (phi, h) 16, a2 32, c 3
 constexpr int kRenderGroups = 3;     // tile groups (4 warps, 128 tensor-memory columns each) per render CTA
+constexpr int kEikCtasPerSm = 5;     // CTAs of the Eikonal kernel per SM (one wave at 191 registers x 64 threads)
 
 struct gs_ctx {
   gs_config cfg;
@@ -30,6 +31,9 @@ struct gs_ctx {
   int store_R = -1, store_N = -1;     // batch shape and depths pointer of the gs_forward that filled it
   const float* store_t = nullptr;
   float* prop_part = nullptr;        // proposal training partial rows (prop_samples > 0)
+  int eik_ctas = 0;                  // largest grid of the Eikonal kernel
+  float* eik_part = nullptr;         // its per-CTA loss sums
+  unsigned* eik_ticket = nullptr;    // CTAs finished in the running call (0 between calls)
   cudaStream_t last_stream = nullptr;
   std::string last_error;
 };
@@ -56,6 +60,8 @@ gs_status gs_launch_prop_sample(const gs_ctx* ctx, const float* theta, const flo
                                 cudaStream_t st);
 gs_status gs_launch_prop_backward(const gs_ctx* ctx, const float* theta, const float* q, const gs_batch* b,
                                   float* grad, float* ce, cudaStream_t st);
+gs_status gs_launch_eikonal(const gs_ctx* ctx, const float* theta, const gs_batch* b, const float* dloss, float* loss,
+                            float* grad, cudaStream_t st);
 gs_status gs_launch_query_backward(const gs_ctx* ctx, const float* theta, const float* x, int P, const float* dsdf,
                                    const float* dgrad, float* grad, cudaStream_t st);
 gs_status gs_launch_query(const gs_ctx* ctx, const float* theta, const float* x, int P, float* sdf, float* grad,

@@ -1,0 +1,111 @@
+"""Eikonal term (gs_eikonal, Sec. 3.3 Eq. eikonal_loss on S_fs) against the FP64 oracle:
+loss and parameter gradient on sampled batches of the cube workload (several tiles and
+ragged tails), the degenerate cases, and the room workload at its full batch and grid."""
+import numpy as np
+import pytest
+import torch
+
+import oracle as oc
+import scenegen as sg
+from gpu_common import Problem, assert_grad_close, upload_oracle_batch
+from helpers import CUBE, sdf_parity_params
+
+pytestmark = pytest.mark.gpu
+SEED = 2024
+NO_COLOUR = ("W3", "b3", "W4", "b4", "kappa")
+
+
+def _gpu(p, theta, batch, want_grad=True, dloss=None, want_loss=True):
+    th = torch.from_numpy(theta).cuda()
+    loss = torch.full((1,), float("nan"), device="cuda") if want_loss else None
+    grad = torch.zeros_like(th) if want_grad else None
+    dl = None if dloss is None else torch.tensor([dloss], dtype=torch.float32, device="cuda")
+    p.ctx.eikonal(th, batch, loss=loss, grad=grad, dloss=dl)
+    torch.cuda.synchronize()
+    return (float(loss.item()) if want_loss else None), (grad.cpu().numpy() if want_grad else None)
+
+
+def _loss_tol(ref_loss, gnorm):
+    """|Delta L_eik| allowed for a binary32 evaluation of grad_x phi.
+
+    Each |g| carries a relative error of at most about 1e-5 (a 48-term FP32 dot product of
+    trilinear derivatives with the decoder sensitivities, then a square root), so
+    |Delta (1 - |g|)^2| <= 2 |1 - |g|| 1e-5 |g| + (1e-5 |g|)^2 per sample; the mean of that,
+    plus 1e-6 relative for the FP32 per-lane partial sums."""
+    n = gnorm[gnorm >= 0]
+    if len(n) == 0:
+        return 0.0
+    e = 1e-5 * n
+    return float(np.mean(2 * np.abs(1 - n) * e + e * e)) + 1e-6 * ref_loss
+
+
+@pytest.fixture(scope="module")
+def cube():
+    p = Problem(CUBE)
+    theta = sdf_parity_params(CUBE, sg.cube_scene(), seed=21)
+    return p, theta
+
+
+@pytest.mark.parametrize("R", [CUBE.rays, 333, 7, 1])
+def test_eikonal_parity_cube(cube, R):
+    p, theta = cube
+    bt, _ = p.oracle_sample(SEED, 3, R=R, P=0)
+    batch = upload_oracle_batch(bt, None, 0)
+    ref_l, ref_g, n_fs, gnorm = oc.eikonal(p.cfg, theta, bt)
+    assert n_fs == int(bt["counts"][2])
+    got_l, got_g = _gpu(p, theta, batch)
+    assert abs(got_l - ref_l) <= _loss_tol(ref_l, gnorm), (got_l, ref_l, n_fs)
+    assert_grad_close(p, got_g, ref_g, skip=NO_COLOUR)
+    n_grid = p.n_grid
+    assert not np.any(got_g[n_grid + 512:n_grid + 544])  # b1: the mask carries no gradient
+    assert not np.any(got_g[n_grid + 576:])              # W2 rows 1.., b2, colour decoder, kappa: unreachable
+    if R == CUBE.rays:
+        assert n_fs > 1000 and n_fs % 32 != 0
+
+
+def test_eikonal_loss_only_seed_and_repeated_calls(cube):
+    """Loss-only calls give the same loss (the last-CTA reduction resets its counter); the
+    gradient is linear in the upstream seed."""
+    p, theta = cube
+    bt, _ = p.oracle_sample(SEED, 4, R=CUBE.rays, P=0)
+    batch = upload_oracle_batch(bt, None, 0)
+    l1, g1 = _gpu(p, theta, batch)
+    for _ in range(3):
+        l2, _ = _gpu(p, theta, batch, want_grad=False)
+        assert abs(l2 - l1) <= 1e-6 * l1
+    _, g3 = _gpu(p, theta, batch, dloss=-2.5, want_loss=False)
+    scale = np.abs(g1).max()
+    assert np.abs(g3 + 2.5 * g1).max() <= 1e-5 * 2.5 * scale
+
+
+def test_eikonal_without_free_space_samples(cube):
+    p, theta = cube
+    bt, _ = p.oracle_sample(SEED, 5, R=64, P=0)
+    bt["cls"][:] = oc.CLS_TR
+    bt["counts"] = np.array([bt["counts"][0], bt["cls"].size, 0, 0], np.int64)
+    batch = upload_oracle_batch(bt, None, 0)
+    got_l, got_g = _gpu(p, theta, batch)
+    assert got_l == 0.0 and not np.any(got_g)
+
+
+def test_eikonal_empty_batch(cube):
+    p, theta = cube
+    bt, _ = p.oracle_sample(SEED, 6, R=0, P=0)
+    batch = upload_oracle_batch(bt, None, 0)
+    got_l, got_g = _gpu(p, theta, batch)
+    assert got_l == 0.0 and not np.any(got_g)
+
+
+def test_eikonal_room_scale_parity():
+    """The room workload at its full batch (8192 rays x 96 samples) and full grid (75.7 M
+    parameters) on the first 40 frames of its trajectory."""
+    w = sg.WORKLOADS["room-8192x96"]
+    p = Problem(w, n_frames=40)
+    bt, _ = p.oracle_sample(SEED, 11, P=0)
+    theta = sdf_parity_params(w, sg.room_scene(), seed=31)
+    batch = upload_oracle_batch(bt, None, 0)
+    ref_l, ref_g, n_fs, gnorm = oc.eikonal(p.cfg, theta, bt)
+    assert n_fs > 100000
+    got_l, got_g = _gpu(p, theta, batch)
+    assert abs(got_l - ref_l) <= _loss_tol(ref_l, gnorm), (got_l, ref_l)
+    assert_grad_close(p, got_g, ref_g, skip=NO_COLOUR)
