@@ -41,27 +41,44 @@ def _peaks():
 class ClockSampler:
     """nvidia-smi clock / throttle samples while the timed region runs."""
 
-    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,clocks_event_reasons.hw_slowdown,"
+    FIELDS = ("timestamp,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,clocks_event_reasons.hw_slowdown,"
               "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
               "clocks_event_reasons.sw_power_cap")
 
     def __init__(self, index=0):
+        """Starts sampling every 50 ms and returns once the first sample is in (nvidia-smi takes
+        a moment to start), so that the timed region that follows is covered."""
         self.f = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
         try:
             self.p = subprocess.Popen(["nvidia-smi", "-i", str(index), f"--query-gpu={self.FIELDS}",
-                                       "--format=csv,noheader,nounits", "-lms", "200"], stdout=self.f,
+                                       "--format=csv,noheader,nounits", "-lms", "50"], stdout=self.f,
                                       stderr=subprocess.DEVNULL)
+            t0 = time.time()
+            while time.time() - t0 < 5.0 and os.path.getsize(self.f.name) == 0:
+                time.sleep(0.02)
         except Exception:
             self.p = None
+        self.t_start = time.time()
 
     def stop(self):
         if self.p is None:
             return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        t_stop = time.time()
+        time.sleep(0.06)  # one more sample at the end of the region
         self.p.terminate()
         self.p.wait()
         self.f.seek(0)
-        rows = [r.split(",") for r in self.f.read().strip().splitlines() if r.count(",") >= 7]
+        rows = [r.split(",")[1:] + [r.split(",")[0]] for r in self.f.read().strip().splitlines() if r.count(",") >= 8]
         os.unlink(self.f.name)
+
+        def stamp(r):
+            try:
+                import datetime
+                return datetime.datetime.strptime(r[-1].strip(), "%Y/%m/%d %H:%M:%S.%f").timestamp()
+            except Exception:
+                return None
+        inside = [r for r in rows if stamp(r) is not None and self.t_start - 0.06 <= stamp(r) <= t_stop + 0.06]
+        rows = inside or rows
         sm = [float(r[0]) for r in rows if r[0].strip().replace(".", "").isdigit()]
         mx = [float(r[1]) for r in rows if r[1].strip().replace(".", "").isdigit()]
         names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]

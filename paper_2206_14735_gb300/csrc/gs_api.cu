@@ -75,6 +75,9 @@ gs_status gs_create(const gs_config* cfg, gs_ctx** out) {
       if (cfg->dims[l][a] < 2) return fail(nullptr, GS_ERR_INVALID_ARG, "gs_create: every level needs >= 2 vertices per axis");
     if (!(cfg->voxel[l] > 0.0f)) return fail(nullptr, GS_ERR_INVALID_ARG, "gs_create: voxel size must be > 0");
   }
+  for (int l = 0; l < 2; ++l)  // the coarse-level scatters key their runs by a 32-bit vertex index
+    if (level_floats(cfg, l) / GS_FEAT >= (1LL << 31))
+      return fail(nullptr, GS_ERR_UNSUPPORTED, "gs_create: levels 0 and 1 must have fewer than 2^31 vertices");
   const int N = cfg->n_strat + cfg->n_guided;
   if (cfg->n_strat < 1 || cfg->n_guided < 0 || N < 2) return fail(nullptr, GS_ERR_INVALID_ARG, "gs_create: need n_strat >= 1 and N >= 2");
   if (N > 128) return fail(nullptr, GS_ERR_UNSUPPORTED, "gs_create: this build renders at most 128 samples per ray");

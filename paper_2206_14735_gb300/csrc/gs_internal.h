@@ -13,7 +13,7 @@ constexpr int kSmoothCtas = 128;  // CTAs of the smoothness kernel (fixed, so pa
 constexpr int kRenderCtasPerSm = 1;  // persistent render CTAs per SM
 constexpr int kStoreFloatsPerSample = 99;  // stored activations: z 16, a1 32, (phi, h) 16, a2 32, c 3
 constexpr int kRenderGroups = 3;     // tile groups (4 warps, 128 tensor-memory columns each) per render CTA
-constexpr int kEikCtasPerSm = 5;     // CTAs of the Eikonal kernel per SM (one wave at 191 registers x 64 threads)
+constexpr int kEikCtasPerSm = 4;     // CTAs of the Eikonal kernel per SM (one wave at 230 registers x 64 threads)
 
 struct gs_ctx {
   gs_config cfg;

@@ -380,6 +380,7 @@ __global__ void __launch_bounds__(kSmoothWarps * 32) query_backward_kernel(Query
 // not lost to the other classes.  The loss is reduced in FP64 by the last CTA to finish.
 // ------------------------------------------------------------------------------------
 constexpr int kEikWarps = 2;
+constexpr int kEikRunLevels = 2;  // levels whose scatter is reduced over runs of equal cells first
 
 struct EikArgs {
   GridDesc g;
@@ -448,22 +449,49 @@ __global__ void __launch_bounds__(kEikWarps * 32, 4) eikonal_kernel(EikArgs a) {
       const float r3[3] = {a.r[3 * i], a.r[3 * i + 1], a.r[3 * i + 2]};
       sample_pos(o3, r3, a.t[s], y);
     }
-    float pz[kZ], mw2[kH1];
-    unsigned mask;
-    {
-      float z[kZ];
-      features_only(a.g, a.theta, y, z);
-      mask = phi_sensitivity(sm, z, mw2, pz);
-    }
-    float gq[3] = {0.f, 0.f, 0.f};  // grad_x phi = sum_l (d z_l / d x)^T p_l
+    // z and d z / d x in one pass over each level's 8 corners.  The Jacobian is kept in this
+    // lane's staging row (floats 36..83, free until the decoder-gradient rows are written):
+    // in registers it pushed the kernel into spills, and a second gather cost more.
+    float z[kZ];
+    float4* dls = reinterpret_cast<float4*>(st + lane * kSt + 36);
 #pragma unroll
     for (int l = 0; l < kLevels; ++l) {
       float4 dl[3];
-      float dw[8][3];
-      level_jacobian(a.g, a.theta, l, y, dl, dw);
+      const Cell c = locate(a.g, l, y);
+      float w[8], dw[8][3];
+      corner_weights(c.f, w);
+      corner_weight_grads(c.f, c.clamped, dw);
+      const float4* lv = reinterpret_cast<const float4*>(a.theta + a.g.off[l]);
+      float4 zz = make_float4(0.f, 0.f, 0.f, 0.f);
+      dl[0] = dl[1] = dl[2] = zz;
 #pragma unroll
-      for (int d = 0; d < 3; ++d)
-        gq[d] += pz[4 * l] * dl[d].x + pz[4 * l + 1] * dl[d].y + pz[4 * l + 2] * dl[d].z + pz[4 * l + 3] * dl[d].w;
+      for (int k = 0; k < 8; ++k) {
+        const float4 v = __ldg(lv + c.vtx + corner_offset(a.g, l, k));
+        f4fma(zz, w[k], v);
+        f4fma(dl[0], dw[k][0], v);
+        f4fma(dl[1], dw[k][1], v);
+        f4fma(dl[2], dw[k][2], v);
+      }
+      const float iv = a.g.inv_voxel[l];
+#pragma unroll
+      for (int d = 0; d < 3; ++d) dls[3 * l + d] = f4scale(dl[d], iv);
+      z[4 * l] = zz.x;
+      z[4 * l + 1] = zz.y;
+      z[4 * l + 2] = zz.z;
+      z[4 * l + 3] = zz.w;
+    }
+    float pz[kZ], mw2[kH1];
+    const unsigned mask = phi_sensitivity(sm, z, mw2, pz);
+    float gq[3];
+#pragma unroll
+    for (int d = 0; d < 3; ++d) {
+      float v = 0.f;
+#pragma unroll
+      for (int l = 0; l < kLevels; ++l) {
+        const float4 q4 = dls[3 * l + d];
+        v += pz[4 * l] * q4.x + pz[4 * l + 1] * q4.y + pz[4 * l + 2] * q4.z + pz[4 * l + 3] * q4.w;
+      }
+      gq[d] = v;
     }
     const float nrm = __fsqrt_rn(gq[0] * gq[0] + gq[1] * gq[1] + gq[2] * gq[2]);
     if (valid) l_eik += (1.f - nrm) * (1.f - nrm);
@@ -474,16 +502,47 @@ __global__ void __launch_bounds__(kEikWarps * 32, 4) eikonal_kernel(EikArgs a) {
     float jv[kZ];
 #pragma unroll
     for (int l = 0; l < kLevels; ++l) {
-      float4 dl[3];
+      const Cell c = locate(a.g, l, y);
       float dw[8][3];
-      const Cell c = level_jacobian(a.g, a.theta, l, y, dl, dw);
-      jv[4 * l] = av[0] * dl[0].x + av[1] * dl[1].x + av[2] * dl[2].x;
-      jv[4 * l + 1] = av[0] * dl[0].y + av[1] * dl[1].y + av[2] * dl[2].y;
-      jv[4 * l + 2] = av[0] * dl[0].z + av[1] * dl[1].z + av[2] * dl[2].z;
-      jv[4 * l + 3] = av[0] * dl[0].w + av[1] * dl[1].w + av[2] * dl[2].w;
-      if (kk != 0.f) {
-        const float iv = a.g.inv_voxel[l];
-        const float4 p4 = make_float4(pz[4 * l], pz[4 * l + 1], pz[4 * l + 2], pz[4 * l + 3]);
+      corner_weight_grads(c.f, c.clamped, dw);
+      {
+        const float4 d0 = dls[3 * l], d1 = dls[3 * l + 1], d2 = dls[3 * l + 2];
+        jv[4 * l] = av[0] * d0.x + av[1] * d1.x + av[2] * d2.x;
+        jv[4 * l + 1] = av[0] * d0.y + av[1] * d1.y + av[2] * d2.y;
+        jv[4 * l + 2] = av[0] * d0.z + av[1] * d1.z + av[2] * d2.z;
+        jv[4 * l + 3] = av[0] * d0.w + av[1] * d1.w + av[2] * d2.w;
+      }
+      const float iv = a.g.inv_voxel[l];
+      const float4 p4 = make_float4(pz[4 * l], pz[4 * l + 1], pz[4 * l + 2], pz[4 * l + 3]);
+      if (l < kEikRunLevels) {
+        // coarse levels: consecutive queued samples (along one ray) mostly share the cell, so
+        // the warp sums runs of equal cells first.  Lane r stages its 8 corner vectors as row
+        // r; lane c then walks the 32 rows summing component c (corner c / 4, feature c % 4)
+        // and adds each run's sum with one atomic.
+        float* row = st + lane * kSt;
+#pragma unroll
+        for (int k = 0; k < 8; ++k) {
+          const float ad = (av[0] * dw[k][0] + av[1] * dw[k][1] + av[2] * dw[k][2]) * iv;
+          *reinterpret_cast<float4*>(row + 4 * k) = f4scale(p4, ad);
+        }
+        row[32] = __int_as_float(kk != 0.f ? (int)c.vtx : -1);
+        __syncwarp();
+        const long long coff = corner_offset(a.g, l, lane >> 2);
+        float* gl = a.grad + a.g.off[l] + (lane & 3);
+        int key = __float_as_int(st[32]);
+        float sum = 0.f;
+#pragma unroll 4
+        for (int r = 0; r < 32; ++r) {
+          sum += st[r * kSt + lane];
+          const int next = r < 31 ? __float_as_int(st[(r + 1) * kSt + 32]) : -2;
+          if (next != key) {
+            if (key >= 0) atomicAdd(gl + ((long long)key + coff) * 4, sum);
+            sum = 0.f;
+            key = next;
+          }
+        }
+        __syncwarp();
+      } else if (kk != 0.f) {
         float4* gl = reinterpret_cast<float4*>(a.grad + a.g.off[l]) + c.vtx;
 #pragma unroll
         for (int k = 0; k < 8; ++k) {
@@ -501,13 +560,18 @@ __global__ void __launch_bounds__(kEikWarps * 32, 4) eikonal_kernel(EikArgs a) {
     for (int i = 0; i < 4; ++i)
       *reinterpret_cast<float4*>(row + sJ + 4 * i) = make_float4(jv[4 * i], jv[4 * i + 1], jv[4 * i + 2], jv[4 * i + 3]);
 #pragma unroll
-    for (int j = 0; j < kH1; ++j) {
-      float u = 0.f;
-      if ((mask >> j) & 1u) {
+    for (int j4 = 0; j4 < kH1; j4 += 4) {  // u_j = m_j (W1 j)_j, stored 4 at a time (no bank conflicts)
+      float u[4];
 #pragma unroll
-        for (int k = 0; k < kZ; ++k) u = fmaf(sm[sW1 + j * 16 + k], jv[k], u);
+      for (int jj = 0; jj < 4; ++jj) {
+        const int j = j4 + jj;
+        u[jj] = 0.f;
+        if ((mask >> j) & 1u) {
+#pragma unroll
+          for (int k = 0; k < kZ; ++k) u[jj] = fmaf(sm[sW1 + j * 16 + k], jv[k], u[jj]);
+        }
       }
-      row[sU + j] = u;
+      *reinterpret_cast<float4*>(row + sU + j4) = make_float4(u[0], u[1], u[2], u[3]);
     }
     __syncwarp();
     {  // dW1 += mw2 (x) j and dW2[0,:] += u over the warp's 32 rows (invalid rows are zero)
