@@ -89,6 +89,8 @@ def lib():
             L.oc_query_sdf_backward.argtypes = [vp, vp, vp, i32, vp, vp, vp]
             L.oc_eikonal.restype = i64
             L.oc_eikonal.argtypes = [vp, vp, i32, i32, vp, vp, vp, vp, dbl, vp, vp, vp]
+            L.oc_sample_importance.restype = i32
+            L.oc_sample_importance.argtypes = [vp, vp, vp, u64, u32, i32, i32, i32, i32] + [vp] * 9
             L.oc_voxel_index.restype = None
             L.oc_voxel_index.argtypes = [vp, vp, i32, vp]
             L.oc_trilinear_coeffs.restype = None
@@ -156,6 +158,23 @@ def sample_rays(cfg: OcConfig, frames: OcFramesHolder, seed: int, step: int, R: 
     lib().oc_sample_rays(ctypes.byref(cfg), ctypes.byref(frames.s), seed, step, R, *[_p(out[k]) for k in
                                                                                      ("pix", "o", "r", "rgb", "D", "t",
                                                                                       "cls", "counts")])
+    return out
+
+
+def sample_importance(cfg: OcConfig, frames: OcFramesHolder, theta, seed: int, step: int, R: int, n_coarse: int,
+                      n_steps: int, per_step: int) -> dict:
+    """Hierarchical importance sampling (N_c coarse + n_steps x per_step): the rays of
+    sample_rays for (seed, step) with N = n_coarse + n_steps * per_step depths; phi [R][N]."""
+    th = np.ascontiguousarray(theta, dtype=np.float64)
+    N = n_coarse + n_steps * per_step
+    out = dict(pix=np.empty(R, np.int64), o=np.empty((R, 3), np.float32), r=np.empty((R, 3), np.float32),
+               rgb=np.empty((R, 3), np.float32), D=np.empty(R, np.float32), t=np.empty((R, N), np.float32),
+               cls=np.empty((R, N), np.uint8), counts=np.empty(4, np.int64), phi=np.empty((R, N)))
+    rc = lib().oc_sample_importance(ctypes.byref(cfg), ctypes.byref(frames.s), _p(th), seed, step, R, n_coarse,
+                                    n_steps, per_step, *[_p(out[k]) for k in ("pix", "o", "r", "rgb", "D", "t", "cls",
+                                                                              "counts", "phi")])
+    if rc != 0:
+        raise ValueError("oc_sample_importance rejected its arguments")
     return out
 
 

@@ -18,6 +18,7 @@
  *   l_smooth on near-surface points, grad_x phi .................. Sec. 3.3 Eq. (smoothness_loss); Supp. Sec. 1 Eq. (sdf_first_grad, jacobian)
  *   gradients (hand reverse mode, incl. d/dtheta of grad_x phi) .. Supp. Sec. 1 Eq. (second_order_theta)
  *   l_eik on the free-space samples (separate entry) ............. Sec. 3.3 Eq. (eikonal_loss), Sec. 3.4
+ *   hierarchical importance sampler (separate entry) ............. Sec. 3.2 (3 x 12 from N_c = 96), Sec. 4
  *   Adam ......................................................... Sec. 4 (Implementation Details)
  *
  * Precision: every quantity that decides an integer (pixel index, sample depths and their
@@ -1052,6 +1053,141 @@ int oc_step(const oc_config* c, const double* theta, int R, int N, const float* 
   free(mg_all);
   free(dz_all);
   free(dzs_all);
+  return 0;
+}
+
+/* ------------------------------------------------------------------------------------ */
+/* hierarchical importance sampler (Sec. 3.2: 3 steps of 12 from N_c = 96, as in NeuS)     */
+/* ------------------------------------------------------------------------------------ */
+/* The rays are those of oc_sample_rays for the same (seed, step) (stream 0, slot 0 picks the
+ * pixel).  Per ray, in the order the paper gives:
+ *   1. N_c coarse depths stratified over [near, far]: t_k = near + (k + u_k)(far - near)/N_c,
+ *      u_k from stream 3, slot 1 + k (binary32, as the plain sampler forms its strata);
+ *   2. n_steps times: phi at every current sample (FP64), the NeuS weights of the current
+ *      samples with the model's s = exp(kappa) (Sec. 3.2 Eq. volume_rendering_alpha: Phi =
+ *      sigmoid(s phi), alpha_k = max((Phi_k - Phi_k+1) / max(Phi_k, 1e-6), 0), T_k the product
+ *      of (1 - alpha_j) over j < k, w_k = T_k alpha_k) on the n - 1 intervals [t_k, t_k+1]; the
+ *      interval masses p_k = (w_k + 1e-5) / sum (w + 1e-5); M new depths by stratified
+ *      inverse-CDF draws u_j = (j + xi_j) / M (xi_j from stream 3, slot 1 + N_c + step_i M + j),
+ *      each placed linearly inside its interval: t = t_k + (u - C_k) / p_k (t_k+1 - t_k) with
+ *      C_k the mass left of interval k (FP64, rounded to binary32 at the end); the new
+ *      depths are merged into the sorted list (an existing depth first on ties);
+ *   3. classes by the bound b = D - t, as in oc_sample_rays.
+ * Outputs as oc_sample_rays with N = N_c + n_steps M; phi_out [R][N] (may be NULL) receives
+ * phi (FP64) at the final samples.  Returns 0, or -1 on a bad argument (M is at most 64). */
+/* phi at depth tv of the ray (o, r): binary32 position as in oc_step, FP64 from there on */
+static double phi_on_ray(const oc_config* c, const double* theta, const mlp_t* m, const float o[3], const float r[3],
+                         float tv) {
+  float x[3];
+  for (int a = 0; a < 3; ++a) {
+    float st = tv * r[a];
+    x[a] = o[a] + st;
+  }
+  cell_t cl[OC_LEVELS];
+  act_t A;
+  features(c, theta, x, cl, A.z, NULL);
+  decode(m, &A);
+  return A.out[0];
+}
+
+int oc_sample_importance(const oc_config* c, const oc_frames* fr, const double* theta, uint64_t seed,
+                         uint32_t step, int R, int Nc, int n_steps, int M, int64_t* pix, float* o, float* r,
+                         float* rgb, float* D, float* t, uint8_t* cls, int64_t* counts, double* phi_out) {
+  if (R < 0 || Nc < 2 || n_steps < 0 || M < 1 || M > 64) return -1;
+  const int N = Nc + n_steps * M;
+  const int64_t npix = (int64_t)fr->F * fr->H * fr->W;
+  const mlp_t m = mlp_view(theta + grid_size(c));
+  const double s = exp(*m.kappa);
+  int64_t nd = 0, ntr = 0, nfs = 0;
+#pragma omp parallel for schedule(static) reduction(+ : nd, ntr, nfs)
+  for (int i = 0; i < R; ++i) {
+    float* ts = (float*)malloc(sizeof(float) * N);
+    float* tn = (float*)malloc(sizeof(float) * N);
+    double* ph = (double*)malloc(sizeof(double) * N);
+    double* pn = (double*)malloc(sizeof(double) * N);
+    double* C = (double*)malloc(sizeof(double) * N);
+    double* Phi = (double*)malloc(sizeof(double) * N);
+    double* al = (double*)malloc(sizeof(double) * N);
+    double* Tr = (double*)malloc(sizeof(double) * N);
+    double* wk = (double*)malloc(sizeof(double) * N);
+    double ch3[3];
+    float tnew[64];
+    double phnew[64];
+    uint64_t h = oc_draw(seed, 0, step, (uint64_t)i, 0);
+    int64_t p = (int64_t)(h % (uint64_t)npix);
+    pix[i] = p;
+    float Di;
+    pixel_ray(fr, p, o + 3 * i, r + 3 * i, rgb + 3 * i, &Di);
+    D[i] = Di;
+    nd += Di > 0.0f;
+    const float* oi = o + 3 * i;
+    const float* ri = r + 3 * i;
+    const float delta = (c->far_m - c->near_m) / (float)Nc;
+    for (int k = 0; k < Nc; ++k) {
+      float u = unif24(oc_draw(seed, 3, step, (uint64_t)i, 1 + (uint64_t)k));
+      ts[k] = c->near_m + ((float)k + u) * delta;
+      ph[k] = phi_on_ray(c, theta, &m, oi, ri, ts[k]);
+    }
+    int n = Nc;
+    for (int si = 0; si < n_steps; ++si) {
+      /* NeuS weights of the current samples (the renderer's own compositing), interval
+       * masses and their running sums */
+      double dh, wsum, tot = 0.0;
+      composite(n, ph, s, NULL, ts, Phi, al, Tr, wk, ch3, &dh, &wsum);
+      for (int k = 0; k + 1 < n; ++k) {
+        C[k] = wk[k] + 1e-5; /* unnormalised mass of interval k, for now */
+        tot += C[k];
+      }
+      double run = 0.0;
+      for (int k = 0; k + 1 < n; ++k) {
+        const double pk = C[k] / tot;
+        C[k] = run; /* mass left of interval k */
+        run += pk;
+      }
+      for (int j = 0; j < M; ++j) {
+        const double xi = (double)unif24(oc_draw(seed, 3, step, (uint64_t)i, 1 + (uint64_t)Nc + (uint64_t)si * M + j));
+        const double u = ((double)j + xi) / (double)M;
+        int k = 0;
+        while (k + 2 < n && C[k + 1] <= u) ++k; /* last interval whose left mass is <= u */
+        const double pk = (k + 2 < n ? C[k + 1] : 1.0) - C[k];
+        double f = pk > 0.0 ? (u - C[k]) / pk : 0.0;
+        if (f < 0.0) f = 0.0;
+        if (f > 1.0) f = 1.0;
+        tnew[j] = (float)((double)ts[k] + f * ((double)ts[k + 1] - (double)ts[k]));
+        phnew[j] = phi_on_ray(c, theta, &m, oi, ri, tnew[j]);
+      }
+      /* merge (the new depths ascend with j): an existing depth first on ties */
+      int a = 0, b = 0;
+      for (int k = 0; k < n + M; ++k) {
+        if (b >= M || (a < n && ts[a] <= tnew[b])) { tn[k] = ts[a]; pn[k] = ph[a]; ++a; }
+        else { tn[k] = tnew[b]; pn[k] = phnew[b]; ++b; }
+      }
+      n += M;
+      memcpy(ts, tn, sizeof(float) * n);
+      memcpy(ph, pn, sizeof(double) * n);
+    }
+    for (int k = 0; k < N; ++k) {
+      t[(size_t)i * N + k] = ts[k];
+      if (phi_out) phi_out[(size_t)i * N + k] = ph[k];
+      const int cl = sample_class(Di, ts[k], c->trunc);
+      cls[(size_t)i * N + k] = (uint8_t)cl;
+      ntr += cl == CLS_TR;
+      nfs += cl == CLS_FS;
+    }
+    free(ts);
+    free(tn);
+    free(ph);
+    free(pn);
+    free(C);
+    free(Phi);
+    free(al);
+    free(Tr);
+    free(wk);
+  }
+  counts[0] = nd;
+  counts[1] = ntr;
+  counts[2] = nfs;
+  counts[3] = 0;
   return 0;
 }
 
