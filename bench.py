@@ -110,7 +110,7 @@ def run_ours(args):
     gbuild.build()
     w = sg.WORKLOADS[args.workload]
     t0 = time.time()
-    fr = sg.make_frames(w, n_frames=args.frames)
+    fr = sg.make_frames(w, n_frames=args.frames, with_gt=args.sampler_report > 0)
     t_frames = time.time() - t0
     ctx = gs.Context(w, store_activations=not args.recompute)
     dfr = gs.DeviceFrames(fr.rgb, fr.depth, fr.c2w, fr.fx, fr.fy, fr.cx, fr.cy)
@@ -126,10 +126,16 @@ def run_ours(args):
     seed = 3 + 1000 * rank
     b1, b2 = w.betas
 
+    def sample(k):
+        if w.imp_coarse > 0:  # the paper's hierarchical importance sampler (reads theta)
+            ctx.sample_importance(dfr, theta, seed, k, batch)
+        else:
+            ctx.sample_rays(dfr, seed, k, batch)
+
     def step(k, ev=None):
         if ev is not None:
             ev[0].record(stream)
-        ctx.sample_rays(dfr, seed, k, batch)
+        sample(k)
         if ev is not None:
             ev[1].record(stream)
         if args.split:
@@ -192,7 +198,7 @@ def run_ours(args):
     base = args.warmup + args.steps
     for k in range(e2e_steps):
         dl_dev.copy_(dl_host, non_blocking=True)
-        ctx.sample_rays(dfr, seed, base + k, batch)
+        sample(base + k)
         if args.split:
             ctx.forward(theta, batch, loss, theta_bf16=mirror)
             ctx.backward(theta, batch, dl_dev, grad, theta_bf16=mirror)
@@ -241,6 +247,8 @@ def run_ours(args):
                    "params": w.layout()[2], "grid_params": n_grid, "frames": fr.depth.shape[0],
                    "resolution": [w.width, w.height], "parallelism": f"replicas{world}",
                    "activations": "recomputed" if args.recompute else "stored (396 B/sample)",
+                   "sampler": (f"importance: {w.imp_coarse} coarse + {w.imp_steps} x {w.imp_per_step}"
+                               if w.imp_coarse > 0 else f"stratified {w.n_strat} + depth-guided {w.n_guided}"),
                    "calls": ("gs_forward + gs_backward" if args.split else "gs_forward_backward") +
                             (" + gs_eikonal" if args.eikonal else ""),
                    "loss_terms": "rgb, depth, sdf, fs, smooth" + (", eikonal (lam 1, free-space samples)"
@@ -266,6 +274,8 @@ def run_ours(args):
     }
     if args.diff_report:
         line["differentiation"] = differentiation_report(w, dfr, theta, mirror)
+    if args.sampler_report > 0 and w.imp_coarse > 0:
+        line["sampler_report"] = sampler_report(w, fr, dfr, args.sampler_report)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(w, fr, args.cpu_rays)
     return line
@@ -280,8 +290,11 @@ def _eval_depth(ctx, w, dfr, gt, theta, sampler, q=None, R=65536, seed=99):
     import paper_2206_14735_gb300 as gs
     R = min(R, w.rays)
     if sampler == "plain":
-        b = gs.Batch.allocate(R, w.n_samples, 0)
+        b = gs.Batch.allocate(R, w.n_strat + w.n_guided, 0)
         ctx.sample_rays(dfr, seed, 0, b)
+    elif sampler == "importance":
+        b = gs.Batch.allocate(R, w.n_samples, 0)
+        ctx.sample_importance(dfr, theta, seed, 0, b)
     else:
         b = gs.Batch.allocate(R, w.prop_samples, 0)
         ctx.proposal_sample(dfr, seed, 0, b, theta=theta, prop=q)
@@ -297,6 +310,46 @@ def _eval_depth(ctx, w, dfr, gt, theta, sampler, q=None, R=65536, seed=99):
     return {"depth_l1_gt_m": round(float(np.abs(d_hat - g)[ok].mean()), 5),
             "depth_l1_gt_dropped_m": round(float(np.abs(d_hat - g)[drop].mean()), 5) if drop.any() else None,
             "rays": int(R), "dropped_rays": int(drop.sum())}
+
+
+def sampler_report(w, fr, dfr, steps):
+    """Trains the workload's plain form (stratified + depth-guided samples) and the paper's
+    hierarchical importance form from the same initial parameters for `steps` steps each;
+    reports the host wall clock per step and the rendered-depth error against the noise-free
+    depth on fresh rays, each model with its own sampler and both with the plain one."""
+    import torch
+
+    import paper_2206_14735_gb300 as gs
+    import scenegen as sg
+    out = {}
+    for form in ("plain", "importance"):
+        wf = w if form == "importance" else w.with_(imp_coarse=0, imp_steps=0, imp_per_step=0)
+        ctx = gs.Context(wf, store_activations=True)
+        theta = torch.from_numpy(sg.init_params(wf)).cuda()
+        grad, m, v = torch.zeros_like(theta), torch.zeros_like(theta), torch.zeros_like(theta)
+        loss = torch.empty(6, device="cuda")
+        batch = gs.Batch.allocate(wf.rays, wf.n_samples, wf.n_smooth)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for k in range(steps):
+            if form == "importance":
+                ctx.sample_importance(dfr, theta, 5, k, batch)
+            else:
+                ctx.sample_rays(dfr, 5, k, batch)
+            ctx.forward_backward(theta, batch, None, loss, grad)
+            ctx.adam_step(theta, grad, m, v, k + 1, wf.lr_grid, wf.lr_mlp, wf.betas[0], wf.betas[1], wf.adam_eps)
+        torch.cuda.synchronize()
+        dt = time.perf_counter() - t0
+        ctx.sync_status()
+        res = {"steps": steps, "ms_per_step": round(1e3 * dt / steps, 3), "rays_per_s": round(wf.rays * steps / dt, 1),
+               "samples_per_ray": wf.n_samples, "with_own_sampler": _eval_depth(ctx, wf, dfr, fr.gt_depth, theta, form)}
+        if form == "importance":
+            res["with_plain_sampler"] = _eval_depth(ctx, wf, dfr, fr.gt_depth, theta, "plain")
+        out[form] = res
+        ctx.close()
+    out["what"] = ("both forms trained from the same initial parameters on the same frames; depth error of the "
+                   "rendered depth against the noise-free depth on fresh rays (host wall clock per step)")
+    return out
 
 
 def proposal_report(w, fr, dfr, steps):
@@ -506,7 +559,10 @@ def _oracle_sample_step(w, fr, R, P, n_adam, reps_min_s, reps_max):
     k = 0
     while True:
         t0 = time.perf_counter()
-        bt = oc.sample_rays(cfg, ofr, 3, k, R)
+        if w.imp_coarse > 0:
+            bt = oc.sample_importance(cfg, ofr, theta, 3, k, R, w.imp_coarse, w.imp_steps, w.imp_per_step)
+        else:
+            bt = oc.sample_rays(cfg, ofr, 3, k, R)
         sm = oc.sample_smooth(cfg, ofr, 3, k, P)
         out = oc.step(cfg, theta, bt, sm)
         g = np.ascontiguousarray(out["grad"][:n_adam])
@@ -584,6 +640,9 @@ def main():
     ap.add_argument("--lr-prop", type=float, default=None, help="proposal workloads: override the proposal's lr")
     ap.add_argument("--prop-report", type=int, default=0,
                     help="proposal workloads: train plain and proposal forms this many steps and compare depth")
+    ap.add_argument("--sampler-report", type=int, default=0,
+                    help="importance workloads: train the plain and the importance form this many steps and compare "
+                         "depth")
     args = ap.parse_args()
     if args.impl == "reference":
         line = run_reference(args)

@@ -39,7 +39,7 @@ extern "C" {
 #define GS_LEVELS 4
 #define GS_FEAT 4
 #define GS_MLP_PARAMS 1684
-#define GS_MAX_SAMPLES 128 /* n_strat + n_guided per ray */
+#define GS_MAX_SAMPLES 160 /* samples per ray of any batch (5 chunks of 32) */
 #define GS_NUM_LOSS 6      /* rgb, depth, sdf, fs, smooth, total */
 #define GS_PROP_BINS 32    /* bins of the learned proposal over [near_m, far_m] */
 #define GS_PROP_PARAMS 1473 /* proposal network: W1[32][11], b1[32], W2[32][32], b2[32], w3[32], b3 */
@@ -88,6 +88,11 @@ typedef struct gs_config {
   int32_t prop_samples;       /* learned proposal sampler (not part of the paper): samples per
                                  ray of a proposal batch, 2..32; 0 disables gs_proposal_* */
   int32_t prop_guided;        /* of those, samples stratified over [D - g, D + g] when D > 0 */
+  int32_t imp_coarse;         /* hierarchical importance sampler (Sec. 3.2): coarse samples per ray,
+                                 >= 2; 0 disables gs_sample_importance */
+  int32_t imp_steps;          /* importance steps (Sec. 4: 3) */
+  int32_t imp_per_step;       /* samples added per step, 1..32 (Sec. 4: 12); batches of this sampler
+                                 hold imp_coarse + imp_steps * imp_per_step <= 160 samples per ray */
 } gs_config;
 
 /* Posed RGB-D frames resident in device memory (Sec. 3: {I_t, D_t}, xi_t). */
@@ -137,7 +142,8 @@ int64_t gs_param_count(const gs_config* cfg, int64_t* n_grid);
  * by (seed, stream, step, index, slot); every quantity is computed in binary32 with
  * round-to-nearest and no contraction, so results are reproducible bit for bit.
  * batch->R, N, P select the sizes; N must equal n_strat + n_guided.  The render entry
- * points also accept batches of N = prop_samples made by gs_proposal_sample. */
+ * points also accept batches of N = prop_samples made by gs_proposal_sample and of
+ * N = imp_coarse + imp_steps * imp_per_step made by gs_sample_importance. */
 gs_status gs_sample_rays(gs_ctx* ctx, const gs_frames* frames, uint64_t seed, uint32_t step, gs_batch* batch,
                          void* stream);
 
@@ -195,6 +201,20 @@ gs_status gs_query_sdf(gs_ctx* ctx, const float* theta, const float* x, int32_t 
 gs_status gs_proposal_sample(gs_ctx* ctx, const float* theta, const float* prop, const gs_frames* frames,
                              uint64_t seed, uint32_t step, const float* pdf_in, float* pdf_out, gs_batch* batch,
                              void* stream);
+
+/* Hierarchical importance sampling (Sec. 3.2: from N_c coarse samples, 3 steps each add 12
+ * samples drawn from the weights of the samples so far, as in NeuS; Sec. 4: N_c = 96,
+ * N_f = 36).  The rays (pix, origin, dir, rgb, depth) and the smoothness points are those of
+ * gs_sample_rays for the same (seed, step).  Per ray: imp_coarse depths stratified over
+ * [near_m, far_m]; then imp_steps times: phi at the current samples (theta, FP32), the NeuS
+ * weights w_k = T_k alpha_k of Sec. 3.2 Eq. volume_rendering_alpha with s = exp(kappa),
+ * interval masses w_k + 1e-5 over [t_k, t_k+1], and imp_per_step stratified inverse-CDF
+ * draws u_j = (j + xi_j) / imp_per_step, each placed linearly inside its interval and merged
+ * into the sorted depths (an existing depth first on ties); classes as in gs_sample_rays.
+ * batch->N must be imp_coarse + imp_steps * imp_per_step; needs imp_coarse > 0 in the
+ * configuration (GS_ERR_UNSUPPORTED otherwise).  theta 16-byte aligned. */
+gs_status gs_sample_importance(gs_ctx* ctx, const float* theta, const gs_frames* frames, uint64_t seed, uint32_t step,
+                               gs_batch* batch, void* stream);
 
 /* Training step of the proposal: for every ray the weights batch->w at the depths batch->t
  * (from a forward pass of the main model on this batch, any sampler) are summed per bin,

@@ -40,6 +40,9 @@ def make_config(workload, max_rays=None, max_smooth=None, store_activations=Fals
     c.store_activations = 1 if store_activations else 0
     c.prop_samples = int(getattr(workload, "prop_samples", 0))
     c.prop_guided = int(getattr(workload, "prop_guided", 0))
+    c.imp_coarse = int(getattr(workload, "imp_coarse", 0))
+    c.imp_steps = int(getattr(workload, "imp_steps", 0))
+    c.imp_per_step = int(getattr(workload, "imp_per_step", 0))
     return c
 
 
@@ -169,6 +172,12 @@ class Context:
         b = batch.struct()
         self._check(self.L.gs_proposal_sample(self.h, _ptr(theta), _ptr(prop), ctypes.byref(frames.s), seed, step,
                                               _ptr(pdf_in), _ptr(pdf_out), ctypes.byref(b), _stream()))
+
+    def sample_importance(self, frames: DeviceFrames, theta, seed: int, step: int, batch: Batch):
+        """Hierarchical importance sampling of the rays of sample_rays(seed, step)."""
+        b = batch.struct()
+        self._check(self.L.gs_sample_importance(self.h, _ptr(theta), ctypes.byref(frames.s), seed, step,
+                                                ctypes.byref(b), _stream()))
 
     def proposal_backward(self, theta, prop, batch: Batch, prop_grad, ce=None):
         b = batch.struct()

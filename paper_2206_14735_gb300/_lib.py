@@ -18,7 +18,7 @@ STATUS = {0: "GS_OK", 1: "GS_ERR_INVALID_ARG", 2: "GS_ERR_SHAPE", 3: "GS_ERR_ALI
           5: "GS_ERR_DEVICE", 6: "GS_ERR_UNSUPPORTED"}
 
 EXPORTS = ["gs_create", "gs_destroy", "gs_param_count", "gs_sample_rays", "gs_forward", "gs_backward",
-           "gs_forward_backward", "gs_adam_step", "gs_query_sdf", "gs_query_sdf_backward", "gs_eikonal", "gs_proposal_sample", "gs_proposal_backward", "gs_voxel_index", "gs_sync_status",
+           "gs_forward_backward", "gs_adam_step", "gs_query_sdf", "gs_query_sdf_backward", "gs_eikonal", "gs_sample_importance", "gs_proposal_sample", "gs_proposal_backward", "gs_voxel_index", "gs_sync_status",
            "gs_last_error", "gs_forward_backward_noalloc"]
 
 
@@ -29,7 +29,8 @@ class GsConfig(ctypes.Structure):
                 ("kappa_fs", ctypes.c_float), ("lam", ctypes.c_float * 5), ("max_rays", ctypes.c_int32),
                 ("max_smooth", ctypes.c_int32), ("delta_s", ctypes.c_float), ("precision", ctypes.c_int32),
                 ("store_activations", ctypes.c_int32), ("prop_samples", ctypes.c_int32),
-                ("prop_guided", ctypes.c_int32)]
+                ("prop_guided", ctypes.c_int32), ("imp_coarse", ctypes.c_int32), ("imp_steps", ctypes.c_int32),
+                ("imp_per_step", ctypes.c_int32)]
 
 
 class GsFrames(ctypes.Structure):
@@ -85,6 +86,8 @@ def lib():
             L.gs_proposal_backward.restype = i32
             L.gs_proposal_backward.argtypes = [vp, vp, vp, vp, vp, vp, vp]
             L.gs_eikonal.restype = i32
+            L.gs_sample_importance.restype = i32
+            L.gs_sample_importance.argtypes = [vp, vp, vp, ctypes.c_uint64, ctypes.c_uint32, vp, vp]
             L.gs_eikonal.argtypes = [vp, vp, vp, vp, vp, vp, vp]
             L.gs_query_sdf_backward.restype = i32
             L.gs_query_sdf_backward.argtypes = [vp, vp, vp, i32, vp, vp, vp, vp]

@@ -28,11 +28,14 @@ long long level_floats(const gs_config* c, int l) {
   return (long long)c->dims[l][0] * c->dims[l][1] * c->dims[l][2] * GS_FEAT;
 }
 
+int imp_samples(const gs_config* c) { return c->imp_coarse + c->imp_steps * c->imp_per_step; }
+
 gs_status check_batch(gs_ctx* ctx, const gs_batch* b, bool need_smooth_arrays) {
   if (!b) return fail(ctx, GS_ERR_INVALID_ARG, "batch is NULL");
   if (b->R < 0 || b->R > ctx->cfg.max_rays) return fail(ctx, GS_ERR_SHAPE, "batch R outside [0, max_rays]");
-  if (b->N != ctx->cfg.n_strat + ctx->cfg.n_guided && !(ctx->cfg.prop_samples > 0 && b->N == ctx->cfg.prop_samples))
-    return fail(ctx, GS_ERR_SHAPE, "batch N is neither n_strat + n_guided nor prop_samples");
+  if (b->N != ctx->cfg.n_strat + ctx->cfg.n_guided && !(ctx->cfg.prop_samples > 0 && b->N == ctx->cfg.prop_samples) &&
+      !(ctx->cfg.imp_coarse > 0 && b->N == imp_samples(&ctx->cfg)))
+    return fail(ctx, GS_ERR_SHAPE, "batch N is neither n_strat + n_guided, prop_samples nor the importance sampler's");
   if (b->P < 0 || b->P > ctx->cfg.max_smooth) return fail(ctx, GS_ERR_SHAPE, "batch P outside [0, max_smooth]");
   if (!b->counts) return fail(ctx, GS_ERR_INVALID_ARG, "batch counts is NULL");
   if (b->R > 0 && (!b->origin || !b->dir || !b->rgb || !b->depth || !b->t || !b->cls))
@@ -80,7 +83,12 @@ gs_status gs_create(const gs_config* cfg, gs_ctx** out) {
       return fail(nullptr, GS_ERR_UNSUPPORTED, "gs_create: levels 0 and 1 must have fewer than 2^31 vertices");
   const int N = cfg->n_strat + cfg->n_guided;
   if (cfg->n_strat < 1 || cfg->n_guided < 0 || N < 2) return fail(nullptr, GS_ERR_INVALID_ARG, "gs_create: need n_strat >= 1 and N >= 2");
-  if (N > 128) return fail(nullptr, GS_ERR_UNSUPPORTED, "gs_create: this build renders at most 128 samples per ray");
+  if (N > GS_MAX_SAMPLES) return fail(nullptr, GS_ERR_UNSUPPORTED, "gs_create: this build renders at most 160 samples per ray");
+  if (cfg->imp_coarse != 0 &&
+      (cfg->imp_coarse < 2 || cfg->imp_steps < 0 || cfg->imp_per_step < 1 || cfg->imp_per_step > 32 ||
+       imp_samples(cfg) > GS_MAX_SAMPLES))
+    return fail(nullptr, GS_ERR_INVALID_ARG,
+                "gs_create: the importance sampler needs imp_coarse >= 2, 1 <= imp_per_step <= 32 and at most 160 samples");
   if (!(cfg->far_m > cfg->near_m) || !(cfg->trunc > 0.0f) || !(cfg->guide_half >= 0.0f))
     return fail(nullptr, GS_ERR_INVALID_ARG, "gs_create: bad near/far/trunc/guide_half");
   if (cfg->max_rays < 0 || cfg->max_smooth < 0) return fail(nullptr, GS_ERR_INVALID_ARG, "gs_create: negative batch bound");
@@ -111,6 +119,9 @@ gs_status gs_create(const gs_config* cfg, gs_ctx** out) {
   c->render_ctas = kRenderCtasPerSm * c->num_sms;
   c->n_parts = c->render_ctas + kSmoothCtas;
   c->eik_ctas = kEikCtasPerSm * c->num_sms;
+  c->max_n = N;
+  if (cfg->prop_samples > c->max_n) c->max_n = cfg->prop_samples;
+  if (cfg->imp_coarse > 0 && imp_samples(cfg) > c->max_n) c->max_n = imp_samples(cfg);
   const float dl[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 1.f};
   if (cudaMalloc(&c->loss_part, sizeof(float) * kLossPad * c->n_parts) != cudaSuccess ||
       cudaMalloc(&c->mlp_part, sizeof(float) * kMlpPad * c->n_parts) != cudaSuccess ||
@@ -124,7 +135,7 @@ gs_status gs_create(const gs_config* cfg, gs_ctx** out) {
       (cfg->prop_samples > 0 &&
        cudaMalloc(&c->prop_part, sizeof(float) * gs_prop_part_floats(c->num_sms)) != cudaSuccess) ||
       (cfg->store_activations &&
-       cudaMalloc(&c->store, c->store_bytes = (size_t)cfg->max_rays * N * kStoreFloatsPerSample * sizeof(float)) !=
+       cudaMalloc(&c->store, c->store_bytes = (size_t)cfg->max_rays * c->max_n * kStoreFloatsPerSample * sizeof(float)) !=
            cudaSuccess)) {
     gs_status s = cuda_fail(nullptr, "gs_create: workspace allocation");
     gs_destroy(c);
@@ -277,6 +288,24 @@ gs_status gs_proposal_sample(gs_ctx* ctx, const float* theta, const float* prop,
   ctx->last_stream = st;
   s = gs_launch_prop_sample(ctx, theta, prop, frames, seed, step, pdf_in, pdf_out, batch, st);
   return s == GS_OK ? s : cuda_fail(ctx, "gs_proposal_sample");
+}
+
+gs_status gs_sample_importance(gs_ctx* ctx, const float* theta, const gs_frames* frames, uint64_t seed, uint32_t step,
+                               gs_batch* batch, void* stream) {
+  if (!ctx) return fail(nullptr, GS_ERR_INVALID_ARG, "gs_sample_importance: ctx is NULL");
+  if (ctx->cfg.imp_coarse <= 0) return fail(ctx, GS_ERR_UNSUPPORTED, "gs_sample_importance: imp_coarse is 0");
+  gs_status s = check_frames(ctx, frames, "gs_sample_importance");
+  if (s != GS_OK) return s;
+  s = check_batch(ctx, batch, true);
+  if (s != GS_OK) return s;
+  if (batch->N != imp_samples(&ctx->cfg))
+    return fail(ctx, GS_ERR_SHAPE, "gs_sample_importance: batch N != imp_coarse + imp_steps * imp_per_step");
+  if (batch->R > 0 && !theta) return fail(ctx, GS_ERR_INVALID_ARG, "gs_sample_importance: theta is NULL");
+  if (batch->R > 0 && !aligned16(theta)) return fail(ctx, GS_ERR_ALIGN, "gs_sample_importance: theta is not 16-byte aligned");
+  cudaStream_t st = (cudaStream_t)stream;
+  ctx->last_stream = st;
+  s = gs_launch_importance(ctx, theta, frames, seed, step, batch, st);
+  return s == GS_OK ? s : cuda_fail(ctx, "gs_sample_importance");
 }
 
 gs_status gs_proposal_backward(gs_ctx* ctx, const float* theta, const float* prop, const gs_batch* batch,

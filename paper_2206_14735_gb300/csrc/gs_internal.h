@@ -22,6 +22,7 @@ struct gs_ctx {
   int num_sms = 0;
   int render_ctas = 0;  // persistent CTAs of the fused render kernel
   int n_parts = 0;      // render_ctas + kSmoothCtas
+  int max_n = 0;        // most samples per ray of any batch form (sizes the activation store)
   float* loss_part = nullptr;
   float* mlp_part = nullptr;
   float* default_dloss = nullptr;  // (0,0,0,0,0,1)
@@ -60,6 +61,8 @@ gs_status gs_launch_prop_sample(const gs_ctx* ctx, const float* theta, const flo
                                 cudaStream_t st);
 gs_status gs_launch_prop_backward(const gs_ctx* ctx, const float* theta, const float* q, const gs_batch* b,
                                   float* grad, float* ce, cudaStream_t st);
+gs_status gs_launch_importance(const gs_ctx* ctx, const float* theta, const gs_frames* f, uint64_t seed,
+                               uint32_t step, const gs_batch* b, cudaStream_t st);
 gs_status gs_launch_eikonal(const gs_ctx* ctx, const float* theta, const gs_batch* b, const float* dloss, float* loss,
                             float* grad, cudaStream_t st);
 gs_status gs_launch_query_backward(const gs_ctx* ctx, const float* theta, const float* x, int P, const float* dsdf,

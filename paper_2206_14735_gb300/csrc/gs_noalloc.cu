@@ -61,8 +61,8 @@ extern "C" gs_status gs_forward_backward_noalloc(const gs_config* cfg, const flo
   if (cfg->precision != GS_PREC_FP32)
     return noalloc_fail(GS_ERR_UNSUPPORTED, "gs_forward_backward_noalloc: FP32 form only");
   const int N = cfg->n_strat + cfg->n_guided;
-  if (cfg->n_strat < 1 || cfg->n_guided < 0 || N < 2 || N > 128)
-    return noalloc_fail(GS_ERR_SHAPE, "gs_forward_backward_noalloc: samples per ray must be in [2, 128]");
+  if (cfg->n_strat < 1 || cfg->n_guided < 0 || N < 2 || N > GS_MAX_SAMPLES)
+    return noalloc_fail(GS_ERR_SHAPE, "gs_forward_backward_noalloc: samples per ray must be in [2, 160]");
   if (!theta || !loss || !grad || !batch) return noalloc_fail(GS_ERR_INVALID_ARG, "gs_forward_backward_noalloc: NULL argument");
   if ((reinterpret_cast<uintptr_t>(theta) & 15u) || (reinterpret_cast<uintptr_t>(grad) & 15u))
     return noalloc_fail(GS_ERR_ALIGN, "gs_forward_backward_noalloc: theta and grad must be 16-byte aligned");
@@ -100,6 +100,7 @@ extern "C" gs_status gs_forward_backward_noalloc(const gs_config* cfg, const flo
   c.device = dev;
   c.num_sms = sms;
   c.render_ctas = kRenderCtasPerSm * sms;
+  c.max_n = N;
   c.loss_part = scratch;
   c.mlp_part = scratch + (size_t)kNoAllocRows * kLossPad;
   c.default_dloss = scratch + (size_t)kNoAllocRows * (kLossPad + kMlpPad);

@@ -8,10 +8,12 @@ extern template gs_status launch_tc_n<PrecBF16x3, 1>(const gs_ctx*, RenderTcArgs
 extern template gs_status launch_tc_n<PrecBF16x3, 2>(const gs_ctx*, RenderTcArgs&, int, cudaStream_t);
 extern template gs_status launch_tc_n<PrecBF16x3, 3>(const gs_ctx*, RenderTcArgs&, int, cudaStream_t);
 extern template gs_status launch_tc_n<PrecBF16x3, 4>(const gs_ctx*, RenderTcArgs&, int, cudaStream_t);
+extern template gs_status launch_tc_n<PrecBF16x3, 5>(const gs_ctx*, RenderTcArgs&, int, cudaStream_t);
 extern template gs_status launch_tc_n<PrecBF16, 1>(const gs_ctx*, RenderTcArgs&, int, cudaStream_t);
 extern template gs_status launch_tc_n<PrecBF16, 2>(const gs_ctx*, RenderTcArgs&, int, cudaStream_t);
 extern template gs_status launch_tc_n<PrecBF16, 3>(const gs_ctx*, RenderTcArgs&, int, cudaStream_t);
 extern template gs_status launch_tc_n<PrecBF16, 4>(const gs_ctx*, RenderTcArgs&, int, cudaStream_t);
+extern template gs_status launch_tc_n<PrecBF16, 5>(const gs_ctx*, RenderTcArgs&, int, cudaStream_t);
 
 // ------------------------------------------------------------------------------------
 // combine per-CTA partials: losses in FP64, decoder gradients in a fixed order
@@ -219,7 +221,7 @@ gs_status gs_launch_render(const gs_ctx* ctx, const float* theta, const uint16_t
       if (!encode_level_map(ctx, theta, 2 + q, &a.tmap[q])) return GS_ERR_CUDA;
   a.store = ctx->store;
   a.w_out = b->w;
-  a.store_stride = (long long)ctx->cfg.max_rays * (ctx->cfg.n_strat + ctx->cfg.n_guided);
+  a.store_stride = (long long)ctx->cfg.max_rays * ctx->max_n;
   const int nch = (b->N + 31) / 32;
   if (ctx->cfg.precision == GS_PREC_BF16) {
     switch (nch) {
@@ -227,6 +229,7 @@ gs_status gs_launch_render(const gs_ctx* ctx, const float* theta, const uint16_t
       case 2: return launch_tc_n<PrecBF16, 2>(ctx, a, mode, st);
       case 3: return launch_tc_n<PrecBF16, 3>(ctx, a, mode, st);
       case 4: return launch_tc_n<PrecBF16, 4>(ctx, a, mode, st);
+      case 5: return launch_tc_n<PrecBF16, 5>(ctx, a, mode, st);
       default: return GS_ERR_UNSUPPORTED;
     }
   }
@@ -235,6 +238,7 @@ gs_status gs_launch_render(const gs_ctx* ctx, const float* theta, const uint16_t
     case 2: return launch_tc_n<PrecBF16x3, 2>(ctx, a, mode, st);
     case 3: return launch_tc_n<PrecBF16x3, 3>(ctx, a, mode, st);
     case 4: return launch_tc_n<PrecBF16x3, 4>(ctx, a, mode, st);
+    case 5: return launch_tc_n<PrecBF16x3, 5>(ctx, a, mode, st);
     default: return GS_ERR_UNSUPPORTED;
   }
 }

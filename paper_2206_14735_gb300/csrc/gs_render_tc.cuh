@@ -1110,7 +1110,9 @@ gs_status launch_tc_t(const gs_ctx* ctx, RenderTcArgs& a, cudaStream_t st) {
 
 template <class P, int NCH>
 gs_status launch_tc_n(const gs_ctx* ctx, RenderTcArgs& a, int mode, cudaStream_t st) {
-  constexpr int GR = kRenderGroups;  // tile groups of 128 tensor-memory columns in one CTA per SM
+  // tile groups in one CTA per SM; rays of 5 chunks keep more per-ray state in registers,
+  // which only fits with 2 groups (255 registers per thread)
+  constexpr int GR = NCH > 4 ? 2 : kRenderGroups;
   if (mode == 1) return launch_tc_t<P, NCH, GR, true, false>(ctx, a, st);
   if (mode == 2) return launch_tc_t<P, NCH, GR, false, true>(ctx, a, st);
   return launch_tc_t<P, NCH, GR, true, true>(ctx, a, st);

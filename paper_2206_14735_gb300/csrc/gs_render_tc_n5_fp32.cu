@@ -1,0 +1,6 @@
+// Fused render kernel (tcgen05 decoders, FP32 form) instantiated for rays of up to 160 samples.
+#include "gs_render_tc.cuh"
+
+namespace gs {
+template gs_status launch_tc_n<PrecBF16x3, 5>(const gs_ctx*, RenderTcArgs&, int, cudaStream_t);
+}  // namespace gs

@@ -257,10 +257,16 @@ class Workload:
     prop_samples: int = 0   # learned proposal: samples per ray of a proposal batch (0 = off)
     prop_guided: int = 8    # of those, depth-guided when D > 0
     lr_prop: float = 1e-3
+    imp_coarse: int = 0     # hierarchical importance sampler: coarse samples (0 = off)
+    imp_steps: int = 0      # importance steps
+    imp_per_step: int = 0   # samples added per step
     extra: dict = field(default_factory=dict)
 
     @property
     def n_samples(self) -> int:
+        """Samples per ray of the workload's batches (the importance sampler's when it is on)."""
+        if self.imp_coarse > 0:
+            return self.imp_coarse + self.imp_steps * self.imp_per_step
         return self.n_strat + self.n_guided
 
     @property
@@ -298,6 +304,9 @@ WORKLOADS = {
 WORKLOADS["room-bf16-32768x96"] = WORKLOADS["room-8192x96"].with_(name="room-bf16-32768x96", rays=32768,
                                                                    precision="bf16")
 WORKLOADS["room-diff-65536x96"] = WORKLOADS["room-8192x96"].with_(name="room-diff-65536x96", rays=65536)
+# the paper's own sampler (Sec. 3.2, Sec. 4): 96 coarse samples and 3 importance steps of 12
+WORKLOADS["room-imp-8192x132"] = WORKLOADS["room-8192x96"].with_(name="room-imp-8192x132", imp_coarse=96, imp_steps=3,
+                                                                  imp_per_step=12)
 # learned-proposal form: 30% of every depth frame zeroed in contiguous blobs, 65536 rays,
 # 32 samples per ray (24 drawn from the proposal + 8 depth-guided), plain 64 + 32 as fallback
 WORKLOADS["room-prop-65536x32"] = WORKLOADS["room-8192x96"].with_(name="room-prop-65536x32", rays=65536,
