@@ -130,6 +130,9 @@ gs_status gs_create(const gs_config* cfg, gs_ctx** out) {
       cudaMalloc(&c->eik_part, sizeof(float) * kEikCtasPerSm * c->num_sms) != cudaSuccess ||
       cudaMalloc(&c->eik_ticket, sizeof(unsigned)) != cudaSuccess ||
       cudaMemset(c->eik_ticket, 0, sizeof(unsigned)) != cudaSuccess ||
+      cudaStreamCreateWithFlags(&c->side, cudaStreamNonBlocking) != cudaSuccess ||
+      cudaEventCreateWithFlags(&c->ev_fork, cudaEventDisableTiming) != cudaSuccess ||
+      cudaEventCreateWithFlags(&c->ev_join, cudaEventDisableTiming) != cudaSuccess ||
       cudaMemcpy(c->default_dloss, dl, sizeof(dl), cudaMemcpyHostToDevice) != cudaSuccess ||
       cudaMemset(c->status, 0, sizeof(int)) != cudaSuccess ||
       (cfg->prop_samples > 0 &&
@@ -155,6 +158,9 @@ void gs_destroy(gs_ctx* ctx) {
   cudaFree(ctx->prop_part);
   cudaFree(ctx->eik_part);
   cudaFree(ctx->eik_ticket);
+  if (ctx->ev_fork) cudaEventDestroy(ctx->ev_fork);
+  if (ctx->ev_join) cudaEventDestroy(ctx->ev_join);
+  if (ctx->side) cudaStreamDestroy(ctx->side);
   delete ctx;
 }
 
@@ -195,10 +201,22 @@ static gs_status render_common(gs_ctx* ctx, const char* who, const float* theta,
   cudaStream_t st = (cudaStream_t)stream;
   ctx->last_stream = st;
   const float* dl = dloss ? dloss : ctx->default_dloss;
+  // The smoothness kernel is independent of the render kernel (its own partial rows, atomics
+  // into grad).  On a side stream that forks from the calling stream before the render launch,
+  // and launched after it, it runs on the SMs that the render kernel's last ray-quads leave
+  // idle.  The calling stream waits for it before the combine (a fork-join that stream
+  // capture records as such).
+  const bool fork = batch->R > 0 && batch->P > 0;
+  if (fork && (cudaEventRecord(ctx->ev_fork, st) != cudaSuccess ||
+               cudaStreamWaitEvent(ctx->side, ctx->ev_fork, 0) != cudaSuccess))
+    return cuda_fail(ctx, who);
   if (batch->R > 0 &&
       gs_launch_render(ctx, theta, theta_bf16, batch, dl, grad, rgb_hat, d_hat, wsum, mode, st) != GS_OK)
     return cuda_fail(ctx, who);
-  if (gs_launch_smooth(ctx, theta, batch, dl, grad, mode, st) != GS_OK) return cuda_fail(ctx, who);
+  if (gs_launch_smooth(ctx, theta, batch, dl, grad, mode, fork ? ctx->side : st) != GS_OK) return cuda_fail(ctx, who);
+  if (fork && (cudaEventRecord(ctx->ev_join, ctx->side) != cudaSuccess ||
+               cudaStreamWaitEvent(st, ctx->ev_join, 0) != cudaSuccess))
+    return cuda_fail(ctx, who);
   // partial rows: render CTAs (if any rays) then smoothness CTAs (if any points)
   gs_ctx tmp = *ctx;
   if (batch->R == 0 || batch->P == 0) {

@@ -36,6 +36,8 @@ struct gs_ctx {
   float* eik_part = nullptr;         // its per-CTA loss sums
   unsigned* eik_ticket = nullptr;    // CTAs finished in the running call (0 between calls)
   cudaStream_t last_stream = nullptr;
+  cudaStream_t side = nullptr;       // the smoothness kernel runs here beside the render kernel
+  cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
   std::string last_error;
 };
 

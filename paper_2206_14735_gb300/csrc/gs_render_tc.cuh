@@ -625,6 +625,9 @@ __global__ void __launch_bounds__(GR * kGroupThreads, 1) render_tc_kernel(const 
   bool dw_acc = false;  // the weight-gradient accumulators hold a first tile (accumulate from then on)
   float w4acc[3] = {0.f, 0.f, 0.f}, b4acc = 0.f;  // this warp's dW4[.][lane] and (lanes < 3) db4[lane]
 
+  // ray-quads are dealt CTA-major (quad = round * G + CTA * GR + gi): when the quads do not
+  // divide evenly, whole SMs finish a round early, and the smoothness kernel, launched beside
+  // this one on another stream, runs there
   for (int quad = blockIdx.x * GR + gi; quad * 4 < a.R && alive; quad += gridDim.x * GR) {
     const int ray = quad * 4 + warp_g;
     const bool has_ray = ray < a.R;
