@@ -7,6 +7,10 @@ points, 75.7 M parameters).  Frames are rendered once on the host and stay resid
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
 
+The plain sampler reads no parameters, so each step's batch is sampled on a side stream
+during the step before (double-buffered; --no-pipeline samples in line); the work per step
+is the same.
+
 --impl reference times the FP64 CPU oracle (the only baseline this method has here) on
 the host cores, each step a bounded sample of the same workload.  Under torchrun each rank
 runs an independent replica (rays are independent; no collective) and rank 0 prints the
@@ -126,33 +130,68 @@ def run_ours(args):
     seed = 3 + 1000 * rank
     b1, b2 = w.betas
 
-    def sample(k):
+    def sample(k, b=batch):
         if w.imp_coarse > 0:  # the paper's hierarchical importance sampler (reads theta)
-            ctx.sample_importance(dfr, theta, seed, k, batch)
+            ctx.sample_importance(dfr, theta, seed, k, b)
         else:
-            ctx.sample_rays(dfr, seed, k, batch)
+            ctx.sample_rays(dfr, seed, k, b)
+
+    # The plain sampler does not read theta: the batch of step k + 1 is sampled on a side
+    # stream (its own context, a second batch buffer) while step k renders and updates, and
+    # lands on the SMs that the render kernel's last round leaves idle.  The importance
+    # sampler reads theta, so it stays in line.
+    pipelined = w.imp_coarse == 0 and not args.no_pipeline
+    if pipelined:
+        ctx_s = gs.Context(w)
+        side = torch.cuda.Stream()
+        batches = [batch, gs.Batch.allocate(w.rays, w.n_samples, w.n_smooth)]
+        ev_ready = [torch.cuda.Event(), torch.cuda.Event()]  # batch j sampled
+        ev_free = [torch.cuda.Event(), torch.cuda.Event()]   # batch j no longer read
+        sample_ev = {}
+
+        def issue_sample(k):
+            j = k % 2
+            side.wait_event(ev_free[j])
+            e = (torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+            e[0].record(side)
+            with torch.cuda.stream(side):
+                ctx_s.sample_rays(dfr, seed, k, batches[j])
+            e[1].record(side)
+            ev_ready[j].record(side)
+            sample_ev[k] = e
+    else:
+        batches = [batch, batch]
 
     def step(k, ev=None):
+        b = batches[k % 2]
         if ev is not None:
             ev[0].record(stream)
-        sample(k)
+        if pipelined:
+            stream.wait_event(ev_ready[k % 2])
+        else:
+            sample(k)
         if ev is not None:
             ev[1].record(stream)
         if args.split:
-            ctx.forward(theta, batch, loss, theta_bf16=mirror)
-            ctx.backward(theta, batch, None, grad, theta_bf16=mirror)
+            ctx.forward(theta, b, loss, theta_bf16=mirror)
+            ctx.backward(theta, b, None, grad, theta_bf16=mirror)
         else:
-            ctx.forward_backward(theta, batch, None, loss, grad, theta_bf16=mirror)
+            ctx.forward_backward(theta, b, None, loss, grad, theta_bf16=mirror)
         if ev is not None:
             ev[2].record(stream)
         if args.eikonal:
-            ctx.eikonal(theta, batch, loss=eik, grad=grad)
+            ctx.eikonal(theta, b, loss=eik, grad=grad)
         if ev is not None:
             ev[3].record(stream)
+        if pipelined:
+            ev_free[k % 2].record(stream)
+            issue_sample(k + 1)
         ctx.adam_step(theta, grad, m, v, k + 1, w.lr_grid, w.lr_mlp, b1, b2, w.adam_eps, theta_bf16=mirror)
         if ev is not None:
             ev[4].record(stream)
 
+    if pipelined:
+        issue_sample(0)
     for k in range(args.warmup):
         step(k)
     torch.cuda.synchronize()
@@ -177,8 +216,12 @@ def run_ours(args):
     per = {"sample": [], "render": [], "adam": []}
     if args.eikonal:
         per["eikonal"] = []
-    for e in evs:
-        per["sample"].append(e[0].elapsed_time(e[1]))
+    for k, e in enumerate(evs):
+        if pipelined:  # the sampler's own time on the side stream (overlapped with the step before)
+            se = sample_ev[args.warmup + k]
+            per["sample"].append(se[0].elapsed_time(se[1]))
+        else:
+            per["sample"].append(e[0].elapsed_time(e[1]))
         per["render"].append(e[1].elapsed_time(e[2]))
         if args.eikonal:
             per["eikonal"].append(e[2].elapsed_time(e[3]))
@@ -249,6 +292,8 @@ def run_ours(args):
                    "activations": "recomputed" if args.recompute else "stored (396 B/sample)",
                    "sampler": (f"importance: {w.imp_coarse} coarse + {w.imp_steps} x {w.imp_per_step}"
                                if w.imp_coarse > 0 else f"stratified {w.n_strat} + depth-guided {w.n_guided}"),
+                   "pipeline": ("the next step's batch sampled on a side stream during this step (double-buffered)"
+                                if pipelined else "in line"),
                    "calls": ("gs_forward + gs_backward" if args.split else "gs_forward_backward") +
                             (" + gs_eikonal" if args.eikonal else ""),
                    "loss_terms": "rgb, depth, sdf, fs, smooth" + (", eikonal (lam 1, free-space samples)"
@@ -632,6 +677,8 @@ def main():
     ap.add_argument("--recompute", action="store_true",
                     help="recompute the decoder activations in the backward pass instead of storing them")
     ap.add_argument("--split", action="store_true", help="gs_forward then gs_backward instead of the fused call")
+    ap.add_argument("--no-pipeline", action="store_true",
+                    help="sample each step's batch in line instead of during the previous step")
     ap.add_argument("--eikonal", action="store_true",
                     help="add the Eikonal term on the free-space samples (gs_eikonal, lam_eik = 1) to every step")
     ap.add_argument("--prop-pretrain", type=int, default=300,
