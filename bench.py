@@ -91,6 +91,29 @@ class ClockSampler:
                 "reasons": reasons, "samples": len(rows)}
 
 
+def replica_seed(rank: int) -> int:
+    """Each replica samples its own rays: the seed of rank r (rays are independent, so the
+    replicas share nothing and exchange nothing)."""
+    return 3 + 1000 * rank
+
+
+def max_over_ranks(values, world: int, device: str = "cuda"):
+    """Element-wise maximum of per-rank timings over all ranks (the slowest replica sets the
+    whole job's time); the identity on one rank."""
+    if world <= 1:
+        return [float(v) for v in values]
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([float(v) for v in values], device=device, dtype=torch.float64)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return [float(x) for x in t.tolist()]
+
+
+def aggregate_rays_per_s(rays_per_replica_step: int, steps: int, world: int, ms: float) -> float:
+    """Whole-job throughput: the rays every replica processed over the slowest replica's time."""
+    return rays_per_replica_step * steps * world / (ms / 1e3)
+
+
 def dist_env():
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -127,7 +150,7 @@ def run_ours(args):
     loss = torch.empty(6, device="cuda")
     eik = torch.zeros(1, device="cuda")  # L_eik when --eikonal (Sec. 3.3, lam_eik = 1)
     stream = torch.cuda.current_stream()
-    seed = 3 + 1000 * rank
+    seed = replica_seed(rank)
     b1, b2 = w.betas
 
     def sample(k, b=batch):
@@ -255,15 +278,11 @@ def run_ours(args):
         torch.cuda.current_stream().synchronize()
     e2e_s = time.perf_counter() - t1
 
-    if world > 1:
-        t = torch.tensor([ms, e2e_s], device="cuda", dtype=torch.float64)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        ms, e2e_s = float(t[0]), float(t[1])
+    ms, e2e_s = max_over_ranks([ms, e2e_s], world)
     if rank != 0:
         return None
 
-    rays_total = w.rays * args.steps * world
-    value = rays_total / (ms / 1e3)
+    value = aggregate_rays_per_s(w.rays, args.steps, world, ms)
     peaks, kind = _peaks()
     S = w.rays * w.n_samples
     n_grid = w.layout()[1]
@@ -501,13 +520,10 @@ def run_proposal(args):
     clk = clocks.stop()
     ms = start.elapsed_time(stop)
     ctx.sync_status()
-    if world > 1:
-        t = torch.tensor([ms], device="cuda", dtype=torch.float64)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        ms = float(t[0])
+    ms = max_over_ranks([ms], world)[0]
     if rank != 0:
         return None
-    value = w.rays * args.steps * world / (ms / 1e3)
+    value = aggregate_rays_per_s(w.rays, args.steps, world, ms)
     line = {
         "metric": METRIC, "value": round(value, 1), "unit": "rays/s", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": round(ms / args.steps, 4), "higher_is_better": True,
