@@ -185,27 +185,33 @@ def run_ours(args):
     else:
         batches = [batch, batch]
 
-    def step(k, ev=None):
+    def step(k, ev=None, io=None):
+        """One step; io = (dloss on the device, pinned loss and counts buffers) for the
+        end-to-end loop: the upstream seed comes from the host and the results go back."""
         b = batches[k % 2]
+        dl = io[0] if io is not None else None
         if ev is not None:
             ev[0].record(stream)
         if pipelined:
             stream.wait_event(ev_ready[k % 2])
         else:
-            sample(k)
+            sample(k, b)
         if ev is not None:
             ev[1].record(stream)
         if args.split:
             ctx.forward(theta, b, loss, theta_bf16=mirror)
-            ctx.backward(theta, b, None, grad, theta_bf16=mirror)
+            ctx.backward(theta, b, dl, grad, theta_bf16=mirror)
         else:
-            ctx.forward_backward(theta, b, None, loss, grad, theta_bf16=mirror)
+            ctx.forward_backward(theta, b, dl, loss, grad, theta_bf16=mirror)
         if ev is not None:
             ev[2].record(stream)
         if args.eikonal:
             ctx.eikonal(theta, b, loss=eik, grad=grad)
         if ev is not None:
             ev[3].record(stream)
+        if io is not None:  # before the batch is handed back to the sampler
+            io[1].copy_(loss, non_blocking=True)
+            io[2].copy_(b.counts, non_blocking=True)
         if pipelined:
             ev_free[k % 2].record(stream)
             issue_sample(k + 1)
@@ -254,29 +260,32 @@ def run_ours(args):
     lossv = loss.cpu().numpy().tolist() + (eik.cpu().numpy().tolist() if args.eikonal else [])
 
     # ---- end-to-end region: the same steps through the public API with host round trips ----
+    # Every step copies its upstream seed in from pinned host memory and its six losses and
+    # four counts out to a pinned double buffer; the host reads step k's results while step
+    # k + 1 runs (no idle GPU between steps).
     e2e_steps = max(1, min(args.steps, args.e2e_steps))
     dl_host = torch.tensor([0, 0, 0, 0, 0, 1.0], dtype=torch.float32).pin_memory()
-    out_host = torch.empty(6, dtype=torch.float32).pin_memory()
-    cnt_host = torch.empty(4, dtype=torch.int32).pin_memory()
+    outs = [(torch.empty(6, dtype=torch.float32).pin_memory(), torch.empty(4, dtype=torch.int32).pin_memory(),
+             torch.cuda.Event()) for _ in range(2)]
     dl_dev = torch.empty(6, device="cuda")
+    seen = []
     torch.cuda.synchronize()
     t1 = time.perf_counter()
     base = args.warmup + args.steps
     for k in range(e2e_steps):
         dl_dev.copy_(dl_host, non_blocking=True)
-        sample(base + k)
-        if args.split:
-            ctx.forward(theta, batch, loss, theta_bf16=mirror)
-            ctx.backward(theta, batch, dl_dev, grad, theta_bf16=mirror)
-        else:
-            ctx.forward_backward(theta, batch, dl_dev, loss, grad, theta_bf16=mirror)
-        if args.eikonal:
-            ctx.eikonal(theta, batch, loss=eik, grad=grad)
-        ctx.adam_step(theta, grad, m, v, base + k + 1, w.lr_grid, w.lr_mlp, b1, b2, w.adam_eps, theta_bf16=mirror)
-        out_host.copy_(loss, non_blocking=True)
-        cnt_host.copy_(batch.counts, non_blocking=True)
-        torch.cuda.current_stream().synchronize()
+        o = outs[k % 2]
+        step(base + k, io=(dl_dev, o[0], o[1]))
+        o[2].record(stream)
+        if k >= 1:
+            p = outs[(k - 1) % 2]
+            p[2].synchronize()
+            seen.append((float(p[0][5]), int(p[1][0])))
+    p = outs[(e2e_steps - 1) % 2]
+    p[2].synchronize()
+    seen.append((float(p[0][5]), int(p[1][0])))
     e2e_s = time.perf_counter() - t1
+    assert len(seen) == e2e_steps and all(math.isfinite(x) for x, _ in seen)
 
     ms, e2e_s = max_over_ranks([ms, e2e_s], world)
     if rank != 0:
@@ -330,8 +339,8 @@ def run_ours(args):
                  "frac_of_peak": round(adam_bytes / (avg['adam'] / 1e3) / 1e9 / peak, 4)},
         "e2e": {"value": round(w.rays * e2e_steps * world / e2e_s, 1), "unit": "rays/s",
                 "h2d_bytes_per_step": 24, "d2h_bytes_per_step": 40, "steps": e2e_steps,
-                "what": "per step: H2D dloss seed (pinned), the C-ABI calls of the step, D2H loss and counts, host sync; "
-                        "frames resident on the device"},
+                "what": "per step: H2D dloss seed (pinned), the C-ABI calls of the step, D2H loss and counts into a "
+                        "pinned double buffer that the host reads one step later; frames resident on the device"},
         "gpu_launches": ((9 if args.split else 6) + (1 if args.eikonal else 0)) * args.steps,
         "clocks": clk,
         "loss_last": [round(x, 6) for x in lossv],
