@@ -91,6 +91,8 @@ def lib():
             L.oc_eikonal.argtypes = [vp, vp, i32, i32, vp, vp, vp, vp, dbl, vp, vp, vp]
             L.oc_sample_importance.restype = i32
             L.oc_sample_importance.argtypes = [vp, vp, vp, u64, u32, i32, i32, i32, i32] + [vp] * 9
+            L.oc_extract_mesh.restype = i64
+            L.oc_extract_mesh.argtypes = [vp, vp, vp, ctypes.c_float, i32, i32, i32, dbl, vp, i64, vp]
             L.oc_voxel_index.restype = None
             L.oc_voxel_index.argtypes = [vp, vp, i32, vp]
             L.oc_trilinear_coeffs.restype = None
@@ -294,6 +296,20 @@ def eikonal(cfg: OcConfig, theta, batch: dict, dscale: float = 1.0, want_grad=Tr
     if n < 0:
         raise ValueError("oc_eikonal rejected its arguments")
     return float(loss[0]), grad, int(n), gnorm
+
+
+def extract_mesh(cfg: OcConfig, theta, lo, step: float, dims, iso: float = 0.0, max_tris: int | None = None):
+    """Isosurface phi = iso on the lattice lo + (i, j, k) * step, dims = (nx, ny, nz): returns
+    (triangles [T][3][3] FP64, lattice phi [nz][ny][nx])."""
+    th = np.ascontiguousarray(theta, dtype=np.float64)
+    lo = np.ascontiguousarray(lo, dtype=np.float32).reshape(3)
+    nx, ny, nz = (int(d) for d in dims)
+    phi = np.empty((nz, ny, nx))
+    cap = max_tris if max_tris is not None else 12 * (nx - 1) * (ny - 1) * (nz - 1)
+    tris = np.empty((max(cap, 1), 3, 3))
+    n = lib().oc_extract_mesh(ctypes.byref(cfg), _p(th), _p(lo), ctypes.c_float(step), nx, ny, nz,
+                              ctypes.c_double(iso), _p(tris), cap, _p(phi))
+    return tris[:min(n, cap)], phi
 
 
 def voxel_index(cfg: OcConfig, x) -> np.ndarray:

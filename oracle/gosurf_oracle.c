@@ -19,6 +19,7 @@
  *   gradients (hand reverse mode, incl. d/dtheta of grad_x phi) .. Supp. Sec. 1 Eq. (second_order_theta)
  *   l_eik on the free-space samples (separate entry) ............. Sec. 3.3 Eq. (eikonal_loss), Sec. 3.4
  *   hierarchical importance sampler (separate entry) ............. Sec. 3.2 (3 x 12 from N_c = 96), Sec. 4
+ *   mesh extraction from phi on a lattice (separate entry) ....... Sec. 4 (marching cubes at 1 cm; tetrahedra here)
  *   Adam ......................................................... Sec. 4 (Implementation Details)
  *
  * Precision: every quantity that decides an integer (pixel index, sample depths and their
@@ -576,6 +577,115 @@ int64_t oc_eikonal(const oc_config* c, const double* theta, int R, int N, const 
   free(sdf);
   free(g);
   return n_fs;
+}
+
+/* ------------------------------------------------------------------------------------ */
+/* mesh extraction (Sec. 4: the meshes are extracted from phi on a 1 cm lattice)          */
+/* ------------------------------------------------------------------------------------ */
+/* Lattice point (i, j, k) sits at lo + (i, j, k) * step (binary32, two roundings per axis);
+ * phi there in FP64.  Each lattice cell is split into 6 tetrahedra around its diagonal from
+ * corner 0 to corner 7 (corner c at offset (c & 1, (c >> 1) & 1, c >> 2)); a tetrahedron with
+ * 1 or 3 corners below iso yields one triangle, with 2 below two, their vertices on the
+ * tetrahedron's edges where the linear interpolation of phi equals iso.  An edge's point is
+ * interpolated from its endpoint of lower lattice index, so that cells and tetrahedra that
+ * share an edge produce the same point.  Triangles are oriented with their normal towards
+ * the tetrahedron's corners above iso (increasing phi, out of the surface).
+ * tris [max_tris][3][3] receives the first max_tris triangles, cells in x-fastest order;
+ * phi_out [nz][ny][nx] (may be NULL) the lattice values.  Returns the number of triangles. */
+static const int oc_tets[6][4] = {{0, 1, 3, 7}, {0, 3, 2, 7}, {0, 2, 6, 7}, {0, 6, 4, 7}, {0, 4, 5, 7}, {0, 5, 1, 7}};
+
+static void mesh_edge(const double P[8][3], const double f[8], const int64_t id[8], int a, int b, double iso,
+                      double out[3]) {
+  if (id[b] < id[a]) { int t = a; a = b; b = t; }
+  const double w = (iso - f[a]) / (f[b] - f[a]);
+  for (int q = 0; q < 3; ++q) out[q] = P[a][q] + w * (P[b][q] - P[a][q]);
+}
+
+static int64_t mesh_emit(double* tris, int64_t max_tris, int64_t n, const double p0[3], const double p1[3],
+                         const double p2[3], const double dir[3]) {
+  double e1[3], e2[3], nrm[3];
+  for (int q = 0; q < 3; ++q) { e1[q] = p1[q] - p0[q]; e2[q] = p2[q] - p0[q]; }
+  nrm[0] = e1[1] * e2[2] - e1[2] * e2[1];
+  nrm[1] = e1[2] * e2[0] - e1[0] * e2[2];
+  nrm[2] = e1[0] * e2[1] - e1[1] * e2[0];
+  const int flip = nrm[0] * dir[0] + nrm[1] * dir[1] + nrm[2] * dir[2] < 0.0;
+  if (n < max_tris) {
+    double* t = tris + 9 * n;
+    for (int q = 0; q < 3; ++q) {
+      t[q] = p0[q];
+      t[3 + q] = flip ? p2[q] : p1[q];
+      t[6 + q] = flip ? p1[q] : p2[q];
+    }
+  }
+  return n + 1;
+}
+
+int64_t oc_extract_mesh(const oc_config* c, const double* theta, const float lo[3], float step, int nx, int ny, int nz,
+                        double iso, double* tris, int64_t max_tris, double* phi_out) {
+  if (nx < 2 || ny < 2 || nz < 2) return 0;
+  const int64_t np = (int64_t)nx * ny * nz;
+  float* x = (float*)malloc(sizeof(float) * 3 * (size_t)np);
+  double* phi = phi_out ? phi_out : (double*)malloc(sizeof(double) * (size_t)np);
+  for (int k = 0; k < nz; ++k)
+    for (int j = 0; j < ny; ++j)
+      for (int i = 0; i < nx; ++i) {
+        const int64_t id = ((int64_t)k * ny + j) * nx + i;
+        const int ijk[3] = {i, j, k};
+        for (int a = 0; a < 3; ++a) {
+          float d = (float)ijk[a] * step;
+          x[3 * id + a] = lo[a] + d;
+        }
+      }
+  /* phi by the pinned SDF query, in chunks (its P is an int) */
+  for (int64_t s0 = 0; s0 < np; s0 += (1 << 24)) {
+    const int64_t cnt = np - s0 < (1 << 24) ? np - s0 : (1 << 24);
+    oc_query_sdf(c, theta, x + 3 * s0, (int)cnt, phi + s0, NULL);
+  }
+  int64_t n = 0;
+  for (int k = 0; k + 1 < nz; ++k)
+    for (int j = 0; j + 1 < ny; ++j)
+      for (int i = 0; i + 1 < nx; ++i) {
+        double P[8][3], f[8];
+        int64_t id[8];
+        for (int cc = 0; cc < 8; ++cc) {
+          id[cc] = ((int64_t)(k + (cc >> 2)) * ny + (j + ((cc >> 1) & 1))) * nx + (i + (cc & 1));
+          for (int a = 0; a < 3; ++a) P[cc][a] = (double)x[3 * id[cc] + a];
+          f[cc] = phi[id[cc]];
+        }
+        for (int tt = 0; tt < 6; ++tt) {
+          const int* v = oc_tets[tt];
+          int in[4], out[4], ni = 0, no = 0;
+          for (int q = 0; q < 4; ++q) {
+            if (f[v[q]] < iso) in[ni++] = v[q];
+            else out[no++] = v[q];
+          }
+          if (ni == 0 || no == 0) continue;
+          double dir[3] = {0, 0, 0};
+          for (int a = 0; a < 3; ++a) {
+            for (int q = 0; q < no; ++q) dir[a] += P[out[q]][a] / no;
+            for (int q = 0; q < ni; ++q) dir[a] -= P[in[q]][a] / ni;
+          }
+          double p0[3], p1[3], p2[3], p3[3];
+          if (ni == 1 || no == 1) {
+            const int apex = ni == 1 ? in[0] : out[0];
+            const int* rest = ni == 1 ? out : in;
+            mesh_edge(P, f, id, apex, rest[0], iso, p0);
+            mesh_edge(P, f, id, apex, rest[1], iso, p1);
+            mesh_edge(P, f, id, apex, rest[2], iso, p2);
+            n = mesh_emit(tris, max_tris, n, p0, p1, p2, dir);
+          } else { /* two below, two above: the quad in0-out0, in0-out1, in1-out1, in1-out0 */
+            mesh_edge(P, f, id, in[0], out[0], iso, p0);
+            mesh_edge(P, f, id, in[0], out[1], iso, p1);
+            mesh_edge(P, f, id, in[1], out[1], iso, p2);
+            mesh_edge(P, f, id, in[1], out[0], iso, p3);
+            n = mesh_emit(tris, max_tris, n, p0, p1, p2, dir);
+            n = mesh_emit(tris, max_tris, n, p0, p2, p3, dir);
+          }
+        }
+      }
+  free(x);
+  if (!phi_out) free(phi);
+  return n;
 }
 
 /* base vertex (cell) index per level, binary32 decision; out [P][4] flat vertex ids */
