@@ -247,6 +247,22 @@ gs_status gs_query_sdf_backward(gs_ctx* ctx, const float* theta, const float* x,
 gs_status gs_eikonal(gs_ctx* ctx, const float* theta, const gs_batch* batch, const float* dloss, float* loss,
                      float* grad, void* stream);
 
+/* Mesh extraction (Sec. 4: meshes are extracted from phi on a 1 cm lattice by marching
+ * cubes).  phi [nz][ny][nx] (device scratch, written) receives phi at the lattice points
+ * lo + (i, j, k) * step (lo host float[3], binary32 positions, FP32 SDF).  Each lattice cell is
+ * split into 6 tetrahedra around its corner-0-to-corner-7 diagonal (corner c at offset
+ * (c & 1, (c >> 1) & 1, c >> 2)); a tetrahedron with 1 or 3 corners below iso yields one
+ * triangle, with 2 below two, their vertices on its edges where the linear interpolation of
+ * phi equals iso (interpolated from the endpoint of lower lattice index, so shared edges give
+ * identical points: the mesh is closed wherever the surface stays inside the lattice).
+ * Normals (p1 - p0) x (p2 - p0) point towards increasing phi.  tris [max_tris][3][3] (device,
+ * may be NULL with max_tris 0) receives triangles in no fixed order; *n_tris (device int64)
+ * the total number, which may exceed max_tris (then only max_tris are written: call again with
+ * more room).  nx, ny, nz >= 2, step > 0. */
+gs_status gs_extract_mesh(gs_ctx* ctx, const float* theta, const float* lo, float step, int32_t nx, int32_t ny,
+                          int32_t nz, float iso, float* phi, float* tris, int64_t max_tris, int64_t* n_tris,
+                          void* stream);
+
 /* Cell lookup used by every gather: out [P][4] = flat base-vertex index of the cell holding
  * x (clamped to the grid box) at each level, decided in binary32. */
 gs_status gs_voxel_index(gs_ctx* ctx, const float* x, int32_t P, int64_t* out, void* stream);

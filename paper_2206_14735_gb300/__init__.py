@@ -194,6 +194,25 @@ class Context:
         self._check(self.L.gs_eikonal(self.h, _ptr(theta), ctypes.byref(bs), _ptr(dloss), _ptr(loss), _ptr(grad),
                                       _stream()))
 
+    def extract_mesh(self, theta, lo, step: float, dims, iso: float = 0.0, max_tris: int | None = None,
+                     phi=None):
+        """Isosurface phi = iso on the lattice lo + (i, j, k) * step, dims = (nx, ny, nz):
+        returns (triangles [T][3][3] on the device, T); phi [nz][ny][nx] may be given as scratch."""
+        nx, ny, nz = (int(d) for d in dims)
+        if phi is None:
+            phi = torch.empty((nz, ny, nx), device=theta.device, dtype=torch.float32)
+        cap = max_tris if max_tris is not None else 4 * (nx * ny + ny * nz + nx * nz)
+        n = torch.zeros(1, device=theta.device, dtype=torch.int64)
+        lo_h = (ctypes.c_float * 3)(*[float(v) for v in lo])
+        while True:
+            tris = torch.empty((max(cap, 1), 3, 3), device=theta.device, dtype=torch.float32)
+            self._check(self.L.gs_extract_mesh(self.h, _ptr(theta), lo_h, float(step), nx, ny, nz, float(iso),
+                                               _ptr(phi), _ptr(tris), cap, _ptr(n), _stream()))
+            total = int(n.item())
+            if total <= cap:
+                return tris[:total], total
+            cap = total
+
     def voxel_index(self, x, out):
         self._check(self.L.gs_voxel_index(self.h, _ptr(x), x.shape[0], _ptr(out), _stream()))
 

@@ -371,6 +371,23 @@ gs_status gs_eikonal(gs_ctx* ctx, const float* theta, const gs_batch* batch, con
   return GS_OK;
 }
 
+gs_status gs_extract_mesh(gs_ctx* ctx, const float* theta, const float* lo, float step, int32_t nx, int32_t ny,
+                          int32_t nz, float iso, float* phi, float* tris, int64_t max_tris, int64_t* n_tris,
+                          void* stream) {
+  if (!ctx) return fail(nullptr, GS_ERR_INVALID_ARG, "gs_extract_mesh: ctx is NULL");
+  if (!theta || !lo || !phi || !n_tris) return fail(ctx, GS_ERR_INVALID_ARG, "gs_extract_mesh: NULL argument");
+  if (max_tris < 0 || (max_tris > 0 && !tris)) return fail(ctx, GS_ERR_INVALID_ARG, "gs_extract_mesh: bad tris / max_tris");
+  if (nx < 2 || ny < 2 || nz < 2 || !(step > 0.0f)) return fail(ctx, GS_ERR_SHAPE, "gs_extract_mesh: need nx, ny, nz >= 2 and step > 0");
+  if (!aligned16(theta)) return fail(ctx, GS_ERR_ALIGN, "gs_extract_mesh: theta is not 16-byte aligned");
+  if ((reinterpret_cast<uintptr_t>(n_tris) & 7u)) return fail(ctx, GS_ERR_ALIGN, "gs_extract_mesh: n_tris is not 8-byte aligned");
+  cudaStream_t st = (cudaStream_t)stream;
+  ctx->last_stream = st;
+  if (gs_launch_mesh(ctx, theta, lo, step, nx, ny, nz, iso, phi, tris, max_tris,
+                     reinterpret_cast<unsigned long long*>(n_tris), st) != GS_OK)
+    return cuda_fail(ctx, "gs_extract_mesh");
+  return GS_OK;
+}
+
 gs_status gs_voxel_index(gs_ctx* ctx, const float* x, int32_t P, int64_t* out, void* stream) {
   if (!ctx) return fail(nullptr, GS_ERR_INVALID_ARG, "gs_voxel_index: ctx is NULL");
   if (P < 0) return fail(ctx, GS_ERR_SHAPE, "gs_voxel_index: P < 0");

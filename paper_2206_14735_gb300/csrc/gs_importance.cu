@@ -37,35 +37,6 @@ struct ImpArgs {
   int* counts;
 };
 
-// phi(x): trilinear features of the 4 levels, then the SDF decoder's first output
-__device__ __forceinline__ float sdf_at(const GridDesc& g, const float* __restrict__ theta, const float* sm,
-                                        const float x[3]) {
-  float z[kZ];
-#pragma unroll
-  for (int l = 0; l < kLevels; ++l) {
-    const Cell c = locate(g, l, x);
-    float w[8];
-    corner_weights(c.f, w);
-    const float4* lv = reinterpret_cast<const float4*>(theta + g.off[l]);
-    float4 acc = make_float4(0.f, 0.f, 0.f, 0.f);
-#pragma unroll
-    for (int k = 0; k < 8; ++k) f4fma(acc, w[k], __ldg(lv + c.vtx + corner_offset(g, l, k)));
-    z[4 * l] = acc.x;
-    z[4 * l + 1] = acc.y;
-    z[4 * l + 2] = acc.z;
-    z[4 * l + 3] = acc.w;
-  }
-  float phi = sm[sb2];
-#pragma unroll 8
-  for (int j = 0; j < kH1; ++j) {
-    float s = sm[sb1 + j];
-#pragma unroll
-    for (int k = 0; k < kZ; ++k) s = fmaf(sm[sW1 + j * 16 + k], z[k], s);
-    phi = fmaf(sm[sW2 + j], fmaxf(s, 0.f), phi);
-  }
-  return phi;
-}
-
 __global__ void __launch_bounds__(kImpWarps * 32, 1) importance_kernel(ImpArgs a) {
   __shared__ __align__(16) float sm[sb2 + 4];  // W1 | b1 | W2 row 0 | b2[0]
   __shared__ float ts[kImpWarps][2][kImpMax], ps[kImpWarps][2][kImpMax];

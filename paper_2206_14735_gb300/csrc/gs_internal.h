@@ -65,6 +65,9 @@ gs_status gs_launch_prop_backward(const gs_ctx* ctx, const float* theta, const f
                                   float* grad, float* ce, cudaStream_t st);
 gs_status gs_launch_importance(const gs_ctx* ctx, const float* theta, const gs_frames* f, uint64_t seed,
                                uint32_t step, const gs_batch* b, cudaStream_t st);
+gs_status gs_launch_mesh(const gs_ctx* ctx, const float* theta, const float lo[3], float step, int nx, int ny, int nz,
+                         float iso, float* phi, float* tris, long long max_tris, unsigned long long* n_tris,
+                         cudaStream_t st);
 gs_status gs_launch_eikonal(const gs_ctx* ctx, const float* theta, const gs_batch* b, const float* dloss, float* loss,
                             float* grad, cudaStream_t st);
 gs_status gs_launch_query_backward(const gs_ctx* ctx, const float* theta, const float* x, int P, const float* dsdf,
