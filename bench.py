@@ -347,6 +347,8 @@ def run_ours(args):
     }
     if args.diff_report:
         line["differentiation"] = differentiation_report(w, dfr, theta, mirror)
+    if args.mesh_report > 0:
+        line["mesh_report"] = mesh_report(w, ctx, args.mesh_report)
     if args.sampler_report > 0 and w.imp_coarse > 0:
         line["sampler_report"] = sampler_report(w, fr, dfr, args.sampler_report)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
@@ -423,6 +425,35 @@ def sampler_report(w, fr, dfr, steps):
     out["what"] = ("both forms trained from the same initial parameters on the same frames; depth error of the "
                    "rendered depth against the noise-free depth on fresh rays (host wall clock per step)")
     return out
+
+
+def mesh_report(w, ctx, step_m, reps=3):
+    """Mesh extraction of the workload's scene (its exact SDF baked into the finest level) on a
+    lattice of step_m metres over the whole grid box: lattice points, triangles, CUDA-event
+    time of gs_extract_mesh (lattice SDF + isosurface), after one untimed call."""
+    import torch
+
+    import scenegen as sg
+    scene = sg.room_scene() if w.scene == "room" else sg.cube_scene()
+    th = torch.from_numpy(sg.sdf_params(w, scene, seed=31)).cuda()
+    lo = [a + 0.5 * step_m for a in w.extent_min]
+    dims = [int((b - a) / step_m) for a, b in zip(w.extent_min, w.extent_max)]
+    phi = torch.empty((dims[2], dims[1], dims[0]), device="cuda")
+    _, n = ctx.extract_mesh(th, lo, step_m, dims, phi=phi)
+    times = []
+    for _ in range(reps):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        _, n = ctx.extract_mesh(th, lo, step_m, dims, max_tris=n, phi=phi)
+        e1.record()
+        torch.cuda.synchronize()
+        times.append(e0.elapsed_time(e1))
+    ms = sorted(times)[len(times) // 2]
+    pts = dims[0] * dims[1] * dims[2]
+    return {"step_m": step_m, "lattice": dims, "points": pts, "triangles": n, "ms": round(ms, 3),
+            "points_per_s": round(pts / (ms / 1e3), 1),
+            "what": "gs_extract_mesh on the scene's SDF baked into the finest level; the count comes back to the host "
+                    "inside the timed call"}
 
 
 def proposal_report(w, fr, dfr, steps):
@@ -712,6 +743,8 @@ def main():
     ap.add_argument("--lr-prop", type=float, default=None, help="proposal workloads: override the proposal's lr")
     ap.add_argument("--prop-report", type=int, default=0,
                     help="proposal workloads: train plain and proposal forms this many steps and compare depth")
+    ap.add_argument("--mesh-report", type=float, default=0.0,
+                    help="also time mesh extraction of the scene at this lattice step (metres; the paper uses 0.01)")
     ap.add_argument("--sampler-report", type=int, default=0,
                     help="importance workloads: train the plain and the importance form this many steps and compare "
                          "depth")
