@@ -93,6 +93,14 @@ def lib():
             L.oc_sample_importance.argtypes = [vp, vp, vp, u64, u32, i32, i32, i32, i32] + [vp] * 9
             L.oc_extract_mesh.restype = i64
             L.oc_extract_mesh.argtypes = [vp, vp, vp, ctypes.c_float, i32, i32, i32, dbl, vp, i64, vp]
+            L.oc_step_dz.restype = i32
+            L.oc_step_dz.argtypes = [vp, vp, i32, i32] + [vp] * 6 + [i32] + [vp] * 7
+            L.oc_pose_apply.restype = None
+            L.oc_pose_apply.argtypes = [vp, vp, i32, vp]
+            L.oc_rays_of_pixels.restype = None
+            L.oc_rays_of_pixels.argtypes = [vp, vp, i32, vp, vp]
+            L.oc_pose_grad.restype = None
+            L.oc_pose_grad.argtypes = [vp, vp, vp, vp, vp, i32, i32] + [vp] * 6
             L.oc_voxel_index.restype = None
             L.oc_voxel_index.argtypes = [vp, vp, i32, vp]
             L.oc_trilinear_coeffs.restype = None
@@ -124,10 +132,10 @@ def make_config(w) -> OcConfig:
 class OcFramesHolder:
     """Keeps the numpy arrays alive next to the ctypes struct that points at them."""
 
-    def __init__(self, frames):
+    def __init__(self, frames, c2w=None):
         self.rgb = np.ascontiguousarray(frames.rgb, dtype=np.uint8)
         self.depth = np.ascontiguousarray(frames.depth, dtype=np.float32)
-        self.c2w = np.ascontiguousarray(frames.c2w, dtype=np.float32)
+        self.c2w = np.ascontiguousarray(frames.c2w if c2w is None else c2w, dtype=np.float32)
         F, H, W = self.depth.shape
         self.s = OcFrames(F, H, W, self.rgb.ctypes.data, self.depth.ctypes.data, self.c2w.ctypes.data,
                           frames.fx, frames.fy, frames.cx, frames.cy)
@@ -186,6 +194,54 @@ def sample_smooth(cfg: OcConfig, frames: OcFramesHolder, seed: int, step: int, P
     lib().oc_sample_smooth(ctypes.byref(cfg), ctypes.byref(frames.s), seed, step, P,
                            *[_p(out[k]) for k in ("xs", "eps", "valid", "n_valid")])
     return out
+
+
+def step_dz(cfg: OcConfig, theta, batch: dict, smooth: dict | None, dloss=None):
+    """Losses, gradient and dL/dz of every main sample [R][N][16] of one step."""
+    th = np.ascontiguousarray(theta, dtype=np.float64)
+    R, N = batch["t"].shape
+    if smooth is None:
+        P, xs, eps, valid = 0, np.zeros((1, 3), np.float32), np.zeros((1, 3), np.float32), np.zeros(1, np.uint8)
+    else:
+        P, xs, eps, valid = len(smooth["valid"]), smooth["xs"], smooth["eps"], smooth["valid"]
+    loss, grad, dz = np.zeros(6), np.zeros_like(th), np.zeros((R, N, 16))
+    dl = None if dloss is None else np.ascontiguousarray(dloss, dtype=np.float64)
+    rc = lib().oc_step_dz(ctypes.byref(cfg), _p(th), R, N, _p(batch["o"]), _p(batch["r"]), _p(batch["rgb"]),
+                          _p(batch["D"]), _p(batch["t"]), _p(batch["cls"]), P, _p(xs), _p(eps), _p(valid), _p(dl),
+                          _p(loss), _p(grad), _p(dz))
+    if rc != 0:
+        raise ValueError("oc_step_dz rejected its arguments")
+    return dict(loss=loss, grad=grad, dz=dz)
+
+
+def pose_apply(c2w0, xi) -> np.ndarray:
+    """Refined camera-to-world [F][3][4] (FP64): R0 Exp(nu), t0 + dt for xi [F][6] = (dt, nu)."""
+    c2w0 = np.ascontiguousarray(c2w0, dtype=np.float32).reshape(-1, 3, 4)
+    xi = np.ascontiguousarray(xi, dtype=np.float64).reshape(len(c2w0), 6)
+    out = np.empty((len(c2w0), 3, 4))
+    lib().oc_pose_apply(_p(c2w0), _p(xi), len(c2w0), _p(out))
+    return out
+
+
+def rays_of_pixels(frames: OcFramesHolder, pix):
+    pix = np.ascontiguousarray(pix, dtype=np.int64)
+    o, r = np.empty((len(pix), 3), np.float32), np.empty((len(pix), 3), np.float32)
+    lib().oc_rays_of_pixels(ctypes.byref(frames.s), _p(pix), len(pix), _p(o), _p(r))
+    return o, r
+
+
+def pose_grad(cfg: OcConfig, frames: OcFramesHolder, theta, c2w, xi, batch: dict, dz) -> np.ndarray:
+    """dL/dxi [F][6] of the rays of batch (pix, o, r, t) from the step's dL/dz [R][N][16]."""
+    th = np.ascontiguousarray(theta, dtype=np.float64)
+    c2w = np.ascontiguousarray(c2w, dtype=np.float64)
+    xi = np.ascontiguousarray(xi, dtype=np.float64)
+    F = len(c2w)
+    R, N = batch["t"].shape
+    g = np.zeros((F, 6))
+    lib().oc_pose_grad(ctypes.byref(cfg), ctypes.byref(frames.s), _p(th), _p(c2w), _p(xi), R, N,
+                       _p(np.ascontiguousarray(batch["pix"], dtype=np.int64)), _p(batch["o"]), _p(batch["r"]),
+                       _p(batch["t"]), _p(np.ascontiguousarray(dz, dtype=np.float64)), _p(g))
+    return g
 
 
 def step(cfg: OcConfig, theta, batch: dict, smooth: dict | None, dloss=None, want_grad=True, want_margins=False,

@@ -20,6 +20,7 @@
  *   l_eik on the free-space samples (separate entry) ............. Sec. 3.3 Eq. (eikonal_loss), Sec. 3.4
  *   hierarchical importance sampler (separate entry) ............. Sec. 3.2 (3 x 12 from N_c = 96), Sec. 4
  *   mesh extraction from phi on a lattice (separate entry) ....... Sec. 4 (marching cubes at 1 cm; tetrahedra here)
+ *   camera-pose refinement gradient (separate entry) ............. Sec. 3.4, Sec. 4 (t, so(3))
  *   Adam ......................................................... Sec. 4 (Implementation Details)
  *
  * Precision: every quantity that decides an integer (pixel index, sample depths and their
@@ -826,10 +827,11 @@ static void mmin(double* a, double v) {
  * than 1e-7.  w_out [R,N] (may be NULL) receives the rendering weights w_i = T_i alpha_i.
  * Returns 0, or -1 on a bad argument.
  */
-int oc_step(const oc_config* c, const double* theta, int R, int N, const float* o, const float* r,
-            const float* rgb, const float* D, const float* t, const uint8_t* cls, int P, const float* xs,
-            const float* eps, const uint8_t* valid, const double* dloss, double* loss, double* rgb_hat,
-            double* d_hat, double* wsum, double* grad, double* margins, uint8_t* amb, double* w_out) {
+static int step_impl(const oc_config* c, const double* theta, int R, int N, const float* o, const float* r,
+                     const float* rgb, const float* D, const float* t, const uint8_t* cls, int P, const float* xs,
+                     const float* eps, const uint8_t* valid, const double* dloss, double* loss, double* rgb_hat,
+                     double* d_hat, double* wsum, double* grad, double* margins, uint8_t* amb, double* w_out,
+                     double* dz_out) {
   if (R < 0 || N < 2 || P < 0) return -1;
   const int64_t ng = grid_size(c);
   mlp_t m = mlp_view(theta + ng);
@@ -1158,6 +1160,7 @@ int oc_step(const oc_config* c, const double* theta, int R, int N, const float* 
         }
       }
   }
+  if (dz_out && do_grad) memcpy(dz_out, dz_all, sizeof(double) * (size_t)R * N * OC_Z);
   free(gm_all);
   free(lsum_all);
   free(mg_all);
@@ -1299,6 +1302,131 @@ int oc_sample_importance(const oc_config* c, const oc_frames* fr, const double* 
   counts[2] = nfs;
   counts[3] = 0;
   return 0;
+}
+
+int oc_step(const oc_config* c, const double* theta, int R, int N, const float* o, const float* r,
+            const float* rgb, const float* D, const float* t, const uint8_t* cls, int P, const float* xs,
+            const float* eps, const uint8_t* valid, const double* dloss, double* loss, double* rgb_hat,
+            double* d_hat, double* wsum, double* grad, double* margins, uint8_t* amb, double* w_out) {
+  return step_impl(c, theta, R, N, o, r, rgb, D, t, cls, P, xs, eps, valid, dloss, loss, rgb_hat, d_hat, wsum, grad,
+                   margins, amb, w_out, NULL);
+}
+/* oc_step that also returns dL/dz of every main sample, dz_out [R][N][16] (needs grad) */
+int oc_step_dz(const oc_config* c, const double* theta, int R, int N, const float* o, const float* r,
+               const float* rgb, const float* D, const float* t, const uint8_t* cls, int P, const float* xs,
+               const float* eps, const uint8_t* valid, const double* dloss, double* loss, double* grad,
+               double* dz_out) {
+  return step_impl(c, theta, R, N, o, r, rgb, D, t, cls, P, xs, eps, valid, dloss, loss, NULL, NULL, NULL, grad,
+                   NULL, NULL, NULL, dz_out);
+}
+
+/* ------------------------------------------------------------------------------------ */
+/* camera-pose refinement (Sec. 3.4: P includes the poses; Sec. 4: t in R^3, nu in so(3),  */
+/* learning rate 5e-4)                                                                    */
+/* ------------------------------------------------------------------------------------ */
+/* Frame f's pose is the given camera-to-world [R0 | t0] corrected by xi_f = (dt, nu):
+ *   R = R0 Exp(nu),  t = t0 + dt,  Exp by Rodrigues' formula.
+ * A ray of pixel (u, v) has o = t and r = R d, d = ((u + 0.5 - cx)/fx, (v + 0.5 - cy)/fy, 1);
+ * its samples x_s = o + d_s r move with the pose while their depths d_s and classes do not.
+ * With g_s = dL/dx_s = sum_l (d z_l / d x)^T dL/dz_l (the step's own dL/dz):
+ *   dL/d dt = sum over the frame's rays and samples of g_s,
+ *   dL/d nu = J_r(nu)^T [d]_x R^T sum_s d_s g_s      (d(Exp(nu) d)/d nu = -Exp(nu) [d]_x J_r(nu)),
+ * J_r(nu) = I - (1 - cos a)/a^2 [nu]_x + (a - sin a)/a^3 [nu]_x^2, a = |nu| (series near 0). */
+static void skew(const double v[3], double K[3][3]) {
+  K[0][0] = 0; K[0][1] = -v[2]; K[0][2] = v[1];
+  K[1][0] = v[2]; K[1][1] = 0; K[1][2] = -v[0];
+  K[2][0] = -v[1]; K[2][1] = v[0]; K[2][2] = 0;
+}
+static void so3_exp_jr(const double nu[3], double E[3][3], double J[3][3]) {
+  const double a2 = nu[0] * nu[0] + nu[1] * nu[1] + nu[2] * nu[2], a = sqrt(a2);
+  double K[3][3], K2[3][3];
+  skew(nu, K);
+  for (int i = 0; i < 3; ++i)
+    for (int j = 0; j < 3; ++j) {
+      K2[i][j] = 0;
+      for (int k = 0; k < 3; ++k) K2[i][j] += K[i][k] * K[k][j];
+    }
+  double s1, s2, j1, j2; /* E = I + s1 K + s2 K^2,  J = I - j1 K + j2 K^2 */
+  if (a < 1e-4) {
+    s1 = 1.0 - a2 / 6.0; s2 = 0.5 - a2 / 24.0; j1 = 0.5 - a2 / 24.0; j2 = 1.0 / 6.0 - a2 / 120.0;
+  } else {
+    s1 = sin(a) / a; s2 = (1.0 - cos(a)) / a2; j1 = (1.0 - cos(a)) / a2; j2 = (a - sin(a)) / (a2 * a);
+  }
+  for (int i = 0; i < 3; ++i)
+    for (int j = 0; j < 3; ++j) {
+      const double I = i == j ? 1.0 : 0.0;
+      E[i][j] = I + s1 * K[i][j] + s2 * K2[i][j];
+      J[i][j] = I - j1 * K[i][j] + j2 * K2[i][j];
+    }
+}
+
+/* refined camera-to-world matrices c2w [F][3][4] (FP64) from the given ones and xi [F][6] */
+void oc_pose_apply(const float* c2w0, const double* xi, int F, double* c2w) {
+  for (int f = 0; f < F; ++f) {
+    double E[3][3], J[3][3];
+    so3_exp_jr(xi + 6 * f + 3, E, J);
+    const float* P = c2w0 + 12 * f;
+    double* Q = c2w + 12 * f;
+    for (int i = 0; i < 3; ++i) {
+      for (int j = 0; j < 3; ++j) {
+        double sacc = 0;
+        for (int k = 0; k < 3; ++k) sacc += (double)P[4 * i + k] * E[k][j];
+        Q[4 * i + j] = sacc;
+      }
+      Q[4 * i + 3] = (double)P[4 * i + 3] + xi[6 * f + i];
+    }
+  }
+}
+
+/* o, r (binary32, as the sampler forms them) of the rays of pixels pix [R] */
+void oc_rays_of_pixels(const oc_frames* fr, const int64_t* pix, int R, float* o, float* r) {
+  for (int i = 0; i < R; ++i) {
+    float rgb[3], D;
+    pixel_ray(fr, pix[i], o + 3 * i, r + 3 * i, rgb, &D);
+  }
+}
+
+/* dL/dxi [F][6] += the pose gradient of the rays pix [R] with sample depths t [R][N] and the
+ * step's dL/dz [R][N][16], for frames whose refined poses are c2w [F][3][4] (FP64) with
+ * corrections xi [F][6]; o, r [R][3] the rays the step used. */
+void oc_pose_grad(const oc_config* c, const oc_frames* fr, const double* theta, const double* c2w, const double* xi,
+                  int R, int N, const int64_t* pix, const float* o, const float* r, const float* t, const double* dz,
+                  double* g) {
+  const int64_t hw = (int64_t)fr->H * fr->W;
+  for (int i = 0; i < R; ++i) {
+    const int64_t f = pix[i] / hw, rem = pix[i] % hw;
+    const int v = (int)(rem / fr->W), u = (int)(rem % fr->W);
+    const double d[3] = {(((double)u + 0.5) - fr->cx) / fr->fx, (((double)v + 0.5) - fr->cy) / fr->fy, 1.0};
+    double go[3] = {0, 0, 0}, gr[3] = {0, 0, 0};
+    for (int k = 0; k < N; ++k) {
+      const float* ti = t + (size_t)i * N;
+      float x[3];
+      for (int a = 0; a < 3; ++a) {
+        float st = ti[k] * r[3 * i + a];
+        x[a] = o[3 * i + a] + st;
+      }
+      cell_t cells[OC_LEVELS];
+      double z[OC_Z], dzdx[OC_Z][3];
+      features(c, theta, x, cells, z, dzdx);
+      const double* dzk = dz + ((size_t)i * N + k) * OC_Z;
+      for (int a = 0; a < 3; ++a) {
+        double gx = 0;
+        for (int q = 0; q < OC_Z; ++q) gx += dzdx[q][a] * dzk[q];
+        go[a] += gx;
+        gr[a] += (double)ti[k] * gx;
+      }
+    }
+    /* translation */
+    for (int a = 0; a < 3; ++a) g[6 * f + a] += go[a];
+    /* rotation: J_r^T [d]_x R^T gr */
+    double E[3][3], J[3][3], Rt_gr[3], K[3][3], w[3];
+    so3_exp_jr(xi + 6 * f + 3, E, J);
+    const double* Q = c2w + 12 * f;
+    for (int a = 0; a < 3; ++a) Rt_gr[a] = Q[a] * gr[0] + Q[4 + a] * gr[1] + Q[8 + a] * gr[2];
+    skew(d, K);
+    for (int a = 0; a < 3; ++a) w[a] = K[a][0] * Rt_gr[0] + K[a][1] * Rt_gr[1] + K[a][2] * Rt_gr[2];
+    for (int a = 0; a < 3; ++a) g[6 * f + 3 + a] += J[0][a] * w[0] + J[1][a] * w[1] + J[2][a] * w[2];
+  }
 }
 
 /* ------------------------------------------------------------------------------------ */
