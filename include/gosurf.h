@@ -122,6 +122,9 @@ typedef struct gs_batch {
   int32_t* counts; /* [4] rays with D > 0, |S_tr|, |S_fs|, valid smoothness points */
   float* w;        /* [R][N] rendering weights w_i = T_i alpha_i, written by the forward passes
                       when not NULL; read by gs_proposal_backward */
+  float* dz;       /* [R][N][16] dL/dz of every sample (the upstream gradient of its geometry
+                      feature), written by the backward passes when not NULL; read by
+                      gs_pose_backward */
 } gs_batch;
 
 typedef struct gs_ctx gs_ctx;
@@ -262,6 +265,24 @@ gs_status gs_eikonal(gs_ctx* ctx, const float* theta, const gs_batch* batch, con
 gs_status gs_extract_mesh(gs_ctx* ctx, const float* theta, const float* lo, float step, int32_t nx, int32_t ny,
                           int32_t nz, float iso, float* phi, float* tris, int64_t max_tris, int64_t* n_tris,
                           void* stream);
+
+/* Camera-pose refinement (Sec. 3.4: the optimised parameters include the poses; Sec. 4: a
+ * translation t in R^3 and nu in so(3) per frame).  Frame f's pose is its given
+ * camera-to-world [R0 | t0] corrected by xi [F][6] = (dt, nu) (device floats):
+ *   R = R0 Exp(nu) (Rodrigues' formula), t = t0 + dt.
+ * gs_pose_apply writes the corrected c2w [F][3][4] (device) from c2w0 [F][3][4]; sample with
+ * frames whose c2w points there.  The samples x = o + d r of a ray move with its frame's pose
+ * (o = t, r = R d, d the pixel's direction with unit camera z); their depths and classes do
+ * not.  gs_pose_backward adds to pose_grad [F][6] (device) the gradient of the per-ray losses
+ * (rgb, depth, truncated SDF, free space) through the sample positions:
+ *   dL/d dt = sum_s g_s,  dL/d nu = J_r(nu)^T [d]_x R^T sum_s d_s g_s,  g_s = sum_l (dz_l/dx)^T dL/dz_l,
+ * over each frame's rays, with J_r the right Jacobian of Exp; dL/dz is batch->dz, which the
+ * preceding gs_backward / gs_forward_backward of this batch wrote (batch->dz must be set
+ * there and here).  frames: the corrected poses the batch was sampled with.  The smoothness
+ * points are not differentiated with respect to the poses.  Accumulates with atomics. */
+gs_status gs_pose_apply(gs_ctx* ctx, const float* c2w0, const float* xi, int32_t F, float* c2w, void* stream);
+gs_status gs_pose_backward(gs_ctx* ctx, const float* theta, const gs_frames* frames, const float* xi,
+                           const gs_batch* batch, float* pose_grad, void* stream);
 
 /* Cell lookup used by every gather: out [P][4] = flat base-vertex index of the cell holding
  * x (clamped to the grid box) at each level, decided in binary32. */

@@ -62,7 +62,17 @@ class DeviceFrames:
         self.depth = torch.as_tensor(depth).to(device=device, dtype=torch.float32).contiguous()
         self.c2w = torch.as_tensor(c2w).to(device=device, dtype=torch.float32).contiguous()
         F, H, W = self.depth.shape
+        self.intr = (fx, fy, cx, cy)
         self.s = GsFrames(F, H, W, self.rgb.data_ptr(), self.depth.data_ptr(), self.c2w.data_ptr(), fx, fy, cx, cy)
+
+    def with_poses(self, c2w) -> "DeviceFrames":
+        """The same images with other camera-to-world matrices c2w [F][3][4] (a device tensor that
+        the caller keeps alive, e.g. the output of Context.pose_apply)."""
+        out = DeviceFrames.__new__(DeviceFrames)
+        out.rgb, out.depth, out.c2w, out.intr = self.rgb, self.depth, c2w, self.intr
+        F, H, W = self.depth.shape
+        out.s = GsFrames(F, H, W, self.rgb.data_ptr(), self.depth.data_ptr(), c2w.data_ptr(), *self.intr)
+        return out
 
 
 @dataclass
@@ -83,9 +93,10 @@ class Batch:
     valid: torch.Tensor
     counts: torch.Tensor
     w: torch.Tensor | None = None  # [R][N] rendering weights (written by forward passes when present)
+    dz: torch.Tensor | None = None  # [R][N][16] dL/dz (written by backward passes when present)
 
     @staticmethod
-    def allocate(R: int, N: int, P: int, device="cuda", weights=False) -> "Batch":
+    def allocate(R: int, N: int, P: int, device="cuda", weights=False, dz=False) -> "Batch":
         f = dict(device=device, dtype=torch.float32)
         return Batch(R=R, N=N, P=P, pix=torch.empty(R, device=device, dtype=torch.int64),
                      origin=torch.empty(R, 3, **f), dir=torch.empty(R, 3, **f), rgb=torch.empty(R, 3, **f),
@@ -93,13 +104,14 @@ class Batch:
                      cls=torch.empty(R, N, device=device, dtype=torch.uint8), xs=torch.empty(max(P, 1), 3, **f),
                      eps=torch.empty(max(P, 1), 3, **f), valid=torch.empty(max(P, 1), device=device, dtype=torch.uint8),
                      counts=torch.zeros(4, device=device, dtype=torch.int32),
-                     w=torch.zeros(R, N, **f) if weights else None)
+                     w=torch.zeros(R, N, **f) if weights else None,
+                     dz=torch.zeros(R, N, 16, **f) if dz else None)
 
     def struct(self) -> GsBatch:
         return GsBatch(self.R, self.N, self.P, self.pix.data_ptr(), self.origin.data_ptr(), self.dir.data_ptr(),
                        self.rgb.data_ptr(), self.depth.data_ptr(), self.t.data_ptr(), self.cls.data_ptr(),
                        self.xs.data_ptr(), self.eps.data_ptr(), self.valid.data_ptr(), self.counts.data_ptr(),
-                       None if self.w is None else self.w.data_ptr())
+                       None if self.w is None else self.w.data_ptr(), None if self.dz is None else self.dz.data_ptr())
 
 
 class Context:
@@ -193,6 +205,16 @@ class Context:
         bs = batch.struct()
         self._check(self.L.gs_eikonal(self.h, _ptr(theta), ctypes.byref(bs), _ptr(dloss), _ptr(loss), _ptr(grad),
                                       _stream()))
+
+    def pose_apply(self, c2w0, xi, c2w):
+        """c2w [F][3][4] = the corrected poses [R0 Exp(nu) | t0 + dt] for xi [F][6] = (dt, nu)."""
+        self._check(self.L.gs_pose_apply(self.h, _ptr(c2w0), _ptr(xi), c2w0.shape[0], _ptr(c2w), _stream()))
+
+    def pose_backward(self, theta, frames: DeviceFrames, xi, batch: Batch, pose_grad):
+        """pose_grad [F][6] += dL/dxi of the batch's per-ray losses (batch.dz from its backward pass)."""
+        b = batch.struct()
+        self._check(self.L.gs_pose_backward(self.h, _ptr(theta), ctypes.byref(frames.s), _ptr(xi), ctypes.byref(b),
+                                            _ptr(pose_grad), _stream()))
 
     def extract_mesh(self, theta, lo, step: float, dims, iso: float = 0.0, max_tris: int | None = None,
                      phi=None):

@@ -371,6 +371,34 @@ gs_status gs_eikonal(gs_ctx* ctx, const float* theta, const gs_batch* batch, con
   return GS_OK;
 }
 
+gs_status gs_pose_apply(gs_ctx* ctx, const float* c2w0, const float* xi, int32_t F, float* c2w, void* stream) {
+  if (!ctx) return fail(nullptr, GS_ERR_INVALID_ARG, "gs_pose_apply: ctx is NULL");
+  if (F < 0) return fail(ctx, GS_ERR_SHAPE, "gs_pose_apply: F < 0");
+  if (F > 0 && (!c2w0 || !xi || !c2w)) return fail(ctx, GS_ERR_INVALID_ARG, "gs_pose_apply: NULL array");
+  cudaStream_t st = (cudaStream_t)stream;
+  ctx->last_stream = st;
+  if (gs_launch_pose_apply(c2w0, xi, F, c2w, st) != GS_OK) return cuda_fail(ctx, "gs_pose_apply");
+  return GS_OK;
+}
+
+gs_status gs_pose_backward(gs_ctx* ctx, const float* theta, const gs_frames* frames, const float* xi,
+                           const gs_batch* batch, float* pose_grad, void* stream) {
+  if (!ctx) return fail(nullptr, GS_ERR_INVALID_ARG, "gs_pose_backward: ctx is NULL");
+  gs_status s = check_frames(ctx, frames, "gs_pose_backward");
+  if (s != GS_OK) return s;
+  s = check_batch(ctx, batch, true);
+  if (s != GS_OK) return s;
+  if (!theta || !xi || !pose_grad) return fail(ctx, GS_ERR_INVALID_ARG, "gs_pose_backward: NULL array");
+  if (batch->R > 0 && !batch->dz) return fail(ctx, GS_ERR_INVALID_ARG, "gs_pose_backward: batch dz is NULL");
+  if (!aligned16(theta) || (batch->dz && !aligned16(batch->dz)))
+    return fail(ctx, GS_ERR_ALIGN, "gs_pose_backward: theta or batch dz is not 16-byte aligned");
+  cudaStream_t st = (cudaStream_t)stream;
+  ctx->last_stream = st;
+  if (gs_launch_pose_backward(ctx, theta, frames, xi, batch, pose_grad, st) != GS_OK)
+    return cuda_fail(ctx, "gs_pose_backward");
+  return GS_OK;
+}
+
 gs_status gs_extract_mesh(gs_ctx* ctx, const float* theta, const float* lo, float step, int32_t nx, int32_t ny,
                           int32_t nz, float iso, float* phi, float* tris, int64_t max_tris, int64_t* n_tris,
                           void* stream) {

@@ -221,6 +221,7 @@ gs_status gs_launch_render(const gs_ctx* ctx, const float* theta, const uint16_t
       if (!encode_level_map(ctx, theta, 2 + q, &a.tmap[q])) return GS_ERR_CUDA;
   a.store = ctx->store;
   a.w_out = b->w;
+  a.dz_out = b->dz;
   a.store_stride = (long long)ctx->cfg.max_rays * ctx->max_n;
   const int nch = (b->N + 31) / 32;
   if (ctx->cfg.precision == GS_PREC_BF16) {

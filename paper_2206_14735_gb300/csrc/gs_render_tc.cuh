@@ -482,6 +482,7 @@ struct RenderTcArgs {
   float* store;
   long long store_stride;
   float* w_out;  // [R][N] rendering weights, written by forward passes when not nullptr
+  float* dz_out; // [R][N][16] dL/dz of every sample, written by backward passes when not nullptr
   // FP32 form: 2D views [nz * ny][nx * 4] of grid levels 2 and 3 for the TMA gathers (a box of
   // 2 vertices x 4 features; one tile::gather4 brings a cell's 8 corners)
   CUtensorMap tmap[2];
@@ -1024,6 +1025,11 @@ __global__ void __launch_bounds__(GR * kGroupThreads, 1) render_tc_kernel(const 
       dw_acc = true;
       tc::tmem_ld16(lane_addr(G, cYb, warp_g), u);
       tc::tmem_ld_wait();
+      if (a.dz_out != nullptr && valid) {  // dL/dz of this sample (camera-pose gradients)
+        float4* dzo = reinterpret_cast<float4*>(a.dz_out + ((size_t)rr * N + si) * kZ);
+#pragma unroll
+        for (int q = 0; q < 4; ++q) dzo[q] = make_float4(u[4 * q], u[4 * q + 1], u[4 * q + 2], u[4 * q + 3]);
+      }
       dw_wait(G);  // the tiles' space holds the scatter's staging rows
       scatter_dz(a.g, a.grad, x, u, valid, reinterpret_cast<float*>(G.a) + warp_g * (33 * 36));
       group_sync(G.g);  // every warp is done with its rows before the tiles are rewritten

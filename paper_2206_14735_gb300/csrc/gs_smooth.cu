@@ -52,26 +52,6 @@ __device__ __forceinline__ void features_only(const GridDesc& g, const float* __
     z[4 * l + 3] = acc.w;
   }
 }
-// d z_l / d x (4 features x 3 axes) at level l, and the cell (for the scatter)
-__device__ __forceinline__ Cell level_jacobian(const GridDesc& g, const float* __restrict__ theta, int l,
-                                               const float y[3], float4 (&dl)[3], float (&dw)[8][3]) {
-  const Cell c = locate(g, l, y);
-  corner_weight_grads(c.f, c.clamped, dw);
-  const float4* base = reinterpret_cast<const float4*>(theta + g.off[l]);
-  dl[0] = dl[1] = dl[2] = make_float4(0.f, 0.f, 0.f, 0.f);
-#pragma unroll
-  for (int k = 0; k < 8; ++k) {
-    const float4 v = __ldg(base + c.vtx + corner_offset(g, l, k));
-    f4fma(dl[0], dw[k][0], v);
-    f4fma(dl[1], dw[k][1], v);
-    f4fma(dl[2], dw[k][2], v);
-  }
-  const float iv = g.inv_voxel[l];
-#pragma unroll
-  for (int a = 0; a < 3; ++a) dl[a] = f4scale(dl[a], iv);
-  return c;
-}
-
 // ReLU mask m (bit j = unit j on), m (.) W2[0,:], and p = d phi / d z
 __device__ __forceinline__ unsigned phi_sensitivity(const float* sm, const float z[kZ], float mw2[kH1], float p[kZ]) {
   unsigned mask = 0;
