@@ -146,24 +146,40 @@ def run_ours(args):
     n_grid_ = w.layout()[1]
     # BF16 form: the grid copy the gathers read, refreshed by every Adam step
     mirror = theta[:n_grid_].to(torch.bfloat16).view(torch.int16).contiguous() if ctx.bf16 else None
-    batch = gs.Batch.allocate(w.rays, w.n_samples, w.n_smooth)
+    batch = gs.Batch.allocate(w.rays, w.n_samples, w.n_smooth, dz=args.poses)
     loss = torch.empty(6, device="cuda")
     eik = torch.zeros(1, device="cuda")  # L_eik when --eikonal (Sec. 3.3, lam_eik = 1)
     stream = torch.cuda.current_stream()
     seed = replica_seed(rank)
     b1, b2 = w.betas
 
+    # camera-pose refinement (--poses): per-frame corrections xi = (dt, nu), the corrected
+    # poses applied before sampling, their gradient after the render call, Adam at 5e-4
+    if args.poses:
+        n_fr = dfr.c2w.shape[0]
+        xi = torch.zeros((6 * n_fr + 3) // 4 * 4, device="cuda")
+        xi_m, xi_v, xi_g = torch.zeros_like(xi), torch.zeros_like(xi), torch.zeros_like(xi)
+        c2w_cur = torch.empty_like(dfr.c2w)
+        dfr_pose = dfr.with_poses(c2w_cur)
+
+    def frames_now():
+        if not args.poses:
+            return dfr
+        ctx.pose_apply(dfr.c2w, xi[:6 * n_fr].view(n_fr, 6), c2w_cur)
+        return dfr_pose
+
     def sample(k, b=batch):
+        fr_k = frames_now()
         if w.imp_coarse > 0:  # the paper's hierarchical importance sampler (reads theta)
-            ctx.sample_importance(dfr, theta, seed, k, b)
+            ctx.sample_importance(fr_k, theta, seed, k, b)
         else:
-            ctx.sample_rays(dfr, seed, k, b)
+            ctx.sample_rays(fr_k, seed, k, b)
 
     # The plain sampler does not read theta: the batch of step k + 1 is sampled on a side
     # stream (its own context, a second batch buffer) while step k renders and updates, and
     # lands on the SMs that the render kernel's last round leaves idle.  The importance
     # sampler reads theta, so it stays in line.
-    pipelined = w.imp_coarse == 0 and not args.no_pipeline
+    pipelined = w.imp_coarse == 0 and not args.no_pipeline and not args.poses
     if pipelined:
         ctx_s = gs.Context(w)
         side = torch.cuda.Stream()
@@ -207,6 +223,9 @@ def run_ours(args):
             ev[2].record(stream)
         if args.eikonal:
             ctx.eikonal(theta, b, loss=eik, grad=grad)
+        if args.poses:
+            ctx.pose_backward(theta, dfr_pose, xi[:6 * n_fr].view(n_fr, 6), b, xi_g[:6 * n_fr].view(n_fr, 6))
+            ctx.adam_step(xi, xi_g, xi_m, xi_v, k + 1, 0.0, 5e-4, n_grid=0)
         if ev is not None:
             ev[3].record(stream)
         if io is not None:  # before the batch is handed back to the sampler
@@ -243,8 +262,9 @@ def run_ours(args):
     clk = clocks.stop()
     ms = start.elapsed_time(stop)
     per = {"sample": [], "render": [], "adam": []}
-    if args.eikonal:
-        per["eikonal"] = []
+    extra = "eikonal" if args.eikonal else ("poses" if args.poses else None)
+    if extra:
+        per[extra] = []
     for k, e in enumerate(evs):
         if pipelined:  # the sampler's own time on the side stream (overlapped with the step before)
             se = sample_ev[args.warmup + k]
@@ -252,8 +272,8 @@ def run_ours(args):
         else:
             per["sample"].append(e[0].elapsed_time(e[1]))
         per["render"].append(e[1].elapsed_time(e[2]))
-        if args.eikonal:
-            per["eikonal"].append(e[2].elapsed_time(e[3]))
+        if extra:
+            per[extra].append(e[2].elapsed_time(e[3]))
         per["adam"].append(e[3].elapsed_time(e[4]))
     avg = {k: sum(vv) / len(vv) for k, vv in per.items()}
     ctx.sync_status()
@@ -305,7 +325,7 @@ def run_ours(args):
     peak = peaks["hbm_gbs"]
     traffic = args.traffic_render if dom == "render" else args.traffic_adam
     default_step = (w.name == WORKLOAD and not args.recompute and not args.split and not args.eikonal and
-                    args.frames in (None, 50))
+                    not args.poses and args.frames in (None, 50))
     if traffic is None and dom == "render" and default_step:
         traffic = _profiled_traffic("render_tc_kernel_room-8192x96.md",
                                     ("gs_render_tc.cuh", "gs_tc.cuh", "gs_device.cuh"))
@@ -326,6 +346,8 @@ def run_ours(args):
                             (" + gs_eikonal" if args.eikonal else ""),
                    "loss_terms": "rgb, depth, sdf, fs, smooth" + (", eikonal (lam 1, free-space samples)"
                                                                   if args.eikonal else ""),
+                   "poses": ("refined: per-frame (dt, nu), gs_pose_apply + gs_pose_backward + Adam 5e-4 in every step"
+                             if args.poses else "fixed"),
                    "l2": "inputs larger than L2: 1.2 GB of parameter/gradient/moment state streamed per step",
                    "frame_render_s": round(t_frames, 1)},
         "kernels_ms": {k: round(vv, 4) for k, vv in avg.items()},
@@ -341,7 +363,7 @@ def run_ours(args):
                 "h2d_bytes_per_step": 24, "d2h_bytes_per_step": 40, "steps": e2e_steps,
                 "what": "per step: H2D dloss seed (pinned), the C-ABI calls of the step, D2H loss and counts into a "
                         "pinned double buffer that the host reads one step later; frames resident on the device"},
-        "gpu_launches": ((9 if args.split else 6) + (1 if args.eikonal else 0)) * args.steps,
+        "gpu_launches": ((9 if args.split else 6) + (1 if args.eikonal else 0) + (3 if args.poses else 0)) * args.steps,
         "clocks": clk,
         "loss_last": [round(x, 6) for x in lossv],
     }
@@ -735,6 +757,8 @@ def main():
     ap.add_argument("--split", action="store_true", help="gs_forward then gs_backward instead of the fused call")
     ap.add_argument("--no-pipeline", action="store_true",
                     help="sample each step's batch in line instead of during the previous step")
+    ap.add_argument("--poses", action="store_true",
+                    help="refine the camera poses in every step (gs_pose_apply, gs_pose_backward, Adam at 5e-4)")
     ap.add_argument("--eikonal", action="store_true",
                     help="add the Eikonal term on the free-space samples (gs_eikonal, lam_eik = 1) to every step")
     ap.add_argument("--prop-pretrain", type=int, default=300,
