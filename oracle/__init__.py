@@ -32,7 +32,7 @@ class OcConfig(ctypes.Structure):
                 ("n_strat", ctypes.c_int32), ("n_guided", ctypes.c_int32), ("near_m", ctypes.c_float),
                 ("far_m", ctypes.c_float), ("guide_half", ctypes.c_float), ("trunc", ctypes.c_float),
                 ("kappa_fs", ctypes.c_float), ("lam", ctypes.c_float * 5), ("n_smooth", ctypes.c_int32),
-                ("delta_s", ctypes.c_float)]
+                ("delta_s", ctypes.c_float), ("arch", ctypes.c_int32)]
 
 
 class OcFrames(ctypes.Structure):
@@ -110,6 +110,10 @@ def lib():
             L.oc_adam.restype = None
             L.oc_adam.argtypes = [vp, vp, vp, vp, i64, i64, i32, dbl, dbl, dbl, dbl, dbl]
             L.oc_num_threads.restype = i32
+            L.oc_paper_param_count.restype = i64
+            L.oc_paper_param_count.argtypes = [vp, vp]
+            L.oc_step_paper.restype = i32
+            L.oc_step_paper.argtypes = [vp, vp, i32, i32] + [vp] * 6 + [i32] + [vp] * 12
             _LIB = L
     return _LIB
 
@@ -126,6 +130,7 @@ def make_config(w) -> OcConfig:
     c.near_m, c.far_m, c.guide_half, c.trunc, c.kappa_fs = w.near, w.far, w.guide_half, w.trunc, w.kappa_fs
     c.lam[:] = list(w.lambdas)
     c.n_smooth, c.delta_s = w.n_smooth, w.delta_s
+    c.arch = 1 if getattr(w, "arch", "compact") == "paper" else 0
     return c
 
 
@@ -244,9 +249,17 @@ def pose_grad(cfg: OcConfig, frames: OcFramesHolder, theta, c2w, xi, batch: dict
     return g
 
 
+def paper_param_count(cfg: OcConfig) -> tuple[int, int]:
+    """(total floats, grid floats) of the flat vector of the paper's architecture."""
+    ng = np.zeros(1, np.int64)
+    n = lib().oc_paper_param_count(ctypes.byref(cfg), _p(ng))
+    return int(n), int(ng[0])
+
+
 def step(cfg: OcConfig, theta, batch: dict, smooth: dict | None, dloss=None, want_grad=True, want_margins=False,
          want_weights=False):
-    """Losses (and gradients) of one step.  theta: flat parameters (promoted to FP64)."""
+    """Losses (and gradients) of one step.  theta: flat parameters (promoted to FP64).
+    cfg.arch selects the decoders: 0 the workload's (oc_step), 1 the paper's (oc_step_paper)."""
     th = np.ascontiguousarray(theta, dtype=np.float64)
     R, N = batch["t"].shape
     if smooth is None:
@@ -263,7 +276,8 @@ def step(cfg: OcConfig, theta, batch: dict, smooth: dict | None, dloss=None, wan
     amb = np.zeros((R, N), np.uint8) if want_margins else None
     dl = None if dloss is None else np.ascontiguousarray(dloss, dtype=np.float64)
     w = np.zeros((R, N)) if want_weights else None
-    rc = lib().oc_step(ctypes.byref(cfg), _p(th), R, N, _p(batch["o"]), _p(batch["r"]), _p(batch["rgb"]),
+    fn = lib().oc_step_paper if cfg.arch == 1 else lib().oc_step
+    rc = fn(ctypes.byref(cfg), _p(th), R, N, _p(batch["o"]), _p(batch["r"]), _p(batch["rgb"]),
                        _p(batch["D"]), _p(batch["t"]), _p(batch["cls"]), P, _p(xs), _p(eps), _p(valid), _p(dl),
                        _p(loss), _p(rgb_hat), _p(d_hat), _p(wsum), _p(grad), _p(margins), _p(amb), _p(w))
     if rc != 0:

@@ -21,6 +21,10 @@
  *   hierarchical importance sampler (separate entry) ............. Sec. 3.2 (3 x 12 from N_c = 96), Sec. 4
  *   mesh extraction from phi on a lattice (separate entry) ....... Sec. 4 (marching cubes at 1 cm; tetrahedra here)
  *   camera-pose refinement gradient (separate entry) ............. Sec. 3.4, Sec. 4 (t, so(3))
+ *   the paper's architecture: colour grid W_beta (h_c = 6) at the
+ *     finest level, colour decoder fed W_beta(x) and the viewing
+ *     direction, decoders with two hidden layers of 32 (separate
+ *     entry oc_step_paper) ..................................... Sec. 3.1 Eq. (COLOR_MLP), Architecture Details
  *   Adam ......................................................... Sec. 4 (Implementation Details)
  *
  * Precision: every quantity that decides an integer (pixel index, sample depths and their
@@ -80,6 +84,7 @@ typedef struct {
   float lam[5];     /* rgb, depth, sdf, fs, smooth */
   int32_t n_smooth;
   float delta_s;
+  int32_t arch; /* 0: the workload's decoders (16-32-16, 15-32-3); 1: the paper's architecture (oc_step_paper) */
 } oc_config;
 
 typedef struct {
@@ -1668,4 +1673,413 @@ int oc_num_threads(void) {
 #else
   return 1;
 #endif
+}
+
+/* ------------------------------------------------------------------------------------ */
+/* the paper's architecture (Sec. 3.1 Eq. SDF_MLP, Eq. COLOR_MLP, "Architecture Details") */
+/* ------------------------------------------------------------------------------------ */
+/* Geometry: phi = f_omega(V_theta(x)) with f_omega a decoder of two hidden layers of 32
+ * (ReLU) and one linear output.  Colour: c = g_gamma(W_beta(x), d), where W_beta(x) is the
+ * trilinear interpolation of a separate grid of h_c = 6 colour features per vertex at the
+ * finest level (same vertices as geometry level 3) and d the viewing direction, taken as
+ * the unit ray direction r/|r|; g_gamma has two hidden layers of 32 (ReLU) and a sigmoid
+ * on its 3 outputs.
+ * Flat parameter vector: geometry levels 0..3 ([nz][ny][nx][4] each), the colour grid
+ * [nz][ny][nx][6] of level 3 padded with zeros to a multiple of 4 floats, then PA_MLP
+ * decoder floats: gW1[32][16], gb1[32], gW2[32][32], gb2[32], gw3[32], gb3,
+ * cW1[32][9], cb1[32], cW2[32][32], cb2[32], cW3[3][32], cb3[3], kappa. */
+#define PA_C 6            /* h_c */
+#define PA_H 32           /* neurons per hidden layer */
+#define PA_U (PA_C + 3)   /* colour decoder input [W_beta(x), d] */
+#define PA_MLP (PA_H * OC_Z + PA_H + PA_H * PA_H + PA_H + PA_H + 1 + PA_H * PA_U + PA_H + PA_H * PA_H + PA_H + 3 * PA_H + 3 + 1)
+
+static int64_t pa_colour_floats(const oc_config* c) {
+  int64_t n = (int64_t)c->dims[3][0] * c->dims[3][1] * c->dims[3][2] * PA_C;
+  return (n + 3) / 4 * 4;
+}
+
+/* number of floats of the flat vector; *n_grid (may be NULL) = geometry + colour grid floats */
+int64_t oc_paper_param_count(const oc_config* c, int64_t* n_grid) {
+  int64_t g = grid_size(c) + pa_colour_floats(c);
+  if (n_grid) *n_grid = g;
+  return g + PA_MLP;
+}
+
+typedef struct {
+  const double *gW1, *gb1, *gW2, *gb2, *gw3, *gb3, *cW1, *cb1, *cW2, *cb2, *cW3, *cb3, *kappa;
+} pa_mlp_t;
+
+static pa_mlp_t pa_view(const double* b) {
+  pa_mlp_t m;
+  m.gW1 = b;
+  m.gb1 = m.gW1 + PA_H * OC_Z;
+  m.gW2 = m.gb1 + PA_H;
+  m.gb2 = m.gW2 + PA_H * PA_H;
+  m.gw3 = m.gb2 + PA_H;
+  m.gb3 = m.gw3 + PA_H;
+  m.cW1 = m.gb3 + 1;
+  m.cb1 = m.cW1 + PA_H * PA_U;
+  m.cW2 = m.cb1 + PA_H;
+  m.cb2 = m.cW2 + PA_H * PA_H;
+  m.cW3 = m.cb2 + PA_H;
+  m.cb3 = m.cW3 + 3 * PA_H;
+  m.kappa = m.cb3 + 3;
+  return m;
+}
+
+typedef struct {
+  double z[OC_Z], y1[PA_H], a1[PA_H], y2[PA_H], a2[PA_H], phi;  /* geometry decoder */
+  double u[PA_U], q1[PA_H], r1[PA_H], q2[PA_H], r2[PA_H], pre[3], c[3]; /* colour decoder */
+  int64_t cvtx[8];  /* flat colour-grid float index of feature 0 of each level-3 corner */
+  double cw[8];     /* their trilinear weights */
+} pa_act_t;
+
+/* y = b + W x for W [n][k] row-major */
+static void pa_affine(const double* W, const double* b, const double* x, int n, int k, double* y) {
+  for (int j = 0; j < n; ++j) {
+    double s = b[j];
+    for (int i = 0; i < k; ++i) s += W[j * k + i] * x[i];
+    y[j] = s;
+  }
+}
+
+/* features and both decoders at the binary32 position x seen along unit direction d */
+static void pa_eval(const oc_config* c, const double* theta, const pa_mlp_t* m, const float x[3], const double d[3],
+                    cell_t cells[OC_LEVELS], double dzdx[OC_Z][3], pa_act_t* A) {
+  features(c, theta, x, cells, A->z, dzdx);
+  /* W_beta(x): the colour grid shares level 3's vertices, so it uses level 3's cell */
+  const int64_t cbase = grid_size(c), off3 = level_offset(c, 3);
+  for (int k = 0; k < PA_C; ++k) A->u[k] = 0.0;
+  for (int cc = 0; cc < 8; ++cc) {
+    const int64_t vtx = (cells[3].corner[cc] - off3) / OC_FEAT;
+    A->cvtx[cc] = cbase + vtx * PA_C;
+    A->cw[cc] = cells[3].w[cc];
+    for (int k = 0; k < PA_C; ++k) A->u[k] += cells[3].w[cc] * theta[A->cvtx[cc] + k];
+  }
+  for (int a = 0; a < 3; ++a) A->u[PA_C + a] = d[a];
+  pa_affine(m->gW1, m->gb1, A->z, PA_H, OC_Z, A->y1);
+  for (int j = 0; j < PA_H; ++j) A->a1[j] = A->y1[j] > 0 ? A->y1[j] : 0;
+  pa_affine(m->gW2, m->gb2, A->a1, PA_H, PA_H, A->y2);
+  for (int j = 0; j < PA_H; ++j) A->a2[j] = A->y2[j] > 0 ? A->y2[j] : 0;
+  pa_affine(m->gw3, m->gb3, A->a2, 1, PA_H, &A->phi);
+  pa_affine(m->cW1, m->cb1, A->u, PA_H, PA_U, A->q1);
+  for (int j = 0; j < PA_H; ++j) A->r1[j] = A->q1[j] > 0 ? A->q1[j] : 0;
+  pa_affine(m->cW2, m->cb2, A->r1, PA_H, PA_H, A->q2);
+  for (int j = 0; j < PA_H; ++j) A->r2[j] = A->q2[j] > 0 ? A->q2[j] : 0;
+  pa_affine(m->cW3, m->cb3, A->r2, 3, PA_H, A->pre);
+  for (int j = 0; j < 3; ++j) A->c[j] = sigm(A->pre[j]);
+}
+
+/* one dense layer backwards: gW += dy x^T, gb += dy, and (dx != NULL) dx = W^T dy */
+static void pa_affine_back(const double* W, const double* x, const double* dy, int n, int k, double* gW, double* gb,
+                           double* dx) {
+  for (int j = 0; j < n; ++j) {
+    gb[j] += dy[j];
+    for (int i = 0; i < k; ++i) gW[j * k + i] += dy[j] * x[i];
+  }
+  if (dx)
+    for (int i = 0; i < k; ++i) {
+      double s = 0;
+      for (int j = 0; j < n; ++j) s += W[j * k + i] * dy[j];
+      dx[i] = s;
+    }
+}
+
+/* reverse mode of pa_eval's decoders for upstream dphi, dc: decoder gradients into gm (the
+ * PA_MLP block), dL/dz [16] and dL/dW_beta(x) [6] returned */
+static void pa_backward(const pa_mlp_t* m, const pa_act_t* A, double dphi, const double dc[3], double* gm,
+                        double dz[OC_Z], double dcf[PA_C]) {
+  pa_mlp_t g = pa_view(gm); /* same offsets in the gradient block */
+  double d2[PA_H], d1[PA_H], du[PA_U];
+  /* geometry: phi = gw3 . a2 + gb3 */
+  pa_affine_back(m->gw3, A->a2, &dphi, 1, PA_H, (double*)g.gw3, (double*)g.gb3, d2);
+  for (int j = 0; j < PA_H; ++j) d2[j] = A->y2[j] > 0 ? d2[j] : 0.0;
+  pa_affine_back(m->gW2, A->a1, d2, PA_H, PA_H, (double*)g.gW2, (double*)g.gb2, d1);
+  for (int j = 0; j < PA_H; ++j) d1[j] = A->y1[j] > 0 ? d1[j] : 0.0;
+  pa_affine_back(m->gW1, A->z, d1, PA_H, OC_Z, (double*)g.gW1, (double*)g.gb1, dz);
+  /* colour: c = sigmoid(cW3 r2 + cb3) */
+  double dpre[3];
+  for (int j = 0; j < 3; ++j) dpre[j] = dc[j] * A->c[j] * (1.0 - A->c[j]);
+  pa_affine_back(m->cW3, A->r2, dpre, 3, PA_H, (double*)g.cW3, (double*)g.cb3, d2);
+  for (int j = 0; j < PA_H; ++j) d2[j] = A->q2[j] > 0 ? d2[j] : 0.0;
+  pa_affine_back(m->cW2, A->r1, d2, PA_H, PA_H, (double*)g.cW2, (double*)g.cb2, d1);
+  for (int j = 0; j < PA_H; ++j) d1[j] = A->q1[j] > 0 ? d1[j] : 0.0;
+  pa_affine_back(m->cW1, A->u, d1, PA_H, PA_U, (double*)g.cW1, (double*)g.cb1, du);
+  for (int k = 0; k < PA_C; ++k) dcf[k] = du[k]; /* the viewing direction is not a parameter */
+}
+
+/* d phi / d z of the two-hidden-layer geometry decoder (piecewise linear, masks fixed):
+ * e = m2 (.) gw3, pm = m1 (.) (gW2^T e), p = gW1^T pm */
+static void pa_dphi_dz(const pa_mlp_t* m, const pa_act_t* A, double p[OC_Z], double pm[PA_H], double e[PA_H]) {
+  for (int j = 0; j < PA_H; ++j) e[j] = A->y2[j] > 0 ? m->gw3[j] : 0.0;
+  for (int i = 0; i < PA_H; ++i) {
+    double s = 0;
+    for (int j = 0; j < PA_H; ++j) s += m->gW2[j * PA_H + i] * e[j];
+    pm[i] = A->y1[i] > 0 ? s : 0.0;
+  }
+  for (int k = 0; k < OC_Z; ++k) {
+    double s = 0;
+    for (int i = 0; i < PA_H; ++i) s += m->gW1[i * OC_Z + k] * pm[i];
+    p[k] = s;
+  }
+}
+
+/*
+ * One step of the paper's architecture: the losses of oc_step (rgb, depth, truncated SDF,
+ * free space, smoothness, weighted total; same batch normalisations and readings) with
+ * phi = f_omega(V_theta(x)) and c = g_gamma(W_beta(x), d), and (grad != NULL) their
+ * gradient with respect to the flat vector laid out as oc_paper_param_count describes.
+ * Arguments as oc_step.  margins: entry 0 = min |hidden pre-activation| of both decoders
+ * (main samples and smoothness points), 5 = min |d_hat - D|, 7 = signature of the branch
+ * decisions; the others are set to +inf (8 and 9 to 0).  amb flags as in oc_step.
+ */
+int oc_step_paper(const oc_config* c, const double* theta, int R, int N, const float* o, const float* r,
+                  const float* rgb, const float* D, const float* t, const uint8_t* cls, int P, const float* xs,
+                  const float* eps, const uint8_t* valid, const double* dloss, double* loss, double* rgb_hat,
+                  double* d_hat, double* wsum, double* grad, double* margins, uint8_t* amb, double* w_out) {
+  if (R < 0 || N < 2 || P < 0) return -1;
+  int64_t ng = 0;
+  const int64_t ntot = oc_paper_param_count(c, &ng);
+  const pa_mlp_t m = pa_view(theta + ng);
+  const double s = exp(*m.kappa);
+
+  int64_t n_d = 0, n_tr = 0, n_fs = 0, n_g = 0;
+  for (int i = 0; i < R; ++i) {
+    n_d += D[i] > 0.0f;
+    for (int k = 0; k < N; ++k) {
+      n_tr += cls[(size_t)i * N + k] == CLS_TR;
+      n_fs += cls[(size_t)i * N + k] == CLS_FS;
+    }
+  }
+  for (int p = 0; p < P; ++p) n_g += valid[p] != 0;
+  double wt[5];
+  for (int k = 0; k < 5; ++k) wt[k] = dloss ? dloss[k] + (double)c->lam[k] * dloss[5] : (double)c->lam[k];
+  if (amb) memset(amb, 0, (size_t)R * N);
+  const int do_grad = grad != NULL;
+  double lsum[5] = {0, 0, 0, 0, 0};
+  double hid_margin = INFINITY, d_margin = INFINITY;
+  uint64_t sig = 0;
+  if (do_grad) memset(grad, 0, sizeof(double) * (size_t)ntot);
+  double* gm = do_grad ? grad + ng : NULL;
+
+  /* Rays one after another (plain and sequential: this form is checked on small batches). */
+  pa_act_t* A = (pa_act_t*)malloc(sizeof(pa_act_t) * (size_t)N);
+  cell_t* cells = (cell_t*)malloc(sizeof(cell_t) * (size_t)N * OC_LEVELS);
+  double *phi = malloc(sizeof(double) * N), *Phi = malloc(sizeof(double) * N), *alpha = malloc(sizeof(double) * N),
+         *T = malloc(sizeof(double) * N), *w = malloc(sizeof(double) * N), *U = malloc(sizeof(double) * N),
+         *dPhi = malloc(sizeof(double) * N);
+  for (int i = 0; i < R; ++i) {
+    const float* ti = t + (size_t)i * N;
+    double d[3], rn = 0;
+    for (int a = 0; a < 3; ++a) rn += (double)r[3 * i + a] * (double)r[3 * i + a];
+    rn = sqrt(rn);
+    for (int a = 0; a < 3; ++a) d[a] = (double)r[3 * i + a] / rn;
+    for (int k = 0; k < N; ++k) {
+      float x[3];
+      for (int a = 0; a < 3; ++a) {
+        float step_ = ti[k] * r[3 * i + a];
+        x[a] = o[3 * i + a] + step_;
+      }
+      pa_eval(c, theta, &m, x, d, cells + (size_t)k * OC_LEVELS, NULL, &A[k]);
+      phi[k] = A[k].phi;
+      const double* hid[4] = {A[k].y1, A[k].y2, A[k].q1, A[k].q2};
+      for (int h = 0; h < 4; ++h) {
+        for (int j = 0; j < PA_H; ++j) mmin(&hid_margin, hid[h][j]);
+        sigmix(&sig, ((uint64_t)i * (uint64_t)N + (uint64_t)k) * 8 + (uint64_t)h, relu_mask(hid[h], PA_H));
+      }
+    }
+    /* NeuS weights (Sec. 3.2); the colours are composited here with the same weights */
+    double ch[3] = {0, 0, 0}, dh, ws;
+    composite(N, phi, s, NULL, ti, Phi, alpha, T, w, ch, &dh, &ws);
+    for (int k = 0; k < N; ++k)
+      for (int j = 0; j < 3; ++j) ch[j] += w[k] * A[k].c[j];
+    for (int k = 0; k + 1 < N; ++k)
+      sigmix(&sig, ((uint64_t)i * (uint64_t)N + (uint64_t)k) * 8 + 5,
+             (uint64_t)(alpha[k] > 0) | (uint64_t)(Phi[k] > 1e-6) << 1);
+    if (rgb_hat)
+      for (int j = 0; j < 3; ++j) rgb_hat[3 * i + j] = ch[j];
+    if (d_hat) d_hat[i] = dh;
+    if (wsum) wsum[i] = ws;
+    if (w_out)
+      for (int k = 0; k < N; ++k) w_out[(size_t)i * N + k] = w[k];
+    for (int j = 0; j < 3; ++j) {
+      double e = (double)rgb[3 * i + j] - ch[j];
+      lsum[0] += e * e;
+    }
+    const double Di = (double)D[i];
+    if (D[i] > 0.0f) {
+      lsum[1] += fabs(Di - dh);
+      mmin(&d_margin, dh - Di);
+      sigmix(&sig, ((uint64_t)i * (uint64_t)N) * 8 + 7, (uint64_t)(dh > Di));
+    }
+    for (int k = 0; k < N; ++k) {
+      const int cl = cls[(size_t)i * N + k];
+      const double b = Di - (double)ti[k];
+      if (cl == CLS_TR) {
+        lsum[2] += fabs(phi[k] - b);
+        if (amb && fabs(phi[k] - b) < 2e-5) amb[(size_t)i * N + k] |= 2;
+        sigmix(&sig, ((uint64_t)i * (uint64_t)N + (uint64_t)k) * 8 + 6, (uint64_t)(phi[k] > b));
+      } else if (cl == CLS_FS) {
+        double v[3] = {0.0, exp(-(double)c->kappa_fs * phi[k]) - 1.0, phi[k] - b};
+        int arg = 0;
+        for (int q = 1; q < 3; ++q)
+          if (v[q] > v[arg]) arg = q;
+        double second = -INFINITY;
+        for (int q = 0; q < 3; ++q)
+          if (q != arg && v[q] > second) second = v[q];
+        if (amb && v[arg] - second < 2e-5) amb[(size_t)i * N + k] |= 4;
+        sigmix(&sig, ((uint64_t)i * (uint64_t)N + (uint64_t)k) * 8 + 6, (uint64_t)arg + 2);
+        lsum[3] += v[arg];
+      }
+    }
+    if (!do_grad) continue;
+
+    /* backward through the compositing (as in oc_step) */
+    double gc[3], gd = 0;
+    for (int j = 0; j < 3; ++j) gc[j] = wt[0] / (double)R * 2.0 * (ch[j] - (double)rgb[3 * i + j]);
+    if (D[i] > 0.0f && n_d > 0) gd = wt[1] / (double)n_d * sgn(dh - Di);
+    U[N - 1] = 0;
+    for (int k = N - 1; k >= 1; --k) {
+      double ek = gc[0] * A[k].c[0] + gc[1] * A[k].c[1] + gc[2] * A[k].c[2] + gd * (double)ti[k];
+      U[k - 1] = alpha[k] * ek + (1.0 - alpha[k]) * U[k];
+    }
+    for (int k = 0; k < N; ++k) dPhi[k] = 0;
+    for (int k = 0; k < N - 1; ++k) {
+      double ek = gc[0] * A[k].c[0] + gc[1] * A[k].c[1] + gc[2] * A[k].c[2] + gd * (double)ti[k];
+      double dalpha = T[k] * (ek - U[k]);
+      double den = Phi[k] > 1e-6 ? Phi[k] : 1e-6;
+      double q = (Phi[k] - Phi[k + 1]) / den;
+      if (amb && fabs(q) < 1e-5 && phi[k] != phi[k + 1] && 1.0 - Phi[k] > 1e-5) {
+        double self = fabs(dalpha) * s * Phi[k] * (1.0 - Phi[k]) / den;
+        double next = fabs(dalpha) * s * Phi[k + 1] * (1.0 - Phi[k + 1]) / den;
+        double dphi_rel = fabs(phi[k] - phi[k + 1]) / (fabs(phi[k]) > 1.0 ? fabs(phi[k]) : 1.0);
+        if ((self > next ? self : next) > 1e-7 && dphi_rel < 2e-6) amb[(size_t)i * N + k] |= 1;
+      }
+      if (q > 0) {
+        dPhi[k + 1] += dalpha * (-1.0 / den);
+        if (Phi[k] > 1e-6) dPhi[k] += dalpha * (Phi[k + 1] / (Phi[k] * Phi[k]));
+        else dPhi[k] += dalpha * (1.0 / 1e-6);
+      }
+    }
+    for (int k = 0; k < N; ++k) {
+      const double dsig = Phi[k] * (1.0 - Phi[k]);
+      double dphi = dPhi[k] * s * dsig;
+      gm[PA_MLP - 1] += dPhi[k] * dsig * s * phi[k];
+      const int cl = cls[(size_t)i * N + k];
+      const double b = Di - (double)ti[k];
+      if (cl == CLS_TR && n_tr > 0) dphi += wt[2] / (double)n_tr * sgn(phi[k] - b);
+      if (cl == CLS_FS && n_fs > 0) {
+        double e = exp(-(double)c->kappa_fs * phi[k]) - 1.0, lin = phi[k] - b;
+        int arg = 0;
+        double top = 0;
+        if (e > top) { top = e; arg = 1; }
+        if (lin > top) { arg = 2; }
+        dphi += wt[3] / (double)n_fs * (arg == 1 ? -(double)c->kappa_fs * (e + 1.0) : (arg == 2 ? 1.0 : 0.0));
+      }
+      double dc[3], dz[OC_Z], dcf[PA_C];
+      for (int j = 0; j < 3; ++j) dc[j] = w[k] * gc[j];
+      pa_backward(&m, &A[k], dphi, dc, gm, dz, dcf);
+      /* adjoint of the trilinear gathers: geometry levels and the colour grid */
+      for (int l = 0; l < OC_LEVELS; ++l) {
+        const cell_t* cl_ = &cells[(size_t)k * OC_LEVELS + l];
+        for (int cc = 0; cc < 8; ++cc)
+          for (int f = 0; f < OC_FEAT; ++f) grad[cl_->corner[cc] + f] += cl_->w[cc] * dz[OC_FEAT * l + f];
+      }
+      for (int cc = 0; cc < 8; ++cc)
+        for (int f = 0; f < PA_C; ++f) grad[A[k].cvtx[cc] + f] += A[k].cw[cc] * dcf[f];
+    }
+  }
+
+  /* smoothness on S_g (Sec. 3.3) with the two-hidden-layer geometry decoder:
+   * g(x) = grad_x phi = sum_k p_k dz_k/dx, p = d phi/dz (pa_dphi_dz) */
+  for (int p = 0; p < P; ++p) {
+    if (!valid[p]) continue;
+    float y[2][3];
+    for (int a = 0; a < 3; ++a) {
+      y[0][a] = xs[3 * p + a];
+      y[1][a] = xs[3 * p + a] + eps[3 * p + a];
+    }
+    const double dnone[3] = {0, 0, 1};
+    cell_t cl[2][OC_LEVELS];
+    pa_act_t Ay[2];
+    double dzdx[2][OC_Z][3], pz[2][OC_Z], pm[2][PA_H], e[2][PA_H], g[2][3];
+    for (int ev = 0; ev < 2; ++ev) {
+      pa_eval(c, theta, &m, y[ev], dnone, cl[ev], dzdx[ev], &Ay[ev]);
+      for (int j = 0; j < PA_H; ++j) {
+        mmin(&hid_margin, Ay[ev].y1[j]);
+        mmin(&hid_margin, Ay[ev].y2[j]);
+      }
+      sigmix(&sig, ((uint64_t)1 << 60) + (uint64_t)p * 4 + (uint64_t)ev * 2, relu_mask(Ay[ev].y1, PA_H));
+      sigmix(&sig, ((uint64_t)1 << 60) + (uint64_t)p * 4 + (uint64_t)ev * 2 + 1, relu_mask(Ay[ev].y2, PA_H));
+      pa_dphi_dz(&m, &Ay[ev], pz[ev], pm[ev], e[ev]);
+      for (int a = 0; a < 3; ++a) {
+        double acc = 0;
+        for (int k = 0; k < OC_Z; ++k) acc += pz[ev][k] * dzdx[ev][k][a];
+        g[ev][a] = acc;
+      }
+    }
+    double dg[3], l2 = 0;
+    for (int a = 0; a < 3; ++a) {
+      dg[a] = g[0][a] - g[1][a];
+      l2 += dg[a] * dg[a];
+    }
+    lsum[4] += l2;
+    if (!do_grad || n_g == 0) continue;
+    pa_mlp_t gg = pa_view(gm);
+    for (int ev = 0; ev < 2; ++ev) {
+      /* a = dL/dg at this evaluation; a . g = p . j with j_k = a . dz_k/dx */
+      double av[3], jv[OC_Z], vj[PA_H];
+      for (int a = 0; a < 3; ++a) av[a] = (ev == 0 ? 1.0 : -1.0) * wt[4] / (double)n_g * 2.0 * dg[a];
+      for (int k = 0; k < OC_Z; ++k) jv[k] = av[0] * dzdx[ev][k][0] + av[1] * dzdx[ev][k][1] + av[2] * dzdx[ev][k][2];
+      /* grid: d(a . g)/d theta_{l,c,f} = p_{l,f} (1/v_l) (a . d w_c / d f) */
+      for (int l = 0; l < OC_LEVELS; ++l)
+        for (int cc = 0; cc < 8; ++cc) {
+          double ad = (av[0] * cl[ev][l].dw[cc][0] + av[1] * cl[ev][l].dw[cc][1] + av[2] * cl[ev][l].dw[cc][2]) *
+                      cl[ev][l].inv_v;
+          for (int f = 0; f < OC_FEAT; ++f) grad[cl[ev][l].corner[cc] + f] += pz[ev][OC_FEAT * l + f] * ad;
+        }
+      /* decoder: a . g = (gW2 (m1 (.) gW1 j)) . (m2 (.) gw3) */
+      for (int i1 = 0; i1 < PA_H; ++i1) {
+        double acc = 0;
+        for (int k = 0; k < OC_Z; ++k) {
+          ((double*)gg.gW1)[i1 * OC_Z + k] += pm[ev][i1] * jv[k];
+          acc += m.gW1[i1 * OC_Z + k] * jv[k];
+        }
+        vj[i1] = Ay[ev].y1[i1] > 0 ? acc : 0.0;
+      }
+      for (int i2 = 0; i2 < PA_H; ++i2) {
+        double acc = 0;
+        for (int i1 = 0; i1 < PA_H; ++i1) {
+          ((double*)gg.gW2)[i2 * PA_H + i1] += e[ev][i2] * vj[i1];
+          acc += m.gW2[i2 * PA_H + i1] * vj[i1];
+        }
+        if (Ay[ev].y2[i2] > 0) ((double*)gg.gw3)[i2] += acc;
+      }
+    }
+  }
+  free(A);
+  free(cells);
+  free(phi);
+  free(Phi);
+  free(alpha);
+  free(T);
+  free(w);
+  free(U);
+  free(dPhi);
+
+  loss[0] = R > 0 ? lsum[0] / (double)R : 0.0;
+  loss[1] = n_d > 0 ? lsum[1] / (double)n_d : 0.0;
+  loss[2] = n_tr > 0 ? lsum[2] / (double)n_tr : 0.0;
+  loss[3] = n_fs > 0 ? lsum[3] / (double)n_fs : 0.0;
+  loss[4] = n_g > 0 ? lsum[4] / (double)n_g : 0.0;
+  loss[5] = 0;
+  for (int k = 0; k < 5; ++k) loss[5] += (double)c->lam[k] * loss[k];
+  if (margins) {
+    for (int k = 0; k < 10; ++k) margins[k] = INFINITY;
+    margins[0] = hid_margin;
+    margins[5] = d_margin;
+    margins[7] = (double)(sig & ((1ULL << 52) - 1));
+    margins[8] = margins[9] = 0.0;
+  }
+  return 0;
 }

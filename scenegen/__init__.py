@@ -34,6 +34,14 @@ MLP_SHAPES = [("W1", (32, 16)), ("b1", (32,)), ("W2", (16, 32)), ("b2", (16,)),
 MLP_PARAMS = sum(int(np.prod(s)) for _, s in MLP_SHAPES)  # 1684
 FEAT = 4
 LEVELS = 4
+# the paper's architecture (Sec. 3.1): a colour grid of 6 features per vertex at the finest
+# level, and two decoders with two hidden layers of 32 (the colour decoder also reads the
+# unit viewing direction)
+COLOUR_FEAT = 6
+PAPER_MLP_SHAPES = [("gW1", (32, 16)), ("gb1", (32,)), ("gW2", (32, 32)), ("gb2", (32,)), ("gw3", (1, 32)),
+                    ("gb3", (1,)), ("cW1", (32, 9)), ("cb1", (32,)), ("cW2", (32, 32)), ("cb2", (32,)),
+                    ("cW3", (3, 32)), ("cb3", (3,)), ("kappa", (1,))]
+PAPER_MLP_PARAMS = sum(int(np.prod(s)) for _, s in PAPER_MLP_SHAPES)  # 3109
 
 
 class _Prim(ctypes.Structure):
@@ -260,6 +268,7 @@ class Workload:
     imp_coarse: int = 0     # hierarchical importance sampler: coarse samples (0 = off)
     imp_steps: int = 0      # importance steps
     imp_per_step: int = 0   # samples added per step
+    arch: str = "compact"   # "compact": 16-32-16 / 15-32-3 decoders; "paper": colour grid + 2-hidden-layer decoders
     extra: dict = field(default_factory=dict)
 
     @property
@@ -273,14 +282,30 @@ class Workload:
     def dims(self):
         return grid_dims(self.extent_min, self.extent_max, self.voxels)
 
+    @property
+    def mlp_shapes(self):
+        return PAPER_MLP_SHAPES if self.arch == "paper" else MLP_SHAPES
+
     def layout(self):
-        """Flat parameter vector: grid levels 0..3 as [nz][ny][nx][4] float32, then the MLP block."""
+        """Flat parameter vector: grid levels 0..3 as [nz][ny][nx][4] float32, then (paper
+        architecture) the colour grid [nz][ny][nx][6] of level 3 padded to a multiple of 4
+        floats, then the decoder block.  Returns (level offsets, grid floats, total floats)."""
         offs, o = [], 0
         for (nx, ny, nz) in self.dims:
             offs.append(o)
             o += nx * ny * nz * FEAT
-        n_grid = o
-        return offs, n_grid, n_grid + MLP_PARAMS
+        if self.arch == "paper":
+            o += self.colour_floats()
+            return offs, o, o + PAPER_MLP_PARAMS
+        return offs, o, o + MLP_PARAMS
+
+    def colour_offset(self) -> int:
+        """Float offset of the colour grid (paper architecture): right after the geometry levels."""
+        return sum(nx * ny * nz * FEAT for (nx, ny, nz) in self.dims)
+
+    def colour_floats(self) -> int:
+        nx, ny, nz = self.dims[3]
+        return (nx * ny * nz * COLOUR_FEAT + 3) // 4 * 4
 
     def with_(self, **kw) -> "Workload":
         d = dict(self.__dict__)
@@ -311,6 +336,10 @@ WORKLOADS["room-imp-8192x132"] = WORKLOADS["room-8192x96"].with_(name="room-imp-
 # 32 samples per ray (24 drawn from the proposal + 8 depth-guided), plain 64 + 32 as fallback
 WORKLOADS["room-prop-65536x32"] = WORKLOADS["room-8192x96"].with_(name="room-prop-65536x32", rays=65536,
                                                                    blob_frac=0.3, prop_samples=32, prop_guided=8)
+# the paper's architecture (Sec. 3.1): colour grid at the finest level, view direction,
+# decoders with two hidden layers of 32
+WORKLOADS["cube-paper-1024x64"] = WORKLOADS["cube-1024x64"].with_(name="cube-paper-1024x64", arch="paper")
+WORKLOADS["room-paper-8192x96"] = WORKLOADS["room-8192x96"].with_(name="room-paper-8192x96", arch="paper")
 
 
 @dataclass
@@ -413,10 +442,12 @@ def init_params(w: Workload, seed: int = SEED_INIT) -> np.ndarray:
     offs, n_grid, n_total = w.layout()
     theta = np.empty(n_total, np.float32)
     theta[:n_grid] = rng.normal(0.0, 1e-4, n_grid).astype(np.float32)
+    if w.arch == "paper":
+        _zero_colour_padding(w, theta)
     o = n_grid
-    for name, shape in MLP_SHAPES:
+    for name, shape in w.mlp_shapes:
         n = int(np.prod(shape))
-        if name.startswith("W"):
+        if name.startswith("W") or name[1:2] in ("W", "w"):
             bound = 1.0 / math.sqrt(shape[1])
             theta[o:o + n] = rng.uniform(-bound, bound, n).astype(np.float32)
         elif name == "kappa":
@@ -454,10 +485,72 @@ def parity_params(w: Workload, seed: int = 11, grid_std: float = 0.05, bias: flo
     return theta
 
 
-def mlp_views(theta: np.ndarray, n_grid: int) -> dict:
-    """Named views of the MLP block of a flat parameter vector."""
+def _zero_colour_padding(w, theta):
+    nx, ny, nz = w.dims[3]
+    theta[w.colour_offset() + nx * ny * nz * COLOUR_FEAT:w.colour_offset() + w.colour_floats()] = 0.0
+
+
+def colour_view(w, theta) -> np.ndarray:
+    """The colour grid [nz][ny][nx][6] of a paper-architecture parameter vector (a view)."""
+    nx, ny, nz = w.dims[3]
+    o = w.colour_offset()
+    return theta[o:o + nx * ny * nz * COLOUR_FEAT].reshape(nz, ny, nx, COLOUR_FEAT)
+
+
+def paper_sdf_params(w, scene, seed=23, grid_std=0.05, mix=0.1):
+    """Paper-architecture parameters for element-wise parity (the analogue of sdf_params):
+    the scene's exact SDF in feature 0 of the finest geometry level, random features elsewhere
+    (colour grid included), and decoders whose every hidden unit stays far from its kink.
+
+    Geometry: hidden-1 units 0, 1 carry z[12] as relu(z + 3), relu(3 - z); hidden-2 unit 0
+    takes 0.5 (difference) + 3 = z + 3 (always on) and gw3[0] = 1, gb3 = -3, so phi = z[12]
+    plus a small term (weights `mix`) from the other units.  Those units have biases of
+    alternating sign (0.25 in layer 1, 0.5 in layer 2) and weights small enough that no
+    pre-activation reaches zero.  Colour: biases of alternating sign 0.5, small weights on
+    the viewing direction."""
+    assert w.arch == "paper"
+    rng = np.random.default_rng(seed)
+    offs, n_grid, n_tot = w.layout()
+    theta = np.zeros(n_tot, np.float32)
+    theta[:n_grid] = rng.normal(0.0, grid_std, n_grid).astype(np.float32)
+    _zero_colour_padding(w, theta)
+    nx, ny, nz = w.dims[3]
+    X = vertex_positions(w, 3)
+    sdf = scene.sdf(X.reshape(-1, 3)).reshape(nz, ny, nx)
+    set_level_field(w, theta, 3, 0, lambda _: sdf)
+    m = mlp_views(theta, n_grid, PAPER_MLP_SHAPES)
+    alt = np.where(np.arange(32) % 2 == 0, 1.0, -1.0)
+    m["gW1"][:] = rng.uniform(-0.25, 0.25, (32, 16))
+    m["gW1"][:, 12] = 0.0
+    m["gW1"][:2, :] = 0.0
+    m["gW1"][0, 12], m["gW1"][1, 12] = 1.0, -1.0
+    m["gb1"][:] = 0.25 * alt
+    m["gb1"][0] = m["gb1"][1] = 3.0
+    m["gW2"][:] = rng.uniform(-0.05, 0.05, (32, 32))
+    m["gW2"][:, :2] = 0.0
+    m["gW2"][0, :] = 0.0
+    m["gW2"][0, 0], m["gW2"][0, 1] = 0.5, -0.5
+    m["gb2"][:] = 0.5 * alt
+    m["gb2"][0] = 3.0
+    m["gw3"][0, :] = rng.uniform(-mix, mix, 32)
+    m["gw3"][0, 0] = 1.0
+    m["gb3"][0] = -3.0
+    m["cW1"][:] = rng.uniform(-0.25, 0.25, (32, 9))
+    m["cW1"][:, 6:] = rng.uniform(-0.1, 0.1, (32, 3))
+    m["cb1"][:] = 0.5 * alt
+    m["cW2"][:] = rng.uniform(-0.03, 0.03, (32, 32))
+    m["cb2"][:] = 0.5 * alt
+    m["cW3"][:] = rng.uniform(-0.5, 0.5, (3, 32))
+    m["cb3"][:] = rng.uniform(-0.2, 0.2, 3)
+    m["kappa"][0] = math.log(20.0)
+    return theta
+
+
+def mlp_views(theta: np.ndarray, n_grid: int, shapes=None) -> dict:
+    """Named views of the MLP block of a flat parameter vector (shapes: MLP_SHAPES by default,
+    PAPER_MLP_SHAPES for the paper's architecture)."""
     out, o = {}, n_grid
-    for name, shape in MLP_SHAPES:
+    for name, shape in (MLP_SHAPES if shapes is None else shapes):
         n = int(np.prod(shape))
         out[name] = theta[o:o + n].reshape(shape)
         o += n
