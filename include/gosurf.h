@@ -26,6 +26,19 @@
  *   decoder block of GS_MLP_PARAMS floats: W1[32][16], b1[32], W2[16][32], b2[16],
  *     W3[32][15], b3[32], W4[3][32], b4[3], kappa (sharpness s = exp(kappa)).
  *   The gradient vector and the Adam moments use the same layout.
+ *
+ * The paper's architecture (gs_config.arch = GS_ARCH_PAPER; Sec. 3.1 Eq. SDF_MLP and
+ * Eq. COLOR_MLP, "Architecture Details") has its own flat vector:
+ *   grid levels 0..3 as above (geometry features V_theta);
+ *   the colour grid W_beta: dims[3] vertices (those of the finest level), 6 features per
+ *     vertex ([nz][ny][nx][6], 24 bytes per vertex), padded with zeros to a multiple of 4 floats;
+ *   decoder block of GS_PAPER_MLP_PARAMS floats: geometry decoder gW1[32][16], gb1[32],
+ *     gW2[32][32], gb2[32], gw3[32], gb3 (phi = gw3 . relu(gW2 relu(gW1 z + gb1) + gb2) + gb3);
+ *     colour decoder cW1[32][9], cb1[32], cW2[32][32], cb2[32], cW3[3][32], cb3[3]
+ *     (c = sigmoid(cW3 relu(cW2 relu(cW1 u + cb1) + cb2) + cb3), u = [W_beta(x), d] with d the
+ *     unit viewing direction r/|r|); kappa.
+ *   gs_param_count reports its size (not a multiple of 4: pad the arrays given to
+ *   gs_adam_step to one; the padding entries keep a zero gradient).
  */
 #ifndef GOSURF_H
 #define GOSURF_H
@@ -43,6 +56,8 @@ extern "C" {
 #define GS_NUM_LOSS 6      /* rgb, depth, sdf, fs, smooth, total */
 #define GS_PROP_BINS 32    /* bins of the learned proposal over [near_m, far_m] */
 #define GS_PROP_PARAMS 1473 /* proposal network: W1[32][11], b1[32], W2[32][32], b2[32], w3[32], b3 */
+#define GS_COLOUR_FEAT 6       /* colour features per vertex of the paper architecture's colour grid (h_c) */
+#define GS_PAPER_MLP_PARAMS 3109 /* decoder block of the paper architecture (layout above) */
 
 typedef enum {
   GS_OK = 0,
@@ -57,6 +72,15 @@ typedef enum {
 /* Arithmetic forms of the render pass (gs_config.precision): */
 #define GS_PREC_FP32 0 /* FP32 grid gathers; decoders on tensor cores with FP32-grade products */
 #define GS_PREC_BF16 1 /* gathers from the bfloat16 grid copy; decoders in BF16 with FP32 accumulation */
+
+/* Scene models (gs_config.arch): */
+#define GS_ARCH_COMPACT 0 /* geometry decoder 16-32-16 ([phi, 15 geometric features]), colour decoder
+                             15-32-3 fed the geometric features: the workload's model */
+#define GS_ARCH_PAPER 1   /* the paper's (Sec. 3.1): colour grid W_beta at the finest level, colour decoder
+                             fed W_beta(x) and the viewing direction, both decoders with two hidden layers
+                             of 32.  Supported by gs_sample_rays, gs_forward, gs_backward,
+                             gs_forward_backward and gs_adam_step (FP32, activations recomputed); the other
+                             model entry points return GS_ERR_UNSUPPORTED */
 
 /* Sample classes written by gs_sample_rays (Sec. 3.3): */
 #define GS_CLS_NONE 0 /* no SDF supervision (behind the surface, or the ray has no depth) */
@@ -93,6 +117,7 @@ typedef struct gs_config {
   int32_t imp_steps;          /* importance steps (Sec. 4: 3) */
   int32_t imp_per_step;       /* samples added per step, 1..32 (Sec. 4: 12); batches of this sampler
                                  hold imp_coarse + imp_steps * imp_per_step <= 160 samples per ray */
+  int32_t arch;               /* GS_ARCH_COMPACT or GS_ARCH_PAPER (the parameter layout follows it) */
 } gs_config;
 
 /* Posed RGB-D frames resident in device memory (Sec. 3: {I_t, D_t}, xi_t). */
@@ -134,8 +159,9 @@ typedef struct gs_ctx gs_ctx;
 gs_status gs_create(const gs_config* cfg, gs_ctx** out);
 void gs_destroy(gs_ctx* ctx);
 
-/* Host: number of floats in the flat parameter vector; *n_grid (may be NULL) receives the
- * number of grid floats that precede the decoder block. */
+/* Host: number of floats in the flat parameter vector of cfg->arch; *n_grid (may be NULL)
+ * receives the number of grid floats (geometry levels, and the padded colour grid of
+ * GS_ARCH_PAPER) that precede the decoder block. */
 int64_t gs_param_count(const gs_config* cfg, int64_t* n_grid);
 
 /* Ray batch sampling (Sec. 3.4 "we sample a batch of R rays from all pixels across all
@@ -169,7 +195,12 @@ gs_status gs_forward(gs_ctx* ctx, const float* theta, const uint16_t* theta_bf16
 gs_status gs_backward(gs_ctx* ctx, const float* theta, const uint16_t* theta_bf16, const gs_batch* batch,
                       const float* dloss, float* grad, void* stream);
 
-/* Forward and backward in one pass over the batch (loss and grad as above). */
+/* Forward and backward in one pass over the batch (loss and grad as above).
+ * With GS_ARCH_PAPER these three entry points evaluate the paper's architecture (layout at
+ * the top of this file): the same losses, batch normalisations and smoothness term with
+ * phi = f_omega(V_theta(x)) and c = g_gamma(W_beta(x), r/|r|), the gradient reaching the
+ * geometry grid, the colour grid and both decoders; FP32 only, the decoder activations are
+ * recomputed by the backward pass, batch->dz is not supported (GS_ERR_UNSUPPORTED). */
 gs_status gs_forward_backward(gs_ctx* ctx, const float* theta, const uint16_t* theta_bf16, const gs_batch* batch,
                               const float* dloss, float* loss, float* grad, void* stream);
 

@@ -12,11 +12,12 @@ from dataclasses import dataclass
 
 import torch
 
-from ._lib import (GS_FEAT, GS_LEVELS, GS_MLP_PARAMS, GS_NUM_LOSS, GS_PREC_BF16, GS_PREC_FP32, GS_PROP_BINS,
-                   GS_PROP_PARAMS, EXPORTS, GoSurfError,
+from ._lib import (GS_ARCH_COMPACT, GS_ARCH_PAPER, GS_FEAT, GS_LEVELS, GS_MLP_PARAMS, GS_NUM_LOSS,
+                   GS_PAPER_MLP_PARAMS, GS_PREC_BF16, GS_PREC_FP32, GS_PROP_BINS, GS_PROP_PARAMS, EXPORTS, GoSurfError,
                    GsBatch, GsConfig, GsFrames, lib, library_path)
 
 __all__ = ["Context", "Batch", "DeviceFrames", "GoSurfStep", "SdfGrad", "GoSurfError", "make_config", "GS_MLP_PARAMS", "GS_NUM_LOSS",
+           "GS_PAPER_MLP_PARAMS", "GS_ARCH_COMPACT", "GS_ARCH_PAPER",
            "library_path", "EXPORTS"]
 
 
@@ -43,6 +44,7 @@ def make_config(workload, max_rays=None, max_smooth=None, store_activations=Fals
     c.imp_coarse = int(getattr(workload, "imp_coarse", 0))
     c.imp_steps = int(getattr(workload, "imp_steps", 0))
     c.imp_per_step = int(getattr(workload, "imp_per_step", 0))
+    c.arch = GS_ARCH_PAPER if getattr(workload, "arch", "compact") == "paper" else GS_ARCH_COMPACT
     return c
 
 

@@ -14,6 +14,8 @@ _LOCK = threading.Lock()
 GS_LEVELS, GS_FEAT, GS_MLP_PARAMS, GS_NUM_LOSS = 4, 4, 1684, 6
 GS_PREC_FP32, GS_PREC_BF16 = 0, 1
 GS_PROP_BINS, GS_PROP_PARAMS = 32, 1473
+GS_ARCH_COMPACT, GS_ARCH_PAPER = 0, 1
+GS_COLOUR_FEAT, GS_PAPER_MLP_PARAMS = 6, 3109
 STATUS = {0: "GS_OK", 1: "GS_ERR_INVALID_ARG", 2: "GS_ERR_SHAPE", 3: "GS_ERR_ALIGN", 4: "GS_ERR_CUDA",
           5: "GS_ERR_DEVICE", 6: "GS_ERR_UNSUPPORTED"}
 
@@ -30,7 +32,7 @@ class GsConfig(ctypes.Structure):
                 ("max_smooth", ctypes.c_int32), ("delta_s", ctypes.c_float), ("precision", ctypes.c_int32),
                 ("store_activations", ctypes.c_int32), ("prop_samples", ctypes.c_int32),
                 ("prop_guided", ctypes.c_int32), ("imp_coarse", ctypes.c_int32), ("imp_steps", ctypes.c_int32),
-                ("imp_per_step", ctypes.c_int32)]
+                ("imp_per_step", ctypes.c_int32), ("arch", ctypes.c_int32)]
 
 
 class GsFrames(ctypes.Structure):

@@ -30,6 +30,18 @@ long long level_floats(const gs_config* c, int l) {
 
 int imp_samples(const gs_config* c) { return c->imp_coarse + c->imp_steps * c->imp_per_step; }
 
+// colour grid floats of the paper architecture: 6 per finest-level vertex, padded to a multiple of 4
+long long colour_floats(const gs_config* c) {
+  const long long n = (long long)c->dims[3][0] * c->dims[3][1] * c->dims[3][2] * GS_COLOUR_FEAT;
+  return (n + 3) / 4 * 4;
+}
+
+// model entry points that exist for the workload's decoders only
+gs_status compact_only(gs_ctx* ctx, const char* who) {
+  std::string m(who);
+  return fail(ctx, GS_ERR_UNSUPPORTED, (m + ": not available for GS_ARCH_PAPER").c_str());
+}
+
 gs_status check_batch(gs_ctx* ctx, const gs_batch* b, bool need_smooth_arrays) {
   if (!b) return fail(ctx, GS_ERR_INVALID_ARG, "batch is NULL");
   if (b->R < 0 || b->R > ctx->cfg.max_rays) return fail(ctx, GS_ERR_SHAPE, "batch R outside [0, max_rays]");
@@ -66,8 +78,9 @@ int64_t gs_param_count(const gs_config* cfg, int64_t* n_grid) {
   if (!cfg) return -1;
   long long g = 0;
   for (int l = 0; l < GS_LEVELS; ++l) g += level_floats(cfg, l);
+  if (cfg->arch == GS_ARCH_PAPER) g += colour_floats(cfg);
   if (n_grid) *n_grid = g;
-  return g + GS_MLP_PARAMS;
+  return g + (cfg->arch == GS_ARCH_PAPER ? GS_PAPER_MLP_PARAMS : GS_MLP_PARAMS);
 }
 
 gs_status gs_create(const gs_config* cfg, gs_ctx** out) {
@@ -96,6 +109,13 @@ gs_status gs_create(const gs_config* cfg, gs_ctx** out) {
       (cfg->prop_samples < 2 || cfg->prop_samples > GS_PROP_BINS || cfg->prop_guided < 0 ||
        cfg->prop_guided >= cfg->prop_samples))
     return fail(nullptr, GS_ERR_INVALID_ARG, "gs_create: need 2 <= prop_samples <= 32 and 0 <= prop_guided < prop_samples");
+  if (cfg->arch != GS_ARCH_COMPACT && cfg->arch != GS_ARCH_PAPER)
+    return fail(nullptr, GS_ERR_INVALID_ARG, "gs_create: arch must be GS_ARCH_COMPACT or GS_ARCH_PAPER");
+  if (cfg->arch == GS_ARCH_PAPER &&
+      (cfg->precision != GS_PREC_FP32 || cfg->store_activations || cfg->prop_samples || cfg->imp_coarse))
+    return fail(nullptr, GS_ERR_UNSUPPORTED,
+                "gs_create: GS_ARCH_PAPER runs in FP32 with recomputed activations, without the proposal or "
+                "importance samplers");
 
   gs_ctx* c = new (std::nothrow) gs_ctx();
   if (!c) return fail(nullptr, GS_ERR_INVALID_ARG, "gs_create: out of host memory");
@@ -115,6 +135,8 @@ gs_status gs_create(const gs_config* cfg, gs_ctx** out) {
     off += level_floats(cfg, l);
   }
   for (int a = 0; a < 3; ++a) g.origin[a] = cfg->origin[a];
+  c->colour_off = off;
+  if (cfg->arch == GS_ARCH_PAPER) off += colour_floats(cfg);
   g.n_grid = off;
   c->render_ctas = kRenderCtasPerSm * c->num_sms;
   c->n_parts = c->render_ctas + kSmoothCtas;
@@ -137,6 +159,9 @@ gs_status gs_create(const gs_config* cfg, gs_ctx** out) {
       cudaMemset(c->status, 0, sizeof(int)) != cudaSuccess ||
       (cfg->prop_samples > 0 &&
        cudaMalloc(&c->prop_part, sizeof(float) * gs_prop_part_floats(c->num_sms)) != cudaSuccess) ||
+      (cfg->arch == GS_ARCH_PAPER &&
+       (cudaMalloc(&c->paper_part, sizeof(float) * gs_paper_part_floats(c->num_sms)) != cudaSuccess ||
+        cudaMalloc(&c->paper_loss_part, sizeof(float) * kLossPad * gs_paper_part_rows(c->num_sms)) != cudaSuccess)) ||
       (cfg->store_activations &&
        cudaMalloc(&c->store, c->store_bytes = (size_t)cfg->max_rays * c->max_n * kStoreFloatsPerSample * sizeof(float)) !=
            cudaSuccess)) {
@@ -158,6 +183,8 @@ void gs_destroy(gs_ctx* ctx) {
   cudaFree(ctx->prop_part);
   cudaFree(ctx->eik_part);
   cudaFree(ctx->eik_ticket);
+  cudaFree(ctx->paper_part);
+  cudaFree(ctx->paper_loss_part);
   if (ctx->ev_fork) cudaEventDestroy(ctx->ev_fork);
   if (ctx->ev_join) cudaEventDestroy(ctx->ev_join);
   if (ctx->side) cudaStreamDestroy(ctx->side);
@@ -201,6 +228,12 @@ static gs_status render_common(gs_ctx* ctx, const char* who, const float* theta,
   cudaStream_t st = (cudaStream_t)stream;
   ctx->last_stream = st;
   const float* dl = dloss ? dloss : ctx->default_dloss;
+  if (ctx->cfg.arch == GS_ARCH_PAPER) {
+    if (batch->dz) return fail(ctx, GS_ERR_UNSUPPORTED, "batch dz is not written for GS_ARCH_PAPER");
+    if (gs_launch_paper(ctx, theta, batch, dl, grad, loss, rgb_hat, d_hat, wsum, mode, st) != GS_OK)
+      return cuda_fail(ctx, who);
+    return GS_OK;
+  }
   // The smoothness kernel is independent of the render kernel (its own partial rows, atomics
   // into grad).  On a side stream that forks from the calling stream before the render launch,
   // and launched after it, it runs on the SMs that the render kernel's last ray-quads leave
@@ -280,6 +313,7 @@ gs_status gs_adam_step(gs_ctx* ctx, float* theta, float* grad, float* m, float* 
 gs_status gs_query_sdf(gs_ctx* ctx, const float* theta, const float* x, int32_t P, float* sdf, float* grad,
                        void* stream) {
   if (!ctx) return fail(nullptr, GS_ERR_INVALID_ARG, "gs_query_sdf: ctx is NULL");
+  if (ctx->cfg.arch != GS_ARCH_COMPACT) return compact_only(ctx, "gs_query_sdf");
   if (P < 0) return fail(ctx, GS_ERR_SHAPE, "gs_query_sdf: P < 0");
   if (P > 0 && (!theta || !x || !sdf)) return fail(ctx, GS_ERR_INVALID_ARG, "gs_query_sdf: NULL array");
   if (P > 0 && !aligned16(theta)) return fail(ctx, GS_ERR_ALIGN, "gs_query_sdf: theta is not 16-byte aligned");
@@ -344,6 +378,7 @@ gs_status gs_proposal_backward(gs_ctx* ctx, const float* theta, const float* pro
 gs_status gs_query_sdf_backward(gs_ctx* ctx, const float* theta, const float* x, int32_t P, const float* dsdf,
                                 const float* dgrad, float* grad, void* stream) {
   if (!ctx) return fail(nullptr, GS_ERR_INVALID_ARG, "gs_query_sdf_backward: ctx is NULL");
+  if (ctx->cfg.arch != GS_ARCH_COMPACT) return compact_only(ctx, "gs_query_sdf_backward");
   if (P < 0) return fail(ctx, GS_ERR_SHAPE, "gs_query_sdf_backward: P < 0");
   if (P > 0 && (!theta || !x || !grad)) return fail(ctx, GS_ERR_INVALID_ARG, "gs_query_sdf_backward: NULL array");
   if (P > 0 && (!aligned16(theta) || !aligned16(grad)))
@@ -358,6 +393,7 @@ gs_status gs_query_sdf_backward(gs_ctx* ctx, const float* theta, const float* x,
 gs_status gs_eikonal(gs_ctx* ctx, const float* theta, const gs_batch* batch, const float* dloss, float* loss,
                      float* grad, void* stream) {
   if (!ctx) return fail(nullptr, GS_ERR_INVALID_ARG, "gs_eikonal: ctx is NULL");
+  if (ctx->cfg.arch != GS_ARCH_COMPACT) return compact_only(ctx, "gs_eikonal");
   if (!theta) return fail(ctx, GS_ERR_INVALID_ARG, "gs_eikonal: theta is NULL");
   if (!loss && !grad) return fail(ctx, GS_ERR_INVALID_ARG, "gs_eikonal: loss and grad are both NULL");
   if (!aligned16(theta) || (grad && !aligned16(grad)))
@@ -384,6 +420,7 @@ gs_status gs_pose_apply(gs_ctx* ctx, const float* c2w0, const float* xi, int32_t
 gs_status gs_pose_backward(gs_ctx* ctx, const float* theta, const gs_frames* frames, const float* xi,
                            const gs_batch* batch, float* pose_grad, void* stream) {
   if (!ctx) return fail(nullptr, GS_ERR_INVALID_ARG, "gs_pose_backward: ctx is NULL");
+  if (ctx->cfg.arch != GS_ARCH_COMPACT) return compact_only(ctx, "gs_pose_backward");
   gs_status s = check_frames(ctx, frames, "gs_pose_backward");
   if (s != GS_OK) return s;
   s = check_batch(ctx, batch, true);
@@ -403,6 +440,7 @@ gs_status gs_extract_mesh(gs_ctx* ctx, const float* theta, const float* lo, floa
                           int32_t nz, float iso, float* phi, float* tris, int64_t max_tris, int64_t* n_tris,
                           void* stream) {
   if (!ctx) return fail(nullptr, GS_ERR_INVALID_ARG, "gs_extract_mesh: ctx is NULL");
+  if (ctx->cfg.arch != GS_ARCH_COMPACT) return compact_only(ctx, "gs_extract_mesh");
   if (!theta || !lo || !phi || !n_tris) return fail(ctx, GS_ERR_INVALID_ARG, "gs_extract_mesh: NULL argument");
   if (max_tris < 0 || (max_tris > 0 && !tris)) return fail(ctx, GS_ERR_INVALID_ARG, "gs_extract_mesh: bad tris / max_tris");
   if (nx < 2 || ny < 2 || nz < 2 || !(step > 0.0f)) return fail(ctx, GS_ERR_SHAPE, "gs_extract_mesh: need nx, ny, nz >= 2 and step > 0");

@@ -35,6 +35,9 @@ struct gs_ctx {
   int eik_ctas = 0;                  // largest grid of the Eikonal kernel
   float* eik_part = nullptr;         // its per-CTA loss sums
   unsigned* eik_ticket = nullptr;    // CTAs finished in the running call (0 between calls)
+  long long colour_off = 0;          // paper architecture: float offset of the colour grid
+  float* paper_part = nullptr;       // paper architecture: per-CTA decoder-gradient partial rows
+  float* paper_loss_part = nullptr;  // and loss partial rows
   cudaStream_t last_stream = nullptr;
   cudaStream_t side = nullptr;       // the smoothness kernel runs here beside the render kernel
   cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
@@ -79,3 +82,7 @@ gs_status gs_launch_query(const gs_ctx* ctx, const float* theta, const float* x,
                           cudaStream_t st);
 gs_status gs_launch_voxel_index(const gs_ctx* ctx, const float* x, int P, long long* out, cudaStream_t st);
 void gs_set_thread_error(const char* msg);
+int gs_paper_part_rows(int num_sms);
+size_t gs_paper_part_floats(int num_sms);
+gs_status gs_launch_paper(const gs_ctx* ctx, const float* theta, const gs_batch* b, const float* dloss, float* grad,
+                          float* loss, float* rgb_hat, float* d_hat, float* wsum, int mode, cudaStream_t st);

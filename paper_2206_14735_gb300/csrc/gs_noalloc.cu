@@ -60,6 +60,8 @@ extern "C" gs_status gs_forward_backward_noalloc(const gs_config* cfg, const flo
   }
   if (cfg->precision != GS_PREC_FP32)
     return noalloc_fail(GS_ERR_UNSUPPORTED, "gs_forward_backward_noalloc: FP32 form only");
+  if (cfg->arch != GS_ARCH_COMPACT)
+    return noalloc_fail(GS_ERR_UNSUPPORTED, "gs_forward_backward_noalloc: GS_ARCH_COMPACT only");
   const int N = cfg->n_strat + cfg->n_guided;
   if (cfg->n_strat < 1 || cfg->n_guided < 0 || N < 2 || N > GS_MAX_SAMPLES)
     return noalloc_fail(GS_ERR_SHAPE, "gs_forward_backward_noalloc: samples per ray must be in [2, 160]");

@@ -1,0 +1,956 @@
+// The paper's architecture (Sec. 3.1 Eq. SDF_MLP and Eq. COLOR_MLP, "Architecture Details"):
+// geometry features V_theta(x) from the four grid levels, colour features W_beta(x) (h_c = 6)
+// from a separate grid on the finest level's vertices, phi = f_omega(V_theta(x)) and
+// c = g_gamma(W_beta(x), d) with d the unit viewing direction, both decoders with two hidden
+// layers of 32.  Rendering, losses and the smoothness term are those of the workload's model.
+//
+// Kernels (FP32 on CUDA cores):
+//   paper_render_kernel  one warp per ray, one lane per sample of a 32-sample chunk: gathers,
+//                        both decoders, NeuS compositing and losses; then the compositing
+//                        adjoint, and per chunk the recomputed decoders' adjoints, the weight
+//                        gradients (warp-level products over the chunk's 32 samples staged in
+//                        shared memory) and the scatter into both grids;
+//   paper_smooth_kernel  the smoothness term on S_g and its second-order adjoint, one lane per
+//                        evaluation (x or x + eps of 16 points per warp);
+//   paper_combine_kernel per-CTA partial rows combined in a fixed order (losses in FP64).
+#include "gs_internal.h"
+
+namespace gs {
+namespace paper {
+
+constexpr int kH = 32;              // neurons per hidden layer
+constexpr int kC = GS_COLOUR_FEAT;  // colour features
+constexpr int kU = kC + 3;          // colour decoder input [W_beta(x), d]
+
+// decoder block offsets in the flat parameter vector (header layout)
+constexpr int A_gW1 = 0, A_gb1 = A_gW1 + kH * kZ, A_gW2 = A_gb1 + kH, A_gb2 = A_gW2 + kH * kH, A_gw3 = A_gb2 + kH,
+              A_gb3 = A_gw3 + kH, A_cW1 = A_gb3 + 1, A_cb1 = A_cW1 + kH * kU, A_cW2 = A_cb1 + kH,
+              A_cb2 = A_cW2 + kH * kH, A_cW3 = A_cb2 + kH, A_cb3 = A_cW3 + 3 * kH, A_kappa = A_cb3 + 3;
+static_assert(A_kappa + 1 == GS_PAPER_MLP_PARAMS, "paper decoder layout");
+
+// shared-memory copy: the matrices whose rows are read as float4 (gW1, gW2, gw3, cW2, cW3)
+// start on 16-byte boundaries
+constexpr int S_gW1 = 0, S_gb1 = 512, S_gW2 = 544, S_gb2 = 1568, S_gw3 = 1600, S_gb3 = 1632, S_cW1 = 1636,
+              S_cb1 = 1924, S_cW2 = 1956, S_cb2 = 2980, S_cW3 = 3012, S_cb3 = 3108, S_kappa = 3111, kSm = 3112;
+static_assert(S_gW2 % 4 == 0 && S_gw3 % 4 == 0 && S_cW2 % 4 == 0 && S_cW3 % 4 == 0, "float4 rows");
+constexpr int kPart = 3112;  // per-CTA decoder-gradient partial row (>= GS_PAPER_MLP_PARAMS)
+
+// One block of the decoder: its range in the flat vector, its start in shared memory, and
+// (matrices with 32 rows) its column count.  The gradient accumulators of those matrices
+// are kept transposed in shared memory (entry (j, k) at k * 32 + j) so that lane j, which
+// sums row j, touches bank j.
+struct Block {
+  int a, n, s, cols;
+};
+__constant__ Block kBlocks[13] = {{A_gW1, 512, S_gW1, kZ}, {A_gb1, 32, S_gb1, 0},  {A_gW2, 1024, S_gW2, kH},
+                                  {A_gb2, 32, S_gb2, 0},   {A_gw3, 32, S_gw3, 0},  {A_gb3, 1, S_gb3, 0},
+                                  {A_cW1, 288, S_cW1, kU}, {A_cb1, 32, S_cb1, 0},  {A_cW2, 1024, S_cW2, kH},
+                                  {A_cb2, 32, S_cb2, 0},   {A_cW3, 96, S_cW3, 0},  {A_cb3, 3, S_cb3, 0},
+                                  {A_kappa, 1, S_kappa, 0}};
+
+__device__ __forceinline__ void copy_decoder(const float* __restrict__ mlp, float* sW) {
+  for (int i = threadIdx.x; i < kSm; i += blockDim.x) sW[i] = 0.f;
+  __syncthreads();
+  for (int b = 0; b < 13; ++b)
+    for (int i = threadIdx.x; i < kBlocks[b].n; i += blockDim.x) sW[kBlocks[b].s + i] = mlp[kBlocks[b].a + i];
+}
+
+// shared accumulator index of flat decoder entry i (inverse of the transposed storage)
+__device__ __forceinline__ int acc_index(int i) {
+  for (int b = 0; b < 13; ++b) {
+    const Block k = kBlocks[b];
+    if (i >= k.a && i < k.a + k.n) {
+      const int r = i - k.a;
+      return k.cols ? k.s + (r % k.cols) * 32 + r / k.cols : k.s + r;
+    }
+  }
+  return -1;
+}
+
+// per-lane row of staged sample vectors (odd stride: lane-own rows are conflict-free)
+constexpr int kRow = 161;
+constexpr int fZ = 0, fU = 16, fA1 = 25, fA2 = 57, fR1 = 89, fR2 = 121, fDP = 153, fDPHI = 156;
+constexpr int kWarps = 4;  // warps per CTA
+constexpr int kThreads = kWarps * 32;
+constexpr size_t kSmemBytes = sizeof(float) * (2 * kSm + 8 + kWarps * 32 * kRow);
+constexpr int kCtasPerSm = 2;
+
+struct Args {
+  GridDesc g;            // geometry levels; g.n_grid = decoder block offset (after the colour grid)
+  long long colour_off;  // float offset of the colour grid
+  const float* theta;
+  float* grad;
+  const float *o, *r, *rgb, *D, *t;
+  const uint8_t* cls;
+  const float *xs, *eps;
+  const uint8_t* valid;
+  const int* counts;
+  const float* dloss;
+  float *rgb_hat, *d_hat, *wsum, *w_out;
+  float *loss_part, *mlp_part;  // this kernel's first partial row
+  int R, N, P, mode;
+  float lam[5];
+  float kappa_fs;
+};
+
+// lane j (row j of a 32-row matrix) sums delta_s[j] * act_s[k] over the warp's 32 staged
+// samples for k < K (and delta_s[j] for the bias) and adds them to the CTA accumulators
+template <int K, bool kBias>
+__device__ __forceinline__ void outer_rows(const float* wr, int fd, int fa, float* acc_m, float* acc_b, int lane) {
+  float acc[K];
+#pragma unroll
+  for (int k = 0; k < K; ++k) acc[k] = 0.f;
+  float ab = 0.f;
+#pragma unroll 2
+  for (int s = 0; s < 32; ++s) {
+    const float* rs = wr + s * kRow;
+    const float d = rs[fd + lane];
+    ab += d;
+#pragma unroll
+    for (int k = 0; k < K; ++k) acc[k] = fmaf(d, rs[fa + k], acc[k]);
+  }
+#pragma unroll
+  for (int k = 0; k < K; ++k) atomicAdd(acc_m + k * 32 + lane, acc[k]);
+  if (kBias) atomicAdd(acc_b + lane, ab);
+}
+
+__device__ __forceinline__ float4 ld4(const float* p) { return *reinterpret_cast<const float4*>(p); }
+
+// geometry features z (4 levels x 4) and colour features cf (level-3 cell, 6) at x
+__device__ __forceinline__ void gather(const Args& a, const float x[3], float z[kZ], float cf[kC]) {
+#pragma unroll
+  for (int l = 0; l < kLevels; ++l) {
+    const Cell c = locate(a.g, l, x);
+    float w[8];
+    corner_weights(c.f, w);
+    const float4* lv = reinterpret_cast<const float4*>(a.theta + a.g.off[l]);
+    float4 acc = make_float4(0.f, 0.f, 0.f, 0.f);
+#pragma unroll
+    for (int k = 0; k < 8; ++k) f4fma(acc, w[k], __ldg(lv + c.vtx + corner_offset(a.g, l, k)));
+    z[4 * l] = acc.x;
+    z[4 * l + 1] = acc.y;
+    z[4 * l + 2] = acc.z;
+    z[4 * l + 3] = acc.w;
+    if (l == kLevels - 1) {
+#pragma unroll
+      for (int q = 0; q < kC; ++q) cf[q] = 0.f;
+      const float2* cg = reinterpret_cast<const float2*>(a.theta + a.colour_off);
+#pragma unroll
+      for (int k = 0; k < 8; ++k) {
+        const long long v2 = (c.vtx + corner_offset(a.g, l, k)) * 3;  // 3 float2 per vertex
+#pragma unroll
+        for (int q = 0; q < 3; ++q) {
+          const float2 f = __ldg(cg + v2 + q);
+          cf[2 * q] = fmaf(w[k], f.x, cf[2 * q]);
+          cf[2 * q + 1] = fmaf(w[k], f.y, cf[2 * q + 1]);
+        }
+      }
+    }
+  }
+}
+
+// both decoders at one sample; with row != nullptr the inputs and hidden activations are
+// staged there (z, u, a1, a2, r1, r2) for the backward pass
+__device__ __forceinline__ void decode(const float* sW, const float z[kZ], const float u[kU], float* row, float& phi,
+                                       float col[3]) {
+  float h[kH];
+#pragma unroll
+  for (int j = 0; j < kH; ++j) {
+    float y = sW[S_gb1 + j];
+#pragma unroll
+    for (int k4 = 0; k4 < 4; ++k4) {
+      const float4 w = ld4(sW + S_gW1 + j * kZ + 4 * k4);
+      y = fmaf(w.x, z[4 * k4], y);
+      y = fmaf(w.y, z[4 * k4 + 1], y);
+      y = fmaf(w.z, z[4 * k4 + 2], y);
+      y = fmaf(w.w, z[4 * k4 + 3], y);
+    }
+    h[j] = fmaxf(y, 0.f);
+  }
+  float p = sW[S_gb3];
+#pragma unroll 4
+  for (int j = 0; j < kH; ++j) {
+    float y = sW[S_gb2 + j];
+#pragma unroll
+    for (int k4 = 0; k4 < 8; ++k4) {
+      const float4 w = ld4(sW + S_gW2 + j * kH + 4 * k4);
+      y = fmaf(w.x, h[4 * k4], y);
+      y = fmaf(w.y, h[4 * k4 + 1], y);
+      y = fmaf(w.z, h[4 * k4 + 2], y);
+      y = fmaf(w.w, h[4 * k4 + 3], y);
+    }
+    y = fmaxf(y, 0.f);
+    if (row) row[fA2 + j] = y;
+    p = fmaf(sW[S_gw3 + j], y, p);
+  }
+  phi = p;
+  if (row) {
+#pragma unroll
+    for (int k = 0; k < kZ; ++k) row[fZ + k] = z[k];
+#pragma unroll
+    for (int j = 0; j < kH; ++j) row[fA1 + j] = h[j];
+#pragma unroll
+    for (int k = 0; k < kU; ++k) row[fU + k] = u[k];
+  }
+#pragma unroll
+  for (int j = 0; j < kH; ++j) {
+    float y = sW[S_cb1 + j];
+#pragma unroll
+    for (int k = 0; k < kU; ++k) y = fmaf(sW[S_cW1 + j * kU + k], u[k], y);
+    h[j] = fmaxf(y, 0.f);
+  }
+  float pre[3] = {sW[S_cb3], sW[S_cb3 + 1], sW[S_cb3 + 2]};
+#pragma unroll 4
+  for (int j = 0; j < kH; ++j) {
+    float y = sW[S_cb2 + j];
+#pragma unroll
+    for (int k4 = 0; k4 < 8; ++k4) {
+      const float4 w = ld4(sW + S_cW2 + j * kH + 4 * k4);
+      y = fmaf(w.x, h[4 * k4], y);
+      y = fmaf(w.y, h[4 * k4 + 1], y);
+      y = fmaf(w.z, h[4 * k4 + 2], y);
+      y = fmaf(w.w, h[4 * k4 + 3], y);
+    }
+    y = fmaxf(y, 0.f);
+    if (row) row[fR2 + j] = y;
+#pragma unroll
+    for (int i = 0; i < 3; ++i) pre[i] = fmaf(sW[S_cW3 + i * kH + j], y, pre[i]);
+  }
+  if (row) {
+#pragma unroll
+    for (int j = 0; j < kH; ++j) row[fR1 + j] = h[j];
+  }
+#pragma unroll
+  for (int i = 0; i < 3; ++i) col[i] = sigmoidf_(pre[i]);
+}
+
+// grid-gradient scatter of one sample: dz into the 4 geometry levels, dcf into the colour grid
+__device__ __forceinline__ void scatter(const Args& a, const float x[3], const float dz[kZ], const float dcf[kC]) {
+#pragma unroll
+  for (int l = 0; l < kLevels; ++l) {
+    const Cell c = locate(a.g, l, x);
+    float w[8];
+    corner_weights(c.f, w);
+    float4* gl = reinterpret_cast<float4*>(a.grad + a.g.off[l]);
+    const float4 d = make_float4(dz[4 * l], dz[4 * l + 1], dz[4 * l + 2], dz[4 * l + 3]);
+#pragma unroll
+    for (int k = 0; k < 8; ++k) atomicAdd(gl + c.vtx + corner_offset(a.g, l, k), f4scale(d, w[k]));
+    if (l == kLevels - 1) {
+      float2* cg = reinterpret_cast<float2*>(a.grad + a.colour_off);
+#pragma unroll
+      for (int k = 0; k < 8; ++k) {
+        const long long v2 = (c.vtx + corner_offset(a.g, l, k)) * 3;
+#pragma unroll
+        for (int q = 0; q < 3; ++q) atomicAdd(cg + v2 + q, make_float2(w[k] * dcf[2 * q], w[k] * dcf[2 * q + 1]));
+      }
+    }
+  }
+}
+
+__device__ __forceinline__ void write_partials(const Args& a, const float* sG, const float* sL) {
+  float* row = a.mlp_part + (size_t)blockIdx.x * kPart;
+  for (int i = threadIdx.x; i < kPart; i += blockDim.x) row[i] = i < GS_PAPER_MLP_PARAMS ? sG[acc_index(i)] : 0.f;
+  if (threadIdx.x < kLossPad) a.loss_part[(size_t)blockIdx.x * kLossPad + threadIdx.x] = sL[threadIdx.x];
+}
+
+template <int NCH>
+__global__ void __launch_bounds__(kThreads, kCtasPerSm) paper_render_kernel(Args a) {
+  extern __shared__ __align__(16) float smem[];
+  float* sW = smem;
+  float* sG = sW + kSm;
+  float* sL = sG + kSm;
+  float* rows = sL + 8;
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  float* wr = rows + wid * 32 * kRow;
+  float* my = wr + lane * kRow;
+  copy_decoder(a.theta + a.g.n_grid, sW);
+  for (int i = threadIdx.x; i < kSm; i += blockDim.x) sG[i] = 0.f;
+  if (threadIdx.x < 8) sL[threadIdx.x] = 0.f;
+  __syncthreads();
+  const bool bwd = (a.mode & 2) != 0;
+  const float s = expf(sW[S_kappa]);
+  float wt[5];
+#pragma unroll
+  for (int k = 0; k < 5; ++k) wt[k] = a.dloss[k] + a.lam[k] * a.dloss[5];
+  const int n_d = a.counts[0], n_tr = a.counts[1], n_fs = a.counts[2];
+  const int N = a.N;
+  float lsum[5] = {0.f, 0.f, 0.f, 0.f, 0.f};
+  float gkappa = 0.f;
+
+  for (int ray = blockIdx.x * kWarps + wid; ray < a.R; ray += gridDim.x * kWarps) {
+    float o[3], r[3], I[3], d[3];
+#pragma unroll
+    for (int q = 0; q < 3; ++q) {
+      o[q] = a.o[3 * ray + q];
+      r[q] = a.r[3 * ray + q];
+      I[q] = a.rgb[3 * ray + q];
+    }
+    const float D = a.D[ray];
+    const float rn = sqrtf(r[0] * r[0] + r[1] * r[1] + r[2] * r[2]);
+#pragma unroll
+    for (int q = 0; q < 3; ++q) d[q] = r[q] / rn;
+    float tk[NCH], phi[NCH], col[NCH][3];
+    int cl[NCH];
+#pragma unroll
+    for (int c = 0; c < NCH; ++c) {
+      const int k = 32 * c + lane;
+      tk[c] = k < N ? a.t[(size_t)ray * N + k] : 0.f;
+      cl[c] = k < N ? a.cls[(size_t)ray * N + k] : CLS_NONE;
+    }
+    // one decoder body for all chunks (rolled loop; per-chunk registers picked by unrolled selects)
+#pragma unroll 1
+    for (int c = 0; c < NCH; ++c) {
+      const bool ok = 32 * c + lane < N;
+      float tc = tk[0];
+#pragma unroll
+      for (int q = 1; q < NCH; ++q)
+        if (c == q) tc = tk[q];
+      float z[kZ], u[kU];
+      if (ok) {
+        float x[3];
+        sample_pos(o, r, tc, x);
+        gather(a, x, z, u);
+      } else {
+#pragma unroll
+        for (int q = 0; q < kZ; ++q) z[q] = 0.f;
+#pragma unroll
+        for (int q = 0; q < kC; ++q) u[q] = 0.f;
+      }
+#pragma unroll
+      for (int q = 0; q < 3; ++q) u[kC + q] = d[q];
+      float ph, cc[3];
+      decode(sW, z, u, nullptr, ph, cc);
+#pragma unroll
+      for (int q = 0; q < NCH; ++q)
+        if (c == q) {
+          phi[q] = ph;
+          col[q][0] = cc[0];
+          col[q][1] = cc[1];
+          col[q][2] = cc[2];
+        }
+    }
+    // NeuS opacities, transmittance, weights (Sec. 3.2 Eq. volume_rendering_alpha)
+    float Phi[NCH], PhiN[NCH], alpha[NCH], T[NCH], w[NCH];
+#pragma unroll
+    for (int c = 0; c < NCH; ++c) Phi[c] = sigmoidf_(s * phi[c]);
+#pragma unroll
+    for (int c = 0; c < NCH; ++c) {
+      float nx = __shfl_down_sync(0xffffffffu, Phi[c], 1);
+      const float first_next = c + 1 < NCH ? __shfl_sync(0xffffffffu, Phi[c + 1 < NCH ? c + 1 : c], 0) : 0.f;
+      if (lane == 31) nx = first_next;
+      PhiN[c] = nx;
+      const float q = (Phi[c] - nx) / fmaxf(Phi[c], 1e-6f);
+      alpha[c] = (32 * c + lane < N - 1) ? fmaxf(q, 0.f) : 0.f;
+    }
+    float carry = 1.f;
+#pragma unroll
+    for (int c = 0; c < NCH; ++c) {
+      float incl = 1.f - alpha[c];
+#pragma unroll
+      for (int off = 1; off < 32; off <<= 1) {
+        const float v = __shfl_up_sync(0xffffffffu, incl, off);
+        if (lane >= off) incl *= v;
+      }
+      float excl = __shfl_up_sync(0xffffffffu, incl, 1);
+      if (lane == 0) excl = 1.f;
+      T[c] = carry * excl;
+      w[c] = T[c] * alpha[c];
+      carry *= __shfl_sync(0xffffffffu, incl, 31);
+    }
+    float ch[3] = {0.f, 0.f, 0.f}, dh = 0.f, ws = 0.f;
+#pragma unroll
+    for (int c = 0; c < NCH; ++c) {
+#pragma unroll
+      for (int q = 0; q < 3; ++q) ch[q] = fmaf(w[c], col[c][q], ch[q]);
+      dh = fmaf(w[c], tk[c], dh);
+      ws += w[c];
+      if (a.w_out && 32 * c + lane < N) a.w_out[(size_t)ray * N + 32 * c + lane] = w[c];
+    }
+#pragma unroll
+    for (int q = 0; q < 3; ++q) ch[q] = warp_sum(ch[q]);
+    dh = warp_sum(dh);
+    ws = warp_sum(ws);
+    if (lane == 0) {
+      if (a.rgb_hat)
+#pragma unroll
+        for (int q = 0; q < 3; ++q) a.rgb_hat[3 * ray + q] = ch[q];
+      if (a.d_hat) a.d_hat[ray] = dh;
+      if (a.wsum) a.wsum[ray] = ws;
+      float e2 = 0.f;
+#pragma unroll
+      for (int q = 0; q < 3; ++q) e2 = fmaf(I[q] - ch[q], I[q] - ch[q], e2);
+      lsum[0] += e2;
+      if (D > 0.f) lsum[1] += fabsf(D - dh);
+    }
+    // approximate SDF supervision (Sec. 3.3)
+#pragma unroll
+    for (int c = 0; c < NCH; ++c) {
+      const float b = D - tk[c];
+      if (cl[c] == CLS_TR) lsum[2] += fabsf(phi[c] - b);
+      else if (cl[c] == CLS_FS) lsum[3] += fmaxf(fmaxf(0.f, expf(-a.kappa_fs * phi[c]) - 1.f), phi[c] - b);
+    }
+    if (!bwd) continue;
+
+    // ---------------- compositing adjoint ----------------
+    float gc[3], gd = 0.f;
+#pragma unroll
+    for (int q = 0; q < 3; ++q) gc[q] = wt[0] / (float)a.R * 2.f * (ch[q] - I[q]);
+    if (D > 0.f && n_d > 0) gd = wt[1] / (float)n_d * (dh > D ? 1.f : (dh < D ? -1.f : 0.f));
+    float e[NCH], U[NCH];
+#pragma unroll
+    for (int c = 0; c < NCH; ++c) e[c] = gc[0] * col[c][0] + gc[1] * col[c][1] + gc[2] * col[c][2] + gd * tk[c];
+    // U_{k-1} = alpha_k e_k + (1 - alpha_k) U_k from U_{N-1} = 0: a suffix scan of affine maps
+    float Unext = 0.f;
+#pragma unroll
+    for (int c = NCH - 1; c >= 0; --c) {
+      float A = 1.f - alpha[c], B = alpha[c] * e[c];
+#pragma unroll
+      for (int off = 1; off < 32; off <<= 1) {
+        const float Ah = __shfl_down_sync(0xffffffffu, A, off), Bh = __shfl_down_sync(0xffffffffu, B, off);
+        if (lane + off < 32) {
+          B = fmaf(A, Bh, B);
+          A *= Ah;
+        }
+      }
+      const float Uprev = fmaf(A, Unext, B);
+      float Uk = __shfl_down_sync(0xffffffffu, Uprev, 1);
+      if (lane == 31) Uk = Unext;
+      U[c] = Uk;
+      Unext = __shfl_sync(0xffffffffu, Uprev, 0);
+    }
+    float dphi[NCH];
+    float to_next_carry = 0.f;
+#pragma unroll
+    for (int c = 0; c < NCH; ++c) {
+      const int k = 32 * c + lane;
+      float own = 0.f, to_next = 0.f;
+      if (k < N - 1 && alpha[c] > 0.f) {
+        const float dalpha = T[c] * (e[c] - U[c]);
+        const float den = fmaxf(Phi[c], 1e-6f);
+        to_next = -dalpha / den;
+        own = Phi[c] > 1e-6f ? dalpha * (PhiN[c] / (Phi[c] * Phi[c])) : dalpha * 1e6f;
+      }
+      float from_prev = __shfl_up_sync(0xffffffffu, to_next, 1);
+      if (lane == 0) from_prev = to_next_carry;
+      to_next_carry = __shfl_sync(0xffffffffu, to_next, 31);
+      const float dPhi = own + from_prev;
+      const float dsig = Phi[c] * (1.f - Phi[c]);
+      float g = dPhi * s * dsig;
+      gkappa = fmaf(dPhi * dsig * s, phi[c], gkappa);
+      const float b = D - tk[c];
+      if (cl[c] == CLS_TR && n_tr > 0) g += wt[2] / (float)n_tr * (phi[c] > b ? 1.f : (phi[c] < b ? -1.f : 0.f));
+      if (cl[c] == CLS_FS && n_fs > 0) {
+        const float ex = expf(-a.kappa_fs * phi[c]) - 1.f, lin = phi[c] - b;
+        int arg = 0;
+        float top = 0.f;
+        if (ex > top) {
+          top = ex;
+          arg = 1;
+        }
+        if (lin > top) arg = 2;
+        g += wt[3] / (float)n_fs * (arg == 1 ? -a.kappa_fs * (ex + 1.f) : (arg == 2 ? 1.f : 0.f));
+      }
+      dphi[c] = k < N ? g : 0.f;
+    }
+
+    // ---------------- decoder adjoints and scatter, chunk by chunk ----------------
+#pragma unroll 1
+    for (int c = 0; c < NCH; ++c) {
+      const int k = 32 * c + lane;
+      const bool ok = k < N;
+      float tc = tk[0], wc = w[0], dp = dphi[0];
+#pragma unroll
+      for (int q = 1; q < NCH; ++q)
+        if (c == q) {
+          tc = tk[q];
+          wc = w[q];
+          dp = dphi[q];
+        }
+      float x[3], z[kZ], u[kU];
+      __syncwarp();  // the previous chunk's products have read every row
+      if (ok) {
+        sample_pos(o, r, tc, x);
+        gather(a, x, z, u);
+      } else {
+#pragma unroll
+        for (int q = 0; q < kZ; ++q) z[q] = 0.f;
+#pragma unroll
+        for (int q = 0; q < kC; ++q) u[q] = 0.f;
+      }
+#pragma unroll
+      for (int q = 0; q < 3; ++q) u[kC + q] = d[q];
+      float ph, cc[3];
+      decode(sW, z, u, my, ph, cc);
+      float dpre[3];
+#pragma unroll
+      for (int q = 0; q < 3; ++q) dpre[q] = ok ? wc * gc[q] * cc[q] * (1.f - cc[q]) : 0.f;
+      my[fDP] = dpre[0];
+      my[fDP + 1] = dpre[1];
+      my[fDP + 2] = dpre[2];
+      my[fDPHI] = dp;
+      __syncwarp();
+      {  // output layers: gw3, gb3 (lane = column), cW3, cb3
+        float ag = 0.f, a0 = 0.f, a1 = 0.f, a2 = 0.f, bg = 0.f, bc = 0.f;
+        const int lq = lane < 3 ? lane : 2;
+#pragma unroll 4
+        for (int sidx = 0; sidx < 32; ++sidx) {
+          const float* rs = wr + sidx * kRow;
+          const float dph = rs[fDPHI], r2 = rs[fR2 + lane];
+          ag = fmaf(dph, rs[fA2 + lane], ag);
+          a0 = fmaf(rs[fDP], r2, a0);
+          a1 = fmaf(rs[fDP + 1], r2, a1);
+          a2 = fmaf(rs[fDP + 2], r2, a2);
+          bg += dph;
+          bc += rs[fDP + lq];
+        }
+        atomicAdd(sG + S_gw3 + lane, ag);
+        atomicAdd(sG + S_cW3 + lane, a0);
+        atomicAdd(sG + S_cW3 + kH + lane, a1);
+        atomicAdd(sG + S_cW3 + 2 * kH + lane, a2);
+        if (lane == 0) atomicAdd(sG + S_gb3, bg);
+        if (lane < 3) atomicAdd(sG + S_cb3 + lane, bc);
+      }
+      __syncwarp();
+      // own sample: dy2 = m2 (.) gw3 dphi over a2; dq2 = m(q2) (.) cW3^T dpre over r2
+#pragma unroll
+      for (int j = 0; j < kH; ++j) {
+        const float a2v = my[fA2 + j];
+        my[fA2 + j] = a2v > 0.f ? sW[S_gw3 + j] * dp : 0.f;
+        const float r2v = my[fR2 + j];
+        const float v = sW[S_cW3 + j] * dpre[0] + sW[S_cW3 + kH + j] * dpre[1] + sW[S_cW3 + 2 * kH + j] * dpre[2];
+        my[fR2 + j] = r2v > 0.f ? v : 0.f;
+      }
+      __syncwarp();
+      outer_rows<kH, true>(wr, fA2, fA1, sG + S_gW2, sG + S_gb2, lane);
+      outer_rows<kH, true>(wr, fR2, fR1, sG + S_cW2, sG + S_cb2, lane);
+      __syncwarp();
+      {  // own sample: dy1 = m1 (.) gW2^T dy2 over a1; dq1 = m(q1) (.) cW2^T dq2 over r1
+        float acc[kH];
+#pragma unroll
+        for (int q = 0; q < kH; ++q) acc[q] = 0.f;
+#pragma unroll 4
+        for (int j = 0; j < kH; ++j) {
+          const float dy = my[fA2 + j];
+#pragma unroll
+          for (int k4 = 0; k4 < 8; ++k4) {
+            const float4 wv = ld4(sW + S_gW2 + j * kH + 4 * k4);
+            acc[4 * k4] = fmaf(wv.x, dy, acc[4 * k4]);
+            acc[4 * k4 + 1] = fmaf(wv.y, dy, acc[4 * k4 + 1]);
+            acc[4 * k4 + 2] = fmaf(wv.z, dy, acc[4 * k4 + 2]);
+            acc[4 * k4 + 3] = fmaf(wv.w, dy, acc[4 * k4 + 3]);
+          }
+        }
+#pragma unroll
+        for (int q = 0; q < kH; ++q) my[fA1 + q] = my[fA1 + q] > 0.f ? acc[q] : 0.f;
+#pragma unroll
+        for (int q = 0; q < kH; ++q) acc[q] = 0.f;
+#pragma unroll 4
+        for (int j = 0; j < kH; ++j) {
+          const float dy = my[fR2 + j];
+#pragma unroll
+          for (int k4 = 0; k4 < 8; ++k4) {
+            const float4 wv = ld4(sW + S_cW2 + j * kH + 4 * k4);
+            acc[4 * k4] = fmaf(wv.x, dy, acc[4 * k4]);
+            acc[4 * k4 + 1] = fmaf(wv.y, dy, acc[4 * k4 + 1]);
+            acc[4 * k4 + 2] = fmaf(wv.z, dy, acc[4 * k4 + 2]);
+            acc[4 * k4 + 3] = fmaf(wv.w, dy, acc[4 * k4 + 3]);
+          }
+        }
+#pragma unroll
+        for (int q = 0; q < kH; ++q) my[fR1 + q] = my[fR1 + q] > 0.f ? acc[q] : 0.f;
+      }
+      __syncwarp();
+      outer_rows<kZ, true>(wr, fA1, fZ, sG + S_gW1, sG + S_gb1, lane);
+      outer_rows<kU, true>(wr, fR1, fU, sG + S_cW1, sG + S_cb1, lane);
+      if (ok) {  // dz = gW1^T dy1, dcf = cW1[:, :6]^T dq1, then the scatter
+        float dz[kZ], dcf[kC];
+#pragma unroll
+        for (int q = 0; q < kZ; ++q) dz[q] = 0.f;
+#pragma unroll
+        for (int q = 0; q < kC; ++q) dcf[q] = 0.f;
+#pragma unroll 4
+        for (int j = 0; j < kH; ++j) {
+          const float dy = my[fA1 + j], dq = my[fR1 + j];
+#pragma unroll
+          for (int k4 = 0; k4 < 4; ++k4) {
+            const float4 wv = ld4(sW + S_gW1 + j * kZ + 4 * k4);
+            dz[4 * k4] = fmaf(wv.x, dy, dz[4 * k4]);
+            dz[4 * k4 + 1] = fmaf(wv.y, dy, dz[4 * k4 + 1]);
+            dz[4 * k4 + 2] = fmaf(wv.z, dy, dz[4 * k4 + 2]);
+            dz[4 * k4 + 3] = fmaf(wv.w, dy, dz[4 * k4 + 3]);
+          }
+#pragma unroll
+          for (int q = 0; q < kC; ++q) dcf[q] = fmaf(sW[S_cW1 + j * kU + q], dq, dcf[q]);
+        }
+        scatter(a, x, dz, dcf);
+      }
+    }
+  }
+  // CTA sums of the loss terms and of d kappa
+#pragma unroll
+  for (int q = 0; q < 5; ++q) {
+    const float v = warp_sum(lsum[q]);
+    if (lane == 0) atomicAdd(sL + q, v);
+  }
+  const float gk = warp_sum(gkappa);
+  if (lane == 0 && bwd) atomicAdd(sG + S_kappa, gk);
+  __syncthreads();
+  write_partials(a, sG, sL);
+}
+
+// Smoothness term on S_g (Sec. 3.3 Eq. smoothness_loss) and its second-order adjoint
+// (Supp. Sec. 1) for the two-hidden-layer geometry decoder.  Lane l of a warp evaluates
+// point 16 * group + (l & 15) at x (l < 16) or x + eps (l >= 16):
+//   g = grad_x phi = sum_k p_k dz_k/dx, p = gW1^T (m1 (.) gW2^T (m2 (.) gw3)).
+// The adjoint a = dL/dg gives the grid term p_{l,f} (1/v_l) (a . dw_c/df) and the decoder
+// terms gW1 += pm j^T, gW2 += e vj^T, gw3 += m2 (.) gW2 vj with j_k = a . dz_k/dx,
+// pm = m1 (.) gW2^T e, e = m2 (.) gw3, vj = m1 (.) gW1 j (biases get none).
+__global__ void __launch_bounds__(kThreads, 1) paper_smooth_kernel(Args a) {
+  extern __shared__ __align__(16) float smem[];
+  float* sW = smem;
+  float* sG = sW + kSm;
+  float* sL = sG + kSm;
+  float* rows = sL + 8;
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  float* wr = rows + wid * 32 * kRow;
+  float* my = wr + lane * kRow;
+  copy_decoder(a.theta + a.g.n_grid, sW);
+  for (int i = threadIdx.x; i < kSm; i += blockDim.x) sG[i] = 0.f;
+  if (threadIdx.x < 8) sL[threadIdx.x] = 0.f;
+  __syncthreads();
+  const bool bwd = (a.mode & 2) != 0;
+  const int n_g = a.counts[3];
+  const float w4 = a.dloss[4] + a.lam[4] * a.dloss[5];
+  const int ev = lane >> 4;
+  float lsum = 0.f;
+  for (int grp = blockIdx.x * kWarps + wid; grp * 16 < a.P; grp += gridDim.x * kWarps) {
+    const int p = grp * 16 + (lane & 15);
+    const bool ok = p < a.P && a.valid[p] != 0;
+    float y[3] = {0.f, 0.f, 0.f};
+    if (ok) {
+#pragma unroll
+      for (int q = 0; q < 3; ++q) y[q] = ev ? __fadd_rn(a.xs[3 * p + q], a.eps[3 * p + q]) : a.xs[3 * p + q];
+    }
+    // z; the x-derivatives dz/dx are gathered again level by level where they are used
+    // (keeping all 48 of them in registers beside the decoder sensitivities spills)
+    float z[kZ];
+#pragma unroll
+    for (int l = 0; l < kLevels; ++l) {
+      const Cell c = locate(a.g, l, y);
+      float wv[8];
+      corner_weights(c.f, wv);
+      const float4* lv = reinterpret_cast<const float4*>(a.theta + a.g.off[l]);
+      float4 acc = make_float4(0.f, 0.f, 0.f, 0.f);
+#pragma unroll
+      for (int k = 0; k < 8; ++k) f4fma(acc, wv[k], __ldg(lv + c.vtx + corner_offset(a.g, l, k)));
+      z[4 * l] = acc.x;
+      z[4 * l + 1] = acc.y;
+      z[4 * l + 2] = acc.z;
+      z[4 * l + 3] = acc.w;
+    }
+    // forward masks
+    unsigned m1 = 0u, m2 = 0u;
+    {
+      float h[kH];
+#pragma unroll
+      for (int j = 0; j < kH; ++j) {
+        float v = sW[S_gb1 + j];
+#pragma unroll
+        for (int k4 = 0; k4 < 4; ++k4) {
+          const float4 wv = ld4(sW + S_gW1 + j * kZ + 4 * k4);
+          v = fmaf(wv.x, z[4 * k4], v);
+          v = fmaf(wv.y, z[4 * k4 + 1], v);
+          v = fmaf(wv.z, z[4 * k4 + 2], v);
+          v = fmaf(wv.w, z[4 * k4 + 3], v);
+        }
+        h[j] = fmaxf(v, 0.f);
+        m1 |= (v > 0.f ? 1u : 0u) << j;
+      }
+#pragma unroll 1
+      for (int j = 0; j < kH; ++j) {
+        float v = sW[S_gb2 + j];
+#pragma unroll
+        for (int k4 = 0; k4 < 8; ++k4) {
+          const float4 wv = ld4(sW + S_gW2 + j * kH + 4 * k4);
+          v = fmaf(wv.x, h[4 * k4], v);
+          v = fmaf(wv.y, h[4 * k4 + 1], v);
+          v = fmaf(wv.z, h[4 * k4 + 2], v);
+          v = fmaf(wv.w, h[4 * k4 + 3], v);
+        }
+        m2 |= (v > 0.f ? 1u : 0u) << j;
+      }
+    }
+    // e = m2 (.) gw3 (row field A2), pm = m1 (.) gW2^T e (row field A1), p = gW1^T pm
+    float pz[kZ];
+    {
+      float pm[kH];
+#pragma unroll
+      for (int k = 0; k < kH; ++k) pm[k] = 0.f;
+#pragma unroll 1
+      for (int j = 0; j < kH; ++j) {
+        const float e = (m2 >> j) & 1u ? sW[S_gw3 + j] : 0.f;
+        my[fA2 + j] = e;
+#pragma unroll
+        for (int k4 = 0; k4 < 8; ++k4) {
+          const float4 wv = ld4(sW + S_gW2 + j * kH + 4 * k4);
+          pm[4 * k4] = fmaf(wv.x, e, pm[4 * k4]);
+          pm[4 * k4 + 1] = fmaf(wv.y, e, pm[4 * k4 + 1]);
+          pm[4 * k4 + 2] = fmaf(wv.z, e, pm[4 * k4 + 2]);
+          pm[4 * k4 + 3] = fmaf(wv.w, e, pm[4 * k4 + 3]);
+        }
+      }
+#pragma unroll
+      for (int k = 0; k < kZ; ++k) pz[k] = 0.f;
+#pragma unroll
+      for (int j = 0; j < kH; ++j) {
+        const float pj = (m1 >> j) & 1u ? pm[j] : 0.f;
+        my[fA1 + j] = pj;
+#pragma unroll
+        for (int k4 = 0; k4 < 4; ++k4) {
+          const float4 wv = ld4(sW + S_gW1 + j * kZ + 4 * k4);
+          pz[4 * k4] = fmaf(wv.x, pj, pz[4 * k4]);
+          pz[4 * k4 + 1] = fmaf(wv.y, pj, pz[4 * k4 + 1]);
+          pz[4 * k4 + 2] = fmaf(wv.z, pj, pz[4 * k4 + 2]);
+          pz[4 * k4 + 3] = fmaf(wv.w, pj, pz[4 * k4 + 3]);
+        }
+      }
+    }
+    float g[3] = {0.f, 0.f, 0.f};
+#pragma unroll
+    for (int l = 0; l < kLevels; ++l) {
+      float4 dl[3];
+      float dw[8][3];
+      level_jacobian(a.g, a.theta, l, y, dl, dw);
+#pragma unroll
+      for (int q = 0; q < 3; ++q)
+        g[q] += pz[4 * l] * dl[q].x + pz[4 * l + 1] * dl[q].y + pz[4 * l + 2] * dl[q].z + pz[4 * l + 3] * dl[q].w;
+    }
+    float dg[3];
+#pragma unroll
+    for (int q = 0; q < 3; ++q) {
+      const float other = __shfl_xor_sync(0xffffffffu, g[q], 16);
+      dg[q] = ev ? other - g[q] : g[q] - other;  // g(x) - g(x + eps) on both lanes
+    }
+    if (ok && ev == 0) lsum += dg[0] * dg[0] + dg[1] * dg[1] + dg[2] * dg[2];
+    if (!bwd) continue;
+    float av[3] = {0.f, 0.f, 0.f};
+    if (ok && n_g > 0) {
+      const float sc = (ev ? -2.f : 2.f) * w4 / (float)n_g;
+#pragma unroll
+      for (int q = 0; q < 3; ++q) av[q] = sc * dg[q];
+    }
+    float jv[kZ];  // j_k = a . dz_k/dx
+#pragma unroll
+    for (int l = 0; l < kLevels; ++l) {
+      float4 dl[3];
+      float dw[8][3];
+      level_jacobian(a.g, a.theta, l, y, dl, dw);
+      jv[4 * l] = av[0] * dl[0].x + av[1] * dl[1].x + av[2] * dl[2].x;
+      jv[4 * l + 1] = av[0] * dl[0].y + av[1] * dl[1].y + av[2] * dl[2].y;
+      jv[4 * l + 2] = av[0] * dl[0].z + av[1] * dl[1].z + av[2] * dl[2].z;
+      jv[4 * l + 3] = av[0] * dl[0].w + av[1] * dl[1].w + av[2] * dl[2].w;
+    }
+#pragma unroll
+    for (int k = 0; k < kZ; ++k) my[fZ + k] = jv[k];
+    // vj = m1 (.) gW1 j (row field R1);  w3g = m2 (.) gW2 vj (row field R2)
+    {
+      float vj[kH];
+#pragma unroll
+      for (int j = 0; j < kH; ++j) {
+        float v = 0.f;
+#pragma unroll
+        for (int k4 = 0; k4 < 4; ++k4) {
+          const float4 wv = ld4(sW + S_gW1 + j * kZ + 4 * k4);
+          v = fmaf(wv.x, jv[4 * k4], v);
+          v = fmaf(wv.y, jv[4 * k4 + 1], v);
+          v = fmaf(wv.z, jv[4 * k4 + 2], v);
+          v = fmaf(wv.w, jv[4 * k4 + 3], v);
+        }
+        vj[j] = (m1 >> j) & 1u ? v : 0.f;
+        my[fR1 + j] = vj[j];
+      }
+#pragma unroll 1
+      for (int j = 0; j < kH; ++j) {
+        float v = 0.f;
+#pragma unroll
+        for (int k4 = 0; k4 < 8; ++k4) {
+          const float4 wv = ld4(sW + S_gW2 + j * kH + 4 * k4);
+          v = fmaf(wv.x, vj[4 * k4], v);
+          v = fmaf(wv.y, vj[4 * k4 + 1], v);
+          v = fmaf(wv.z, vj[4 * k4 + 2], v);
+          v = fmaf(wv.w, vj[4 * k4 + 3], v);
+        }
+        my[fR2 + j] = (m2 >> j) & 1u ? v : 0.f;
+      }
+    }
+    __syncwarp();
+    outer_rows<kZ, false>(wr, fA1, fZ, sG + S_gW1, nullptr, lane);  // pm j^T
+    outer_rows<kH, false>(wr, fA2, fR1, sG + S_gW2, nullptr, lane);  // e vj^T
+    {
+      float acc = 0.f;
+#pragma unroll 8
+      for (int sidx = 0; sidx < 32; ++sidx) acc += wr[sidx * kRow + fR2 + lane];
+      atomicAdd(sG + S_gw3 + lane, acc);
+    }
+    __syncwarp();
+    // grid term
+    if (ok && n_g > 0) {
+#pragma unroll
+      for (int l = 0; l < kLevels; ++l) {
+        const Cell c = locate(a.g, l, y);
+        float dw[8][3];
+        corner_weight_grads(c.f, c.clamped, dw);
+        const float4 p4 = make_float4(pz[4 * l], pz[4 * l + 1], pz[4 * l + 2], pz[4 * l + 3]);
+        float4* gl = reinterpret_cast<float4*>(a.grad + a.g.off[l]);
+#pragma unroll
+        for (int k = 0; k < 8; ++k) {
+          const float ad = (av[0] * dw[k][0] + av[1] * dw[k][1] + av[2] * dw[k][2]) * a.g.inv_voxel[l];
+          atomicAdd(gl + c.vtx + corner_offset(a.g, l, k), f4scale(p4, ad));
+        }
+      }
+    }
+  }
+  const float v = warp_sum(lsum);
+  if (lane == 0) atomicAdd(sL + 4, v);
+  __syncthreads();
+  write_partials(a, sG, sL);
+}
+
+// combine the per-CTA partial rows: decoder gradients in a fixed order into gmlp, losses
+// in FP64 normalised by the set sizes (rgb: R, depth: rays with D > 0, sdf: |S_tr|,
+// fs: |S_fs|, smooth: valid points) with the weighted total
+__global__ void __launch_bounds__(256) paper_combine_kernel(const float* loss_part, const float* mlp_part,
+                                                            int nparts, const int* counts, int R, float l0, float l1,
+                                                            float l2, float l3, float l4, float* loss, float* gmlp) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (gmlp && i < GS_PAPER_MLP_PARAMS) {
+    float sacc = 0.f;
+    for (int p = 0; p < nparts; ++p) sacc += mlp_part[(size_t)p * kPart + i];
+    gmlp[i] += sacc;
+  }
+  if (loss && blockIdx.x == 0 && threadIdx.x < 32) {
+    const int lane = threadIdx.x;
+    double sk[5] = {0.0, 0.0, 0.0, 0.0, 0.0};
+    for (int p = lane; p < nparts; p += 32)
+#pragma unroll
+      for (int k = 0; k < 5; ++k) sk[k] += (double)loss_part[(size_t)p * kLossPad + k];
+#pragma unroll
+    for (int k = 0; k < 5; ++k)
+#pragma unroll
+      for (int off = 16; off > 0; off >>= 1) sk[k] += __shfl_xor_sync(0xffffffffu, sk[k], off);
+    if (lane == 0) {
+      const double den[5] = {(double)R, (double)counts[0], (double)counts[1], (double)counts[2], (double)counts[3]};
+      const double lam[5] = {l0, l1, l2, l3, l4};
+      double tot = 0.0;
+#pragma unroll
+      for (int k = 0; k < 5; ++k) {
+        const double v = den[k] > 0 ? sk[k] / den[k] : 0.0;
+        loss[k] = (float)v;
+        tot += lam[k] * v;
+      }
+      loss[5] = (float)tot;
+    }
+  }
+}
+
+template <int NCH>
+static gs_status launch_render(const gs_ctx* ctx, const Args& a, int ctas, cudaStream_t st) {
+  static bool attr = false;  // per process; the attribute is a property of the function
+  if (!attr) {
+    if (cudaFuncSetAttribute(paper_render_kernel<NCH>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)kSmemBytes) != cudaSuccess)
+      return GS_ERR_CUDA;
+    attr = true;
+  }
+  paper_render_kernel<NCH><<<ctas, kThreads, kSmemBytes, st>>>(a);
+  (void)ctx;
+  return cudaPeekAtLastError() == cudaSuccess ? GS_OK : GS_ERR_CUDA;
+}
+
+}  // namespace paper
+}  // namespace gs
+
+using namespace gs;
+
+int gs_paper_part_rows(int num_sms) { return paper::kCtasPerSm * num_sms + kSmoothCtas; }
+size_t gs_paper_part_floats(int num_sms) { return (size_t)gs_paper_part_rows(num_sms) * paper::kPart; }
+
+gs_status gs_launch_paper(const gs_ctx* ctx, const float* theta, const gs_batch* b, const float* dloss, float* grad,
+                          float* loss, float* rgb_hat, float* d_hat, float* wsum, int mode, cudaStream_t st) {
+  using namespace paper;
+  Args a;
+  a.g = ctx->grid;
+  a.colour_off = ctx->colour_off;
+  a.theta = theta;
+  a.grad = grad;
+  a.o = b->origin;
+  a.r = b->dir;
+  a.rgb = b->rgb;
+  a.D = b->depth;
+  a.t = b->t;
+  a.cls = b->cls;
+  a.xs = b->xs;
+  a.eps = b->eps;
+  a.valid = b->valid;
+  a.counts = b->counts;
+  a.dloss = dloss;
+  a.rgb_hat = rgb_hat;
+  a.d_hat = d_hat;
+  a.wsum = wsum;
+  a.w_out = b->w;
+  a.R = b->R;
+  a.N = b->N;
+  a.P = b->P;
+  a.mode = mode;
+  for (int k = 0; k < 5; ++k) a.lam[k] = ctx->cfg.lam[k];
+  a.kappa_fs = ctx->cfg.kappa_fs;
+  const int render_ctas = kCtasPerSm * ctx->num_sms;
+  int nparts = 0;
+  float* first_loss = ctx->paper_loss_part;
+  float* first_mlp = ctx->paper_part;
+  if (b->R > 0) {
+    a.loss_part = ctx->paper_loss_part;
+    a.mlp_part = ctx->paper_part;
+    gs_status s;
+    switch ((b->N + 31) / 32) {
+      case 1: s = launch_render<1>(ctx, a, render_ctas, st); break;
+      case 2: s = launch_render<2>(ctx, a, render_ctas, st); break;
+      case 3: s = launch_render<3>(ctx, a, render_ctas, st); break;
+      case 4: s = launch_render<4>(ctx, a, render_ctas, st); break;
+      case 5: s = launch_render<5>(ctx, a, render_ctas, st); break;
+      default: return GS_ERR_UNSUPPORTED;
+    }
+    if (s != GS_OK) return s;
+    nparts += render_ctas;
+  }
+  if (b->P > 0) {
+    static bool attr = false;
+    if (!attr) {
+      if (cudaFuncSetAttribute(paper_smooth_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmemBytes) !=
+          cudaSuccess)
+        return GS_ERR_CUDA;
+      attr = true;
+    }
+    a.loss_part = ctx->paper_loss_part + (size_t)render_ctas * kLossPad;
+    a.mlp_part = ctx->paper_part + (size_t)render_ctas * kPart;
+    paper_smooth_kernel<<<kSmoothCtas, kThreads, kSmemBytes, st>>>(a);
+    if (cudaPeekAtLastError() != cudaSuccess) return GS_ERR_CUDA;
+    if (b->R == 0) {
+      first_loss = a.loss_part;
+      first_mlp = a.mlp_part;
+    }
+    nparts += kSmoothCtas;
+  }
+  if (nparts == 0) {
+    // an empty batch: losses 0, gradient unchanged
+    if (mode & 1) {
+      if (cudaMemsetAsync(loss, 0, sizeof(float) * GS_NUM_LOSS, st) != cudaSuccess) return GS_ERR_CUDA;
+    }
+    return GS_OK;
+  }
+  const float* l = ctx->cfg.lam;
+  paper_combine_kernel<<<(GS_PAPER_MLP_PARAMS + 255) / 256, 256, 0, st>>>(
+      first_loss, first_mlp, nparts, b->counts, b->R, l[0], l[1], l[2], l[3], l[4], (mode & 1) ? loss : nullptr,
+      (mode & 2) ? grad + ctx->grid.n_grid : nullptr);
+  return cudaPeekAtLastError() == cudaSuccess ? GS_OK : GS_ERR_CUDA;
+}

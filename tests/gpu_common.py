@@ -54,8 +54,10 @@ class Problem:
         for l in range(4):
             nx, ny, nz = self.w.dims[l]
             out[f"grid{l}"] = g[self.offs[l]:self.offs[l] + nx * ny * nz * 4]
+        if self.w.arch == "paper":
+            out["colour_grid"] = g[self.w.colour_offset():self.n_grid]
         o = self.n_grid
-        for name, shape in sg.MLP_SHAPES:
+        for name, shape in self.w.mlp_shapes:
             n = int(np.prod(shape))
             out[name] = g[o:o + n]
             o += n

@@ -1,0 +1,167 @@
+"""The paper's architecture on the GPU (gs_config.arch = GS_ARCH_PAPER: colour grid W_beta at
+the finest level, colour decoder fed the unit viewing direction, two hidden layers of 32 in
+both decoders) through the C ABI, against the FP64 oracle on identical seeded inputs.
+
+Tolerances as for the workload's decoders: each loss term to 1e-5 relative; each gradient
+tensor (geometry levels, colour grid, every decoder matrix and bias, kappa) to 1e-4 of its
+largest entry, and 1e-3 relative element-wise where an entry exceeds 1% of that maximum.
+"""
+import numpy as np
+import pytest
+import torch
+
+import oracle as oc
+import paper_2206_14735_gb300 as gs
+import scenegen as sg
+from gpu_common import LOSS_RTOL, Problem, assert_grad_close, prepare_parity_batch, upload_oracle_batch
+
+pytestmark = pytest.mark.gpu
+
+CUBE_P = sg.WORKLOADS["cube-paper-1024x64"]
+SEED, STEP = 3, 5
+
+
+def _padded(theta):
+    """Device copy of theta padded to a multiple of 4 floats (the Adam kernel's vector unit)."""
+    n = len(theta)
+    t = torch.zeros((n + 3) // 4 * 4, dtype=torch.float32, device="cuda")
+    t[:n] = torch.from_numpy(np.ascontiguousarray(theta, np.float32))
+    return t
+
+
+def _case(w, R=None, P=None, seed=SEED, step=STEP, max_drop=0.1):
+    p = Problem(w, max_rays=R)
+    theta = sg.paper_sdf_params(w, sg.cube_scene(), seed=23)
+    bt, sm = p.oracle_sample(seed, step, R, P)
+    bt_s, ref, dropped = prepare_parity_batch(p, theta, bt, sm, max_drop=max_drop)
+    assert ref["margins"][0] > 1e-2, ref["margins"]  # hidden units clear of their kinks
+    assert ref["margins"][5] > 1e-5, ref["margins"]
+    batch = upload_oracle_batch(bt_s, sm, 0 if sm is None else sm["n_valid"][0])
+    return dict(p=p, theta=theta, bt=bt_s, sm=sm, ref=ref, batch=batch)
+
+
+@pytest.fixture(scope="module")
+def cube_paper():
+    return _case(CUBE_P)
+
+
+def _forward(c, with_outputs=True):
+    th = _padded(c["theta"])
+    b = c["batch"]
+    loss = torch.empty(6, device="cuda")
+    outs = [torch.empty(b.R, 3, device="cuda"), torch.empty(b.R, device="cuda"), torch.empty(b.R, device="cuda")]
+    if with_outputs:
+        c["p"].ctx.forward(th, b, loss, *outs)
+    else:
+        c["p"].ctx.forward(th, b, loss)
+    torch.cuda.synchronize()
+    return loss.cpu().numpy().astype(np.float64), [o.cpu().numpy() for o in outs]
+
+
+def _check_loss(got, want):
+    for k in range(6):
+        assert abs(got[k] - want[k]) <= LOSS_RTOL * abs(want[k]) + 1e-12, (k, got, want)
+
+
+def test_paper_forward_loss_parity(cube_paper):
+    got, (rgb_hat, d_hat, wsum) = _forward(cube_paper)
+    ref = cube_paper["ref"]
+    _check_loss(got, ref["loss"])
+    assert got[0] > 0 and got[2] > 0 and got[3] > 0 and got[4] > 0
+    np.testing.assert_allclose(rgb_hat, ref["rgb_hat"], atol=2e-6)
+    np.testing.assert_allclose(d_hat, ref["d_hat"], atol=2e-5)
+    np.testing.assert_allclose(wsum, ref["wsum"], atol=2e-6)
+    assert wsum.max() <= 1.0 + 1e-6
+
+
+def test_paper_backward_gradient_parity(cube_paper):
+    c = cube_paper
+    th = _padded(c["theta"])
+    grad = torch.zeros_like(th)
+    c["p"].ctx.backward(th, c["batch"], None, grad)
+    torch.cuda.synchronize()
+    g = grad.cpu().numpy()[:len(c["theta"])]
+    rep = assert_grad_close(c["p"], g, c["ref"]["grad"])
+    assert "colour_grid" in rep and "cW2" in rep and "gW2" in rep and "kappa" in rep
+
+
+def test_paper_forward_backward_matches_separate_calls(cube_paper):
+    c = cube_paper
+    th = _padded(c["theta"])
+    dloss = torch.tensor([0.3, -1.1, 0.7, 2.0, 5.0, 0.25], device="cuda")
+    g1, g2 = torch.zeros_like(th), torch.zeros_like(th)
+    loss = torch.empty(6, device="cuda")
+    c["p"].ctx.forward_backward(th, c["batch"], dloss, loss, g1)
+    c["p"].ctx.backward(th, c["batch"], dloss, g2)
+    torch.cuda.synchronize()
+    _check_loss(loss.cpu().numpy().astype(np.float64), c["ref"]["loss"])
+    ref = oc.step(c["p"].cfg, c["theta"], c["bt"], c["sm"], dloss=dloss.cpu().numpy().astype(np.float64))
+    n = len(c["theta"])
+    assert_grad_close(c["p"], g1.cpu().numpy()[:n], ref["grad"])
+    # the two calls differ only in the order of their FP32 atomics
+    np.testing.assert_allclose(g1.cpu().numpy(), g2.cpu().numpy(), rtol=0,
+                               atol=1e-5 * float(np.abs(ref["grad"]).max()))
+
+
+def test_paper_smoothness_term_alone(cube_paper):
+    """Upstream seed on L_smooth only: the second-order path alone (no colour gradient)."""
+    c = cube_paper
+    th = _padded(c["theta"])
+    dl = np.array([0, 0, 0, 0, 1.0, 0])
+    grad = torch.zeros_like(th)
+    c["p"].ctx.backward(th, c["batch"], torch.tensor(dl, dtype=torch.float32, device="cuda"), grad)
+    torch.cuda.synchronize()
+    ref = oc.step(c["p"].cfg, c["theta"], c["bt"], c["sm"], dloss=dl)
+    g = grad.cpu().numpy()[:len(c["theta"])]
+    assert_grad_close(c["p"], g, ref["grad"])
+    assert np.abs(g[CUBE_P.colour_offset():c["p"].n_grid]).max() == 0
+
+
+@pytest.mark.parametrize("n_strat,n_guided,R,P", [(100, 32, 77, 13), (30, 9, 33, 0), (8, 0, 5, 40)])
+def test_paper_ragged_shapes(n_strat, n_guided, R, P):
+    """Samples per ray spanning 1, 5 chunks with a ragged last chunk; ray and point counts that
+    fill no whole warp group; a batch without smoothness points."""
+    w = CUBE_P.with_(name=f"cube-paper-{n_strat}+{n_guided}", n_strat=n_strat, n_guided=n_guided, n_smooth=P)
+    c = _case(w, R=R, P=P, seed=7, step=n_strat, max_drop=0.25)
+    got, (rgb_hat, d_hat, wsum) = _forward(c)
+    _check_loss(got, c["ref"]["loss"])
+    np.testing.assert_allclose(d_hat, c["ref"]["d_hat"], atol=2e-5)
+    th = _padded(c["theta"])
+    grad = torch.zeros_like(th)
+    c["p"].ctx.backward(th, c["batch"], None, grad)
+    torch.cuda.synchronize()
+    assert_grad_close(c["p"], grad.cpu().numpy()[:len(c["theta"])], c["ref"]["grad"])
+
+
+def test_paper_empty_batches():
+    """No rays and no points: losses 0, gradient untouched; points only: the smoothness term."""
+    p = Problem(CUBE_P)
+    theta = sg.paper_sdf_params(CUBE_P, sg.cube_scene(), seed=23)
+    th = _padded(theta)
+    empty = gs.Batch.allocate(0, CUBE_P.n_samples, 0)
+    loss = torch.full((6,), 7.0, device="cuda")
+    grad = torch.full_like(th, 0.5)
+    p.ctx.forward_backward(th, empty, None, loss, grad)
+    torch.cuda.synchronize()
+    assert np.all(loss.cpu().numpy() == 0) and torch.all(grad == 0.5)
+    _, sm = p.oracle_sample(SEED, STEP, 0, 64)
+    bt0 = {k: v[:0] for k, v in p.oracle_sample(SEED, STEP, 1, 0)[0].items() if k != "counts"}
+    bt0["counts"] = np.zeros(4, np.int64)
+    ref = oc.step(p.cfg, theta, bt0, sm)
+    b = upload_oracle_batch(bt0, sm, sm["n_valid"][0])
+    grad = torch.zeros_like(th)
+    p.ctx.forward_backward(th, b, None, loss, grad)
+    torch.cuda.synchronize()
+    _check_loss(loss.cpu().numpy().astype(np.float64), ref["loss"])
+    assert_grad_close(p, grad.cpu().numpy()[:len(theta)], ref["grad"])
+
+
+def test_paper_rejections():
+    p = Problem(CUBE_P)
+    th = _padded(sg.paper_sdf_params(CUBE_P, sg.cube_scene(), seed=23))
+    x = torch.zeros(4, 3, device="cuda")
+    with pytest.raises(gs.GoSurfError, match="GS_ARCH_PAPER"):
+        p.ctx.query_sdf(th, x, torch.empty(4, device="cuda"))
+    b = gs.Batch.allocate(8, CUBE_P.n_samples, 0, dz=True)
+    with pytest.raises(gs.GoSurfError, match="UNSUPPORTED"):
+        p.ctx.forward_backward(th, b, None, torch.empty(6, device="cuda"), torch.zeros_like(th))
