@@ -139,9 +139,13 @@ def run_ours(args):
     t0 = time.time()
     fr = sg.make_frames(w, n_frames=args.frames, with_gt=args.sampler_report > 0)
     t_frames = time.time() - t0
-    ctx = gs.Context(w, store_activations=not args.recompute)
+    paper = w.arch == "paper"  # the paper's architecture recomputes its activations (no store)
+    recompute = args.recompute or paper
+    ctx = gs.Context(w, store_activations=not recompute)
     dfr = gs.DeviceFrames(fr.rgb, fr.depth, fr.c2w, fr.fx, fr.fy, fr.cx, fr.cy)
-    theta = torch.from_numpy(sg.init_params(w)).cuda()
+    theta0 = sg.init_params(w)
+    theta = torch.zeros((len(theta0) + 3) // 4 * 4, device="cuda")  # Adam works on 4-float vectors
+    theta[:len(theta0)] = torch.from_numpy(theta0).cuda()
     grad, m, v = torch.zeros_like(theta), torch.zeros_like(theta), torch.zeros_like(theta)
     n_grid_ = w.layout()[1]
     # BF16 form: the grid copy the gathers read, refreshed by every Adam step
@@ -317,14 +321,15 @@ def run_ours(args):
     n_grid = w.layout()[1]
     # algorithmic bytes: gather 4 levels x 8 corners x 16 B (8 B from the BF16 copy) and 512 B
     # of FP32 gradient scattered per sample; Adam 32 B per parameter (+2 B per grid entry copied)
-    render_bytes = S * ((256 if ctx.bf16 else 512) + 512)
+    # (paper architecture: + the colour grid's 8 corners x 24 B gathered and scattered)
+    render_bytes = S * (2 * (512 + 192) if paper else (256 if ctx.bf16 else 512) + 512)
     adam_bytes = w.layout()[2] * 32 + (2 * n_grid_ if ctx.bf16 else 0)
     dom = max(("render", "adam"), key=lambda k: avg[k])
     dom_bytes = render_bytes if dom == "render" else adam_bytes
     achieved = dom_bytes / (avg[dom] / 1e3) / 1e9
     peak = peaks["hbm_gbs"]
     traffic = args.traffic_render if dom == "render" else args.traffic_adam
-    default_step = (w.name == WORKLOAD and not args.recompute and not args.split and not args.eikonal and
+    default_step = (w.name == WORKLOAD and not recompute and not args.split and not args.eikonal and
                     not args.poses and args.frames in (None, 50))
     if traffic is None and dom == "render" and default_step:
         traffic = _profiled_traffic("render_tc_kernel_room-8192x96.md",
@@ -337,7 +342,9 @@ def run_ours(args):
                    "samples_per_s": round(value * w.n_samples, 1), "smooth_points": w.n_smooth,
                    "params": w.layout()[2], "grid_params": n_grid, "frames": fr.depth.shape[0],
                    "resolution": [w.width, w.height], "parallelism": f"replicas{world}",
-                   "activations": "recomputed" if args.recompute else "stored (396 B/sample)",
+                   "model": ("paper: colour grid (6 features, finest level) + view direction, decoders with "
+                             "2 hidden layers of 32" if paper else "compact: decoders 16-32-16 and 15-32-3"),
+                   "activations": "recomputed" if recompute else "stored (396 B/sample)",
                    "sampler": (f"importance: {w.imp_coarse} coarse + {w.imp_steps} x {w.imp_per_step}"
                                if w.imp_coarse > 0 else f"stratified {w.n_strat} + depth-guided {w.n_guided}"),
                    "pipeline": ("the next step's batch sampled on a side stream during this step (double-buffered)"
@@ -351,8 +358,10 @@ def run_ours(args):
                    "l2": "inputs larger than L2: 1.2 GB of parameter/gradient/moment state streamed per step",
                    "frame_render_s": round(t_frames, 1)},
         "kernels_ms": {k: round(vv, 4) for k, vv in avg.items()},
-        "roofline": {"kernel": "render call: render_tc_kernel (fused gather / tcgen05 decoders / compositing / "
-                               "backward / scatter, 90 % of the call) + smooth_kernel + finalize_kernel"
+        "roofline": {"kernel": ("render call: paper_render_kernel (fused gathers / CUDA-core decoders / compositing "
+                                "/ backward / scatter) + paper_smooth_kernel + paper_combine_kernel" if paper else
+                                "render call: render_tc_kernel (fused gather / tcgen05 decoders / compositing / "
+                                "backward / scatter, 90 % of the call) + smooth_kernel + finalize_kernel")
                      if dom == "render" else "adam_kernel", "bound": "hbm", "achieved": round(achieved, 1), "peak": peak,
                      "unit": "GB/s", "frac": round(achieved / peak, 4), "traffic": traffic,
                      "peak_kind": f"{kind} hbm_gbs (copy)",
