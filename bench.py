@@ -387,7 +387,7 @@ def run_ours(args):
     return line
 
 
-def _eval_depth(ctx, w, dfr, gt, theta, sampler, q=None, R=65536, seed=99):
+def _eval_depth(ctx, w, dfr, gt, theta, sampler, q=None, R=65536, seed=99, mirror=None):
     """Rendered depth of R fresh rays against the noise-free depth: mean |d_hat - D_gt| over
     rays with D_gt > 0, and over those whose observed depth was dropped (D = 0)."""
     import numpy as np
@@ -406,7 +406,7 @@ def _eval_depth(ctx, w, dfr, gt, theta, sampler, q=None, R=65536, seed=99):
         ctx.proposal_sample(dfr, seed, 0, b, theta=theta, prop=q)
     loss = torch.empty(6, device="cuda")
     dh = torch.empty(R, device="cuda")
-    ctx.forward(theta, b, loss, d_hat=dh)
+    ctx.forward(theta, b, loss, d_hat=dh, theta_bf16=mirror)
     d_hat = dh.cpu().numpy().astype(np.float64)
     pix = b.pix.cpu().numpy()
     D = b.depth.cpu().numpy()
@@ -500,11 +500,14 @@ def proposal_report(w, fr, dfr, steps):
     from paper_2206_14735_gb300.proposal import ProposalTrainer
     out = {}
     for form in ("plain", "proposal"):
-        ctx = gs.Context(w, store_activations=True)
+        # the plain form is always the FP32 one; the proposal form takes the workload's precision
+        wf = w.with_(precision="fp32") if form == "plain" else w
+        ctx = gs.Context(wf, store_activations=True)
         theta = torch.from_numpy(sg.init_params(w)).cuda()
         grad, m, v = torch.zeros_like(theta), torch.zeros_like(theta), torch.zeros_like(theta)
+        mirror = theta[:w.layout()[1]].to(torch.bfloat16).view(torch.int16).contiguous() if ctx.bf16 else None
         loss = torch.empty(6, device="cuda")
-        trainer = ProposalTrainer(ctx, w, dfr, seed=5) if form == "proposal" else None
+        trainer = ProposalTrainer(ctx, w, dfr, seed=5, mirror=mirror) if form == "proposal" else None
         batch = gs.Batch.allocate(w.rays, w.n_samples, w.n_smooth) if form == "plain" else None
         n_prop = 0
         torch.cuda.synchronize()
@@ -529,9 +532,11 @@ def proposal_report(w, fr, dfr, steps):
             hist = trainer.controller.history
             res["controller_trace"] = [[round(a, 4), round(b, 4), c] for a, b, c in hist[::max(1, len(hist) // 12)]]
             res["ce_last"] = round(float(trainer.ce[0].item()), 5)
-            res["with_proposal"] = _eval_depth(ctx, w, dfr, fr.gt_depth, theta, "proposal", q=trainer.q)
-            res["with_plain"] = _eval_depth(ctx, w, dfr, fr.gt_depth, theta, "plain")
+            res["with_proposal"] = _eval_depth(ctx, w, dfr, fr.gt_depth, theta, "proposal", q=trainer.q,
+                                               mirror=mirror)
+            res["with_plain"] = _eval_depth(ctx, w, dfr, fr.gt_depth, theta, "plain", mirror=mirror)
             res["samples_per_ray"] = w.prop_samples
+            res["precision"] = w.precision
         out[form] = res
         ctx.close()
     out["what"] = ("both forms trained from the same initial parameters on the same frames; depth error of the "
@@ -567,8 +572,9 @@ def run_proposal(args):
     ctx = gs.Context(w, store_activations=not args.recompute)
     theta = torch.from_numpy(sg.init_params(w)).cuda()
     grad, m, v = torch.zeros_like(theta), torch.zeros_like(theta), torch.zeros_like(theta)
+    mirror = theta[:w.layout()[1]].to(torch.bfloat16).view(torch.int16).contiguous() if ctx.bf16 else None
     loss = torch.empty(6, device="cuda")
-    trainer = ProposalTrainer(ctx, w, dfr, seed=3 + 1000 * rank)
+    trainer = ProposalTrainer(ctx, w, dfr, seed=3 + 1000 * rank, mirror=mirror)
     for k in range(args.warmup + args.prop_pretrain):
         trainer.step(k, theta, grad, m, v, loss)
     torch.cuda.synchronize()
@@ -598,7 +604,7 @@ def run_proposal(args):
     line = {
         "metric": METRIC, "value": round(value, 1), "unit": "rays/s", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": round(ms / args.steps, 4), "higher_is_better": True,
-        "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "scaling": "weak", "vs_baseline": None, "dtype": "bf16" if ctx.bf16 else "f32", "data": "synthetic",
         "config": {"workload": w.name, "rays": w.rays, "samples_per_ray": w.prop_samples,
                    "guided_of_those": w.prop_guided, "lr_prop": w.lr_prop,
                    "fallback_samples_per_ray": w.n_samples, "pretrain_steps": args.prop_pretrain,

@@ -52,10 +52,12 @@ class ProposalTrainer:
     fallback), the proposal's own training step, and the periodic fallback decision."""
 
     def __init__(self, ctx, workload, frames, *, seed: int = 3, eval_every: int = 25, holdout: int | None = None,
-                 tolerance: float = 1.05, q0: np.ndarray | None = None, train_rays: int | None = 16384):
+                 tolerance: float = 1.05, q0: np.ndarray | None = None, train_rays: int | None = 16384,
+                 mirror=None):
         from . import Batch  # local import: the package imports this module lazily
         w = workload
         self.ctx, self.w, self.frames, self.seed = ctx, w, frames, seed
+        self.mirror = mirror  # BF16 form: the grid copy the gathers read (refreshed by every Adam step)
         self.eval_every = eval_every
         R, P = w.rays, w.n_smooth
         self.batch_plain = Batch.allocate(R, w.n_samples, P, weights=True)
@@ -97,9 +99,9 @@ class ProposalTrainer:
         another seed); updates the controller."""
         hs = self.seed + 7919
         self.ctx.sample_rays(self.frames, hs, step, self.hold_plain)
-        self.ctx.forward(theta, self.hold_plain, self.hold_loss[0])
+        self.ctx.forward(theta, self.hold_plain, self.hold_loss[0], theta_bf16=self.mirror)
         self.ctx.proposal_sample(self.frames, hs, step, self.hold_prop, theta=theta, prop=self.q)
-        self.ctx.forward(theta, self.hold_prop, self.hold_loss[1])
+        self.ctx.forward(theta, self.hold_prop, self.hold_loss[1], theta_bf16=self.mirror)
         l = self.hold_loss[:, 1].cpu().numpy()
         return self.controller.update(float(l[1]), float(l[0]))
 
@@ -107,10 +109,11 @@ class ProposalTrainer:
         """One full step: sample, fused forward/backward of the main model (writes the
         rendering weights), proposal training, Adam on both, periodic fallback decision."""
         b = self.batch(step, theta)
-        self.ctx.forward_backward(theta, b, None, loss, grad)
+        self.ctx.forward_backward(theta, b, None, loss, grad, theta_bf16=self.mirror)
         self.train_proposal(theta, b)
         w = self.w
-        self.ctx.adam_step(theta, grad, m, v, step + 1, w.lr_grid, w.lr_mlp, w.betas[0], w.betas[1], w.adam_eps)
+        self.ctx.adam_step(theta, grad, m, v, step + 1, w.lr_grid, w.lr_mlp, w.betas[0], w.betas[1], w.adam_eps,
+                           theta_bf16=self.mirror)
         if self.eval_every > 0 and (step + 1) % self.eval_every == 0:
             self.evaluate(step, theta)
         return b
