@@ -67,9 +67,12 @@ __device__ __forceinline__ int acc_index(int i) {
   return -1;
 }
 
-// per-lane row of staged sample vectors (odd stride: lane-own rows are conflict-free)
-constexpr int kRow = 161;
-constexpr int fZ = 0, fU = 16, fA1 = 25, fA2 = 57, fR1 = 89, fR2 = 121, fDP = 153, fDPHI = 156;
+// Per-lane row of staged sample vectors.  Every field starts on a 16-byte boundary and the
+// stride is 4 (mod 32) words, so a lane's float4 access to its own row and a float4 read of
+// one row by the whole warp (broadcast) are both free of bank conflicts.
+constexpr int kRow = 164;
+constexpr int fZ = 0, fU = 16, fA1 = 28, fA2 = 60, fR1 = 92, fR2 = 124, fDP = 156;  // fDP: dpre[3], dphi
+static_assert(kRow % 32 == 4 && fU % 4 == 0 && fA1 % 4 == 0 && fDP % 4 == 0, "row layout");
 constexpr int kWarps = 4;  // warps per CTA
 constexpr int kThreads = kWarps * 32;
 constexpr size_t kSmemBytes = sizeof(float) * (2 * kSm + 8 + kWarps * 32 * kRow);
@@ -107,7 +110,13 @@ __device__ __forceinline__ void outer_rows(const float* wr, int fd, int fa, floa
     const float d = rs[fd + lane];
     ab += d;
 #pragma unroll
-    for (int k = 0; k < K; ++k) acc[k] = fmaf(d, rs[fa + k], acc[k]);
+    for (int k4 = 0; k4 < (K + 3) / 4; ++k4) {
+      const float4 v = *reinterpret_cast<const float4*>(rs + fa + 4 * k4);
+      acc[4 * k4] = fmaf(d, v.x, acc[4 * k4]);
+      if (4 * k4 + 1 < K) acc[4 * k4 + 1 < K ? 4 * k4 + 1 : 0] = fmaf(d, v.y, acc[4 * k4 + 1 < K ? 4 * k4 + 1 : 0]);
+      if (4 * k4 + 2 < K) acc[4 * k4 + 2 < K ? 4 * k4 + 2 : 0] = fmaf(d, v.z, acc[4 * k4 + 2 < K ? 4 * k4 + 2 : 0]);
+      if (4 * k4 + 3 < K) acc[4 * k4 + 3 < K ? 4 * k4 + 3 : 0] = fmaf(d, v.w, acc[4 * k4 + 3 < K ? 4 * k4 + 3 : 0]);
+    }
   }
 #pragma unroll
   for (int k = 0; k < K; ++k) atomicAdd(acc_m + k * 32 + lane, acc[k]);
@@ -115,6 +124,9 @@ __device__ __forceinline__ void outer_rows(const float* wr, int fd, int fa, floa
 }
 
 __device__ __forceinline__ float4 ld4(const float* p) { return *reinterpret_cast<const float4*>(p); }
+__device__ __forceinline__ void st4(float* p, float a, float b, float c, float d) {
+  *reinterpret_cast<float4*>(p) = make_float4(a, b, c, d);
+}
 
 // geometry features z (4 levels x 4) and colour features cf (level-3 cell, 6) at x
 __device__ __forceinline__ void gather(const Args& a, const float x[3], float z[kZ], float cf[kC]) {
@@ -168,29 +180,35 @@ __device__ __forceinline__ void decode(const float* sW, const float z[kZ], const
     h[j] = fmaxf(y, 0.f);
   }
   float p = sW[S_gb3];
-#pragma unroll 4
-  for (int j = 0; j < kH; ++j) {
-    float y = sW[S_gb2 + j];
+#pragma unroll 1
+  for (int j4 = 0; j4 < kH / 4; ++j4) {
+    float yv[4];
 #pragma unroll
-    for (int k4 = 0; k4 < 8; ++k4) {
-      const float4 w = ld4(sW + S_gW2 + j * kH + 4 * k4);
-      y = fmaf(w.x, h[4 * k4], y);
-      y = fmaf(w.y, h[4 * k4 + 1], y);
-      y = fmaf(w.z, h[4 * k4 + 2], y);
-      y = fmaf(w.w, h[4 * k4 + 3], y);
+    for (int q = 0; q < 4; ++q) {
+      const int j = 4 * j4 + q;
+      float y = sW[S_gb2 + j];
+#pragma unroll
+      for (int k4 = 0; k4 < 8; ++k4) {
+        const float4 w = ld4(sW + S_gW2 + j * kH + 4 * k4);
+        y = fmaf(w.x, h[4 * k4], y);
+        y = fmaf(w.y, h[4 * k4 + 1], y);
+        y = fmaf(w.z, h[4 * k4 + 2], y);
+        y = fmaf(w.w, h[4 * k4 + 3], y);
+      }
+      yv[q] = fmaxf(y, 0.f);
+      p = fmaf(sW[S_gw3 + j], yv[q], p);
     }
-    y = fmaxf(y, 0.f);
-    if (row) row[fA2 + j] = y;
-    p = fmaf(sW[S_gw3 + j], y, p);
+    if (row) st4(row + fA2 + 4 * j4, yv[0], yv[1], yv[2], yv[3]);
   }
   phi = p;
   if (row) {
 #pragma unroll
-    for (int k = 0; k < kZ; ++k) row[fZ + k] = z[k];
+    for (int k4 = 0; k4 < kZ / 4; ++k4) st4(row + fZ + 4 * k4, z[4 * k4], z[4 * k4 + 1], z[4 * k4 + 2], z[4 * k4 + 3]);
 #pragma unroll
-    for (int j = 0; j < kH; ++j) row[fA1 + j] = h[j];
-#pragma unroll
-    for (int k = 0; k < kU; ++k) row[fU + k] = u[k];
+    for (int j4 = 0; j4 < kH / 4; ++j4) st4(row + fA1 + 4 * j4, h[4 * j4], h[4 * j4 + 1], h[4 * j4 + 2], h[4 * j4 + 3]);
+    st4(row + fU, u[0], u[1], u[2], u[3]);
+    st4(row + fU + 4, u[4], u[5], u[6], u[7]);
+    st4(row + fU + 8, u[8], 0.f, 0.f, 0.f);
   }
 #pragma unroll
   for (int j = 0; j < kH; ++j) {
@@ -200,25 +218,30 @@ __device__ __forceinline__ void decode(const float* sW, const float z[kZ], const
     h[j] = fmaxf(y, 0.f);
   }
   float pre[3] = {sW[S_cb3], sW[S_cb3 + 1], sW[S_cb3 + 2]};
-#pragma unroll 4
-  for (int j = 0; j < kH; ++j) {
-    float y = sW[S_cb2 + j];
+#pragma unroll 1
+  for (int j4 = 0; j4 < kH / 4; ++j4) {
+    float yv[4];
 #pragma unroll
-    for (int k4 = 0; k4 < 8; ++k4) {
-      const float4 w = ld4(sW + S_cW2 + j * kH + 4 * k4);
-      y = fmaf(w.x, h[4 * k4], y);
-      y = fmaf(w.y, h[4 * k4 + 1], y);
-      y = fmaf(w.z, h[4 * k4 + 2], y);
-      y = fmaf(w.w, h[4 * k4 + 3], y);
+    for (int q = 0; q < 4; ++q) {
+      const int j = 4 * j4 + q;
+      float y = sW[S_cb2 + j];
+#pragma unroll
+      for (int k4 = 0; k4 < 8; ++k4) {
+        const float4 w = ld4(sW + S_cW2 + j * kH + 4 * k4);
+        y = fmaf(w.x, h[4 * k4], y);
+        y = fmaf(w.y, h[4 * k4 + 1], y);
+        y = fmaf(w.z, h[4 * k4 + 2], y);
+        y = fmaf(w.w, h[4 * k4 + 3], y);
+      }
+      yv[q] = fmaxf(y, 0.f);
+#pragma unroll
+      for (int i = 0; i < 3; ++i) pre[i] = fmaf(sW[S_cW3 + i * kH + j], yv[q], pre[i]);
     }
-    y = fmaxf(y, 0.f);
-    if (row) row[fR2 + j] = y;
-#pragma unroll
-    for (int i = 0; i < 3; ++i) pre[i] = fmaf(sW[S_cW3 + i * kH + j], y, pre[i]);
+    if (row) st4(row + fR2 + 4 * j4, yv[0], yv[1], yv[2], yv[3]);
   }
   if (row) {
 #pragma unroll
-    for (int j = 0; j < kH; ++j) row[fR1 + j] = h[j];
+    for (int j4 = 0; j4 < kH / 4; ++j4) st4(row + fR1 + 4 * j4, h[4 * j4], h[4 * j4 + 1], h[4 * j4 + 2], h[4 * j4 + 3]);
   }
 #pragma unroll
   for (int i = 0; i < 3; ++i) col[i] = sigmoidf_(pre[i]);
@@ -286,6 +309,7 @@ __global__ void __launch_bounds__(kThreads, kCtasPerSm) paper_render_kernel(Args
       I[q] = a.rgb[3 * ray + q];
     }
     const float D = a.D[ray];
+    __syncwarp();  // the previous ray's products have read every row before this ray stages its last chunk
     const float rn = sqrtf(r[0] * r[0] + r[1] * r[1] + r[2] * r[2]);
 #pragma unroll
     for (int q = 0; q < 3; ++q) d[q] = r[q] / rn;
@@ -319,7 +343,7 @@ __global__ void __launch_bounds__(kThreads, kCtasPerSm) paper_render_kernel(Args
 #pragma unroll
       for (int q = 0; q < 3; ++q) u[kC + q] = d[q];
       float ph, cc[3];
-      decode(sW, z, u, nullptr, ph, cc);
+      decode(sW, z, u, bwd && c == NCH - 1 ? my : nullptr, ph, cc);
 #pragma unroll
       for (int q = 0; q < NCH; ++q)
         if (c == q) {
@@ -454,110 +478,121 @@ __global__ void __launch_bounds__(kThreads, kCtasPerSm) paper_render_kernel(Args
     }
 
     // ---------------- decoder adjoints and scatter, chunk by chunk ----------------
+    // Last chunk first: its inputs and activations are still staged in the rows by the
+    // forward pass; the other chunks gather and decode again.
 #pragma unroll 1
-    for (int c = 0; c < NCH; ++c) {
+    for (int c = NCH - 1; c >= 0; --c) {
       const int k = 32 * c + lane;
       const bool ok = k < N;
-      float tc = tk[0], wc = w[0], dp = dphi[0];
+      float tc = tk[0], wc = w[0], dp = dphi[0], cc[3] = {col[0][0], col[0][1], col[0][2]};
 #pragma unroll
       for (int q = 1; q < NCH; ++q)
         if (c == q) {
           tc = tk[q];
           wc = w[q];
           dp = dphi[q];
+          cc[0] = col[q][0];
+          cc[1] = col[q][1];
+          cc[2] = col[q][2];
         }
-      float x[3], z[kZ], u[kU];
-      __syncwarp();  // the previous chunk's products have read every row
-      if (ok) {
-        sample_pos(o, r, tc, x);
-        gather(a, x, z, u);
-      } else {
+      float x[3] = {0.f, 0.f, 0.f};
+      if (ok) sample_pos(o, r, tc, x);
+      if (c != NCH - 1) {
+        float z[kZ], u[kU];
+        __syncwarp();  // the previous chunk's products have read every row
+        if (ok) {
+          gather(a, x, z, u);
+        } else {
 #pragma unroll
-        for (int q = 0; q < kZ; ++q) z[q] = 0.f;
+          for (int q = 0; q < kZ; ++q) z[q] = 0.f;
 #pragma unroll
-        for (int q = 0; q < kC; ++q) u[q] = 0.f;
+          for (int q = 0; q < kC; ++q) u[q] = 0.f;
+        }
+#pragma unroll
+        for (int q = 0; q < 3; ++q) u[kC + q] = d[q];
+        float ph, c2[3];
+        decode(sW, z, u, my, ph, c2);
       }
-#pragma unroll
-      for (int q = 0; q < 3; ++q) u[kC + q] = d[q];
-      float ph, cc[3];
-      decode(sW, z, u, my, ph, cc);
       float dpre[3];
 #pragma unroll
       for (int q = 0; q < 3; ++q) dpre[q] = ok ? wc * gc[q] * cc[q] * (1.f - cc[q]) : 0.f;
-      my[fDP] = dpre[0];
-      my[fDP + 1] = dpre[1];
-      my[fDP + 2] = dpre[2];
-      my[fDPHI] = dp;
+      st4(my + fDP, dpre[0], dpre[1], dpre[2], dp);
       __syncwarp();
       {  // output layers: gw3, gb3 (lane = column), cW3, cb3
-        float ag = 0.f, a0 = 0.f, a1 = 0.f, a2 = 0.f, bg = 0.f, bc = 0.f;
-        const int lq = lane < 3 ? lane : 2;
+        float ag = 0.f, a0 = 0.f, a1 = 0.f, a2 = 0.f, bg = 0.f, b0 = 0.f, b1 = 0.f, b2 = 0.f;
 #pragma unroll 4
         for (int sidx = 0; sidx < 32; ++sidx) {
           const float* rs = wr + sidx * kRow;
-          const float dph = rs[fDPHI], r2 = rs[fR2 + lane];
-          ag = fmaf(dph, rs[fA2 + lane], ag);
-          a0 = fmaf(rs[fDP], r2, a0);
-          a1 = fmaf(rs[fDP + 1], r2, a1);
-          a2 = fmaf(rs[fDP + 2], r2, a2);
-          bg += dph;
-          bc += rs[fDP + lq];
+          const float4 dd = ld4(rs + fDP);  // dpre[0..2], dphi
+          const float r2 = rs[fR2 + lane];
+          ag = fmaf(dd.w, rs[fA2 + lane], ag);
+          a0 = fmaf(dd.x, r2, a0);
+          a1 = fmaf(dd.y, r2, a1);
+          a2 = fmaf(dd.z, r2, a2);
+          bg += dd.w;
+          b0 += dd.x;
+          b1 += dd.y;
+          b2 += dd.z;
         }
         atomicAdd(sG + S_gw3 + lane, ag);
         atomicAdd(sG + S_cW3 + lane, a0);
         atomicAdd(sG + S_cW3 + kH + lane, a1);
         atomicAdd(sG + S_cW3 + 2 * kH + lane, a2);
-        if (lane == 0) atomicAdd(sG + S_gb3, bg);
-        if (lane < 3) atomicAdd(sG + S_cb3 + lane, bc);
+        if (lane == 0) {
+          atomicAdd(sG + S_gb3, bg);
+          atomicAdd(sG + S_cb3, b0);
+          atomicAdd(sG + S_cb3 + 1, b1);
+          atomicAdd(sG + S_cb3 + 2, b2);
+        }
       }
       __syncwarp();
       // own sample: dy2 = m2 (.) gw3 dphi over a2; dq2 = m(q2) (.) cW3^T dpre over r2
 #pragma unroll
-      for (int j = 0; j < kH; ++j) {
-        const float a2v = my[fA2 + j];
-        my[fA2 + j] = a2v > 0.f ? sW[S_gw3 + j] * dp : 0.f;
-        const float r2v = my[fR2 + j];
-        const float v = sW[S_cW3 + j] * dpre[0] + sW[S_cW3 + kH + j] * dpre[1] + sW[S_cW3 + 2 * kH + j] * dpre[2];
-        my[fR2 + j] = r2v > 0.f ? v : 0.f;
+      for (int j4 = 0; j4 < kH / 4; ++j4) {
+        const float4 a2v = ld4(my + fA2 + 4 * j4), w3 = ld4(sW + S_gw3 + 4 * j4);
+        st4(my + fA2 + 4 * j4, a2v.x > 0.f ? w3.x * dp : 0.f, a2v.y > 0.f ? w3.y * dp : 0.f,
+            a2v.z > 0.f ? w3.z * dp : 0.f, a2v.w > 0.f ? w3.w * dp : 0.f);
+        const float4 r2v = ld4(my + fR2 + 4 * j4), c0 = ld4(sW + S_cW3 + 4 * j4),
+                     c1 = ld4(sW + S_cW3 + kH + 4 * j4), c2 = ld4(sW + S_cW3 + 2 * kH + 4 * j4);
+        st4(my + fR2 + 4 * j4, r2v.x > 0.f ? c0.x * dpre[0] + c1.x * dpre[1] + c2.x * dpre[2] : 0.f,
+            r2v.y > 0.f ? c0.y * dpre[0] + c1.y * dpre[1] + c2.y * dpre[2] : 0.f,
+            r2v.z > 0.f ? c0.z * dpre[0] + c1.z * dpre[1] + c2.z * dpre[2] : 0.f,
+            r2v.w > 0.f ? c0.w * dpre[0] + c1.w * dpre[1] + c2.w * dpre[2] : 0.f);
       }
       __syncwarp();
       outer_rows<kH, true>(wr, fA2, fA1, sG + S_gW2, sG + S_gb2, lane);
       outer_rows<kH, true>(wr, fR2, fR1, sG + S_cW2, sG + S_cb2, lane);
       __syncwarp();
-      {  // own sample: dy1 = m1 (.) gW2^T dy2 over a1; dq1 = m(q1) (.) cW2^T dq2 over r1
+      // own sample: dy1 = m1 (.) gW2^T dy2 over a1; dq1 = m(q1) (.) cW2^T dq2 over r1
+#pragma unroll
+      for (int half = 0; half < 2; ++half) {
+        const int fin = half ? fR2 : fA2, fout = half ? fR1 : fA1, sw = half ? S_cW2 : S_gW2;
         float acc[kH];
 #pragma unroll
         for (int q = 0; q < kH; ++q) acc[q] = 0.f;
-#pragma unroll 4
-        for (int j = 0; j < kH; ++j) {
-          const float dy = my[fA2 + j];
+#pragma unroll 1
+        for (int j4 = 0; j4 < kH / 4; ++j4) {
+          const float4 dy4 = ld4(my + fin + 4 * j4);
+          const float dys[4] = {dy4.x, dy4.y, dy4.z, dy4.w};
 #pragma unroll
-          for (int k4 = 0; k4 < 8; ++k4) {
-            const float4 wv = ld4(sW + S_gW2 + j * kH + 4 * k4);
-            acc[4 * k4] = fmaf(wv.x, dy, acc[4 * k4]);
-            acc[4 * k4 + 1] = fmaf(wv.y, dy, acc[4 * k4 + 1]);
-            acc[4 * k4 + 2] = fmaf(wv.z, dy, acc[4 * k4 + 2]);
-            acc[4 * k4 + 3] = fmaf(wv.w, dy, acc[4 * k4 + 3]);
+          for (int q = 0; q < 4; ++q) {
+            const int j = 4 * j4 + q;
+#pragma unroll
+            for (int k4 = 0; k4 < 8; ++k4) {
+              const float4 wv = ld4(sW + sw + j * kH + 4 * k4);
+              acc[4 * k4] = fmaf(wv.x, dys[q], acc[4 * k4]);
+              acc[4 * k4 + 1] = fmaf(wv.y, dys[q], acc[4 * k4 + 1]);
+              acc[4 * k4 + 2] = fmaf(wv.z, dys[q], acc[4 * k4 + 2]);
+              acc[4 * k4 + 3] = fmaf(wv.w, dys[q], acc[4 * k4 + 3]);
+            }
           }
         }
 #pragma unroll
-        for (int q = 0; q < kH; ++q) my[fA1 + q] = my[fA1 + q] > 0.f ? acc[q] : 0.f;
-#pragma unroll
-        for (int q = 0; q < kH; ++q) acc[q] = 0.f;
-#pragma unroll 4
-        for (int j = 0; j < kH; ++j) {
-          const float dy = my[fR2 + j];
-#pragma unroll
-          for (int k4 = 0; k4 < 8; ++k4) {
-            const float4 wv = ld4(sW + S_cW2 + j * kH + 4 * k4);
-            acc[4 * k4] = fmaf(wv.x, dy, acc[4 * k4]);
-            acc[4 * k4 + 1] = fmaf(wv.y, dy, acc[4 * k4 + 1]);
-            acc[4 * k4 + 2] = fmaf(wv.z, dy, acc[4 * k4 + 2]);
-            acc[4 * k4 + 3] = fmaf(wv.w, dy, acc[4 * k4 + 3]);
-          }
+        for (int q4 = 0; q4 < kH / 4; ++q4) {
+          const float4 hv = ld4(my + fout + 4 * q4);
+          st4(my + fout + 4 * q4, hv.x > 0.f ? acc[4 * q4] : 0.f, hv.y > 0.f ? acc[4 * q4 + 1] : 0.f,
+              hv.z > 0.f ? acc[4 * q4 + 2] : 0.f, hv.w > 0.f ? acc[4 * q4 + 3] : 0.f);
         }
-#pragma unroll
-        for (int q = 0; q < kH; ++q) my[fR1 + q] = my[fR1 + q] > 0.f ? acc[q] : 0.f;
       }
       __syncwarp();
       outer_rows<kZ, true>(wr, fA1, fZ, sG + S_gW1, sG + S_gb1, lane);
@@ -568,19 +603,24 @@ __global__ void __launch_bounds__(kThreads, kCtasPerSm) paper_render_kernel(Args
         for (int q = 0; q < kZ; ++q) dz[q] = 0.f;
 #pragma unroll
         for (int q = 0; q < kC; ++q) dcf[q] = 0.f;
-#pragma unroll 4
-        for (int j = 0; j < kH; ++j) {
-          const float dy = my[fA1 + j], dq = my[fR1 + j];
+#pragma unroll 1
+        for (int j4 = 0; j4 < kH / 4; ++j4) {
+          const float4 dy4 = ld4(my + fA1 + 4 * j4), dq4 = ld4(my + fR1 + 4 * j4);
+          const float dys[4] = {dy4.x, dy4.y, dy4.z, dy4.w}, dqs[4] = {dq4.x, dq4.y, dq4.z, dq4.w};
 #pragma unroll
-          for (int k4 = 0; k4 < 4; ++k4) {
-            const float4 wv = ld4(sW + S_gW1 + j * kZ + 4 * k4);
-            dz[4 * k4] = fmaf(wv.x, dy, dz[4 * k4]);
-            dz[4 * k4 + 1] = fmaf(wv.y, dy, dz[4 * k4 + 1]);
-            dz[4 * k4 + 2] = fmaf(wv.z, dy, dz[4 * k4 + 2]);
-            dz[4 * k4 + 3] = fmaf(wv.w, dy, dz[4 * k4 + 3]);
+          for (int q = 0; q < 4; ++q) {
+            const int j = 4 * j4 + q;
+#pragma unroll
+            for (int k4 = 0; k4 < 4; ++k4) {
+              const float4 wv = ld4(sW + S_gW1 + j * kZ + 4 * k4);
+              dz[4 * k4] = fmaf(wv.x, dys[q], dz[4 * k4]);
+              dz[4 * k4 + 1] = fmaf(wv.y, dys[q], dz[4 * k4 + 1]);
+              dz[4 * k4 + 2] = fmaf(wv.z, dys[q], dz[4 * k4 + 2]);
+              dz[4 * k4 + 3] = fmaf(wv.w, dys[q], dz[4 * k4 + 3]);
+            }
+#pragma unroll
+            for (int e = 0; e < kC; ++e) dcf[e] = fmaf(sW[S_cW1 + j * kU + e], dqs[q], dcf[e]);
           }
-#pragma unroll
-          for (int q = 0; q < kC; ++q) dcf[q] = fmaf(sW[S_cW1 + j * kU + q], dq, dcf[q]);
         }
         scatter(a, x, dz, dcf);
       }
@@ -689,7 +729,6 @@ __global__ void __launch_bounds__(kThreads, 1) paper_smooth_kernel(Args a) {
 #pragma unroll 1
       for (int j = 0; j < kH; ++j) {
         const float e = (m2 >> j) & 1u ? sW[S_gw3 + j] : 0.f;
-        my[fA2 + j] = e;
 #pragma unroll
         for (int k4 = 0; k4 < 8; ++k4) {
           const float4 wv = ld4(sW + S_gW2 + j * kH + 4 * k4);
@@ -702,9 +741,18 @@ __global__ void __launch_bounds__(kThreads, 1) paper_smooth_kernel(Args a) {
 #pragma unroll
       for (int k = 0; k < kZ; ++k) pz[k] = 0.f;
 #pragma unroll
+      for (int j = 0; j < kH; ++j) pm[j] = (m1 >> j) & 1u ? pm[j] : 0.f;
+#pragma unroll
+      for (int j4 = 0; j4 < kH / 4; ++j4) {
+        const float4 w3 = ld4(sW + S_gw3 + 4 * j4);
+        const int b = 4 * j4;
+        st4(my + fA2 + b, (m2 >> b) & 1u ? w3.x : 0.f, (m2 >> (b + 1)) & 1u ? w3.y : 0.f,
+            (m2 >> (b + 2)) & 1u ? w3.z : 0.f, (m2 >> (b + 3)) & 1u ? w3.w : 0.f);
+        st4(my + fA1 + b, pm[b], pm[b + 1], pm[b + 2], pm[b + 3]);
+      }
+#pragma unroll
       for (int j = 0; j < kH; ++j) {
-        const float pj = (m1 >> j) & 1u ? pm[j] : 0.f;
-        my[fA1 + j] = pj;
+        const float pj = pm[j];
 #pragma unroll
         for (int k4 = 0; k4 < 4; ++k4) {
           const float4 wv = ld4(sW + S_gW1 + j * kZ + 4 * k4);
@@ -751,7 +799,7 @@ __global__ void __launch_bounds__(kThreads, 1) paper_smooth_kernel(Args a) {
       jv[4 * l + 3] = av[0] * dl[0].w + av[1] * dl[1].w + av[2] * dl[2].w;
     }
 #pragma unroll
-    for (int k = 0; k < kZ; ++k) my[fZ + k] = jv[k];
+    for (int k4 = 0; k4 < kZ / 4; ++k4) st4(my + fZ + 4 * k4, jv[4 * k4], jv[4 * k4 + 1], jv[4 * k4 + 2], jv[4 * k4 + 3]);
     // vj = m1 (.) gW1 j (row field R1);  w3g = m2 (.) gW2 vj (row field R2)
     {
       float vj[kH];
@@ -767,20 +815,27 @@ __global__ void __launch_bounds__(kThreads, 1) paper_smooth_kernel(Args a) {
           v = fmaf(wv.w, jv[4 * k4 + 3], v);
         }
         vj[j] = (m1 >> j) & 1u ? v : 0.f;
-        my[fR1 + j] = vj[j];
       }
-#pragma unroll 1
-      for (int j = 0; j < kH; ++j) {
-        float v = 0.f;
 #pragma unroll
-        for (int k4 = 0; k4 < 8; ++k4) {
-          const float4 wv = ld4(sW + S_gW2 + j * kH + 4 * k4);
-          v = fmaf(wv.x, vj[4 * k4], v);
-          v = fmaf(wv.y, vj[4 * k4 + 1], v);
-          v = fmaf(wv.z, vj[4 * k4 + 2], v);
-          v = fmaf(wv.w, vj[4 * k4 + 3], v);
+      for (int j4 = 0; j4 < kH / 4; ++j4) st4(my + fR1 + 4 * j4, vj[4 * j4], vj[4 * j4 + 1], vj[4 * j4 + 2], vj[4 * j4 + 3]);
+#pragma unroll 1
+      for (int j4 = 0; j4 < kH / 4; ++j4) {
+        float vv[4];
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+          const int j = 4 * j4 + q;
+          float v = 0.f;
+#pragma unroll
+          for (int k4 = 0; k4 < 8; ++k4) {
+            const float4 wv = ld4(sW + S_gW2 + j * kH + 4 * k4);
+            v = fmaf(wv.x, vj[4 * k4], v);
+            v = fmaf(wv.y, vj[4 * k4 + 1], v);
+            v = fmaf(wv.z, vj[4 * k4 + 2], v);
+            v = fmaf(wv.w, vj[4 * k4 + 3], v);
+          }
+          vv[q] = (m2 >> j) & 1u ? v : 0.f;
         }
-        my[fR2 + j] = (m2 >> j) & 1u ? v : 0.f;
+        st4(my + fR2 + 4 * j4, vv[0], vv[1], vv[2], vv[3]);
       }
     }
     __syncwarp();

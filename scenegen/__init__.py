@@ -337,9 +337,10 @@ WORKLOADS["room-imp-8192x132"] = WORKLOADS["room-8192x96"].with_(name="room-imp-
 WORKLOADS["room-prop-65536x32"] = WORKLOADS["room-8192x96"].with_(name="room-prop-65536x32", rays=65536,
                                                                    blob_frac=0.3, prop_samples=32, prop_guided=8)
 # the precision form with the learned proposal: BF16 gathers and decoders (FP32 master,
-# gradients and moments), 24 proposal + 8 depth-guided samples per ray, plain FP32 96 as fallback
+# gradients and moments), 8 proposal + 24 depth-guided samples per ray where the observed
+# depth exists (all 32 from the proposal where it is missing), plain 64 + 32 as fallback
 WORKLOADS["room-prop-bf16-65536x32"] = WORKLOADS["room-prop-65536x32"].with_(name="room-prop-bf16-65536x32",
-                                                                             precision="bf16")
+                                                                             precision="bf16", prop_guided=24)
 # the paper's architecture (Sec. 3.1): colour grid at the finest level, view direction,
 # decoders with two hidden layers of 32
 WORKLOADS["cube-paper-1024x64"] = WORKLOADS["cube-1024x64"].with_(name="cube-paper-1024x64", arch="paper")
