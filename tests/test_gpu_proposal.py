@@ -136,3 +136,32 @@ def test_proposal_entry_points_reject_bad_shapes(prob):
     with pytest.raises(gs.GoSurfError):  # no weights to learn from
         p.ctx.proposal_backward(torch.from_numpy(prob["theta"]).cuda(), torch.from_numpy(prob["q"]).cuda(), bp,
                                 torch.zeros(oc.PROP_PARAMS, device="cuda"))
+
+
+def test_bf16_trainer_reads_the_bf16_copy_and_trains():
+    """The BF16 proposal form: every main-model call of the trainer (fused step, held-out
+    renders, Adam) takes the bfloat16 grid copy, which Adam keeps equal to the RNE copy of
+    theta; the proposal's cross entropy falls and the main loss stays finite."""
+    from paper_2206_14735_gb300.proposal import ProposalTrainer
+    w = CUBE_P.with_(name="cube-prop-bf16", precision="bf16", prop_guided=24, rays=512, n_smooth=64)
+    p = Problem(w)
+    theta = torch.from_numpy(sg.init_params(w)).cuda()
+    grad, m, v = torch.zeros_like(theta), torch.zeros_like(theta), torch.zeros_like(theta)
+    mirror = theta[:p.n_grid].to(torch.bfloat16).view(torch.int16).contiguous()
+    tr = ProposalTrainer(p.ctx, w, p.dfr, seed=5, eval_every=10, mirror=mirror)
+    loss = torch.empty(6, device="cuda")
+    ce = []
+    for k in range(60):
+        tr.step(k, theta, grad, m, v, loss)
+        if k in (0, 59):
+            ce.append(float(tr.ce[0].item()))
+    torch.cuda.synchronize()
+    p.ctx.sync_status()
+    assert np.all(np.isfinite(loss.cpu().numpy()))
+    assert ce[1] < ce[0]
+    assert len(tr.controller.history) == 6
+    want = theta[:p.n_grid].to(torch.bfloat16).view(torch.int16)
+    assert torch.equal(mirror, want)
+    # without the copy the BF16 context refuses the render call
+    with pytest.raises(gs.GoSurfError, match="theta_bf16"):
+        p.ctx.forward_backward(theta, tr.batch_plain, None, loss, grad)
