@@ -95,6 +95,13 @@ typedef struct {
   float fx, fy, cx, cy;
 } oc_frames;
 
+/* the paper's architecture (oc_config.arch = 1), defined at the end of this file */
+static void pa_query_sdf(const oc_config* c, const double* theta, const float* x, int P, double* sdf, double* grad);
+static void pa_query_sdf_backward(const oc_config* c, const double* theta, const float* x, int P, const double* dsdf,
+                                  const double* dgrad, double* grad);
+static double pa_phi_at(const oc_config* c, const double* theta, const float x[3]);
+static double pa_kappa(const oc_config* c, const double* theta);
+
 /* ------------------------------------------------------------------------------------ */
 /* counter-based random numbers: SplitMix64 (Steele, Lea & Flood, OOPSLA 2014)            */
 /* ------------------------------------------------------------------------------------ */
@@ -456,6 +463,10 @@ static void dphi_dz(const mlp_t* m, const act_t* A, double p[OC_Z], double mw2[O
 /* query: phi(x) and grad_x phi(x) (Supp. Eq. sdf_first_grad)                            */
 /* ------------------------------------------------------------------------------------ */
 void oc_query_sdf(const oc_config* c, const double* theta, const float* x, int P, double* sdf, double* grad) {
+  if (c->arch == 1) {
+    pa_query_sdf(c, theta, x, P, sdf, grad);
+    return;
+  }
   mlp_t m = mlp_view(theta + grid_size(c));
 #pragma omp parallel for schedule(static)
   for (int i = 0; i < P; ++i) {
@@ -488,6 +499,10 @@ void oc_query_sdf(const oc_config* c, const double* theta, const float* x, int P
  * piecewise linear in z).  dsdf or dgrad may be NULL (zero).  x is not differentiated. */
 void oc_query_sdf_backward(const oc_config* c, const double* theta, const float* x, int P, const double* dsdf,
                            const double* dgrad, double* grad) {
+  if (c->arch == 1) {
+    pa_query_sdf_backward(c, theta, x, P, dsdf, dgrad, grad);
+    return;
+  }
   const int64_t ng = grid_size(c);
   mlp_t m = mlp_view(theta + ng);
   double* gm = grad + ng;
@@ -1201,6 +1216,7 @@ static double phi_on_ray(const oc_config* c, const double* theta, const mlp_t* m
     float st = tv * r[a];
     x[a] = o[a] + st;
   }
+  if (c->arch == 1) return pa_phi_at(c, theta, x);
   cell_t cl[OC_LEVELS];
   act_t A;
   features(c, theta, x, cl, A.z, NULL);
@@ -1214,8 +1230,8 @@ int oc_sample_importance(const oc_config* c, const oc_frames* fr, const double* 
   if (R < 0 || Nc < 2 || n_steps < 0 || M < 1 || M > 64) return -1;
   const int N = Nc + n_steps * M;
   const int64_t npix = (int64_t)fr->F * fr->H * fr->W;
-  const mlp_t m = mlp_view(theta + grid_size(c));
-  const double s = exp(*m.kappa);
+  const mlp_t m = mlp_view(theta + grid_size(c)); /* not read for the paper's architecture */
+  const double s = exp(c->arch == 1 ? pa_kappa(c, theta) : *m.kappa);
   int64_t nd = 0, ntr = 0, nfs = 0;
 #pragma omp parallel for schedule(static) reduction(+ : nd, ntr, nfs)
   for (int i = 0; i < R; ++i) {
@@ -2082,4 +2098,106 @@ int oc_step_paper(const oc_config* c, const double* theta, int R, int N, const f
     margins[8] = margins[9] = 0.0;
   }
   return 0;
+}
+
+/* ------------------------------------------------------------------------------------ */
+/* the paper's architecture: SDF query, its reverse mode, phi and kappa for the samplers  */
+/* ------------------------------------------------------------------------------------ */
+static double pa_kappa(const oc_config* c, const double* theta) {
+  int64_t ng = 0;
+  oc_paper_param_count(c, &ng);
+  return theta[ng + PA_MLP - 1];
+}
+
+static double pa_phi_at(const oc_config* c, const double* theta, const float x[3]) {
+  int64_t ng = 0;
+  oc_paper_param_count(c, &ng);
+  const pa_mlp_t m = pa_view(theta + ng);
+  const double d[3] = {0, 0, 1}; /* the colour decoder's input; phi does not read it */
+  cell_t cells[OC_LEVELS];
+  pa_act_t A;
+  pa_eval(c, theta, &m, x, d, cells, NULL, &A);
+  return A.phi;
+}
+
+/* phi(x) and grad_x phi(x) = sum_k p_k dz_k/dx with p = d phi/dz (Supp. Eq. sdf_first_grad) */
+static void pa_query_sdf(const oc_config* c, const double* theta, const float* x, int P, double* sdf, double* grad) {
+  int64_t ng = 0;
+  oc_paper_param_count(c, &ng);
+  const pa_mlp_t m = pa_view(theta + ng);
+  const double d[3] = {0, 0, 1};
+#pragma omp parallel for schedule(static)
+  for (int i = 0; i < P; ++i) {
+    cell_t cells[OC_LEVELS];
+    pa_act_t A;
+    double dzdx[OC_Z][3];
+    pa_eval(c, theta, &m, x + 3 * i, d, cells, dzdx, &A);
+    sdf[i] = A.phi;
+    if (grad) {
+      double p[OC_Z], pm[PA_H], e[PA_H];
+      pa_dphi_dz(&m, &A, p, pm, e);
+      for (int a = 0; a < 3; ++a) {
+        double acc = 0;
+        for (int k = 0; k < OC_Z; ++k) acc += p[k] * dzdx[k][a];
+        grad[3 * i + a] = acc;
+      }
+    }
+  }
+}
+
+/* grad += sum_i dsdf_i d phi(x_i)/d theta + dgrad_i . d grad_x phi(x_i)/d theta for the
+ * paper's architecture: the first term is the geometry decoder's backward pass and the
+ * adjoint of the gathers; the second the second-order path of Supp. Sec. 1 through the
+ * two-hidden-layer decoder (as in the smoothness term of oc_step_paper).  The colour grid
+ * and the colour decoder get nothing.  dsdf or dgrad may be NULL; x carries no gradient. */
+static void pa_query_sdf_backward(const oc_config* c, const double* theta, const float* x, int P, const double* dsdf,
+                                  const double* dgrad, double* grad) {
+  int64_t ng = 0;
+  oc_paper_param_count(c, &ng);
+  const pa_mlp_t m = pa_view(theta + ng);
+  double* gm = grad + ng;
+  pa_mlp_t gg = pa_view(gm);
+  const double d[3] = {0, 0, 1};
+  for (int i = 0; i < P; ++i) {
+    cell_t cells[OC_LEVELS];
+    pa_act_t A;
+    double dzdx[OC_Z][3];
+    pa_eval(c, theta, &m, x + 3 * i, d, cells, dzdx, &A);
+    if (dsdf && dsdf[i] != 0.0) {
+      const double dc[3] = {0, 0, 0};
+      double dz[OC_Z], dcf[PA_C];
+      pa_backward(&m, &A, dsdf[i], dc, gm, dz, dcf);
+      for (int l = 0; l < OC_LEVELS; ++l)
+        for (int cc = 0; cc < 8; ++cc)
+          for (int f = 0; f < OC_FEAT; ++f) grad[cells[l].corner[cc] + f] += cells[l].w[cc] * dz[OC_FEAT * l + f];
+    }
+    if (dgrad) {
+      const double* av = dgrad + 3 * i;
+      double p[OC_Z], pm[PA_H], e[PA_H], jv[OC_Z], vj[PA_H];
+      pa_dphi_dz(&m, &A, p, pm, e);
+      for (int k = 0; k < OC_Z; ++k) jv[k] = av[0] * dzdx[k][0] + av[1] * dzdx[k][1] + av[2] * dzdx[k][2];
+      for (int l = 0; l < OC_LEVELS; ++l)
+        for (int cc = 0; cc < 8; ++cc) {
+          const double ad =
+              (av[0] * cells[l].dw[cc][0] + av[1] * cells[l].dw[cc][1] + av[2] * cells[l].dw[cc][2]) * cells[l].inv_v;
+          for (int f = 0; f < OC_FEAT; ++f) grad[cells[l].corner[cc] + f] += p[OC_FEAT * l + f] * ad;
+        }
+      for (int i1 = 0; i1 < PA_H; ++i1) {
+        double acc = 0;
+        for (int k = 0; k < OC_Z; ++k) {
+          ((double*)gg.gW1)[i1 * OC_Z + k] += pm[i1] * jv[k];
+          acc += m.gW1[i1 * OC_Z + k] * jv[k];
+        }
+        vj[i1] = A.y1[i1] > 0 ? acc : 0.0;
+      }
+      for (int i2 = 0; i2 < PA_H; ++i2) {
+        double acc = 0;
+        for (int i1 = 0; i1 < PA_H; ++i1) {
+          ((double*)gg.gW2)[i2 * PA_H + i1] += e[i2] * vj[i1];
+          acc += m.gW2[i2 * PA_H + i1] * vj[i1];
+        }
+        if (A.y2[i2] > 0) ((double*)gg.gw3)[i2] += acc;
+      }
+    }
+  }
 }

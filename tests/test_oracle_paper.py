@@ -244,3 +244,141 @@ def test_paper_smoothness_second_order_gradient_alone(tiny_paper):
 def test_paper_gradients_h1e3(tiny_paper):
     """The h = 1e-3 central-difference check."""
     _check(tiny_paper, None, h=1e-3, tol=1e-4, stride=3)
+
+
+# ----------------------------------------------------------------------------------------
+# the SDF query, its reverse mode, the Eikonal term, the importance sampler and mesh
+# extraction with the paper's architecture
+# ----------------------------------------------------------------------------------------
+def _affine_passthrough(w, n, c0=0.1):
+    th = np.zeros(w.layout()[2], np.float32)
+    set_level_field(w, th, 3, 0, lambda X: X @ np.asarray(n) + c0)
+    return passthrough_paper(w, th, zindex=12)
+
+
+def test_paper_query_affine_field_closed_form():
+    """phi = n . x + c through the two-hidden-layer decoder: the query returns it and its
+    gradient n exactly (inside the grid box)."""
+    n = np.array([0.3, -0.6, 0.2])
+    th = _affine_passthrough(CUBE_P, n)
+    x = np.random.default_rng(3).uniform(-1.2, 1.2, (200, 3)).astype(np.float32)
+    phi, g = oc.query_sdf(oc.make_config(CUBE_P), th, x)
+    np.testing.assert_allclose(phi, x.astype(np.float64) @ n + 0.1, atol=2e-6)
+    np.testing.assert_allclose(g, np.tile(n, (len(x), 1)), atol=2e-6)
+
+
+def test_paper_query_gradient_matches_central_differences_in_x(tiny_paper):
+    """grad_x phi against central differences of phi along each axis, for points whose two
+    probes stay in the same cell of every level (phi is multilinear per cell and the
+    decoder is linear on its piece, so the difference quotient is exact up to rounding)."""
+    cfg, _, _, th = tiny_paper
+    rng = np.random.default_rng(4)
+    x = rng.uniform(-1.1, 1.1, (300, 3)).astype(np.float32)
+    phi, g = oc.query_sdf(cfg, th, x)
+    h = np.float32(1e-3)
+    checked = 0
+    for a in range(3):
+        xp, xm = x.copy(), x.copy()
+        xp[:, a] += h
+        xm[:, a] -= h
+        same = np.all(oc.voxel_index(cfg, xp) == oc.voxel_index(cfg, xm), axis=1)
+        fp, _ = oc.query_sdf(cfg, th, xp, want_grad=False)
+        fm, _ = oc.query_sdf(cfg, th, xm, want_grad=False)
+        fd = (fp - fm) / (xp[:, a].astype(np.float64) - xm[:, a].astype(np.float64))
+        np.testing.assert_allclose(fd[same], g[same, a], rtol=1e-6, atol=1e-7)
+        checked += same.sum()
+    assert checked > 600
+
+
+def test_paper_query_backward_matches_central_differences(tiny_paper):
+    """d/dtheta of sum dsdf phi + dgrad . grad_x phi (both terms, and the second alone)."""
+    cfg, _, _, th = tiny_paper
+    offs, n_grid, n_tot = TINY_P.layout()
+    rng = np.random.default_rng(5)
+    x = rng.uniform(-1.0, 1.0, (40, 3)).astype(np.float32)
+    dsdf, dgrad = rng.normal(size=40), rng.normal(size=(40, 3))
+    for ds in (dsdf, None):
+        g = oc.query_sdf_backward(cfg, th, x, ds, dgrad)
+
+        def obj(t):
+            p, gr = oc.query_sdf(cfg, t, x)
+            return (0.0 if ds is None else float(p @ ds)) + float((gr * dgrad).sum())
+
+        idx = np.r_[np.nonzero(g[:n_grid])[0][::5], np.arange(n_grid, n_tot, 3)]
+        fd = []
+        for i in idx:
+            t = th.copy()
+            t[i] += 1e-6
+            fp = obj(t)
+            t[i] -= 2e-6
+            fd.append((fp - obj(t)) / 2e-6)
+        fd = np.array(fd)
+        assert np.abs(fd - g[idx]).max() <= 1e-6 * np.abs(g[idx]).max()
+        m = sg.mlp_views(g, n_grid, sg.PAPER_MLP_SHAPES)
+        assert all(np.abs(m[k]).max() == 0 for k in ("cW1", "cb1", "cW2", "cb2", "cW3", "cb3", "kappa"))
+        assert np.abs(g[TINY_P.colour_offset():n_grid]).max() == 0
+
+
+def test_paper_eikonal_affine_closed_form_and_central_differences(tiny_paper):
+    """L_eik = (1 - |n|)^2 for phi = n . x + c; the gradient matches central differences."""
+    n = np.array([0.3, -0.6, 0.2])
+    th = _affine_passthrough(CUBE_P, n)
+    bt = _plane_batch(0.0)
+    le, _, nfs, gn = oc.eikonal(oc.make_config(CUBE_P), th, bt, want_grad=False)
+    assert nfs > 0 and abs(le - (1 - np.linalg.norm(n)) ** 2) < 1e-7  # binary32 vertex values
+    cfg, bt2, _, th2 = tiny_paper
+    offs, n_grid, n_tot = TINY_P.layout()
+    le, g, nfs, _ = oc.eikonal(cfg, th2, bt2)
+    assert nfs > 10 and le > 0
+    idx = np.r_[np.nonzero(g[:n_grid])[0][::3], np.arange(n_grid, n_tot, 2)]
+    fd = []
+    for i in idx:
+        t = th2.copy()
+        t[i] += 1e-6
+        fp = oc.eikonal(cfg, t, bt2, want_grad=False)[0]
+        t[i] -= 2e-6
+        fd.append((fp - oc.eikonal(cfg, t, bt2, want_grad=False)[0]) / 2e-6)
+    assert np.abs(np.array(fd) - g[idx]).max() <= 1e-6 * np.abs(g[idx]).max()
+
+
+def _compact_twin(th_paper, w_paper, w_compact, kappa):
+    """The workload's model with the same geometry grid and a pass-through decoder of z[12]."""
+    from helpers import passthrough_decoder
+    th = np.zeros(w_compact.layout()[2], np.float32)
+    ng = w_compact.layout()[1]
+    th[:ng] = th_paper[:ng]
+    return passthrough_decoder(w_compact, th, 12, kappa=kappa)
+
+
+def test_paper_importance_sampler_reduces_to_the_workload_model():
+    """With phi = z[12] in both models (same geometry grid, same kappa) the importance
+    sampler draws the same depths for the paper's architecture as for the workload's."""
+    wp = CUBE_P.with_(imp_coarse=32, imp_steps=2, imp_per_step=8, rays=64)
+    wc = CUBE.with_(imp_coarse=32, imp_steps=2, imp_per_step=8, rays=64)
+    fr = sg.make_frames(wp)
+    th_p = np.zeros(wp.layout()[2], np.float32)
+    set_level_field(wp, th_p, 3, 0, lambda X: np.linalg.norm(X - [-0.4, 0, 0], axis=-1) - 0.5)
+    passthrough_paper(wp, th_p, zindex=12, kappa=math.log(60.0))
+    th_c = _compact_twin(th_p, wp, wc, math.log(60.0))
+    outs = []
+    for w, th in ((wp, th_p), (wc, th_c)):
+        cfg = oc.make_config(w)
+        outs.append(oc.sample_importance(cfg, oc.OcFramesHolder(fr), th, 3, 1, w.rays, 32, 2, 8))
+    a, b = outs
+    np.testing.assert_allclose(a["phi"], b["phi"], atol=1e-12)
+    same = (a["t"] == b["t"]).mean()
+    assert same > 0.999 and np.abs(a["t"] - b["t"]).max() < 1e-5
+
+
+def test_paper_mesh_reduces_to_the_workload_model():
+    """With phi = z[12] in both models the lattice values agree to rounding and the
+    isosurface has the same triangles."""
+    th_p = np.zeros(CUBE_P.layout()[2], np.float32)
+    set_level_field(CUBE_P, th_p, 3, 0, lambda X: np.linalg.norm(X - [-0.4, 0, 0], axis=-1) - 0.5)
+    passthrough_paper(CUBE_P, th_p, zindex=12)
+    th_c = _compact_twin(th_p, CUBE_P, CUBE, math.log(20.0))
+    lo, step, dims = (-1.0, -0.7, -0.7), 0.05, (25, 29, 29)
+    tp, pp = oc.extract_mesh(oc.make_config(CUBE_P), th_p, lo, step, dims)
+    tc, pc = oc.extract_mesh(oc.make_config(CUBE), th_c, lo, step, dims)
+    np.testing.assert_allclose(pp, pc, atol=1e-12)
+    assert len(tp) == len(tc) > 500
