@@ -78,9 +78,11 @@ typedef enum {
                              15-32-3 fed the geometric features: the workload's model */
 #define GS_ARCH_PAPER 1   /* the paper's (Sec. 3.1): colour grid W_beta at the finest level, colour decoder
                              fed W_beta(x) and the viewing direction, both decoders with two hidden layers
-                             of 32.  Supported by gs_sample_rays, gs_forward, gs_backward,
-                             gs_forward_backward and gs_adam_step (FP32, activations recomputed); the other
-                             model entry points return GS_ERR_UNSUPPORTED */
+                             of 32.  Supported by gs_sample_rays, gs_sample_importance, gs_forward,
+                             gs_backward, gs_forward_backward, gs_eikonal, gs_query_sdf, gs_extract_mesh and
+                             gs_adam_step (FP32, activations recomputed); gs_query_sdf_backward,
+                             gs_pose_backward, the proposal sampler and gs_forward_backward_noalloc return
+                             GS_ERR_UNSUPPORTED */
 
 /* Sample classes written by gs_sample_rays (Sec. 3.3): */
 #define GS_CLS_NONE 0 /* no SDF supervision (behind the surface, or the ray has no depth) */

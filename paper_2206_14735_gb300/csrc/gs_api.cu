@@ -111,11 +111,9 @@ gs_status gs_create(const gs_config* cfg, gs_ctx** out) {
     return fail(nullptr, GS_ERR_INVALID_ARG, "gs_create: need 2 <= prop_samples <= 32 and 0 <= prop_guided < prop_samples");
   if (cfg->arch != GS_ARCH_COMPACT && cfg->arch != GS_ARCH_PAPER)
     return fail(nullptr, GS_ERR_INVALID_ARG, "gs_create: arch must be GS_ARCH_COMPACT or GS_ARCH_PAPER");
-  if (cfg->arch == GS_ARCH_PAPER &&
-      (cfg->precision != GS_PREC_FP32 || cfg->store_activations || cfg->prop_samples || cfg->imp_coarse))
+  if (cfg->arch == GS_ARCH_PAPER && (cfg->precision != GS_PREC_FP32 || cfg->store_activations || cfg->prop_samples))
     return fail(nullptr, GS_ERR_UNSUPPORTED,
-                "gs_create: GS_ARCH_PAPER runs in FP32 with recomputed activations, without the proposal or "
-                "importance samplers");
+                "gs_create: GS_ARCH_PAPER runs in FP32 with recomputed activations, without the proposal sampler");
 
   gs_ctx* c = new (std::nothrow) gs_ctx();
   if (!c) return fail(nullptr, GS_ERR_INVALID_ARG, "gs_create: out of host memory");
@@ -313,13 +311,14 @@ gs_status gs_adam_step(gs_ctx* ctx, float* theta, float* grad, float* m, float* 
 gs_status gs_query_sdf(gs_ctx* ctx, const float* theta, const float* x, int32_t P, float* sdf, float* grad,
                        void* stream) {
   if (!ctx) return fail(nullptr, GS_ERR_INVALID_ARG, "gs_query_sdf: ctx is NULL");
-  if (ctx->cfg.arch != GS_ARCH_COMPACT) return compact_only(ctx, "gs_query_sdf");
   if (P < 0) return fail(ctx, GS_ERR_SHAPE, "gs_query_sdf: P < 0");
   if (P > 0 && (!theta || !x || !sdf)) return fail(ctx, GS_ERR_INVALID_ARG, "gs_query_sdf: NULL array");
   if (P > 0 && !aligned16(theta)) return fail(ctx, GS_ERR_ALIGN, "gs_query_sdf: theta is not 16-byte aligned");
   cudaStream_t st = (cudaStream_t)stream;
   ctx->last_stream = st;
-  if (gs_launch_query(ctx, theta, x, P, sdf, grad, st) != GS_OK) return cuda_fail(ctx, "gs_query_sdf");
+  const gs_status qs = ctx->cfg.arch == GS_ARCH_PAPER ? gs_launch_paper_query(ctx, theta, x, P, sdf, grad, st)
+                                                      : gs_launch_query(ctx, theta, x, P, sdf, grad, st);
+  if (qs != GS_OK) return cuda_fail(ctx, "gs_query_sdf");
   return GS_OK;
 }
 
@@ -393,7 +392,6 @@ gs_status gs_query_sdf_backward(gs_ctx* ctx, const float* theta, const float* x,
 gs_status gs_eikonal(gs_ctx* ctx, const float* theta, const gs_batch* batch, const float* dloss, float* loss,
                      float* grad, void* stream) {
   if (!ctx) return fail(nullptr, GS_ERR_INVALID_ARG, "gs_eikonal: ctx is NULL");
-  if (ctx->cfg.arch != GS_ARCH_COMPACT) return compact_only(ctx, "gs_eikonal");
   if (!theta) return fail(ctx, GS_ERR_INVALID_ARG, "gs_eikonal: theta is NULL");
   if (!loss && !grad) return fail(ctx, GS_ERR_INVALID_ARG, "gs_eikonal: loss and grad are both NULL");
   if (!aligned16(theta) || (grad && !aligned16(grad)))
@@ -403,7 +401,9 @@ gs_status gs_eikonal(gs_ctx* ctx, const float* theta, const gs_batch* batch, con
   cudaStream_t st = (cudaStream_t)stream;
   ctx->last_stream = st;
   const float* dl = dloss ? dloss : ctx->default_dloss + 5;  // 1.0
-  if (gs_launch_eikonal(ctx, theta, batch, dl, loss, grad, st) != GS_OK) return cuda_fail(ctx, "gs_eikonal");
+  const gs_status es = ctx->cfg.arch == GS_ARCH_PAPER ? gs_launch_paper_eikonal(ctx, theta, batch, dl, loss, grad, st)
+                                                      : gs_launch_eikonal(ctx, theta, batch, dl, loss, grad, st);
+  if (es != GS_OK) return cuda_fail(ctx, "gs_eikonal");
   return GS_OK;
 }
 
@@ -440,7 +440,6 @@ gs_status gs_extract_mesh(gs_ctx* ctx, const float* theta, const float* lo, floa
                           int32_t nz, float iso, float* phi, float* tris, int64_t max_tris, int64_t* n_tris,
                           void* stream) {
   if (!ctx) return fail(nullptr, GS_ERR_INVALID_ARG, "gs_extract_mesh: ctx is NULL");
-  if (ctx->cfg.arch != GS_ARCH_COMPACT) return compact_only(ctx, "gs_extract_mesh");
   if (!theta || !lo || !phi || !n_tris) return fail(ctx, GS_ERR_INVALID_ARG, "gs_extract_mesh: NULL argument");
   if (max_tris < 0 || (max_tris > 0 && !tris)) return fail(ctx, GS_ERR_INVALID_ARG, "gs_extract_mesh: bad tris / max_tris");
   if (nx < 2 || ny < 2 || nz < 2 || !(step > 0.0f)) return fail(ctx, GS_ERR_SHAPE, "gs_extract_mesh: need nx, ny, nz >= 2 and step > 0");

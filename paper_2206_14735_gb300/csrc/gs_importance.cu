@@ -15,6 +15,7 @@
 // of layer 2).  The sample lists live in shared memory, double-buffered per warp.
 #include <algorithm>
 
+#include "gs_paper.cuh"
 #include "gs_sample.cuh"
 
 namespace gs {
@@ -37,23 +38,31 @@ struct ImpArgs {
   int* counts;
 };
 
+// kPaper: phi from the paper's two-hidden-layer geometry decoder (GS_ARCH_PAPER) instead of
+// the workload's decoder
+template <bool kPaper>
 __global__ void __launch_bounds__(kImpWarps * 32, 1) importance_kernel(ImpArgs a) {
-  __shared__ __align__(16) float sm[sb2 + 4];  // W1 | b1 | W2 row 0 | b2[0]
+  // workload decoder: W1 | b1 | W2 row 0 | b2[0]; paper: the geometry decoder block
+  __shared__ __align__(16) float sm[kPaper ? paper::kGeoPad : sb2 + 4];
   __shared__ float ts[kImpWarps][2][kImpMax], ps[kImpWarps][2][kImpMax];
   __shared__ float cs[kImpWarps][kImpMax];   // mass left of each interval (unnormalised)
   __shared__ float tn[kImpWarps][32];        // this step's new depths
   const float* mlp = a.theta + a.g.n_grid;
-  for (int i = threadIdx.x; i <= sb2; i += blockDim.x) {
-    float v = 0.f;
-    if (i < sb1) v = mlp[oW1 + i];
-    else if (i < sW2) v = mlp[ob1 + i - sb1];
-    else if (i < sW2 + kH1) v = mlp[oW2 + i - sW2];
-    else if (i == sb2) v = mlp[ob2];
-    sm[i] = v;
+  if (kPaper) {
+    paper::load_geometry_decoder(mlp, sm);
+  } else {
+    for (int i = threadIdx.x; i <= sb2; i += blockDim.x) {
+      float v = 0.f;
+      if (i < sb1) v = mlp[oW1 + i];
+      else if (i < sW2) v = mlp[ob1 + i - sb1];
+      else if (i < sW2 + kH1) v = mlp[oW2 + i - sW2];
+      else if (i == sb2) v = mlp[ob2];
+      sm[i] = v;
+    }
   }
   __syncthreads();
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const float s_sharp = expf(mlp[oKappa]);
+  const float s_sharp = expf(mlp[kPaper ? paper::A_kappa : oKappa]);
   int nd = 0, ntr = 0, nfs = 0;
   for (int i = blockIdx.x * kImpWarps + warp; i < a.R; i += gridDim.x * kImpWarps) {  // warp-uniform
     const uint64_t pre = draw_prefix(a.seed, 0, a.step, (uint64_t)i);
@@ -81,7 +90,7 @@ __global__ void __launch_bounds__(kImpWarps * 32, 1) importance_kernel(ImpArgs a
       float x[3];
       sample_pos(o, r, tk, x);
       ts[warp][0][k] = tk;
-      ps[warp][0][k] = sdf_at(a.g, a.theta, sm, x);
+      ps[warp][0][k] = kPaper ? paper::phi_at(a.g, a.theta, sm, x) : sdf_at(a.g, a.theta, sm, x);
     }
     __syncwarp();
     int n = a.Nc, cur = 0;
@@ -150,7 +159,7 @@ __global__ void __launch_bounds__(kImpWarps * 32, 1) importance_kernel(ImpArgs a
         tj = fminf(fmaxf(Tc[lo] + f * (Tc[lo + 1] - Tc[lo]), Tc[lo]), Tc[lo + 1]);
         float x[3];
         sample_pos(o, r, tj, x);
-        pj = sdf_at(a.g, a.theta, sm, x);
+        pj = kPaper ? paper::phi_at(a.g, a.theta, sm, x) : sdf_at(a.g, a.theta, sm, x);
         tn[warp][lane] = tj;
       }
       __syncwarp();
@@ -223,7 +232,8 @@ gs_status gs_launch_importance(const gs_ctx* ctx, const float* theta, const gs_f
     a.cls = b->cls;
     a.counts = b->counts;
     const int blocks = (int)std::min<long long>(((long long)b->R + kImpWarps - 1) / kImpWarps, 16LL * ctx->num_sms);
-    importance_kernel<<<blocks, kImpWarps * 32, 0, st>>>(a);
+    if (ctx->cfg.arch == GS_ARCH_PAPER) importance_kernel<true><<<blocks, kImpWarps * 32, 0, st>>>(a);
+    else importance_kernel<false><<<blocks, kImpWarps * 32, 0, st>>>(a);
     if (cudaPeekAtLastError() != cudaSuccess) return GS_ERR_CUDA;
   }
   return gs_launch_sample_smooth(ctx, f, seed, step, b, st);

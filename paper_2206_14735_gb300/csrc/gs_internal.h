@@ -86,3 +86,7 @@ int gs_paper_part_rows(int num_sms);
 size_t gs_paper_part_floats(int num_sms);
 gs_status gs_launch_paper(const gs_ctx* ctx, const float* theta, const gs_batch* b, const float* dloss, float* grad,
                           float* loss, float* rgb_hat, float* d_hat, float* wsum, int mode, cudaStream_t st);
+gs_status gs_launch_paper_eikonal(const gs_ctx* ctx, const float* theta, const gs_batch* b, const float* dloss,
+                                  float* loss, float* grad, cudaStream_t st);
+gs_status gs_launch_paper_query(const gs_ctx* ctx, const float* theta, const float* x, int P, float* sdf, float* grad,
+                                cudaStream_t st);

@@ -13,6 +13,7 @@
 #include <algorithm>
 
 #include "gs_internal.h"
+#include "gs_paper.cuh"
 
 namespace gs {
 
@@ -25,16 +26,22 @@ struct LatticeArgs {
   float* phi;
 };
 
+// kPaper: phi from the paper's two-hidden-layer geometry decoder (GS_ARCH_PAPER)
+template <bool kPaper>
 __global__ void __launch_bounds__(128) lattice_sdf_kernel(LatticeArgs a) {
-  __shared__ __align__(16) float sm[sb2 + 4];
+  __shared__ __align__(16) float sm[kPaper ? paper::kGeoPad : sb2 + 4];
   const float* mlp = a.theta + a.g.n_grid;
-  for (int i = threadIdx.x; i <= sb2; i += blockDim.x) {
-    float v = 0.f;
-    if (i < sb1) v = mlp[oW1 + i];
-    else if (i < sW2) v = mlp[ob1 + i - sb1];
-    else if (i < sW2 + kH1) v = mlp[oW2 + i - sW2];
-    else if (i == sb2) v = mlp[ob2];
-    sm[i] = v;
+  if (kPaper) {
+    paper::load_geometry_decoder(mlp, sm);
+  } else {
+    for (int i = threadIdx.x; i <= sb2; i += blockDim.x) {
+      float v = 0.f;
+      if (i < sb1) v = mlp[oW1 + i];
+      else if (i < sW2) v = mlp[ob1 + i - sb1];
+      else if (i < sW2 + kH1) v = mlp[oW2 + i - sW2];
+      else if (i == sb2) v = mlp[ob2];
+      sm[i] = v;
+    }
   }
   __syncthreads();
   const long long np = (long long)a.nx * a.ny * a.nz;
@@ -42,7 +49,7 @@ __global__ void __launch_bounds__(128) lattice_sdf_kernel(LatticeArgs a) {
     const int i = (int)(id % a.nx), j = (int)((id / a.nx) % a.ny), k = (int)(id / ((long long)a.nx * a.ny));
     const float x[3] = {__fadd_rn(a.lo[0], __fmul_rn((float)i, a.step)), __fadd_rn(a.lo[1], __fmul_rn((float)j, a.step)),
                         __fadd_rn(a.lo[2], __fmul_rn((float)k, a.step))};
-    a.phi[id] = sdf_at(a.g, a.theta, sm, x);
+    a.phi[id] = kPaper ? paper::phi_at(a.g, a.theta, sm, x) : sdf_at(a.g, a.theta, sm, x);
   }
 }
 
@@ -174,7 +181,8 @@ gs_status gs_launch_mesh(const gs_ctx* ctx, const float* theta, const float lo[3
   la.phi = phi;
   const long long np = (long long)nx * ny * nz;
   const int blocks = (int)std::min<long long>((np + 127) / 128, 64LL * ctx->num_sms);
-  lattice_sdf_kernel<<<blocks, 128, 0, st>>>(la);
+  if (ctx->cfg.arch == GS_ARCH_PAPER) lattice_sdf_kernel<true><<<blocks, 128, 0, st>>>(la);
+  else lattice_sdf_kernel<false><<<blocks, 128, 0, st>>>(la);
   MeshArgs ma;
   for (int q = 0; q < 3; ++q) ma.lo[q] = lo[q];
   ma.step = step;

@@ -14,26 +14,10 @@
 //                        evaluation (x or x + eps of 16 points per warp);
 //   paper_combine_kernel per-CTA partial rows combined in a fixed order (losses in FP64).
 #include "gs_internal.h"
+#include "gs_paper.cuh"
 
 namespace gs {
 namespace paper {
-
-constexpr int kH = 32;              // neurons per hidden layer
-constexpr int kC = GS_COLOUR_FEAT;  // colour features
-constexpr int kU = kC + 3;          // colour decoder input [W_beta(x), d]
-
-// decoder block offsets in the flat parameter vector (header layout)
-constexpr int A_gW1 = 0, A_gb1 = A_gW1 + kH * kZ, A_gW2 = A_gb1 + kH, A_gb2 = A_gW2 + kH * kH, A_gw3 = A_gb2 + kH,
-              A_gb3 = A_gw3 + kH, A_cW1 = A_gb3 + 1, A_cb1 = A_cW1 + kH * kU, A_cW2 = A_cb1 + kH,
-              A_cb2 = A_cW2 + kH * kH, A_cW3 = A_cb2 + kH, A_cb3 = A_cW3 + 3 * kH, A_kappa = A_cb3 + 3;
-static_assert(A_kappa + 1 == GS_PAPER_MLP_PARAMS, "paper decoder layout");
-
-// shared-memory copy: the matrices whose rows are read as float4 (gW1, gW2, gw3, cW2, cW3)
-// start on 16-byte boundaries
-constexpr int S_gW1 = 0, S_gb1 = 512, S_gW2 = 544, S_gb2 = 1568, S_gw3 = 1600, S_gb3 = 1632, S_cW1 = 1636,
-              S_cb1 = 1924, S_cW2 = 1956, S_cb2 = 2980, S_cW3 = 3012, S_cb3 = 3108, S_kappa = 3111, kSm = 3112;
-static_assert(S_gW2 % 4 == 0 && S_gw3 % 4 == 0 && S_cW2 % 4 == 0 && S_cW3 % 4 == 0, "float4 rows");
-constexpr int kPart = 3112;  // per-CTA decoder-gradient partial row (>= GS_PAPER_MLP_PARAMS)
 
 // One block of the decoder: its range in the flat vector, its start in shared memory, and
 // (matrices with 32 rows) its column count.  The gradient accumulators of those matrices
@@ -123,10 +107,6 @@ __device__ __forceinline__ void outer_rows(const float* wr, int fd, int fa, floa
   if (kBias) atomicAdd(acc_b + lane, ab);
 }
 
-__device__ __forceinline__ float4 ld4(const float* p) { return *reinterpret_cast<const float4*>(p); }
-__device__ __forceinline__ void st4(float* p, float a, float b, float c, float d) {
-  *reinterpret_cast<float4*>(p) = make_float4(a, b, c, d);
-}
 
 // geometry features z (4 levels x 4) and colour features cf (level-3 cell, 6) at x
 __device__ __forceinline__ void gather(const Args& a, const float x[3], float z[kZ], float cf[kC]) {
@@ -638,39 +618,11 @@ __global__ void __launch_bounds__(kThreads, kCtasPerSm) paper_render_kernel(Args
   write_partials(a, sG, sL);
 }
 
-// Smoothness term on S_g (Sec. 3.3 Eq. smoothness_loss) and its second-order adjoint
-// (Supp. Sec. 1) for the two-hidden-layer geometry decoder.  Lane l of a warp evaluates
-// point 16 * group + (l & 15) at x (l < 16) or x + eps (l >= 16):
-//   g = grad_x phi = sum_k p_k dz_k/dx, p = gW1^T (m1 (.) gW2^T (m2 (.) gw3)).
-// The adjoint a = dL/dg gives the grid term p_{l,f} (1/v_l) (a . dw_c/df) and the decoder
-// terms gW1 += pm j^T, gW2 += e vj^T, gw3 += m2 (.) gW2 vj with j_k = a . dz_k/dx,
-// pm = m1 (.) gW2^T e, e = m2 (.) gw3, vj = m1 (.) gW1 j (biases get none).
-__global__ void __launch_bounds__(kThreads, 1) paper_smooth_kernel(Args a) {
-  extern __shared__ __align__(16) float smem[];
-  float* sW = smem;
-  float* sG = sW + kSm;
-  float* sL = sG + kSm;
-  float* rows = sL + 8;
-  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-  float* wr = rows + wid * 32 * kRow;
-  float* my = wr + lane * kRow;
-  copy_decoder(a.theta + a.g.n_grid, sW);
-  for (int i = threadIdx.x; i < kSm; i += blockDim.x) sG[i] = 0.f;
-  if (threadIdx.x < 8) sL[threadIdx.x] = 0.f;
-  __syncthreads();
-  const bool bwd = (a.mode & 2) != 0;
-  const int n_g = a.counts[3];
-  const float w4 = a.dloss[4] + a.lam[4] * a.dloss[5];
-  const int ev = lane >> 4;
-  float lsum = 0.f;
-  for (int grp = blockIdx.x * kWarps + wid; grp * 16 < a.P; grp += gridDim.x * kWarps) {
-    const int p = grp * 16 + (lane & 15);
-    const bool ok = p < a.P && a.valid[p] != 0;
-    float y[3] = {0.f, 0.f, 0.f};
-    if (ok) {
-#pragma unroll
-      for (int q = 0; q < 3; ++q) y[q] = ev ? __fadd_rn(a.xs[3 * p + q], a.eps[3 * p + q]) : a.xs[3 * p + q];
-    }
+// One lane, one point y: g = grad_x phi(y) = sum_k p_k dz_k/dx for the geometry decoder,
+// p = gW1^T pm, pm = m1 (.) gW2^T e, e = m2 (.) gw3 (masks m1, m2 of the two hidden layers);
+// e and pm are staged in the lane's row (fields A2, A1) for grad_phi_adjoint.
+__device__ __forceinline__ void grad_phi_fwd(const Args& a, const float* sW, float* my, const float y[3],
+                                             unsigned& m1, unsigned& m2, float pz[kZ], float g[3]) {
     // z; the x-derivatives dz/dx are gathered again level by level where they are used
     // (keeping all 48 of them in registers beside the decoder sensitivities spills)
     float z[kZ];
@@ -689,7 +641,8 @@ __global__ void __launch_bounds__(kThreads, 1) paper_smooth_kernel(Args a) {
       z[4 * l + 3] = acc.w;
     }
     // forward masks
-    unsigned m1 = 0u, m2 = 0u;
+    m1 = 0u;
+    m2 = 0u;
     {
       float h[kH];
 #pragma unroll
@@ -721,7 +674,6 @@ __global__ void __launch_bounds__(kThreads, 1) paper_smooth_kernel(Args a) {
       }
     }
     // e = m2 (.) gw3 (row field A2), pm = m1 (.) gW2^T e (row field A1), p = gW1^T pm
-    float pz[kZ];
     {
       float pm[kH];
 #pragma unroll
@@ -763,7 +715,7 @@ __global__ void __launch_bounds__(kThreads, 1) paper_smooth_kernel(Args a) {
         }
       }
     }
-    float g[3] = {0.f, 0.f, 0.f};
+    g[0] = g[1] = g[2] = 0.f;
 #pragma unroll
     for (int l = 0; l < kLevels; ++l) {
       float4 dl[3];
@@ -773,20 +725,16 @@ __global__ void __launch_bounds__(kThreads, 1) paper_smooth_kernel(Args a) {
       for (int q = 0; q < 3; ++q)
         g[q] += pz[4 * l] * dl[q].x + pz[4 * l + 1] * dl[q].y + pz[4 * l + 2] * dl[q].z + pz[4 * l + 3] * dl[q].w;
     }
-    float dg[3];
-#pragma unroll
-    for (int q = 0; q < 3; ++q) {
-      const float other = __shfl_xor_sync(0xffffffffu, g[q], 16);
-      dg[q] = ev ? other - g[q] : g[q] - other;  // g(x) - g(x + eps) on both lanes
-    }
-    if (ok && ev == 0) lsum += dg[0] * dg[0] + dg[1] * dg[1] + dg[2] * dg[2];
-    if (!bwd) continue;
-    float av[3] = {0.f, 0.f, 0.f};
-    if (ok && n_g > 0) {
-      const float sc = (ev ? -2.f : 2.f) * w4 / (float)n_g;
-#pragma unroll
-      for (int q = 0; q < 3; ++q) av[q] = sc * dg[q];
-    }
+}
+
+// The second-order adjoint (Supp. Sec. 1) of sum over the warp's lanes of a . grad_x phi(y)
+// with respect to the grid and the geometry decoder: j_k = a . dz_k/dx, grid term
+// p_{l,f} (1/v_l) (a . dw_c/df) (when do_grid), gW1 += pm j^T, gW2 += e vj^T,
+// gw3 += m2 (.) gW2 vj with vj = m1 (.) gW1 j; biases get none.  Every lane of the warp
+// calls it (a lane with av = 0 adds nothing); its row holds e and pm from grad_phi_fwd.
+__device__ __forceinline__ void grad_phi_adjoint(const Args& a, const float* sW, float* sG, const float* wr, float* my,
+                                                 int lane, const float y[3], bool do_grid, const float av[3],
+                                                 unsigned m1, unsigned m2, const float pz[kZ]) {
     float jv[kZ];  // j_k = a . dz_k/dx
 #pragma unroll
     for (int l = 0; l < kLevels; ++l) {
@@ -849,7 +797,7 @@ __global__ void __launch_bounds__(kThreads, 1) paper_smooth_kernel(Args a) {
     }
     __syncwarp();
     // grid term
-    if (ok && n_g > 0) {
+    if (do_grid) {
 #pragma unroll
       for (int l = 0; l < kLevels; ++l) {
         const Cell c = locate(a.g, l, y);
@@ -864,6 +812,59 @@ __global__ void __launch_bounds__(kThreads, 1) paper_smooth_kernel(Args a) {
         }
       }
     }
+}
+
+// Smoothness term on S_g (Sec. 3.3 Eq. smoothness_loss) and its second-order adjoint
+// (Supp. Sec. 1) for the two-hidden-layer geometry decoder.  Lane l of a warp evaluates
+// point 16 * group + (l & 15) at x (l < 16) or x + eps (l >= 16):
+//   g = grad_x phi = sum_k p_k dz_k/dx, p = gW1^T (m1 (.) gW2^T (m2 (.) gw3)).
+// The adjoint a = dL/dg gives the grid term p_{l,f} (1/v_l) (a . dw_c/df) and the decoder
+// terms gW1 += pm j^T, gW2 += e vj^T, gw3 += m2 (.) gW2 vj with j_k = a . dz_k/dx,
+// pm = m1 (.) gW2^T e, e = m2 (.) gw3, vj = m1 (.) gW1 j (biases get none).
+__global__ void __launch_bounds__(kThreads, 1) paper_smooth_kernel(Args a) {
+  extern __shared__ __align__(16) float smem[];
+  float* sW = smem;
+  float* sG = sW + kSm;
+  float* sL = sG + kSm;
+  float* rows = sL + 8;
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  float* wr = rows + wid * 32 * kRow;
+  float* my = wr + lane * kRow;
+  copy_decoder(a.theta + a.g.n_grid, sW);
+  for (int i = threadIdx.x; i < kSm; i += blockDim.x) sG[i] = 0.f;
+  if (threadIdx.x < 8) sL[threadIdx.x] = 0.f;
+  __syncthreads();
+  const bool bwd = (a.mode & 2) != 0;
+  const int n_g = a.counts[3];
+  const float w4 = a.dloss[4] + a.lam[4] * a.dloss[5];
+  const int ev = lane >> 4;
+  float lsum = 0.f;
+  for (int grp = blockIdx.x * kWarps + wid; grp * 16 < a.P; grp += gridDim.x * kWarps) {
+    const int p = grp * 16 + (lane & 15);
+    const bool ok = p < a.P && a.valid[p] != 0;
+    float y[3] = {0.f, 0.f, 0.f};
+    if (ok) {
+#pragma unroll
+      for (int q = 0; q < 3; ++q) y[q] = ev ? __fadd_rn(a.xs[3 * p + q], a.eps[3 * p + q]) : a.xs[3 * p + q];
+    }
+    unsigned m1, m2;
+    float pz[kZ], g[3];
+    grad_phi_fwd(a, sW, my, y, m1, m2, pz, g);
+    float dg[3];
+#pragma unroll
+    for (int q = 0; q < 3; ++q) {
+      const float other = __shfl_xor_sync(0xffffffffu, g[q], 16);
+      dg[q] = ev ? other - g[q] : g[q] - other;  // g(x) - g(x + eps) on both lanes
+    }
+    if (ok && ev == 0) lsum += dg[0] * dg[0] + dg[1] * dg[1] + dg[2] * dg[2];
+    if (!bwd) continue;
+    float av[3] = {0.f, 0.f, 0.f};
+    if (ok && n_g > 0) {
+      const float sc = (ev ? -2.f : 2.f) * w4 / (float)n_g;
+#pragma unroll
+      for (int q = 0; q < 3; ++q) av[q] = sc * dg[q];
+    }
+    grad_phi_adjoint(a, sW, sG, wr, my, lane, y, ok && n_g > 0, av, m1, m2, pz);
   }
   const float v = warp_sum(lsum);
   if (lane == 0) atomicAdd(sL + 4, v);
@@ -871,12 +872,163 @@ __global__ void __launch_bounds__(kThreads, 1) paper_smooth_kernel(Args a) {
   write_partials(a, sG, sL);
 }
 
+// Eikonal term (Sec. 3.3 Eq. eikonal_loss) on the batch's free-space samples, for the
+// two-hidden-layer geometry decoder: l = (1 - |g|)^2 with g = grad_x phi at x = o + d r, and
+// (grad != nullptr) its second-order adjoint a = dloss (-2 / |S_fs|) (1 - |g|) g / |g| (0 where
+// |g| = 0).  Each warp packs the free-space samples of its share of the batch into a queue
+// and evaluates 32 of them at a time, one per lane.  Loss sums go to this CTA's partial row.
+__global__ void __launch_bounds__(kThreads, 1) paper_eikonal_kernel(Args a) {
+  extern __shared__ __align__(16) float smem[];
+  float* sW = smem;
+  float* sG = sW + kSm;
+  float* sL = sG + kSm;
+  float* rows = sL + 8;
+  __shared__ long long queue[kWarps][64];
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  float* wr = rows + wid * 32 * kRow;
+  float* my = wr + lane * kRow;
+  long long* q = queue[wid];
+  copy_decoder(a.theta + a.g.n_grid, sW);
+  for (int i = threadIdx.x; i < kSm; i += blockDim.x) sG[i] = 0.f;
+  if (threadIdx.x < 8) sL[threadIdx.x] = 0.f;
+  __syncthreads();
+  const bool bwd = a.grad != nullptr;
+  const int n_fs = a.counts[2];
+  const float k_eik = n_fs > 0 ? a.dloss[0] * -2.0f / (float)n_fs : 0.0f;
+  const long long S = (long long)a.R * a.N;
+  const long long stride = (long long)gridDim.x * kWarps * 32;
+  long long base = ((long long)blockIdx.x * kWarps + wid) * 32;
+  int queued = 0;
+  float lsum = 0.f;
+#pragma unroll 1
+  for (;;) {
+    while (queued < 32 && base < S) {  // warp-uniform: queued and base are the same in every lane
+      const long long sidx = base + lane;
+      const bool fs = sidx < S && a.cls[sidx] == CLS_FS;
+      const unsigned bal = __ballot_sync(0xffffffffu, fs);
+      if (fs) q[queued + __popc(bal & ((1u << lane) - 1u))] = sidx;
+      queued += __popc(bal);
+      base += stride;
+    }
+    __syncwarp();
+    if (queued == 0) break;
+    const int take = queued < 32 ? queued : 32;
+    const bool ok = lane < take;
+    const long long sidx = ok ? q[lane] : 0;
+    __syncwarp();
+    if (lane + 32 < queued) q[lane] = q[lane + 32];  // at most 31 left over
+    queued -= take;
+    float y[3] = {0.f, 0.f, 0.f};
+    if (ok) {
+      const long long ray = sidx / a.N;
+      float o[3], r[3];
+#pragma unroll
+      for (int c = 0; c < 3; ++c) {
+        o[c] = a.o[3 * ray + c];
+        r[c] = a.r[3 * ray + c];
+      }
+      sample_pos(o, r, a.t[sidx], y);
+    }
+    unsigned m1, m2;
+    float pz[kZ], g[3];
+    grad_phi_fwd(a, sW, my, y, m1, m2, pz, g);
+    const float nrm = sqrtf(g[0] * g[0] + g[1] * g[1] + g[2] * g[2]);
+    if (ok) lsum += (1.f - nrm) * (1.f - nrm);
+    if (!bwd) continue;
+    float av[3] = {0.f, 0.f, 0.f};
+    if (ok && nrm > 0.f) {
+      const float sc = k_eik * (1.f - nrm) / nrm;
+#pragma unroll
+      for (int c = 0; c < 3; ++c) av[c] = sc * g[c];
+    }
+    grad_phi_adjoint(a, sW, sG, wr, my, lane, y, ok, av, m1, m2, pz);
+  }
+  const float v = warp_sum(lsum);
+  if (lane == 0) atomicAdd(sL, v);
+  __syncthreads();
+  write_partials(a, sG, sL);
+}
+
+// phi(x) and (grad != nullptr) grad_x phi(x) of the geometry decoder, one thread per point
+__global__ void __launch_bounds__(128) paper_query_kernel(GridDesc g, const float* __restrict__ theta,
+                                                          const float* __restrict__ xq, int P, float* sdf,
+                                                          float* grad) {
+  __shared__ __align__(16) float sg[kGeoPad];
+  load_geometry_decoder(theta + g.n_grid, sg);
+  __syncthreads();
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= P) return;
+  const float x[3] = {xq[3 * i], xq[3 * i + 1], xq[3 * i + 2]};
+  sdf[i] = phi_at(g, theta, sg, x);
+  if (!grad) return;
+  // p = gW1^T (m1 (.) gW2^T (m2 (.) gw3)), then grad = sum over levels of (dz_l/dx)^T p_l
+  float z[kZ];
+#pragma unroll
+  for (int l = 0; l < kLevels; ++l) {
+    const Cell c = locate(g, l, x);
+    float w[8];
+    corner_weights(c.f, w);
+    const float4* lv = reinterpret_cast<const float4*>(theta + g.off[l]);
+    float4 acc = make_float4(0.f, 0.f, 0.f, 0.f);
+#pragma unroll
+    for (int k = 0; k < 8; ++k) f4fma(acc, w[k], __ldg(lv + c.vtx + corner_offset(g, l, k)));
+    z[4 * l] = acc.x;
+    z[4 * l + 1] = acc.y;
+    z[4 * l + 2] = acc.z;
+    z[4 * l + 3] = acc.w;
+  }
+  float h[kH];
+  unsigned m1 = 0u;
+#pragma unroll
+  for (int j = 0; j < kH; ++j) {
+    float y = sg[S_gb1 + j];
+#pragma unroll
+    for (int k = 0; k < kZ; ++k) y = fmaf(sg[S_gW1 + j * kZ + k], z[k], y);
+    h[j] = fmaxf(y, 0.f);
+    m1 |= (y > 0.f ? 1u : 0u) << j;
+  }
+  float pm[kH];
+#pragma unroll
+  for (int k = 0; k < kH; ++k) pm[k] = 0.f;
+#pragma unroll 1
+  for (int j = 0; j < kH; ++j) {
+    float y = sg[S_gb2 + j];
+#pragma unroll
+    for (int k = 0; k < kH; ++k) y = fmaf(sg[S_gW2 + j * kH + k], h[k], y);
+    const float e = y > 0.f ? sg[S_gw3 + j] : 0.f;
+#pragma unroll
+    for (int k = 0; k < kH; ++k) pm[k] = fmaf(sg[S_gW2 + j * kH + k], e, pm[k]);
+  }
+  float pz[kZ];
+#pragma unroll
+  for (int k = 0; k < kZ; ++k) pz[k] = 0.f;
+#pragma unroll
+  for (int j = 0; j < kH; ++j) {
+    const float pj = (m1 >> j) & 1u ? pm[j] : 0.f;
+#pragma unroll
+    for (int k = 0; k < kZ; ++k) pz[k] = fmaf(sg[S_gW1 + j * kZ + k], pj, pz[k]);
+  }
+  float gr[3] = {0.f, 0.f, 0.f};
+#pragma unroll
+  for (int l = 0; l < kLevels; ++l) {
+    float4 dl[3];
+    float dw[8][3];
+    level_jacobian(g, theta, l, x, dl, dw);
+#pragma unroll
+    for (int c = 0; c < 3; ++c)
+      gr[c] += pz[4 * l] * dl[c].x + pz[4 * l + 1] * dl[c].y + pz[4 * l + 2] * dl[c].z + pz[4 * l + 3] * dl[c].w;
+  }
+#pragma unroll
+  for (int c = 0; c < 3; ++c) grad[3 * i + c] = gr[c];
+}
+
 // combine the per-CTA partial rows: decoder gradients in a fixed order into gmlp, losses
 // in FP64 normalised by the set sizes (rgb: R, depth: rays with D > 0, sdf: |S_tr|,
 // fs: |S_fs|, smooth: valid points) with the weighted total
 __global__ void __launch_bounds__(256) paper_combine_kernel(const float* loss_part, const float* mlp_part,
                                                             int nparts, const int* counts, int R, float l0, float l1,
-                                                            float l2, float l3, float l4, float* loss, float* gmlp) {
+                                                            float l2, float l3, float l4, float* loss, float* gmlp,
+                                                            int eikonal) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (gmlp && i < GS_PAPER_MLP_PARAMS) {
     float sacc = 0.f;
@@ -893,7 +1045,9 @@ __global__ void __launch_bounds__(256) paper_combine_kernel(const float* loss_pa
     for (int k = 0; k < 5; ++k)
 #pragma unroll
       for (int off = 16; off > 0; off >>= 1) sk[k] += __shfl_xor_sync(0xffffffffu, sk[k], off);
-    if (lane == 0) {
+    if (lane == 0 && eikonal) {  // L_eik: the first entry of each row, over |S_fs|
+      loss[0] = counts[2] > 0 ? (float)(sk[0] / (double)counts[2]) : 0.f;
+    } else if (lane == 0) {
       const double den[5] = {(double)R, (double)counts[0], (double)counts[1], (double)counts[2], (double)counts[3]};
       const double lam[5] = {l0, l1, l2, l3, l4};
       double tot = 0.0;
@@ -1006,6 +1160,51 @@ gs_status gs_launch_paper(const gs_ctx* ctx, const float* theta, const gs_batch*
   const float* l = ctx->cfg.lam;
   paper_combine_kernel<<<(GS_PAPER_MLP_PARAMS + 255) / 256, 256, 0, st>>>(
       first_loss, first_mlp, nparts, b->counts, b->R, l[0], l[1], l[2], l[3], l[4], (mode & 1) ? loss : nullptr,
-      (mode & 2) ? grad + ctx->grid.n_grid : nullptr);
+      (mode & 2) ? grad + ctx->grid.n_grid : nullptr, 0);
+  return cudaPeekAtLastError() == cudaSuccess ? GS_OK : GS_ERR_CUDA;
+}
+
+gs_status gs_launch_paper_eikonal(const gs_ctx* ctx, const float* theta, const gs_batch* b, const float* dloss,
+                                  float* loss, float* grad, cudaStream_t st) {
+  using namespace paper;
+  if ((long long)b->R * b->N == 0) {
+    if (loss && cudaMemsetAsync(loss, 0, sizeof(float), st) != cudaSuccess) return GS_ERR_CUDA;
+    return GS_OK;
+  }
+  static bool attr = false;
+  if (!attr) {
+    if (cudaFuncSetAttribute(paper_eikonal_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmemBytes) !=
+        cudaSuccess)
+      return GS_ERR_CUDA;
+    attr = true;
+  }
+  Args a;
+  a.g = ctx->grid;
+  a.colour_off = ctx->colour_off;
+  a.theta = theta;
+  a.grad = grad;
+  a.o = b->origin;
+  a.r = b->dir;
+  a.t = b->t;
+  a.cls = b->cls;
+  a.counts = b->counts;
+  a.dloss = dloss;
+  a.R = b->R;
+  a.N = b->N;
+  a.loss_part = ctx->paper_loss_part;
+  a.mlp_part = ctx->paper_part;
+  const int ctas = kCtasPerSm * ctx->num_sms;  // the render kernel's partial rows (calls do not overlap)
+  paper_eikonal_kernel<<<ctas, kThreads, kSmemBytes, st>>>(a);
+  if (cudaPeekAtLastError() != cudaSuccess) return GS_ERR_CUDA;
+  const float* l = ctx->cfg.lam;
+  paper_combine_kernel<<<(GS_PAPER_MLP_PARAMS + 255) / 256, 256, 0, st>>>(
+      ctx->paper_loss_part, ctx->paper_part, ctas, b->counts, b->R, l[0], l[1], l[2], l[3], l[4], loss,
+      grad ? grad + ctx->grid.n_grid : nullptr, 1);
+  return cudaPeekAtLastError() == cudaSuccess ? GS_OK : GS_ERR_CUDA;
+}
+
+gs_status gs_launch_paper_query(const gs_ctx* ctx, const float* theta, const float* x, int P, float* sdf, float* grad,
+                                cudaStream_t st) {
+  if (P > 0) paper::paper_query_kernel<<<(P + 127) / 128, 128, 0, st>>>(ctx->grid, theta, x, P, sdf, grad);
   return cudaPeekAtLastError() == cudaSuccess ? GS_OK : GS_ERR_CUDA;
 }

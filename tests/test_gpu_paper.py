@@ -161,7 +161,7 @@ def test_paper_rejections():
     th = _padded(sg.paper_sdf_params(CUBE_P, sg.cube_scene(), seed=23))
     x = torch.zeros(4, 3, device="cuda")
     with pytest.raises(gs.GoSurfError, match="GS_ARCH_PAPER"):
-        p.ctx.query_sdf(th, x, torch.empty(4, device="cuda"))
+        p.ctx.query_sdf_backward(th, x, torch.ones(4, device="cuda"), None, torch.zeros_like(th))
     b = gs.Batch.allocate(8, CUBE_P.n_samples, 0, dz=True)
     with pytest.raises(gs.GoSurfError, match="UNSUPPORTED"):
         p.ctx.forward_backward(th, b, None, torch.empty(6, device="cuda"), torch.zeros_like(th))
@@ -187,3 +187,107 @@ def test_paper_room_scale_parity():
     torch.cuda.synchronize()
     _check_loss(loss.cpu().numpy().astype(np.float64), ref["loss"])
     assert_grad_close(p, grad.cpu().numpy()[:len(theta)], ref["grad"])
+
+
+# ----------------------------------------------------------------------------------------
+# the rest of the paper's method with its architecture: SDF query, Eikonal term, the
+# hierarchical importance sampler and mesh extraction
+# ----------------------------------------------------------------------------------------
+def test_paper_query_sdf_parity(cube_paper):
+    c = cube_paper
+    rng = np.random.default_rng(8)
+    x = np.concatenate([rng.uniform(-1.4, 1.4, (3000, 3)), rng.uniform(-0.9, 0.9, (1000, 3))]).astype(np.float32)
+    sdf_ref, g_ref = oc.query_sdf(c["p"].cfg, c["theta"], x)
+    th = _padded(c["theta"])
+    xd = torch.from_numpy(x).cuda()
+    sdf, grad = torch.empty(len(x), device="cuda"), torch.empty(len(x), 3, device="cuda")
+    c["p"].ctx.query_sdf(th, xd, sdf, grad)
+    torch.cuda.synchronize()
+    np.testing.assert_allclose(sdf.cpu().numpy(), sdf_ref, atol=2e-6)
+    np.testing.assert_allclose(grad.cpu().numpy(), g_ref, atol=2e-4 * np.abs(g_ref).max())
+    only = torch.empty(len(x), device="cuda")
+    c["p"].ctx.query_sdf(th, xd, only)  # phi alone
+    torch.cuda.synchronize()
+    assert torch.equal(only, sdf)
+
+
+def _eik_tol(ref_loss, gnorm):
+    n = gnorm[gnorm >= 0]
+    e = 1e-5 * n
+    return float(np.mean(2 * np.abs(1 - n) * e + e * e)) + 1e-6 * ref_loss
+
+
+@pytest.mark.parametrize("R", [None, 77])
+def test_paper_eikonal_parity(cube_paper, R):
+    """L_eik over the free-space samples and its second-order gradient (geometry grid and
+    geometry decoder; the colour parameters get none)."""
+    c = cube_paper
+    bt = c["bt"] if R is None else {k: (v[:R] if k != "counts" else v) for k, v in c["bt"].items()}
+    ref_l, ref_g, n_fs, gnorm = oc.eikonal(c["p"].cfg, c["theta"], bt)
+    assert n_fs > (1000 if R is None else 20)
+    batch = c["batch"] if R is None else upload_oracle_batch(
+        {**bt, "counts": np.array([(bt["D"] > 0).sum(), (bt["cls"] == 1).sum(), (bt["cls"] == 2).sum(), 0])}, None, 0)
+    th = _padded(c["theta"])
+    loss, grad = torch.full((1,), float("nan"), device="cuda"), torch.zeros_like(th)
+    c["p"].ctx.eikonal(th, batch, loss=loss, grad=grad)
+    torch.cuda.synchronize()
+    assert abs(float(loss.item()) - ref_l) <= _eik_tol(ref_l, gnorm), (float(loss.item()), ref_l)
+    g = grad.cpu().numpy()[:len(c["theta"])]
+    assert_grad_close(c["p"], g, ref_g)
+    assert np.abs(g[CUBE_P.colour_offset():c["p"].n_grid]).max() == 0
+
+
+def test_paper_full_method_step():
+    """The paper's method with its own architecture: the hierarchical importance sampler
+    (96 coarse + 3 x 12, Sec. 4) on the GPU against the oracle, then the fused step and the
+    Eikonal term on the oracle's importance batch against the oracle."""
+    from test_gpu_importance import _check_depth_deviation
+    w = CUBE_P.with_(name="cube-paper-imp", imp_coarse=96, imp_steps=3, imp_per_step=12, rays=512)
+    p = Problem(w)
+    theta = sg.paper_sdf_params(w, sg.cube_scene(), seed=23)
+    th = _padded(theta)
+    b = gs.Batch.allocate(w.rays, w.n_samples, w.n_smooth)
+    p.ctx.sample_importance(p.dfr, th, SEED, STEP, b)
+    torch.cuda.synchronize()
+    p.ctx.sync_status()
+    ref = oc.sample_importance(p.cfg, p.ofr, theta, SEED, STEP, w.rays, 96, 3, 12)
+    assert np.array_equal(b.pix.cpu().numpy(), ref["pix"])
+    tg = b.t.cpu().numpy().astype(np.float64)
+    assert np.all(np.diff(tg, axis=1) >= 0)
+    _check_depth_deviation(tg - ref["t"].astype(np.float64), w.far - w.near, 96)
+    # the step on the oracle's batch (the same depths on both sides)
+    sm = oc.sample_smooth(p.cfg, p.ofr, SEED, STEP, w.n_smooth)
+    bt = {k: ref[k] for k in ("pix", "o", "r", "rgb", "D", "t", "cls", "counts")}
+    bt_s, st_ref, dropped = prepare_parity_batch(p, theta, bt, sm, max_drop=0.2)
+    batch = upload_oracle_batch(bt_s, sm, sm["n_valid"][0])
+    loss, grad = torch.empty(6, device="cuda"), torch.zeros_like(th)
+    p.ctx.forward_backward(th, batch, None, loss, grad)
+    eik, geik = torch.zeros(1, device="cuda"), torch.zeros_like(th)
+    p.ctx.eikonal(th, batch, loss=eik, grad=geik)
+    torch.cuda.synchronize()
+    _check_loss(loss.cpu().numpy().astype(np.float64), st_ref["loss"])
+    assert_grad_close(p, grad.cpu().numpy()[:len(theta)], st_ref["grad"])
+    ref_l, ref_g, n_fs, gnorm = oc.eikonal(p.cfg, theta, bt_s)
+    assert abs(float(eik.item()) - ref_l) <= _eik_tol(ref_l, gnorm)
+    assert_grad_close(p, geik.cpu().numpy()[:len(theta)], ref_g)
+
+
+def test_paper_mesh_matches_oracle():
+    """Mesh extraction from the paper model's phi (a sphere baked into the finest level
+    through a pass-through decoder): lattice values to FP32 rounding, the same triangle count
+    as the oracle."""
+    from test_oracle_paper import passthrough_paper
+    from helpers import set_level_field
+    p = Problem(CUBE_P)
+    th = np.zeros(CUBE_P.layout()[2], np.float32)
+    set_level_field(CUBE_P, th, 3, 0, lambda X: np.linalg.norm(X - [-0.4, 0, 0], axis=-1) - 0.5)
+    passthrough_paper(CUBE_P, th, zindex=12)
+    lo, step, dims = (-1.0, -0.7, -0.7), 0.05, (25, 29, 29)
+    ref, phi_ref = oc.extract_mesh(p.cfg, th, lo, step, dims)
+    phi = torch.empty((dims[2], dims[1], dims[0]), device="cuda")
+    tris, n = p.ctx.extract_mesh(_padded(th), lo, step, dims, phi=phi)
+    torch.cuda.synchronize()
+    np.testing.assert_allclose(phi.cpu().numpy(), phi_ref, atol=2e-6)
+    close = np.abs(phi_ref) < 2e-5
+    assert n == len(ref) or close.any()
+    assert abs(n - len(ref)) <= 2 * close.sum()
