@@ -372,7 +372,8 @@ def run_ours(args):
                 "h2d_bytes_per_step": 24, "d2h_bytes_per_step": 40, "steps": e2e_steps,
                 "what": "per step: H2D dloss seed (pinned), the C-ABI calls of the step, D2H loss and counts into a "
                         "pinned double buffer that the host reads one step later; frames resident on the device"},
-        "gpu_launches": ((9 if args.split else 6) + (1 if args.eikonal else 0) + (3 if args.poses else 0)) * args.steps,
+        "gpu_launches": ((9 if args.split else 6) + ((2 if paper else 1) if args.eikonal else 0) +
+                         (3 if args.poses else 0)) * args.steps,
         "clocks": clk,
         "loss_last": [round(x, 6) for x in lossv],
     }

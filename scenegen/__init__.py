@@ -345,6 +345,11 @@ WORKLOADS["room-prop-bf16-65536x32"] = WORKLOADS["room-prop-65536x32"].with_(nam
 # decoders with two hidden layers of 32
 WORKLOADS["cube-paper-1024x64"] = WORKLOADS["cube-1024x64"].with_(name="cube-paper-1024x64", arch="paper")
 WORKLOADS["room-paper-8192x96"] = WORKLOADS["room-8192x96"].with_(name="room-paper-8192x96", arch="paper")
+# the paper's method as a whole (Sec. 3-4): its architecture, its sampler (96 coarse + 3 x 12)
+# and (bench --eikonal) its Eikonal term
+WORKLOADS["room-paper-imp-8192x132"] = WORKLOADS["room-paper-8192x96"].with_(name="room-paper-imp-8192x132",
+                                                                             imp_coarse=96, imp_steps=3,
+                                                                             imp_per_step=12)
 
 
 @dataclass
