@@ -54,21 +54,13 @@ __device__ __forceinline__ int acc_index(int i) {
 // Per-lane row of staged sample vectors.  Every field starts on a 16-byte boundary and the
 // stride is 4 (mod 32) words, so a lane's float4 access to its own row and a float4 read of
 // one row by the whole warp (broadcast) are both free of bank conflicts.
-// Gradient kernels (smoothness, Eikonal): j (Z), pm (A1), e (A2), vj (R1), m2 (.) gW2 vj (R2).
 constexpr int kRow = 164;
-constexpr int fZ = 0, fA1 = 28, fA2 = 60, fR1 = 92, fR2 = 124;
-static_assert(kRow % 32 == 4 && fA1 % 4 == 0, "row layout");
-// Render kernel: one decoder at a time (geometry, then colour) in a row of 84 floats: its input
-// (z, or u = [W_beta(x), d] padded to 12), its two hidden layers, and its output adjoint (dphi,
-// or dpre[3]).  Stride 92 = 4 x 23: float4 accesses of 8 consecutive lanes hit distinct banks.
-constexpr int kRowR = 92;
-constexpr int gIn = 0, gH1 = 16, gH2 = 48, gD = 80;
-static_assert((kRowR / 4) % 2 == 1 && gH1 % 4 == 0 && gH2 % 4 == 0 && gD % 4 == 0, "render row layout");
+constexpr int fZ = 0, fU = 16, fA1 = 28, fA2 = 60, fR1 = 92, fR2 = 124, fDP = 156;  // fDP: dpre[3], dphi
+static_assert(kRow % 32 == 4 && fU % 4 == 0 && fA1 % 4 == 0 && fDP % 4 == 0, "row layout");
 constexpr int kWarps = 4;  // warps per CTA
 constexpr int kThreads = kWarps * 32;
-constexpr size_t kSmemBytes = sizeof(float) * (2 * kSm + 8 + kWarps * 32 * kRow);    // gradient kernels
-constexpr size_t kSmemBytesR = sizeof(float) * (2 * kSm + 8 + kWarps * 32 * kRowR);  // render kernel
-constexpr int kCtasPerSm = 3;  // render CTAs per SM (shared memory: 3 x 70.3 KB)
+constexpr size_t kSmemBytes = sizeof(float) * (2 * kSm + 8 + kWarps * 32 * kRow);
+constexpr int kCtasPerSm = 2;
 
 struct Args {
   GridDesc g;            // geometry levels; g.n_grid = decoder block offset (after the colour grid)
@@ -90,7 +82,7 @@ struct Args {
 
 // lane j (row j of a 32-row matrix) sums delta_s[j] * act_s[k] over the warp's 32 staged
 // samples for k < K (and delta_s[j] for the bias) and adds them to the CTA accumulators
-template <int K, bool kBias, int ROW = kRow>
+template <int K, bool kBias>
 __device__ __forceinline__ void outer_rows(const float* wr, int fd, int fa, float* acc_m, float* acc_b, int lane) {
   float acc[K];
 #pragma unroll
@@ -98,7 +90,7 @@ __device__ __forceinline__ void outer_rows(const float* wr, int fd, int fa, floa
   float ab = 0.f;
 #pragma unroll 2
   for (int s = 0; s < 32; ++s) {
-    const float* rs = wr + s * ROW;
+    const float* rs = wr + s * kRow;
     const float d = rs[fd + lane];
     ab += d;
 #pragma unroll
@@ -149,8 +141,9 @@ __device__ __forceinline__ void gather(const Args& a, const float x[3], float z[
   }
 }
 
-// both decoders at one sample (forward pass): phi and the colour
-__device__ __forceinline__ void decode(const float* sW, const float z[kZ], const float u[kU], float& phi,
+// both decoders at one sample; with row != nullptr the inputs and hidden activations are
+// staged there (z, u, a1, a2, r1, r2) for the backward pass
+__device__ __forceinline__ void decode(const float* sW, const float z[kZ], const float u[kU], float* row, float& phi,
                                        float col[3]) {
   float h[kH];
 #pragma unroll
@@ -167,20 +160,36 @@ __device__ __forceinline__ void decode(const float* sW, const float z[kZ], const
     h[j] = fmaxf(y, 0.f);
   }
   float p = sW[S_gb3];
-#pragma unroll 4
-  for (int j = 0; j < kH; ++j) {
-    float y = sW[S_gb2 + j];
+#pragma unroll 1
+  for (int j4 = 0; j4 < kH / 4; ++j4) {
+    float yv[4];
 #pragma unroll
-    for (int k4 = 0; k4 < 8; ++k4) {
-      const float4 w = ld4(sW + S_gW2 + j * kH + 4 * k4);
-      y = fmaf(w.x, h[4 * k4], y);
-      y = fmaf(w.y, h[4 * k4 + 1], y);
-      y = fmaf(w.z, h[4 * k4 + 2], y);
-      y = fmaf(w.w, h[4 * k4 + 3], y);
+    for (int q = 0; q < 4; ++q) {
+      const int j = 4 * j4 + q;
+      float y = sW[S_gb2 + j];
+#pragma unroll
+      for (int k4 = 0; k4 < 8; ++k4) {
+        const float4 w = ld4(sW + S_gW2 + j * kH + 4 * k4);
+        y = fmaf(w.x, h[4 * k4], y);
+        y = fmaf(w.y, h[4 * k4 + 1], y);
+        y = fmaf(w.z, h[4 * k4 + 2], y);
+        y = fmaf(w.w, h[4 * k4 + 3], y);
+      }
+      yv[q] = fmaxf(y, 0.f);
+      p = fmaf(sW[S_gw3 + j], yv[q], p);
     }
-    p = fmaf(sW[S_gw3 + j], fmaxf(y, 0.f), p);
+    if (row) st4(row + fA2 + 4 * j4, yv[0], yv[1], yv[2], yv[3]);
   }
   phi = p;
+  if (row) {
+#pragma unroll
+    for (int k4 = 0; k4 < kZ / 4; ++k4) st4(row + fZ + 4 * k4, z[4 * k4], z[4 * k4 + 1], z[4 * k4 + 2], z[4 * k4 + 3]);
+#pragma unroll
+    for (int j4 = 0; j4 < kH / 4; ++j4) st4(row + fA1 + 4 * j4, h[4 * j4], h[4 * j4 + 1], h[4 * j4 + 2], h[4 * j4 + 3]);
+    st4(row + fU, u[0], u[1], u[2], u[3]);
+    st4(row + fU + 4, u[4], u[5], u[6], u[7]);
+    st4(row + fU + 8, u[8], 0.f, 0.f, 0.f);
+  }
 #pragma unroll
   for (int j = 0; j < kH; ++j) {
     float y = sW[S_cb1 + j];
@@ -189,107 +198,33 @@ __device__ __forceinline__ void decode(const float* sW, const float z[kZ], const
     h[j] = fmaxf(y, 0.f);
   }
   float pre[3] = {sW[S_cb3], sW[S_cb3 + 1], sW[S_cb3 + 2]};
-#pragma unroll 4
-  for (int j = 0; j < kH; ++j) {
-    float y = sW[S_cb2 + j];
-#pragma unroll
-    for (int k4 = 0; k4 < 8; ++k4) {
-      const float4 w = ld4(sW + S_cW2 + j * kH + 4 * k4);
-      y = fmaf(w.x, h[4 * k4], y);
-      y = fmaf(w.y, h[4 * k4 + 1], y);
-      y = fmaf(w.z, h[4 * k4 + 2], y);
-      y = fmaf(w.w, h[4 * k4 + 3], y);
-    }
-    y = fmaxf(y, 0.f);
-#pragma unroll
-    for (int i = 0; i < 3; ++i) pre[i] = fmaf(sW[S_cW3 + i * kH + j], y, pre[i]);
-  }
-#pragma unroll
-  for (int i = 0; i < 3; ++i) col[i] = sigmoidf_(pre[i]);
-}
-
-// One decoder's input and hidden layers of one sample into its render row (backward pass):
-// in (gIn, KIN values, zero-padded to a multiple of 4), h1 = relu(W1 in + b1) (gH1),
-// h2 = relu(W2 h1 + b2) (gH2).  W1 rows of KIN floats at w1 (float4-readable when KIN = 16).
-template <int KIN>
-__device__ __forceinline__ void stage_decoder(const float* w1, const float* b1, const float* w2, const float* b2,
-                                              const float (&in)[KIN], float* row) {
-  float h[kH];
-#pragma unroll
-  for (int j = 0; j < kH; ++j) {
-    float y = b1[j];
-    if (KIN % 4 == 0) {
-#pragma unroll
-      for (int k4 = 0; k4 < KIN / 4; ++k4) {
-        const float4 w = ld4(w1 + j * KIN + 4 * k4);
-        y = fmaf(w.x, in[4 * k4], y);
-        y = fmaf(w.y, in[4 * k4 + 1 < KIN ? 4 * k4 + 1 : 0], y);
-        y = fmaf(w.z, in[4 * k4 + 2 < KIN ? 4 * k4 + 2 : 0], y);
-        y = fmaf(w.w, in[4 * k4 + 3 < KIN ? 4 * k4 + 3 : 0], y);
-      }
-    } else {
-#pragma unroll
-      for (int k = 0; k < KIN; ++k) y = fmaf(w1[j * KIN + k], in[k], y);
-    }
-    h[j] = fmaxf(y, 0.f);
-  }
-#pragma unroll
-  for (int k4 = 0; k4 < (KIN + 3) / 4; ++k4)
-    st4(row + gIn + 4 * k4, in[4 * k4], 4 * k4 + 1 < KIN ? in[4 * k4 + 1 < KIN ? 4 * k4 + 1 : 0] : 0.f,
-        4 * k4 + 2 < KIN ? in[4 * k4 + 2 < KIN ? 4 * k4 + 2 : 0] : 0.f,
-        4 * k4 + 3 < KIN ? in[4 * k4 + 3 < KIN ? 4 * k4 + 3 : 0] : 0.f);
-#pragma unroll
-  for (int j4 = 0; j4 < kH / 4; ++j4) st4(row + gH1 + 4 * j4, h[4 * j4], h[4 * j4 + 1], h[4 * j4 + 2], h[4 * j4 + 3]);
 #pragma unroll 1
   for (int j4 = 0; j4 < kH / 4; ++j4) {
     float yv[4];
 #pragma unroll
     for (int q = 0; q < 4; ++q) {
       const int j = 4 * j4 + q;
-      float y = b2[j];
+      float y = sW[S_cb2 + j];
 #pragma unroll
       for (int k4 = 0; k4 < 8; ++k4) {
-        const float4 w = ld4(w2 + j * kH + 4 * k4);
+        const float4 w = ld4(sW + S_cW2 + j * kH + 4 * k4);
         y = fmaf(w.x, h[4 * k4], y);
         y = fmaf(w.y, h[4 * k4 + 1], y);
         y = fmaf(w.z, h[4 * k4 + 2], y);
         y = fmaf(w.w, h[4 * k4 + 3], y);
       }
       yv[q] = fmaxf(y, 0.f);
+#pragma unroll
+      for (int i = 0; i < 3; ++i) pre[i] = fmaf(sW[S_cW3 + i * kH + j], yv[q], pre[i]);
     }
-    st4(row + gH2 + 4 * j4, yv[0], yv[1], yv[2], yv[3]);
+    if (row) st4(row + fR2 + 4 * j4, yv[0], yv[1], yv[2], yv[3]);
   }
-}
-
-// own sample: the adjoint in the row's h2 field (dy2) through W2 [32][32] at w2, masked by h1 > 0,
-// replaces h1 (-> dy1)
-__device__ __forceinline__ void hidden_adjoint(const float* w2, float* my) {
-  float acc[kH];
+  if (row) {
 #pragma unroll
-  for (int q = 0; q < kH; ++q) acc[q] = 0.f;
-#pragma unroll 1
-  for (int j4 = 0; j4 < kH / 4; ++j4) {
-    const float4 dy4 = ld4(my + gH2 + 4 * j4);
-    const float dys[4] = {dy4.x, dy4.y, dy4.z, dy4.w};
-#pragma unroll
-    for (int q = 0; q < 4; ++q) {
-      const int j = 4 * j4 + q;
-#pragma unroll
-      for (int k4 = 0; k4 < 8; ++k4) {
-        const float4 wv = ld4(w2 + j * kH + 4 * k4);
-        acc[4 * k4] = fmaf(wv.x, dys[q], acc[4 * k4]);
-        acc[4 * k4 + 1] = fmaf(wv.y, dys[q], acc[4 * k4 + 1]);
-        acc[4 * k4 + 2] = fmaf(wv.z, dys[q], acc[4 * k4 + 2]);
-        acc[4 * k4 + 3] = fmaf(wv.w, dys[q], acc[4 * k4 + 3]);
-      }
-    }
+    for (int j4 = 0; j4 < kH / 4; ++j4) st4(row + fR1 + 4 * j4, h[4 * j4], h[4 * j4 + 1], h[4 * j4 + 2], h[4 * j4 + 3]);
   }
 #pragma unroll
-  for (int q4 = 0; q4 < kH / 4; ++q4) {
-    const float4 hv = ld4(my + gH1 + 4 * q4);
-    st4(my + gH1 + 4 * q4, hv.x > 0.f ? acc[4 * q4] : 0.f, hv.y > 0.f ? acc[4 * q4 + 1] : 0.f,
-        hv.z > 0.f ? acc[4 * q4 + 2] : 0.f, hv.w > 0.f ? acc[4 * q4 + 3] : 0.f);
-  }
+  for (int i = 0; i < 3; ++i) col[i] = sigmoidf_(pre[i]);
 }
 
 // grid-gradient scatter of one sample: dz into the 4 geometry levels, dcf into the colour grid
@@ -329,8 +264,8 @@ __global__ void __launch_bounds__(kThreads, kCtasPerSm) paper_render_kernel(Args
   float* sL = sG + kSm;
   float* rows = sL + 8;
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-  float* wr = rows + wid * 32 * kRowR;
-  float* my = wr + lane * kRowR;
+  float* wr = rows + wid * 32 * kRow;
+  float* my = wr + lane * kRow;
   copy_decoder(a.theta + a.g.n_grid, sW);
   for (int i = threadIdx.x; i < kSm; i += blockDim.x) sG[i] = 0.f;
   if (threadIdx.x < 8) sL[threadIdx.x] = 0.f;
@@ -354,6 +289,7 @@ __global__ void __launch_bounds__(kThreads, kCtasPerSm) paper_render_kernel(Args
       I[q] = a.rgb[3 * ray + q];
     }
     const float D = a.D[ray];
+    __syncwarp();  // the previous ray's products have read every row before this ray stages its last chunk
     const float rn = sqrtf(r[0] * r[0] + r[1] * r[1] + r[2] * r[2]);
 #pragma unroll
     for (int q = 0; q < 3; ++q) d[q] = r[q] / rn;
@@ -387,7 +323,7 @@ __global__ void __launch_bounds__(kThreads, kCtasPerSm) paper_render_kernel(Args
 #pragma unroll
       for (int q = 0; q < 3; ++q) u[kC + q] = d[q];
       float ph, cc[3];
-      decode(sW, z, u, ph, cc);
+      decode(sW, z, u, bwd && c == NCH - 1 ? my : nullptr, ph, cc);
 #pragma unroll
       for (int q = 0; q < NCH; ++q)
         if (c == q) {
@@ -522,10 +458,10 @@ __global__ void __launch_bounds__(kThreads, kCtasPerSm) paper_render_kernel(Args
     }
 
     // ---------------- decoder adjoints and scatter, chunk by chunk ----------------
-    // Per chunk the sample's features are gathered again; the geometry decoder is recomputed
-    // into the rows and back-propagated, then the colour decoder in the same rows.
+    // Last chunk first: its inputs and activations are still staged in the rows by the
+    // forward pass; the other chunks gather and decode again.
 #pragma unroll 1
-    for (int c = 0; c < NCH; ++c) {
+    for (int c = NCH - 1; c >= 0; --c) {
       const int k = 32 * c + lane;
       const bool ok = k < N;
       float tc = tk[0], wc = w[0], dp = dphi[0], cc[3] = {col[0][0], col[0][1], col[0][2]};
@@ -539,128 +475,135 @@ __global__ void __launch_bounds__(kThreads, kCtasPerSm) paper_render_kernel(Args
           cc[1] = col[q][1];
           cc[2] = col[q][2];
         }
-      float x[3] = {0.f, 0.f, 0.f}, z[kZ], u[kU];
-      if (ok) {
-        sample_pos(o, r, tc, x);
-        gather(a, x, z, u);
-      } else {
+      float x[3] = {0.f, 0.f, 0.f};
+      if (ok) sample_pos(o, r, tc, x);
+      if (c != NCH - 1) {
+        float z[kZ], u[kU];
+        __syncwarp();  // the previous chunk's products have read every row
+        if (ok) {
+          gather(a, x, z, u);
+        } else {
 #pragma unroll
-        for (int q = 0; q < kZ; ++q) z[q] = 0.f;
+          for (int q = 0; q < kZ; ++q) z[q] = 0.f;
 #pragma unroll
-        for (int q = 0; q < kC; ++q) u[q] = 0.f;
+          for (int q = 0; q < kC; ++q) u[q] = 0.f;
+        }
+#pragma unroll
+        for (int q = 0; q < 3; ++q) u[kC + q] = d[q];
+        float ph, c2[3];
+        decode(sW, z, u, my, ph, c2);
       }
-#pragma unroll
-      for (int q = 0; q < 3; ++q) u[kC + q] = d[q];
       float dpre[3];
 #pragma unroll
       for (int q = 0; q < 3; ++q) dpre[q] = ok ? wc * gc[q] * cc[q] * (1.f - cc[q]) : 0.f;
-      float dz[kZ], dcf[kC];
-
-      // ---- geometry decoder: phi = gw3 . a2 + gb3 ----
-      __syncwarp();  // the previous products have read every row
-      stage_decoder<kZ>(sW + S_gW1, sW + S_gb1, sW + S_gW2, sW + S_gb2, z, my);
-      st4(my + gD, dp, 0.f, 0.f, 0.f);
+      st4(my + fDP, dpre[0], dpre[1], dpre[2], dp);
       __syncwarp();
-      {  // gw3 (lane = column), gb3
-        float ag = 0.f, bg = 0.f;
+      {  // output layers: gw3, gb3 (lane = column), cW3, cb3
+        float ag = 0.f, a0 = 0.f, a1 = 0.f, a2 = 0.f, bg = 0.f, b0 = 0.f, b1 = 0.f, b2 = 0.f;
 #pragma unroll 4
         for (int sidx = 0; sidx < 32; ++sidx) {
-          const float* rs = wr + sidx * kRowR;
-          const float dph = rs[gD];
-          ag = fmaf(dph, rs[gH2 + lane], ag);
-          bg += dph;
-        }
-        atomicAdd(sG + S_gw3 + lane, ag);
-        if (lane == 0) atomicAdd(sG + S_gb3, bg);
-      }
-      __syncwarp();
-#pragma unroll
-      for (int j4 = 0; j4 < kH / 4; ++j4) {  // dy2 = m2 (.) gw3 dphi over a2
-        const float4 a2v = ld4(my + gH2 + 4 * j4), w3 = ld4(sW + S_gw3 + 4 * j4);
-        st4(my + gH2 + 4 * j4, a2v.x > 0.f ? w3.x * dp : 0.f, a2v.y > 0.f ? w3.y * dp : 0.f,
-            a2v.z > 0.f ? w3.z * dp : 0.f, a2v.w > 0.f ? w3.w * dp : 0.f);
-      }
-      __syncwarp();
-      outer_rows<kH, true, kRowR>(wr, gH2, gH1, sG + S_gW2, sG + S_gb2, lane);
-      __syncwarp();
-      hidden_adjoint(sW + S_gW2, my);  // dy1 over a1
-      __syncwarp();
-      outer_rows<kZ, true, kRowR>(wr, gH1, gIn, sG + S_gW1, sG + S_gb1, lane);
-#pragma unroll
-      for (int q = 0; q < kZ; ++q) dz[q] = 0.f;
-#pragma unroll 1
-      for (int j4 = 0; j4 < kH / 4; ++j4) {  // dz = gW1^T dy1
-        const float4 dy4 = ld4(my + gH1 + 4 * j4);
-        const float dys[4] = {dy4.x, dy4.y, dy4.z, dy4.w};
-#pragma unroll
-        for (int q = 0; q < 4; ++q) {
-#pragma unroll
-          for (int k4 = 0; k4 < 4; ++k4) {
-            const float4 wv = ld4(sW + S_gW1 + (4 * j4 + q) * kZ + 4 * k4);
-            dz[4 * k4] = fmaf(wv.x, dys[q], dz[4 * k4]);
-            dz[4 * k4 + 1] = fmaf(wv.y, dys[q], dz[4 * k4 + 1]);
-            dz[4 * k4 + 2] = fmaf(wv.z, dys[q], dz[4 * k4 + 2]);
-            dz[4 * k4 + 3] = fmaf(wv.w, dys[q], dz[4 * k4 + 3]);
-          }
-        }
-      }
-
-      // ---- colour decoder: c = sigmoid(cW3 r2 + cb3) ----
-      __syncwarp();
-      stage_decoder<kU>(sW + S_cW1, sW + S_cb1, sW + S_cW2, sW + S_cb2, u, my);
-      st4(my + gD, dpre[0], dpre[1], dpre[2], 0.f);
-      __syncwarp();
-      {  // cW3 (lane = column), cb3
-        float a0 = 0.f, a1 = 0.f, a2 = 0.f, b0 = 0.f, b1 = 0.f, b2 = 0.f;
-#pragma unroll 4
-        for (int sidx = 0; sidx < 32; ++sidx) {
-          const float* rs = wr + sidx * kRowR;
-          const float4 dd = ld4(rs + gD);
-          const float r2 = rs[gH2 + lane];
+          const float* rs = wr + sidx * kRow;
+          const float4 dd = ld4(rs + fDP);  // dpre[0..2], dphi
+          const float r2 = rs[fR2 + lane];
+          ag = fmaf(dd.w, rs[fA2 + lane], ag);
           a0 = fmaf(dd.x, r2, a0);
           a1 = fmaf(dd.y, r2, a1);
           a2 = fmaf(dd.z, r2, a2);
+          bg += dd.w;
           b0 += dd.x;
           b1 += dd.y;
           b2 += dd.z;
         }
+        atomicAdd(sG + S_gw3 + lane, ag);
         atomicAdd(sG + S_cW3 + lane, a0);
         atomicAdd(sG + S_cW3 + kH + lane, a1);
         atomicAdd(sG + S_cW3 + 2 * kH + lane, a2);
         if (lane == 0) {
+          atomicAdd(sG + S_gb3, bg);
           atomicAdd(sG + S_cb3, b0);
           atomicAdd(sG + S_cb3 + 1, b1);
           atomicAdd(sG + S_cb3 + 2, b2);
         }
       }
       __syncwarp();
+      // own sample: dy2 = m2 (.) gw3 dphi over a2; dq2 = m(q2) (.) cW3^T dpre over r2
 #pragma unroll
-      for (int j4 = 0; j4 < kH / 4; ++j4) {  // dq2 = m(q2) (.) cW3^T dpre over r2
-        const float4 r2v = ld4(my + gH2 + 4 * j4), c0 = ld4(sW + S_cW3 + 4 * j4),
+      for (int j4 = 0; j4 < kH / 4; ++j4) {
+        const float4 a2v = ld4(my + fA2 + 4 * j4), w3 = ld4(sW + S_gw3 + 4 * j4);
+        st4(my + fA2 + 4 * j4, a2v.x > 0.f ? w3.x * dp : 0.f, a2v.y > 0.f ? w3.y * dp : 0.f,
+            a2v.z > 0.f ? w3.z * dp : 0.f, a2v.w > 0.f ? w3.w * dp : 0.f);
+        const float4 r2v = ld4(my + fR2 + 4 * j4), c0 = ld4(sW + S_cW3 + 4 * j4),
                      c1 = ld4(sW + S_cW3 + kH + 4 * j4), c2 = ld4(sW + S_cW3 + 2 * kH + 4 * j4);
-        st4(my + gH2 + 4 * j4, r2v.x > 0.f ? c0.x * dpre[0] + c1.x * dpre[1] + c2.x * dpre[2] : 0.f,
+        st4(my + fR2 + 4 * j4, r2v.x > 0.f ? c0.x * dpre[0] + c1.x * dpre[1] + c2.x * dpre[2] : 0.f,
             r2v.y > 0.f ? c0.y * dpre[0] + c1.y * dpre[1] + c2.y * dpre[2] : 0.f,
             r2v.z > 0.f ? c0.z * dpre[0] + c1.z * dpre[1] + c2.z * dpre[2] : 0.f,
             r2v.w > 0.f ? c0.w * dpre[0] + c1.w * dpre[1] + c2.w * dpre[2] : 0.f);
       }
       __syncwarp();
-      outer_rows<kH, true, kRowR>(wr, gH2, gH1, sG + S_cW2, sG + S_cb2, lane);
+      outer_rows<kH, true>(wr, fA2, fA1, sG + S_gW2, sG + S_gb2, lane);
+      outer_rows<kH, true>(wr, fR2, fR1, sG + S_cW2, sG + S_cb2, lane);
       __syncwarp();
-      hidden_adjoint(sW + S_cW2, my);  // dq1 over r1
-      __syncwarp();
-      outer_rows<kU, true, kRowR>(wr, gH1, gIn, sG + S_cW1, sG + S_cb1, lane);
+      // own sample: dy1 = m1 (.) gW2^T dy2 over a1; dq1 = m(q1) (.) cW2^T dq2 over r1
 #pragma unroll
-      for (int q = 0; q < kC; ++q) dcf[q] = 0.f;
+      for (int half = 0; half < 2; ++half) {
+        const int fin = half ? fR2 : fA2, fout = half ? fR1 : fA1, sw = half ? S_cW2 : S_gW2;
+        float acc[kH];
+#pragma unroll
+        for (int q = 0; q < kH; ++q) acc[q] = 0.f;
 #pragma unroll 1
-      for (int j4 = 0; j4 < kH / 4; ++j4) {  // dcf = cW1[:, :6]^T dq1
-        const float4 dq4 = ld4(my + gH1 + 4 * j4);
-        const float dqs[4] = {dq4.x, dq4.y, dq4.z, dq4.w};
+        for (int j4 = 0; j4 < kH / 4; ++j4) {
+          const float4 dy4 = ld4(my + fin + 4 * j4);
+          const float dys[4] = {dy4.x, dy4.y, dy4.z, dy4.w};
 #pragma unroll
-        for (int q = 0; q < 4; ++q)
+          for (int q = 0; q < 4; ++q) {
+            const int j = 4 * j4 + q;
 #pragma unroll
-          for (int e = 0; e < kC; ++e) dcf[e] = fmaf(sW[S_cW1 + (4 * j4 + q) * kU + e], dqs[q], dcf[e]);
+            for (int k4 = 0; k4 < 8; ++k4) {
+              const float4 wv = ld4(sW + sw + j * kH + 4 * k4);
+              acc[4 * k4] = fmaf(wv.x, dys[q], acc[4 * k4]);
+              acc[4 * k4 + 1] = fmaf(wv.y, dys[q], acc[4 * k4 + 1]);
+              acc[4 * k4 + 2] = fmaf(wv.z, dys[q], acc[4 * k4 + 2]);
+              acc[4 * k4 + 3] = fmaf(wv.w, dys[q], acc[4 * k4 + 3]);
+            }
+          }
+        }
+#pragma unroll
+        for (int q4 = 0; q4 < kH / 4; ++q4) {
+          const float4 hv = ld4(my + fout + 4 * q4);
+          st4(my + fout + 4 * q4, hv.x > 0.f ? acc[4 * q4] : 0.f, hv.y > 0.f ? acc[4 * q4 + 1] : 0.f,
+              hv.z > 0.f ? acc[4 * q4 + 2] : 0.f, hv.w > 0.f ? acc[4 * q4 + 3] : 0.f);
+        }
       }
-      if (ok) scatter(a, x, dz, dcf);
+      __syncwarp();
+      outer_rows<kZ, true>(wr, fA1, fZ, sG + S_gW1, sG + S_gb1, lane);
+      outer_rows<kU, true>(wr, fR1, fU, sG + S_cW1, sG + S_cb1, lane);
+      if (ok) {  // dz = gW1^T dy1, dcf = cW1[:, :6]^T dq1, then the scatter
+        float dz[kZ], dcf[kC];
+#pragma unroll
+        for (int q = 0; q < kZ; ++q) dz[q] = 0.f;
+#pragma unroll
+        for (int q = 0; q < kC; ++q) dcf[q] = 0.f;
+#pragma unroll 1
+        for (int j4 = 0; j4 < kH / 4; ++j4) {
+          const float4 dy4 = ld4(my + fA1 + 4 * j4), dq4 = ld4(my + fR1 + 4 * j4);
+          const float dys[4] = {dy4.x, dy4.y, dy4.z, dy4.w}, dqs[4] = {dq4.x, dq4.y, dq4.z, dq4.w};
+#pragma unroll
+          for (int q = 0; q < 4; ++q) {
+            const int j = 4 * j4 + q;
+#pragma unroll
+            for (int k4 = 0; k4 < 4; ++k4) {
+              const float4 wv = ld4(sW + S_gW1 + j * kZ + 4 * k4);
+              dz[4 * k4] = fmaf(wv.x, dys[q], dz[4 * k4]);
+              dz[4 * k4 + 1] = fmaf(wv.y, dys[q], dz[4 * k4 + 1]);
+              dz[4 * k4 + 2] = fmaf(wv.z, dys[q], dz[4 * k4 + 2]);
+              dz[4 * k4 + 3] = fmaf(wv.w, dys[q], dz[4 * k4 + 3]);
+            }
+#pragma unroll
+            for (int e = 0; e < kC; ++e) dcf[e] = fmaf(sW[S_cW1 + j * kU + e], dqs[q], dcf[e]);
+          }
+        }
+        scatter(a, x, dz, dcf);
+      }
     }
   }
   // CTA sums of the loss terms and of d kappa
@@ -1124,11 +1067,11 @@ static gs_status launch_render(const gs_ctx* ctx, const Args& a, int ctas, cudaS
   static bool attr = false;  // per process; the attribute is a property of the function
   if (!attr) {
     if (cudaFuncSetAttribute(paper_render_kernel<NCH>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             (int)kSmemBytesR) != cudaSuccess)
+                             (int)kSmemBytes) != cudaSuccess)
       return GS_ERR_CUDA;
     attr = true;
   }
-  paper_render_kernel<NCH><<<ctas, kThreads, kSmemBytesR, st>>>(a);
+  paper_render_kernel<NCH><<<ctas, kThreads, kSmemBytes, st>>>(a);
   (void)ctx;
   return cudaPeekAtLastError() == cudaSuccess ? GS_OK : GS_ERR_CUDA;
 }
@@ -1250,9 +1193,7 @@ gs_status gs_launch_paper_eikonal(const gs_ctx* ctx, const float* theta, const g
   a.N = b->N;
   a.loss_part = ctx->paper_loss_part;
   a.mlp_part = ctx->paper_part;
-  // two CTAs per SM fit this kernel's shared memory; it writes the first of the render kernel's
-  // partial rows (the calls do not overlap)
-  const int ctas = 2 * ctx->num_sms;
+  const int ctas = kCtasPerSm * ctx->num_sms;  // the render kernel's partial rows (calls do not overlap)
   paper_eikonal_kernel<<<ctas, kThreads, kSmemBytes, st>>>(a);
   if (cudaPeekAtLastError() != cudaSuccess) return GS_ERR_CUDA;
   const float* l = ctx->cfg.lam;
