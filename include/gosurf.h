@@ -78,10 +78,10 @@ typedef enum {
                              15-32-3 fed the geometric features: the workload's model */
 #define GS_ARCH_PAPER 1   /* the paper's (Sec. 3.1): colour grid W_beta at the finest level, colour decoder
                              fed W_beta(x) and the viewing direction, both decoders with two hidden layers
-                             of 32.  Supported by gs_sample_rays, gs_sample_importance, gs_forward,
-                             gs_backward, gs_forward_backward, gs_eikonal, gs_query_sdf, gs_extract_mesh and
-                             gs_adam_step (FP32, activations recomputed); gs_query_sdf_backward,
-                             gs_pose_backward, the proposal sampler and gs_forward_backward_noalloc return
+                             of 32.  Supported by gs_sample_rays, gs_sample_importance, gs_proposal_sample,
+                             gs_proposal_backward, gs_forward, gs_backward, gs_forward_backward, gs_eikonal,
+                             gs_query_sdf, gs_query_sdf_backward, gs_extract_mesh and gs_adam_step (FP32,
+                             activations recomputed); gs_pose_backward and gs_forward_backward_noalloc return
                              GS_ERR_UNSUPPORTED */
 
 /* Sample classes written by gs_sample_rays (Sec. 3.3): */

@@ -111,9 +111,8 @@ gs_status gs_create(const gs_config* cfg, gs_ctx** out) {
     return fail(nullptr, GS_ERR_INVALID_ARG, "gs_create: need 2 <= prop_samples <= 32 and 0 <= prop_guided < prop_samples");
   if (cfg->arch != GS_ARCH_COMPACT && cfg->arch != GS_ARCH_PAPER)
     return fail(nullptr, GS_ERR_INVALID_ARG, "gs_create: arch must be GS_ARCH_COMPACT or GS_ARCH_PAPER");
-  if (cfg->arch == GS_ARCH_PAPER && (cfg->precision != GS_PREC_FP32 || cfg->store_activations || cfg->prop_samples))
-    return fail(nullptr, GS_ERR_UNSUPPORTED,
-                "gs_create: GS_ARCH_PAPER runs in FP32 with recomputed activations, without the proposal sampler");
+  if (cfg->arch == GS_ARCH_PAPER && (cfg->precision != GS_PREC_FP32 || cfg->store_activations))
+    return fail(nullptr, GS_ERR_UNSUPPORTED, "gs_create: GS_ARCH_PAPER runs in FP32 with recomputed activations");
 
   gs_ctx* c = new (std::nothrow) gs_ctx();
   if (!c) return fail(nullptr, GS_ERR_INVALID_ARG, "gs_create: out of host memory");
@@ -377,15 +376,16 @@ gs_status gs_proposal_backward(gs_ctx* ctx, const float* theta, const float* pro
 gs_status gs_query_sdf_backward(gs_ctx* ctx, const float* theta, const float* x, int32_t P, const float* dsdf,
                                 const float* dgrad, float* grad, void* stream) {
   if (!ctx) return fail(nullptr, GS_ERR_INVALID_ARG, "gs_query_sdf_backward: ctx is NULL");
-  if (ctx->cfg.arch != GS_ARCH_COMPACT) return compact_only(ctx, "gs_query_sdf_backward");
   if (P < 0) return fail(ctx, GS_ERR_SHAPE, "gs_query_sdf_backward: P < 0");
   if (P > 0 && (!theta || !x || !grad)) return fail(ctx, GS_ERR_INVALID_ARG, "gs_query_sdf_backward: NULL array");
   if (P > 0 && (!aligned16(theta) || !aligned16(grad)))
     return fail(ctx, GS_ERR_ALIGN, "gs_query_sdf_backward: theta or grad is not 16-byte aligned");
   cudaStream_t st = (cudaStream_t)stream;
   ctx->last_stream = st;
-  if (gs_launch_query_backward(ctx, theta, x, P, dsdf, dgrad, grad, st) != GS_OK)
-    return cuda_fail(ctx, "gs_query_sdf_backward");
+  const gs_status bs = ctx->cfg.arch == GS_ARCH_PAPER
+                           ? gs_launch_paper_query_backward(ctx, theta, x, P, dsdf, dgrad, grad, st)
+                           : gs_launch_query_backward(ctx, theta, x, P, dsdf, dgrad, grad, st);
+  if (bs != GS_OK) return cuda_fail(ctx, "gs_query_sdf_backward");
   return GS_OK;
 }
 

@@ -90,3 +90,5 @@ gs_status gs_launch_paper_eikonal(const gs_ctx* ctx, const float* theta, const g
                                   float* loss, float* grad, cudaStream_t st);
 gs_status gs_launch_paper_query(const gs_ctx* ctx, const float* theta, const float* x, int P, float* sdf, float* grad,
                                 cudaStream_t st);
+gs_status gs_launch_paper_query_backward(const gs_ctx* ctx, const float* theta, const float* x, int P,
+                                         const float* dsdf, const float* dgrad, float* grad, cudaStream_t st);

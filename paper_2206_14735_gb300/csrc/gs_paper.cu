@@ -1022,6 +1022,168 @@ __global__ void __launch_bounds__(128) paper_query_kernel(GridDesc g, const floa
   for (int c = 0; c < 3; ++c) grad[3 * i + c] = gr[c];
 }
 
+// Reverse mode of the SDF query with respect to the parameters (the double backward of
+// grad_x phi, Supp. Sec. 1): grad += sum_p dsdf_p d phi(x_p)/d theta + dgrad_p . d grad_x phi(x_p)/d theta.
+// One lane per point.  The second term is the second-order adjoint of the smoothness and
+// Eikonal kernels; the first the geometry decoder's backward pass (its input and hidden
+// layers staged in the rows) and the adjoint of the gathers.  Colour parameters get nothing.
+__global__ void __launch_bounds__(kThreads, 1) paper_query_backward_kernel(Args a, const float* __restrict__ xq, int P,
+                                                                            const float* __restrict__ dsdf,
+                                                                            const float* __restrict__ dgrad) {
+  extern __shared__ __align__(16) float smem[];
+  float* sW = smem;
+  float* sG = sW + kSm;
+  float* sL = sG + kSm;
+  float* rows = sL + 8;
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  float* wr = rows + wid * 32 * kRow;
+  float* my = wr + lane * kRow;
+  copy_decoder(a.theta + a.g.n_grid, sW);
+  for (int i = threadIdx.x; i < kSm; i += blockDim.x) sG[i] = 0.f;
+  if (threadIdx.x < 8) sL[threadIdx.x] = 0.f;
+  __syncthreads();
+  for (int base = (blockIdx.x * kWarps + wid) * 32; base < P; base += gridDim.x * kWarps * 32) {  // warp-uniform
+    const int p = base + lane;
+    const bool ok = p < P;
+    float y[3] = {0.f, 0.f, 0.f};
+    if (ok) {
+#pragma unroll
+      for (int c = 0; c < 3; ++c) y[c] = xq[3 * p + c];
+    }
+    if (dgrad) {  // second-order term
+      unsigned m1, m2;
+      float pz[kZ], g[3];
+      grad_phi_fwd(a, sW, my, y, m1, m2, pz, g);
+      float av[3] = {0.f, 0.f, 0.f};
+      if (ok) {
+#pragma unroll
+        for (int c = 0; c < 3; ++c) av[c] = dgrad[3 * p + c];
+      }
+      grad_phi_adjoint(a, sW, sG, wr, my, lane, y, ok, av, m1, m2, pz);
+    }
+    if (dsdf) {  // first-order term: phi = gw3 . a2 + gb3, a2 = relu(gW2 a1 + gb2), a1 = relu(gW1 z + gb1)
+      float z[kZ], cf[kC];
+      gather(a, y, z, cf);
+      float h[kH];
+#pragma unroll
+      for (int j = 0; j < kH; ++j) {
+        float v = sW[S_gb1 + j];
+#pragma unroll
+        for (int k4 = 0; k4 < 4; ++k4) {
+          const float4 w = ld4(sW + S_gW1 + j * kZ + 4 * k4);
+          v = fmaf(w.x, z[4 * k4], v);
+          v = fmaf(w.y, z[4 * k4 + 1], v);
+          v = fmaf(w.z, z[4 * k4 + 2], v);
+          v = fmaf(w.w, z[4 * k4 + 3], v);
+        }
+        h[j] = fmaxf(v, 0.f);
+      }
+      const float dp = ok ? dsdf[p] : 0.f;
+      __syncwarp();  // the second-order products have read every row
+#pragma unroll
+      for (int k4 = 0; k4 < kZ / 4; ++k4) st4(my + fZ + 4 * k4, z[4 * k4], z[4 * k4 + 1], z[4 * k4 + 2], z[4 * k4 + 3]);
+#pragma unroll
+      for (int j4 = 0; j4 < kH / 4; ++j4) st4(my + fA1 + 4 * j4, h[4 * j4], h[4 * j4 + 1], h[4 * j4 + 2], h[4 * j4 + 3]);
+#pragma unroll 1
+      for (int j4 = 0; j4 < kH / 4; ++j4) {  // a2 and, in its place, dy2 = m2 (.) gw3 dphi
+        float a2[4];
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+          const int j = 4 * j4 + q;
+          float v = sW[S_gb2 + j];
+#pragma unroll
+          for (int k4 = 0; k4 < 8; ++k4) {
+            const float4 w = ld4(sW + S_gW2 + j * kH + 4 * k4);
+            v = fmaf(w.x, h[4 * k4], v);
+            v = fmaf(w.y, h[4 * k4 + 1], v);
+            v = fmaf(w.z, h[4 * k4 + 2], v);
+            v = fmaf(w.w, h[4 * k4 + 3], v);
+          }
+          a2[q] = fmaxf(v, 0.f);
+        }
+        st4(my + fR1 + 4 * j4, a2[0], a2[1], a2[2], a2[3]);
+        const float4 w3 = ld4(sW + S_gw3 + 4 * j4);
+        st4(my + fA2 + 4 * j4, a2[0] > 0.f ? w3.x * dp : 0.f, a2[1] > 0.f ? w3.y * dp : 0.f,
+            a2[2] > 0.f ? w3.z * dp : 0.f, a2[3] > 0.f ? w3.w * dp : 0.f);
+      }
+      st4(my + fR2, dp, 0.f, 0.f, 0.f);
+      __syncwarp();
+      {  // gw3 (lane = column), gb3
+        float ag = 0.f, bg = 0.f;
+#pragma unroll 4
+        for (int sidx = 0; sidx < 32; ++sidx) {
+          const float* rs = wr + sidx * kRow;
+          ag = fmaf(rs[fR2], rs[fR1 + lane], ag);
+          bg += rs[fR2];
+        }
+        atomicAdd(sG + S_gw3 + lane, ag);
+        if (lane == 0) atomicAdd(sG + S_gb3, bg);
+      }
+      outer_rows<kH, true>(wr, fA2, fA1, sG + S_gW2, sG + S_gb2, lane);
+      __syncwarp();
+      {  // dy1 = m1 (.) gW2^T dy2 over a1
+        float acc[kH];
+#pragma unroll
+        for (int q = 0; q < kH; ++q) acc[q] = 0.f;
+#pragma unroll 1
+        for (int j4 = 0; j4 < kH / 4; ++j4) {
+          const float4 dy4 = ld4(my + fA2 + 4 * j4);
+          const float dys[4] = {dy4.x, dy4.y, dy4.z, dy4.w};
+#pragma unroll
+          for (int q = 0; q < 4; ++q) {
+#pragma unroll
+            for (int k4 = 0; k4 < 8; ++k4) {
+              const float4 wv = ld4(sW + S_gW2 + (4 * j4 + q) * kH + 4 * k4);
+              acc[4 * k4] = fmaf(wv.x, dys[q], acc[4 * k4]);
+              acc[4 * k4 + 1] = fmaf(wv.y, dys[q], acc[4 * k4 + 1]);
+              acc[4 * k4 + 2] = fmaf(wv.z, dys[q], acc[4 * k4 + 2]);
+              acc[4 * k4 + 3] = fmaf(wv.w, dys[q], acc[4 * k4 + 3]);
+            }
+          }
+        }
+#pragma unroll
+        for (int q = 0; q < kH; ++q) h[q] = h[q] > 0.f ? acc[q] : 0.f;
+#pragma unroll
+        for (int j4 = 0; j4 < kH / 4; ++j4) st4(my + fA1 + 4 * j4, h[4 * j4], h[4 * j4 + 1], h[4 * j4 + 2], h[4 * j4 + 3]);
+      }
+      __syncwarp();
+      outer_rows<kZ, true>(wr, fA1, fZ, sG + S_gW1, sG + S_gb1, lane);
+      if (ok && dp != 0.f) {  // dz = gW1^T dy1 into the four levels
+        float dz[kZ], dcf[kC];
+#pragma unroll
+        for (int q = 0; q < kZ; ++q) dz[q] = 0.f;
+#pragma unroll
+        for (int q = 0; q < kC; ++q) dcf[q] = 0.f;
+#pragma unroll 4
+        for (int j = 0; j < kH; ++j) {
+#pragma unroll
+          for (int k4 = 0; k4 < 4; ++k4) {
+            const float4 wv = ld4(sW + S_gW1 + j * kZ + 4 * k4);
+            dz[4 * k4] = fmaf(wv.x, h[j], dz[4 * k4]);
+            dz[4 * k4 + 1] = fmaf(wv.y, h[j], dz[4 * k4 + 1]);
+            dz[4 * k4 + 2] = fmaf(wv.z, h[j], dz[4 * k4 + 2]);
+            dz[4 * k4 + 3] = fmaf(wv.w, h[j], dz[4 * k4 + 3]);
+          }
+        }
+#pragma unroll
+        for (int l = 0; l < kLevels; ++l) {
+          const Cell c = locate(a.g, l, y);
+          float wv[8];
+          corner_weights(c.f, wv);
+          float4* gl = reinterpret_cast<float4*>(a.grad + a.g.off[l]);
+          const float4 d4 = make_float4(dz[4 * l], dz[4 * l + 1], dz[4 * l + 2], dz[4 * l + 3]);
+#pragma unroll
+          for (int k = 0; k < 8; ++k) atomicAdd(gl + c.vtx + corner_offset(a.g, l, k), f4scale(d4, wv[k]));
+        }
+        (void)dcf;
+      }
+      __syncwarp();
+    }
+  }
+  __syncthreads();
+  write_partials(a, sG, sL);
+}
+
 // combine the per-CTA partial rows: decoder gradients in a fixed order into gmlp, losses
 // in FP64 normalised by the set sizes (rgb: R, depth: rays with D > 0, sdf: |S_tr|,
 // fs: |S_fs|, smooth: valid points) with the weighted total
@@ -1200,6 +1362,35 @@ gs_status gs_launch_paper_eikonal(const gs_ctx* ctx, const float* theta, const g
   paper_combine_kernel<<<(GS_PAPER_MLP_PARAMS + 255) / 256, 256, 0, st>>>(
       ctx->paper_loss_part, ctx->paper_part, ctas, b->counts, b->R, l[0], l[1], l[2], l[3], l[4], loss,
       grad ? grad + ctx->grid.n_grid : nullptr, 1);
+  return cudaPeekAtLastError() == cudaSuccess ? GS_OK : GS_ERR_CUDA;
+}
+
+gs_status gs_launch_paper_query_backward(const gs_ctx* ctx, const float* theta, const float* x, int P,
+                                         const float* dsdf, const float* dgrad, float* grad, cudaStream_t st) {
+  using namespace paper;
+  if (P == 0 || (!dsdf && !dgrad)) return GS_OK;
+  static bool attr = false;
+  if (!attr) {
+    if (cudaFuncSetAttribute(paper_query_backward_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)kSmemBytes) != cudaSuccess)
+      return GS_ERR_CUDA;
+    attr = true;
+  }
+  Args a;
+  a.g = ctx->grid;
+  a.colour_off = ctx->colour_off;
+  a.theta = theta;
+  a.grad = grad;
+  a.loss_part = ctx->paper_loss_part;
+  a.mlp_part = ctx->paper_part;
+  const int want = (P + kWarps * 32 - 1) / (kWarps * 32);
+  const int ctas = want < 2 * ctx->num_sms ? want : 2 * ctx->num_sms;  // within the render kernel's partial rows
+  paper_query_backward_kernel<<<ctas, kThreads, kSmemBytes, st>>>(a, x, P, dsdf, dgrad);
+  if (cudaPeekAtLastError() != cudaSuccess) return GS_ERR_CUDA;
+  const float* l = ctx->cfg.lam;
+  paper_combine_kernel<<<(GS_PAPER_MLP_PARAMS + 255) / 256, 256, 0, st>>>(
+      ctx->paper_loss_part, ctx->paper_part, ctas, nullptr, 0, l[0], l[1], l[2], l[3], l[4], nullptr,
+      grad + ctx->grid.n_grid, 0);
   return cudaPeekAtLastError() == cudaSuccess ? GS_OK : GS_ERR_CUDA;
 }
 

@@ -159,9 +159,6 @@ def test_paper_empty_batches():
 def test_paper_rejections():
     p = Problem(CUBE_P)
     th = _padded(sg.paper_sdf_params(CUBE_P, sg.cube_scene(), seed=23))
-    x = torch.zeros(4, 3, device="cuda")
-    with pytest.raises(gs.GoSurfError, match="GS_ARCH_PAPER"):
-        p.ctx.query_sdf_backward(th, x, torch.ones(4, device="cuda"), None, torch.zeros_like(th))
     b = gs.Batch.allocate(8, CUBE_P.n_samples, 0, dz=True)
     with pytest.raises(gs.GoSurfError, match="UNSUPPORTED"):
         p.ctx.forward_backward(th, b, None, torch.empty(6, device="cuda"), torch.zeros_like(th))
@@ -291,3 +288,76 @@ def test_paper_mesh_matches_oracle():
     close = np.abs(phi_ref) < 2e-5
     assert n == len(ref) or close.any()
     assert abs(n - len(ref)) <= 2 * close.sum()
+
+
+def test_paper_proposal_learns_from_the_paper_models_weights():
+    """The learned proposal with the paper's architecture: the paper model's forward pass
+    writes the rendering weights of a proposal batch (against the oracle), and the proposal's
+    cross-entropy gradient from those weights matches the oracle's."""
+    w = CUBE_P.with_(name="cube-paper-prop", prop_samples=32, prop_guided=8)
+    p = Problem(w, max_rays=512)
+    theta = sg.paper_sdf_params(w, sg.cube_scene(), seed=23)
+    q = np.random.default_rng(3).normal(0.0, 0.3, oc.PROP_PARAMS).astype(np.float32)
+    R = 512
+    bt, _ = p.oracle_sample(SEED, STEP, R, 0)
+    pdf = oc.prop_forward(p.cfg, theta, q, bt["o"], bt["r"]).astype(np.float32)
+    ref_s = oc.prop_sample(p.cfg, bt["D"], pdf, 32, 8, SEED, STEP)
+    b = gs.Batch.allocate(R, 32, 0, weights=True)
+    p.ctx.proposal_sample(p.dfr, SEED, STEP, b, pdf_in=torch.from_numpy(pdf).cuda())
+    torch.cuda.synchronize()
+    assert np.array_equal(b.t.cpu().numpy().view(np.uint32), ref_s["t"].view(np.uint32))
+    th = _padded(theta)
+    loss = torch.empty(6, device="cuda")
+    p.ctx.forward(th, b, loss)
+    torch.cuda.synchronize()
+    wt = b.w.cpu().numpy()
+    bo = dict(bt, t=ref_s["t"], cls=ref_s["cls"], counts=ref_s["counts"])
+    ref = oc.step(p.cfg, theta, bo, None, want_grad=False, want_weights=True)
+    np.testing.assert_allclose(wt, ref["w"], atol=2e-6)
+    grad, ce = torch.zeros(oc.PROP_PARAMS, device="cuda"), torch.zeros(2, device="cuda")
+    p.ctx.proposal_backward(th, torch.from_numpy(q).cuda(), b, grad, ce)
+    torch.cuda.synchronize()
+    l_ref, g_ref, n_used = oc.prop_ce(p.cfg, theta, q, bt["o"], bt["r"], ref_s["t"], wt)
+    assert int(ce[1].item()) == n_used > 100
+    assert abs(float(ce[0].item()) - l_ref) <= 1e-5 * abs(l_ref)
+    g = grad.cpu().numpy().astype(np.float64)
+    for a0, a1 in ((0, 352), (352, 384), (384, 1408), (1408, 1440), (1440, 1472)):
+        assert np.abs(g[a0:a1] - g_ref[a0:a1]).max() <= 1e-4 * np.abs(g_ref[a0:a1]).max()
+
+
+@pytest.mark.parametrize("terms", ["both", "sdf", "grad"])
+def test_paper_query_sdf_backward_parity(cube_paper, terms):
+    """The double backward of the SDF query with the paper's architecture (SdfGrad): the
+    gradient of sum dsdf phi + dgrad . grad_x phi against the oracle's reverse mode."""
+    c = cube_paper
+    rng = np.random.default_rng(11)
+    P = 2000
+    x = rng.uniform(-1.2, 1.2, (P, 3)).astype(np.float32)
+    ds = rng.normal(size=P) if terms in ("both", "sdf") else None
+    dg = rng.normal(size=(P, 3)) if terms in ("both", "grad") else None
+    ref = oc.query_sdf_backward(c["p"].cfg, c["theta"], x, ds, dg)
+    th = _padded(c["theta"])
+    grad = torch.zeros_like(th)
+    tod = lambda v: None if v is None else torch.from_numpy(np.ascontiguousarray(v, np.float32)).cuda()
+    c["p"].ctx.query_sdf_backward(th, torch.from_numpy(x).cuda(), tod(ds), tod(dg), grad)
+    torch.cuda.synchronize()
+    g = grad.cpu().numpy()[:len(c["theta"])]
+    assert_grad_close(c["p"], g, ref)
+    assert np.abs(g[CUBE_P.colour_offset():c["p"].n_grid]).max() == 0
+
+
+def test_paper_sdfgrad_autograd(cube_paper):
+    """SdfGrad over the paper model: torch.autograd of a loss on (phi, grad_x phi) gives the
+    oracle's gradient."""
+    c = cube_paper
+    rng = np.random.default_rng(12)
+    x = torch.from_numpy(rng.uniform(-1.0, 1.0, (500, 3)).astype(np.float32)).cuda()
+    th = _padded(c["theta"]).requires_grad_(True)
+    sdf, g = gs.SdfGrad.apply(th, c["p"].ctx, x)
+    loss = (sdf ** 2).sum() + ((g.norm(dim=1) - 1.0) ** 2).sum()
+    loss.backward()
+    sdf_r, g_r = oc.query_sdf(c["p"].cfg, c["theta"], x.cpu().numpy())
+    n = np.linalg.norm(g_r, axis=1)
+    ref = oc.query_sdf_backward(c["p"].cfg, c["theta"], x.cpu().numpy(), 2 * sdf_r,
+                                2 * (n - 1.0)[:, None] * g_r / n[:, None])
+    assert_grad_close(c["p"], th.grad.cpu().numpy()[:len(c["theta"])], ref)
