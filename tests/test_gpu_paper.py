@@ -313,7 +313,9 @@ def test_paper_proposal_learns_from_the_paper_models_weights():
     wt = b.w.cpu().numpy()
     bo = dict(bt, t=ref_s["t"], cls=ref_s["cls"], counts=ref_s["counts"])
     ref = oc.step(p.cfg, theta, bo, None, want_grad=False, want_weights=True)
-    np.testing.assert_allclose(wt, ref["w"], atol=2e-6)
+    # alpha = (Phi_i - Phi_i+1) / Phi_i loses relative precision in binary32 when the two
+    # opacities are close: a relative as well as an absolute bound, as for the workload's model
+    np.testing.assert_allclose(wt, ref["w"], rtol=1e-4, atol=2e-6)
     grad, ce = torch.zeros(oc.PROP_PARAMS, device="cuda"), torch.zeros(2, device="cuda")
     p.ctx.proposal_backward(th, torch.from_numpy(q).cuda(), b, grad, ce)
     torch.cuda.synchronize()
