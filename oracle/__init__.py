@@ -114,6 +114,10 @@ def lib():
             L.oc_paper_param_count.argtypes = [vp, vp]
             L.oc_step_paper.restype = i32
             L.oc_step_paper.argtypes = [vp, vp, i32, i32] + [vp] * 6 + [i32] + [vp] * 12
+            L.oc_step_paper_dz.restype = i32
+            L.oc_step_paper_dz.argtypes = [vp, vp, i32, i32] + [vp] * 6 + [i32] + [vp] * 7
+            L.oc_pose_grad_paper.restype = None
+            L.oc_pose_grad_paper.argtypes = [vp, vp, vp, vp, vp, i32, i32] + [vp] * 6
             _LIB = L
     return _LIB
 
@@ -202,16 +206,18 @@ def sample_smooth(cfg: OcConfig, frames: OcFramesHolder, seed: int, step: int, P
 
 
 def step_dz(cfg: OcConfig, theta, batch: dict, smooth: dict | None, dloss=None):
-    """Losses, gradient and dL/dz of every main sample [R][N][16] of one step."""
+    """Losses, gradient and dL/dz of every main sample of one step: [R][N][16] for the
+    workload's model; for the paper's architecture (cfg.arch == 1) [R][N][32] holding dL/dz
+    (16), dL/dW_beta(x) (6), dL/d(viewing direction) (3) and zeros."""
     th = np.ascontiguousarray(theta, dtype=np.float64)
     R, N = batch["t"].shape
     if smooth is None:
         P, xs, eps, valid = 0, np.zeros((1, 3), np.float32), np.zeros((1, 3), np.float32), np.zeros(1, np.uint8)
     else:
         P, xs, eps, valid = len(smooth["valid"]), smooth["xs"], smooth["eps"], smooth["valid"]
-    loss, grad, dz = np.zeros(6), np.zeros_like(th), np.zeros((R, N, 16))
+    loss, grad, dz = np.zeros(6), np.zeros_like(th), np.zeros((R, N, 32 if cfg.arch == 1 else 16))
     dl = None if dloss is None else np.ascontiguousarray(dloss, dtype=np.float64)
-    rc = lib().oc_step_dz(ctypes.byref(cfg), _p(th), R, N, _p(batch["o"]), _p(batch["r"]), _p(batch["rgb"]),
+    rc = (lib().oc_step_paper_dz if cfg.arch == 1 else lib().oc_step_dz)(ctypes.byref(cfg), _p(th), R, N, _p(batch["o"]), _p(batch["r"]), _p(batch["rgb"]),
                           _p(batch["D"]), _p(batch["t"]), _p(batch["cls"]), P, _p(xs), _p(eps), _p(valid), _p(dl),
                           _p(loss), _p(grad), _p(dz))
     if rc != 0:
@@ -243,7 +249,7 @@ def pose_grad(cfg: OcConfig, frames: OcFramesHolder, theta, c2w, xi, batch: dict
     F = len(c2w)
     R, N = batch["t"].shape
     g = np.zeros((F, 6))
-    lib().oc_pose_grad(ctypes.byref(cfg), ctypes.byref(frames.s), _p(th), _p(c2w), _p(xi), R, N,
+    (lib().oc_pose_grad_paper if cfg.arch == 1 else lib().oc_pose_grad)(ctypes.byref(cfg), ctypes.byref(frames.s), _p(th), _p(c2w), _p(xi), R, N,
                        _p(np.ascontiguousarray(batch["pix"], dtype=np.int64)), _p(batch["o"]), _p(batch["r"]),
                        _p(batch["t"]), _p(np.ascontiguousarray(dz, dtype=np.float64)), _p(g))
     return g

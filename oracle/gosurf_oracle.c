@@ -1804,7 +1804,7 @@ static void pa_affine_back(const double* W, const double* x, const double* dy, i
 /* reverse mode of pa_eval's decoders for upstream dphi, dc: decoder gradients into gm (the
  * PA_MLP block), dL/dz [16] and dL/dW_beta(x) [6] returned */
 static void pa_backward(const pa_mlp_t* m, const pa_act_t* A, double dphi, const double dc[3], double* gm,
-                        double dz[OC_Z], double dcf[PA_C]) {
+                        double dz[OC_Z], double dcf[PA_C], double ddir[3]) {
   pa_mlp_t g = pa_view(gm); /* same offsets in the gradient block */
   double d2[PA_H], d1[PA_H], du[PA_U];
   /* geometry: phi = gw3 . a2 + gb3 */
@@ -1821,7 +1821,9 @@ static void pa_backward(const pa_mlp_t* m, const pa_act_t* A, double dphi, const
   pa_affine_back(m->cW2, A->r1, d2, PA_H, PA_H, (double*)g.cW2, (double*)g.cb2, d1);
   for (int j = 0; j < PA_H; ++j) d1[j] = A->q1[j] > 0 ? d1[j] : 0.0;
   pa_affine_back(m->cW1, A->u, d1, PA_H, PA_U, (double*)g.cW1, (double*)g.cb1, du);
-  for (int k = 0; k < PA_C; ++k) dcf[k] = du[k]; /* the viewing direction is not a parameter */
+  for (int k = 0; k < PA_C; ++k) dcf[k] = du[k];
+  if (ddir) /* the viewing direction is not a parameter; its gradient serves the pose refinement */
+    for (int a = 0; a < 3; ++a) ddir[a] = du[PA_C + a];
 }
 
 /* d phi / d z of the two-hidden-layer geometry decoder (piecewise linear, masks fixed):
@@ -1849,10 +1851,11 @@ static void pa_dphi_dz(const pa_mlp_t* m, const pa_act_t* A, double p[OC_Z], dou
  * (main samples and smoothness points), 5 = min |d_hat - D|, 7 = signature of the branch
  * decisions; the others are set to +inf (8 and 9 to 0).  amb flags as in oc_step.
  */
-int oc_step_paper(const oc_config* c, const double* theta, int R, int N, const float* o, const float* r,
-                  const float* rgb, const float* D, const float* t, const uint8_t* cls, int P, const float* xs,
-                  const float* eps, const uint8_t* valid, const double* dloss, double* loss, double* rgb_hat,
-                  double* d_hat, double* wsum, double* grad, double* margins, uint8_t* amb, double* w_out) {
+static int step_paper_impl(const oc_config* c, const double* theta, int R, int N, const float* o, const float* r,
+                           const float* rgb, const float* D, const float* t, const uint8_t* cls, int P,
+                           const float* xs, const float* eps, const uint8_t* valid, const double* dloss,
+                           double* loss, double* rgb_hat, double* d_hat, double* wsum, double* grad, double* margins,
+                           uint8_t* amb, double* w_out, double* dzc_out) {
   if (R < 0 || N < 2 || P < 0) return -1;
   int64_t ng = 0;
   const int64_t ntot = oc_paper_param_count(c, &ng);
@@ -1994,7 +1997,15 @@ int oc_step_paper(const oc_config* c, const double* theta, int R, int N, const f
       }
       double dc[3], dz[OC_Z], dcf[PA_C];
       for (int j = 0; j < 3; ++j) dc[j] = w[k] * gc[j];
-      pa_backward(&m, &A[k], dphi, dc, gm, dz, dcf);
+      double ddir[3];
+      pa_backward(&m, &A[k], dphi, dc, gm, dz, dcf, ddir);
+      if (dzc_out) { /* per sample: dL/dz, dL/dW_beta(x), dL/d(direction) */
+        double* q = dzc_out + ((size_t)i * N + k) * 32;
+        for (int f = 0; f < 32; ++f) q[f] = 0.0;
+        for (int f = 0; f < OC_Z; ++f) q[f] = dz[f];
+        for (int f = 0; f < PA_C; ++f) q[OC_Z + f] = dcf[f];
+        for (int a = 0; a < 3; ++a) q[OC_Z + PA_C + a] = ddir[a];
+      }
       /* adjoint of the trilinear gathers: geometry levels and the colour grid */
       for (int l = 0; l < OC_LEVELS; ++l) {
         const cell_t* cl_ = &cells[(size_t)k * OC_LEVELS + l];
@@ -2166,7 +2177,7 @@ static void pa_query_sdf_backward(const oc_config* c, const double* theta, const
     if (dsdf && dsdf[i] != 0.0) {
       const double dc[3] = {0, 0, 0};
       double dz[OC_Z], dcf[PA_C];
-      pa_backward(&m, &A, dsdf[i], dc, gm, dz, dcf);
+      pa_backward(&m, &A, dsdf[i], dc, gm, dz, dcf, NULL);
       for (int l = 0; l < OC_LEVELS; ++l)
         for (int cc = 0; cc < 8; ++cc)
           for (int f = 0; f < OC_FEAT; ++f) grad[cells[l].corner[cc] + f] += cells[l].w[cc] * dz[OC_FEAT * l + f];
@@ -2199,5 +2210,78 @@ static void pa_query_sdf_backward(const oc_config* c, const double* theta, const
         if (A.y2[i2] > 0) ((double*)gg.gw3)[i2] += acc;
       }
     }
+  }
+}
+
+int oc_step_paper(const oc_config* c, const double* theta, int R, int N, const float* o, const float* r,
+                  const float* rgb, const float* D, const float* t, const uint8_t* cls, int P, const float* xs,
+                  const float* eps, const uint8_t* valid, const double* dloss, double* loss, double* rgb_hat,
+                  double* d_hat, double* wsum, double* grad, double* margins, uint8_t* amb, double* w_out) {
+  return step_paper_impl(c, theta, R, N, o, r, rgb, D, t, cls, P, xs, eps, valid, dloss, loss, rgb_hat, d_hat, wsum,
+                         grad, margins, amb, w_out, NULL);
+}
+
+/* oc_step_paper that also returns, per main sample, dzc_out [R][N][32]: dL/dz (16), dL/dW_beta(x)
+ * (6) and dL/d(viewing direction) (3), zeros after (needs grad) */
+int oc_step_paper_dz(const oc_config* c, const double* theta, int R, int N, const float* o, const float* r,
+                     const float* rgb, const float* D, const float* t, const uint8_t* cls, int P, const float* xs,
+                     const float* eps, const uint8_t* valid, const double* dloss, double* loss, double* grad,
+                     double* dzc_out) {
+  return step_paper_impl(c, theta, R, N, o, r, rgb, D, t, cls, P, xs, eps, valid, dloss, loss, NULL, NULL, NULL, grad,
+                         NULL, NULL, NULL, dzc_out);
+}
+
+/* Camera-pose gradient with the paper's architecture (Sec. 3.4): as oc_pose_grad, where the
+ * per-ray losses reach the pose through the sample positions x_s = o + d_s r (geometry grid
+ * and colour grid: g_s = (dz/dx)^T dL/dz + (dW_beta/dx)^T dL/dW_beta) and through the viewing
+ * direction r/|r| = R d/|d| (d the pixel's camera direction):
+ *   dL/d dt = sum_s g_s,   dL/d nu = J_r(nu)^T [d]_x R^T (sum_s d_s g_s + dL/d(dir) / |d|),
+ * with dL/d(dir) = sum_s of the per-sample direction gradients in dzc [R][N][32]. */
+void oc_pose_grad_paper(const oc_config* c, const oc_frames* fr, const double* theta, const double* c2w,
+                        const double* xi, int R, int N, const int64_t* pix, const float* o, const float* r,
+                        const float* t, const double* dzc, double* g) {
+  const int64_t hw = (int64_t)fr->H * fr->W;
+  const int64_t cbase = grid_size(c), off3 = level_offset(c, 3);
+  for (int i = 0; i < R; ++i) {
+    const int64_t f = pix[i] / hw, rem = pix[i] % hw;
+    const int v = (int)(rem / fr->W), u = (int)(rem % fr->W);
+    const double d[3] = {(((double)u + 0.5) - fr->cx) / fr->fx, (((double)v + 0.5) - fr->cy) / fr->fy, 1.0};
+    const double dn = sqrt(d[0] * d[0] + d[1] * d[1] + d[2] * d[2]);
+    double go[3] = {0, 0, 0}, gr[3] = {0, 0, 0}, gd[3] = {0, 0, 0};
+    for (int k = 0; k < N; ++k) {
+      const float* ti = t + (size_t)i * N;
+      float x[3];
+      for (int a = 0; a < 3; ++a) {
+        float st = ti[k] * r[3 * i + a];
+        x[a] = o[3 * i + a] + st;
+      }
+      cell_t cells[OC_LEVELS];
+      double z[OC_Z], dzdx[OC_Z][3];
+      features(c, theta, x, cells, z, dzdx);
+      const double* q = dzc + ((size_t)i * N + k) * 32;
+      for (int a = 0; a < 3; ++a) {
+        double gx = 0;
+        for (int e = 0; e < OC_Z; ++e) gx += dzdx[e][a] * q[e];
+        /* colour features: d W_beta_f / d x_a = (1/v_3) sum_c beta_{c,f} d w_c / d f_a */
+        for (int cc = 0; cc < 8; ++cc) {
+          const int64_t cv = cbase + (cells[3].corner[cc] - off3) / OC_FEAT * PA_C;
+          double sf = 0;
+          for (int e = 0; e < PA_C; ++e) sf += theta[cv + e] * q[OC_Z + e];
+          gx += sf * cells[3].dw[cc][a] * cells[3].inv_v;
+        }
+        go[a] += gx;
+        gr[a] += (double)ti[k] * gx;
+        gd[a] += q[OC_Z + PA_C + a];
+      }
+    }
+    for (int a = 0; a < 3; ++a) g[6 * f + a] += go[a];
+    double E[3][3], J[3][3], Rt_gr[3], K[3][3], w[3];
+    so3_exp_jr(xi + 6 * f + 3, E, J);
+    const double* Q = c2w + 12 * f;
+    for (int a = 0; a < 3; ++a) gr[a] += gd[a] / dn;
+    for (int a = 0; a < 3; ++a) Rt_gr[a] = Q[a] * gr[0] + Q[4 + a] * gr[1] + Q[8 + a] * gr[2];
+    skew(d, K);
+    for (int a = 0; a < 3; ++a) w[a] = K[a][0] * Rt_gr[0] + K[a][1] * Rt_gr[1] + K[a][2] * Rt_gr[2];
+    for (int a = 0; a < 3; ++a) g[6 * f + 3 + a] += J[0][a] * w[0] + J[1][a] * w[1] + J[2][a] * w[2];
   }
 }
