@@ -150,7 +150,7 @@ def run_ours(args):
     n_grid_ = w.layout()[1]
     # BF16 form: the grid copy the gathers read, refreshed by every Adam step
     mirror = theta[:n_grid_].to(torch.bfloat16).view(torch.int16).contiguous() if ctx.bf16 else None
-    batch = gs.Batch.allocate(w.rays, w.n_samples, w.n_smooth, dz=args.poses)
+    batch = gs.Batch.allocate(w.rays, w.n_samples, w.n_smooth, dz=args.poses, dz_width=32 if paper else 16)
     loss = torch.empty(6, device="cuda")
     eik = torch.zeros(1, device="cuda")  # L_eik when --eikonal (Sec. 3.3, lam_eik = 1)
     stream = torch.cuda.current_stream()

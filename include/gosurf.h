@@ -80,9 +80,9 @@ typedef enum {
                              fed W_beta(x) and the viewing direction, both decoders with two hidden layers
                              of 32.  Supported by gs_sample_rays, gs_sample_importance, gs_proposal_sample,
                              gs_proposal_backward, gs_forward, gs_backward, gs_forward_backward, gs_eikonal,
-                             gs_query_sdf, gs_query_sdf_backward, gs_extract_mesh and gs_adam_step (FP32,
-                             activations recomputed); gs_pose_backward and gs_forward_backward_noalloc return
-                             GS_ERR_UNSUPPORTED */
+                             gs_query_sdf, gs_query_sdf_backward, gs_extract_mesh, gs_pose_apply,
+                             gs_pose_backward and gs_adam_step (FP32, activations recomputed);
+                             gs_forward_backward_noalloc returns GS_ERR_UNSUPPORTED */
 
 /* Sample classes written by gs_sample_rays (Sec. 3.3): */
 #define GS_CLS_NONE 0 /* no SDF supervision (behind the surface, or the ray has no depth) */
@@ -151,7 +151,8 @@ typedef struct gs_batch {
                       when not NULL; read by gs_proposal_backward */
   float* dz;       /* [R][N][16] dL/dz of every sample (the upstream gradient of its geometry
                       feature), written by the backward passes when not NULL; read by
-                      gs_pose_backward */
+                      gs_pose_backward.  GS_ARCH_PAPER: [R][N][32] per sample, dL/dz (16),
+                      dL/dW_beta(x) (6), dL/d(viewing direction) (3), zeros (7) */
 } gs_batch;
 
 typedef struct gs_ctx gs_ctx;
@@ -312,7 +313,10 @@ gs_status gs_extract_mesh(gs_ctx* ctx, const float* theta, const float* lo, floa
  * over each frame's rays, with J_r the right Jacobian of Exp; dL/dz is batch->dz, which the
  * preceding gs_backward / gs_forward_backward of this batch wrote (batch->dz must be set
  * there and here).  frames: the corrected poses the batch was sampled with.  The smoothness
- * points are not differentiated with respect to the poses.  Accumulates with atomics. */
+ * points are not differentiated with respect to the poses.  Accumulates with atomics.
+ * GS_ARCH_PAPER: the colour grid moves with x too, g_s = sum_l (dz_l/dx)^T dL/dz_l +
+ * (dW_beta/dx)^T dL/dW_beta, and the viewing direction r/|r| = R d/|d| turns with the pose:
+ * dL/d nu = J_r(nu)^T [d]_x R^T (sum_s d_s g_s + sum_s dL/d(direction)_s / |d|). */
 gs_status gs_pose_apply(gs_ctx* ctx, const float* c2w0, const float* xi, int32_t F, float* c2w, void* stream);
 gs_status gs_pose_backward(gs_ctx* ctx, const float* theta, const gs_frames* frames, const float* xi,
                            const gs_batch* batch, float* pose_grad, void* stream);

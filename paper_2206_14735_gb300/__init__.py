@@ -95,10 +95,11 @@ class Batch:
     valid: torch.Tensor
     counts: torch.Tensor
     w: torch.Tensor | None = None  # [R][N] rendering weights (written by forward passes when present)
-    dz: torch.Tensor | None = None  # [R][N][16] dL/dz (written by backward passes when present)
+    dz: torch.Tensor | None = None  # [R][N][16] dL/dz (written by backward passes when present;
+    #                                 [R][N][32] records for the paper's architecture)
 
     @staticmethod
-    def allocate(R: int, N: int, P: int, device="cuda", weights=False, dz=False) -> "Batch":
+    def allocate(R: int, N: int, P: int, device="cuda", weights=False, dz=False, dz_width=16) -> "Batch":
         f = dict(device=device, dtype=torch.float32)
         return Batch(R=R, N=N, P=P, pix=torch.empty(R, device=device, dtype=torch.int64),
                      origin=torch.empty(R, 3, **f), dir=torch.empty(R, 3, **f), rgb=torch.empty(R, 3, **f),
@@ -107,7 +108,7 @@ class Batch:
                      eps=torch.empty(max(P, 1), 3, **f), valid=torch.empty(max(P, 1), device=device, dtype=torch.uint8),
                      counts=torch.zeros(4, device=device, dtype=torch.int32),
                      w=torch.zeros(R, N, **f) if weights else None,
-                     dz=torch.zeros(R, N, 16, **f) if dz else None)
+                     dz=torch.zeros(R, N, dz_width, **f) if dz else None)
 
     def struct(self) -> GsBatch:
         return GsBatch(self.R, self.N, self.P, self.pix.data_ptr(), self.origin.data_ptr(), self.dir.data_ptr(),

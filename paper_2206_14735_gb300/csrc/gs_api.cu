@@ -36,11 +36,6 @@ long long colour_floats(const gs_config* c) {
   return (n + 3) / 4 * 4;
 }
 
-// model entry points that exist for the workload's decoders only
-gs_status compact_only(gs_ctx* ctx, const char* who) {
-  std::string m(who);
-  return fail(ctx, GS_ERR_UNSUPPORTED, (m + ": not available for GS_ARCH_PAPER").c_str());
-}
 
 gs_status check_batch(gs_ctx* ctx, const gs_batch* b, bool need_smooth_arrays) {
   if (!b) return fail(ctx, GS_ERR_INVALID_ARG, "batch is NULL");
@@ -226,7 +221,7 @@ static gs_status render_common(gs_ctx* ctx, const char* who, const float* theta,
   ctx->last_stream = st;
   const float* dl = dloss ? dloss : ctx->default_dloss;
   if (ctx->cfg.arch == GS_ARCH_PAPER) {
-    if (batch->dz) return fail(ctx, GS_ERR_UNSUPPORTED, "batch dz is not written for GS_ARCH_PAPER");
+    if (batch->dz && (reinterpret_cast<uintptr_t>(batch->dz) & 15u)) return fail(ctx, GS_ERR_ALIGN, "batch dz is not 16-byte aligned");
     if (gs_launch_paper(ctx, theta, batch, dl, grad, loss, rgb_hat, d_hat, wsum, mode, st) != GS_OK)
       return cuda_fail(ctx, who);
     return GS_OK;
@@ -420,7 +415,6 @@ gs_status gs_pose_apply(gs_ctx* ctx, const float* c2w0, const float* xi, int32_t
 gs_status gs_pose_backward(gs_ctx* ctx, const float* theta, const gs_frames* frames, const float* xi,
                            const gs_batch* batch, float* pose_grad, void* stream) {
   if (!ctx) return fail(nullptr, GS_ERR_INVALID_ARG, "gs_pose_backward: ctx is NULL");
-  if (ctx->cfg.arch != GS_ARCH_COMPACT) return compact_only(ctx, "gs_pose_backward");
   gs_status s = check_frames(ctx, frames, "gs_pose_backward");
   if (s != GS_OK) return s;
   s = check_batch(ctx, batch, true);

@@ -74,6 +74,7 @@ struct Args {
   const int* counts;
   const float* dloss;
   float *rgb_hat, *d_hat, *wsum, *w_out;
+  float* dz_out;                // [R][N][32] per-sample records for the pose gradient (may be nullptr)
   float *loss_part, *mlp_part;  // this kernel's first partial row
   int R, N, P, mode;
   float lam[5];
@@ -577,12 +578,12 @@ __global__ void __launch_bounds__(kThreads, kCtasPerSm) paper_render_kernel(Args
       __syncwarp();
       outer_rows<kZ, true>(wr, fA1, fZ, sG + S_gW1, sG + S_gb1, lane);
       outer_rows<kU, true>(wr, fR1, fU, sG + S_cW1, sG + S_cb1, lane);
-      if (ok) {  // dz = gW1^T dy1, dcf = cW1[:, :6]^T dq1, then the scatter
-        float dz[kZ], dcf[kC];
+      if (ok) {  // dz = gW1^T dy1, dcf = cW1[:, :6]^T dq1 (ddir: the direction's rows), then the scatter
+        float dz[kZ], dcf[kU];
 #pragma unroll
         for (int q = 0; q < kZ; ++q) dz[q] = 0.f;
 #pragma unroll
-        for (int q = 0; q < kC; ++q) dcf[q] = 0.f;
+        for (int q = 0; q < kU; ++q) dcf[q] = 0.f;
 #pragma unroll 1
         for (int j4 = 0; j4 < kH / 4; ++j4) {
           const float4 dy4 = ld4(my + fA1 + 4 * j4), dq4 = ld4(my + fR1 + 4 * j4);
@@ -599,10 +600,19 @@ __global__ void __launch_bounds__(kThreads, kCtasPerSm) paper_render_kernel(Args
               dz[4 * k4 + 3] = fmaf(wv.w, dys[q], dz[4 * k4 + 3]);
             }
 #pragma unroll
-            for (int e = 0; e < kC; ++e) dcf[e] = fmaf(sW[S_cW1 + j * kU + e], dqs[q], dcf[e]);
+            for (int e = 0; e < kU; ++e) dcf[e] = fmaf(sW[S_cW1 + j * kU + e], dqs[q], dcf[e]);
           }
         }
         scatter(a, x, dz, dcf);
+        if (a.dz_out) {  // the sample's record for the pose gradient: dz (16), dcf (6), ddir (3), zeros
+          float* rec = a.dz_out + ((size_t)ray * N + k) * 32;
+#pragma unroll
+          for (int q = 0; q < 4; ++q) st4(rec + 4 * q, dz[4 * q], dz[4 * q + 1], dz[4 * q + 2], dz[4 * q + 3]);
+          st4(rec + 16, dcf[0], dcf[1], dcf[2], dcf[3]);
+          st4(rec + 20, dcf[4], dcf[5], dcf[6], dcf[7]);
+          st4(rec + 24, dcf[8], 0.f, 0.f, 0.f);
+          st4(rec + 28, 0.f, 0.f, 0.f, 0.f);
+        }
       }
     }
   }
@@ -1269,6 +1279,7 @@ gs_status gs_launch_paper(const gs_ctx* ctx, const float* theta, const gs_batch*
   a.d_hat = d_hat;
   a.wsum = wsum;
   a.w_out = b->w;
+  a.dz_out = b->dz;
   a.R = b->R;
   a.N = b->N;
   a.P = b->P;

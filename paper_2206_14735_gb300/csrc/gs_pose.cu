@@ -65,6 +65,7 @@ __global__ void pose_apply_kernel(const float* __restrict__ c2w0, const float* _
 struct PoseBwdArgs {
   FramesDev fr;  // the refined poses (c2w) the batch was sampled with
   GridDesc g;
+  long long colour_off;  // paper architecture: float offset of the colour grid
   const float* theta;
   const float* xi;
   int R, N;
@@ -74,27 +75,54 @@ struct PoseBwdArgs {
 };
 
 // one warp per ray: lanes over its samples, then lane 0 turns the ray's sums into the frame's
-// six pose derivatives
+// six pose derivatives.  kPaper (the paper's architecture): each sample's record holds 32
+// floats, dL/dz (16), dL/dW_beta(x) (6) and dL/d(viewing direction) (3); the colour grid's
+// x-derivative adds to g_s, and the direction r/|r| = R d/|d| adds dL/d(direction) / |d| to
+// the rotation's moment.
+template <bool kPaper>
 __global__ void __launch_bounds__(128) pose_backward_kernel(PoseBwdArgs a) {
+  constexpr int kRec = kPaper ? 32 : kZ;  // floats per sample record
   const int lane = threadIdx.x & 31;
   for (int i = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; i < a.R; i += (gridDim.x * blockDim.x) >> 5) {
     const float o[3] = {a.o[3 * i], a.o[3 * i + 1], a.o[3 * i + 2]};
     const float r[3] = {a.r[3 * i], a.r[3 * i + 1], a.r[3 * i + 2]};
-    float go[3] = {0.f, 0.f, 0.f}, gr[3] = {0.f, 0.f, 0.f};
+    float go[3] = {0.f, 0.f, 0.f}, gr[3] = {0.f, 0.f, 0.f}, gd[3] = {0.f, 0.f, 0.f};
     for (int k = lane; k < a.N; k += 32) {
       const float tk = a.t[(size_t)i * a.N + k];
       float x[3];
       sample_pos(o, r, tk, x);
-      const float4* dzk = reinterpret_cast<const float4*>(a.dz + ((size_t)i * a.N + k) * kZ);
+      const float4* dzk = reinterpret_cast<const float4*>(a.dz + ((size_t)i * a.N + k) * kRec);
       float gx[3] = {0.f, 0.f, 0.f};
 #pragma unroll
       for (int l = 0; l < kLevels; ++l) {
         float4 dl[3];
         float dw[8][3];
-        level_jacobian(a.g, a.theta, l, x, dl, dw);
+        const Cell c = level_jacobian(a.g, a.theta, l, x, dl, dw);
         const float4 d4 = dzk[l];
 #pragma unroll
         for (int q = 0; q < 3; ++q) gx[q] += dl[q].x * d4.x + dl[q].y * d4.y + dl[q].z * d4.z + dl[q].w * d4.w;
+        if (kPaper && l == kLevels - 1) {  // colour grid on the finest level's cell
+          const float4 c0 = dzk[4], c1 = dzk[5];
+          const float dcf[6] = {c0.x, c0.y, c0.z, c0.w, c1.x, c1.y};
+          gd[0] += c1.z;
+          gd[1] += c1.w;
+          gd[2] += dzk[6].x;
+          const float2* cg = reinterpret_cast<const float2*>(a.theta + a.colour_off);
+          const float iv = a.g.inv_voxel[l];
+#pragma unroll
+          for (int cc = 0; cc < 8; ++cc) {
+            const long long v2 = (c.vtx + corner_offset(a.g, l, cc)) * 3;
+            float sf = 0.f;
+#pragma unroll
+            for (int e = 0; e < 3; ++e) {
+              const float2 f2 = __ldg(cg + v2 + e);
+              sf = fmaf(f2.x, dcf[2 * e], sf);
+              sf = fmaf(f2.y, dcf[2 * e + 1], sf);
+            }
+#pragma unroll
+            for (int q = 0; q < 3; ++q) gx[q] = fmaf(sf * iv, dw[cc][q], gx[q]);
+          }
+        }
       }
 #pragma unroll
       for (int q = 0; q < 3; ++q) {
@@ -106,12 +134,18 @@ __global__ void __launch_bounds__(128) pose_backward_kernel(PoseBwdArgs a) {
     for (int q = 0; q < 3; ++q) {
       go[q] = warp_sum(go[q]);
       gr[q] = warp_sum(gr[q]);
+      if (kPaper) gd[q] = warp_sum(gd[q]);
     }
     if (lane == 0) {
       const long long hw = (long long)a.fr.H * a.fr.W;
       const long long p = a.pix[i], f = p / hw, rem = p - f * hw;
       const int v = (int)(rem / a.fr.W), u = (int)(rem - (long long)v * a.fr.W);
       const float d[3] = {((float)u + 0.5f - a.fr.cx) / a.fr.fx, ((float)v + 0.5f - a.fr.cy) / a.fr.fy, 1.f};
+      if (kPaper) {
+        const float inv_dn = rsqrtf(d[0] * d[0] + d[1] * d[1] + d[2] * d[2]);
+#pragma unroll
+        for (int q = 0; q < 3; ++q) gr[q] = fmaf(gd[q], inv_dn, gr[q]);
+      }
       const float* Q = a.fr.c2w + 12 * f;
       float Rt[3];  // R^T gr
 #pragma unroll
@@ -145,6 +179,7 @@ gs_status gs_launch_pose_backward(const gs_ctx* ctx, const float* theta, const g
   PoseBwdArgs a;
   a.fr = FramesDev{f->F, f->H, f->W, f->rgb, f->depth, f->c2w, f->fx, f->fy, f->cx, f->cy};
   a.g = ctx->grid;
+  a.colour_off = ctx->colour_off;
   a.theta = theta;
   a.xi = xi;
   a.R = b->R;
@@ -156,6 +191,7 @@ gs_status gs_launch_pose_backward(const gs_ctx* ctx, const float* theta, const g
   a.dz = b->dz;
   a.pose_grad = pose_grad;
   const int blocks = (int)std::min<long long>(((long long)b->R * 32 + 127) / 128, 16LL * ctx->num_sms);
-  pose_backward_kernel<<<blocks, 128, 0, st>>>(a);
+  if (ctx->cfg.arch == GS_ARCH_PAPER) pose_backward_kernel<true><<<blocks, 128, 0, st>>>(a);
+  else pose_backward_kernel<false><<<blocks, 128, 0, st>>>(a);
   return cudaPeekAtLastError() == cudaSuccess ? GS_OK : GS_ERR_CUDA;
 }

@@ -363,3 +363,39 @@ def test_paper_sdfgrad_autograd(cube_paper):
     ref = oc.query_sdf_backward(c["p"].cfg, c["theta"], x.cpu().numpy(), 2 * sdf_r,
                                 2 * (n - 1.0)[:, None] * g_r / n[:, None])
     assert_grad_close(c["p"], th.grad.cpu().numpy()[:len(c["theta"])], ref)
+
+
+def test_paper_pose_records_and_gradient_match_oracle():
+    """Camera-pose refinement with the paper's architecture: the per-sample records of the
+    backward pass (dL/dz, dL/dW_beta(x), dL/d(viewing direction)) and the pose gradient
+    (through both grids and the direction) against the oracle."""
+    w = CUBE_P.with_(name="cube-paper-3frames", frames=3)
+    p = Problem(w)
+    rng = np.random.default_rng(5)
+    xi = np.c_[rng.normal(0, 0.01, (3, 3)), rng.normal(0, 0.01, (3, 3))]
+    c2w = oc.pose_apply(p.frames.c2w, xi)
+    F = oc.OcFramesHolder(p.frames, c2w=c2w)
+    theta = sg.paper_sdf_params(w, sg.cube_scene(), seed=23)
+    bt = oc.sample_rays(p.cfg, F, 9, 2, w.rays)
+    sm = oc.sample_smooth(p.cfg, F, 9, 2, w.n_smooth)
+    bt_s, _, _ = prepare_parity_batch(p, theta, bt, sm)
+    ref_dz = oc.step_dz(p.cfg, theta, bt_s, sm)["dz"]
+    g_ref = oc.pose_grad(p.cfg, F, theta, c2w, xi, bt_s, ref_dz)
+    batch = upload_oracle_batch(bt_s, sm, sm["n_valid"][0])
+    batch.dz = torch.zeros(batch.R, batch.N, 32, device="cuda")
+    th = _padded(theta)
+    loss, grad = torch.empty(6, device="cuda"), torch.zeros_like(th)
+    p.ctx.forward_backward(th, batch, None, loss, grad)
+    dz = batch.dz.cpu().numpy().astype(np.float64)
+    for a0, a1 in ((0, 16), (16, 22), (22, 25)):  # per-sample chains in FP32: 1e-3 of the largest
+        scale = np.abs(ref_dz[..., a0:a1]).max()
+        assert scale > 0 and np.abs(dz[..., a0:a1] - ref_dz[..., a0:a1]).max() <= 1e-3 * scale, (a0, a1)
+    assert not np.any(dz[..., 25:])
+    dfr = p.dfr.with_poses(torch.from_numpy(c2w.astype(np.float32)).cuda())
+    pg = torch.zeros(3, 6, device="cuda")
+    p.ctx.pose_backward(th, dfr, torch.from_numpy(xi.astype(np.float32)).cuda(), batch, pg)
+    torch.cuda.synchronize()
+    p.ctx.sync_status()
+    g = pg.cpu().numpy().astype(np.float64)
+    assert np.abs(g_ref).max() > 1e-3
+    assert np.abs(g - g_ref).max() <= 1e-4 * np.abs(g_ref).max(), (g, g_ref)
