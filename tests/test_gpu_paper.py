@@ -157,11 +157,23 @@ def test_paper_empty_batches():
 
 
 def test_paper_rejections():
-    p = Problem(CUBE_P)
+    """Host-side rejections (nothing is launched): the allocation-free entry point serves the
+    workload's model only; the paper's architecture runs in FP32 with recomputed activations."""
+    import ctypes
+    from paper_2206_14735_gb300 import _lib
+    L = _lib.lib()
+    cfg = gs.make_config(CUBE_P)
     th = _padded(sg.paper_sdf_params(CUBE_P, sg.cube_scene(), seed=23))
-    b = gs.Batch.allocate(8, CUBE_P.n_samples, 0, dz=True)
+    b = gs.Batch.allocate(8, CUBE_P.n_samples, 0).struct()
+    loss, grad = torch.empty(6, device="cuda"), torch.zeros_like(th)
+    st = L.gs_forward_backward_noalloc(ctypes.byref(cfg), ctypes.c_void_p(th.data_ptr()), ctypes.byref(b), None,
+                                       ctypes.c_void_p(loss.data_ptr()), ctypes.c_void_p(grad.data_ptr()), None)
+    assert st == 6 and b"GS_ARCH_COMPACT" in L.gs_last_error(None)
+    for bad in (dict(precision="bf16"),):
+        with pytest.raises(gs.GoSurfError, match="UNSUPPORTED"):
+            gs.Context(CUBE_P.with_(**bad))
     with pytest.raises(gs.GoSurfError, match="UNSUPPORTED"):
-        p.ctx.forward_backward(th, b, None, torch.empty(6, device="cuda"), torch.zeros_like(th))
+        gs.Context(CUBE_P, store_activations=True)
 
 
 def test_paper_room_scale_parity():
