@@ -139,8 +139,8 @@ def run_ours(args):
     t0 = time.time()
     fr = sg.make_frames(w, n_frames=args.frames, with_gt=args.sampler_report > 0)
     t_frames = time.time() - t0
-    paper = w.arch == "paper"  # the paper's architecture recomputes its activations (no store)
-    recompute = args.recompute or paper
+    paper = w.arch == "paper"
+    recompute = args.recompute
     ctx = gs.Context(w, store_activations=not recompute)
     dfr = gs.DeviceFrames(fr.rgb, fr.depth, fr.c2w, fr.fx, fr.fy, fr.cx, fr.cy)
     theta0 = sg.init_params(w)
@@ -344,7 +344,8 @@ def run_ours(args):
                    "resolution": [w.width, w.height], "parallelism": f"replicas{world}",
                    "model": ("paper: colour grid (6 features, finest level) + view direction, decoders with "
                              "2 hidden layers of 32" if paper else "compact: decoders 16-32-16 and 15-32-3"),
-                   "activations": "recomputed" if recompute else "stored (396 B/sample)",
+                   "activations": "recomputed" if recompute else
+                                  f"stored ({624 if paper else 396} B/sample)",
                    "sampler": (f"importance: {w.imp_coarse} coarse + {w.imp_steps} x {w.imp_per_step}"
                                if w.imp_coarse > 0 else f"stratified {w.n_strat} + depth-guided {w.n_guided}"),
                    "pipeline": ("the next step's batch sampled on a side stream during this step (double-buffered)"

@@ -81,7 +81,8 @@ typedef enum {
                              of 32.  Supported by gs_sample_rays, gs_sample_importance, gs_proposal_sample,
                              gs_proposal_backward, gs_forward, gs_backward, gs_forward_backward, gs_eikonal,
                              gs_query_sdf, gs_query_sdf_backward, gs_extract_mesh, gs_pose_apply,
-                             gs_pose_backward and gs_adam_step (FP32, activations recomputed);
+                             gs_pose_backward and gs_adam_step (FP32; store_activations keeps 156 floats
+                             per sample: z, [W_beta(x), d] padded to 12, and the four hidden layers);
                              gs_forward_backward_noalloc returns GS_ERR_UNSUPPORTED */
 
 /* Sample classes written by gs_sample_rays (Sec. 3.3): */
@@ -202,8 +203,8 @@ gs_status gs_backward(gs_ctx* ctx, const float* theta, const uint16_t* theta_bf1
  * With GS_ARCH_PAPER these three entry points evaluate the paper's architecture (layout at
  * the top of this file): the same losses, batch normalisations and smoothness term with
  * phi = f_omega(V_theta(x)) and c = g_gamma(W_beta(x), r/|r|), the gradient reaching the
- * geometry grid, the colour grid and both decoders; FP32 only, the decoder activations are
- * recomputed by the backward pass, batch->dz is not supported (GS_ERR_UNSUPPORTED). */
+ * geometry grid, the colour grid and both decoders; FP32 only; batch->dz receives the
+ * 32-float records described at gs_batch. */
 gs_status gs_forward_backward(gs_ctx* ctx, const float* theta, const uint16_t* theta_bf16, const gs_batch* batch,
                               const float* dloss, float* loss, float* grad, void* stream);
 

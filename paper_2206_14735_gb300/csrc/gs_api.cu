@@ -106,8 +106,8 @@ gs_status gs_create(const gs_config* cfg, gs_ctx** out) {
     return fail(nullptr, GS_ERR_INVALID_ARG, "gs_create: need 2 <= prop_samples <= 32 and 0 <= prop_guided < prop_samples");
   if (cfg->arch != GS_ARCH_COMPACT && cfg->arch != GS_ARCH_PAPER)
     return fail(nullptr, GS_ERR_INVALID_ARG, "gs_create: arch must be GS_ARCH_COMPACT or GS_ARCH_PAPER");
-  if (cfg->arch == GS_ARCH_PAPER && (cfg->precision != GS_PREC_FP32 || cfg->store_activations))
-    return fail(nullptr, GS_ERR_UNSUPPORTED, "gs_create: GS_ARCH_PAPER runs in FP32 with recomputed activations");
+  if (cfg->arch == GS_ARCH_PAPER && cfg->precision != GS_PREC_FP32)
+    return fail(nullptr, GS_ERR_UNSUPPORTED, "gs_create: GS_ARCH_PAPER runs in FP32");
 
   gs_ctx* c = new (std::nothrow) gs_ctx();
   if (!c) return fail(nullptr, GS_ERR_INVALID_ARG, "gs_create: out of host memory");
@@ -155,7 +155,9 @@ gs_status gs_create(const gs_config* cfg, gs_ctx** out) {
        (cudaMalloc(&c->paper_part, sizeof(float) * gs_paper_part_floats(c->num_sms)) != cudaSuccess ||
         cudaMalloc(&c->paper_loss_part, sizeof(float) * kLossPad * gs_paper_part_rows(c->num_sms)) != cudaSuccess)) ||
       (cfg->store_activations &&
-       cudaMalloc(&c->store, c->store_bytes = (size_t)cfg->max_rays * c->max_n * kStoreFloatsPerSample * sizeof(float)) !=
+       cudaMalloc(&c->store, c->store_bytes = (size_t)cfg->max_rays * c->max_n *
+                                             (cfg->arch == GS_ARCH_PAPER ? gs_paper_store_fields() : kStoreFloatsPerSample) *
+                                             sizeof(float)) !=
            cudaSuccess)) {
     gs_status s = cuda_fail(nullptr, "gs_create: workspace allocation");
     gs_destroy(c);
@@ -224,6 +226,11 @@ static gs_status render_common(gs_ctx* ctx, const char* who, const float* theta,
     if (batch->dz && (reinterpret_cast<uintptr_t>(batch->dz) & 15u)) return fail(ctx, GS_ERR_ALIGN, "batch dz is not 16-byte aligned");
     if (gs_launch_paper(ctx, theta, batch, dl, grad, loss, rgb_hat, d_hat, wsum, mode, st) != GS_OK)
       return cuda_fail(ctx, who);
+    if (ctx->store && (mode & 1)) {
+      ctx->store_R = batch->R;
+      ctx->store_N = batch->N;
+      ctx->store_t = batch->t;
+    }
     return GS_OK;
   }
   // The smoothness kernel is independent of the render kernel (its own partial rows, atomics

@@ -83,6 +83,7 @@ gs_status gs_launch_query(const gs_ctx* ctx, const float* theta, const float* x,
 gs_status gs_launch_voxel_index(const gs_ctx* ctx, const float* x, int P, long long* out, cudaStream_t st);
 void gs_set_thread_error(const char* msg);
 int gs_paper_part_rows(int num_sms);
+int gs_paper_store_fields();  // floats per sample of the paper architecture's stored activations
 size_t gs_paper_part_floats(int num_sms);
 gs_status gs_launch_paper(const gs_ctx* ctx, const float* theta, const gs_batch* b, const float* dloss, float* grad,
                           float* loss, float* rgb_hat, float* d_hat, float* wsum, int mode, cudaStream_t st);

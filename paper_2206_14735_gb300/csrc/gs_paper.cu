@@ -57,6 +57,11 @@ __device__ __forceinline__ int acc_index(int i) {
 constexpr int kRow = 164;
 constexpr int fZ = 0, fU = 16, fA1 = 28, fA2 = 60, fR1 = 92, fR2 = 124, fDP = 156;  // fDP: dpre[3], dphi
 static_assert(kRow % 32 == 4 && fU % 4 == 0 && fA1 % 4 == 0 && fDP % 4 == 0, "row layout");
+// Stored activations (store mode): the row fields z, u, a1, a2, r1, r2 of every sample, one
+// plane per field (field f of sample s at f * sstride + s), written by the forward pass and
+// read back by the backward pass instead of gathering and decoding again.
+constexpr int kStoreFields = fDP;
+static_assert(kStoreFields % 4 == 0, "store fields in float4 groups");
 constexpr int kWarps = 4;  // warps per CTA
 constexpr int kThreads = kWarps * 32;
 constexpr size_t kSmemBytes = sizeof(float) * (2 * kSm + 8 + kWarps * 32 * kRow);
@@ -75,6 +80,8 @@ struct Args {
   const float* dloss;
   float *rgb_hat, *d_hat, *wsum, *w_out;
   float* dz_out;                // [R][N][32] per-sample records for the pose gradient (may be nullptr)
+  float* store;                 // stored activations: kStoreFields planes of sstride floats (may be nullptr)
+  long long sstride;
   float *loss_part, *mlp_part;  // this kernel's first partial row
   int R, N, P, mode;
   float lam[5];
@@ -271,7 +278,7 @@ __global__ void __launch_bounds__(kThreads, kCtasPerSm) paper_render_kernel(Args
   for (int i = threadIdx.x; i < kSm; i += blockDim.x) sG[i] = 0.f;
   if (threadIdx.x < 8) sL[threadIdx.x] = 0.f;
   __syncthreads();
-  const bool bwd = (a.mode & 2) != 0;
+  const bool bwd = (a.mode & 2) != 0, fwd = (a.mode & 1) != 0;
   const float s = expf(sW[S_kappa]);
   float wt[5];
 #pragma unroll
@@ -324,7 +331,19 @@ __global__ void __launch_bounds__(kThreads, kCtasPerSm) paper_render_kernel(Args
 #pragma unroll
       for (int q = 0; q < 3; ++q) u[kC + q] = d[q];
       float ph, cc[3];
-      decode(sW, z, u, bwd && c == NCH - 1 ? my : nullptr, ph, cc);
+      const bool put = a.store != nullptr && fwd;
+      decode(sW, z, u, put || (bwd && c == NCH - 1) ? my : nullptr, ph, cc);
+      if (put && 32 * c + lane < N) {
+        float* sp = a.store + (size_t)ray * N + 32 * c + lane;
+#pragma unroll 4
+        for (int f4 = 0; f4 < kStoreFields / 4; ++f4) {
+          const float4 v = ld4(my + 4 * f4);
+          sp[(4 * f4) * a.sstride] = v.x;
+          sp[(4 * f4 + 1) * a.sstride] = v.y;
+          sp[(4 * f4 + 2) * a.sstride] = v.z;
+          sp[(4 * f4 + 3) * a.sstride] = v.w;
+        }
+      }
 #pragma unroll
       for (int q = 0; q < NCH; ++q)
         if (c == q) {
@@ -478,7 +497,18 @@ __global__ void __launch_bounds__(kThreads, kCtasPerSm) paper_render_kernel(Args
         }
       float x[3] = {0.f, 0.f, 0.f};
       if (ok) sample_pos(o, r, tc, x);
-      if (c != NCH - 1) {
+      if (c != NCH - 1 && a.store != nullptr) {  // stored by the forward pass: back into the row
+        __syncwarp();  // the previous chunk's products have read every row
+        const float* sp = a.store + (size_t)ray * N + (ok ? k : 0);
+#pragma unroll 4
+        for (int f4 = 0; f4 < kStoreFields / 4; ++f4) {
+          if (ok)
+            st4(my + 4 * f4, sp[(4 * f4) * a.sstride], sp[(4 * f4 + 1) * a.sstride], sp[(4 * f4 + 2) * a.sstride],
+                sp[(4 * f4 + 3) * a.sstride]);
+          else
+            st4(my + 4 * f4, 0.f, 0.f, 0.f, 0.f);
+        }
+      } else if (c != NCH - 1) {
         float z[kZ], u[kU];
         __syncwarp();  // the previous chunk's products have read every row
         if (ok) {
@@ -1253,6 +1283,7 @@ static gs_status launch_render(const gs_ctx* ctx, const Args& a, int ctas, cudaS
 
 using namespace gs;
 
+int gs_paper_store_fields() { return paper::kStoreFields; }
 int gs_paper_part_rows(int num_sms) { return paper::kCtasPerSm * num_sms + kSmoothCtas; }
 size_t gs_paper_part_floats(int num_sms) { return (size_t)gs_paper_part_rows(num_sms) * paper::kPart; }
 
@@ -1280,6 +1311,8 @@ gs_status gs_launch_paper(const gs_ctx* ctx, const float* theta, const gs_batch*
   a.wsum = wsum;
   a.w_out = b->w;
   a.dz_out = b->dz;
+  a.store = ctx->store;
+  a.sstride = (long long)ctx->cfg.max_rays * ctx->max_n;
   a.R = b->R;
   a.N = b->N;
   a.P = b->P;

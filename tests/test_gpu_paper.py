@@ -158,7 +158,7 @@ def test_paper_empty_batches():
 
 def test_paper_rejections():
     """Host-side rejections (nothing is launched): the allocation-free entry point serves the
-    workload's model only; the paper's architecture runs in FP32 with recomputed activations."""
+    workload's model only; the paper's architecture runs in FP32."""
     import ctypes
     from paper_2206_14735_gb300 import _lib
     L = _lib.lib()
@@ -169,11 +169,8 @@ def test_paper_rejections():
     st = L.gs_forward_backward_noalloc(ctypes.byref(cfg), ctypes.c_void_p(th.data_ptr()), ctypes.byref(b), None,
                                        ctypes.c_void_p(loss.data_ptr()), ctypes.c_void_p(grad.data_ptr()), None)
     assert st == 6 and b"GS_ARCH_COMPACT" in L.gs_last_error(None)
-    for bad in (dict(precision="bf16"),):
-        with pytest.raises(gs.GoSurfError, match="UNSUPPORTED"):
-            gs.Context(CUBE_P.with_(**bad))
     with pytest.raises(gs.GoSurfError, match="UNSUPPORTED"):
-        gs.Context(CUBE_P, store_activations=True)
+        gs.Context(CUBE_P.with_(precision="bf16"))
 
 
 def test_paper_room_scale_parity():
@@ -411,3 +408,29 @@ def test_paper_pose_records_and_gradient_match_oracle():
     g = pg.cpu().numpy().astype(np.float64)
     assert np.abs(g_ref).max() > 1e-3
     assert np.abs(g - g_ref).max() <= 1e-4 * np.abs(g_ref).max(), (g, g_ref)
+
+
+@pytest.mark.parametrize("n_strat,n_guided", [(48, 16), (100, 32)])
+def test_paper_stored_activations(n_strat, n_guided):
+    """Store mode of the paper's architecture: the forward pass keeps every sample's decoder
+    inputs and hidden layers, the backward pass reads them instead of gathering and decoding
+    again.  The fused call, and a gs_forward followed by gs_backward, against the oracle."""
+    w = CUBE_P.with_(name=f"cube-paper-store-{n_strat}", n_strat=n_strat, n_guided=n_guided)
+    c = _case(w, R=500, max_drop=0.25)
+    ctx = gs.Context(w, max_rays=500, store_activations=True)
+    th = _padded(c["theta"])
+    loss, g1, g2 = torch.empty(6, device="cuda"), torch.zeros_like(th), torch.zeros_like(th)
+    ctx.forward_backward(th, c["batch"], None, loss, g1)
+    torch.cuda.synchronize()
+    _check_loss(loss.cpu().numpy().astype(np.float64), c["ref"]["loss"])
+    n = len(c["theta"])
+    assert_grad_close(c["p"], g1.cpu().numpy()[:n], c["ref"]["grad"])
+    l2 = torch.empty(6, device="cuda")
+    ctx.forward(th, c["batch"], l2)
+    ctx.backward(th, c["batch"], None, g2)
+    torch.cuda.synchronize()
+    _check_loss(l2.cpu().numpy().astype(np.float64), c["ref"]["loss"])
+    assert_grad_close(c["p"], g2.cpu().numpy()[:n], c["ref"]["grad"])
+    other = gs.Batch.allocate(500, w.n_samples, 0)
+    with pytest.raises(gs.GoSurfError, match="store_activations"):
+        ctx.backward(th, other, None, g2)  # no forward pass of this batch yet
