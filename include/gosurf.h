@@ -109,9 +109,10 @@ typedef struct gs_config {
   int32_t store_activations;  /* 1: every forward pass writes each sample's decoder inputs and
                                  activations (z, ReLU outputs, SDF, geometric feature, colour:
                                  99 floats = 396 bytes per sample, max_rays x N samples, one
-                                 plane per field, allocated by gs_create) and every backward
-                                 pass reads them instead of gathering again and recomputing the
-                                 decoders; 0: the backward pass recomputes them (no memory) */
+                                 plane per field, allocated by gs_create; GS_ARCH_PAPER: 156
+                                 floats) and every backward pass reads them instead of gathering
+                                 again and recomputing the decoders; 0: the backward pass
+                                 recomputes them (no memory) */
   int32_t prop_samples;       /* learned proposal sampler (not part of the paper): samples per
                                  ray of a proposal batch, 2..32; 0 disables gs_proposal_* */
   int32_t prop_guided;        /* of those, samples stratified over [D - g, D + g] when D > 0 */
