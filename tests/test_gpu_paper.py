@@ -117,10 +117,11 @@ def test_paper_smoothness_term_alone(cube_paper):
     assert np.abs(g[CUBE_P.colour_offset():c["p"].n_grid]).max() == 0
 
 
-@pytest.mark.parametrize("n_strat,n_guided,R,P", [(100, 32, 77, 13), (30, 9, 33, 0), (8, 0, 5, 40)])
+@pytest.mark.parametrize("n_strat,n_guided,R,P", [(100, 32, 77, 13), (128, 32, 40, 8), (30, 9, 33, 0), (8, 0, 5, 40)])
 def test_paper_ragged_shapes(n_strat, n_guided, R, P):
-    """Samples per ray spanning 1, 5 chunks with a ragged last chunk; ray and point counts that
-    fill no whole warp group; a batch without smoothness points."""
+    """Samples per ray spanning 1 to 5 chunks, with a ragged last chunk and at the largest
+    count (160 = 5 full chunks); ray and point counts that fill no whole warp group; a batch
+    without smoothness points."""
     w = CUBE_P.with_(name=f"cube-paper-{n_strat}+{n_guided}", n_strat=n_strat, n_guided=n_guided, n_smooth=P)
     c = _case(w, R=R, P=P, seed=7, step=n_strat, max_drop=0.25)
     got, (rgb_hat, d_hat, wsum) = _forward(c)
