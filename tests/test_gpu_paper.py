@@ -435,3 +435,16 @@ def test_paper_stored_activations(n_strat, n_guided):
     other = gs.Batch.allocate(500, w.n_samples, 0)
     with pytest.raises(gs.GoSurfError, match="store_activations"):
         ctx.backward(th, other, None, g2)  # no forward pass of this batch yet
+
+
+def test_paper_autograd_step(cube_paper):
+    """GoSurfStep (the torch.autograd.Function over the fused passes) with the paper's
+    architecture: the six outputs and the gradient of a weighted sum against the oracle."""
+    c = cube_paper
+    th = _padded(c["theta"]).requires_grad_(True)
+    loss = gs.GoSurfStep.apply(th, c["p"].ctx, c["batch"])
+    seed = torch.tensor([0.3, -1.1, 0.7, 2.0, 5.0, 0.25], device="cuda")
+    (loss * seed).sum().backward()
+    _check_loss(loss.detach().cpu().numpy().astype(np.float64), c["ref"]["loss"])
+    ref = oc.step(c["p"].cfg, c["theta"], c["bt"], c["sm"], dloss=seed.cpu().numpy().astype(np.float64))
+    assert_grad_close(c["p"], th.grad.cpu().numpy()[:len(c["theta"])], ref["grad"])
