@@ -680,13 +680,16 @@ __device__ __forceinline__ void grad_phi_fwd(const Args& a, const float* sW, flo
       z[4 * l + 2] = acc.z;
       z[4 * l + 3] = acc.w;
     }
-    // forward masks
+    // forward masks; the layer-1 activations go through the lane's row (field R1, free until
+    // grad_phi_adjoint) instead of 32 registers
     m1 = 0u;
     m2 = 0u;
-    {
-      float h[kH];
+#pragma unroll 1
+    for (int j4 = 0; j4 < kH / 4; ++j4) {
+      float hv[4];
 #pragma unroll
-      for (int j = 0; j < kH; ++j) {
+      for (int q = 0; q < 4; ++q) {
+        const int j = 4 * j4 + q;
         float v = sW[S_gb1 + j];
 #pragma unroll
         for (int k4 = 0; k4 < 4; ++k4) {
@@ -696,22 +699,23 @@ __device__ __forceinline__ void grad_phi_fwd(const Args& a, const float* sW, flo
           v = fmaf(wv.z, z[4 * k4 + 2], v);
           v = fmaf(wv.w, z[4 * k4 + 3], v);
         }
-        h[j] = fmaxf(v, 0.f);
+        hv[q] = fmaxf(v, 0.f);
         m1 |= (v > 0.f ? 1u : 0u) << j;
       }
+      st4(my + fR1 + 4 * j4, hv[0], hv[1], hv[2], hv[3]);
+    }
 #pragma unroll 1
-      for (int j = 0; j < kH; ++j) {
-        float v = sW[S_gb2 + j];
+    for (int j = 0; j < kH; ++j) {
+      float v = sW[S_gb2 + j];
 #pragma unroll
-        for (int k4 = 0; k4 < 8; ++k4) {
-          const float4 wv = ld4(sW + S_gW2 + j * kH + 4 * k4);
-          v = fmaf(wv.x, h[4 * k4], v);
-          v = fmaf(wv.y, h[4 * k4 + 1], v);
-          v = fmaf(wv.z, h[4 * k4 + 2], v);
-          v = fmaf(wv.w, h[4 * k4 + 3], v);
-        }
-        m2 |= (v > 0.f ? 1u : 0u) << j;
+      for (int k4 = 0; k4 < 8; ++k4) {
+        const float4 wv = ld4(sW + S_gW2 + j * kH + 4 * k4), hv = ld4(my + fR1 + 4 * k4);
+        v = fmaf(wv.x, hv.x, v);
+        v = fmaf(wv.y, hv.y, v);
+        v = fmaf(wv.z, hv.z, v);
+        v = fmaf(wv.w, hv.w, v);
       }
+      m2 |= (v > 0.f ? 1u : 0u) << j;
     }
     // e = m2 (.) gw3 (row field A2), pm = m1 (.) gW2^T e (row field A1), p = gW1^T pm
     {
