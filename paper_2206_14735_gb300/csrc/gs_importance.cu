@@ -41,9 +41,11 @@ struct ImpArgs {
 // kPaper: phi from the paper's two-hidden-layer geometry decoder (GS_ARCH_PAPER) instead of
 // the workload's decoder
 template <bool kPaper>
-__global__ void __launch_bounds__(kImpWarps * 32, 1) importance_kernel(ImpArgs a) {
+__global__ void __launch_bounds__(kImpWarps * 32, 3) importance_kernel(ImpArgs a) {
   // workload decoder: W1 | b1 | W2 row 0 | b2[0]; paper: the geometry decoder block
   __shared__ __align__(16) float sm[kPaper ? paper::kGeoPad : sb2 + 4];
+  // paper decoder: each thread's hidden layer in shared memory (stride 33), not in registers
+  __shared__ float hsc[kPaper ? kImpWarps * 32 : 1][kPaper ? 33 : 1];
   __shared__ float ts[kImpWarps][2][kImpMax], ps[kImpWarps][2][kImpMax];
   __shared__ float cs[kImpWarps][kImpMax];   // mass left of each interval (unnormalised)
   __shared__ float tn[kImpWarps][32];        // this step's new depths
@@ -90,7 +92,7 @@ __global__ void __launch_bounds__(kImpWarps * 32, 1) importance_kernel(ImpArgs a
       float x[3];
       sample_pos(o, r, tk, x);
       ts[warp][0][k] = tk;
-      ps[warp][0][k] = kPaper ? paper::phi_at(a.g, a.theta, sm, x) : sdf_at(a.g, a.theta, sm, x);
+      ps[warp][0][k] = kPaper ? paper::phi_at(a.g, a.theta, sm, x, hsc[threadIdx.x]) : sdf_at(a.g, a.theta, sm, x);
     }
     __syncwarp();
     int n = a.Nc, cur = 0;
@@ -159,7 +161,7 @@ __global__ void __launch_bounds__(kImpWarps * 32, 1) importance_kernel(ImpArgs a
         tj = fminf(fmaxf(Tc[lo] + f * (Tc[lo + 1] - Tc[lo]), Tc[lo]), Tc[lo + 1]);
         float x[3];
         sample_pos(o, r, tj, x);
-        pj = kPaper ? paper::phi_at(a.g, a.theta, sm, x) : sdf_at(a.g, a.theta, sm, x);
+        pj = kPaper ? paper::phi_at(a.g, a.theta, sm, x, hsc[threadIdx.x]) : sdf_at(a.g, a.theta, sm, x);
         tn[warp][lane] = tj;
       }
       __syncwarp();

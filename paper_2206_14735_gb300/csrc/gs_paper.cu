@@ -998,14 +998,13 @@ __global__ void __launch_bounds__(128) paper_query_kernel(GridDesc g, const floa
                                                           const float* __restrict__ xq, int P, float* sdf,
                                                           float* grad) {
   __shared__ __align__(16) float sg[kGeoPad];
+  __shared__ float hs[128][kH + 1];  // each thread's layer-1 activations (stride 33: conflict-free)
   load_geometry_decoder(theta + g.n_grid, sg);
   __syncthreads();
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= P) return;
+  float* h = hs[threadIdx.x];
   const float x[3] = {xq[3 * i], xq[3 * i + 1], xq[3 * i + 2]};
-  sdf[i] = phi_at(g, theta, sg, x);
-  if (!grad) return;
-  // p = gW1^T (m1 (.) gW2^T (m2 (.) gw3)), then grad = sum over levels of (dz_l/dx)^T p_l
   float z[kZ];
 #pragma unroll
   for (int l = 0; l < kLevels; ++l) {
@@ -1021,16 +1020,24 @@ __global__ void __launch_bounds__(128) paper_query_kernel(GridDesc g, const floa
     z[4 * l + 2] = acc.z;
     z[4 * l + 3] = acc.w;
   }
-  float h[kH];
+  // phi = gw3 . relu(gW2 h + gb2) + gb3 with h = relu(gW1 z + gb1); for the gradient also
+  // p = gW1^T (m1 (.) gW2^T (m2 (.) gw3)) and grad = sum over levels of (dz_l/dx)^T p_l
   unsigned m1 = 0u;
-#pragma unroll
+#pragma unroll 4
   for (int j = 0; j < kH; ++j) {
     float y = sg[S_gb1 + j];
 #pragma unroll
-    for (int k = 0; k < kZ; ++k) y = fmaf(sg[S_gW1 + j * kZ + k], z[k], y);
+    for (int k4 = 0; k4 < 4; ++k4) {
+      const float4 w = ld4(sg + S_gW1 + j * kZ + 4 * k4);
+      y = fmaf(w.x, z[4 * k4], y);
+      y = fmaf(w.y, z[4 * k4 + 1], y);
+      y = fmaf(w.z, z[4 * k4 + 2], y);
+      y = fmaf(w.w, z[4 * k4 + 3], y);
+    }
     h[j] = fmaxf(y, 0.f);
     m1 |= (y > 0.f ? 1u : 0u) << j;
   }
+  float phi = sg[S_gb3];
   float pm[kH];
 #pragma unroll
   for (int k = 0; k < kH; ++k) pm[k] = 0.f;
@@ -1039,10 +1046,15 @@ __global__ void __launch_bounds__(128) paper_query_kernel(GridDesc g, const floa
     float y = sg[S_gb2 + j];
 #pragma unroll
     for (int k = 0; k < kH; ++k) y = fmaf(sg[S_gW2 + j * kH + k], h[k], y);
-    const float e = y > 0.f ? sg[S_gw3 + j] : 0.f;
+    phi = fmaf(sg[S_gw3 + j], fmaxf(y, 0.f), phi);
+    if (grad) {
+      const float e = y > 0.f ? sg[S_gw3 + j] : 0.f;
 #pragma unroll
-    for (int k = 0; k < kH; ++k) pm[k] = fmaf(sg[S_gW2 + j * kH + k], e, pm[k]);
+      for (int k = 0; k < kH; ++k) pm[k] = fmaf(sg[S_gW2 + j * kH + k], e, pm[k]);
+    }
   }
+  sdf[i] = phi;
+  if (!grad) return;
   float pz[kZ];
 #pragma unroll
   for (int k = 0; k < kZ; ++k) pz[k] = 0.f;

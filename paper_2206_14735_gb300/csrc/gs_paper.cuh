@@ -41,9 +41,10 @@ __device__ __forceinline__ void load_geometry_decoder(const float* __restrict__ 
 }
 
 // phi(x) = gw3 . relu(gW2 relu(gW1 z + gb1) + gb2) + gb3 with z the four levels' trilinear
-// features at x (binary32 cell decisions as everywhere); sg from load_geometry_decoder
+// features at x (binary32 cell decisions as everywhere); sg from load_geometry_decoder; hs
+// (may be nullptr) 32 floats of the calling thread's shared scratch for the hidden layer
 __device__ __forceinline__ float phi_at(const GridDesc& g, const float* __restrict__ theta, const float* sg,
-                                        const float x[3]) {
+                                        const float x[3], float* hs = nullptr) {
   float z[kZ];
 #pragma unroll
   for (int l = 0; l < kLevels; ++l) {
@@ -59,7 +60,8 @@ __device__ __forceinline__ float phi_at(const GridDesc& g, const float* __restri
     z[4 * l + 2] = acc.z;
     z[4 * l + 3] = acc.w;
   }
-  float h[kH];
+  float hr[kH];
+  float* h = hs != nullptr ? hs : hr;  // the caller's shared scratch keeps the 32 values out of registers
 #pragma unroll
   for (int j = 0; j < kH; ++j) {
     float y = sg[S_gb1 + j];
@@ -78,13 +80,7 @@ __device__ __forceinline__ float phi_at(const GridDesc& g, const float* __restri
   for (int j = 0; j < kH; ++j) {
     float y = sg[S_gb2 + j];
 #pragma unroll
-    for (int k4 = 0; k4 < 8; ++k4) {
-      const float4 w = ld4(sg + S_gW2 + j * kH + 4 * k4);
-      y = fmaf(w.x, h[4 * k4], y);
-      y = fmaf(w.y, h[4 * k4 + 1], y);
-      y = fmaf(w.z, h[4 * k4 + 2], y);
-      y = fmaf(w.w, h[4 * k4 + 3], y);
-    }
+    for (int k = 0; k < kH; ++k) y = fmaf(sg[S_gW2 + j * kH + k], h[k], y);
     p = fmaf(sg[S_gw3 + j], fmaxf(y, 0.f), p);
   }
   return p;
