@@ -7,9 +7,10 @@
 // mesh_kernel: one thread per cell; a tetrahedron with 1 or 3 corners below iso gives one
 // triangle, with 2 below two; each vertex is interpolated along its tetrahedron edge from the
 // endpoint of lower lattice index (cells sharing an edge produce the same point), and each
-// triangle is oriented with its normal towards the corners above iso.  A cell's triangles
-// take their slots with one atomic on a 64-bit counter; slots at or past max_tris are counted
-// but not written.
+// triangle is oriented with its normal towards the corners above iso.  A warp's 32 cells take
+// their slots with one atomic on a 64-bit counter (an exclusive warp scan of the per-cell
+// counts places each cell's run; a floor or a wall parallel to x puts a surface cell in every
+// lane); slots at or past max_tris are counted but not written.
 #include <algorithm>
 
 #include "gs_internal.h"
@@ -25,6 +26,22 @@ struct LatticeArgs {
   int nx, ny, nz;
   float* phi;
 };
+
+// (i, j, k) of the flat index id = (k ny + j) nx + i; 32-bit division when every index of
+// the lattice fits in 32 bits (a 64-bit division costs several times as many instructions)
+__device__ __forceinline__ void lattice_ijk(long long id, int nx, int ny, bool narrow, int& i, int& j, int& k) {
+  if (narrow) {
+    const unsigned u = (unsigned)id, q = u / (unsigned)nx;
+    i = (int)(u - q * (unsigned)nx);
+    j = (int)(q % (unsigned)ny);
+    k = (int)(q / (unsigned)ny);
+  } else {
+    const long long q = id / nx;
+    i = (int)(id - q * nx);
+    j = (int)(q % ny);
+    k = (int)(q / ny);
+  }
+}
 
 // kPaper: phi from the paper's two-hidden-layer geometry decoder (GS_ARCH_PAPER)
 template <bool kPaper>
@@ -45,8 +62,10 @@ __global__ void __launch_bounds__(128) lattice_sdf_kernel(LatticeArgs a) {
   }
   __syncthreads();
   const long long np = (long long)a.nx * a.ny * a.nz;
+  const bool narrow = np <= 0xffffffffLL;
   for (long long id = (long long)blockIdx.x * blockDim.x + threadIdx.x; id < np; id += (long long)gridDim.x * blockDim.x) {
-    const int i = (int)(id % a.nx), j = (int)((id / a.nx) % a.ny), k = (int)(id / ((long long)a.nx * a.ny));
+    int i, j, k;
+    lattice_ijk(id, a.nx, a.ny, narrow, i, j, k);
     const float x[3] = {__fadd_rn(a.lo[0], __fmul_rn((float)i, a.step)), __fadd_rn(a.lo[1], __fmul_rn((float)j, a.step)),
                         __fadd_rn(a.lo[2], __fmul_rn((float)k, a.step))};
     a.phi[id] = kPaper ? paper::phi_at(a.g, a.theta, sm, x) : sdf_at(a.g, a.theta, sm, x);
@@ -66,16 +85,28 @@ struct MeshArgs {
 
 __constant__ int kTets[6][4] = {{0, 1, 3, 7}, {0, 3, 2, 7}, {0, 2, 6, 7}, {0, 6, 4, 7}, {0, 4, 5, 7}, {0, 5, 1, 7}};
 
-__device__ __forceinline__ void mesh_edge(const float P[8][3], const float f[8], const long long id[8], int a, int b,
-                                          float iso, float out[3]) {
-  if (id[b] < id[a]) {
-    const int t = a;
-    a = b;
-    b = t;
+// corner q (bit 0: +x, bit 1: +y, bit 2: +z) of the cell with lower corner (i, j, k)
+__device__ __forceinline__ void mesh_corner(const MeshArgs& a, int i, int j, int k, int q, float out[3]) {
+  out[0] = __fadd_rn(a.lo[0], __fmul_rn((float)(i + (q & 1)), a.step));
+  out[1] = __fadd_rn(a.lo[1], __fmul_rn((float)(j + ((q >> 1) & 1)), a.step));
+  out[2] = __fadd_rn(a.lo[2], __fmul_rn((float)(k + (q >> 2)), a.step));
+}
+
+// the point of phi = iso on the edge between corners qa and qb, interpolated from the endpoint
+// of lower lattice index: with nx, ny >= 2 the lattice index of corner q grows with q
+__device__ __forceinline__ void mesh_edge(const MeshArgs& a, int i, int j, int k, const float f[8], int qa, int qb,
+                                          float out[3]) {
+  if (qb < qa) {
+    const int t = qa;
+    qa = qb;
+    qb = t;
   }
-  const float w = (iso - f[a]) / (f[b] - f[a]);
+  const float w = (a.iso - f[qa]) / (f[qb] - f[qa]);
+  float A[3], B[3];
+  mesh_corner(a, i, j, k, qa, A);
+  mesh_corner(a, i, j, k, qb, B);
 #pragma unroll
-  for (int q = 0; q < 3; ++q) out[q] = P[a][q] + w * (P[b][q] - P[a][q]);
+  for (int q = 0; q < 3; ++q) out[q] = A[q] + w * (B[q] - A[q]);
 }
 
 __device__ __forceinline__ void mesh_put(float* dst, const float p0[3], const float p1[3], const float p2[3],
@@ -94,65 +125,87 @@ __device__ __forceinline__ void mesh_put(float* dst, const float p0[3], const fl
 
 __global__ void __launch_bounds__(128) mesh_kernel(MeshArgs a) {
   const long long cx = a.nx - 1, cy = a.ny - 1, ncell = cx * cy * (a.nz - 1);
-  for (long long c = (long long)blockIdx.x * blockDim.x + threadIdx.x; c < ncell; c += (long long)gridDim.x * blockDim.x) {
-    const int i = (int)(c % cx), j = (int)((c / cx) % cy), k = (int)(c / (cx * cy));
-    float P[8][3], f[8];
-    long long id[8];
-    bool below = false, above = false;
+  const int lane = threadIdx.x & 31;
+  const bool narrow = ncell + 32LL * gridDim.x * blockDim.x <= 0xffffffffLL;
+  // the loop runs warp-uniformly (c0 is the same for all lanes) so that the slot scan below
+  // always has the whole warp; lanes past the last cell take part with a count of 0
+  for (long long c0 = (long long)blockIdx.x * blockDim.x + (threadIdx.x & ~31); c0 < ncell;
+       c0 += (long long)gridDim.x * blockDim.x) {
+    const long long c = c0 + lane;
+    const bool live = c < ncell;
+    const long long cc = live ? c : 0;
+    int i, j, k;
+    lattice_ijk(cc, (int)cx, (int)cy, narrow, i, j, k);
+    // the eight values stay in registers (static indices) for the test every cell takes
+    float f[8];
+    unsigned m = 0;  // bit q: corner q below iso
 #pragma unroll
     for (int q = 0; q < 8; ++q) {
-      const int ii = i + (q & 1), jj = j + ((q >> 1) & 1), kk = k + (q >> 2);
-      id[q] = ((long long)kk * a.ny + jj) * a.nx + ii;
-      f[q] = a.phi[id[q]];
-      P[q][0] = __fadd_rn(a.lo[0], __fmul_rn((float)ii, a.step));
-      P[q][1] = __fadd_rn(a.lo[1], __fmul_rn((float)jj, a.step));
-      P[q][2] = __fadd_rn(a.lo[2], __fmul_rn((float)kk, a.step));
-      below |= f[q] < a.iso;
-      above |= !(f[q] < a.iso);
+      f[q] = a.phi[((long long)(k + (q >> 2)) * a.ny + j + ((q >> 1) & 1)) * a.nx + i + (q & 1)];
+      m |= (f[q] < a.iso ? 1u : 0u) << q;
     }
-    if (!(below && above)) continue;
-    // triangles of this cell: count first, then one slot reservation
+    // triangles of this cell: the corners of tetrahedron t below iso are m & kTetMask[t]
     int cnt = 0;
+    if (live && m != 0u && m != 0xffu) {
+      constexpr unsigned kTetMask[6] = {0x8Bu, 0x8Du, 0xC5u, 0xD1u, 0xB1u, 0xA3u};
 #pragma unroll
-    for (int t = 0; t < 6; ++t) {
-      int ni = 0;
-#pragma unroll
-      for (int q = 0; q < 4; ++q) ni += f[kTets[t][q]] < a.iso;
-      cnt += (ni == 0 || ni == 4) ? 0 : (ni == 2 ? 2 : 1);
+      for (int t = 0; t < 6; ++t) {
+        const int ni = __popc(m & kTetMask[t]);
+        cnt += (ni == 0 || ni == 4) ? 0 : (ni == 2 ? 2 : 1);
+      }
     }
-    unsigned long long slot = atomicAdd(a.n_tris, (unsigned long long)cnt);
+    int incl = cnt;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const int v = __shfl_up_sync(0xffffffffu, incl, o);
+      if (lane >= o) incl += v;
+    }
+    unsigned long long base = 0;
+    if (lane == 31 && incl > 0) base = atomicAdd(a.n_tris, (unsigned long long)incl);
+    base = __shfl_sync(0xffffffffu, base, 31);
+    if (cnt == 0) continue;
+    unsigned long long slot = base + (unsigned long long)(incl - cnt);
+    // surface cells only: a copy that the tetrahedra below index by corner number
+    float fs[8];
+#pragma unroll
+    for (int q = 0; q < 8; ++q) fs[q] = f[q];
 #pragma unroll 1
     for (int t = 0; t < 6; ++t) {
       int in[4], out[4], ni = 0, no = 0;
 #pragma unroll
       for (int q = 0; q < 4; ++q) {
         const int v = kTets[t][q];
-        if (f[v] < a.iso) in[ni++] = v;
+        if (fs[v] < a.iso) in[ni++] = v;
         else out[no++] = v;
       }
       if (ni == 0 || no == 0) continue;
-      float dir[3];
+      float dir[3], so[3] = {0.f, 0.f, 0.f}, si[3] = {0.f, 0.f, 0.f}, Pq[3];
+      for (int q = 0; q < no; ++q) {
+        mesh_corner(a, i, j, k, out[q], Pq);
 #pragma unroll
-      for (int d = 0; d < 3; ++d) {
-        float so = 0.f, si = 0.f;
-        for (int q = 0; q < no; ++q) so += P[out[q]][d];
-        for (int q = 0; q < ni; ++q) si += P[in[q]][d];
-        dir[d] = so / (float)no - si / (float)ni;
+        for (int d = 0; d < 3; ++d) so[d] += Pq[d];
       }
+      for (int q = 0; q < ni; ++q) {
+        mesh_corner(a, i, j, k, in[q], Pq);
+#pragma unroll
+        for (int d = 0; d < 3; ++d) si[d] += Pq[d];
+      }
+#pragma unroll
+      for (int d = 0; d < 3; ++d) dir[d] = so[d] / (float)no - si[d] / (float)ni;
       float p0[3], p1[3], p2[3], p3[3];
       if (ni == 1 || no == 1) {
         const int apex = ni == 1 ? in[0] : out[0];
         const int* rest = ni == 1 ? out : in;
-        mesh_edge(P, f, id, apex, rest[0], a.iso, p0);
-        mesh_edge(P, f, id, apex, rest[1], a.iso, p1);
-        mesh_edge(P, f, id, apex, rest[2], a.iso, p2);
+        mesh_edge(a, i, j, k, fs, apex, rest[0], p0);
+        mesh_edge(a, i, j, k, fs, apex, rest[1], p1);
+        mesh_edge(a, i, j, k, fs, apex, rest[2], p2);
         if ((long long)slot < a.max_tris) mesh_put(a.tris + 9 * slot, p0, p1, p2, dir);
         ++slot;
       } else {
-        mesh_edge(P, f, id, in[0], out[0], a.iso, p0);
-        mesh_edge(P, f, id, in[0], out[1], a.iso, p1);
-        mesh_edge(P, f, id, in[1], out[1], a.iso, p2);
-        mesh_edge(P, f, id, in[1], out[0], a.iso, p3);
+        mesh_edge(a, i, j, k, fs, in[0], out[0], p0);
+        mesh_edge(a, i, j, k, fs, in[0], out[1], p1);
+        mesh_edge(a, i, j, k, fs, in[1], out[1], p2);
+        mesh_edge(a, i, j, k, fs, in[1], out[0], p3);
         if ((long long)slot < a.max_tris) mesh_put(a.tris + 9 * slot, p0, p1, p2, dir);
         ++slot;
         if ((long long)slot < a.max_tris) mesh_put(a.tris + 9 * slot, p0, p2, p3, dir);
