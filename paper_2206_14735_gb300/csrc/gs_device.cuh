@@ -138,11 +138,9 @@ __device__ __forceinline__ void sample_pos(const float o[3], const float r[3], f
   for (int a = 0; a < 3; ++a) x[a] = __fadd_rn(o[a], __fmul_rn(t, r[a]));
 }
 
-// phi(x) in FP32 on CUDA cores: trilinear features of the 4 levels, then the SDF decoder's
-// first output; sm holds W1 at sW1, b1 at sb1, row 0 of W2 at sW2 and b2[0] at sb2
-__device__ __forceinline__ float sdf_at(const GridDesc& g, const float* __restrict__ theta, const float* sm,
-                                        const float x[3]) {
-  float z[kZ];
+// z = [f_0(x), ..., f_3(x)]: the four levels' trilinear features, coarse to fine
+__device__ __forceinline__ void grid_z(const GridDesc& g, const float* __restrict__ theta, const float x[3],
+                                       float (&z)[kZ]) {
 #pragma unroll
   for (int l = 0; l < kLevels; ++l) {
     const Cell c = locate(g, l, x);
@@ -157,6 +155,14 @@ __device__ __forceinline__ float sdf_at(const GridDesc& g, const float* __restri
     z[4 * l + 2] = acc.z;
     z[4 * l + 3] = acc.w;
   }
+}
+
+// phi(x) in FP32 on CUDA cores: trilinear features of the 4 levels, then the SDF decoder's
+// first output; sm holds W1 at sW1, b1 at sb1, row 0 of W2 at sW2 and b2[0] at sb2
+__device__ __forceinline__ float sdf_at(const GridDesc& g, const float* __restrict__ theta, const float* sm,
+                                        const float x[3]) {
+  float z[kZ];
+  grid_z(g, theta, x, z);
   float phi = sm[sb2];
 #pragma unroll 8
   for (int j = 0; j < kH1; ++j) {

@@ -3,7 +3,9 @@
 // tetrahedra around its corner-0-to-corner-7 diagonal, which needs no case table and gives a
 // closed surface wherever the lattice values do).
 //
-// lattice_sdf_kernel: phi at lo + (i, j, k) * step (binary32 positions, FP32 SDF).
+// lattice_sdf_pair_kernel / lattice_sdf_paper_kernel: phi at lo + (i, j, k) * step (binary32
+// positions, FP32 SDF) with the workload's decoder (two points per thread, packed FMAs) or the
+// paper's.
 // mesh_kernel: one thread per cell; a tetrahedron with 1 or 3 corners below iso gives one
 // triangle, with 2 below two; each vertex is interpolated along its tetrahedron edge from the
 // endpoint of lower lattice index (cells sharing an edge produce the same point), and each
@@ -43,32 +45,96 @@ __device__ __forceinline__ void lattice_ijk(long long id, int nx, int ny, bool n
   }
 }
 
-// kPaper: phi from the paper's two-hidden-layer geometry decoder (GS_ARCH_PAPER)
-template <bool kPaper>
-__global__ void __launch_bounds__(128) lattice_sdf_kernel(LatticeArgs a) {
-  __shared__ __align__(16) float sm[kPaper ? paper::kGeoPad : sb2 + 4];
-  const float* mlp = a.theta + a.g.n_grid;
-  if (kPaper) {
-    paper::load_geometry_decoder(mlp, sm);
-  } else {
-    for (int i = threadIdx.x; i <= sb2; i += blockDim.x) {
-      float v = 0.f;
-      if (i < sb1) v = mlp[oW1 + i];
-      else if (i < sW2) v = mlp[ob1 + i - sb1];
-      else if (i < sW2 + kH1) v = mlp[oW2 + i - sW2];
-      else if (i == sb2) v = mlp[ob2];
-      sm[i] = v;
-    }
-  }
+// lattice point id's position lo + (i, j, k) step
+__device__ __forceinline__ void lattice_x(const LatticeArgs& a, long long id, bool narrow, float x[3]) {
+  int i, j, k;
+  lattice_ijk(id, a.nx, a.ny, narrow, i, j, k);
+  x[0] = __fadd_rn(a.lo[0], __fmul_rn((float)i, a.step));
+  x[1] = __fadd_rn(a.lo[1], __fmul_rn((float)j, a.step));
+  x[2] = __fadd_rn(a.lo[2], __fmul_rn((float)k, a.step));
+}
+
+// The paper's decoder: one lattice point per thread, phi from its two hidden layers.
+__global__ void __launch_bounds__(128) lattice_sdf_paper_kernel(LatticeArgs a) {
+  __shared__ __align__(16) float sm[paper::kGeoPad];
+  paper::load_geometry_decoder(a.theta + a.g.n_grid, sm);
   __syncthreads();
   const long long np = (long long)a.nx * a.ny * a.nz;
   const bool narrow = np <= 0xffffffffLL;
   for (long long id = (long long)blockIdx.x * blockDim.x + threadIdx.x; id < np; id += (long long)gridDim.x * blockDim.x) {
-    int i, j, k;
-    lattice_ijk(id, a.nx, a.ny, narrow, i, j, k);
-    const float x[3] = {__fadd_rn(a.lo[0], __fmul_rn((float)i, a.step)), __fadd_rn(a.lo[1], __fmul_rn((float)j, a.step)),
-                        __fadd_rn(a.lo[2], __fmul_rn((float)k, a.step))};
-    a.phi[id] = kPaper ? paper::phi_at(a.g, a.theta, sm, x) : sdf_at(a.g, a.theta, sm, x);
+    float x[3];
+    lattice_x(a, id, narrow, x);
+    a.phi[id] = paper::phi_at(a.g, a.theta, sm, x);
+  }
+}
+
+// packed pair of FP32 values: element 0 in the low half
+__device__ __forceinline__ unsigned long long pk2(float lo, float hi) {
+  unsigned long long r;
+  asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(lo), "f"(hi));
+  return r;
+}
+__device__ __forceinline__ void upk2(unsigned long long r, float& lo, float& hi) {
+  asm("mov.b64 {%0, %1}, %2;" : "=f"(lo), "=f"(hi) : "l"(r));
+}
+// both halves: d = a * b + c, each an IEEE fma rounded to nearest, as fmaf
+__device__ __forceinline__ unsigned long long ffma2(unsigned long long a, unsigned long long b, unsigned long long c) {
+  unsigned long long d;
+  asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(d) : "l"(a), "l"(b), "l"(c));
+  return d;
+}
+
+// The workload's decoder: two neighbouring lattice points per thread, their features side by
+// side in packed pairs; every weight is kept twice in shared memory so that one 128-bit
+// broadcast read gives two packed weight pairs and one packed FMA advances both points.  Per
+// point the operations and their order are sdf_at's, so phi is the same to the bit.
+struct LatticePairDecoder {
+  unsigned long long W1[kH1][kZ];  // (W1[j][k], W1[j][k])
+  unsigned long long bw[kH1][2];   // (b1[j], b1[j]), (W2[0][j], W2[0][j])
+  unsigned long long b2;           // (b2[0], b2[0])
+};
+
+__global__ void __launch_bounds__(128) lattice_sdf_pair_kernel(LatticeArgs a) {
+  __shared__ __align__(16) LatticePairDecoder d;
+  const float* mlp = a.theta + a.g.n_grid;
+  for (int i = threadIdx.x; i < kH1 * kZ; i += blockDim.x) {
+    const float v = mlp[oW1 + i];
+    d.W1[i / kZ][i % kZ] = pk2(v, v);
+  }
+  for (int j = threadIdx.x; j < kH1; j += blockDim.x) {
+    d.bw[j][0] = pk2(mlp[ob1 + j], mlp[ob1 + j]);
+    d.bw[j][1] = pk2(mlp[oW2 + j], mlp[oW2 + j]);
+  }
+  if (threadIdx.x == 0) d.b2 = pk2(mlp[ob2], mlp[ob2]);
+  __syncthreads();
+  const long long np = (long long)a.nx * a.ny * a.nz, npair = (np + 1) / 2;
+  const bool narrow = np <= 0xffffffffLL;
+  for (long long p = (long long)blockIdx.x * blockDim.x + threadIdx.x; p < npair; p += (long long)gridDim.x * blockDim.x) {
+    const long long id0 = 2 * p, id1 = id0 + 1 < np ? id0 + 1 : id0;  // an odd count repeats the last point
+    unsigned long long zz[kZ];
+    {
+      float x[3], z0[kZ], z1[kZ];
+      lattice_x(a, id0, narrow, x);
+      grid_z(a.g, a.theta, x, z0);
+      lattice_x(a, id1, narrow, x);
+      grid_z(a.g, a.theta, x, z1);
+#pragma unroll
+      for (int k = 0; k < kZ; ++k) zz[k] = pk2(z0[k], z1[k]);
+    }
+    unsigned long long phi = d.b2;
+#pragma unroll 4
+    for (int j = 0; j < kH1; ++j) {
+      unsigned long long s = d.bw[j][0];
+#pragma unroll
+      for (int k = 0; k < kZ; ++k) s = ffma2(d.W1[j][k], zz[k], s);
+      float s0, s1;
+      upk2(s, s0, s1);
+      phi = ffma2(d.bw[j][1], pk2(fmaxf(s0, 0.f), fmaxf(s1, 0.f)), phi);
+    }
+    float phi0, phi1;
+    upk2(phi, phi0, phi1);
+    a.phi[id0] = phi0;
+    if (id1 != id0) a.phi[id1] = phi1;
   }
 }
 
@@ -233,9 +299,13 @@ gs_status gs_launch_mesh(const gs_ctx* ctx, const float* theta, const float lo[3
   la.nz = nz;
   la.phi = phi;
   const long long np = (long long)nx * ny * nz;
-  const int blocks = (int)std::min<long long>((np + 127) / 128, 64LL * ctx->num_sms);
-  if (ctx->cfg.arch == GS_ARCH_PAPER) lattice_sdf_kernel<true><<<blocks, 128, 0, st>>>(la);
-  else lattice_sdf_kernel<false><<<blocks, 128, 0, st>>>(la);
+  if (ctx->cfg.arch == GS_ARCH_PAPER) {
+    const int blocks = (int)std::min<long long>((np + 127) / 128, 64LL * ctx->num_sms);
+    lattice_sdf_paper_kernel<<<blocks, 128, 0, st>>>(la);
+  } else {
+    const int blocks = (int)std::min<long long>(((np + 1) / 2 + 127) / 128, 64LL * ctx->num_sms);
+    lattice_sdf_pair_kernel<<<blocks, 128, 0, st>>>(la);
+  }
   MeshArgs ma;
   for (int q = 0; q < 3; ++q) ma.lo[q] = lo[q];
   ma.step = step;
