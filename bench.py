@@ -121,6 +121,35 @@ def dist_env():
     return rank, world, local
 
 
+def step_config(w, args, world, n_frames):
+    """The workload and the form of the timed step, as both arms print it (no measured values)."""
+    if w.prop_samples > 0:
+        return {"workload": w.name, "rays": w.rays, "samples_per_ray": w.prop_samples,
+                "guided_of_those": w.prop_guided, "lr_prop": w.lr_prop,
+                "fallback_samples_per_ray": w.n_samples, "pretrain_steps": args.prop_pretrain,
+                "parallelism": f"replicas{world}"}
+    paper = w.arch == "paper"
+    recompute = args.recompute or paper
+    pipelined = w.imp_coarse == 0 and not args.no_pipeline and not args.poses
+    return {"workload": w.name, "rays": w.rays, "samples_per_ray": w.n_samples, "smooth_points": w.n_smooth,
+            "params": w.layout()[2], "grid_params": w.layout()[1], "frames": n_frames,
+            "resolution": [w.width, w.height], "parallelism": f"replicas{world}",
+            "model": ("paper: colour grid (6 features, finest level) + view direction, decoders with "
+                      "2 hidden layers of 32" if paper else "compact: decoders 16-32-16 and 15-32-3"),
+            "activations": "recomputed" if recompute else f"stored ({624 if paper else 396} B/sample)",
+            "sampler": (f"importance: {w.imp_coarse} coarse + {w.imp_steps} x {w.imp_per_step}"
+                        if w.imp_coarse > 0 else f"stratified {w.n_strat} + depth-guided {w.n_guided}"),
+            "pipeline": ("the next step's batch sampled on a side stream during this step (double-buffered)"
+                         if pipelined else "in line"),
+            "calls": ("gs_forward + gs_backward" if args.split else "gs_forward_backward") +
+                     (" + gs_eikonal" if args.eikonal else ""),
+            "loss_terms": "rgb, depth, sdf, fs, smooth" + (", eikonal (lam 1, free-space samples)"
+                                                           if args.eikonal else ""),
+            "poses": ("refined: per-frame (dt, nu), gs_pose_apply + gs_pose_backward + Adam 5e-4 in every step"
+                      if args.poses else "fixed"),
+            "l2": "inputs larger than L2: 1.2 GB of parameter/gradient/moment state streamed per step"}
+
+
 def run_ours(args):
     import numpy as np
     import torch
@@ -340,26 +369,8 @@ def run_ours(args):
         "metric": METRIC, "value": round(value, 1), "unit": "rays/s", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": round(ms / args.steps, 4), "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "bf16" if ctx.bf16 else "f32", "data": "synthetic",
-        "config": {"workload": w.name, "rays": w.rays, "samples_per_ray": w.n_samples,
-                   "samples_per_s": round(value * w.n_samples, 1), "smooth_points": w.n_smooth,
-                   "params": w.layout()[2], "grid_params": n_grid, "frames": fr.depth.shape[0],
-                   "resolution": [w.width, w.height], "parallelism": f"replicas{world}",
-                   "model": ("paper: colour grid (6 features, finest level) + view direction, decoders with "
-                             "2 hidden layers of 32" if paper else "compact: decoders 16-32-16 and 15-32-3"),
-                   "activations": "recomputed" if recompute else
-                                  f"stored ({624 if paper else 396} B/sample)",
-                   "sampler": (f"importance: {w.imp_coarse} coarse + {w.imp_steps} x {w.imp_per_step}"
-                               if w.imp_coarse > 0 else f"stratified {w.n_strat} + depth-guided {w.n_guided}"),
-                   "pipeline": ("the next step's batch sampled on a side stream during this step (double-buffered)"
-                                if pipelined else "in line"),
-                   "calls": ("gs_forward + gs_backward" if args.split else "gs_forward_backward") +
-                            (" + gs_eikonal" if args.eikonal else ""),
-                   "loss_terms": "rgb, depth, sdf, fs, smooth" + (", eikonal (lam 1, free-space samples)"
-                                                                  if args.eikonal else ""),
-                   "poses": ("refined: per-frame (dt, nu), gs_pose_apply + gs_pose_backward + Adam 5e-4 in every step"
-                             if args.poses else "fixed"),
-                   "l2": "inputs larger than L2: 1.2 GB of parameter/gradient/moment state streamed per step",
-                   "frame_render_s": round(t_frames, 1)},
+        "config": step_config(w, args, world, fr.depth.shape[0]),
+        "samples_per_s": round(value * w.n_samples, 1), "frame_render_s": round(t_frames, 1),
         "kernels_ms": {k: round(vv, 4) for k, vv in avg.items()},
         "roofline": {"kernel": ("render call: paper_render_kernel (fused gathers / CUDA-core decoders / compositing "
                                 "/ backward / scatter) + paper_smooth_kernel + paper_combine_kernel" if paper else
@@ -609,10 +620,7 @@ def run_proposal(args):
         "metric": METRIC, "value": round(value, 1), "unit": "rays/s", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": round(ms / args.steps, 4), "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "bf16" if ctx.bf16 else "f32", "data": "synthetic",
-        "config": {"workload": w.name, "rays": w.rays, "samples_per_ray": w.prop_samples,
-                   "guided_of_those": w.prop_guided, "lr_prop": w.lr_prop,
-                   "fallback_samples_per_ray": w.n_samples, "pretrain_steps": args.prop_pretrain,
-                   "parallelism": f"replicas{world}"},
+        "config": step_config(w, args, world, fr.depth.shape[0]),
         "proposal": {"timed_steps_on_proposal": n_prop, "controller_last": trainer.controller.history[-3:],
                      "ce_last": round(float(trainer.ce[0].item()), 5)},
         "clocks": clk,
@@ -684,8 +692,10 @@ def _profiled_traffic(profile: str, sources) -> float | None:
     return traffic if h.hexdigest() == want else None
 
 
-def _oracle_sample_step(w, fr, R, P, n_adam, reps_min_s, reps_max):
-    """Time the oracle on R rays (P smoothness points) plus Adam over n_adam parameters."""
+def _oracle_steps(w, fr, R, P, n_steps, time_cap_s=None, k0=0):
+    """Run n_steps full oracle steps (sample R rays and P smoothness points, FP64 forward and
+    backward, FP64 Adam over every parameter) and return their durations.  With time_cap_s,
+    stop early once that much time has passed (at least one step runs)."""
     import numpy as np
 
     import oracle as oc
@@ -695,11 +705,10 @@ def _oracle_sample_step(w, fr, R, P, n_adam, reps_min_s, reps_max):
     ofr = oc.OcFramesHolder(fr)
     theta = sg.init_params(w).astype(np.float64)
     n = w.layout()[2]
-    mom, vel = np.zeros(n_adam), np.zeros(n_adam)
+    mom, vel = np.zeros(n), np.zeros(n)
     times = []
     t_all = time.perf_counter()
-    k = 0
-    while True:
+    for k in range(k0, k0 + n_steps):
         t0 = time.perf_counter()
         if w.imp_coarse > 0:
             bt = oc.sample_importance(cfg, ofr, theta, 3, k, R, w.imp_coarse, w.imp_steps, w.imp_per_step)
@@ -707,49 +716,49 @@ def _oracle_sample_step(w, fr, R, P, n_adam, reps_min_s, reps_max):
             bt = oc.sample_rays(cfg, ofr, 3, k, R)
         sm = oc.sample_smooth(cfg, ofr, 3, k, P)
         out = oc.step(cfg, theta, bt, sm)
-        g = np.ascontiguousarray(out["grad"][:n_adam])
-        p = np.ascontiguousarray(theta[:n_adam])
-        oc.adam(p, g, mom, vel, min(n_adam, w.layout()[1]), k + 1, w.lr_grid, w.lr_mlp)
-        theta[:n_adam] = p
+        g = np.ascontiguousarray(out["grad"])
+        oc.adam(theta, g, mom, vel, w.layout()[1], k + 1, w.lr_grid, w.lr_mlp)
         times.append(time.perf_counter() - t0)
-        k += 1
-        if k >= reps_max or (time.perf_counter() - t_all) > reps_min_s:
+        if time_cap_s is not None and time.perf_counter() - t_all > time_cap_s:
             break
     return times, oc.num_threads()
 
 
 def cpu_baseline(w, fr, R):
-    times, cores = _oracle_sample_step(w, fr, R, max(1, w.n_smooth * R // w.rays), w.layout()[2], 10.0, 3)
+    P = max(1, w.n_smooth * R // w.rays)
+    times, cores = _oracle_steps(w, fr, R, P, 3, time_cap_s=10.0)
     t = statistics.median(times)
     return {"value": round(R / t, 2), "unit": "rays/s", "cores": cores, "kind": "oracle",
             "sample": f"{len(times)} oracle step(s) of {R} rays x {w.n_samples} samples + "
-                      f"{max(1, w.n_smooth * R // w.rays)} smoothness points + FP64 Adam over all "
+                      f"{P} smoothness points + FP64 Adam over all "
                       f"{w.layout()[2]} parameters; value = rays / median step time"}
 
 
 def run_reference(args):
+    """The oracle as the reference arm: W untimed then exactly K timed full steps of the same
+    workload (every ray, smoothness point and parameter of the GPU arm's step), on the host
+    cores.  Rank 0 only; other ranks exit without work."""
     rank, world, local = dist_env()
     if rank != 0:
         return None
     import scenegen as sg
     w = sg.WORKLOADS[args.workload]
+    if w.prop_samples > 0 or w.arch == "paper":
+        return {"impl": "reference", "unavailable": "the oracle arm covers the plain compact-architecture workloads"}
     fr = sg.make_frames(w, n_frames=args.frames)
-    R = args.ref_rays
-    # per step: R rays and the matching share of smoothness points and of the dense Adam pass
-    frac = R / w.rays
-    n_adam = max(4, int(w.layout()[2] * frac) // 4 * 4)
-    P = max(1, int(w.n_smooth * frac))
-    _oracle_sample_step(w, fr, R, P, n_adam, 0.0, args.warmup)  # warm-up steps
+    _oracle_steps(w, fr, w.rays, w.n_smooth, args.warmup)
     t0 = time.perf_counter()
-    times, cores = _oracle_sample_step(w, fr, R, P, n_adam, 0.0, args.steps)
+    times, cores = _oracle_steps(w, fr, w.rays, w.n_smooth, args.steps, k0=args.warmup)
     total = time.perf_counter() - t0
-    value = R * len(times) / total
-    sample = (f"per step {R} rays x {w.n_samples} samples, {P} smoothness points and FP64 Adam over {n_adam} "
-              f"parameters (the same {frac:.4f} share of the step's dense update)")
+    assert len(times) == args.steps
+    value = w.rays * args.steps / total
+    sample = (f"every step in full: {w.rays} rays x {w.n_samples} samples, {w.n_smooth} smoothness points, "
+              f"FP64 forward + backward and FP64 Adam over all {w.layout()[2]} parameters; "
+              f"{args.warmup} untimed + {args.steps} timed steps")
     return {"impl": "reference", "metric": METRIC, "value": round(value, 2), "unit": "rays/s", "n_gpus": world,
-            "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(1e3 * total / len(times), 3),
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(1e3 * total / args.steps, 3),
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-            "data": "synthetic", "config": {"workload": w.name, "rays": w.rays, "samples_per_ray": w.n_samples},
+            "data": "synthetic", "config": step_config(w, args, world, fr.depth.shape[0]),
             "cpu_baseline": {"value": round(value, 2), "unit": "rays/s", "cores": cores, "kind": "oracle",
                              "sample": sample},
             "e2e": {"value": round(value, 2), "unit": "rays/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
@@ -765,7 +774,6 @@ def main():
     ap.add_argument("--frames", type=int, default=None, help="render only the first F poses (default: all)")
     ap.add_argument("--e2e-steps", type=int, default=50)
     ap.add_argument("--cpu-rays", type=int, default=8192)
-    ap.add_argument("--ref-rays", type=int, default=128)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--traffic-render", type=float, default=None)
     ap.add_argument("--traffic-adam", type=float, default=None)

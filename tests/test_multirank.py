@@ -2,6 +2,7 @@
 so the replicas exchange nothing but their timings)."""
 import os
 import sys
+import time
 
 import numpy as np
 import pytest
@@ -61,5 +62,37 @@ def test_reference_arm_other_ranks_exit_without_work(monkeypatch):
     monkeypatch.setenv("WORLD_SIZE", "2")
 
     class Args:
-        workload, frames, ref_rays, warmup, steps = "room-8192x96", 1, 8, 0, 1
+        workload, frames, warmup, steps = "room-8192x96", 1, 0, 1
     assert bench.run_reference(Args()) is None
+
+
+class _RefArgs:
+    workload, frames, warmup, steps = "cube-1024x64", None, 1, 2
+    recompute = no_pipeline = poses = split = eikonal = False
+    prop_pretrain = 300
+
+
+def test_reference_arm_times_the_steps_it_prints(monkeypatch):
+    """Rank 0 of the reference arm runs W + K full oracle steps of the GPU arm's workload and
+    prints K, the GPU arm's config and a per-step time that covers K steps."""
+    import bench
+    import scenegen as sg
+    monkeypatch.setenv("RANK", "0")
+    monkeypatch.setenv("WORLD_SIZE", "1")
+    calls = []
+    real = bench._oracle_steps
+
+    def spy(w, fr, R, P, n_steps, **kw):
+        calls.append((R, P, n_steps))
+        return real(w, fr, R, P, n_steps, **kw)
+
+    monkeypatch.setattr(bench, "_oracle_steps", spy)
+    t0 = time.perf_counter()
+    line = bench.run_reference(_RefArgs())
+    wall = time.perf_counter() - t0
+    w = sg.WORKLOADS["cube-1024x64"]
+    assert calls == [(w.rays, w.n_smooth, 1), (w.rays, w.n_smooth, 2)]
+    assert line["impl"] == "reference" and line["steps"] == 2 and line["warmup"] == 1
+    assert line["config"] == bench.step_config(w, _RefArgs(), 1, 1)
+    assert 2 * line["ms_per_step"] / 1e3 <= wall
+    assert abs(line["value"] - w.rays / (line["ms_per_step"] / 1e3)) <= 1e-3 * line["value"] + 0.01
