@@ -334,12 +334,18 @@ gs_status gs_voxel_index(gs_ctx* ctx, const float* x, int32_t P, int64_t* out, v
  * It takes the configuration instead of a context and allocates nothing: the kernels'
  * per-CTA partial rows live in a file-scope device array of 3.04 MB (rows for 448 CTAs),
  * which every GPU that loads the library holds until the process exits.  Devices with more
- * than 320 SMs are rejected with GS_ERR_UNSUPPORTED.  The first call on a device resolves the
- * array's device address and writes its default dloss (a synchronous set-up), so make that
- * first call before any stream capture.  All calls share the array: calls whose work
- * overlaps on the GPU (other streams, other host threads) race and give wrong results.
- * FP32 form only (cfg->precision must be GS_PREC_FP32).  Arguments, outputs and errors as
- * gs_forward_backward; messages via gs_last_error(NULL). */
+ * than 320 SMs are rejected with GS_ERR_UNSUPPORTED.  Every call resolves the array's device
+ * address on the current device (cudaGetSymbolAddress, no allocation); the first call on a
+ * device may also load the library's device code, so make that first call before any stream
+ * capture.  All calls share the array: calls whose work overlaps on the GPU (other streams,
+ * other host threads) race and give wrong results.  Each call starts by clearing the array's
+ * status word and writing its default dloss on the stream (so nothing depends on an earlier
+ * call) and ends by writing NaN into all six loss entries if a device-side check of this call
+ * failed (a bounded wait of the render kernel that ran out): without a context there is no
+ * gs_sync_status, so a caller checks the losses it reads back.  Configurations are checked by
+ * the same rules as gs_create (same status codes); FP32 form and GS_ARCH_COMPACT only
+ * (GS_ERR_UNSUPPORTED otherwise).  Arguments, outputs and errors as gs_forward_backward;
+ * messages via gs_last_error(NULL). */
 gs_status gs_forward_backward_noalloc(const gs_config* cfg, const float* theta, const gs_batch* batch,
                                       const float* dloss, float* loss, float* grad, void* stream);
 

@@ -67,6 +67,41 @@ gs_status check_frames(gs_ctx* ctx, const gs_frames* frames, const char* who) {
 // Records a message for gs_last_error(NULL) (used by entry points that have no context).
 void gs_set_thread_error(const char* msg) { g_err = msg; }
 
+// Checks a configuration without touching the device.  Returns GS_OK, or the status and a
+// message (without the caller's name) for the first violated rule.  gs_create and
+// gs_forward_backward_noalloc share it, so both accept exactly the same configurations.
+gs_status gs_check_config(const gs_config* cfg, const char** msg) {
+  auto bad = [&](gs_status s, const char* m) { *msg = m; return s; };
+  for (int l = 0; l < GS_LEVELS; ++l) {
+    for (int a = 0; a < 3; ++a)
+      if (cfg->dims[l][a] < 2) return bad(GS_ERR_INVALID_ARG, "every level needs >= 2 vertices per axis");
+    if (!(cfg->voxel[l] > 0.0f)) return bad(GS_ERR_INVALID_ARG, "voxel size must be > 0");
+  }
+  for (int l = 0; l < 2; ++l)  // the coarse-level scatters key their runs by a 32-bit vertex index
+    if (level_floats(cfg, l) / GS_FEAT >= (1LL << 31))
+      return bad(GS_ERR_UNSUPPORTED, "levels 0 and 1 must have fewer than 2^31 vertices");
+  const int N = cfg->n_strat + cfg->n_guided;
+  if (cfg->n_strat < 1 || cfg->n_guided < 0 || N < 2) return bad(GS_ERR_INVALID_ARG, "need n_strat >= 1 and N >= 2");
+  if (N > GS_MAX_SAMPLES) return bad(GS_ERR_UNSUPPORTED, "this build renders at most 160 samples per ray");
+  if (cfg->imp_coarse != 0 &&
+      (cfg->imp_coarse < 2 || cfg->imp_steps < 0 || cfg->imp_per_step < 1 || cfg->imp_per_step > 32 ||
+       imp_samples(cfg) > GS_MAX_SAMPLES))
+    return bad(GS_ERR_INVALID_ARG,
+               "the importance sampler needs imp_coarse >= 2, 1 <= imp_per_step <= 32 and at most 160 samples");
+  if (!(cfg->far_m > cfg->near_m) || !(cfg->trunc > 0.0f) || !(cfg->guide_half >= 0.0f))
+    return bad(GS_ERR_INVALID_ARG, "bad near/far/trunc/guide_half");
+  if (cfg->max_rays < 0 || cfg->max_smooth < 0) return bad(GS_ERR_INVALID_ARG, "negative batch bound");
+  if (cfg->prop_samples != 0 &&
+      (cfg->prop_samples < 2 || cfg->prop_samples > GS_PROP_BINS || cfg->prop_guided < 0 ||
+       cfg->prop_guided >= cfg->prop_samples))
+    return bad(GS_ERR_INVALID_ARG, "need 2 <= prop_samples <= 32 and 0 <= prop_guided < prop_samples");
+  if (cfg->arch != GS_ARCH_COMPACT && cfg->arch != GS_ARCH_PAPER)
+    return bad(GS_ERR_INVALID_ARG, "arch must be GS_ARCH_COMPACT or GS_ARCH_PAPER");
+  if (cfg->arch == GS_ARCH_PAPER && cfg->precision != GS_PREC_FP32)
+    return bad(GS_ERR_UNSUPPORTED, "GS_ARCH_PAPER runs in FP32");
+  return GS_OK;
+}
+
 extern "C" {
 
 int64_t gs_param_count(const gs_config* cfg, int64_t* n_grid) {
@@ -81,33 +116,10 @@ int64_t gs_param_count(const gs_config* cfg, int64_t* n_grid) {
 gs_status gs_create(const gs_config* cfg, gs_ctx** out) {
   if (!cfg || !out) return fail(nullptr, GS_ERR_INVALID_ARG, "gs_create: NULL argument");
   *out = nullptr;
-  for (int l = 0; l < GS_LEVELS; ++l) {
-    for (int a = 0; a < 3; ++a)
-      if (cfg->dims[l][a] < 2) return fail(nullptr, GS_ERR_INVALID_ARG, "gs_create: every level needs >= 2 vertices per axis");
-    if (!(cfg->voxel[l] > 0.0f)) return fail(nullptr, GS_ERR_INVALID_ARG, "gs_create: voxel size must be > 0");
-  }
-  for (int l = 0; l < 2; ++l)  // the coarse-level scatters key their runs by a 32-bit vertex index
-    if (level_floats(cfg, l) / GS_FEAT >= (1LL << 31))
-      return fail(nullptr, GS_ERR_UNSUPPORTED, "gs_create: levels 0 and 1 must have fewer than 2^31 vertices");
+  const char* why = nullptr;
+  const gs_status cs = gs_check_config(cfg, &why);
+  if (cs != GS_OK) return fail(nullptr, cs, (std::string("gs_create: ") + why).c_str());
   const int N = cfg->n_strat + cfg->n_guided;
-  if (cfg->n_strat < 1 || cfg->n_guided < 0 || N < 2) return fail(nullptr, GS_ERR_INVALID_ARG, "gs_create: need n_strat >= 1 and N >= 2");
-  if (N > GS_MAX_SAMPLES) return fail(nullptr, GS_ERR_UNSUPPORTED, "gs_create: this build renders at most 160 samples per ray");
-  if (cfg->imp_coarse != 0 &&
-      (cfg->imp_coarse < 2 || cfg->imp_steps < 0 || cfg->imp_per_step < 1 || cfg->imp_per_step > 32 ||
-       imp_samples(cfg) > GS_MAX_SAMPLES))
-    return fail(nullptr, GS_ERR_INVALID_ARG,
-                "gs_create: the importance sampler needs imp_coarse >= 2, 1 <= imp_per_step <= 32 and at most 160 samples");
-  if (!(cfg->far_m > cfg->near_m) || !(cfg->trunc > 0.0f) || !(cfg->guide_half >= 0.0f))
-    return fail(nullptr, GS_ERR_INVALID_ARG, "gs_create: bad near/far/trunc/guide_half");
-  if (cfg->max_rays < 0 || cfg->max_smooth < 0) return fail(nullptr, GS_ERR_INVALID_ARG, "gs_create: negative batch bound");
-  if (cfg->prop_samples != 0 &&
-      (cfg->prop_samples < 2 || cfg->prop_samples > GS_PROP_BINS || cfg->prop_guided < 0 ||
-       cfg->prop_guided >= cfg->prop_samples))
-    return fail(nullptr, GS_ERR_INVALID_ARG, "gs_create: need 2 <= prop_samples <= 32 and 0 <= prop_guided < prop_samples");
-  if (cfg->arch != GS_ARCH_COMPACT && cfg->arch != GS_ARCH_PAPER)
-    return fail(nullptr, GS_ERR_INVALID_ARG, "gs_create: arch must be GS_ARCH_COMPACT or GS_ARCH_PAPER");
-  if (cfg->arch == GS_ARCH_PAPER && cfg->precision != GS_PREC_FP32)
-    return fail(nullptr, GS_ERR_UNSUPPORTED, "gs_create: GS_ARCH_PAPER runs in FP32");
 
   gs_ctx* c = new (std::nothrow) gs_ctx();
   if (!c) return fail(nullptr, GS_ERR_INVALID_ARG, "gs_create: out of host memory");

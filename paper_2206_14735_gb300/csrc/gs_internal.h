@@ -82,6 +82,8 @@ gs_status gs_launch_query(const gs_ctx* ctx, const float* theta, const float* x,
                           cudaStream_t st);
 gs_status gs_launch_voxel_index(const gs_ctx* ctx, const float* x, int P, long long* out, cudaStream_t st);
 void gs_set_thread_error(const char* msg);
+// Host-side configuration rules shared by gs_create and gs_forward_backward_noalloc.
+gs_status gs_check_config(const gs_config* cfg, const char** msg);
 int gs_paper_part_rows(int num_sms);
 int gs_paper_store_fields();  // floats per sample of the paper architecture's stored activations
 size_t gs_paper_part_floats(int num_sms);

@@ -7,7 +7,7 @@
 // The fused render kernel needs per-CTA partial rows (loss sums and decoder-gradient sums)
 // that gs_create would otherwise allocate.  Here they live in one file-scope device array
 // of fixed size, which every GPU that loads this library holds until the process exits.
-#include <mutex>
+#include <cmath>
 
 #include "gs_internal.h"
 
@@ -20,26 +20,18 @@ constexpr size_t kNoAllocFloats = (size_t)kNoAllocRows * (kLossPad + kMlpPad) + 
 
 __device__ __align__(256) float g_noalloc_scratch[kNoAllocFloats];  // 3.04 MB
 
-constexpr int kMaxDevices = 64;
-std::mutex g_setup_mu;
-float* g_scratch_ptr[kMaxDevices] = {};  // device address of g_noalloc_scratch, per device
+// Stream-ordered start of a call: the default upstream derivative (0,0,0,0,0,1) and a
+// cleared status word, so neither depends on what an earlier call left in the array.
+__global__ void noalloc_begin_kernel(float* default_dloss, int* status) {
+  if (threadIdx.x < 8) default_dloss[threadIdx.x] = threadIdx.x == 5 ? 1.0f : 0.0f;
+  if (threadIdx.x == 0) *status = 0;
+}
 
-// Once per device, with that device current: the array's device address (the host-side
-// name is only a stand-in) and the default upstream derivative (0,0,0,0,0,1).
-gs_status setup_device(int dev, float** out) {
-  std::lock_guard<std::mutex> lock(g_setup_mu);
-  if (g_scratch_ptr[dev] == nullptr) {
-    float* p = nullptr;
-    if (cudaGetSymbolAddress(reinterpret_cast<void**>(&p), g_noalloc_scratch) != cudaSuccess || p == nullptr)
-      return GS_ERR_CUDA;
-    const float dl[16] = {0.f, 0.f, 0.f, 0.f, 0.f, 1.f};  // default dloss, then a zeroed status word
-    if (cudaMemcpy(p + (size_t)kNoAllocRows * (kLossPad + kMlpPad), dl, sizeof(dl), cudaMemcpyHostToDevice) !=
-        cudaSuccess)
-      return GS_ERR_CUDA;
-    g_scratch_ptr[dev] = p;
-  }
-  *out = g_scratch_ptr[dev];
-  return GS_OK;
+// Stream-ordered end of a call: a device-side failure of this call (a bounded wait of the
+// render kernel that ran out) turns every loss entry into NaN, because no context exists
+// whose status gs_sync_status could report.
+__global__ void noalloc_end_kernel(const int* status, float* loss) {
+  if (threadIdx.x < 6 && *status != 0) loss[threadIdx.x] = nanf("");
 }
 
 }  // namespace
@@ -52,19 +44,17 @@ static gs_status noalloc_fail(gs_status s, const char* msg) {
 extern "C" gs_status gs_forward_backward_noalloc(const gs_config* cfg, const float* theta, const gs_batch* batch,
                                                  const float* dloss, float* loss, float* grad, void* stream) {
   if (!cfg) return noalloc_fail(GS_ERR_INVALID_ARG, "gs_forward_backward_noalloc: cfg is NULL");
-  for (int l = 0; l < GS_LEVELS; ++l) {
-    for (int a = 0; a < 3; ++a)
-      if (cfg->dims[l][a] < 2)
-        return noalloc_fail(GS_ERR_INVALID_ARG, "gs_forward_backward_noalloc: every level needs >= 2 vertices per axis");
-    if (!(cfg->voxel[l] > 0.0f)) return noalloc_fail(GS_ERR_INVALID_ARG, "gs_forward_backward_noalloc: voxel size must be > 0");
+  const char* why = nullptr;
+  const gs_status cs = gs_check_config(cfg, &why);
+  if (cs != GS_OK) {
+    gs_set_thread_error((std::string("gs_forward_backward_noalloc: ") + why).c_str());
+    return cs;
   }
   if (cfg->precision != GS_PREC_FP32)
     return noalloc_fail(GS_ERR_UNSUPPORTED, "gs_forward_backward_noalloc: FP32 form only");
   if (cfg->arch != GS_ARCH_COMPACT)
     return noalloc_fail(GS_ERR_UNSUPPORTED, "gs_forward_backward_noalloc: GS_ARCH_COMPACT only");
   const int N = cfg->n_strat + cfg->n_guided;
-  if (cfg->n_strat < 1 || cfg->n_guided < 0 || N < 2 || N > GS_MAX_SAMPLES)
-    return noalloc_fail(GS_ERR_SHAPE, "gs_forward_backward_noalloc: samples per ray must be in [2, 160]");
   if (!theta || !loss || !grad || !batch) return noalloc_fail(GS_ERR_INVALID_ARG, "gs_forward_backward_noalloc: NULL argument");
   if ((reinterpret_cast<uintptr_t>(theta) & 15u) || (reinterpret_cast<uintptr_t>(grad) & 15u))
     return noalloc_fail(GS_ERR_ALIGN, "gs_forward_backward_noalloc: theta and grad must be 16-byte aligned");
@@ -76,14 +66,17 @@ extern "C" gs_status gs_forward_backward_noalloc(const gs_config* cfg, const flo
   if (batch->P > 0 && (!batch->xs || !batch->eps || !batch->valid))
     return noalloc_fail(GS_ERR_INVALID_ARG, "gs_forward_backward_noalloc: batch smoothness array is NULL");
   int dev = 0, sms = 0;
-  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices ||
+  if (cudaGetDevice(&dev) != cudaSuccess ||
       cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
     return noalloc_fail(GS_ERR_CUDA, "gs_forward_backward_noalloc: no usable CUDA device");
   if (kRenderCtasPerSm * sms + kSmoothCtas > kNoAllocRows)
     return noalloc_fail(GS_ERR_UNSUPPORTED,
                         "gs_forward_backward_noalloc: the static scratch holds partial rows for at most 320 SMs");
+  // The array's device address on the current device (its host-side name is only a stand-in).
+  // Resolved on every call, so nothing cached can outlive a cudaDeviceReset; the first call
+  // on a device may also load the module.
   float* scratch = nullptr;
-  if (setup_device(dev, &scratch) != GS_OK)
+  if (cudaGetSymbolAddress(reinterpret_cast<void**>(&scratch), g_noalloc_scratch) != cudaSuccess || !scratch)
     return noalloc_fail(GS_ERR_CUDA, "gs_forward_backward_noalloc: could not resolve the static scratch array");
 
   // a context on the stack whose workspace points into the static array (no allocation)
@@ -109,6 +102,9 @@ extern "C" gs_status gs_forward_backward_noalloc(const gs_config* cfg, const flo
   c.status = reinterpret_cast<int*>(c.default_dloss + 8);  // device-side check word
   const float* dl = dloss ? dloss : c.default_dloss;
   cudaStream_t st = (cudaStream_t)stream;
+  noalloc_begin_kernel<<<1, 32, 0, st>>>(c.default_dloss, c.status);
+  if (cudaGetLastError() != cudaSuccess)
+    return noalloc_fail(GS_ERR_CUDA, "gs_forward_backward_noalloc: launch failed");
   if (batch->R > 0 && gs_launch_render(&c, theta, nullptr, batch, dl, grad, nullptr, nullptr, nullptr, 3, st) != GS_OK)
     return noalloc_fail(GS_ERR_CUDA, "gs_forward_backward_noalloc: render launch failed");
   if (gs_launch_smooth(&c, theta, batch, dl, grad, 3, st) != GS_OK)
@@ -121,5 +117,8 @@ extern "C" gs_status gs_forward_backward_noalloc(const gs_config* cfg, const flo
   }
   if (gs_launch_finalize(&c, batch, loss, grad, 3, st) != GS_OK)
     return noalloc_fail(GS_ERR_CUDA, "gs_forward_backward_noalloc: finalize launch failed");
+  noalloc_end_kernel<<<1, 32, 0, st>>>(c.status, loss);
+  if (cudaGetLastError() != cudaSuccess)
+    return noalloc_fail(GS_ERR_CUDA, "gs_forward_backward_noalloc: launch failed");
   return GS_OK;
 }

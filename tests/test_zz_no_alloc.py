@@ -21,9 +21,20 @@ from paper_2206_14735_gb300 import _lib
 pytestmark = pytest.mark.gpu
 
 
-def test_noalloc_matches_forward_backward_twice():
+def _noalloc(cfg, theta, b, dl, loss, grad):
+    L = _lib.lib()
+    stream = ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+    return L.gs_forward_backward_noalloc(ctypes.byref(cfg), ctypes.c_void_p(theta.data_ptr()), ctypes.byref(b),
+                                         ctypes.c_void_p(0 if dl is None else dl.data_ptr()),
+                                         ctypes.c_void_p(loss.data_ptr()), ctypes.c_void_p(grad.data_ptr()), stream)
+
+
+# rays and smoothness points; rays only (no smoothness rows to combine); smoothness points only
+# (the rows start after the render CTAs' rows)
+@pytest.mark.parametrize("R,P", [(None, None), (None, 0), (0, None)])
+def test_noalloc_matches_forward_backward_twice(R, P):
     p = Problem(CUBE)
-    batch = p.gpu_sample(7, 3)
+    batch = p.gpu_sample(7, 3, R=R, P=P)
     theta = torch.from_numpy(sdf_parity_params(CUBE, sg.cube_scene(), seed=21)).cuda()
     # existing entry point (context workspace)
     loss_ref = torch.empty(6, device="cuda")
@@ -33,17 +44,16 @@ def test_noalloc_matches_forward_backward_twice():
     L = _lib.lib()
     cfg = gs.make_config(CUBE)
     b = batch.struct()
-    stream = ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
     dl = torch.tensor([0.0, 0.0, 0.0, 0.0, 0.0, 1.0], device="cuda")
     for call in range(2):
         loss = torch.full((6,), float("nan"), device="cuda")
         grad = torch.zeros_like(theta)
-        st = L.gs_forward_backward_noalloc(ctypes.byref(cfg), ctypes.c_void_p(theta.data_ptr()), ctypes.byref(b),
-                                           ctypes.c_void_p(dl.data_ptr() if call else 0),
-                                           ctypes.c_void_p(loss.data_ptr()), ctypes.c_void_p(grad.data_ptr()), stream)
+        st = _noalloc(cfg, theta, b, dl if call else None, loss, grad)
         assert st == 0, L.gs_last_error(None)
         torch.cuda.synchronize()
         got, ref = loss.cpu().numpy().astype(np.float64), loss_ref.cpu().numpy().astype(np.float64)
+        # every entry finite: the call's status word (cleared at its start) reports no failure
+        assert np.isfinite(got).all(), got
         np.testing.assert_array_less(np.abs(got - ref), LOSS_RTOL * np.abs(ref) + 1e-12)
         assert_grad_close(p, grad.cpu().numpy(), grad_ref.cpu().numpy())
 
@@ -52,9 +62,33 @@ def test_noalloc_rejects_bad_arguments():
     L = _lib.lib()
     cfg = gs.make_config(CUBE)
     assert L.gs_forward_backward_noalloc(None, None, None, None, None, None, None) == 1
-    bad = gs.make_config(CUBE)
-    bad.voxel[1] = -1.0
-    assert L.gs_forward_backward_noalloc(ctypes.byref(bad), None, None, None, None, None, None) == 1
     theta = torch.zeros(CUBE.layout()[2], device="cuda")
-    assert L.gs_forward_backward_noalloc(ctypes.byref(cfg), ctypes.c_void_p(theta.data_ptr()), None, None, None,
-                                         None, None) == 1
+    th = ctypes.c_void_p(theta.data_ptr())
+    assert L.gs_forward_backward_noalloc(ctypes.byref(cfg), th, None, None, None, None, None) == 1
+
+    def code(**change):
+        bad = gs.make_config(CUBE)
+        for k, v in change.items():
+            if k == "voxel1":
+                bad.voxel[1] = v
+            elif k == "dims0":
+                bad.dims[0][0] = v
+            elif k == "dims1_huge":
+                bad.dims[1][0], bad.dims[1][1], bad.dims[1][2] = 2048, 2048, 512
+            else:
+                setattr(bad, k, v)
+        return L.gs_forward_backward_noalloc(ctypes.byref(bad), th, None, None, None, None, None)
+
+    # the rules gs_create applies, with its status codes
+    assert code(voxel1=-1.0) == 1
+    assert code(dims0=1) == 1
+    assert code(dims1_huge=True) == 6  # 2^31 vertices on level 1: the run keys are 32-bit
+    assert code(near_m=5.0, far_m=1.0) == 1
+    assert code(trunc=0.0) == 1
+    assert code(guide_half=-0.1) == 1
+    assert code(n_strat=0) == 1
+    assert code(n_strat=150, n_guided=20) == 6
+    assert code(max_rays=-1) == 1
+    # forms this entry point does not run
+    assert code(precision=gs.GS_PREC_BF16) == 6
+    assert code(arch=gs.GS_ARCH_PAPER) == 6
