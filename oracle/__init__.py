@@ -62,64 +62,116 @@ def lib():
     global _LIB
     with _LOCK:
         if _LIB is None:
-            L = ctypes.CDLL(build())
-            vp, i32, i64, u64, u32, dbl = (ctypes.c_void_p, ctypes.c_int, ctypes.c_int64, ctypes.c_uint64,
-                                          ctypes.c_uint32, ctypes.c_double)
-            L.oc_sm64.restype = u64
-            L.oc_sm64.argtypes = [u64]
-            L.oc_composite.restype = None
-            L.oc_composite.argtypes = [i32, vp, dbl, vp, vp, vp, vp, vp, vp]
-            L.oc_draw.restype = u64
-            L.oc_draw.argtypes = [u64, u64, u64, u64, u64]
-            L.oc_sample_rays.restype = None
-            L.oc_sample_rays.argtypes = [vp, vp, u64, u32, i32] + [vp] * 8
-            L.oc_sample_smooth.restype = None
-            L.oc_sample_smooth.argtypes = [vp, vp, u64, u32, i32, vp, vp, vp, vp]
-            L.oc_step.restype = i32
-            L.oc_step.argtypes = [vp, vp, i32, i32] + [vp] * 6 + [i32] + [vp] * 12
-            L.oc_prop_forward.restype = None
-            L.oc_prop_forward.argtypes = [vp, vp, vp, i32, vp, vp, vp]
-            L.oc_prop_ce.restype = dbl
-            L.oc_prop_ce.argtypes = [vp, vp, vp, i32, i32, vp, vp, vp, vp, vp, vp]
-            L.oc_prop_sample.restype = None
-            L.oc_prop_sample.argtypes = [vp, i32, i32, i32, vp, vp, ctypes.c_uint64, ctypes.c_uint32, vp, vp, vp]
-            L.oc_query_sdf.restype = None
-            L.oc_query_sdf.argtypes = [vp, vp, vp, i32, vp, vp]
-            L.oc_query_sdf_backward.restype = None
-            L.oc_query_sdf_backward.argtypes = [vp, vp, vp, i32, vp, vp, vp]
-            L.oc_eikonal.restype = i64
-            L.oc_eikonal.argtypes = [vp, vp, i32, i32, vp, vp, vp, vp, dbl, vp, vp, vp]
-            L.oc_sample_importance.restype = i32
-            L.oc_sample_importance.argtypes = [vp, vp, vp, u64, u32, i32, i32, i32, i32] + [vp] * 9
-            L.oc_extract_mesh.restype = i64
-            L.oc_extract_mesh.argtypes = [vp, vp, vp, ctypes.c_float, i32, i32, i32, dbl, vp, i64, vp]
-            L.oc_step_dz.restype = i32
-            L.oc_step_dz.argtypes = [vp, vp, i32, i32] + [vp] * 6 + [i32] + [vp] * 7
-            L.oc_pose_apply.restype = None
-            L.oc_pose_apply.argtypes = [vp, vp, i32, vp]
-            L.oc_rays_of_pixels.restype = None
-            L.oc_rays_of_pixels.argtypes = [vp, vp, i32, vp, vp]
-            L.oc_pose_grad.restype = None
-            L.oc_pose_grad.argtypes = [vp, vp, vp, vp, vp, i32, i32] + [vp] * 6
-            L.oc_voxel_index.restype = None
-            L.oc_voxel_index.argtypes = [vp, vp, i32, vp]
-            L.oc_trilinear_coeffs.restype = None
-            L.oc_trilinear_coeffs.argtypes = [vp, vp, vp]
-            L.oc_trilinear_hessian.restype = None
-            L.oc_trilinear_hessian.argtypes = [vp, vp, vp]
-            L.oc_adam.restype = None
-            L.oc_adam.argtypes = [vp, vp, vp, vp, i64, i64, i32, dbl, dbl, dbl, dbl, dbl]
-            L.oc_num_threads.restype = i32
-            L.oc_paper_param_count.restype = i64
-            L.oc_paper_param_count.argtypes = [vp, vp]
-            L.oc_step_paper.restype = i32
-            L.oc_step_paper.argtypes = [vp, vp, i32, i32] + [vp] * 6 + [i32] + [vp] * 12
-            L.oc_step_paper_dz.restype = i32
-            L.oc_step_paper_dz.argtypes = [vp, vp, i32, i32] + [vp] * 6 + [i32] + [vp] * 7
-            L.oc_pose_grad_paper.restype = None
-            L.oc_pose_grad_paper.argtypes = [vp, vp, vp, vp, vp, i32, i32] + [vp] * 6
-            _LIB = L
+            _LIB = _load(build())
     return _LIB
+
+
+def _load(path: str):
+    """Open one build of the oracle and declare its entry points."""
+    L = ctypes.CDLL(path)
+    vp, i32, i64, u64, u32, dbl = (ctypes.c_void_p, ctypes.c_int, ctypes.c_int64, ctypes.c_uint64,
+                                   ctypes.c_uint32, ctypes.c_double)
+    L.oc_sm64.restype = u64
+    L.oc_sm64.argtypes = [u64]
+    L.oc_composite.restype = None
+    L.oc_composite.argtypes = [i32, vp, dbl, vp, vp, vp, vp, vp, vp]
+    L.oc_draw.restype = u64
+    L.oc_draw.argtypes = [u64, u64, u64, u64, u64]
+    L.oc_sample_rays.restype = None
+    L.oc_sample_rays.argtypes = [vp, vp, u64, u32, i32] + [vp] * 8
+    L.oc_sample_smooth.restype = None
+    L.oc_sample_smooth.argtypes = [vp, vp, u64, u32, i32, vp, vp, vp, vp]
+    L.oc_step.restype = i32
+    L.oc_step.argtypes = [vp, vp, i32, i32] + [vp] * 6 + [i32] + [vp] * 12
+    L.oc_prop_forward.restype = None
+    L.oc_prop_forward.argtypes = [vp, vp, vp, i32, vp, vp, vp]
+    L.oc_prop_ce.restype = dbl
+    L.oc_prop_ce.argtypes = [vp, vp, vp, i32, i32, vp, vp, vp, vp, vp, vp]
+    L.oc_prop_sample.restype = None
+    L.oc_prop_sample.argtypes = [vp, i32, i32, i32, vp, vp, ctypes.c_uint64, ctypes.c_uint32, vp, vp, vp]
+    L.oc_query_sdf.restype = None
+    L.oc_query_sdf.argtypes = [vp, vp, vp, i32, vp, vp]
+    L.oc_query_sdf_backward.restype = None
+    L.oc_hidden_at.restype = None
+    L.oc_hidden_at.argtypes = [vp, vp, vp, vp, i32, vp, vp, vp, vp, vp]
+    L.oc_query_sdf_backward.argtypes = [vp, vp, vp, i32, vp, vp, vp]
+    L.oc_eikonal.restype = i64
+    L.oc_eikonal.argtypes = [vp, vp, i32, i32, vp, vp, vp, vp, dbl, vp, vp, vp]
+    L.oc_sample_importance.restype = i32
+    L.oc_sample_importance.argtypes = [vp, vp, vp, u64, u32, i32, i32, i32, i32] + [vp] * 9
+    L.oc_extract_mesh.restype = i64
+    L.oc_extract_mesh.argtypes = [vp, vp, vp, ctypes.c_float, i32, i32, i32, dbl, vp, i64, vp]
+    L.oc_step_dz.restype = i32
+    L.oc_step_dz.argtypes = [vp, vp, i32, i32] + [vp] * 6 + [i32] + [vp] * 7
+    L.oc_pose_apply.restype = None
+    L.oc_pose_apply.argtypes = [vp, vp, i32, vp]
+    L.oc_rays_of_pixels.restype = None
+    L.oc_rays_of_pixels.argtypes = [vp, vp, i32, vp, vp]
+    L.oc_pose_grad.restype = None
+    L.oc_pose_grad.argtypes = [vp, vp, vp, vp, vp, i32, i32] + [vp] * 6
+    L.oc_voxel_index.restype = None
+    L.oc_voxel_index.argtypes = [vp, vp, i32, vp]
+    L.oc_trilinear_coeffs.restype = None
+    L.oc_trilinear_coeffs.argtypes = [vp, vp, vp]
+    L.oc_trilinear_hessian.restype = None
+    L.oc_trilinear_hessian.argtypes = [vp, vp, vp]
+    L.oc_adam.restype = None
+    L.oc_adam.argtypes = [vp, vp, vp, vp, i64, i64, i32, dbl, dbl, dbl, dbl, dbl]
+    L.oc_num_threads.restype = i32
+    L.oc_paper_param_count.restype = i64
+    L.oc_paper_param_count.argtypes = [vp, vp]
+    L.oc_step_paper.restype = i32
+    L.oc_step_paper.argtypes = [vp, vp, i32, i32] + [vp] * 6 + [i32] + [vp] * 12
+    L.oc_step_paper_dz.restype = i32
+    L.oc_step_paper_dz.argtypes = [vp, vp, i32, i32] + [vp] * 6 + [i32] + [vp] * 7
+    L.oc_pose_grad_paper.restype = None
+    L.oc_pose_grad_paper.argtypes = [vp, vp, vp, vp, vp, i32, i32] + [vp] * 6
+    return L
+
+
+def build_variant(replacements, tag: str) -> str:
+    """Compile a copy of the oracle with textual replacements [(old, new), ...] applied, for
+    tests that plant a mistake in the oracle and check that a pin catches it.  Each `old`
+    must occur exactly once in the source.  Returns the library's path."""
+    import hashlib
+    src = open(os.path.join(_HERE, "gosurf_oracle.c")).read()
+    for old, new in replacements:
+        assert src.count(old) == 1, old
+        src = src.replace(old, new)
+    key = hashlib.sha256(src.encode()).hexdigest()[:16]
+    d = os.path.join(_BUILD, "variants")
+    os.makedirs(d, exist_ok=True)
+    so = os.path.join(d, f"liboracle_{tag}_{key}.so")
+    if not os.path.exists(so):
+        c = os.path.join(d, f"oracle_{tag}_{key}.c")
+        with open(c, "w") as f:
+            f.write(src)
+        tmp = so + f".{os.getpid()}.tmp"
+        subprocess.check_call(["gcc", "-O2", "-std=c11", "-fPIC", "-shared", "-fopenmp", "-ffp-contract=off",
+                               "-fno-fast-math", c, "-o", tmp, "-lm"])
+        os.replace(tmp, so)
+    return so
+
+
+class using_variant:
+    """Context manager: every oracle call inside uses the library at `path`."""
+
+    def __init__(self, path: str):
+        self.path = path
+
+    def __enter__(self):
+        global _LIB
+        lib()
+        with _LOCK:
+            self.saved = _LIB
+            _LIB = _load(self.path)
+        return self
+
+    def __exit__(self, *exc):
+        global _LIB
+        with _LOCK:
+            _LIB = self.saved
+        return False
 
 
 def make_config(w) -> OcConfig:
@@ -342,6 +394,28 @@ def query_sdf(cfg: OcConfig, theta, x, want_grad=True):
     grad = np.empty((len(x), 3)) if want_grad else None
     lib().oc_query_sdf(ctypes.byref(cfg), _p(th), _p(x), len(x), _p(sdf), _p(grad))
     return sdf, grad
+
+
+def hidden_at(cfg: OcConfig, theta, x, d=None):
+    """Hidden pre-activations at points (diagnostic): (kink [P], [h1, h2, ...] each [P][32]).
+    kink is the smallest distance of any evaluated hidden unit from its ReLU kink relative to
+    the magnitude of its terms.  Workload decoders: the geometry and the colour decoder's
+    hidden layer.  Paper architecture: the geometry decoder's two layers, and with unit
+    viewing directions d [P][3] also the colour decoder's two."""
+    th = np.ascontiguousarray(theta, dtype=np.float64)
+    x = np.ascontiguousarray(x, dtype=np.float32).reshape(-1, 3)
+    P = len(x)
+    dd = None if d is None else np.ascontiguousarray(d, dtype=np.float64).reshape(P, 3)
+    kink = np.empty(P)
+    hs = [np.empty((P, 32)) for _ in range(4)]
+    lib().oc_hidden_at(ctypes.byref(cfg), _p(th), _p(x), _p(dd), P, _p(kink), *[_p(h) for h in hs])
+    n = 4 if (cfg.arch == 1 and dd is not None) else 2
+    return kink, hs[:n]
+
+
+# relative distance below which the oracle flags a hidden unit as possibly decided
+# differently by binary32 arithmetic (amb bit 3; OC_KINK_REL in the C source)
+KINK_REL = 1e-5
 
 
 def query_sdf_backward(cfg: OcConfig, theta, x, dsdf=None, dgrad=None) -> np.ndarray:

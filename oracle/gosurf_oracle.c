@@ -358,6 +358,7 @@ static mlp_t mlp_view(const double* base) {
 
 typedef struct {
   double z[OC_Z];
+  double zmag[OC_Z]; /* sum_c w_c |theta_c| per feature (feature_mag; diagnostics only) */
   double y1[OC_H1], a1[OC_H1];
   double out[OC_OUT]; /* out[0] = phi, out[1..15] = h */
   double y2[OC_H2], a2[OC_H2];
@@ -392,10 +393,78 @@ static void decode(const mlp_t* m, act_t* A) {
   }
 }
 
+/* Distance of a hidden unit from its ReLU kink relative to the scale of the rounding error of
+ * a binary32 evaluation of it: |y| / mag(y), with mag propagated layer by layer as a
+ * root-sum-square of independent rounding errors, mag(y_j) = sqrt(b_j^2 + sum_i (W_ji
+ * mag(x_i))^2), starting from the features' corner magnitudes zmag_k = sum_c w_c |theta_c,k|
+ * (where corner values of opposite sign cancel, |z_k| is much smaller than the scale of its
+ * binary32 rounding).  An inactive unit's output is exactly 0 and carries no rounding.  A unit
+ * closer to its kink than OC_KINK_REL (about 170 units in the last place of mag) may take the
+ * other branch in binary32 (reading R9 puts the sub-gradient at the kink itself; this only
+ * flags the neighbourhood where binary32 cannot tell the sides apart).  Diagnostic only: no
+ * result depends on it. */
+#define OC_KINK_REL 1e-5
+/* a flip that moves a sample's gradient contribution by less than this is below every
+ * gradient tolerance of the parity tests, so only larger ones are flagged (as for alpha) */
+#define OC_KINK_IMPACT 1e-9
+static double kink_rel(double y, double mag) { return mag > 0 ? fabs(y) / mag : INFINITY; }
+
+/* mag(y) of one dense layer: out[j] = sqrt(b_j^2 + sum_i (W_ji xmag_i)^2) for W [n][k] */
+static void layer_mag(const double* W, const double* b, const double* xmag, int n, int k, double* out) {
+  for (int j = 0; j < n; ++j) {
+    double s = b[j] * b[j];
+    for (int i = 0; i < k; ++i) s += (W[j * k + i] * xmag[i]) * (W[j * k + i] * xmag[i]);
+    out[j] = sqrt(s);
+  }
+}
+
+/* corner magnitudes of the features at a sample: zmag_k = sum_c w_c |theta_c,k| */
+static void feature_mag(const double* theta, const cell_t cells[OC_LEVELS], double zmag[OC_Z]) {
+  for (int l = 0; l < OC_LEVELS; ++l)
+    for (int k = 0; k < OC_FEAT; ++k) {
+      double s = 0;
+      for (int cc = 0; cc < 8; ++cc) s += cells[l].w[cc] * fabs(theta[cells[l].corner[cc] + k]);
+      zmag[OC_FEAT * l + k] = s;
+    }
+}
+
+/* mag of the hidden units of both decoders (geometry layer 1, colour layer 1 fed by
+ * h = out[1..15]) from A->zmag */
+static void decode_mags(const mlp_t* m, const act_t* A, double mag1[OC_H1], double mag2[OC_H2]) {
+  double am[OC_H1], om[OC_OUT];
+  layer_mag(m->W1, m->b1, A->zmag, OC_H1, OC_Z, mag1);
+  for (int j = 0; j < OC_H1; ++j) am[j] = A->y1[j] > 0 ? mag1[j] : 0.0;
+  layer_mag(m->W2, m->b2, am, OC_OUT, OC_H1, om);
+  layer_mag(m->W3, m->b3, om + 1, OC_H2, OC_HF, mag2);
+}
+
+/* smallest relative kink distance over the hidden units of both decoders */
+static double decode_kink(const mlp_t* m, const act_t* A) {
+  double mag1[OC_H1], mag2[OC_H2], r = INFINITY, v;
+  decode_mags(m, A, mag1, mag2);
+  for (int j = 0; j < OC_H1; ++j)
+    if ((v = kink_rel(A->y1[j], mag1[j])) < r) r = v;
+  for (int j = 0; j < OC_H2; ++j)
+    if ((v = kink_rel(A->y2[j], mag2[j])) < r) r = v;
+  return r;
+}
+
+/* max(1, max_i |W_i|, max_i |x_i|): the scale of what a unit's mask multiplies */
+static double unit_scale(const double* W, const double* x, int k) {
+  double s = 1.0;
+  for (int i = 0; i < k; ++i) {
+    if (fabs(W[i]) > s) s = fabs(W[i]);
+    if (fabs(x[i]) > s) s = fabs(x[i]);
+  }
+  return s;
+}
+
 /* reverse mode of decode(): given dphi and dc, accumulate parameter grads into gm (MLP
- * block) and return dz */
+ * block) and return dz.  flip (may be NULL; diagnostic): over the hidden units within
+ * OC_KINK_REL of their kink, the largest |dL/d(unit output)| times unit_scale, i.e. how much
+ * this sample's gradient would move if binary32 arithmetic took the unit's other branch. */
 static void decode_backward(const mlp_t* m, const act_t* A, double dphi, const double dc[OC_RGB], double* gm,
-                            double dz[OC_Z]) {
+                            double dz[OC_Z], double* flip) {
   double* gW1 = gm;
   double* gb1 = gW1 + OC_H1 * OC_Z;
   double* gW2 = gb1 + OC_H1;
@@ -445,8 +514,21 @@ static void decode_backward(const mlp_t* m, const act_t* A, double dphi, const d
     for (int j = 0; j < OC_H1; ++j) s += m->W1[j * OC_Z + k] * dy1[j];
     dz[k] = s;
   }
-  (void)da2;
-  (void)da1;
+  if (flip) {
+    double f = 0, mag1[OC_H1], mag2[OC_H2];
+    decode_mags(m, A, mag1, mag2);
+    for (int j = 0; j < OC_H2; ++j)
+      if (kink_rel(A->y2[j], mag2[j]) < OC_KINK_REL) {
+        double v = fabs(da2[j]) * unit_scale(m->W3 + j * OC_HF, A->out + 1, OC_HF);
+        if (v > f) f = v;
+      }
+    for (int j = 0; j < OC_H1; ++j)
+      if (kink_rel(A->y1[j], mag1[j]) < OC_KINK_REL) {
+        double v = fabs(da1[j]) * unit_scale(m->W1 + j * OC_Z, A->z, OC_Z);
+        if (v > f) f = v;
+      }
+    *flip = f;
+  }
 }
 
 /* p = d phi / d z = W1^T (m (.) W2[0,:]^T), m = 1[y1 > 0] (ReLU => piecewise linear) */
@@ -515,7 +597,7 @@ void oc_query_sdf_backward(const oc_config* c, const double* theta, const float*
     if (dsdf && dsdf[i] != 0.0) {
       const double dc[OC_RGB] = {0, 0, 0};
       double dz[OC_Z];
-      decode_backward(&m, &A, dsdf[i], dc, gm, dz);
+      decode_backward(&m, &A, dsdf[i], dc, gm, dz, NULL);
       for (int l = 0; l < OC_LEVELS; ++l)
         for (int cc = 0; cc < 8; ++cc)
           for (int f = 0; f < OC_FEAT; ++f) grad[cells[l].corner[cc] + f] += cells[l].w[cc] * dz[OC_FEAT * l + f];
@@ -842,7 +924,10 @@ static void mmin(double* a, double v) {
  * NULL.  grad: same layout as theta, overwritten.  margins[10] may be NULL.
  * amb [R,N] (may be NULL) flags the samples whose branch decisions lie within binary32
  * rounding of a tie: bit 0 the alpha_k > 0 decision (|q_k| < 1e-5, unsaturated, untied),
- * bit 1 the sign of phi - b on S_tr (|phi - b| < 2e-5), bit 2 the free-space max (gap < 2e-5).
+ * bit 1 the sign of phi - b on S_tr (|phi - b| < 2e-5), bit 2 the free-space max (gap < 2e-5),
+ * bit 3 a hidden unit of either decoder within OC_KINK_REL (relative) of its ReLU kink whose
+ * flip would move the sample's gradient by more than OC_KINK_IMPACT (gradients requested),
+ * bit 4 (on the ray's first sample) the sign of d_hat - D (|d_hat - D| < 1e-5 max(D, 1)).
  * Bit 0 is set only when gradients are requested and a flip would change dL/dphi by more
  * than 1e-7.  w_out [R,N] (may be NULL) receives the rendering weights w_i = T_i alpha_i.
  * Returns 0, or -1 on a bad argument.
@@ -916,6 +1001,7 @@ static int step_impl(const oc_config* c, const double* theta, int R, int N, cons
           x[a] = o[3 * i + a] + step_;
         }
         features(c, theta, x, cells + (size_t)k * OC_LEVELS, A[k].z, NULL);
+        feature_mag(theta, cells + (size_t)k * OC_LEVELS, A[k].zmag);
         decode(&m, &A[k]);
         phi[k] = A[k].out[0];
         for (int j = 0; j < OC_H1; ++j) mmin(&mg->m[0], A[k].y1[j]);
@@ -957,6 +1043,9 @@ static int step_impl(const oc_config* c, const double* theta, int R, int N, cons
       if (D[i] > 0.0f) {
         lsum[1] += fabs(Di - dh);
         mmin(&mg->m[5], dh - Di);
+        /* the sign of d_hat - D decides the sign of every sample's depth gradient; a binary32
+         * d_hat (a sum of N products w_k t_k) errs by up to about N ulps of D */
+        if (amb && fabs(dh - Di) < 1e-5 * (Di > 1.0 ? Di : 1.0)) amb[(size_t)i * N] |= 16;
         sigmix(&mg->sig, ((uint64_t)i * (uint64_t)N) * 8 + 7, (uint64_t)(dh > Di));
       }
       /* approximate SDF supervision (Sec. 3.3) */
@@ -1037,7 +1126,9 @@ static int step_impl(const oc_config* c, const double* theta, int R, int N, cons
         double dc[3];
         for (int j = 0; j < 3; ++j) dc[j] = w[k] * gc[j];
         double* dz = dz_all + ((size_t)i * N + k) * OC_Z;
-        decode_backward(&m, &A[k], dphi, dc, gm, dz);
+        double flip = 0;
+        decode_backward(&m, &A[k], dphi, dc, gm, dz, amb ? &flip : NULL);
+        if (amb && flip > OC_KINK_IMPACT) amb[(size_t)i * N + k] |= 8;
       }
     }
 
@@ -1745,6 +1836,7 @@ static pa_mlp_t pa_view(const double* b) {
 
 typedef struct {
   double z[OC_Z], y1[PA_H], a1[PA_H], y2[PA_H], a2[PA_H], phi;  /* geometry decoder */
+  double zmag[OC_Z], umag[PA_U]; /* input magnitudes for the kink diagnostics (see kink_rel) */
   double u[PA_U], q1[PA_H], r1[PA_H], q2[PA_H], r2[PA_H], pre[3], c[3]; /* colour decoder */
   int64_t cvtx[8];  /* flat colour-grid float index of feature 0 of each level-3 corner */
   double cw[8];     /* their trilinear weights */
@@ -1765,14 +1857,18 @@ static void pa_eval(const oc_config* c, const double* theta, const pa_mlp_t* m, 
   features(c, theta, x, cells, A->z, dzdx);
   /* W_beta(x): the colour grid shares level 3's vertices, so it uses level 3's cell */
   const int64_t cbase = grid_size(c), off3 = level_offset(c, 3);
-  for (int k = 0; k < PA_C; ++k) A->u[k] = 0.0;
+  for (int k = 0; k < PA_C; ++k) A->u[k] = A->umag[k] = 0.0;
   for (int cc = 0; cc < 8; ++cc) {
     const int64_t vtx = (cells[3].corner[cc] - off3) / OC_FEAT;
     A->cvtx[cc] = cbase + vtx * PA_C;
     A->cw[cc] = cells[3].w[cc];
-    for (int k = 0; k < PA_C; ++k) A->u[k] += cells[3].w[cc] * theta[A->cvtx[cc] + k];
+    for (int k = 0; k < PA_C; ++k) {
+      A->u[k] += cells[3].w[cc] * theta[A->cvtx[cc] + k];
+      A->umag[k] += cells[3].w[cc] * fabs(theta[A->cvtx[cc] + k]);
+    }
   }
-  for (int a = 0; a < 3; ++a) A->u[PA_C + a] = d[a];
+  for (int a = 0; a < 3; ++a) A->u[PA_C + a] = d[a], A->umag[PA_C + a] = fabs(d[a]);
+  feature_mag(theta, cells, A->zmag);
   pa_affine(m->gW1, m->gb1, A->z, PA_H, OC_Z, A->y1);
   for (int j = 0; j < PA_H; ++j) A->a1[j] = A->y1[j] > 0 ? A->y1[j] : 0;
   pa_affine(m->gW2, m->gb2, A->a1, PA_H, PA_H, A->y2);
@@ -1784,6 +1880,33 @@ static void pa_eval(const oc_config* c, const double* theta, const pa_mlp_t* m, 
   for (int j = 0; j < PA_H; ++j) A->r2[j] = A->q2[j] > 0 ? A->q2[j] : 0;
   pa_affine(m->cW3, m->cb3, A->r2, 3, PA_H, A->pre);
   for (int j = 0; j < 3; ++j) A->c[j] = sigm(A->pre[j]);
+}
+
+/* mag (see kink_rel) of the four hidden layers of the paper's decoders */
+static void pa_mags(const pa_mlp_t* m, const pa_act_t* A, double g1[PA_H], double g2[PA_H], double c1[PA_H],
+                    double c2[PA_H]) {
+  double on[PA_H];
+  layer_mag(m->gW1, m->gb1, A->zmag, PA_H, OC_Z, g1);
+  for (int j = 0; j < PA_H; ++j) on[j] = A->y1[j] > 0 ? g1[j] : 0.0;
+  layer_mag(m->gW2, m->gb2, on, PA_H, PA_H, g2);
+  layer_mag(m->cW1, m->cb1, A->umag, PA_H, PA_U, c1);
+  for (int j = 0; j < PA_H; ++j) on[j] = A->q1[j] > 0 ? c1[j] : 0.0;
+  layer_mag(m->cW2, m->cb2, on, PA_H, PA_H, c2);
+}
+
+/* smallest relative kink distance (kink_rel) over the hidden units of the geometry decoder
+ * and, when colour != 0, of the colour decoder */
+static double pa_kink(const pa_mlp_t* m, const pa_act_t* A, int colour) {
+  double g1[PA_H], g2[PA_H], c1[PA_H], c2[PA_H], r = INFINITY, v;
+  pa_mags(m, A, g1, g2, c1, c2);
+  for (int j = 0; j < PA_H; ++j) {
+    if ((v = kink_rel(A->y1[j], g1[j])) < r) r = v;
+    if ((v = kink_rel(A->y2[j], g2[j])) < r) r = v;
+    if (!colour) continue;
+    if ((v = kink_rel(A->q1[j], c1[j])) < r) r = v;
+    if ((v = kink_rel(A->q2[j], c2[j])) < r) r = v;
+  }
+  return r;
 }
 
 /* one dense layer backwards: gW += dy x^T, gb += dy, and (dx != NULL) dx = W^T dy */
@@ -1803,22 +1926,40 @@ static void pa_affine_back(const double* W, const double* x, const double* dy, i
 
 /* reverse mode of pa_eval's decoders for upstream dphi, dc: decoder gradients into gm (the
  * PA_MLP block), dL/dz [16] and dL/dW_beta(x) [6] returned */
+/* flip diagnostic of one hidden layer (as decode_backward's): over its units within
+ * OC_KINK_REL of their kink (mag: the layer's pa_mags), the largest |dL/d(unit output)| times
+ * unit_scale */
+static void pa_flip(const double* W, const double* x, int k, const double* y, const double* mag, const double* dy,
+                    double* f) {
+  for (int j = 0; j < PA_H; ++j)
+    if (kink_rel(y[j], mag[j]) < OC_KINK_REL) {
+      double v = fabs(dy[j]) * unit_scale(W + j * k, x, k);
+      if (v > *f) *f = v;
+    }
+}
+
 static void pa_backward(const pa_mlp_t* m, const pa_act_t* A, double dphi, const double dc[3], double* gm,
-                        double dz[OC_Z], double dcf[PA_C], double ddir[3]) {
+                        double dz[OC_Z], double dcf[PA_C], double ddir[3], double* flip) {
   pa_mlp_t g = pa_view(gm); /* same offsets in the gradient block */
-  double d2[PA_H], d1[PA_H], du[PA_U];
+  double d2[PA_H], d1[PA_H], du[PA_U], f = 0, g1m[PA_H], g2m[PA_H], c1m[PA_H], c2m[PA_H];
+  if (flip) pa_mags(m, A, g1m, g2m, c1m, c2m);
   /* geometry: phi = gw3 . a2 + gb3 */
   pa_affine_back(m->gw3, A->a2, &dphi, 1, PA_H, (double*)g.gw3, (double*)g.gb3, d2);
+  if (flip) pa_flip(m->gW2, A->a1, PA_H, A->y2, g2m, d2, &f);
   for (int j = 0; j < PA_H; ++j) d2[j] = A->y2[j] > 0 ? d2[j] : 0.0;
   pa_affine_back(m->gW2, A->a1, d2, PA_H, PA_H, (double*)g.gW2, (double*)g.gb2, d1);
+  if (flip) pa_flip(m->gW1, A->z, OC_Z, A->y1, g1m, d1, &f);
   for (int j = 0; j < PA_H; ++j) d1[j] = A->y1[j] > 0 ? d1[j] : 0.0;
   pa_affine_back(m->gW1, A->z, d1, PA_H, OC_Z, (double*)g.gW1, (double*)g.gb1, dz);
   /* colour: c = sigmoid(cW3 r2 + cb3) */
   double dpre[3];
   for (int j = 0; j < 3; ++j) dpre[j] = dc[j] * A->c[j] * (1.0 - A->c[j]);
   pa_affine_back(m->cW3, A->r2, dpre, 3, PA_H, (double*)g.cW3, (double*)g.cb3, d2);
+  if (flip) pa_flip(m->cW2, A->r1, PA_H, A->q2, c2m, d2, &f);
   for (int j = 0; j < PA_H; ++j) d2[j] = A->q2[j] > 0 ? d2[j] : 0.0;
   pa_affine_back(m->cW2, A->r1, d2, PA_H, PA_H, (double*)g.cW2, (double*)g.cb2, d1);
+  if (flip) pa_flip(m->cW1, A->u, PA_U, A->q1, c1m, d1, &f);
+  if (flip) *flip = f;
   for (int j = 0; j < PA_H; ++j) d1[j] = A->q1[j] > 0 ? d1[j] : 0.0;
   pa_affine_back(m->cW1, A->u, d1, PA_H, PA_U, (double*)g.cW1, (double*)g.cb1, du);
   for (int k = 0; k < PA_C; ++k) dcf[k] = du[k];
@@ -1929,6 +2070,7 @@ static int step_paper_impl(const oc_config* c, const double* theta, int R, int N
     if (D[i] > 0.0f) {
       lsum[1] += fabs(Di - dh);
       mmin(&d_margin, dh - Di);
+      if (amb && fabs(dh - Di) < 1e-5 * (Di > 1.0 ? Di : 1.0)) amb[(size_t)i * N] |= 16;
       sigmix(&sig, ((uint64_t)i * (uint64_t)N) * 8 + 7, (uint64_t)(dh > Di));
     }
     for (int k = 0; k < N; ++k) {
@@ -1998,7 +2140,9 @@ static int step_paper_impl(const oc_config* c, const double* theta, int R, int N
       double dc[3], dz[OC_Z], dcf[PA_C];
       for (int j = 0; j < 3; ++j) dc[j] = w[k] * gc[j];
       double ddir[3];
-      pa_backward(&m, &A[k], dphi, dc, gm, dz, dcf, ddir);
+      double flip = 0;
+      pa_backward(&m, &A[k], dphi, dc, gm, dz, dcf, ddir, amb ? &flip : NULL);
+      if (amb && flip > OC_KINK_IMPACT) amb[(size_t)i * N + k] |= 8;
       if (dzc_out) { /* per sample: dL/dz, dL/dW_beta(x), dL/d(direction) */
         double* q = dzc_out + ((size_t)i * N + k) * 32;
         for (int f = 0; f < 32; ++f) q[f] = 0.0;
@@ -2177,7 +2321,7 @@ static void pa_query_sdf_backward(const oc_config* c, const double* theta, const
     if (dsdf && dsdf[i] != 0.0) {
       const double dc[3] = {0, 0, 0};
       double dz[OC_Z], dcf[PA_C];
-      pa_backward(&m, &A, dsdf[i], dc, gm, dz, dcf, NULL);
+      pa_backward(&m, &A, dsdf[i], dc, gm, dz, dcf, NULL, NULL);
       for (int l = 0; l < OC_LEVELS; ++l)
         for (int cc = 0; cc < 8; ++cc)
           for (int f = 0; f < OC_FEAT; ++f) grad[cells[l].corner[cc] + f] += cells[l].w[cc] * dz[OC_FEAT * l + f];
@@ -2210,6 +2354,51 @@ static void pa_query_sdf_backward(const oc_config* c, const double* theta, const
         if (A.y2[i2] > 0) ((double*)gg.gw3)[i2] += acc;
       }
     }
+  }
+}
+
+/* Hidden pre-activations at points, for tests that must know which ReLU branches the points
+ * take (diagnostic; no step result depends on it).  kink[P]: smallest relative distance of
+ * any evaluated hidden unit from its kink (kink_rel).  Workload decoders: h1 [P][32] the
+ * geometry decoder's layer 1, h2 [P][32] the colour decoder's layer 1 (h3, h4, d unused).
+ * Paper architecture (c->arch == 1): h1, h2 the geometry decoder's two hidden layers; with
+ * unit viewing directions d [P][3] also the colour decoder's, h3 and h4 (d NULL: the colour
+ * decoder is not evaluated).  h1..h4 may be NULL. */
+void oc_hidden_at(const oc_config* c, const double* theta, const float* x, const double* d, int P, double* kink,
+                  double* h1, double* h2, double* h3, double* h4) {
+  if (c->arch == 1) {
+    int64_t ng = 0;
+    oc_paper_param_count(c, &ng);
+    pa_mlp_t m = pa_view(theta + ng);
+    const double dnone[3] = {0, 0, 1};
+#pragma omp parallel for schedule(static)
+    for (int i = 0; i < P; ++i) {
+      cell_t cells[OC_LEVELS];
+      pa_act_t A;
+      pa_eval(c, theta, &m, x + 3 * i, d ? d + 3 * i : dnone, cells, NULL, &A);
+      kink[i] = pa_kink(&m, &A, d != NULL);
+      for (int j = 0; j < PA_H; ++j) {
+        if (h1) h1[(size_t)i * PA_H + j] = A.y1[j];
+        if (h2) h2[(size_t)i * PA_H + j] = A.y2[j];
+        if (h3 && d) h3[(size_t)i * PA_H + j] = A.q1[j];
+        if (h4 && d) h4[(size_t)i * PA_H + j] = A.q2[j];
+      }
+    }
+    return;
+  }
+  mlp_t m = mlp_view(theta + grid_size(c));
+#pragma omp parallel for schedule(static)
+  for (int i = 0; i < P; ++i) {
+    cell_t cells[OC_LEVELS];
+    act_t A;
+    features(c, theta, x + 3 * i, cells, A.z, NULL);
+    feature_mag(theta, cells, A.zmag);
+    decode(&m, &A);
+    kink[i] = decode_kink(&m, &A);
+    for (int j = 0; j < OC_H1; ++j)
+      if (h1) h1[(size_t)i * OC_H1 + j] = A.y1[j];
+    for (int j = 0; j < OC_H2; ++j)
+      if (h2) h2[(size_t)i * OC_H2 + j] = A.y2[j];
   }
 }
 
