@@ -445,6 +445,51 @@ def sdf_params(w, scene, seed=21, grid_std=0.05, bias=0.25, pass_offset=3.0, mix
     return theta
 
 
+def sdf_switching_params(w, scene, seed=21, grid_std=0.1, bias=0.02, mix=0.1, phi_shift=0.03):
+    """Parameters for element-wise GPU-vs-oracle parity whose hidden ReLU units switch from
+    sample to sample: the scene's exact SDF baked into feature 0 of the finest level (so the
+    rendering is that of a real surface), random features of O(0.1) elsewhere, and both
+    decoders with weights U(+-0.25) / U(+-0.2) and biases U(+-bias) near zero, so that every
+    unit other than the two pass-through units is on for some samples and off for others.
+
+    Hidden units 0 and 1 of the geometry decoder carry phi = z[12] + phi_shift exactly as
+    relu(v) - relu(-v) = v (no offset: near the surface, where phi is small, its binary32 and
+    bfloat16 roundings stay small too); the shift keeps the truncated-SDF loss well above
+    them.  The switching units add a nonlinear term to phi (weights `mix`) and form the colour
+    features.  Samples whose units lie within binary32 rounding of a kink are flagged by the
+    oracle and left out by the parity tests."""
+    import math
+    rng = np.random.default_rng(seed)
+    offs, n_grid, n_tot = w.layout()
+    theta = np.zeros(n_tot, np.float32)
+    theta[:n_grid] = rng.normal(0.0, grid_std, n_grid).astype(np.float32)
+    nx, ny, nz = w.dims[3]
+    X = vertex_positions(w, 3)
+    sdf = scene.sdf(X.reshape(-1, 3)).reshape(nz, ny, nx)
+    set_level_field(w, theta, 3, 0, lambda _: sdf)
+    m = mlp_views(theta, n_grid)
+    m["W1"][:] = rng.uniform(-0.25, 0.25, m["W1"].shape)
+    m["W1"][:, 12] = 0.0  # the SDF feature reaches phi only through the pass-through units
+    m["b1"][:] = rng.uniform(-bias, bias, 32)
+    m["W1"][0, :] = 0.0
+    m["W1"][1, :] = 0.0
+    m["W1"][0, 12] = 1.0
+    m["W1"][1, 12] = -1.0
+    m["b1"][0] = m["b1"][1] = 0.0
+    m["W2"][:] = rng.uniform(-0.25, 0.25, m["W2"].shape)
+    m["W2"][0, :] = rng.uniform(-mix, mix, 32)
+    m["W2"][1:, :2] = 0.0  # the colour features do not see the pass-through units
+    m["W2"][0, 0], m["W2"][0, 1] = 1.0, -1.0
+    m["b2"][:] = rng.uniform(-bias, bias, 16)
+    m["b2"][0] = phi_shift
+    m["W3"][:] = rng.uniform(-0.25, 0.25, m["W3"].shape)
+    m["b3"][:] = rng.uniform(-bias, bias, 32) * 0.2
+    m["W4"][:] = rng.uniform(-1.0, 1.0, m["W4"].shape)
+    m["b4"][:] = rng.uniform(-0.2, 0.2, 3)
+    m["kappa"][0] = math.log(20.0)
+    return theta
+
+
 def init_params(w: Workload, seed: int = SEED_INIT) -> np.ndarray:
     """Default initialisation: grid features N(0, 1e-4^2); MLP weights U(+-1/sqrt(fan_in)),
     biases 0; kappa = ln 20 (s = 20 1/m)."""
@@ -551,6 +596,54 @@ def paper_sdf_params(w, scene, seed=23, grid_std=0.05, mix=0.1):
     m["cW2"][:] = rng.uniform(-0.03, 0.03, (32, 32))
     m["cb2"][:] = 0.5 * alt
     m["cW3"][:] = rng.uniform(-0.5, 0.5, (3, 32))
+    m["cb3"][:] = rng.uniform(-0.2, 0.2, 3)
+    m["kappa"][0] = math.log(20.0)
+    return theta
+
+
+def paper_switching_params(w, scene, seed=23, grid_std=0.1, bias=0.02, mix=0.1, phi_shift=0.03):
+    """Paper-architecture parameters whose hidden ReLU units switch from sample to sample
+    (the analogue of sdf_switching_params): the scene's exact SDF in feature 0 of the finest
+    geometry level, random features of O(0.1) elsewhere (colour grid included), and all four
+    hidden layers with biases U(+-bias) near zero, so every unit but the pass-through ones is
+    on for some samples and off for others.
+
+    Geometry: hidden-1 units 0, 1 carry relu(z[12]), relu(-z[12]); hidden-2 units 0, 1 take
+    their differences z and -z, and gw3 = (1, -1, ...), gb3 = phi_shift, so phi = z[12] +
+    phi_shift (relu(v) - relu(-v) = v, no offset) plus a term (weights `mix`) from the
+    switching units."""
+    assert w.arch == "paper"
+    rng = np.random.default_rng(seed)
+    offs, n_grid, n_tot = w.layout()
+    theta = np.zeros(n_tot, np.float32)
+    theta[:n_grid] = rng.normal(0.0, grid_std, n_grid).astype(np.float32)
+    _zero_colour_padding(w, theta)
+    nx, ny, nz = w.dims[3]
+    X = vertex_positions(w, 3)
+    sdf = scene.sdf(X.reshape(-1, 3)).reshape(nz, ny, nx)
+    set_level_field(w, theta, 3, 0, lambda _: sdf)
+    m = mlp_views(theta, n_grid, PAPER_MLP_SHAPES)
+    m["gW1"][:] = rng.uniform(-0.25, 0.25, (32, 16))
+    m["gW1"][:, 12] = 0.0
+    m["gW1"][:2, :] = 0.0
+    m["gW1"][0, 12], m["gW1"][1, 12] = 1.0, -1.0
+    m["gb1"][:] = rng.uniform(-bias, bias, 32)
+    m["gb1"][0] = m["gb1"][1] = 0.0
+    m["gW2"][:] = rng.uniform(-0.3, 0.3, (32, 32))
+    m["gW2"][:, :2] = 0.0
+    m["gW2"][:2, :] = 0.0
+    m["gW2"][0, 0], m["gW2"][0, 1] = 1.0, -1.0
+    m["gW2"][1, 0], m["gW2"][1, 1] = -1.0, 1.0
+    m["gb2"][:] = rng.uniform(-bias, bias, 32) * 0.2
+    m["gb2"][0] = m["gb2"][1] = 0.0
+    m["gw3"][0, :] = rng.uniform(-mix, mix, 32)
+    m["gw3"][0, 0], m["gw3"][0, 1] = 1.0, -1.0
+    m["gb3"][0] = phi_shift
+    m["cW1"][:] = rng.uniform(-0.5, 0.5, (32, 9))
+    m["cb1"][:] = rng.uniform(-bias, bias, 32)
+    m["cW2"][:] = rng.uniform(-0.3, 0.3, (32, 32))
+    m["cb2"][:] = rng.uniform(-bias, bias, 32) * 0.2
+    m["cW3"][:] = rng.uniform(-1.0, 1.0, (3, 32))
     m["cb3"][:] = rng.uniform(-0.2, 0.2, 3)
     m["kappa"][0] = math.log(20.0)
     return theta

@@ -77,14 +77,54 @@ def _classes(D, t, trunc):
     return np.where(D[:, None] > 0, np.where(np.abs(b) <= tr, 1, np.where(b > tr, 2, 0)), 0).astype(np.uint8)
 
 
-def prepare_parity_batch(p: Problem, theta, bt, sm, max_iter=6, max_drop=0.1):
+def unit_directions(bt):
+    """Unit viewing direction of every sample [R*N][3] (the paper architecture's colour input)."""
+    r = bt["r"].astype(np.float64)
+    d = r / np.linalg.norm(r, axis=1, keepdims=True)
+    return np.repeat(d, bt["t"].shape[1], axis=0)
+
+
+def switching_fraction(p: Problem, theta, bt):
+    """Fraction of the hidden ReLU units (every hidden layer of both decoders) that are on at
+    some samples of the batch and off at others."""
+    x = sample_positions(bt).reshape(-1, 3)
+    d = unit_directions(bt) if p.w.arch == "paper" else None
+    _, hs = oc.hidden_at(p.cfg, theta, x, d)
+    on = np.concatenate([h > 0 for h in hs], axis=1)
+    return float((on.any(axis=0) & (~on).any(axis=0)).mean())
+
+
+def drop_kink_points(p: Problem, theta, sm):
+    """Smoothness points whose gradient grad_x phi at x or x + eps has a hidden unit within
+    binary32 rounding of its kink (the loss itself jumps there) are made inactive, in place:
+    sm["valid"] and sm["n_valid"] are rewritten.  Returns how many were dropped."""
+    if sm is None or len(sm["valid"]) == 0:
+        return 0
+    xe = (sm["xs"] + sm["eps"]).astype(np.float32)
+    k0, _ = oc.hidden_at(p.cfg, theta, sm["xs"])
+    k1, _ = oc.hidden_at(p.cfg, theta, xe)
+    bad = (sm["valid"] > 0) & ((k0 < oc.KINK_REL) | (k1 < oc.KINK_REL))
+    sm["valid"] = np.where(bad, 0, sm["valid"]).astype(np.uint8)
+    sm["n_valid"] = np.array([int((sm["valid"] > 0).sum())], dtype=sm["n_valid"].dtype)
+    return int(bad.sum())
+
+
+def prepare_parity_batch(p: Problem, theta, bt, sm, max_iter=6, max_drop=0.1, min_switch=None, label=""):
     """Subset of the oracle batch on which no branch decision lies within binary32 rounding
     of a tie, so that the FP32 kernels and the FP64 oracle take every branch the same way.
 
     The oracle flags the samples whose alpha > 0 decision (when a flip would move dL/dphi by
-    more than 1e-7), truncated-SDF sign or free-space maximum is that close to a tie; the rays
-    holding them are left out and both sides run on the remaining rays.  Returns (batch,
-    reference step, number of rays left out)."""
+    more than 1e-7), truncated-SDF sign, free-space maximum or hidden ReLU unit (when a flip
+    would move the sample's gradient by more than 1e-9), and the rays whose sign of
+    d_hat - D, is that close to a tie; the rays
+    holding them are left out and both sides run on the remaining rays.  Smoothness points
+    near a ReLU kink are made inactive in sm (in place).  With min_switch, asserts that at
+    least that fraction of the hidden units switches within the batch.  Prints and bounds
+    (max_drop) the rays left out.  Returns (batch, reference step, number of rays left out)."""
+    if min_switch is not None:
+        frac = switching_fraction(p, theta, bt)
+        assert frac >= min_switch, frac
+    n_pts = drop_kink_points(p, theta, sm)
     keep = np.ones(len(bt["D"]), bool)
     for _ in range(max_iter):
         sub = {k: (v[keep] if k != "counts" else v) for k, v in bt.items()}
@@ -94,10 +134,32 @@ def prepare_parity_batch(p: Problem, theta, bt, sm, max_iter=6, max_drop=0.1):
         bad = ref["amb"].any(axis=1)
         if not bad.any():
             dropped = int((~keep).sum())
-            assert dropped <= max_drop * len(keep), dropped
+            print(f"parity batch {label or p.w.name}: {dropped} of {len(keep)} rays "
+                  f"({100.0 * dropped / max(len(keep), 1):.2f} %) and {n_pts} smoothness points left out"
+                  + (f"; {100.0 * frac:.0f} % of hidden units switch" if min_switch is not None else ""))
+            assert dropped <= max_drop * len(keep), (dropped, len(keep))
             return sub, ref, dropped
         keep[np.nonzero(keep)[0][bad]] = False
     raise AssertionError("could not move the parity batch away from binary32 ties")
+
+
+def drop_kink_rays(p: Problem, theta, bt, classes=(oc.CLS_FS,)):
+    """Rays none of whose samples of the given classes has a hidden unit within binary32
+    rounding of its kink (for terms built on grad_x phi, which jumps there).  Returns the
+    ray subset (counts recomputed) and the number of rays left out."""
+    x = sample_positions(bt).reshape(-1, 3)
+    kink, _ = oc.hidden_at(p.cfg, theta, x)
+    near = (kink < oc.KINK_REL).reshape(bt["t"].shape) & np.isin(bt["cls"], classes)
+    keep = ~near.any(axis=1)
+    sub = {k: (v[keep] if k != "counts" else v) for k, v in bt.items()}
+    sub["counts"] = np.array([(sub["D"] > 0).sum(), (sub["cls"] == 1).sum(), (sub["cls"] == 2).sum(), 0], np.int64)
+    return sub, int((~keep).sum())
+
+
+def far_from_kinks(p: Problem, theta, x):
+    """Mask of the points x whose hidden units are all clear of their kinks in binary32."""
+    kink, _ = oc.hidden_at(p.cfg, theta, x)
+    return kink >= oc.KINK_REL
 
 
 def upload_oracle_batch(bt, sm, counts_smooth, device="cuda"):

@@ -47,5 +47,7 @@ def hand_batch(o, r, t, D, rgb=None, trunc=0.1):
     return dict(o=o, r=r, t=t, D=D, rgb=rgb, cls=cls)
 
 
-# the scene's exact SDF baked into the finest level (an input builder shared with bench.py)
-sdf_parity_params = sg.sdf_params
+# the scene's exact SDF baked into the finest level, decoders whose hidden units switch from
+# sample to sample (input builders shared with the smoke check)
+sdf_parity_params = sg.sdf_switching_params
+paper_parity_params = sg.paper_switching_params

@@ -2,13 +2,18 @@
 with FP32 accumulation, FP32 gradients and moments) against the FP64 oracle and against the
 FP32 form.
 
-Per step, its error is a property of the format: bfloat16 SDF values (about 2^-8 relative)
-move some samples across the branch points of the truncated-SDF sign and of alpha > 0, and
-each such flip changes that sample's gradient by a finite amount.  So the per-step test
-states the measured errors (pytest -s prints them) and bounds the total loss to 2 % and the
-gradients in relative L2 norm; the criterion that matters for this form is the end result:
-after the same number of optimisation steps its rendered depth must be as good as the FP32
-form's (L1 within 5 %).
+The oracle runs on the parameters the BF16 form reads in bfloat16 (the grid and the four
+decoder weight matrices) rounded to bfloat16 by the test's input builder, so the format's
+rounding of the parameters leaves the comparison; what remains is the bfloat16 rounding of
+the decoder inputs and activations (about 2^-9 relative) inside the forward and adjoint
+contractions.  That moves some samples across the branch points of the truncated-SDF sign,
+alpha > 0 and the hidden ReLU units (a window about 2^8 times wider than FP32's, so the FP32
+tie exclusion does not cover it), and each such flip changes that sample's gradient by a
+finite amount: the grid levels, whose vertices each collect few samples, show it most.  The
+bounds below are per loss term and per gradient tensor (max-norm relative to the tensor's
+largest entry, and relative L2), about twice the errors measured on GB300 (pytest -s prints
+them); the criterion that matters for this form is the end result: after the same number of
+optimisation steps its rendered depth must be as good as the FP32 form's (L1 within 5 %).
 """
 import math
 
@@ -28,43 +33,68 @@ def _bf16_copy(theta, n_grid):
     return torch.from_numpy(theta[:n_grid]).cuda().to(torch.bfloat16).view(torch.int16).contiguous()
 
 
+def bf16_inputs(w, theta):
+    """theta with the entries the BF16 form reads in bfloat16 (every grid level and the decoder
+    weight matrices W1..W4) rounded to bfloat16 (round to nearest even); biases and kappa stay
+    FP32, as the form reads them."""
+    th = theta.copy()
+    ng = w.layout()[1]
+    rnd = lambda a: torch.from_numpy(np.ascontiguousarray(a, np.float32)).to(torch.bfloat16).float().numpy()
+    th[:ng] = rnd(th[:ng])
+    m = sg.mlp_views(th, ng)
+    for k in ("W1", "W2", "W3", "W4"):
+        m[k][...] = rnd(m[k])
+    return th
+
+
+# per case: (largest relative error of any loss term, {tensor: (max-norm bound, relative L2 bound)})
+BF16_BOUNDS = {
+    "cube": (1e-3, {"grid0": (0.015, 0.015), "grid1": (0.03, 0.03), "grid2": (0.065, 0.055), "grid3": (0.2, 0.08),
+                    "W1": (0.013, 0.012), "b1": (2e-3, 2e-3), "W2": (8e-3, 8e-3), "b2": (1e-3, 1e-3),
+                    "W3": (4e-3, 3e-3), "b3": (4e-3, 3e-3), "W4": (1e-3, 1e-3), "b4": (1e-3, 1e-3),
+                    "kappa": (1e-3, 1e-3)}),
+    "room": (2e-4, {"grid0": (0.075, 0.06), "grid1": (0.19, 0.11), "grid2": (0.24, 0.19), "grid3": (0.8, 0.17),
+                    "W1": (0.015, 0.028), "b1": (0.013, 0.013), "W2": (0.011, 0.01), "b2": (1e-3, 1e-3),
+                    "W3": (0.012, 0.009), "b3": (8e-3, 7e-3), "W4": (1e-3, 1e-3), "b4": (1e-3, 1e-3),
+                    "kappa": (1e-3, 1e-3)}),
+}
+
+
 @pytest.mark.parametrize("wl", ["cube", "room"])
 def test_bf16_form_error_against_oracle(wl):
     if wl == "cube":
         w = CUBE.with_(name="cube-bf16", precision="bf16")
         p = Problem(w)
-        theta = sdf_parity_params(w, sg.cube_scene(), seed=21)
+        theta = bf16_inputs(w, sdf_parity_params(w, sg.cube_scene(), seed=21))
         bt, sm = p.oracle_sample(3, 5)
     else:  # a 1024-ray subset of the BF16 room workload
         w = sg.WORKLOADS["room-bf16-32768x96"].with_(rays=1024)
         p = Problem(w, n_frames=40)
-        theta = sdf_parity_params(w, sg.room_scene(), seed=31)
+        theta = bf16_inputs(w, sdf_parity_params(w, sg.room_scene(), seed=31))
         bt, sm = p.oracle_sample(3, 11)
-    bt_s, ref, _ = prepare_parity_batch(p, theta, bt, sm)
+    bt_s, ref, _ = prepare_parity_batch(p, theta, bt, sm, max_drop=0.15, min_switch=0.25, label=w.name)
     batch = upload_oracle_batch(bt_s, sm, sm["n_valid"][0])
     th = torch.from_numpy(theta).cuda()
     mirror = _bf16_copy(theta, p.n_grid)
+    assert torch.equal(mirror.view(torch.bfloat16).float(), th[:p.n_grid])  # the copy is exact
     loss = torch.empty(6, device="cuda")
     grad = torch.zeros_like(th)
     p.ctx.forward_backward(th, batch, None, loss, grad, theta_bf16=mirror)
     torch.cuda.synchronize()
     got = loss.cpu().numpy().astype(np.float64)
-    loss_err = np.abs(got - ref["loss"]) / np.abs(ref["loss"])
+    loss_err = np.abs(got - ref["loss"]) / np.maximum(np.abs(ref["loss"]), 1e-30)
     A, B = p.split_grad(grad.cpu().numpy().astype(np.float64)), p.split_grad(ref["grad"])
     l2 = {k: float(np.linalg.norm(A[k] - B[k]) / max(np.linalg.norm(B[k]), 1e-30)) for k in A}
     mx = {k: float(np.abs(A[k] - B[k]).max() / max(np.abs(B[k]).max(), 1e-30)) for k in A}
-    print(f"\nBF16 form vs FP64 oracle ({w.name}, {bt_s['t'].shape[0]} rays)")
-    print("  loss rel err [rgb, d, sdf, fs, smooth, total]:", np.round(loss_err, 5).tolist())
-    print("  grad rel L2 err:", {k: round(v, 4) for k, v in l2.items()})
-    print("  grad max-norm err:", {k: round(v, 4) for k, v in mx.items()})
-    # format-determined: the total loss and the smooth-loss terms, the decoder gradients that
-    # do not pass through a kink decision of the SDF sign; the grid and W1 gradients carry the
-    # flips (stated above) and are only required to stay the same vector field (L2 error < 1)
-    assert loss_err[5] <= 2e-2
-    assert max(loss_err[0], loss_err[1]) <= 5e-2
-    for k in ("b1", "W2", "b2", "W3", "b3", "W4", "b4", "kappa"):
-        assert l2[k] <= 5e-2, (k, l2)
-    assert max(l2.values()) < 1.0, l2
+    print(f"\nBF16 form vs FP64 oracle on bfloat16-rounded parameters ({w.name}, {bt_s['t'].shape[0]} rays)")
+    print("  loss rel err [rgb, d, sdf, fs, smooth, total]:", np.round(loss_err, 6).tolist())
+    print("  grad max-norm err:", {k: round(v, 5) for k, v in mx.items()})
+    print("  grad rel L2 err:", {k: round(v, 5) for k, v in l2.items()})
+    loss_bound, bounds = BF16_BOUNDS[wl]
+    assert loss_err.max() <= loss_bound, loss_err
+    assert set(bounds) == set(A)
+    for k, (b_mx, b_l2) in bounds.items():
+        assert mx[k] <= b_mx and l2[k] <= b_l2, (k, mx[k], l2[k])
 
 
 def test_bf16_form_requires_the_grid_copy():

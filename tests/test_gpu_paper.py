@@ -13,7 +13,9 @@ import torch
 import oracle as oc
 import paper_2206_14735_gb300 as gs
 import scenegen as sg
-from gpu_common import LOSS_RTOL, Problem, assert_grad_close, prepare_parity_batch, upload_oracle_batch
+from gpu_common import (LOSS_RTOL, Problem, assert_grad_close, drop_kink_points, drop_kink_rays, far_from_kinks,
+                        prepare_parity_batch, upload_oracle_batch)
+from helpers import paper_parity_params
 
 pytestmark = pytest.mark.gpu
 
@@ -29,12 +31,16 @@ def _padded(theta):
     return t
 
 
-def _case(w, R=None, P=None, seed=SEED, step=STEP, max_drop=0.1):
+def _case(w, R=None, P=None, seed=SEED, step=STEP, max_drop=0.05):
+    """Parity case with hidden units that switch within the batch (all four hidden layers);
+    rays holding a binary32 tie (a unit at its kink, an alpha, an SDF sign, a free-space
+    maximum) are left out, printed and bounded by max_drop."""
     p = Problem(w, max_rays=R)
-    theta = sg.paper_sdf_params(w, sg.cube_scene(), seed=23)
+    theta = paper_parity_params(w, sg.cube_scene(), seed=23)
     bt, sm = p.oracle_sample(seed, step, R, P)
-    bt_s, ref, dropped = prepare_parity_batch(p, theta, bt, sm, max_drop=max_drop)
-    assert ref["margins"][0] > 1e-2, ref["margins"]  # hidden units clear of their kinks
+    big = len(bt["D"]) >= 64
+    bt_s, ref, dropped = prepare_parity_batch(p, theta, bt, sm, max_drop=max_drop, min_switch=0.25 if big else None,
+                                              label=w.name)
     assert ref["margins"][5] > 1e-5, ref["margins"]
     batch = upload_oracle_batch(bt_s, sm, 0 if sm is None else sm["n_valid"][0])
     return dict(p=p, theta=theta, bt=bt_s, sm=sm, ref=ref, batch=batch)
@@ -68,7 +74,10 @@ def test_paper_forward_loss_parity(cube_paper):
     ref = cube_paper["ref"]
     _check_loss(got, ref["loss"])
     assert got[0] > 0 and got[2] > 0 and got[3] > 0 and got[4] > 0
-    np.testing.assert_allclose(rgb_hat, ref["rgb_hat"], atol=2e-6)
+    # binary32 phi carries about ulp(3) = 2.4e-7 from the pass-through units (values near 3);
+    # s = 20 turns that into |dPhi| <= 5 x 2.4e-7 and the weights w = T (Phi_k - Phi_k+1) / Phi_k
+    # into a few 1e-6: 5e-6 on the rendered colour
+    np.testing.assert_allclose(rgb_hat, ref["rgb_hat"], atol=5e-6)
     np.testing.assert_allclose(d_hat, ref["d_hat"], atol=2e-5)
     np.testing.assert_allclose(wsum, ref["wsum"], atol=2e-6)
     assert wsum.max() <= 1.0 + 1e-6
@@ -137,7 +146,7 @@ def test_paper_ragged_shapes(n_strat, n_guided, R, P):
 def test_paper_empty_batches():
     """No rays and no points: losses 0, gradient untouched; points only: the smoothness term."""
     p = Problem(CUBE_P)
-    theta = sg.paper_sdf_params(CUBE_P, sg.cube_scene(), seed=23)
+    theta = paper_parity_params(CUBE_P, sg.cube_scene(), seed=23)
     th = _padded(theta)
     empty = gs.Batch.allocate(0, CUBE_P.n_samples, 0)
     loss = torch.full((6,), 7.0, device="cuda")
@@ -146,6 +155,7 @@ def test_paper_empty_batches():
     torch.cuda.synchronize()
     assert np.all(loss.cpu().numpy() == 0) and torch.all(grad == 0.5)
     _, sm = p.oracle_sample(SEED, STEP, 0, 64)
+    drop_kink_points(p, theta, sm)  # L_smooth jumps where a hidden unit switches
     bt0 = {k: v[:0] for k, v in p.oracle_sample(SEED, STEP, 1, 0)[0].items() if k != "counts"}
     bt0["counts"] = np.zeros(4, np.int64)
     ref = oc.step(p.cfg, theta, bt0, sm)
@@ -179,13 +189,13 @@ def test_paper_room_scale_parity():
     samples, 4096 smoothness points) and full grid (185.1 M parameters, colour grid on the
     2 cm level), in the launch configuration the benchmark times, on the first 40 frames.
     Rays with a binary32 tie (mostly consecutive samples clamped to the room box with nearly
-    equal SDF) are left out: up to 20 % here."""
+    equal SDF, and hidden units at their kinks) are left out: up to 20 % here."""
     w = sg.WORKLOADS["room-paper-8192x96"]
     p = Problem(w, n_frames=40)
     bt, sm = p.oracle_sample(SEED, 11)
-    theta = sg.paper_sdf_params(w, sg.room_scene(), seed=31)
-    bt_s, ref, dropped = prepare_parity_batch(p, theta, bt, sm, max_drop=0.2)
-    assert ref["margins"][0] > 1e-2 and ref["margins"][5] > 1e-5, ref["margins"]
+    theta = paper_parity_params(w, sg.room_scene(), seed=31)
+    bt_s, ref, dropped = prepare_parity_batch(p, theta, bt, sm, max_drop=0.2, min_switch=0.25, label="room paper")
+    assert ref["margins"][5] > 1e-5, ref["margins"]
     batch = upload_oracle_batch(bt_s, sm, sm["n_valid"][0])
     th = _padded(theta)
     loss = torch.empty(6, device="cuda")
@@ -211,7 +221,9 @@ def test_paper_query_sdf_parity(cube_paper):
     c["p"].ctx.query_sdf(th, xd, sdf, grad)
     torch.cuda.synchronize()
     np.testing.assert_allclose(sdf.cpu().numpy(), sdf_ref, atol=2e-6)
-    np.testing.assert_allclose(grad.cpu().numpy(), g_ref, atol=2e-4 * np.abs(g_ref).max())
+    ok = far_from_kinks(c["p"], c["theta"], x)  # grad_x phi jumps where a unit switches
+    assert ok.mean() > 0.99
+    np.testing.assert_allclose(grad.cpu().numpy()[ok], g_ref[ok], atol=2e-4 * np.abs(g_ref).max())
     only = torch.empty(len(x), device="cuda")
     c["p"].ctx.query_sdf(th, xd, only)  # phi alone
     torch.cuda.synchronize()
@@ -230,10 +242,12 @@ def test_paper_eikonal_parity(cube_paper, R):
     geometry decoder; the colour parameters get none)."""
     c = cube_paper
     bt = c["bt"] if R is None else {k: (v[:R] if k != "counts" else v) for k, v in c["bt"].items()}
+    bt, dropped = drop_kink_rays(c["p"], c["theta"], bt)  # L_eik jumps where a unit switches
+    print(f"paper eikonal: {dropped} rays left out")
+    assert dropped <= 0.05 * len(bt["D"]) + 1
     ref_l, ref_g, n_fs, gnorm = oc.eikonal(c["p"].cfg, c["theta"], bt)
     assert n_fs > (1000 if R is None else 20)
-    batch = c["batch"] if R is None else upload_oracle_batch(
-        {**bt, "counts": np.array([(bt["D"] > 0).sum(), (bt["cls"] == 1).sum(), (bt["cls"] == 2).sum(), 0])}, None, 0)
+    batch = upload_oracle_batch(bt, None, 0)
     th = _padded(c["theta"])
     loss, grad = torch.full((1,), float("nan"), device="cuda"), torch.zeros_like(th)
     c["p"].ctx.eikonal(th, batch, loss=loss, grad=grad)
@@ -251,7 +265,7 @@ def test_paper_full_method_step():
     from test_gpu_importance import _check_depth_deviation
     w = CUBE_P.with_(name="cube-paper-imp", imp_coarse=96, imp_steps=3, imp_per_step=12, rays=512)
     p = Problem(w)
-    theta = sg.paper_sdf_params(w, sg.cube_scene(), seed=23)
+    theta = paper_parity_params(w, sg.cube_scene(), seed=23)
     th = _padded(theta)
     b = gs.Batch.allocate(w.rays, w.n_samples, w.n_smooth)
     p.ctx.sample_importance(p.dfr, th, SEED, STEP, b)
@@ -265,7 +279,10 @@ def test_paper_full_method_step():
     # the step on the oracle's batch (the same depths on both sides)
     sm = oc.sample_smooth(p.cfg, p.ofr, SEED, STEP, w.n_smooth)
     bt = {k: ref[k] for k in ("pix", "o", "r", "rgb", "D", "t", "cls", "counts")}
-    bt_s, st_ref, dropped = prepare_parity_batch(p, theta, bt, sm, max_drop=0.2)
+    bt_s, st_ref, dropped = prepare_parity_batch(p, theta, bt, sm, max_drop=0.2, min_switch=0.25,
+                                                 label="paper importance")
+    bt_s, n_eik = drop_kink_rays(p, theta, bt_s)  # and those whose L_eik jumps at a kink
+    st_ref = oc.step(p.cfg, theta, bt_s, sm)
     batch = upload_oracle_batch(bt_s, sm, sm["n_valid"][0])
     loss, grad = torch.empty(6, device="cuda"), torch.zeros_like(th)
     p.ctx.forward_backward(th, batch, None, loss, grad)
@@ -306,7 +323,7 @@ def test_paper_proposal_learns_from_the_paper_models_weights():
     cross-entropy gradient from those weights matches the oracle's."""
     w = CUBE_P.with_(name="cube-paper-prop", prop_samples=32, prop_guided=8)
     p = Problem(w, max_rays=512)
-    theta = sg.paper_sdf_params(w, sg.cube_scene(), seed=23)
+    theta = paper_parity_params(w, sg.cube_scene(), seed=23)
     q = np.random.default_rng(3).normal(0.0, 0.3, oc.PROP_PARAMS).astype(np.float32)
     R = 512
     bt, _ = p.oracle_sample(SEED, STEP, R, 0)
@@ -324,8 +341,10 @@ def test_paper_proposal_learns_from_the_paper_models_weights():
     bo = dict(bt, t=ref_s["t"], cls=ref_s["cls"], counts=ref_s["counts"])
     ref = oc.step(p.cfg, theta, bo, None, want_grad=False, want_weights=True)
     # alpha = (Phi_i - Phi_i+1) / Phi_i loses relative precision in binary32 when the two
-    # opacities are close: a relative as well as an absolute bound, as for the workload's model
-    np.testing.assert_allclose(wt, ref["w"], rtol=1e-4, atol=2e-6)
+    # opacities are close: a relative as well as an absolute bound, the absolute one from the
+    # binary32 rounding of phi (about ulp(3) through the pass-through units) times s / 4 = 5,
+    # twice (Phi_k and Phi_k+1) over Phi_k
+    np.testing.assert_allclose(wt, ref["w"], rtol=1e-4, atol=5e-6)
     grad, ce = torch.zeros(oc.PROP_PARAMS, device="cuda"), torch.zeros(2, device="cuda")
     p.ctx.proposal_backward(th, torch.from_numpy(q).cuda(), b, grad, ce)
     torch.cuda.synchronize()
@@ -345,6 +364,8 @@ def test_paper_query_sdf_backward_parity(cube_paper, terms):
     rng = np.random.default_rng(11)
     P = 2000
     x = rng.uniform(-1.2, 1.2, (P, 3)).astype(np.float32)
+    x = x[far_from_kinks(c["p"], c["theta"], x)]  # grad_x phi jumps where a unit switches
+    P = len(x)
     ds = rng.normal(size=P) if terms in ("both", "sdf") else None
     dg = rng.normal(size=(P, 3)) if terms in ("both", "grad") else None
     ref = oc.query_sdf_backward(c["p"].cfg, c["theta"], x, ds, dg)
@@ -363,7 +384,8 @@ def test_paper_sdfgrad_autograd(cube_paper):
     oracle's gradient."""
     c = cube_paper
     rng = np.random.default_rng(12)
-    x = torch.from_numpy(rng.uniform(-1.0, 1.0, (500, 3)).astype(np.float32)).cuda()
+    xs = rng.uniform(-1.0, 1.0, (500, 3)).astype(np.float32)
+    x = torch.from_numpy(xs[far_from_kinks(c["p"], c["theta"], xs)]).cuda()
     th = _padded(c["theta"]).requires_grad_(True)
     sdf, g = gs.SdfGrad.apply(th, c["p"].ctx, x)
     loss = (sdf ** 2).sum() + ((g.norm(dim=1) - 1.0) ** 2).sum()
@@ -385,7 +407,7 @@ def test_paper_pose_records_and_gradient_match_oracle():
     xi = np.c_[rng.normal(0, 0.01, (3, 3)), rng.normal(0, 0.01, (3, 3))]
     c2w = oc.pose_apply(p.frames.c2w, xi)
     F = oc.OcFramesHolder(p.frames, c2w=c2w)
-    theta = sg.paper_sdf_params(w, sg.cube_scene(), seed=23)
+    theta = paper_parity_params(w, sg.cube_scene(), seed=23)
     bt = oc.sample_rays(p.cfg, F, 9, 2, w.rays)
     sm = oc.sample_smooth(p.cfg, F, 9, 2, w.n_smooth)
     bt_s, _, _ = prepare_parity_batch(p, theta, bt, sm)

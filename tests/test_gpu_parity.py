@@ -14,8 +14,8 @@ import torch
 import oracle as oc
 import paper_2206_14735_gb300 as gs
 import scenegen as sg
-from gpu_common import (GRAD_TOL, LOSS_RTOL, Problem, assert_grad_close, prepare_parity_batch, sample_positions,
-                        upload_oracle_batch)
+from gpu_common import (GRAD_TOL, LOSS_RTOL, Problem, assert_grad_close, far_from_kinks, prepare_parity_batch,
+                        sample_positions, upload_oracle_batch)
 from helpers import CUBE, sdf_parity_params
 
 pytestmark = pytest.mark.gpu
@@ -82,10 +82,10 @@ def test_voxel_index_bit_exact(cube):
 def cube_case(cube):
     theta = sdf_parity_params(CUBE, sg.cube_scene(), seed=21)
     bt, sm = cube.oracle_sample(SEED, STEP)
-    bt_s, ref, n_dropped = prepare_parity_batch(cube, theta, bt, sm)
-    # hidden units and per-ray depth signs are clear of their kinks by construction
-    assert ref["margins"][0] > 1e-2, ref["margins"]
-    assert ref["margins"][5] > 1e-4, ref["margins"]
+    # hidden units switch within the batch; rays with a unit, an alpha, an SDF sign or a
+    # free-space maximum within binary32 rounding of its tie are left out
+    bt_s, ref, n_dropped = prepare_parity_batch(cube, theta, bt, sm, max_drop=0.05, min_switch=0.25, label="cube")
+    assert ref["margins"][5] > 1e-5, ref["margins"]  # per-ray depth signs clear of their kink
     batch = upload_oracle_batch(bt_s, sm, sm["n_valid"][0])
     return dict(theta=theta, bt=bt_s, sm=sm, ref=ref, batch=batch)
 
@@ -179,7 +179,11 @@ def test_query_sdf_parity(cube, cube_case):
     cube.ctx.query_sdf(th, torch.from_numpy(x).cuda(), sdf, grad)
     torch.cuda.synchronize()
     np.testing.assert_allclose(sdf.cpu().numpy(), sdf_ref, atol=2e-6)
-    np.testing.assert_allclose(grad.cpu().numpy(), g_ref, atol=2e-4 * np.abs(g_ref).max())
+    # grad_x phi jumps where a hidden unit switches: points within binary32 rounding of a
+    # kink are not compared
+    ok = far_from_kinks(cube, cube_case["theta"], x)
+    assert ok.mean() > 0.99
+    np.testing.assert_allclose(grad.cpu().numpy()[ok], g_ref[ok], atol=2e-4 * np.abs(g_ref).max())
 
 
 def test_adam_parity(cube):
@@ -235,7 +239,7 @@ def test_ragged_samples_per_ray():
     p = Problem(w)
     theta = sdf_parity_params(w, sg.cube_scene(), seed=22)
     b_gpu, bt, sm = _check_sampler(p, w.rays, w.n_smooth, seed=4, step=1)
-    bt_s, ref, _ = prepare_parity_batch(p, theta, bt, sm)
+    bt_s, ref, _ = prepare_parity_batch(p, theta, bt, sm, max_drop=0.06, min_switch=0.25, label="ragged N=33")
     batch = upload_oracle_batch(bt_s, sm, sm["n_valid"][0])
     th = torch.from_numpy(theta).cuda()
     loss = torch.empty(6, device="cuda")
@@ -257,8 +261,9 @@ def test_room_scale_parity(n_frames):
     _check_sampler(p, w.rays, w.n_smooth, seed=SEED, step=11)
     bt, sm = p.oracle_sample(SEED, 11)
     theta = sdf_parity_params(w, sg.room_scene(), seed=31)
-    bt_s, ref, n_dropped = prepare_parity_batch(p, theta, bt, sm)
-    assert ref["margins"][0] > 1e-2 and ref["margins"][5] > 1e-4
+    # 96 samples per ray, so more rays hold a sample within binary32 rounding of a tie
+    bt_s, ref, n_dropped = prepare_parity_batch(p, theta, bt, sm, max_drop=0.15, min_switch=0.25, label="room")
+    assert ref["margins"][5] > 1e-5
     batch = upload_oracle_batch(bt_s, sm, sm["n_valid"][0])
     th = torch.from_numpy(theta).cuda()
     loss = torch.empty(6, device="cuda")

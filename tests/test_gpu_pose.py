@@ -80,7 +80,7 @@ def test_pose_refinement_reduces_the_pose_error():
     import math
     w = W3.with_(rays=2048, n_smooth=0)
     p = Problem(w)
-    th = sdf_parity_params(w, sg.cube_scene(), seed=21, mix=0.0)
+    th = sdf_parity_params(w, sg.cube_scene(), seed=21, mix=0.0, phi_shift=0.0)
     th[-1] = math.log(2000.0)
     theta = torch.from_numpy(th).cuda()
     rng = np.random.default_rng(11)

@@ -25,7 +25,9 @@ def _q(seed=3, scale=0.3):
 @pytest.fixture(scope="module")
 def prob():
     p = Problem(CUBE_P, max_rays=4096)
-    theta = sdf_parity_params(CUBE_P, sg.cube_scene(), seed=21)
+    # the proposal network's own hidden units switch (q ~ N(0, 0.3)); the main decoder's masks
+    # are not what these tests are about, so its parameters keep every unit clear of its kink
+    theta = sg.sdf_params(CUBE_P, sg.cube_scene(), seed=21)
     theta[:p.n_grid] += np.random.default_rng(5).normal(0, 0.2, p.n_grid).astype(np.float32)  # coarse features vary
     return dict(p=p, theta=theta, q=_q())
 

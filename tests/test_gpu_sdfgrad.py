@@ -7,7 +7,7 @@ import torch
 import oracle as oc
 import paper_2206_14735_gb300 as gs
 import scenegen as sg
-from gpu_common import Problem, assert_grad_close
+from gpu_common import Problem, assert_grad_close, far_from_kinks
 from helpers import CUBE, sdf_parity_params
 
 pytestmark = pytest.mark.gpu
@@ -21,7 +21,12 @@ def case():
     x = sm["xs"][sm["valid"] > 0]  # points near the observed surface, as the smoothness term draws them
     rng = np.random.default_rng(7)
     x = np.concatenate([x, rng.uniform(-1.5, 1.5, (1000, 3)).astype(np.float32)])  # and anywhere, outside too
-    return dict(p=p, theta=theta, x=x, rng=rng)
+    # the hidden units switch between points; grad_x phi (and its reverse mode) jumps at a
+    # kink, so points within binary32 rounding of one are left out
+    ok = far_from_kinks(p, theta, x)
+    print(f"sdfgrad points: {int((~ok).sum())} of {len(x)} left out")
+    assert ok.mean() > 0.99
+    return dict(p=p, theta=theta, x=x[ok], rng=rng)
 
 
 def _run(p, theta, x, dsdf, dgrad):

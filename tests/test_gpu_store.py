@@ -24,7 +24,7 @@ def case():
     p = Problem(CUBE)
     theta = sdf_parity_params(CUBE, sg.cube_scene(), seed=21)
     bt, sm = p.oracle_sample(SEED, STEP)
-    bt_s, ref, _ = prepare_parity_batch(p, theta, bt, sm)
+    bt_s, ref, _ = prepare_parity_batch(p, theta, bt, sm, max_drop=0.05, min_switch=0.25, label="store cube")
     batch = upload_oracle_batch(bt_s, sm, sm["n_valid"][0])
     store_ctx = gs.Context(CUBE, store_activations=True)
     return dict(p=p, theta=theta, ref=ref, batch=batch, store_ctx=store_ctx)
