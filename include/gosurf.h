@@ -108,8 +108,9 @@ typedef struct gs_config {
   int32_t precision;          /* GS_PREC_FP32 or GS_PREC_BF16 */
   int32_t store_activations;  /* 1: every forward pass writes each sample's decoder inputs and
                                  activations (z, ReLU outputs, SDF, geometric feature, colour:
-                                 99 floats = 396 bytes per sample, max_rays x N samples, one
-                                 plane per field, allocated by gs_create; GS_ARCH_PAPER: 156
+                                 100 floats = 400 bytes per sample, max_rays x N samples, in
+                                 float4 planes of four fields each, allocated by gs_create;
+                                 GS_ARCH_PAPER: 156
                                  floats) and every backward pass reads them instead of gathering
                                  again and recomputing the decoders; 0: the backward pass
                                  recomputes them (no memory) */

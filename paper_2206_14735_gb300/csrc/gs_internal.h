@@ -11,7 +11,7 @@ constexpr int kMlpPad = 1688;     // per-CTA decoder-gradient partial row (>= GS
 constexpr int kLossPad = 8;       // per-CTA loss partial row
 constexpr int kSmoothCtas = 128;  // CTAs of the smoothness kernel (fixed, so partial rows are known)
 constexpr int kRenderCtasPerSm = 1;  // persistent render CTAs per SM
-constexpr int kStoreFloatsPerSample = 99;  // stored activations: z 16, a1 32, (phi, h) 16, a2 32, c 3
+constexpr int kStoreFloatsPerSample = 100;  // stored activations: z 16, a1 32, (phi, h) 16, a2 32, c 3 + 1 pad
 constexpr int kRenderGroups = 3;     // tile groups (4 warps, 128 tensor-memory columns each) per render CTA
 constexpr int kEikCtasPerSm = 4;     // CTAs of the Eikonal kernel per SM (one wave at 230 registers x 64 threads)
 

@@ -449,15 +449,27 @@ __device__ __forceinline__ float pick_tc(const float (&arr)[N], int j) {
   return v;
 }
 
+// Stored activations come in groups of four fields, one float4 plane per group: field f of
+// sample s sits in component f % 4 of ((float4*)store)[(f / 4) * ss + s], so a warp's 32
+// consecutive samples read or write one 512-byte line per group.  sp points at sample s's
+// element of plane 0.
 template <int F0, int NF, int M>
-__device__ __forceinline__ void put_fields(float* sp, long long ss, const float (&v)[M]) {
+__device__ __forceinline__ void put_fields(float4* sp, long long ss, const float (&v)[M]) {
+  static_assert(F0 % 4 == 0 && NF % 4 == 0 && NF <= M, "whole groups of four fields");
 #pragma unroll
-  for (int k = 0; k < NF; ++k) sp[(F0 + k) * ss] = v[k];
+  for (int q = 0; q < NF / 4; ++q) sp[(F0 / 4 + q) * ss] = make_float4(v[4 * q], v[4 * q + 1], v[4 * q + 2], v[4 * q + 3]);
 }
 template <int F0, int NF, int M>
-__device__ __forceinline__ void get_fields(const float* sp, long long ss, bool get, float (&v)[M]) {
+__device__ __forceinline__ void get_fields(const float4* sp, long long ss, bool get, float (&v)[M]) {
+  static_assert(F0 % 4 == 0 && NF % 4 == 0 && NF <= M, "whole groups of four fields");
 #pragma unroll
-  for (int k = 0; k < NF; ++k) v[k] = get ? __ldg(sp + (F0 + k) * ss) : 0.f;
+  for (int q = 0; q < NF / 4; ++q) {
+    const float4 u = get ? __ldg(sp + (F0 / 4 + q) * ss) : make_float4(0.f, 0.f, 0.f, 0.f);
+    v[4 * q] = u.x;
+    v[4 * q + 1] = u.y;
+    v[4 * q + 2] = u.z;
+    v[4 * q + 3] = u.w;
+  }
 }
 
 struct RenderTcArgs {
@@ -476,9 +488,10 @@ struct RenderTcArgs {
   float* mlp_part;
   float *rgb_hat, *d_hat, *wsum;
   int* status;      // device status word (bit 1: an MMA never completed)
-  // Stored activations (store mode): field f of sample s = rr * N + si at store[f * store_stride + s],
-  // one coalesced plane per field.  Written by every forward pass, read by every backward pass
-  // in place of the gather and the four recomputed decoder phases.  nullptr: recompute.
+  // Stored activations (store mode): field f of sample s = rr * N + si in component f % 4 of
+  // ((float4*)store)[(f / 4) * store_stride + s], one coalesced float4 plane per four fields.
+  // Written by every forward pass, read by every backward pass in place of the gather and the
+  // four recomputed decoder phases.  nullptr: recompute.
   float* store;
   long long store_stride;
   float* w_out;  // [R][N] rendering weights, written by forward passes when not nullptr
@@ -488,8 +501,8 @@ struct RenderTcArgs {
   CUtensorMap tmap[2];
 };
 
-// fields of one stored sample: z[16] | a1 = ReLU layer-1 output [32] | (phi, h[15]) | a2 [32] | c[3]
-constexpr int kFz = 0, kFa1 = 16, kFout = 48, kFa2 = 64, kFc = 96, kStoreFields = 99;
+// fields of one stored sample: z[16] | a1 = ReLU layer-1 output [32] | (phi, h[15]) | a2 [32] | c[3], 0
+constexpr int kFz = 0, kFa1 = 16, kFout = 48, kFa2 = 64, kFc = 96, kStoreFields = 100;
 static_assert(kStoreFields == kStoreFloatsPerSample, "the store holds every field");
 
 // colour c = sigmoid(W4 a2 + b4) on CUDA cores (3 outputs: too narrow for a tensor-core phase)
@@ -654,17 +667,19 @@ __global__ void __launch_bounds__(GR * kGroupThreads, 1) render_tc_kernel(const 
       const int si = 32 * j + lane;
       const bool valid = has_ray && si < N;
       const float t = pick_tc(tt, j);
-      float* sp = a.store != nullptr ? a.store + (size_t)rr * N + si : nullptr;  // this sample's field 0
+      float4* sp = a.store != nullptr ? reinterpret_cast<float4*>(a.store) + (size_t)rr * N + si : nullptr;
       const long long ss = a.store_stride;
       if (!FWD && sp != nullptr) {  // stored by the forward pass: no decoder phases here
+        const float4 o4 = valid ? sp[(kFout / 4) * ss] : make_float4(0.f, 0.f, 0.f, 0.f);
+        const float4 c4 = valid ? sp[(kFc / 4) * ss] : make_float4(0.f, 0.f, 0.f, 0.f);
 #pragma unroll
         for (int q = 0; q < NCH; ++q)
           if (q == j) {
             tt[q] = t;
-            ph[q] = valid ? sp[kFout * ss] : 0.f;
-            col[q][0] = valid ? sp[kFc * ss] : 0.f;
-            col[q][1] = valid ? sp[(kFc + 1) * ss] : 0.f;
-            col[q][2] = valid ? sp[(kFc + 2) * ss] : 0.f;
+            ph[q] = o4.x;
+            col[q][0] = c4.x;
+            col[q][1] = c4.y;
+            col[q][2] = c4.z;
           }
         continue;
       }
@@ -700,8 +715,11 @@ __global__ void __launch_bounds__(GR * kGroupThreads, 1) render_tc_kernel(const 
       store_row<P, 16>(G.a, row, h);
       mma_phase_issue<P, 32, 16>(G, cD3, wt0 + wOff<P>(2), wplane);
       if (put) {
-        sp[kFout * ss] = phi;
-        put_fields<kFout + 1, 15>(sp, ss, h);
+        float oh[16];
+        oh[0] = phi;
+#pragma unroll
+        for (int k = 0; k < 15; ++k) oh[k + 1] = h[k];
+        put_fields<kFout, 16>(sp, ss, oh);
       }
       if (!(alive = mma_phase_wait(G))) break;
       tc::tmem_ld32(lane_addr(G, cD3, warp_g), v);
@@ -711,7 +729,10 @@ __global__ void __launch_bounds__(GR * kGroupThreads, 1) render_tc_kernel(const 
       if (put) put_fields<kFa2, 32>(sp, ss, v);
       float c3[3];
       colour_out(w4f, b4, v, c3);
-      if (put) put_fields<kFc, 3>(sp, ss, c3);
+      if (put) {
+        const float c4[4] = {c3[0], c3[1], c3[2], 0.f};
+        put_fields<kFc, 4>(sp, ss, c4);
+      }
       // keep per-chunk values in registers (compile-time index via a selector loop)
 #pragma unroll
       for (int q = 0; q < NCH; ++q)
@@ -881,7 +902,7 @@ __global__ void __launch_bounds__(GR * kGroupThreads, 1) render_tc_kernel(const 
       const float t = pick_tc(tt, j);
       float x[3];
       sample_pos(o, r, t, x);
-      const float* sp = a.store != nullptr ? a.store + (size_t)rr * N + si : nullptr;
+      const float4* sp = a.store != nullptr ? reinterpret_cast<const float4*>(a.store) + (size_t)rr * N + si : nullptr;
       const long long ss = a.store_stride;
       const bool get = sp != nullptr && valid;
       float z[kZ], v[32], h[16], u[16], c3[3];
@@ -889,9 +910,16 @@ __global__ void __launch_bounds__(GR * kGroupThreads, 1) render_tc_kernel(const 
       if (sp != nullptr) {  // stored activations: z, a2, h and c now, a1 where it is used
         get_fields<kFz, 16>(sp, ss, get, z);
         get_fields<kFa2, 32>(sp, ss, get, v);
-        get_fields<kFout + 1, 15>(sp, ss, get, h);
+        float oh[16];
+        get_fields<kFout, 16>(sp, ss, get, oh);
+#pragma unroll
+        for (int k = 0; k < 15; ++k) h[k] = oh[k + 1];
         h[15] = 0.f;
-        get_fields<kFc, 3>(sp, ss, get, c3);
+        float c4[4];
+        get_fields<kFc, 4>(sp, ss, get, c4);
+        c3[0] = c4[0];
+        c3[1] = c4[1];
+        c3[2] = c4[2];
       } else {
         dw_wait(G);
         gather_chunk<P>(G, a, x, valid, z);
