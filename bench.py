@@ -136,7 +136,7 @@ def step_config(w, args, world, n_frames):
             "resolution": [w.width, w.height], "parallelism": f"replicas{world}",
             "model": ("paper: colour grid (6 features, finest level) + view direction, decoders with "
                       "2 hidden layers of 32" if paper else "compact: decoders 16-32-16 and 15-32-3"),
-            "activations": "recomputed" if recompute else f"stored ({624 if paper else 396} B/sample)",
+            "activations": "recomputed" if recompute else f"stored ({624 if paper else 400} B/sample)",
             "sampler": (f"importance: {w.imp_coarse} coarse + {w.imp_steps} x {w.imp_per_step}"
                         if w.imp_coarse > 0 else f"stratified {w.n_strat} + depth-guided {w.n_guided}"),
             "pipeline": ("the next step's batch sampled on a side stream during this step (double-buffered)"
@@ -399,7 +399,39 @@ def run_ours(args):
         line["sampler_report"] = sampler_report(w, fr, dfr, args.sampler_report)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(w, fr, args.cpu_rays)
+    if rank == 0 and world == 1 and w.name == WORKLOAD and args.target_steps > 0:
+        line["target_pair"] = target_pair(args)
     return line
+
+
+def target_pair(args):
+    """The pair of forms the method's target compares, measured in the same run: the plain
+    FP32 form at 65536 rays x (64 + 32) samples and the BF16 + learned-proposal form at 65536
+    rays x 32 samples (plain 96 as its fallback), both trained for the same number of steps
+    from the same initial parameters on the room scene with 30 % of every depth frame dropped
+    in discs; rays/s of each over those steps and the final rendered-depth L1 against the
+    noise-free depth."""
+    import scenegen as sg
+    import paper_2206_14735_gb300 as gs
+    wp = sg.WORKLOADS["room-prop-bf16-65536x32"]
+    frp = sg.make_frames(wp, n_frames=args.frames, with_gt=True)
+    dfrp = gs.DeviceFrames(frp.rgb, frp.depth, frp.c2w, frp.fx, frp.fy, frp.cx, frp.cy)
+    tail = max(1, args.target_steps // 8)
+    rep = proposal_report(wp, frp, dfrp, args.target_steps, tail=tail)
+    plain, prop = rep["plain"], rep["proposal"]
+    l1_plain, l1_prop = plain["depth_l1_gt_m"], prop["with_proposal"]["depth_l1_gt_m"]
+    speed = prop["tail_rays_per_s"] / plain["tail_rays_per_s"]
+    keys = ("rays_per_s", "tail_rays_per_s", "samples_per_ray")
+    return {"workload": wp.name, "steps_each": args.target_steps,
+            "plain_fp32": {**{k: plain[k] for k in keys}, "depth_l1_gt_m": l1_plain,
+                           "depth_l1_gt_dropped_m": plain["depth_l1_gt_dropped_m"]},
+            "bf16_proposal": {**{k: prop[k] for k in keys}, "steps_on_proposal": prop["proposal_steps"],
+                              "tail_steps_on_proposal": prop["tail_steps_on_proposal"], "depth_l1_gt_m": l1_prop,
+                              "depth_l1_gt_dropped_m": prop["with_proposal"]["depth_l1_gt_dropped_m"]},
+            "rays_per_s_ratio": round(speed, 4), "depth_l1_ratio": round(l1_prop / l1_plain, 4),
+            "target_met": bool(speed > 1.0 and l1_prop <= 1.05 * l1_plain),
+            "what": (f"{rep['what']}; the rays/s ratio compares the last {tail} steps of each (the trained "
+                     f"regime, where the controller may use the proposal)")}
 
 
 def _eval_depth(ctx, w, dfr, gt, theta, sampler, q=None, R=65536, seed=99, mirror=None):
@@ -502,11 +534,12 @@ def mesh_report(w, ctx, step_m, reps=3):
                     "inside the timed call"}
 
 
-def proposal_report(w, fr, dfr, steps):
+def proposal_report(w, fr, dfr, steps, tail=0):
     """Trains the plain form (n_strat + n_guided samples) and the learned-proposal form
     (prop_samples, plain as the fallback) from the same initial parameters for `steps`
     steps; reports rays/s of each and the final rendered-depth error against the
-    noise-free depth (overall and on rays whose observed depth was dropped)."""
+    noise-free depth (overall and on rays whose observed depth was dropped).  With tail > 0
+    also the rays/s of the last `tail` steps alone (the trained regime)."""
     import numpy as np
     import torch
 
@@ -524,21 +557,33 @@ def proposal_report(w, fr, dfr, steps):
         loss = torch.empty(6, device="cuda")
         trainer = ProposalTrainer(ctx, w, dfr, seed=5, mirror=mirror) if form == "proposal" else None
         batch = gs.Batch.allocate(w.rays, w.n_samples, w.n_smooth) if form == "plain" else None
-        n_prop = 0
+        n_prop = n_prop_tail = 0
         torch.cuda.synchronize()
         t0 = time.perf_counter()
+        t_tail = None
         for k in range(steps):
+            if tail > 0 and k == steps - tail:
+                torch.cuda.synchronize()
+                t_tail = time.perf_counter()
             if trainer is None:
                 ctx.sample_rays(dfr, 5, k, batch)
                 ctx.forward_backward(theta, batch, None, loss, grad)
                 ctx.adam_step(theta, grad, m, v, k + 1, w.lr_grid, w.lr_mlp, w.betas[0], w.betas[1], w.adam_eps)
             else:
-                n_prop += int(trainer.controller.use_proposal)
+                on = int(trainer.controller.use_proposal)
+                n_prop += on
+                n_prop_tail += on if t_tail is not None else 0
                 trainer.step(k, theta, grad, m, v, loss)
         torch.cuda.synchronize()
-        dt = time.perf_counter() - t0
+        t1 = time.perf_counter()
+        dt = t1 - t0
         ctx.sync_status()
         res = {"steps": steps, "ms_per_step": round(1e3 * dt / steps, 3), "rays_per_s": round(w.rays * steps / dt, 1)}
+        if t_tail is not None:
+            res["tail_steps"] = tail
+            res["tail_rays_per_s"] = round(w.rays * tail / (t1 - t_tail), 1)
+            if trainer is not None:
+                res["tail_steps_on_proposal"] = n_prop_tail
         if trainer is None:
             res.update(_eval_depth(ctx, w, dfr, fr.gt_depth, theta, "plain"))
             res["samples_per_ray"] = w.n_samples
@@ -669,7 +714,7 @@ def differentiation_report(w, dfr, theta, mirror, reps=20):
                      "extra_device_bytes": extra}
         c.close()
     out["what"] = (f"{w.rays} rays x {w.n_samples} samples + {w.n_smooth} smoothness points; "
-                   f"store keeps 99 floats per sample (z, both ReLU layers, SDF and geometric feature, colour); "
+                   f"store keeps 100 floats per sample (z, both ReLU layers, SDF and geometric feature, colour, one pad); "
                    f"mean of {reps} calls each")
     return out
 
@@ -794,6 +839,9 @@ def main():
     ap.add_argument("--lr-prop", type=float, default=None, help="proposal workloads: override the proposal's lr")
     ap.add_argument("--prop-report", type=int, default=0,
                     help="proposal workloads: train plain and proposal forms this many steps and compare depth")
+    ap.add_argument("--target-steps", type=int, default=8000,
+                    help="default workload: also train the plain FP32 and the BF16 + proposal forms this many "
+                         "steps each at 65536 rays and report the pair (0: skip)")
     ap.add_argument("--mesh-report", type=float, default=0.0,
                     help="also time mesh extraction of the scene at this lattice step (metres; the paper uses 0.01)")
     ap.add_argument("--sampler-report", type=int, default=0,

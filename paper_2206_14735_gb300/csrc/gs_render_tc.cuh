@@ -391,13 +391,24 @@ __device__ __forceinline__ void coarse_gather(const GridDesc& g, const float* __
   }
 }
 
+// staging floats per warp of scatter_dz: 32 rows of 36 floats, then the 32 keys
+constexpr int kScatterStage = 33 * 36;
+
+// 16-byte vector reduction into global memory (fire and forget; the result is not read)
+__device__ __forceinline__ void red_add_f4(float4* p, float4 v) {
+  asm volatile("red.global.add.v4.f32 [%0], {%1, %2, %3, %4};" ::"l"(p), "f"(v.x), "f"(v.y), "f"(v.z), "f"(v.w)
+               : "memory");
+}
+
 // Adjoint of the gather: dtheta_l[corner] += w_c dz_l.  A warp's lanes hold consecutive
-// samples of one ray, so the cells they fall in are visited monotonically and equal cells
-// form contiguous runs of lanes.  At the two coarse levels (long runs) the 8 weighted corner
-// vectors are summed over each run through shared memory: every lane stages its 32 values as
-// a row, then lane c walks the 32 rows summing component c (corner c / 4, feature c % 4) and
-// issues one atomic at the end of each run.  At the fine levels every lane issues its own
-// 16-byte atomics.  `st`: this warp's 33 x 36 floats of staging space.
+// samples of one ray, so the cells they fall in are visited monotonically and equal cells form
+// contiguous runs of lanes.  At the two coarse levels (long runs) the 8 weighted corner vectors
+// are summed over each run through shared memory: every lane stages its 32 values as a row,
+// lane c walks the 32 rows summing component c (corner c / 4, feature c % 4), and at the end of
+// each run the four features of a corner are gathered into one lane, which issues one 16-byte
+// reduction (8 per run).  At the fine levels, where runs are short, every lane issues its 8
+// corners' 16-byte reductions directly (staging them there measured slower).
+// `st`: this warp's kScatterStage floats of staging space.
 __device__ __forceinline__ void scatter_dz(const GridDesc& g, float* grad, const float x[3], const float dz[kZ],
                                            bool valid, float* st) {
   const unsigned active = __ballot_sync(0xffffffffu, valid);
@@ -410,33 +421,36 @@ __device__ __forceinline__ void scatter_dz(const GridDesc& g, float* grad, const
     corner_weights(cc.f, wc);
     const float4 g4 = valid ? make_float4(dz[4 * l], dz[4 * l + 1], dz[4 * l + 2], dz[4 * l + 3])
                             : make_float4(0.f, 0.f, 0.f, 0.f);
-    if (l < 2) {
-      const int key = valid ? (int)cc.vtx : -1;  // the coarse levels have fewer than 2^31 vertices
-      const int next = __shfl_down_sync(0xffffffffu, key, 1);
-      const unsigned ends = __ballot_sync(0xffffffffu, lane == 31 || next != key || key < 0);  // a run's last lane
-      float* rw = st + lane * 36;
+    float4* gl = reinterpret_cast<float4*>(grad + g.off[l]);
+    if (l >= 2) {
+      if (valid) {
 #pragma unroll
-      for (int k = 0; k < 8; ++k) *reinterpret_cast<float4*>(rw + 4 * k) = f4scale(g4, wc[k]);
-      st[32 * 36 + lane] = __int_as_float(key);  // the keys after the rows
-      __syncwarp();
-      float* gl = grad + g.off[l];
-      const long long coff = corner_offset(g, l, lane >> 2);
-      float acc = 0.f;
-#pragma unroll 4
-      for (int i = 0; i < 32; ++i) {
-        acc += st[i * 36 + lane];
-        if ((ends >> i) & 1u) {  // uniform: the run holding row i ends at row i
-          const int ki = __float_as_int(st[32 * 36 + i]);
-          if (ki >= 0) atomicAdd(gl + 4 * ((long long)ki + coff) + (lane & 3), acc);
-          acc = 0.f;
-        }
+        for (int k = 0; k < 8; ++k) red_add_f4(gl + cc.vtx + corner_offset(g, l, k), f4scale(g4, wc[k]));
       }
-      __syncwarp();
-    } else if (valid) {
-      float4* gl = reinterpret_cast<float4*>(grad + g.off[l]);
-#pragma unroll
-      for (int k = 0; k < 8; ++k) atomicAdd(gl + cc.vtx + corner_offset(g, l, k), f4scale(g4, wc[k]));
+      continue;
     }
+    const int key = valid ? (int)cc.vtx : -1;  // the coarse levels have fewer than 2^31 vertices
+    const int next = __shfl_down_sync(0xffffffffu, key, 1);
+    const unsigned ends = __ballot_sync(0xffffffffu, lane == 31 || next != key || key < 0);  // a run's last lane
+    float* rw = st + lane * 36;
+#pragma unroll
+    for (int k = 0; k < 8; ++k) *reinterpret_cast<float4*>(rw + 4 * k) = f4scale(g4, wc[k]);
+    st[32 * 36 + lane] = __int_as_float(key);  // the keys after the rows
+    __syncwarp();
+    const long long coff = corner_offset(g, l, lane >> 2);
+    float acc = 0.f;
+#pragma unroll 4
+    for (int i = 0; i < 32; ++i) {
+      acc += st[i * 36 + lane];
+      if ((ends >> i) & 1u) {  // uniform: the run holding row i ends at row i
+        const float a1 = __shfl_down_sync(0xffffffffu, acc, 1), a2 = __shfl_down_sync(0xffffffffu, acc, 2),
+                    a3 = __shfl_down_sync(0xffffffffu, acc, 3);
+        const int ki = __float_as_int(st[32 * 36 + i]);
+        if ((lane & 3) == 0 && ki >= 0) red_add_f4(gl + (long long)ki + coff, make_float4(acc, a1, a2, a3));
+        acc = 0.f;
+      }
+    }
+    __syncwarp();
   }
 }
 
@@ -1059,7 +1073,8 @@ __global__ void __launch_bounds__(GR * kGroupThreads, 1) render_tc_kernel(const 
         for (int q = 0; q < 4; ++q) dzo[q] = make_float4(u[4 * q], u[4 * q + 1], u[4 * q + 2], u[4 * q + 3]);
       }
       dw_wait(G);  // the tiles' space holds the scatter's staging rows
-      scatter_dz(a.g, a.grad, x, u, valid, reinterpret_cast<float*>(G.a) + warp_g * (33 * 36));
+      static_assert(L::a_bytes * P::planes + L::b_bytes * L::b_planes >= 4u * kScatterStage * 4u, "staging space");
+      scatter_dz(a.g, a.grad, x, u, valid, reinterpret_cast<float*>(G.a) + warp_g * kScatterStage);
       group_sync(G.g);  // every warp is done with its rows before the tiles are rewritten
     }
   }
