@@ -145,7 +145,8 @@ def step_config(w, args, world, n_frames):
                      (" + gs_eikonal" if args.eikonal else ""),
             "loss_terms": "rgb, depth, sdf, fs, smooth" + (", eikonal (lam 1, free-space samples)"
                                                            if args.eikonal else ""),
-            "poses": ("refined: per-frame (dt, nu), gs_pose_apply + gs_pose_backward + Adam 5e-4 in every step"
+            "poses": ("refined: per-frame (dt, nu), gs_pose_apply + gs_pose_backward" +
+                      (" + gs_eikonal_pose_backward" if args.eikonal else "") + " + Adam 5e-4 in every step"
                       if args.poses else "fixed"),
             "l2": "inputs larger than L2: 1.2 GB of parameter/gradient/moment state streamed per step"}
 
@@ -260,6 +261,9 @@ def run_ours(args):
             ctx.eikonal(theta, b, loss=eik, grad=grad)
         if args.poses:
             ctx.pose_backward(theta, dfr_pose, xi[:6 * n_fr].view(n_fr, 6), b, xi_g[:6 * n_fr].view(n_fr, 6))
+            if args.eikonal:  # the Eikonal term moves with the poses too (x-Hessian of phi)
+                ctx.eikonal_pose_backward(theta, dfr_pose, xi[:6 * n_fr].view(n_fr, 6), b,
+                                          xi_g[:6 * n_fr].view(n_fr, 6))
             ctx.adam_step(xi, xi_g, xi_m, xi_v, k + 1, 0.0, 5e-4, n_grid=0)
         if ev is not None:
             ev[3].record(stream)
@@ -387,7 +391,7 @@ def run_ours(args):
                 "what": "per step: H2D dloss seed (pinned), the C-ABI calls of the step, D2H loss and counts into a "
                         "pinned double buffer that the host reads one step later; frames resident on the device"},
         "gpu_launches": ((9 if args.split else 6) + ((2 if paper else 1) if args.eikonal else 0) +
-                         (3 if args.poses else 0)) * args.steps,
+                         (3 if args.poses else 0) + (1 if args.poses and args.eikonal else 0)) * args.steps,
         "clocks": clk,
         "loss_last": [round(x, 6) for x in lossv],
     }

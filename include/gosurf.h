@@ -324,6 +324,20 @@ gs_status gs_pose_apply(gs_ctx* ctx, const float* c2w0, const float* xi, int32_t
 gs_status gs_pose_backward(gs_ctx* ctx, const float* theta, const gs_frames* frames, const float* xi,
                            const gs_batch* batch, float* pose_grad, void* stream);
 
+/* Camera-pose gradient of the Eikonal term (Sec. 3.3 Eq. eikonal_loss; Sec. 3.4 puts the poses
+ * among the optimised parameters): pose_grad [F][6] += dloss[0] dL_eik/d xi, L_eik the mean over
+ * the batch's free-space samples (counts[2] of them) of (1 - |grad_x phi(x_s)|)^2, as
+ * gs_eikonal.  The samples x_s = o + d_s r move with the pose (depths and classes fixed) and
+ * grad_x phi moves with them through its x-Hessian H_s = sum_{l,k} (d phi/d z_{l,k}) Hess_x
+ * z_{l,k}: the off-diagonal entries h12, h13, h23 of the trilinear interpolation (Supp.
+ * Sec. 1), times 1/v_l^2, zero along clamped axes.  With a_s = dL/d(grad_x phi(x_s)), each
+ * sample's position gradient H_s a_s reaches the pose as in gs_pose_backward.  xi [F][6], the
+ * frames (their poses the refined ones the batch was sampled with) and the batch (pix, origin,
+ * dir, t, cls, counts) as for gs_pose_backward; dloss a device float [1] or NULL (1).  Either
+ * architecture.  Accumulates with atomics. */
+gs_status gs_eikonal_pose_backward(gs_ctx* ctx, const float* theta, const gs_frames* frames, const float* xi,
+                                   const gs_batch* batch, const float* dloss, float* pose_grad, void* stream);
+
 /* Cell lookup used by every gather: out [P][4] = flat base-vertex index of the cell holding
  * x (clamped to the grid box) at each level, decided in binary32. */
 gs_status gs_voxel_index(gs_ctx* ctx, const float* x, int32_t P, int64_t* out, void* stream);

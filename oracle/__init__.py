@@ -92,6 +92,8 @@ def _load(path: str):
     L.oc_query_sdf.restype = None
     L.oc_query_sdf.argtypes = [vp, vp, vp, i32, vp, vp]
     L.oc_query_sdf_backward.restype = None
+    L.oc_eikonal_pose_grad.restype = None
+    L.oc_eikonal_pose_grad.argtypes = [vp, vp, vp, vp, vp, i32, i32] + [vp] * 5 + [dbl, vp]
     L.oc_hidden_at.restype = None
     L.oc_hidden_at.argtypes = [vp, vp, vp, vp, i32, vp, vp, vp, vp, vp]
     L.oc_query_sdf_backward.argtypes = [vp, vp, vp, i32, vp, vp, vp]
@@ -304,6 +306,22 @@ def pose_grad(cfg: OcConfig, frames: OcFramesHolder, theta, c2w, xi, batch: dict
     (lib().oc_pose_grad_paper if cfg.arch == 1 else lib().oc_pose_grad)(ctypes.byref(cfg), ctypes.byref(frames.s), _p(th), _p(c2w), _p(xi), R, N,
                        _p(np.ascontiguousarray(batch["pix"], dtype=np.int64)), _p(batch["o"]), _p(batch["r"]),
                        _p(batch["t"]), _p(np.ascontiguousarray(dz, dtype=np.float64)), _p(g))
+    return g
+
+
+def eikonal_pose_grad(cfg: OcConfig, frames: OcFramesHolder, theta, c2w, xi, batch: dict, dscale: float = 1.0):
+    """dscale * dL_eik/dxi [F][6]: the Eikonal term's pose gradient through the free-space
+    samples' positions (x-Hessian of phi), for either architecture."""
+    th = np.ascontiguousarray(theta, dtype=np.float64)
+    c2w = np.ascontiguousarray(c2w, dtype=np.float64)
+    xi = np.ascontiguousarray(xi, dtype=np.float64)
+    F = len(c2w)
+    R, N = batch["t"].shape
+    g = np.zeros((F, 6))
+    lib().oc_eikonal_pose_grad(ctypes.byref(cfg), ctypes.byref(frames.s), _p(th), _p(c2w), _p(xi), R, N,
+                               _p(np.ascontiguousarray(batch["pix"], dtype=np.int64)), _p(batch["o"]),
+                               _p(batch["r"]), _p(batch["t"]), _p(np.ascontiguousarray(batch["cls"], np.uint8)),
+                               ctypes.c_double(dscale), _p(g))
     return g
 
 

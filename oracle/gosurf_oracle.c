@@ -280,6 +280,8 @@ typedef struct {
   double w[8];        /* w_c(f), Supp. Eq. (coefficient vector) */
   double dw[8][3];    /* d w_c / d f_a (zero on clamped axes), Supp. Eq. (coeff_jacobian) */
   double inv_v;       /* 1 / v_l  (d f / d x) */
+  double f[3];        /* in-cell coordinates */
+  int clamped[3];     /* axis a clamped to the grid box (no x-derivative along it) */
 } cell_t;
 
 /* Cell and in-cell coordinates of x at level l.  The cell and the clamp flags are decided
@@ -299,6 +301,8 @@ static void locate(const oc_config* c, int l, const float x[3], cell_t* cl, int3
     if (clamped[a]) f[a] = (double)u - (double)i;
     else f[a] = ((double)x[a] - (double)c->origin[a]) / (double)c->voxel[l] - (double)i;
     if (base_out) base_out[a] = i;
+    cl->f[a] = f[a];
+    cl->clamped[a] = clamped[a];
   }
   int nx = c->dims[l][0], ny = c->dims[l][1];
   int64_t off = level_offset(c, l);
@@ -2468,6 +2472,112 @@ void oc_pose_grad_paper(const oc_config* c, const oc_frames* fr, const double* t
     so3_exp_jr(xi + 6 * f + 3, E, J);
     const double* Q = c2w + 12 * f;
     for (int a = 0; a < 3; ++a) gr[a] += gd[a] / dn;
+    for (int a = 0; a < 3; ++a) Rt_gr[a] = Q[a] * gr[0] + Q[4 + a] * gr[1] + Q[8 + a] * gr[2];
+    skew(d, K);
+    for (int a = 0; a < 3; ++a) w[a] = K[a][0] * Rt_gr[0] + K[a][1] * Rt_gr[1] + K[a][2] * Rt_gr[2];
+    for (int a = 0; a < 3; ++a) g[6 * f + 3 + a] += J[0][a] * w[0] + J[1][a] * w[1] + J[2][a] * w[2];
+  }
+}
+
+/* ------------------------------------------------------------------------------------ */
+/* camera-pose gradient of the Eikonal term (Sec. 3.3 Eq. eikonal_loss; Sec. 3.4)         */
+/* ------------------------------------------------------------------------------------ */
+/* grad_x phi and its x-Hessian at x, for either architecture.  phi = f(z(x)) with f
+ * piecewise linear in z (ReLU decoders), so within a ReLU region grad_x phi = sum_l J_l^T p_l
+ * with p = d phi / d z constant and H = sum_{l,k} p_{l,k} Hess_x z_{l,k}: the Hessian of a
+ * trilinear interpolation has a zero diagonal and the off-diagonal entries h12, h13, h23 of
+ * Supp. Sec. 1 in cell coordinates (times 1 / v_l^2 in metres, reading R22), zero along a
+ * clamped axis (reading R15). */
+static void sdf_grad_hessian(const oc_config* c, const double* theta, const float x[3], double gx[3], double H[3][3]) {
+  cell_t cells[OC_LEVELS];
+  double z[OC_Z], dzdx[OC_Z][3], p[OC_Z];
+  if (c->arch == 1) {
+    int64_t ng = 0;
+    oc_paper_param_count(c, &ng);
+    pa_mlp_t m = pa_view(theta + ng);
+    pa_act_t A;
+    const double dnone[3] = {0, 0, 1};
+    pa_eval(c, theta, &m, x, dnone, cells, dzdx, &A);
+    double pm[PA_H], e[PA_H];
+    pa_dphi_dz(&m, &A, p, pm, e);
+    (void)z;
+  } else {
+    mlp_t m = mlp_view(theta + grid_size(c));
+    act_t A;
+    features(c, theta, x, cells, A.z, dzdx);
+    decode(&m, &A);
+    double mw2[OC_H1];
+    dphi_dz(&m, &A, p, mw2);
+  }
+  for (int a = 0; a < 3; ++a) {
+    gx[a] = 0.0;
+    for (int k = 0; k < OC_Z; ++k) gx[a] += p[k] * dzdx[k][a];
+    for (int b = 0; b < 3; ++b) H[a][b] = 0.0;
+  }
+  for (int l = 0; l < OC_LEVELS; ++l) {
+    const double iv2 = cells[l].inv_v * cells[l].inv_v;
+    for (int k = 0; k < OC_FEAT; ++k) {
+      double th8[8], h[3];
+      for (int cc = 0; cc < 8; ++cc) th8[cc] = theta[cells[l].corner[cc] + k];
+      oc_trilinear_hessian(th8, cells[l].f, h);
+      const int* cl = cells[l].clamped;
+      const double s = p[OC_FEAT * l + k] * iv2;
+      const double h01 = (cl[0] || cl[1]) ? 0.0 : h[0], h02 = (cl[0] || cl[2]) ? 0.0 : h[1],
+                   h12 = (cl[1] || cl[2]) ? 0.0 : h[2];
+      H[0][1] += s * h01;
+      H[1][0] += s * h01;
+      H[0][2] += s * h02;
+      H[2][0] += s * h02;
+      H[1][2] += s * h12;
+      H[2][1] += s * h12;
+    }
+  }
+}
+
+/* Pose gradient of dscale * L_eik, L_eik = mean over the batch's free-space samples of
+ * (1 - |g_s|)^2, g_s = grad_x phi(x_s).  The samples x_s = o + d_s r move with the pose (the
+ * depths d_s and the classes stay fixed, reading R36), g_s with them: d g_s / d x_s = H_s.
+ * With a_s = dL/d g_s = dscale (-2 (1 - |g_s|) g_s / (|g_s| |S_fs|)) (0 where g_s = 0), the
+ * sample's position gradient is H_s a_s (H_s symmetric), and it reaches the frame's pose as
+ * the per-ray terms' do (oc_pose_grad):
+ *   dL/d dt += sum_s H_s a_s,   dL/d nu += J_r(nu)^T [d]_x R^T sum_s d_s H_s a_s.
+ * Either architecture (c->arch).  g [F][6] (+=). */
+void oc_eikonal_pose_grad(const oc_config* c, const oc_frames* fr, const double* theta, const double* c2w,
+                          const double* xi, int R, int N, const int64_t* pix, const float* o, const float* r,
+                          const float* t, const uint8_t* cls, double dscale, double* g) {
+  int64_t n_fs = 0;
+  for (int64_t s = 0; s < (int64_t)R * N; ++s) n_fs += cls[s] == CLS_FS;
+  if (n_fs == 0) return;
+  const int64_t hw = (int64_t)fr->H * fr->W;
+  for (int i = 0; i < R; ++i) {
+    double go[3] = {0, 0, 0}, gr[3] = {0, 0, 0};
+    for (int k = 0; k < N; ++k) {
+      const int64_t s = (int64_t)i * N + k;
+      if (cls[s] != CLS_FS) continue;
+      float x[3];
+      for (int a = 0; a < 3; ++a) {
+        float st = t[s] * r[3 * i + a];
+        x[a] = o[3 * i + a] + st;
+      }
+      double gx[3], H[3][3];
+      sdf_grad_hessian(c, theta, x, gx, H);
+      const double nrm = sqrt(gx[0] * gx[0] + gx[1] * gx[1] + gx[2] * gx[2]);
+      if (!(nrm > 0.0)) continue;
+      const double kk = dscale * (-2.0 / (double)n_fs) * (1.0 - nrm) / nrm;
+      for (int a = 0; a < 3; ++a) {
+        double v = 0.0;
+        for (int b = 0; b < 3; ++b) v += H[a][b] * kk * gx[b];
+        go[a] += v;
+        gr[a] += (double)t[s] * v;
+      }
+    }
+    const int64_t f = pix[i] / hw, rem = pix[i] % hw;
+    const int v = (int)(rem / fr->W), u = (int)(rem % fr->W);
+    const double d[3] = {(((double)u + 0.5) - fr->cx) / fr->fx, (((double)v + 0.5) - fr->cy) / fr->fy, 1.0};
+    for (int a = 0; a < 3; ++a) g[6 * f + a] += go[a];
+    double E[3][3], J[3][3], Rt_gr[3], K[3][3], w[3];
+    so3_exp_jr(xi + 6 * f + 3, E, J);
+    const double* Q = c2w + 12 * f;
     for (int a = 0; a < 3; ++a) Rt_gr[a] = Q[a] * gr[0] + Q[4 + a] * gr[1] + Q[8 + a] * gr[2];
     skew(d, K);
     for (int a = 0; a < 3; ++a) w[a] = K[a][0] * Rt_gr[0] + K[a][1] * Rt_gr[1] + K[a][2] * Rt_gr[2];

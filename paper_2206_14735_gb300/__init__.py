@@ -219,6 +219,13 @@ class Context:
         self._check(self.L.gs_pose_backward(self.h, _ptr(theta), ctypes.byref(frames.s), _ptr(xi), ctypes.byref(b),
                                             _ptr(pose_grad), _stream()))
 
+    def eikonal_pose_backward(self, theta, frames: DeviceFrames, xi, batch: Batch, pose_grad, dloss=None):
+        """pose_grad [F][6] += dloss * dL_eik/dxi: the Eikonal term's pose gradient through the
+        free-space samples' positions (dloss: device float [1] or None for 1)."""
+        b = batch.struct()
+        self._check(self.L.gs_eikonal_pose_backward(self.h, _ptr(theta), ctypes.byref(frames.s), _ptr(xi),
+                                                    ctypes.byref(b), _ptr(dloss), _ptr(pose_grad), _stream()))
+
     def extract_mesh(self, theta, lo, step: float, dims, iso: float = 0.0, max_tris: int | None = None,
                      phi=None):
         """Isosurface phi = iso on the lattice lo + (i, j, k) * step, dims = (nx, ny, nz):

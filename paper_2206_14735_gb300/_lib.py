@@ -20,7 +20,7 @@ STATUS = {0: "GS_OK", 1: "GS_ERR_INVALID_ARG", 2: "GS_ERR_SHAPE", 3: "GS_ERR_ALI
           5: "GS_ERR_DEVICE", 6: "GS_ERR_UNSUPPORTED"}
 
 EXPORTS = ["gs_create", "gs_destroy", "gs_param_count", "gs_sample_rays", "gs_forward", "gs_backward",
-           "gs_forward_backward", "gs_adam_step", "gs_query_sdf", "gs_query_sdf_backward", "gs_eikonal", "gs_sample_importance", "gs_extract_mesh", "gs_pose_apply", "gs_pose_backward", "gs_proposal_sample", "gs_proposal_backward", "gs_voxel_index", "gs_sync_status",
+           "gs_forward_backward", "gs_adam_step", "gs_query_sdf", "gs_query_sdf_backward", "gs_eikonal", "gs_sample_importance", "gs_extract_mesh", "gs_pose_apply", "gs_pose_backward", "gs_eikonal_pose_backward", "gs_proposal_sample", "gs_proposal_backward", "gs_voxel_index", "gs_sync_status",
            "gs_last_error", "gs_forward_backward_noalloc"]
 
 
@@ -92,6 +92,8 @@ def lib():
             L.gs_pose_apply.argtypes = [vp, vp, vp, i32, vp, vp]
             L.gs_pose_backward.restype = i32
             L.gs_pose_backward.argtypes = [vp, vp, vp, vp, vp, vp, vp]
+            L.gs_eikonal_pose_backward.restype = i32
+            L.gs_eikonal_pose_backward.argtypes = [vp, vp, vp, vp, vp, vp, vp, vp]
             L.gs_extract_mesh.restype = i32
             L.gs_extract_mesh.argtypes = [vp, vp, vp, ctypes.c_float, i32, i32, i32, ctypes.c_float, vp, vp,
                                           ctypes.c_int64, vp, vp]

@@ -449,6 +449,22 @@ gs_status gs_pose_backward(gs_ctx* ctx, const float* theta, const gs_frames* fra
   return GS_OK;
 }
 
+gs_status gs_eikonal_pose_backward(gs_ctx* ctx, const float* theta, const gs_frames* frames, const float* xi,
+                                   const gs_batch* batch, const float* dloss, float* pose_grad, void* stream) {
+  if (!ctx) return fail(nullptr, GS_ERR_INVALID_ARG, "gs_eikonal_pose_backward: ctx is NULL");
+  gs_status s = check_frames(ctx, frames, "gs_eikonal_pose_backward");
+  if (s != GS_OK) return s;
+  s = check_batch(ctx, batch, true);
+  if (s != GS_OK) return s;
+  if (!theta || !xi || !pose_grad) return fail(ctx, GS_ERR_INVALID_ARG, "gs_eikonal_pose_backward: NULL array");
+  if (!aligned16(theta)) return fail(ctx, GS_ERR_ALIGN, "gs_eikonal_pose_backward: theta is not 16-byte aligned");
+  cudaStream_t st = (cudaStream_t)stream;
+  ctx->last_stream = st;
+  if (gs_launch_eikonal_pose_backward(ctx, theta, frames, xi, batch, dloss, pose_grad, st) != GS_OK)
+    return cuda_fail(ctx, "gs_eikonal_pose_backward");
+  return GS_OK;
+}
+
 gs_status gs_extract_mesh(gs_ctx* ctx, const float* theta, const float* lo, float step, int32_t nx, int32_t ny,
                           int32_t nz, float iso, float* phi, float* tris, int64_t max_tris, int64_t* n_tris,
                           void* stream) {

@@ -74,6 +74,8 @@ gs_status gs_launch_mesh(const gs_ctx* ctx, const float* theta, const float lo[3
 gs_status gs_launch_pose_apply(const float* c2w0, const float* xi, int F, float* c2w, cudaStream_t st);
 gs_status gs_launch_pose_backward(const gs_ctx* ctx, const float* theta, const gs_frames* f, const float* xi,
                                   const gs_batch* b, float* pose_grad, cudaStream_t st);
+gs_status gs_launch_eikonal_pose_backward(const gs_ctx* ctx, const float* theta, const gs_frames* f, const float* xi,
+                                          const gs_batch* b, const float* dloss, float* pose_grad, cudaStream_t st);
 gs_status gs_launch_eikonal(const gs_ctx* ctx, const float* theta, const gs_batch* b, const float* dloss, float* loss,
                             float* grad, cudaStream_t st);
 gs_status gs_launch_query_backward(const gs_ctx* ctx, const float* theta, const float* x, int P, const float* dsdf,

@@ -433,6 +433,31 @@ def test_paper_pose_records_and_gradient_match_oracle():
     assert np.abs(g - g_ref).max() <= 1e-4 * np.abs(g_ref).max(), (g, g_ref)
 
 
+def test_paper_eikonal_pose_gradient_matches_oracle():
+    """The Eikonal term's pose gradient with the paper's two-hidden-layer geometry decoder,
+    against the oracle's (rays with a free-space sample at a ReLU kink left out)."""
+    w = CUBE_P.with_(name="cube-paper-3frames", frames=3)
+    p = Problem(w)
+    rng = np.random.default_rng(5)
+    xi = np.c_[rng.normal(0, 0.01, (3, 3)), rng.normal(0, 0.01, (3, 3))]
+    c2w = oc.pose_apply(p.frames.c2w, xi)
+    F = oc.OcFramesHolder(p.frames, c2w=c2w)
+    theta = paper_parity_params(w, sg.cube_scene(), seed=23)
+    bt = oc.sample_rays(p.cfg, F, 9, 2, w.rays)
+    bt, dropped = drop_kink_rays(p, theta, bt)
+    assert dropped <= 0.05 * w.rays and int(bt["counts"][2]) > 1000
+    g_ref = oc.eikonal_pose_grad(p.cfg, F, theta, c2w, xi, bt)
+    batch = upload_oracle_batch(bt, None, 0)
+    dfr = p.dfr.with_poses(torch.from_numpy(c2w.astype(np.float32)).cuda())
+    pg = torch.zeros(3, 6, device="cuda")
+    p.ctx.eikonal_pose_backward(_padded(theta), dfr, torch.from_numpy(xi.astype(np.float32)).cuda(), batch, pg)
+    torch.cuda.synchronize()
+    p.ctx.sync_status()
+    g = pg.cpu().numpy().astype(np.float64)
+    assert np.abs(g_ref).max() > 1e-4
+    assert np.abs(g - g_ref).max() <= 1e-4 * np.abs(g_ref).max(), (g, g_ref)
+
+
 @pytest.mark.parametrize("n_strat,n_guided", [(48, 16), (100, 32)])
 def test_paper_stored_activations(n_strat, n_guided):
     """Store mode of the paper's architecture: the forward pass keeps every sample's decoder

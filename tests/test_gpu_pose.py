@@ -61,6 +61,32 @@ def test_dz_export_and_pose_gradient_match_oracle(posed):
     assert np.abs(g - g_ref).max() <= 1e-4 * np.abs(g_ref).max(), (g, g_ref)
 
 
+def test_eikonal_pose_gradient_matches_oracle(posed):
+    """The Eikonal term's pose gradient (x-Hessian of phi through the free-space samples'
+    positions) against the oracle's, on hidden units that switch from sample to sample; rays
+    holding a free-space sample within binary32 rounding of a ReLU kink are left out (the
+    term jumps there)."""
+    from gpu_common import drop_kink_rays
+    p, xi, c2w, F, theta = posed
+    bt = oc.sample_rays(p.cfg, F, 9, 2, W3.rays)
+    bt, dropped = drop_kink_rays(p, theta, bt)
+    assert dropped <= 0.05 * W3.rays
+    assert int(bt["counts"][2]) > 1000
+    for dscale in (1.0, -0.75):
+        g_ref = oc.eikonal_pose_grad(p.cfg, F, theta, c2w, xi, bt, dscale)
+        batch = upload_oracle_batch(bt, None, 0)
+        dfr = p.dfr.with_poses(torch.from_numpy(c2w.astype(np.float32)).cuda())
+        pg = torch.zeros(3, 6, device="cuda")
+        dl = None if dscale == 1.0 else torch.tensor([dscale], dtype=torch.float32, device="cuda")
+        p.ctx.eikonal_pose_backward(torch.from_numpy(theta).cuda(), dfr, torch.from_numpy(xi.astype(np.float32)).cuda(),
+                                    batch, pg, dloss=dl)
+        torch.cuda.synchronize()
+        p.ctx.sync_status()
+        g = pg.cpu().numpy().astype(np.float64)
+        assert np.abs(g_ref).max() > 1e-4
+        assert np.abs(g - g_ref).max() <= 1e-4 * np.abs(g_ref).max(), (g, g_ref)
+
+
 def test_pose_backward_empty_batch(posed):
     p, xi, c2w, F, theta = posed
     b = gs.Batch.allocate(0, W3.n_samples, 0, dz=True)
