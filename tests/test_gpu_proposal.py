@@ -233,3 +233,87 @@ def test_trained_proposal_beats_the_plain_sampler_where_depth_is_missing():
           f"({res['proposal'][1]} rays); about {res['proposal_steps']} steps on the proposal; CE {res['ce']:.3f}")
     assert res["plain"][1] > 200 and res["proposal"][1] > 200
     assert res["proposal"][0] < 0.8 * res["plain"][0], res
+
+
+# ---- the BF16 form: the network's layers on the tensor core (bfloat16 operands) ----------
+CUBE_PB = CUBE_P.with_(name="cube-prop-bf16", precision="bf16")
+
+
+def _bf16(a):
+    return torch.from_numpy(np.ascontiguousarray(a, np.float32)).to(torch.bfloat16).float().numpy()
+
+
+def _q_bf16(q):
+    """The proposal parameters with the matrices the tensor core reads (W1, W2) rounded to
+    bfloat16, as the oracle's reference for the BF16 form (reading R44)."""
+    qq = q.copy()
+    qq[0:352] = _bf16(qq[0:352])
+    qq[384:1408] = _bf16(qq[384:1408])
+    return qq
+
+
+@pytest.fixture(scope="module")
+def prob_bf16(prob):
+    p = Problem(CUBE_PB, max_rays=4096)
+    return dict(p=p, theta=prob["theta"], q=_q_bf16(prob["q"]))
+
+
+def test_bf16_network_pdf_and_draws(prob_bf16):
+    """PDF of the tensor-core network against the oracle's on the bfloat16-rounded weights:
+    what remains is the bfloat16 rounding of the inputs and of the first hidden layer (about
+    2^-9 relative each, through the logits into the softmax); measured 7.5e-3 of a bin's
+    probability at most (p > 1e-3) and 2.7e-4 absolute, bounded at 1.5e-2 of each bin's
+    probability plus 3e-4; the draws from the kernel's own PDF are the oracle's to the bit."""
+    pr = prob_bf16
+    p = pr["p"]
+    R = 2000
+    bt, _ = p.oracle_sample(SEED, STEP, R, 0)
+    b, pdf = _gpu_prop_sample(pr, R, 0)
+    ref = oc.prop_forward(p.cfg, pr["theta"], pr["q"], bt["o"], bt["r"])
+    err = np.abs(pdf - ref)
+    print(f"\nBF16 proposal PDF vs oracle: max abs {err.max():.2e}, max rel (p > 1e-3) "
+          f"{(err / np.maximum(ref, 1e-3)).max():.2e}, mean abs {err.mean():.2e}")
+    assert np.all(err <= 1.5e-2 * ref + 3e-4)
+    np.testing.assert_allclose(pdf.sum(1), 1.0, atol=2e-6)
+    ref_s = oc.prop_sample(p.cfg, bt["D"], pdf, CUBE_PB.prop_samples, CUBE_PB.prop_guided, SEED, STEP)
+    assert np.array_equal(_bits(b.t.cpu().numpy()), _bits(ref_s["t"]))
+    assert np.array_equal(b.cls.cpu().numpy(), ref_s["cls"])
+
+
+def test_bf16_cross_entropy_gradient(prob_bf16):
+    """Cross-entropy gradient of the tensor-core network against the oracle's on the
+    bfloat16-rounded weights, per parameter block.  The bfloat16 rounding of the inputs, the
+    first hidden layer and the second layer's adjoint (2^-9 relative each) gave max-norm
+    errors of 1.2e-2 (W1), 1.7e-2 (b1: a sum of adjoints that cancel), 6e-3 (W2, b2) and
+    7e-4 (w3, whose adjoint is the FP32 softmax residual); the bounds are about twice those.
+    The cross entropy itself came within 7e-6 relative (bound 3e-5: a mean over all bins
+    whose rounding errors partly cancel, so more headroom)."""
+    pr = prob_bf16
+    p = pr["p"]
+    R = 3000
+    bt, _ = p.oracle_sample(SEED, STEP, R, 0)
+    pdf = oc.prop_forward(p.cfg, pr["theta"], pr["q"], bt["o"], bt["r"]).astype(np.float32)
+    b, _ = _gpu_prop_sample(pr, R, 0, pdf_in=pdf, with_net=False)
+    ref_s = oc.prop_sample(p.cfg, bt["D"], pdf, CUBE_PB.prop_samples, CUBE_PB.prop_guided, SEED, STEP)
+    rng = np.random.default_rng(9)
+    w = rng.dirichlet(np.full(CUBE_PB.prop_samples, 0.2), R) * rng.uniform(0.2, 1.0, (R, 1))
+    w[::17] *= 1e-4
+    w = w.astype(np.float32)
+    b.w.copy_(torch.from_numpy(w))
+    grad = torch.zeros(oc.PROP_PARAMS, device="cuda")
+    ce = torch.zeros(2, device="cuda")
+    p.ctx.proposal_backward(torch.from_numpy(pr["theta"]).cuda(), torch.from_numpy(pr["q"]).cuda(), b, grad, ce)
+    torch.cuda.synchronize()
+    p.ctx.sync_status()
+    loss, g_ref, n_used = oc.prop_ce(p.cfg, pr["theta"], pr["q"], bt["o"], bt["r"], ref_s["t"], w)
+    ce_h = ce.cpu().numpy()
+    assert int(ce_h[1]) == n_used
+    g = grad.cpu().numpy().astype(np.float64)
+    errs = {}
+    for name, a, e in [("W1", 0, 352), ("b1", 352, 384), ("W2", 384, 1408), ("b2", 1408, 1440), ("w3", 1440, 1472)]:
+        errs[name] = float(np.abs(g[a:e] - g_ref[a:e]).max() / np.abs(g_ref[a:e]).max())
+    print(f"\nBF16 proposal CE {ce_h[0]:.6f} vs {loss:.6f} (rel {abs(ce_h[0] - loss) / loss:.2e}); "
+          f"gradient max-norm errors {errs}")
+    assert abs(ce_h[0] - loss) <= 3e-5 * abs(loss)
+    for name, bound in (("W1", 2.5e-2), ("b1", 3.5e-2), ("W2", 1.2e-2), ("b2", 1.2e-2), ("w3", 1.5e-3)):
+        assert errs[name] <= bound, (name, errs)
