@@ -141,8 +141,9 @@ def step_config(w, args, world, n_frames):
                         if w.imp_coarse > 0 else f"stratified {w.n_strat} + depth-guided {w.n_guided}"),
             "pipeline": ("the next step's batch sampled on a side stream during this step (double-buffered)"
                          if pipelined else "in line"),
-            "calls": ("gs_forward + gs_backward" if args.split else "gs_forward_backward") +
-                     (" + gs_eikonal" if args.eikonal else ""),
+            "calls": ("gs_eikonal (grid part deferred to the render call) + " if args.eikonal and not paper else "") +
+                     ("gs_forward + gs_backward" if args.split else "gs_forward_backward") +
+                     (" + gs_eikonal" if args.eikonal and paper else ""),
             "loss_terms": "rgb, depth, sdf, fs, smooth" + (", eikonal (lam 1, free-space samples)"
                                                            if args.eikonal else ""),
             "poses": ("refined: per-frame (dt, nu), gs_pose_apply + gs_pose_backward" +
@@ -182,7 +183,11 @@ def run_ours(args):
     n_grid_ = w.layout()[1]
     # BF16 form: the grid copy the gathers read, refreshed by every Adam step
     mirror = theta[:n_grid_].to(torch.bfloat16).view(torch.int16).contiguous() if ctx.bf16 else None
-    batch = gs.Batch.allocate(w.rays, w.n_samples, w.n_smooth, dz=args.poses, dz_width=32 if paper else 16)
+    # the compact decoder's Eikonal term leaves its grid part to the render kernel's scatter
+    # (deferred records in the batch); the paper's architecture scatters it in its own kernel
+    defer_eik = args.eikonal and not paper
+    batch = gs.Batch.allocate(w.rays, w.n_samples, w.n_smooth, dz=args.poses, dz_width=32 if paper else 16,
+                              eik=defer_eik)
     loss = torch.empty(6, device="cuda")
     eik = torch.zeros(1, device="cuda")  # L_eik when --eikonal (Sec. 3.3, lam_eik = 1)
     stream = torch.cuda.current_stream()
@@ -219,7 +224,7 @@ def run_ours(args):
     if pipelined:
         ctx_s = gs.Context(w)
         side = torch.cuda.Stream()
-        batches = [batch, gs.Batch.allocate(w.rays, w.n_samples, w.n_smooth)]
+        batches = [batch, gs.Batch.allocate(w.rays, w.n_samples, w.n_smooth, eik=defer_eik)]
         ev_ready = [torch.cuda.Event(), torch.cuda.Event()]  # batch j sampled
         ev_free = [torch.cuda.Event(), torch.cuda.Event()]   # batch j no longer read
         sample_ev = {}
@@ -250,6 +255,10 @@ def run_ours(args):
             sample(k, b)
         if ev is not None:
             ev[1].record(stream)
+        if defer_eik:  # before the render call, which adds the Eikonal term's grid part
+            ctx.eikonal(theta, b, loss=eik, grad=grad)
+        if ev is not None:
+            ev[5].record(stream)
         if args.split:
             ctx.forward(theta, b, loss, theta_bf16=mirror)
             ctx.backward(theta, b, dl, grad, theta_bf16=mirror)
@@ -257,7 +266,7 @@ def run_ours(args):
             ctx.forward_backward(theta, b, dl, loss, grad, theta_bf16=mirror)
         if ev is not None:
             ev[2].record(stream)
-        if args.eikonal:
+        if args.eikonal and not defer_eik:
             ctx.eikonal(theta, b, loss=eik, grad=grad)
         if args.poses:
             ctx.pose_backward(theta, dfr_pose, xi[:6 * n_fr].view(n_fr, 6), b, xi_g[:6 * n_fr].view(n_fr, 6))
@@ -285,7 +294,7 @@ def run_ours(args):
     ctx.sync_status()
 
     # ---- device-timed region: K full steps, inputs resident in HBM ----
-    evs = [[torch.cuda.Event(enable_timing=True) for _ in range(5)] for _ in range(args.steps)]
+    evs = [[torch.cuda.Event(enable_timing=True) for _ in range(6)] for _ in range(args.steps)]
     start, stop = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     if world > 1:
         torch.distributed.barrier()
@@ -301,16 +310,21 @@ def run_ours(args):
     clk = clocks.stop()
     ms = start.elapsed_time(stop)
     per = {"sample": [], "render": [], "adam": []}
-    extra = "eikonal" if args.eikonal else ("poses" if args.poses else None)
+    # after the render call: the Eikonal call (paper architecture) and / or the pose calls
+    extra = ("eikonal" if args.eikonal and not defer_eik else ("poses" if args.poses else None))
     if extra:
         per[extra] = []
+    if defer_eik:
+        per["eikonal"] = []  # the Eikonal call before the render call
     for k, e in enumerate(evs):
         if pipelined:  # the sampler's own time on the side stream (overlapped with the step before)
             se = sample_ev[args.warmup + k]
             per["sample"].append(se[0].elapsed_time(se[1]))
         else:
             per["sample"].append(e[0].elapsed_time(e[1]))
-        per["render"].append(e[1].elapsed_time(e[2]))
+        per["render"].append(e[5].elapsed_time(e[2]))
+        if defer_eik:
+            per["eikonal"].append(e[1].elapsed_time(e[5]))
         if extra:
             per[extra].append(e[2].elapsed_time(e[3]))
         per["adam"].append(e[3].elapsed_time(e[4]))

@@ -156,6 +156,12 @@ typedef struct gs_batch {
                       feature), written by the backward passes when not NULL; read by
                       gs_pose_backward.  GS_ARCH_PAPER: [R][N][32] per sample, dL/dz (16),
                       dL/dW_beta(x) (6), dL/d(viewing direction) (3), zeros (7) */
+  float* eik;      /* NULL, or [5][R][N][4] (16-byte aligned) deferred Eikonal records, written
+                      by gs_eikonal for the free-space samples and read by the next backward
+                      pass over this batch (see gs_eikonal); plane k of sample s = r N + i at
+                      ((float4*)eik)[k R N + s]: planes 0..3 p_l / v_l (level l's part of
+                      d phi / d z over its voxel size), plane 4 (a, 0) with a the Eikonal
+                      adjoint dL/d(grad_x phi).  GS_ARCH_COMPACT only (NULL otherwise). */
 } gs_batch;
 
 typedef struct gs_ctx gs_ctx;
@@ -197,7 +203,9 @@ gs_status gs_forward(gs_ctx* ctx, const float* theta, const uint16_t* theta_bf16
  * GS_ERR_INVALID_ARG is returned when no forward pass of a batch with this R, N and t
  * pointer came first.  Otherwise everything is recomputed from theta.  Grid
  * gradients are accumulated with FP32 atomics (summation order not deterministic); decoder
- * gradients are reduced in a fixed order. */
+ * gradients are reduced in a fixed order.  With batch->eik set, the grid gradient also
+ * receives the deferred Eikonal term of every free-space sample (records written by
+ * gs_eikonal on this batch before this call; see there). */
 gs_status gs_backward(gs_ctx* ctx, const float* theta, const uint16_t* theta_bf16, const gs_batch* batch,
                       const float* dloss, float* grad, void* stream);
 
@@ -283,7 +291,13 @@ gs_status gs_query_sdf_backward(gs_ctx* ctx, const float* theta, const float* x,
  * (NULL = 1): the second-order path of Supp. Sec. 1 (grid features through d z/d x, W1 and
  * row 0 of W2 through d phi/d z; the sub-gradient at grad_x phi = 0 is 0), accumulated with
  * atomics (order not fixed).  Reads the FP32 grid in every precision form.  Needs only the
- * batch's ray arrays (origin, dir, t, cls, counts). */
+ * batch's ray arrays (origin, dir, t, cls, counts).
+ * Deferred grid term (GS_ARCH_COMPACT, grad != NULL, batch->eik != NULL): the grid part of the
+ * gradient is not scattered here; every free-space sample's record (p_l / v_l, a) goes to
+ * batch->eik instead, and the next gs_backward / gs_forward_backward over the same batch adds
+ * p_l (1/v_l) (a . dw_c/df) to the corner vectors it scatters anyway (no reductions of its
+ * own).  grad then holds the full gradient only after that backward pass; the decoder part
+ * and the loss are written by this call as without records. */
 gs_status gs_eikonal(gs_ctx* ctx, const float* theta, const gs_batch* batch, const float* dloss, float* loss,
                      float* grad, void* stream);
 

@@ -97,9 +97,12 @@ class Batch:
     w: torch.Tensor | None = None  # [R][N] rendering weights (written by forward passes when present)
     dz: torch.Tensor | None = None  # [R][N][16] dL/dz (written by backward passes when present;
     #                                 [R][N][32] records for the paper's architecture)
+    eik: torch.Tensor | None = None  # [5][R][N][4] deferred Eikonal records (written by eikonal(), read by
+    #                                  the next backward pass over this batch)
 
     @staticmethod
-    def allocate(R: int, N: int, P: int, device="cuda", weights=False, dz=False, dz_width=16) -> "Batch":
+    def allocate(R: int, N: int, P: int, device="cuda", weights=False, dz=False, dz_width=16,
+                 eik=False) -> "Batch":
         f = dict(device=device, dtype=torch.float32)
         return Batch(R=R, N=N, P=P, pix=torch.empty(R, device=device, dtype=torch.int64),
                      origin=torch.empty(R, 3, **f), dir=torch.empty(R, 3, **f), rgb=torch.empty(R, 3, **f),
@@ -108,13 +111,15 @@ class Batch:
                      eps=torch.empty(max(P, 1), 3, **f), valid=torch.empty(max(P, 1), device=device, dtype=torch.uint8),
                      counts=torch.zeros(4, device=device, dtype=torch.int32),
                      w=torch.zeros(R, N, **f) if weights else None,
-                     dz=torch.zeros(R, N, dz_width, **f) if dz else None)
+                     dz=torch.zeros(R, N, dz_width, **f) if dz else None,
+                     eik=torch.zeros(5, R, N, 4, **f) if eik else None)
 
     def struct(self) -> GsBatch:
         return GsBatch(self.R, self.N, self.P, self.pix.data_ptr(), self.origin.data_ptr(), self.dir.data_ptr(),
                        self.rgb.data_ptr(), self.depth.data_ptr(), self.t.data_ptr(), self.cls.data_ptr(),
                        self.xs.data_ptr(), self.eps.data_ptr(), self.valid.data_ptr(), self.counts.data_ptr(),
-                       None if self.w is None else self.w.data_ptr(), None if self.dz is None else self.dz.data_ptr())
+                       None if self.w is None else self.w.data_ptr(), None if self.dz is None else self.dz.data_ptr(),
+                       None if self.eik is None else self.eik.data_ptr())
 
 
 class Context:

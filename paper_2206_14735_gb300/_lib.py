@@ -46,7 +46,8 @@ class GsBatch(ctypes.Structure):
                 ("origin", ctypes.c_void_p), ("dir", ctypes.c_void_p), ("rgb", ctypes.c_void_p),
                 ("depth", ctypes.c_void_p), ("t", ctypes.c_void_p), ("cls", ctypes.c_void_p),
                 ("xs", ctypes.c_void_p), ("eps", ctypes.c_void_p), ("valid", ctypes.c_void_p),
-                ("counts", ctypes.c_void_p), ("w", ctypes.c_void_p), ("dz", ctypes.c_void_p)]
+                ("counts", ctypes.c_void_p), ("w", ctypes.c_void_p), ("dz", ctypes.c_void_p),
+                ("eik", ctypes.c_void_p)]
 
 
 def library_path() -> str:

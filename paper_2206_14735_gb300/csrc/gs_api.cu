@@ -49,6 +49,9 @@ gs_status check_batch(gs_ctx* ctx, const gs_batch* b, bool need_smooth_arrays) {
     return fail(ctx, GS_ERR_INVALID_ARG, "batch ray array is NULL");
   if (b->R > 0 && need_smooth_arrays && !b->pix) return fail(ctx, GS_ERR_INVALID_ARG, "batch pix is NULL");
   if (b->P > 0 && (!b->xs || !b->eps || !b->valid)) return fail(ctx, GS_ERR_INVALID_ARG, "batch smoothness array is NULL");
+  if (b->eik && ctx->cfg.arch == GS_ARCH_PAPER)
+    return fail(ctx, GS_ERR_UNSUPPORTED, "batch eik (deferred Eikonal records) is GS_ARCH_COMPACT only");
+  if (b->eik && (reinterpret_cast<uintptr_t>(b->eik) & 15u)) return fail(ctx, GS_ERR_ALIGN, "batch eik is not 16-byte aligned");
   return GS_OK;
 }
 
@@ -156,6 +159,7 @@ gs_status gs_create(const gs_config* cfg, gs_ctx** out) {
       cudaMalloc(&c->eik_part, sizeof(float) * kEikCtasPerSm * c->num_sms) != cudaSuccess ||
       cudaMalloc(&c->eik_ticket, sizeof(unsigned)) != cudaSuccess ||
       cudaMemset(c->eik_ticket, 0, sizeof(unsigned)) != cudaSuccess ||
+      cudaMalloc(&c->eik_count, sizeof(int) * (4 + (size_t)cfg->max_rays * c->max_n)) != cudaSuccess ||
       cudaStreamCreateWithFlags(&c->side, cudaStreamNonBlocking) != cudaSuccess ||
       cudaEventCreateWithFlags(&c->ev_fork, cudaEventDisableTiming) != cudaSuccess ||
       cudaEventCreateWithFlags(&c->ev_join, cudaEventDisableTiming) != cudaSuccess ||
@@ -175,6 +179,7 @@ gs_status gs_create(const gs_config* cfg, gs_ctx** out) {
     gs_destroy(c);
     return s;
   }
+  c->eik_list = c->eik_count + 4;  // 16-byte aligned, after the count
   *out = c;
   return GS_OK;
 }
@@ -189,6 +194,7 @@ void gs_destroy(gs_ctx* ctx) {
   cudaFree(ctx->prop_part);
   cudaFree(ctx->eik_part);
   cudaFree(ctx->eik_ticket);
+  cudaFree(ctx->eik_count);
   cudaFree(ctx->paper_part);
   cudaFree(ctx->paper_loss_part);
   if (ctx->ev_fork) cudaEventDestroy(ctx->ev_fork);
@@ -412,6 +418,8 @@ gs_status gs_eikonal(gs_ctx* ctx, const float* theta, const gs_batch* batch, con
     return fail(ctx, GS_ERR_ALIGN, "gs_eikonal: theta or grad is not 16-byte aligned");
   gs_status s = check_batch(ctx, batch, false);
   if (s != GS_OK) return s;
+  if ((long long)batch->R * batch->N > 0x7fffffffLL)
+    return fail(ctx, GS_ERR_SHAPE, "gs_eikonal: R * N must stay below 2^31 (32-bit sample indices)");
   cudaStream_t st = (cudaStream_t)stream;
   ctx->last_stream = st;
   const float* dl = dloss ? dloss : ctx->default_dloss + 5;  // 1.0

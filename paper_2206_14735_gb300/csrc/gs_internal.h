@@ -35,6 +35,8 @@ struct gs_ctx {
   int eik_ctas = 0;                  // largest grid of the Eikonal kernel
   float* eik_part = nullptr;         // its per-CTA loss sums
   unsigned* eik_ticket = nullptr;    // CTAs finished in the running call (0 between calls)
+  int* eik_count = nullptr;          // free-space samples listed by the Eikonal call's compaction pass
+  int* eik_list = nullptr;           // their sample indices [max_rays * max_n] (order kept within 1024)
   long long colour_off = 0;          // paper architecture: float offset of the colour grid
   float* paper_part = nullptr;       // paper architecture: per-CTA decoder-gradient partial rows
   float* paper_loss_part = nullptr;  // and loss partial rows

@@ -65,6 +65,8 @@ extern "C" gs_status gs_forward_backward_noalloc(const gs_config* cfg, const flo
     return noalloc_fail(GS_ERR_INVALID_ARG, "gs_forward_backward_noalloc: batch ray array is NULL");
   if (batch->P > 0 && (!batch->xs || !batch->eps || !batch->valid))
     return noalloc_fail(GS_ERR_INVALID_ARG, "gs_forward_backward_noalloc: batch smoothness array is NULL");
+  if (batch->eik && (reinterpret_cast<uintptr_t>(batch->eik) & 15u))
+    return noalloc_fail(GS_ERR_ALIGN, "gs_forward_backward_noalloc: batch eik is not 16-byte aligned");
   int dev = 0, sms = 0;
   if (cudaGetDevice(&dev) != cudaSuccess ||
       cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)

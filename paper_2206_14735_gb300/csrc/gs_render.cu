@@ -222,6 +222,8 @@ gs_status gs_launch_render(const gs_ctx* ctx, const float* theta, const uint16_t
   a.store = ctx->store;
   a.w_out = b->w;
   a.dz_out = b->dz;
+  a.eik = reinterpret_cast<const float4*>(b->eik);
+  a.eik_stride = (long long)b->R * b->N;
   a.store_stride = (long long)ctx->cfg.max_rays * ctx->max_n;
   const int nch = (b->N + 31) / 32;
   if (ctx->cfg.precision == GS_PREC_BF16) {

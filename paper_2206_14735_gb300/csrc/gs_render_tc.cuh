@@ -409,11 +409,23 @@ __device__ __forceinline__ void red_add_f4(float4* p, float4 v) {
 // reduction (8 per run).  At the fine levels, where runs are short, every lane issues its 8
 // corners' 16-byte reductions directly (staging them there measured slower).
 // `st`: this warp's kScatterStage floats of staging space.
+// Deferred Eikonal term: `er` (nullptr for samples without one) points at the sample's record
+// in plane 0 of the batch's Eikonal records (planes `es` float4 apart: q_l = p_l / v_l for the
+// four levels, then the adjoint a); corner c of level l then also receives q_l (a . dw_c/df),
+// the grid part of the Eikonal gradient (Supp. Sec. 1), in the same 16-byte reduction.
 __device__ __forceinline__ void scatter_dz(const GridDesc& g, float* grad, const float x[3], const float dz[kZ],
-                                           bool valid, float* st) {
+                                           bool valid, float* st, const float4* er = nullptr, long long es = 0) {
   const unsigned active = __ballot_sync(0xffffffffu, valid);
   if (active == 0) return;
   const int lane = threadIdx.x & 31;
+  const bool eik_any = __any_sync(0xffffffffu, er != nullptr);
+  float ea[3] = {0.f, 0.f, 0.f};
+  if (er != nullptr) {
+    const float4 a4 = __ldg(er + 4 * es);
+    ea[0] = a4.x;
+    ea[1] = a4.y;
+    ea[2] = a4.z;
+  }
 #pragma unroll
   for (int l = 0; l < kLevels; ++l) {
     const Cell cc = locate(g, l, x);
@@ -421,11 +433,26 @@ __device__ __forceinline__ void scatter_dz(const GridDesc& g, float* grad, const
     corner_weights(cc.f, wc);
     const float4 g4 = valid ? make_float4(dz[4 * l], dz[4 * l + 1], dz[4 * l + 2], dz[4 * l + 3])
                             : make_float4(0.f, 0.f, 0.f, 0.f);
+    float4 q4 = make_float4(0.f, 0.f, 0.f, 0.f);
+    float dd[8];  // a . dw_c/df (zero without a record)
+#pragma unroll
+    for (int k = 0; k < 8; ++k) dd[k] = 0.f;
+    if (eik_any) {  // warp-uniform
+      if (er != nullptr) q4 = __ldg(er + l * es);
+      float dw[8][3];
+      corner_weight_grads(cc.f, cc.clamped, dw);
+#pragma unroll
+      for (int k = 0; k < 8; ++k) dd[k] = ea[0] * dw[k][0] + ea[1] * dw[k][1] + ea[2] * dw[k][2];
+    }
     float4* gl = reinterpret_cast<float4*>(grad + g.off[l]);
     if (l >= 2) {
       if (valid) {
 #pragma unroll
-        for (int k = 0; k < 8; ++k) red_add_f4(gl + cc.vtx + corner_offset(g, l, k), f4scale(g4, wc[k]));
+        for (int k = 0; k < 8; ++k) {
+          float4 cv = f4scale(g4, wc[k]);
+          if (eik_any) f4fma(cv, dd[k], q4);
+          red_add_f4(gl + cc.vtx + corner_offset(g, l, k), cv);
+        }
       }
       continue;
     }
@@ -434,7 +461,11 @@ __device__ __forceinline__ void scatter_dz(const GridDesc& g, float* grad, const
     const unsigned ends = __ballot_sync(0xffffffffu, lane == 31 || next != key || key < 0);  // a run's last lane
     float* rw = st + lane * 36;
 #pragma unroll
-    for (int k = 0; k < 8; ++k) *reinterpret_cast<float4*>(rw + 4 * k) = f4scale(g4, wc[k]);
+    for (int k = 0; k < 8; ++k) {
+      float4 cv = f4scale(g4, wc[k]);
+      if (eik_any) f4fma(cv, dd[k], q4);
+      *reinterpret_cast<float4*>(rw + 4 * k) = cv;
+    }
     st[32 * 36 + lane] = __int_as_float(key);  // the keys after the rows
     __syncwarp();
     const long long coff = corner_offset(g, l, lane >> 2);
@@ -510,6 +541,10 @@ struct RenderTcArgs {
   long long store_stride;
   float* w_out;  // [R][N] rendering weights, written by forward passes when not nullptr
   float* dz_out; // [R][N][16] dL/dz of every sample, written by backward passes when not nullptr
+  // deferred Eikonal records ([5][R][N] float4 planes, eik_stride = R N) of the free-space
+  // samples, added to their grid scatter by backward passes; nullptr: none
+  const float4* eik;
+  long long eik_stride;
   // FP32 form: 2D views [nz * ny][nx * 4] of grid levels 2 and 3 for the TMA gathers (a box of
   // 2 vertices x 4 features; one tile::gather4 brings a cell's 8 corners)
   CUtensorMap tmap[2];
@@ -1074,7 +1109,12 @@ __global__ void __launch_bounds__(GR * kGroupThreads, 1) render_tc_kernel(const 
       }
       dw_wait(G);  // the tiles' space holds the scatter's staging rows
       static_assert(L::a_bytes * P::planes + L::b_bytes * L::b_planes >= 4u * kScatterStage * 4u, "staging space");
-      scatter_dz(a.g, a.grad, x, u, valid, reinterpret_cast<float*>(G.a) + warp_g * kScatterStage);
+      int clj = clv[0];
+#pragma unroll
+      for (int q = 1; q < NCH; ++q)
+        if (q == j) clj = clv[q];
+      const float4* er = a.eik != nullptr && valid && clj == CLS_FS ? a.eik + (size_t)rr * N + si : nullptr;
+      scatter_dz(a.g, a.grad, x, u, valid, reinterpret_cast<float*>(G.a) + warp_g * kScatterStage, er, a.eik_stride);
       group_sync(G.g);  // every warp is done with its rows before the tiles are rewritten
     }
   }

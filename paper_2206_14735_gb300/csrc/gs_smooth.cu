@@ -348,276 +348,6 @@ __global__ void __launch_bounds__(kSmoothWarps * 32) query_backward_kernel(Query
   }
 }
 
-// ------------------------------------------------------------------------------------
-// Eikonal term (Sec. 3.3 Eq. eikonal_loss, normalised as in Sec. 3.4): L_eik = mean over the
-// batch's free-space samples S_fs of (1 - |grad_x phi(x_s)|)^2, x_s = o + d_s r.
-// With g = grad_x phi the per-point adjoint is a = -2 (1 - |g|) g / |g| (0 where |g| = 0),
-// scaled by dloss / |S_fs|, and the parameter gradient is the second-order path of the
-// smoothness kernel: the grid gets p_{l,k} (1/v_l)(a . dw_c/df), the decoder
-// d/d W1 = (m (.) W2[0,:]) j^T and d/d W2[0,:] = m (.) (W1 j), j_k = a . d z_k / d x.
-// A warp walks the samples 32 at a time, packs the free-space ones into a queue in shared
-// memory and evaluates the queue 32 points at a time (one point per lane), so lanes are
-// not lost to the other classes.  The loss is reduced in FP64 by the last CTA to finish.
-// ------------------------------------------------------------------------------------
-constexpr int kEikWarps = 2;
-constexpr int kEikRunLevels = 2;  // levels whose scatter is reduced over runs of equal cells first
-
-struct EikArgs {
-  GridDesc g;
-  const float* theta;
-  long long S;  // R * N samples
-  int N;
-  const float *o, *r, *t;
-  const uint8_t* cls;
-  const int* counts;    // counts[2] = |S_fs|
-  const float* dloss;   // [1]
-  float* loss;          // [1] or nullptr
-  float* grad;          // nullptr: loss only
-  float* part;          // [gridDim.x] per-CTA loss sums
-  unsigned* ticket;     // 0 between calls
-};
-
-// One kernel for both uses (loss only when a.grad is null): a forward-only instantiation
-// was scheduled into spills.
-__global__ void __launch_bounds__(kEikWarps * 32, 4) eikonal_kernel(EikArgs a) {
-  __shared__ __align__(16) float sm[sb2];
-  __shared__ __align__(16) float acc[kH1 * kZ + kH1];  // dW1 | dW2[0,:]
-  __shared__ __align__(16) float stage[kEikWarps][32 * kSt];
-  __shared__ long long queue[kEikWarps][64];
-  __shared__ float lsum[kEikWarps];
-  __shared__ bool last;
-  const float* mlp = a.theta + a.g.n_grid;
-  for (int i = threadIdx.x; i < sb2; i += blockDim.x) {
-    float v;
-    if (i < sb1) v = mlp[oW1 + i];
-    else if (i < sW2) v = mlp[ob1 + i - sb1];
-    else v = mlp[oW2 + i - sW2];
-    sm[i] = v;
-  }
-  for (int i = threadIdx.x; i < kH1 * kZ + kH1; i += blockDim.x) acc[i] = 0.0f;
-  __syncthreads();
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  float* st = stage[warp];
-  long long* q = queue[warp];
-  const int n_fs = a.counts[2];
-  const float k_eik = n_fs > 0 ? a.dloss[0] * -2.0f / (float)n_fs : 0.0f;
-  float l_eik = 0.f;
-  int queued = 0;
-
-  const long long stride = (long long)gridDim.x * kEikWarps * 32;
-  long long base = ((long long)blockIdx.x * kEikWarps + warp) * 32;
-#pragma unroll 1
-  for (;;) {
-    // fill the queue with free-space samples until it holds 32 or the samples run out
-    while (queued < 32 && base < a.S) {
-      const long long s = base + lane;
-      const bool fs = s < a.S && a.cls[s] == CLS_FS;
-      const unsigned bal = __ballot_sync(0xffffffffu, fs);
-      if (fs) q[queued + __popc(bal & ((1u << lane) - 1u))] = s;
-      queued += __popc(bal);
-      base += stride;
-    }
-    if (queued == 0) break;
-    __syncwarp();
-    const int cnt = min(queued, 32);
-    const bool valid = lane < cnt;
-    const long long s = valid ? q[lane] : 0;
-    float y[3] = {0.f, 0.f, 0.f};
-    if (valid) {
-      const long long i = s / a.N;
-      const float o3[3] = {a.o[3 * i], a.o[3 * i + 1], a.o[3 * i + 2]};
-      const float r3[3] = {a.r[3 * i], a.r[3 * i + 1], a.r[3 * i + 2]};
-      sample_pos(o3, r3, a.t[s], y);
-    }
-    // z and d z / d x in one pass over each level's 8 corners.  The Jacobian is kept in this
-    // lane's staging row (floats 36..83, free until the decoder-gradient rows are written):
-    // in registers it pushed the kernel into spills, and a second gather cost more.
-    float z[kZ];
-    float4* dls = reinterpret_cast<float4*>(st + lane * kSt + 36);
-#pragma unroll
-    for (int l = 0; l < kLevels; ++l) {
-      float4 dl[3];
-      const Cell c = locate(a.g, l, y);
-      float w[8], dw[8][3];
-      corner_weights(c.f, w);
-      corner_weight_grads(c.f, c.clamped, dw);
-      const float4* lv = reinterpret_cast<const float4*>(a.theta + a.g.off[l]);
-      float4 zz = make_float4(0.f, 0.f, 0.f, 0.f);
-      dl[0] = dl[1] = dl[2] = zz;
-#pragma unroll
-      for (int k = 0; k < 8; ++k) {
-        const float4 v = __ldg(lv + c.vtx + corner_offset(a.g, l, k));
-        f4fma(zz, w[k], v);
-        f4fma(dl[0], dw[k][0], v);
-        f4fma(dl[1], dw[k][1], v);
-        f4fma(dl[2], dw[k][2], v);
-      }
-      const float iv = a.g.inv_voxel[l];
-#pragma unroll
-      for (int d = 0; d < 3; ++d) dls[3 * l + d] = f4scale(dl[d], iv);
-      z[4 * l] = zz.x;
-      z[4 * l + 1] = zz.y;
-      z[4 * l + 2] = zz.z;
-      z[4 * l + 3] = zz.w;
-    }
-    float pz[kZ], mw2[kH1];
-    const unsigned mask = phi_sensitivity(sm, z, mw2, pz);
-    float gq[3];
-#pragma unroll
-    for (int d = 0; d < 3; ++d) {
-      float v = 0.f;
-#pragma unroll
-      for (int l = 0; l < kLevels; ++l) {
-        const float4 q4 = dls[3 * l + d];
-        v += pz[4 * l] * q4.x + pz[4 * l + 1] * q4.y + pz[4 * l + 2] * q4.z + pz[4 * l + 3] * q4.w;
-      }
-      gq[d] = v;
-    }
-    const float nrm = __fsqrt_rn(gq[0] * gq[0] + gq[1] * gq[1] + gq[2] * gq[2]);
-    if (valid) l_eik += (1.f - nrm) * (1.f - nrm);
-    if (a.grad) {
-    const float kk = valid && nrm > 0.f ? k_eik * (1.f - nrm) / nrm : 0.f;
-    const float av[3] = {kk * gq[0], kk * gq[1], kk * gq[2]};
-    // per level: j_l = a . d z_l / d x, and the grid term p_{l,k} (1/v_l) (a . d w_c / d f)
-    float jv[kZ];
-#pragma unroll
-    for (int l = 0; l < kLevels; ++l) {
-      const Cell c = locate(a.g, l, y);
-      float dw[8][3];
-      corner_weight_grads(c.f, c.clamped, dw);
-      {
-        const float4 d0 = dls[3 * l], d1 = dls[3 * l + 1], d2 = dls[3 * l + 2];
-        jv[4 * l] = av[0] * d0.x + av[1] * d1.x + av[2] * d2.x;
-        jv[4 * l + 1] = av[0] * d0.y + av[1] * d1.y + av[2] * d2.y;
-        jv[4 * l + 2] = av[0] * d0.z + av[1] * d1.z + av[2] * d2.z;
-        jv[4 * l + 3] = av[0] * d0.w + av[1] * d1.w + av[2] * d2.w;
-      }
-      const float iv = a.g.inv_voxel[l];
-      const float4 p4 = make_float4(pz[4 * l], pz[4 * l + 1], pz[4 * l + 2], pz[4 * l + 3]);
-      if (l < kEikRunLevels) {
-        // coarse levels: consecutive queued samples (along one ray) mostly share the cell, so
-        // the warp sums runs of equal cells first.  Lane r stages its 8 corner vectors as row
-        // r; lane c then walks the 32 rows summing component c (corner c / 4, feature c % 4)
-        // and adds each run's sum with one atomic.
-        float* row = st + lane * kSt;
-#pragma unroll
-        for (int k = 0; k < 8; ++k) {
-          const float ad = (av[0] * dw[k][0] + av[1] * dw[k][1] + av[2] * dw[k][2]) * iv;
-          *reinterpret_cast<float4*>(row + 4 * k) = f4scale(p4, ad);
-        }
-        row[32] = __int_as_float(kk != 0.f ? (int)c.vtx : -1);
-        __syncwarp();
-        const long long coff = corner_offset(a.g, l, lane >> 2);
-        float* gl = a.grad + a.g.off[l] + (lane & 3);
-        int key = __float_as_int(st[32]);
-        float sum = 0.f;
-#pragma unroll 4
-        for (int r = 0; r < 32; ++r) {
-          sum += st[r * kSt + lane];
-          const int next = r < 31 ? __float_as_int(st[(r + 1) * kSt + 32]) : -2;
-          if (next != key) {
-            if (key >= 0) atomicAdd(gl + ((long long)key + coff) * 4, sum);
-            sum = 0.f;
-            key = next;
-          }
-        }
-        __syncwarp();
-      } else if (kk != 0.f) {
-        float4* gl = reinterpret_cast<float4*>(a.grad + a.g.off[l]) + c.vtx;
-#pragma unroll
-        for (int k = 0; k < 8; ++k) {
-          const float ad = (av[0] * dw[k][0] + av[1] * dw[k][1] + av[2] * dw[k][2]) * iv;
-          atomicAdd(gl + corner_offset(a.g, l, k), f4scale(p4, ad));
-        }
-      }
-    }
-    float* row = st + lane * kSt;
-#pragma unroll
-    for (int i = 0; i < 8; ++i)
-      *reinterpret_cast<float4*>(row + sMw2 + 4 * i) =
-          make_float4(mw2[4 * i], mw2[4 * i + 1], mw2[4 * i + 2], mw2[4 * i + 3]);
-#pragma unroll
-    for (int i = 0; i < 4; ++i)
-      *reinterpret_cast<float4*>(row + sJ + 4 * i) = make_float4(jv[4 * i], jv[4 * i + 1], jv[4 * i + 2], jv[4 * i + 3]);
-#pragma unroll
-    for (int j4 = 0; j4 < kH1; j4 += 4) {  // u_j = m_j (W1 j)_j, stored 4 at a time (no bank conflicts)
-      float u[4];
-#pragma unroll
-      for (int jj = 0; jj < 4; ++jj) {
-        const int j = j4 + jj;
-        u[jj] = 0.f;
-        if ((mask >> j) & 1u) {
-#pragma unroll
-          for (int k = 0; k < kZ; ++k) u[jj] = fmaf(sm[sW1 + j * 16 + k], jv[k], u[jj]);
-        }
-      }
-      *reinterpret_cast<float4*>(row + sU + j4) = make_float4(u[0], u[1], u[2], u[3]);
-    }
-    __syncwarp();
-    {  // dW1 += mw2 (x) j and dW2[0,:] += u over the warp's 32 rows (invalid rows are zero)
-      const int i0 = 4 * (lane >> 2), j0 = 4 * (lane & 3);
-      float tt[4][4] = {};
-#pragma unroll 4
-      for (int s2 = 0; s2 < 32; ++s2) {
-        const float4 a4 = ldv(st + s2 * kSt + sMw2 + i0), b4 = ldv(st + s2 * kSt + sJ + j0);
-        const float ar[4] = {a4.x, a4.y, a4.z, a4.w}, br[4] = {b4.x, b4.y, b4.z, b4.w};
-#pragma unroll
-        for (int x = 0; x < 4; ++x)
-#pragma unroll
-          for (int c = 0; c < 4; ++c) tt[x][c] = fmaf(ar[x], br[c], tt[x][c]);
-      }
-#pragma unroll
-      for (int x = 0; x < 4; ++x)
-#pragma unroll
-        for (int c = 0; c < 4; ++c) atomicAdd(acc + (i0 + x) * kZ + j0 + c, tt[x][c]);
-      float u = 0.f;
-#pragma unroll 4
-      for (int s2 = 0; s2 < 32; ++s2) u += st[s2 * kSt + sU + lane];
-      atomicAdd(acc + kH1 * kZ + lane, u);
-    }
-    }  // a.grad
-    // drop the evaluated entries, keep the rest at the front
-    queued -= cnt;
-    const long long carry = lane < queued ? q[cnt + lane] : 0;
-    __syncwarp();
-    if (lane < queued) q[lane] = carry;
-    __syncwarp();
-  }
-
-  l_eik = warp_sum(l_eik);
-  if (lane == 0) lsum[warp] = l_eik;
-  __syncthreads();
-  if (a.grad) {
-    float* gm = a.grad + a.g.n_grid;
-    for (int i = threadIdx.x; i < kH1 * kZ + kH1; i += blockDim.x) {
-      const float v = acc[i];
-      if (v == 0.f) continue;
-      if (i < kH1 * kZ) atomicAdd(gm + oW1 + i, v);
-      else atomicAdd(gm + oW2 + i - kH1 * kZ, v);  // row 0 of W2
-    }
-  }
-  if (!a.loss) return;
-  if (threadIdx.x == 0) {
-    float v = 0.f;
-#pragma unroll
-    for (int w = 0; w < kEikWarps; ++w) v += lsum[w];
-    a.part[blockIdx.x] = v;
-    __threadfence();
-    last = atomicAdd(a.ticket, 1u) == gridDim.x - 1;
-  }
-  __syncthreads();
-  if (!last || warp != 0) return;
-  __threadfence();
-  double sum = 0.0;
-  for (int b = lane; b < (int)gridDim.x; b += 32) sum += (double)__ldcg(a.part + b);
-#pragma unroll
-  for (int o = 16; o > 0; o >>= 1) sum += __shfl_xor_sync(0xffffffffu, sum, o);
-  if (lane == 0) {
-    a.loss[0] = n_fs > 0 ? (float)(sum / (double)n_fs) : 0.0f;
-    *a.ticket = 0u;  // ready for the next call
-  }
-}
-
 }  // namespace gs
 
 using namespace gs;
@@ -658,28 +388,5 @@ gs_status gs_launch_smooth(const gs_ctx* ctx, const float* theta, const gs_batch
   if (mode == 1) smooth_kernel<true, false><<<kSmoothCtas, kSmoothWarps * 32, 0, st>>>(a);
   else if (mode == 2) smooth_kernel<false, true><<<kSmoothCtas, kSmoothWarps * 32, 0, st>>>(a);
   else smooth_kernel<true, true><<<kSmoothCtas, kSmoothWarps * 32, 0, st>>>(a);
-  return cudaPeekAtLastError() == cudaSuccess ? GS_OK : GS_ERR_CUDA;
-}
-
-gs_status gs_launch_eikonal(const gs_ctx* ctx, const float* theta, const gs_batch* b, const float* dloss, float* loss,
-                            float* grad, cudaStream_t st) {
-  EikArgs a;
-  a.g = ctx->grid;
-  a.theta = theta;
-  a.S = (long long)b->R * b->N;
-  a.N = b->N;
-  a.o = b->origin;
-  a.r = b->dir;
-  a.t = b->t;
-  a.cls = b->cls;
-  a.counts = b->counts;
-  a.dloss = dloss;
-  a.loss = loss;
-  a.grad = grad;
-  a.part = ctx->eik_part;
-  a.ticket = ctx->eik_ticket;
-  const long long per = kEikWarps * 32;
-  const int blocks = (int)std::max<long long>(1, std::min<long long>((a.S + per - 1) / per, (long long)ctx->eik_ctas));
-  eikonal_kernel<<<blocks, per, 0, st>>>(a);
   return cudaPeekAtLastError() == cudaSuccess ? GS_OK : GS_ERR_CUDA;
 }
