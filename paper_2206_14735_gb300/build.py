@@ -17,8 +17,9 @@ CSRC = os.path.join(HERE, "csrc")
 INCLUDE = os.path.join(ROOT, "include")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(BUILD, "libgosurf.so")
-SOURCES = ["gs_api.cu", "gs_sample.cu", "gs_proposal.cu", "gs_importance.cu", "gs_mesh.cu", "gs_pose.cu", "gs_render.cu", "gs_smooth.cu", "gs_eikonal.cu", "gs_adam.cu", "gs_paper.cu",
-           "gs_noalloc.cu"] + [f"gs_render_tc_n{k}_{p}.cu" for k in (1, 2, 3, 4, 5) for p in ("fp32", "bf16")]
+SOURCES = ["gs_api.cu", "gs_sample.cu", "gs_proposal.cu", "gs_importance.cu", "gs_mesh.cu", "gs_pose.cu", "gs_render.cu", "gs_smooth.cu", "gs_eikonal.cu", "gs_adam.cu", "gs_paper.cu", "gs_paper_tc.cu",
+           "gs_noalloc.cu"] + [f"gs_render_tc_n{k}_{p}.cu" for k in (1, 2, 3, 4, 5) for p in ("fp32", "bf16")] + \
+          [f"gs_paper_tc_n{k}.cu" for k in (1, 2, 3, 4, 5)]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

@@ -170,9 +170,8 @@ gs_status gs_create(const gs_config* cfg, gs_ctx** out) {
       (cfg->arch == GS_ARCH_PAPER &&
        (cudaMalloc(&c->paper_part, sizeof(float) * gs_paper_part_floats(c->num_sms)) != cudaSuccess ||
         cudaMalloc(&c->paper_loss_part, sizeof(float) * kLossPad * gs_paper_part_rows(c->num_sms)) != cudaSuccess)) ||
-      (cfg->store_activations &&
-       cudaMalloc(&c->store, c->store_bytes = (size_t)cfg->max_rays * c->max_n *
-                                             (cfg->arch == GS_ARCH_PAPER ? gs_paper_store_fields() : kStoreFloatsPerSample) *
+      (cfg->store_activations && cfg->arch != GS_ARCH_PAPER &&
+       cudaMalloc(&c->store, c->store_bytes = (size_t)cfg->max_rays * c->max_n * kStoreFloatsPerSample *
                                              sizeof(float)) !=
            cudaSuccess)) {
     gs_status s = cuda_fail(nullptr, "gs_create: workspace allocation");
@@ -233,7 +232,7 @@ static gs_status render_common(gs_ctx* ctx, const char* who, const float* theta,
   if ((mode & 2) && !aligned16(grad)) return fail(ctx, GS_ERR_ALIGN, "grad is not 16-byte aligned");
   gs_status s = check_batch(ctx, batch, false);
   if (s != GS_OK) return s;
-  if (ctx->store && mode == 2 && batch->R > 0 &&
+  if (ctx->cfg.store_activations && mode == 2 && batch->R > 0 &&
       (ctx->store_R != batch->R || ctx->store_N != batch->N || ctx->store_t != batch->t))
     return fail(ctx, GS_ERR_INVALID_ARG,
                 "store_activations: gs_backward needs a gs_forward of the same batch first (none, or another batch)");
@@ -244,7 +243,7 @@ static gs_status render_common(gs_ctx* ctx, const char* who, const float* theta,
     if (batch->dz && (reinterpret_cast<uintptr_t>(batch->dz) & 15u)) return fail(ctx, GS_ERR_ALIGN, "batch dz is not 16-byte aligned");
     if (gs_launch_paper(ctx, theta, batch, dl, grad, loss, rgb_hat, d_hat, wsum, mode, st) != GS_OK)
       return cuda_fail(ctx, who);
-    if (ctx->store && (mode & 1)) {
+    if (ctx->cfg.store_activations && (mode & 1)) {
       ctx->store_R = batch->R;
       ctx->store_N = batch->N;
       ctx->store_t = batch->t;
@@ -279,7 +278,7 @@ static gs_status render_common(gs_ctx* ctx, const char* who, const float* theta,
   }
   if (gs_launch_finalize(&tmp, batch, loss, grad, mode, st) != GS_OK) return cuda_fail(ctx, who);
   tmp.last_error.clear();
-  if (ctx->store && (mode & 1)) {
+  if (ctx->cfg.store_activations && (mode & 1)) {
     ctx->store_R = batch->R;
     ctx->store_N = batch->N;
     ctx->store_t = batch->t;

@@ -89,10 +89,12 @@ void gs_set_thread_error(const char* msg);
 // Host-side configuration rules shared by gs_create and gs_forward_backward_noalloc.
 gs_status gs_check_config(const gs_config* cfg, const char** msg);
 int gs_paper_part_rows(int num_sms);
-int gs_paper_store_fields();  // floats per sample of the paper architecture's stored activations
 size_t gs_paper_part_floats(int num_sms);
 gs_status gs_launch_paper(const gs_ctx* ctx, const float* theta, const gs_batch* b, const float* dloss, float* grad,
                           float* loss, float* rgb_hat, float* d_hat, float* wsum, int mode, cudaStream_t st);
+gs_status gs_launch_paper_tc(const gs_ctx* ctx, const float* theta, const gs_batch* b, const float* dloss, float* grad,
+                             float* rgb_hat, float* d_hat, float* wsum, int mode, float* loss_part, float* mlp_part,
+                             int ctas, cudaStream_t st);
 gs_status gs_launch_paper_eikonal(const gs_ctx* ctx, const float* theta, const gs_batch* b, const float* dloss,
                                   float* loss, float* grad, cudaStream_t st);
 gs_status gs_launch_paper_query(const gs_ctx* ctx, const float* theta, const float* x, int P, float* sdf, float* grad,

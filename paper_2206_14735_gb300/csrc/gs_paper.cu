@@ -4,12 +4,8 @@
 // c = g_gamma(W_beta(x), d) with d the unit viewing direction, both decoders with two hidden
 // layers of 32.  Rendering, losses and the smoothness term are those of the workload's model.
 //
-// Kernels (FP32 on CUDA cores):
-//   paper_render_kernel  one warp per ray, one lane per sample of a 32-sample chunk: gathers,
-//                        both decoders, NeuS compositing and losses; then the compositing
-//                        adjoint, and per chunk the recomputed decoders' adjoints, the weight
-//                        gradients (warp-level products over the chunk's 32 samples staged in
-//                        shared memory) and the scatter into both grids;
+// Kernels here (FP32 on CUDA cores; the render pass is the tensor-core kernel of
+// gs_paper_tc.cuh):
 //   paper_smooth_kernel  the smoothness term on S_g and its second-order adjoint, one lane per
 //                        evaluation (x or x + eps of 16 points per warp);
 //   paper_combine_kernel per-CTA partial rows combined in a fixed order (losses in FP64).
@@ -57,15 +53,10 @@ __device__ __forceinline__ int acc_index(int i) {
 constexpr int kRow = 164;
 constexpr int fZ = 0, fU = 16, fA1 = 28, fA2 = 60, fR1 = 92, fR2 = 124, fDP = 156;  // fDP: dpre[3], dphi
 static_assert(kRow % 32 == 4 && fU % 4 == 0 && fA1 % 4 == 0 && fDP % 4 == 0, "row layout");
-// Stored activations (store mode): the row fields z, u, a1, a2, r1, r2 of every sample, one
-// plane per field (field f of sample s at f * sstride + s), written by the forward pass and
-// read back by the backward pass instead of gathering and decoding again.
-constexpr int kStoreFields = fDP;
-static_assert(kStoreFields % 4 == 0, "store fields in float4 groups");
 constexpr int kWarps = 4;  // warps per CTA
 constexpr int kThreads = kWarps * 32;
 constexpr size_t kSmemBytes = sizeof(float) * (2 * kSm + 8 + kWarps * 32 * kRow);
-constexpr int kCtasPerSm = 2;
+constexpr int kCtasPerSm = 2;  // CTAs per SM of the CUDA-core kernels here (sizes the partial rows)
 
 struct Args {
   GridDesc g;            // geometry levels; g.n_grid = decoder block offset (after the colour grid)
@@ -80,8 +71,6 @@ struct Args {
   const float* dloss;
   float *rgb_hat, *d_hat, *wsum, *w_out;
   float* dz_out;                // [R][N][32] per-sample records for the pose gradient (may be nullptr)
-  float* store;                 // stored activations: kStoreFields planes of sstride floats (may be nullptr)
-  long long sstride;
   float *loss_part, *mlp_part;  // this kernel's first partial row
   int R, N, P, mode;
   float lam[5];
@@ -149,513 +138,10 @@ __device__ __forceinline__ void gather(const Args& a, const float x[3], float z[
   }
 }
 
-// both decoders at one sample; with row != nullptr the inputs and hidden activations are
-// staged there (z, u, a1, a2, r1, r2) for the backward pass
-__device__ __forceinline__ void decode(const float* sW, const float z[kZ], const float u[kU], float* row, float& phi,
-                                       float col[3]) {
-  float h[kH];
-#pragma unroll
-  for (int j = 0; j < kH; ++j) {
-    float y = sW[S_gb1 + j];
-#pragma unroll
-    for (int k4 = 0; k4 < 4; ++k4) {
-      const float4 w = ld4(sW + S_gW1 + j * kZ + 4 * k4);
-      y = fmaf(w.x, z[4 * k4], y);
-      y = fmaf(w.y, z[4 * k4 + 1], y);
-      y = fmaf(w.z, z[4 * k4 + 2], y);
-      y = fmaf(w.w, z[4 * k4 + 3], y);
-    }
-    h[j] = fmaxf(y, 0.f);
-  }
-  float p = sW[S_gb3];
-#pragma unroll 1
-  for (int j4 = 0; j4 < kH / 4; ++j4) {
-    float yv[4];
-#pragma unroll
-    for (int q = 0; q < 4; ++q) {
-      const int j = 4 * j4 + q;
-      float y = sW[S_gb2 + j];
-#pragma unroll
-      for (int k4 = 0; k4 < 8; ++k4) {
-        const float4 w = ld4(sW + S_gW2 + j * kH + 4 * k4);
-        y = fmaf(w.x, h[4 * k4], y);
-        y = fmaf(w.y, h[4 * k4 + 1], y);
-        y = fmaf(w.z, h[4 * k4 + 2], y);
-        y = fmaf(w.w, h[4 * k4 + 3], y);
-      }
-      yv[q] = fmaxf(y, 0.f);
-      p = fmaf(sW[S_gw3 + j], yv[q], p);
-    }
-    if (row) st4(row + fA2 + 4 * j4, yv[0], yv[1], yv[2], yv[3]);
-  }
-  phi = p;
-  if (row) {
-#pragma unroll
-    for (int k4 = 0; k4 < kZ / 4; ++k4) st4(row + fZ + 4 * k4, z[4 * k4], z[4 * k4 + 1], z[4 * k4 + 2], z[4 * k4 + 3]);
-#pragma unroll
-    for (int j4 = 0; j4 < kH / 4; ++j4) st4(row + fA1 + 4 * j4, h[4 * j4], h[4 * j4 + 1], h[4 * j4 + 2], h[4 * j4 + 3]);
-    st4(row + fU, u[0], u[1], u[2], u[3]);
-    st4(row + fU + 4, u[4], u[5], u[6], u[7]);
-    st4(row + fU + 8, u[8], 0.f, 0.f, 0.f);
-  }
-#pragma unroll
-  for (int j = 0; j < kH; ++j) {
-    float y = sW[S_cb1 + j];
-#pragma unroll
-    for (int k = 0; k < kU; ++k) y = fmaf(sW[S_cW1 + j * kU + k], u[k], y);
-    h[j] = fmaxf(y, 0.f);
-  }
-  float pre[3] = {sW[S_cb3], sW[S_cb3 + 1], sW[S_cb3 + 2]};
-#pragma unroll 1
-  for (int j4 = 0; j4 < kH / 4; ++j4) {
-    float yv[4];
-#pragma unroll
-    for (int q = 0; q < 4; ++q) {
-      const int j = 4 * j4 + q;
-      float y = sW[S_cb2 + j];
-#pragma unroll
-      for (int k4 = 0; k4 < 8; ++k4) {
-        const float4 w = ld4(sW + S_cW2 + j * kH + 4 * k4);
-        y = fmaf(w.x, h[4 * k4], y);
-        y = fmaf(w.y, h[4 * k4 + 1], y);
-        y = fmaf(w.z, h[4 * k4 + 2], y);
-        y = fmaf(w.w, h[4 * k4 + 3], y);
-      }
-      yv[q] = fmaxf(y, 0.f);
-#pragma unroll
-      for (int i = 0; i < 3; ++i) pre[i] = fmaf(sW[S_cW3 + i * kH + j], yv[q], pre[i]);
-    }
-    if (row) st4(row + fR2 + 4 * j4, yv[0], yv[1], yv[2], yv[3]);
-  }
-  if (row) {
-#pragma unroll
-    for (int j4 = 0; j4 < kH / 4; ++j4) st4(row + fR1 + 4 * j4, h[4 * j4], h[4 * j4 + 1], h[4 * j4 + 2], h[4 * j4 + 3]);
-  }
-#pragma unroll
-  for (int i = 0; i < 3; ++i) col[i] = sigmoidf_(pre[i]);
-}
-
-// grid-gradient scatter of one sample: dz into the 4 geometry levels, dcf into the colour grid
-__device__ __forceinline__ void scatter(const Args& a, const float x[3], const float dz[kZ], const float dcf[kC]) {
-#pragma unroll
-  for (int l = 0; l < kLevels; ++l) {
-    const Cell c = locate(a.g, l, x);
-    float w[8];
-    corner_weights(c.f, w);
-    float4* gl = reinterpret_cast<float4*>(a.grad + a.g.off[l]);
-    const float4 d = make_float4(dz[4 * l], dz[4 * l + 1], dz[4 * l + 2], dz[4 * l + 3]);
-#pragma unroll
-    for (int k = 0; k < 8; ++k) atomicAdd(gl + c.vtx + corner_offset(a.g, l, k), f4scale(d, w[k]));
-    if (l == kLevels - 1) {
-      float2* cg = reinterpret_cast<float2*>(a.grad + a.colour_off);
-#pragma unroll
-      for (int k = 0; k < 8; ++k) {
-        const long long v2 = (c.vtx + corner_offset(a.g, l, k)) * 3;
-#pragma unroll
-        for (int q = 0; q < 3; ++q) atomicAdd(cg + v2 + q, make_float2(w[k] * dcf[2 * q], w[k] * dcf[2 * q + 1]));
-      }
-    }
-  }
-}
-
 __device__ __forceinline__ void write_partials(const Args& a, const float* sG, const float* sL) {
   float* row = a.mlp_part + (size_t)blockIdx.x * kPart;
   for (int i = threadIdx.x; i < kPart; i += blockDim.x) row[i] = i < GS_PAPER_MLP_PARAMS ? sG[acc_index(i)] : 0.f;
   if (threadIdx.x < kLossPad) a.loss_part[(size_t)blockIdx.x * kLossPad + threadIdx.x] = sL[threadIdx.x];
-}
-
-template <int NCH>
-__global__ void __launch_bounds__(kThreads, kCtasPerSm) paper_render_kernel(Args a) {
-  extern __shared__ __align__(16) float smem[];
-  float* sW = smem;
-  float* sG = sW + kSm;
-  float* sL = sG + kSm;
-  float* rows = sL + 8;
-  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-  float* wr = rows + wid * 32 * kRow;
-  float* my = wr + lane * kRow;
-  copy_decoder(a.theta + a.g.n_grid, sW);
-  for (int i = threadIdx.x; i < kSm; i += blockDim.x) sG[i] = 0.f;
-  if (threadIdx.x < 8) sL[threadIdx.x] = 0.f;
-  __syncthreads();
-  const bool bwd = (a.mode & 2) != 0, fwd = (a.mode & 1) != 0;
-  const float s = expf(sW[S_kappa]);
-  float wt[5];
-#pragma unroll
-  for (int k = 0; k < 5; ++k) wt[k] = a.dloss[k] + a.lam[k] * a.dloss[5];
-  const int n_d = a.counts[0], n_tr = a.counts[1], n_fs = a.counts[2];
-  const int N = a.N;
-  float lsum[5] = {0.f, 0.f, 0.f, 0.f, 0.f};
-  float gkappa = 0.f;
-
-  for (int ray = blockIdx.x * kWarps + wid; ray < a.R; ray += gridDim.x * kWarps) {
-    float o[3], r[3], I[3], d[3];
-#pragma unroll
-    for (int q = 0; q < 3; ++q) {
-      o[q] = a.o[3 * ray + q];
-      r[q] = a.r[3 * ray + q];
-      I[q] = a.rgb[3 * ray + q];
-    }
-    const float D = a.D[ray];
-    __syncwarp();  // the previous ray's products have read every row before this ray stages its last chunk
-    const float rn = sqrtf(r[0] * r[0] + r[1] * r[1] + r[2] * r[2]);
-#pragma unroll
-    for (int q = 0; q < 3; ++q) d[q] = r[q] / rn;
-    float tk[NCH], phi[NCH], col[NCH][3];
-    int cl[NCH];
-#pragma unroll
-    for (int c = 0; c < NCH; ++c) {
-      const int k = 32 * c + lane;
-      tk[c] = k < N ? a.t[(size_t)ray * N + k] : 0.f;
-      cl[c] = k < N ? a.cls[(size_t)ray * N + k] : CLS_NONE;
-    }
-    // one decoder body for all chunks (rolled loop; per-chunk registers picked by unrolled selects)
-#pragma unroll 1
-    for (int c = 0; c < NCH; ++c) {
-      const bool ok = 32 * c + lane < N;
-      float tc = tk[0];
-#pragma unroll
-      for (int q = 1; q < NCH; ++q)
-        if (c == q) tc = tk[q];
-      float z[kZ], u[kU];
-      if (ok) {
-        float x[3];
-        sample_pos(o, r, tc, x);
-        gather(a, x, z, u);
-      } else {
-#pragma unroll
-        for (int q = 0; q < kZ; ++q) z[q] = 0.f;
-#pragma unroll
-        for (int q = 0; q < kC; ++q) u[q] = 0.f;
-      }
-#pragma unroll
-      for (int q = 0; q < 3; ++q) u[kC + q] = d[q];
-      float ph, cc[3];
-      const bool put = a.store != nullptr && fwd;
-      decode(sW, z, u, put || (bwd && c == NCH - 1) ? my : nullptr, ph, cc);
-      if (put && 32 * c + lane < N) {
-        float* sp = a.store + (size_t)ray * N + 32 * c + lane;
-#pragma unroll 4
-        for (int f4 = 0; f4 < kStoreFields / 4; ++f4) {
-          const float4 v = ld4(my + 4 * f4);
-          sp[(4 * f4) * a.sstride] = v.x;
-          sp[(4 * f4 + 1) * a.sstride] = v.y;
-          sp[(4 * f4 + 2) * a.sstride] = v.z;
-          sp[(4 * f4 + 3) * a.sstride] = v.w;
-        }
-      }
-#pragma unroll
-      for (int q = 0; q < NCH; ++q)
-        if (c == q) {
-          phi[q] = ph;
-          col[q][0] = cc[0];
-          col[q][1] = cc[1];
-          col[q][2] = cc[2];
-        }
-    }
-    // NeuS opacities, transmittance, weights (Sec. 3.2 Eq. volume_rendering_alpha)
-    float Phi[NCH], PhiN[NCH], alpha[NCH], T[NCH], w[NCH];
-#pragma unroll
-    for (int c = 0; c < NCH; ++c) Phi[c] = sigmoidf_(s * phi[c]);
-#pragma unroll
-    for (int c = 0; c < NCH; ++c) {
-      float nx = __shfl_down_sync(0xffffffffu, Phi[c], 1);
-      const float first_next = c + 1 < NCH ? __shfl_sync(0xffffffffu, Phi[c + 1 < NCH ? c + 1 : c], 0) : 0.f;
-      if (lane == 31) nx = first_next;
-      PhiN[c] = nx;
-      const float q = (Phi[c] - nx) / fmaxf(Phi[c], 1e-6f);
-      alpha[c] = (32 * c + lane < N - 1) ? fmaxf(q, 0.f) : 0.f;
-    }
-    float carry = 1.f;
-#pragma unroll
-    for (int c = 0; c < NCH; ++c) {
-      float incl = 1.f - alpha[c];
-#pragma unroll
-      for (int off = 1; off < 32; off <<= 1) {
-        const float v = __shfl_up_sync(0xffffffffu, incl, off);
-        if (lane >= off) incl *= v;
-      }
-      float excl = __shfl_up_sync(0xffffffffu, incl, 1);
-      if (lane == 0) excl = 1.f;
-      T[c] = carry * excl;
-      w[c] = T[c] * alpha[c];
-      carry *= __shfl_sync(0xffffffffu, incl, 31);
-    }
-    float ch[3] = {0.f, 0.f, 0.f}, dh = 0.f, ws = 0.f;
-#pragma unroll
-    for (int c = 0; c < NCH; ++c) {
-#pragma unroll
-      for (int q = 0; q < 3; ++q) ch[q] = fmaf(w[c], col[c][q], ch[q]);
-      dh = fmaf(w[c], tk[c], dh);
-      ws += w[c];
-      if (a.w_out && 32 * c + lane < N) a.w_out[(size_t)ray * N + 32 * c + lane] = w[c];
-    }
-#pragma unroll
-    for (int q = 0; q < 3; ++q) ch[q] = warp_sum(ch[q]);
-    dh = warp_sum(dh);
-    ws = warp_sum(ws);
-    if (lane == 0) {
-      if (a.rgb_hat)
-#pragma unroll
-        for (int q = 0; q < 3; ++q) a.rgb_hat[3 * ray + q] = ch[q];
-      if (a.d_hat) a.d_hat[ray] = dh;
-      if (a.wsum) a.wsum[ray] = ws;
-      float e2 = 0.f;
-#pragma unroll
-      for (int q = 0; q < 3; ++q) e2 = fmaf(I[q] - ch[q], I[q] - ch[q], e2);
-      lsum[0] += e2;
-      if (D > 0.f) lsum[1] += fabsf(D - dh);
-    }
-    // approximate SDF supervision (Sec. 3.3)
-#pragma unroll
-    for (int c = 0; c < NCH; ++c) {
-      const float b = D - tk[c];
-      if (cl[c] == CLS_TR) lsum[2] += fabsf(phi[c] - b);
-      else if (cl[c] == CLS_FS) lsum[3] += fmaxf(fmaxf(0.f, expf(-a.kappa_fs * phi[c]) - 1.f), phi[c] - b);
-    }
-    if (!bwd) continue;
-
-    // ---------------- compositing adjoint ----------------
-    float gc[3], gd = 0.f;
-#pragma unroll
-    for (int q = 0; q < 3; ++q) gc[q] = wt[0] / (float)a.R * 2.f * (ch[q] - I[q]);
-    if (D > 0.f && n_d > 0) gd = wt[1] / (float)n_d * (dh > D ? 1.f : (dh < D ? -1.f : 0.f));
-    float e[NCH], U[NCH];
-#pragma unroll
-    for (int c = 0; c < NCH; ++c) e[c] = gc[0] * col[c][0] + gc[1] * col[c][1] + gc[2] * col[c][2] + gd * tk[c];
-    // U_{k-1} = alpha_k e_k + (1 - alpha_k) U_k from U_{N-1} = 0: a suffix scan of affine maps
-    float Unext = 0.f;
-#pragma unroll
-    for (int c = NCH - 1; c >= 0; --c) {
-      float A = 1.f - alpha[c], B = alpha[c] * e[c];
-#pragma unroll
-      for (int off = 1; off < 32; off <<= 1) {
-        const float Ah = __shfl_down_sync(0xffffffffu, A, off), Bh = __shfl_down_sync(0xffffffffu, B, off);
-        if (lane + off < 32) {
-          B = fmaf(A, Bh, B);
-          A *= Ah;
-        }
-      }
-      const float Uprev = fmaf(A, Unext, B);
-      float Uk = __shfl_down_sync(0xffffffffu, Uprev, 1);
-      if (lane == 31) Uk = Unext;
-      U[c] = Uk;
-      Unext = __shfl_sync(0xffffffffu, Uprev, 0);
-    }
-    float dphi[NCH];
-    float to_next_carry = 0.f;
-#pragma unroll
-    for (int c = 0; c < NCH; ++c) {
-      const int k = 32 * c + lane;
-      float own = 0.f, to_next = 0.f;
-      if (k < N - 1 && alpha[c] > 0.f) {
-        const float dalpha = T[c] * (e[c] - U[c]);
-        const float den = fmaxf(Phi[c], 1e-6f);
-        to_next = -dalpha / den;
-        own = Phi[c] > 1e-6f ? dalpha * (PhiN[c] / (Phi[c] * Phi[c])) : dalpha * 1e6f;
-      }
-      float from_prev = __shfl_up_sync(0xffffffffu, to_next, 1);
-      if (lane == 0) from_prev = to_next_carry;
-      to_next_carry = __shfl_sync(0xffffffffu, to_next, 31);
-      const float dPhi = own + from_prev;
-      const float dsig = Phi[c] * (1.f - Phi[c]);
-      float g = dPhi * s * dsig;
-      gkappa = fmaf(dPhi * dsig * s, phi[c], gkappa);
-      const float b = D - tk[c];
-      if (cl[c] == CLS_TR && n_tr > 0) g += wt[2] / (float)n_tr * (phi[c] > b ? 1.f : (phi[c] < b ? -1.f : 0.f));
-      if (cl[c] == CLS_FS && n_fs > 0) {
-        const float ex = expf(-a.kappa_fs * phi[c]) - 1.f, lin = phi[c] - b;
-        int arg = 0;
-        float top = 0.f;
-        if (ex > top) {
-          top = ex;
-          arg = 1;
-        }
-        if (lin > top) arg = 2;
-        g += wt[3] / (float)n_fs * (arg == 1 ? -a.kappa_fs * (ex + 1.f) : (arg == 2 ? 1.f : 0.f));
-      }
-      dphi[c] = k < N ? g : 0.f;
-    }
-
-    // ---------------- decoder adjoints and scatter, chunk by chunk ----------------
-    // Last chunk first: its inputs and activations are still staged in the rows by the
-    // forward pass; the other chunks gather and decode again.
-#pragma unroll 1
-    for (int c = NCH - 1; c >= 0; --c) {
-      const int k = 32 * c + lane;
-      const bool ok = k < N;
-      float tc = tk[0], wc = w[0], dp = dphi[0], cc[3] = {col[0][0], col[0][1], col[0][2]};
-#pragma unroll
-      for (int q = 1; q < NCH; ++q)
-        if (c == q) {
-          tc = tk[q];
-          wc = w[q];
-          dp = dphi[q];
-          cc[0] = col[q][0];
-          cc[1] = col[q][1];
-          cc[2] = col[q][2];
-        }
-      float x[3] = {0.f, 0.f, 0.f};
-      if (ok) sample_pos(o, r, tc, x);
-      if (c != NCH - 1 && a.store != nullptr) {  // stored by the forward pass: back into the row
-        __syncwarp();  // the previous chunk's products have read every row
-        const float* sp = a.store + (size_t)ray * N + (ok ? k : 0);
-#pragma unroll 4
-        for (int f4 = 0; f4 < kStoreFields / 4; ++f4) {
-          if (ok)
-            st4(my + 4 * f4, sp[(4 * f4) * a.sstride], sp[(4 * f4 + 1) * a.sstride], sp[(4 * f4 + 2) * a.sstride],
-                sp[(4 * f4 + 3) * a.sstride]);
-          else
-            st4(my + 4 * f4, 0.f, 0.f, 0.f, 0.f);
-        }
-      } else if (c != NCH - 1) {
-        float z[kZ], u[kU];
-        __syncwarp();  // the previous chunk's products have read every row
-        if (ok) {
-          gather(a, x, z, u);
-        } else {
-#pragma unroll
-          for (int q = 0; q < kZ; ++q) z[q] = 0.f;
-#pragma unroll
-          for (int q = 0; q < kC; ++q) u[q] = 0.f;
-        }
-#pragma unroll
-        for (int q = 0; q < 3; ++q) u[kC + q] = d[q];
-        float ph, c2[3];
-        decode(sW, z, u, my, ph, c2);
-      }
-      float dpre[3];
-#pragma unroll
-      for (int q = 0; q < 3; ++q) dpre[q] = ok ? wc * gc[q] * cc[q] * (1.f - cc[q]) : 0.f;
-      st4(my + fDP, dpre[0], dpre[1], dpre[2], dp);
-      __syncwarp();
-      {  // output layers: gw3, gb3 (lane = column), cW3, cb3
-        float ag = 0.f, a0 = 0.f, a1 = 0.f, a2 = 0.f, bg = 0.f, b0 = 0.f, b1 = 0.f, b2 = 0.f;
-#pragma unroll 4
-        for (int sidx = 0; sidx < 32; ++sidx) {
-          const float* rs = wr + sidx * kRow;
-          const float4 dd = ld4(rs + fDP);  // dpre[0..2], dphi
-          const float r2 = rs[fR2 + lane];
-          ag = fmaf(dd.w, rs[fA2 + lane], ag);
-          a0 = fmaf(dd.x, r2, a0);
-          a1 = fmaf(dd.y, r2, a1);
-          a2 = fmaf(dd.z, r2, a2);
-          bg += dd.w;
-          b0 += dd.x;
-          b1 += dd.y;
-          b2 += dd.z;
-        }
-        atomicAdd(sG + S_gw3 + lane, ag);
-        atomicAdd(sG + S_cW3 + lane, a0);
-        atomicAdd(sG + S_cW3 + kH + lane, a1);
-        atomicAdd(sG + S_cW3 + 2 * kH + lane, a2);
-        if (lane == 0) {
-          atomicAdd(sG + S_gb3, bg);
-          atomicAdd(sG + S_cb3, b0);
-          atomicAdd(sG + S_cb3 + 1, b1);
-          atomicAdd(sG + S_cb3 + 2, b2);
-        }
-      }
-      __syncwarp();
-      // own sample: dy2 = m2 (.) gw3 dphi over a2; dq2 = m(q2) (.) cW3^T dpre over r2
-#pragma unroll
-      for (int j4 = 0; j4 < kH / 4; ++j4) {
-        const float4 a2v = ld4(my + fA2 + 4 * j4), w3 = ld4(sW + S_gw3 + 4 * j4);
-        st4(my + fA2 + 4 * j4, a2v.x > 0.f ? w3.x * dp : 0.f, a2v.y > 0.f ? w3.y * dp : 0.f,
-            a2v.z > 0.f ? w3.z * dp : 0.f, a2v.w > 0.f ? w3.w * dp : 0.f);
-        const float4 r2v = ld4(my + fR2 + 4 * j4), c0 = ld4(sW + S_cW3 + 4 * j4),
-                     c1 = ld4(sW + S_cW3 + kH + 4 * j4), c2 = ld4(sW + S_cW3 + 2 * kH + 4 * j4);
-        st4(my + fR2 + 4 * j4, r2v.x > 0.f ? c0.x * dpre[0] + c1.x * dpre[1] + c2.x * dpre[2] : 0.f,
-            r2v.y > 0.f ? c0.y * dpre[0] + c1.y * dpre[1] + c2.y * dpre[2] : 0.f,
-            r2v.z > 0.f ? c0.z * dpre[0] + c1.z * dpre[1] + c2.z * dpre[2] : 0.f,
-            r2v.w > 0.f ? c0.w * dpre[0] + c1.w * dpre[1] + c2.w * dpre[2] : 0.f);
-      }
-      __syncwarp();
-      outer_rows<kH, true>(wr, fA2, fA1, sG + S_gW2, sG + S_gb2, lane);
-      outer_rows<kH, true>(wr, fR2, fR1, sG + S_cW2, sG + S_cb2, lane);
-      __syncwarp();
-      // own sample: dy1 = m1 (.) gW2^T dy2 over a1; dq1 = m(q1) (.) cW2^T dq2 over r1
-#pragma unroll
-      for (int half = 0; half < 2; ++half) {
-        const int fin = half ? fR2 : fA2, fout = half ? fR1 : fA1, sw = half ? S_cW2 : S_gW2;
-        float acc[kH];
-#pragma unroll
-        for (int q = 0; q < kH; ++q) acc[q] = 0.f;
-#pragma unroll 1
-        for (int j4 = 0; j4 < kH / 4; ++j4) {
-          const float4 dy4 = ld4(my + fin + 4 * j4);
-          const float dys[4] = {dy4.x, dy4.y, dy4.z, dy4.w};
-#pragma unroll
-          for (int q = 0; q < 4; ++q) {
-            const int j = 4 * j4 + q;
-#pragma unroll
-            for (int k4 = 0; k4 < 8; ++k4) {
-              const float4 wv = ld4(sW + sw + j * kH + 4 * k4);
-              acc[4 * k4] = fmaf(wv.x, dys[q], acc[4 * k4]);
-              acc[4 * k4 + 1] = fmaf(wv.y, dys[q], acc[4 * k4 + 1]);
-              acc[4 * k4 + 2] = fmaf(wv.z, dys[q], acc[4 * k4 + 2]);
-              acc[4 * k4 + 3] = fmaf(wv.w, dys[q], acc[4 * k4 + 3]);
-            }
-          }
-        }
-#pragma unroll
-        for (int q4 = 0; q4 < kH / 4; ++q4) {
-          const float4 hv = ld4(my + fout + 4 * q4);
-          st4(my + fout + 4 * q4, hv.x > 0.f ? acc[4 * q4] : 0.f, hv.y > 0.f ? acc[4 * q4 + 1] : 0.f,
-              hv.z > 0.f ? acc[4 * q4 + 2] : 0.f, hv.w > 0.f ? acc[4 * q4 + 3] : 0.f);
-        }
-      }
-      __syncwarp();
-      outer_rows<kZ, true>(wr, fA1, fZ, sG + S_gW1, sG + S_gb1, lane);
-      outer_rows<kU, true>(wr, fR1, fU, sG + S_cW1, sG + S_cb1, lane);
-      if (ok) {  // dz = gW1^T dy1, dcf = cW1[:, :6]^T dq1 (ddir: the direction's rows), then the scatter
-        float dz[kZ], dcf[kU];
-#pragma unroll
-        for (int q = 0; q < kZ; ++q) dz[q] = 0.f;
-#pragma unroll
-        for (int q = 0; q < kU; ++q) dcf[q] = 0.f;
-#pragma unroll 1
-        for (int j4 = 0; j4 < kH / 4; ++j4) {
-          const float4 dy4 = ld4(my + fA1 + 4 * j4), dq4 = ld4(my + fR1 + 4 * j4);
-          const float dys[4] = {dy4.x, dy4.y, dy4.z, dy4.w}, dqs[4] = {dq4.x, dq4.y, dq4.z, dq4.w};
-#pragma unroll
-          for (int q = 0; q < 4; ++q) {
-            const int j = 4 * j4 + q;
-#pragma unroll
-            for (int k4 = 0; k4 < 4; ++k4) {
-              const float4 wv = ld4(sW + S_gW1 + j * kZ + 4 * k4);
-              dz[4 * k4] = fmaf(wv.x, dys[q], dz[4 * k4]);
-              dz[4 * k4 + 1] = fmaf(wv.y, dys[q], dz[4 * k4 + 1]);
-              dz[4 * k4 + 2] = fmaf(wv.z, dys[q], dz[4 * k4 + 2]);
-              dz[4 * k4 + 3] = fmaf(wv.w, dys[q], dz[4 * k4 + 3]);
-            }
-#pragma unroll
-            for (int e = 0; e < kU; ++e) dcf[e] = fmaf(sW[S_cW1 + j * kU + e], dqs[q], dcf[e]);
-          }
-        }
-        scatter(a, x, dz, dcf);
-        if (a.dz_out) {  // the sample's record for the pose gradient: dz (16), dcf (6), ddir (3), zeros
-          float* rec = a.dz_out + ((size_t)ray * N + k) * 32;
-#pragma unroll
-          for (int q = 0; q < 4; ++q) st4(rec + 4 * q, dz[4 * q], dz[4 * q + 1], dz[4 * q + 2], dz[4 * q + 3]);
-          st4(rec + 16, dcf[0], dcf[1], dcf[2], dcf[3]);
-          st4(rec + 20, dcf[4], dcf[5], dcf[6], dcf[7]);
-          st4(rec + 24, dcf[8], 0.f, 0.f, 0.f);
-          st4(rec + 28, 0.f, 0.f, 0.f, 0.f);
-        }
-      }
-    }
-  }
-  // CTA sums of the loss terms and of d kappa
-#pragma unroll
-  for (int q = 0; q < 5; ++q) {
-    const float v = warp_sum(lsum[q]);
-    if (lane == 0) atomicAdd(sL + q, v);
-  }
-  const float gk = warp_sum(gkappa);
-  if (lane == 0 && bwd) atomicAdd(sG + S_kappa, gk);
-  __syncthreads();
-  write_partials(a, sG, sL);
 }
 
 // One lane, one point y: g = grad_x phi(y) = sum_k p_k dz_k/dx for the geometry decoder,
@@ -1280,26 +766,11 @@ __global__ void __launch_bounds__(256) paper_combine_kernel(const float* loss_pa
   }
 }
 
-template <int NCH>
-static gs_status launch_render(const gs_ctx* ctx, const Args& a, int ctas, cudaStream_t st) {
-  static bool attr = false;  // per process; the attribute is a property of the function
-  if (!attr) {
-    if (cudaFuncSetAttribute(paper_render_kernel<NCH>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             (int)kSmemBytes) != cudaSuccess)
-      return GS_ERR_CUDA;
-    attr = true;
-  }
-  paper_render_kernel<NCH><<<ctas, kThreads, kSmemBytes, st>>>(a);
-  (void)ctx;
-  return cudaPeekAtLastError() == cudaSuccess ? GS_OK : GS_ERR_CUDA;
-}
-
 }  // namespace paper
 }  // namespace gs
 
 using namespace gs;
 
-int gs_paper_store_fields() { return paper::kStoreFields; }
 int gs_paper_part_rows(int num_sms) { return paper::kCtasPerSm * num_sms + kSmoothCtas; }
 size_t gs_paper_part_floats(int num_sms) { return (size_t)gs_paper_part_rows(num_sms) * paper::kPart; }
 
@@ -1327,30 +798,19 @@ gs_status gs_launch_paper(const gs_ctx* ctx, const float* theta, const gs_batch*
   a.wsum = wsum;
   a.w_out = b->w;
   a.dz_out = b->dz;
-  a.store = ctx->store;
-  a.sstride = (long long)ctx->cfg.max_rays * ctx->max_n;
   a.R = b->R;
   a.N = b->N;
   a.P = b->P;
   a.mode = mode;
   for (int k = 0; k < 5; ++k) a.lam[k] = ctx->cfg.lam[k];
   a.kappa_fs = ctx->cfg.kappa_fs;
-  const int render_ctas = kCtasPerSm * ctx->num_sms;
+  const int render_ctas = ctx->num_sms;  // the tensor-core render kernel: one CTA per SM
   int nparts = 0;
   float* first_loss = ctx->paper_loss_part;
   float* first_mlp = ctx->paper_part;
   if (b->R > 0) {
-    a.loss_part = ctx->paper_loss_part;
-    a.mlp_part = ctx->paper_part;
-    gs_status s;
-    switch ((b->N + 31) / 32) {
-      case 1: s = launch_render<1>(ctx, a, render_ctas, st); break;
-      case 2: s = launch_render<2>(ctx, a, render_ctas, st); break;
-      case 3: s = launch_render<3>(ctx, a, render_ctas, st); break;
-      case 4: s = launch_render<4>(ctx, a, render_ctas, st); break;
-      case 5: s = launch_render<5>(ctx, a, render_ctas, st); break;
-      default: return GS_ERR_UNSUPPORTED;
-    }
+    const gs_status s = gs_launch_paper_tc(ctx, theta, b, dloss, grad, rgb_hat, d_hat, wsum, mode,
+                                           ctx->paper_loss_part, ctx->paper_part, render_ctas, st);
     if (s != GS_OK) return s;
     nparts += render_ctas;
   }
