@@ -141,9 +141,8 @@ def step_config(w, args, world, n_frames):
                         if w.imp_coarse > 0 else f"stratified {w.n_strat} + depth-guided {w.n_guided}"),
             "pipeline": ("the next step's batch sampled on a side stream during this step (double-buffered)"
                          if pipelined else "in line"),
-            "calls": ("gs_eikonal (grid part deferred to the render call) + " if args.eikonal and not paper else "") +
-                     ("gs_forward + gs_backward" if args.split else "gs_forward_backward") +
-                     (" + gs_eikonal" if args.eikonal and paper else ""),
+            "calls": ("gs_eikonal (grid part deferred to the render call) + " if args.eikonal else "") +
+                     ("gs_forward + gs_backward" if args.split else "gs_forward_backward"),
             "loss_terms": "rgb, depth, sdf, fs, smooth" + (", eikonal (lam 1, free-space samples)"
                                                            if args.eikonal else ""),
             "poses": ("refined: per-frame (dt, nu), gs_pose_apply + gs_pose_backward" +
@@ -183,9 +182,9 @@ def run_ours(args):
     n_grid_ = w.layout()[1]
     # BF16 form: the grid copy the gathers read, refreshed by every Adam step
     mirror = theta[:n_grid_].to(torch.bfloat16).view(torch.int16).contiguous() if ctx.bf16 else None
-    # the compact decoder's Eikonal term leaves its grid part to the render kernel's scatter
-    # (deferred records in the batch); the paper's architecture scatters it in its own kernel
-    defer_eik = args.eikonal and not paper
+    # the Eikonal term leaves its grid part to the render kernel's scatter (deferred records in
+    # the batch), so its call comes before the render call
+    defer_eik = args.eikonal
     batch = gs.Batch.allocate(w.rays, w.n_samples, w.n_smooth, dz=args.poses, dz_width=32 if paper else 16,
                               eik=defer_eik)
     loss = torch.empty(6, device="cuda")

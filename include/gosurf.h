@@ -161,7 +161,7 @@ typedef struct gs_batch {
                       pass over this batch (see gs_eikonal); plane k of sample s = r N + i at
                       ((float4*)eik)[k R N + s]: planes 0..3 p_l / v_l (level l's part of
                       d phi / d z over its voxel size), plane 4 (a, 0) with a the Eikonal
-                      adjoint dL/d(grad_x phi).  GS_ARCH_COMPACT only (NULL otherwise). */
+                      adjoint dL/d(grad_x phi).  Both architectures. */
 } gs_batch;
 
 typedef struct gs_ctx gs_ctx;
@@ -292,8 +292,8 @@ gs_status gs_query_sdf_backward(gs_ctx* ctx, const float* theta, const float* x,
  * row 0 of W2 through d phi/d z; the sub-gradient at grad_x phi = 0 is 0), accumulated with
  * atomics (order not fixed).  Reads the FP32 grid in every precision form.  Needs only the
  * batch's ray arrays (origin, dir, t, cls, counts).
- * Deferred grid term (GS_ARCH_COMPACT, grad != NULL, batch->eik != NULL): the grid part of the
- * gradient is not scattered here; every free-space sample's record (p_l / v_l, a) goes to
+ * Deferred grid term (batch->eik != NULL): the grid part of the gradient is not scattered
+ * here; every free-space sample's record (p_l / v_l, a; a = 0 when grad is NULL) goes to
  * batch->eik instead, and the next gs_backward / gs_forward_backward over the same batch adds
  * p_l (1/v_l) (a . dw_c/df) to the corner vectors it scatters anyway (no reductions of its
  * own).  grad then holds the full gradient only after that backward pass; the decoder part

@@ -49,8 +49,6 @@ gs_status check_batch(gs_ctx* ctx, const gs_batch* b, bool need_smooth_arrays) {
     return fail(ctx, GS_ERR_INVALID_ARG, "batch ray array is NULL");
   if (b->R > 0 && need_smooth_arrays && !b->pix) return fail(ctx, GS_ERR_INVALID_ARG, "batch pix is NULL");
   if (b->P > 0 && (!b->xs || !b->eps || !b->valid)) return fail(ctx, GS_ERR_INVALID_ARG, "batch smoothness array is NULL");
-  if (b->eik && ctx->cfg.arch == GS_ARCH_PAPER)
-    return fail(ctx, GS_ERR_UNSUPPORTED, "batch eik (deferred Eikonal records) is GS_ARCH_COMPACT only");
   if (b->eik && (reinterpret_cast<uintptr_t>(b->eik) & 15u)) return fail(ctx, GS_ERR_ALIGN, "batch eik is not 16-byte aligned");
   return GS_OK;
 }

@@ -75,6 +75,7 @@ struct Args {
   int R, N, P, mode;
   float lam[5];
   float kappa_fs;
+  float4* eik;  // Eikonal call: deferred grid term, [5][R N] records of the free-space samples (or nullptr)
 };
 
 // lane j (row j of a 32-row matrix) sums delta_s[j] * act_s[k] over the warp's 32 staged
@@ -464,14 +465,23 @@ __global__ void __launch_bounds__(kThreads, 1) paper_eikonal_kernel(Args a) {
     grad_phi_fwd(a, sW, my, y, m1, m2, pz, g);
     const float nrm = sqrtf(g[0] * g[0] + g[1] * g[1] + g[2] * g[2]);
     if (ok) lsum += (1.f - nrm) * (1.f - nrm);
-    if (!bwd) continue;
     float av[3] = {0.f, 0.f, 0.f};
-    if (ok && nrm > 0.f) {
+    if (bwd && ok && nrm > 0.f) {
       const float sc = k_eik * (1.f - nrm) / nrm;
 #pragma unroll
       for (int c = 0; c < 3; ++c) av[c] = sc * g[c];
     }
-    grad_phi_adjoint(a, sW, sG, wr, my, lane, y, ok, av, m1, m2, pz);
+    if (a.eik != nullptr && ok) {
+      // the deferred grid term's record: q_l = p_l / v_l, then (a, 0) (zero adjoint without grad);
+      // the render kernel's backward scatter adds q_l (a . dw_c/df) to the corners it reduces
+      float4* rec = a.eik + sidx;
+#pragma unroll
+      for (int l = 0; l < kLevels; ++l)
+        rec[l * S] = f4scale(make_float4(pz[4 * l], pz[4 * l + 1], pz[4 * l + 2], pz[4 * l + 3]), a.g.inv_voxel[l]);
+      rec[4 * S] = make_float4(av[0], av[1], av[2], 0.f);
+    }
+    if (!bwd) continue;
+    grad_phi_adjoint(a, sW, sG, wr, my, lane, y, ok && a.eik == nullptr, av, m1, m2, pz);
   }
   const float v = warp_sum(lsum);
   if (lane == 0) atomicAdd(sL, v);
@@ -777,7 +787,7 @@ size_t gs_paper_part_floats(int num_sms) { return (size_t)gs_paper_part_rows(num
 gs_status gs_launch_paper(const gs_ctx* ctx, const float* theta, const gs_batch* b, const float* dloss, float* grad,
                           float* loss, float* rgb_hat, float* d_hat, float* wsum, int mode, cudaStream_t st) {
   using namespace paper;
-  Args a;
+  Args a{};
   a.g = ctx->grid;
   a.colour_off = ctx->colour_off;
   a.theta = theta;
@@ -860,7 +870,7 @@ gs_status gs_launch_paper_eikonal(const gs_ctx* ctx, const float* theta, const g
       return GS_ERR_CUDA;
     attr = true;
   }
-  Args a;
+  Args a{};
   a.g = ctx->grid;
   a.colour_off = ctx->colour_off;
   a.theta = theta;
@@ -875,6 +885,7 @@ gs_status gs_launch_paper_eikonal(const gs_ctx* ctx, const float* theta, const g
   a.N = b->N;
   a.loss_part = ctx->paper_loss_part;
   a.mlp_part = ctx->paper_part;
+  a.eik = reinterpret_cast<float4*>(b->eik);
   const int ctas = kCtasPerSm * ctx->num_sms;  // the render kernel's partial rows (calls do not overlap)
   paper_eikonal_kernel<<<ctas, kThreads, kSmemBytes, st>>>(a);
   if (cudaPeekAtLastError() != cudaSuccess) return GS_ERR_CUDA;
@@ -896,7 +907,7 @@ gs_status gs_launch_paper_query_backward(const gs_ctx* ctx, const float* theta, 
       return GS_ERR_CUDA;
     attr = true;
   }
-  Args a;
+  Args a{};
   a.g = ctx->grid;
   a.colour_off = ctx->colour_off;
   a.theta = theta;

@@ -42,6 +42,8 @@ gs_status gs_launch_paper_tc(const gs_ctx* ctx, const float* theta, const gs_bat
   a.R = b->R;
   a.N = b->N;
   a.status = ctx->status;
+  a.eik = reinterpret_cast<const float4*>(b->eik);
+  a.eik_stride = (long long)b->R * b->N;
   switch ((b->N + 31) / 32) {
     case 1: return ptc::launch_paper_tc<1>(a, mode, ctas, st);
     case 2: return ptc::launch_paper_tc<2>(a, mode, ctas, st);

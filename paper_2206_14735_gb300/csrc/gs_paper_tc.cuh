@@ -18,8 +18,9 @@
 // Operands are split into three bfloat16 parts with the six leading part products accumulated
 // in FP32 (two parts and three products in the weight-gradient products), as in the compact
 // kernel's FP32 form.  Activations are recomputed (no store).  Grid gradients: the geometry
-// levels through the compact kernel's scatter, the colour grid (6 floats per finest-level
-// vertex) with one 16-byte and one 8-byte reduction per corner.
+// levels through the compact kernel's scatter (which also adds the deferred Eikonal records of
+// the free-space samples), the colour grid (6 floats per finest-level vertex) with one 16-byte
+// and one 8-byte reduction per corner; samples whose vectors are exactly zero issue none.
 #pragma once
 #include "gs_paper.cuh"
 #include "gs_render_tc.cuh"
@@ -87,6 +88,10 @@ struct PaperTcArgs {
   float *loss_part, *mlp_part;  // this kernel's partial rows, one per CTA
   int R, N;
   int* status;  // bit 16: a tensor-core phase did not complete
+  // deferred Eikonal records ([5][R N] float4 planes) of the free-space samples, added to their
+  // geometry scatter; nullptr: none
+  const float4* eik;
+  long long eik_stride;
 };
 
 __device__ __forceinline__ void red_add_f2(float* p, float a, float b) {
@@ -163,6 +168,15 @@ __device__ __forceinline__ void scatter_colour(const PaperTcArgs& a, const float
       red_add_f4(reinterpret_cast<float4*>(p + 2), make_float4(e[2], e[3], e[4], e[5]));
     }
   }
+}
+
+template <int N>
+__device__ __forceinline__ int pick_cls(const int (&v)[N], int j) {
+  int c = v[0];
+#pragma unroll
+  for (int q = 1; q < N; ++q)
+    if (q == j) c = v[q];
+  return c;
 }
 
 // rows written by every thread of the group -> thread 0 issues `mma` and commits to G.mbar;
@@ -712,9 +726,11 @@ __global__ void __launch_bounds__(kPThreads, 1) paper_tc_kernel(const __grid_con
       tc::tmem_ld16(lane_addr(G, cCb, warp_g), du);
       tc::tmem_ld_wait();
       dw_wait(G);  // the scatter's staging rows overwrite the tiles
-      scatter_dz(a.g, a.grad, x, dz, valid, reinterpret_cast<float*>(Ag) + warp_g * kScatterStage);
+      const float4* er = a.eik != nullptr && valid && pick_cls(clv, j) == CLS_FS ? a.eik + (size_t)rr * N + si : nullptr;
+      scatter_dz(a.g, a.grad, x, dz, valid, reinterpret_cast<float*>(Ag) + warp_g * kScatterStage, er, a.eik_stride);
       if (valid) {
-        scatter_colour(a, x, du);
+        if (du[0] != 0.f || du[1] != 0.f || du[2] != 0.f || du[3] != 0.f || du[4] != 0.f || du[5] != 0.f)
+          scatter_colour(a, x, du);  // a zero vector adds nothing
         if (a.dz_out != nullptr) {  // the sample's record: dz (16), dcf (6), d direction (3), zeros (7)
           float4* rec = reinterpret_cast<float4*>(a.dz_out + ((size_t)rr * N + si) * 32);
 #pragma unroll

@@ -446,7 +446,10 @@ __device__ __forceinline__ void scatter_dz(const GridDesc& g, float* grad, const
     }
     float4* gl = reinterpret_cast<float4*>(grad + g.off[l]);
     if (l >= 2) {
-      if (valid) {
+      // a zero vector adds nothing: samples whose dL/dz_l is exactly zero (saturated opacity and
+      // no active loss term) issue no reductions at the fine levels
+      const bool nz = g4.x != 0.f || g4.y != 0.f || g4.z != 0.f || g4.w != 0.f || er != nullptr;
+      if (valid && nz) {
 #pragma unroll
         for (int k = 0; k < 8; ++k) {
           float4 cv = f4scale(g4, wc[k]);

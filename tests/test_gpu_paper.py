@@ -258,6 +258,30 @@ def test_paper_eikonal_parity(cube_paper, R):
     assert np.abs(g[CUBE_P.colour_offset():c["p"].n_grid]).max() == 0
 
 
+def test_paper_deferred_eikonal_grid_term(cube_paper):
+    """With batch->eik the Eikonal call writes each free-space sample's (p_l / v_l, a) and the
+    fused forward/backward adds the grid term to the geometry corners it reduces: the two
+    calls' gradient is the oracle's step gradient plus its Eikonal gradient."""
+    c = cube_paper
+    p = c["p"]
+    bt, dropped = drop_kink_rays(p, c["theta"], c["bt"])
+    assert dropped <= 0.05 * len(c["bt"]["D"]) + 1
+    st_ref = oc.step(p.cfg, c["theta"], bt, c["sm"])
+    ref_l, ref_g, n_fs, gnorm = oc.eikonal(p.cfg, c["theta"], bt)
+    assert n_fs > 1000
+    batch = upload_oracle_batch(bt, c["sm"], c["sm"]["n_valid"][0])
+    batch.eik = torch.full((5, batch.R, batch.N, 4), float("nan"), device="cuda")
+    th = _padded(c["theta"])
+    loss, grad, eik = torch.empty(6, device="cuda"), torch.zeros_like(th), torch.zeros(1, device="cuda")
+    p.ctx.eikonal(th, batch, loss=eik, grad=grad)
+    p.ctx.forward_backward(th, batch, None, loss, grad)
+    torch.cuda.synchronize()
+    p.ctx.sync_status()
+    _check_loss(loss.cpu().numpy().astype(np.float64), st_ref["loss"])
+    assert abs(float(eik.item()) - ref_l) <= _eik_tol(ref_l, gnorm)
+    assert_grad_close(p, grad.cpu().numpy()[:len(c["theta"])], st_ref["grad"] + ref_g)
+
+
 def test_paper_full_method_step():
     """The paper's method with its own architecture: the hierarchical importance sampler
     (96 coarse + 3 x 12, Sec. 4) on the GPU against the oracle, then the fused step and the
