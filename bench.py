@@ -129,7 +129,7 @@ def step_config(w, args, world, n_frames):
                 "fallback_samples_per_ray": w.n_samples, "pretrain_steps": args.prop_pretrain,
                 "parallelism": f"replicas{world}"}
     paper = w.arch == "paper"
-    recompute = args.recompute or paper
+    recompute = args.recompute
     pipelined = w.imp_coarse == 0 and not args.no_pipeline and not args.poses
     return {"workload": w.name, "rays": w.rays, "samples_per_ray": w.n_samples, "smooth_points": w.n_smooth,
             "params": w.layout()[2], "grid_params": w.layout()[1], "frames": n_frames,
@@ -170,9 +170,7 @@ def run_ours(args):
     fr = sg.make_frames(w, n_frames=args.frames, with_gt=args.sampler_report > 0)
     t_frames = time.time() - t0
     paper = w.arch == "paper"
-    # the paper's architecture recomputes by default: its CUDA-core kernel measured faster
-    # recomputing (2.58 ms per render call) than writing and reading 624 B per sample (2.76 ms)
-    recompute = args.recompute or paper
+    recompute = args.recompute
     ctx = gs.Context(w, store_activations=not recompute)
     dfr = gs.DeviceFrames(fr.rgb, fr.depth, fr.c2w, fr.fx, fr.fy, fr.cx, fr.cy)
     theta0 = sg.init_params(w)

@@ -81,8 +81,8 @@ typedef enum {
                              of 32.  Supported by gs_sample_rays, gs_sample_importance, gs_proposal_sample,
                              gs_proposal_backward, gs_forward, gs_backward, gs_forward_backward, gs_eikonal,
                              gs_query_sdf, gs_query_sdf_backward, gs_extract_mesh, gs_pose_apply,
-                             gs_pose_backward and gs_adam_step (FP32; store_activations allocates
-                             nothing: the backward passes recompute both decoders on the tensor cores);
+                             gs_pose_backward and gs_adam_step (FP32; store_activations keeps 156 floats
+                             per sample: z, W_beta(x), phi, c and the four hidden layers);
                              gs_forward_backward_noalloc returns GS_ERR_UNSUPPORTED */
 
 /* Sample classes written by gs_sample_rays (Sec. 3.3): */
@@ -110,8 +110,8 @@ typedef struct gs_config {
                                  activations (z, ReLU outputs, SDF, geometric feature, colour:
                                  100 floats = 400 bytes per sample, max_rays x N samples, in
                                  float4 planes of four fields each, allocated by gs_create;
-                                 GS_ARCH_PAPER: nothing is stored, backward passes recompute)
-                                 and every backward pass reads them instead of gathering
+                                 GS_ARCH_PAPER: 156 floats) and every backward pass reads
+                                 them instead of gathering
                                  again and recomputing the decoders; 0: the backward pass
                                  recomputes them (no memory) */
   int32_t prop_samples;       /* learned proposal sampler (not part of the paper): samples per

@@ -168,8 +168,10 @@ gs_status gs_create(const gs_config* cfg, gs_ctx** out) {
       (cfg->arch == GS_ARCH_PAPER &&
        (cudaMalloc(&c->paper_part, sizeof(float) * gs_paper_part_floats(c->num_sms)) != cudaSuccess ||
         cudaMalloc(&c->paper_loss_part, sizeof(float) * kLossPad * gs_paper_part_rows(c->num_sms)) != cudaSuccess)) ||
-      (cfg->store_activations && cfg->arch != GS_ARCH_PAPER &&
-       cudaMalloc(&c->store, c->store_bytes = (size_t)cfg->max_rays * c->max_n * kStoreFloatsPerSample *
+      (cfg->store_activations &&
+       cudaMalloc(&c->store, c->store_bytes = (size_t)cfg->max_rays * c->max_n *
+                                             (cfg->arch == GS_ARCH_PAPER ? kPaperStoreFloatsPerSample
+                                                                         : kStoreFloatsPerSample) *
                                              sizeof(float)) !=
            cudaSuccess)) {
     gs_status s = cuda_fail(nullptr, "gs_create: workspace allocation");

@@ -44,6 +44,8 @@ gs_status gs_launch_paper_tc(const gs_ctx* ctx, const float* theta, const gs_bat
   a.status = ctx->status;
   a.eik = reinterpret_cast<const float4*>(b->eik);
   a.eik_stride = (long long)b->R * b->N;
+  a.store = ctx->store;
+  a.store_stride = (long long)ctx->cfg.max_rays * ctx->max_n;
   switch ((b->N + 31) / 32) {
     case 1: return ptc::launch_paper_tc<1>(a, mode, ctas, st);
     case 2: return ptc::launch_paper_tc<2>(a, mode, ctas, st);

@@ -17,7 +17,8 @@
 //            thread; the output layers' gradients on CUDA cores.
 // Operands are split into three bfloat16 parts with the six leading part products accumulated
 // in FP32 (two parts and three products in the weight-gradient products), as in the compact
-// kernel's FP32 form.  Activations are recomputed (no store).  Grid gradients: the geometry
+// kernel's FP32 form.  Activations are stored by the forward pass (156 floats per sample) and
+// read back by the reverse pass, or recomputed there (no store).  Grid gradients: the geometry
 // levels through the compact kernel's scatter (which also adds the deferred Eikonal records of
 // the free-space samples), the colour grid (6 floats per finest-level vertex) with one 16-byte
 // and one 8-byte reduction per corner; samples whose vectors are exactly zero issue none.
@@ -92,7 +93,16 @@ struct PaperTcArgs {
   // geometry scatter; nullptr: none
   const float4* eik;
   long long eik_stride;
+  // stored activations: field f of sample s = rr N + si in component f % 4 of
+  // ((float4*)store)[(f / 4) store_stride + s]; written by forward passes, read by backward
+  // passes in place of the gathers and the two recomputed phases; nullptr: recompute
+  float* store;
+  long long store_stride;
 };
+
+// fields of one stored sample: z[16] | cf[6], phi, 0 | c[3], 0 | a1[32] | r1[32] | a2[32] | r2[32]
+constexpr int kQz = 0, kQu = 16, kQc = 24, kQa1 = 28, kQr1 = 60, kQa2 = 92, kQr2 = 124, kQFields = 156;
+static_assert(kQFields == kPaperStoreFloatsPerSample, "the store holds every field");
 
 __device__ __forceinline__ void red_add_f2(float* p, float a, float b) {
   asm volatile("red.global.add.v2.f32 [%0], {%1, %2};" ::"l"(p), "f"(a), "f"(b) : "memory");
@@ -328,6 +338,23 @@ __global__ void __launch_bounds__(kPThreads, 1) paper_tc_kernel(const __grid_con
       const int si = 32 * j + lane;
       const bool valid = has_ray && si < N;
       const float t = pick_tc(tt, j);
+      float4* sp = a.store != nullptr ? reinterpret_cast<float4*>(a.store) + (size_t)rr * N + si : nullptr;
+      const long long ss = a.store_stride;
+      if (!FWD && sp != nullptr) {  // stored by the forward pass: phi and c only
+        const float4 u4 = valid ? sp[(kQu / 4 + 1) * ss] : make_float4(0.f, 0.f, 0.f, 0.f);
+        const float4 c4 = valid ? sp[(kQc / 4) * ss] : make_float4(0.f, 0.f, 0.f, 0.f);
+#pragma unroll
+        for (int q = 0; q < NCH; ++q)
+          if (q == j) {
+            ph[q] = u4.z;
+            col[q][0] = c4.x;
+            col[q][1] = c4.y;
+            col[q][2] = c4.z;
+          }
+        continue;
+      }
+      const bool put = FWD && sp != nullptr && valid;
+      float cfs[8];  // the colour features, phi and a zero: stored fields kQu..kQu + 7
       {
         float z[kZ], u[16];
         if (valid) {
@@ -347,6 +374,9 @@ __global__ void __launch_bounds__(kPThreads, 1) paper_tc_kernel(const __grid_con
         dw_wait(G);  // the previous chunk's weight-gradient products have read the tiles
         store_row_planes<3, 16, kAP>(Ag, row, z);
         store_row_planes<3, 16, kAP>(Ac, row, u);
+        if (put) put_fields<kQz, 16>(sp, ss, z);
+#pragma unroll
+        for (int k = 0; k < kC; ++k) cfs[k] = u[k];
       }
       phase2(G, [&] {
         mma3<32, 16>(G.tcol + cG, Ag, wt + tOff(0));
@@ -360,11 +390,13 @@ __global__ void __launch_bounds__(kPThreads, 1) paper_tc_kernel(const __grid_con
 #pragma unroll
         for (int k = 0; k < 32; ++k) v[k] = fmaxf(v[k] + sc[sc_gb1 + k], 0.f);
         store_row_planes<3, 32, kAP>(Ag, row, v);
+        if (put) put_fields<kQa1, 32>(sp, ss, v);
         tc::tmem_ld32(lane_addr(G, cC, warp_g), v);
         tc::tmem_ld_wait();
 #pragma unroll
         for (int k = 0; k < 32; ++k) v[k] = fmaxf(v[k] + sc[sc_cb1 + k], 0.f);
         store_row_planes<3, 32, kAP>(Ac, row, v);
+        if (put) put_fields<kQr1, 32>(sp, ss, v);
       }
       phase2(G, [&] {
         mma3<32, 32>(G.tcol + cG, Ag, wt + tOff(2));
@@ -378,18 +410,30 @@ __global__ void __launch_bounds__(kPThreads, 1) paper_tc_kernel(const __grid_con
         tc::tmem_ld_wait();
         phi = sc[sc_gb3];
 #pragma unroll
-        for (int k = 0; k < 32; ++k) phi = fmaf(sc[sc_gw3 + k], fmaxf(v[k] + sc[sc_gb2 + k], 0.f), phi);
+        for (int k = 0; k < 32; ++k) {
+          v[k] = fmaxf(v[k] + sc[sc_gb2 + k], 0.f);
+          phi = fmaf(sc[sc_gw3 + k], v[k], phi);
+        }
+        if (put) put_fields<kQa2, 32>(sp, ss, v);
         tc::tmem_ld32(lane_addr(G, cC, warp_g), v);
         tc::tmem_ld_wait();
         float pre[3] = {sc[sc_cb3], sc[sc_cb3 + 1], sc[sc_cb3 + 2]};
 #pragma unroll
         for (int k = 0; k < 32; ++k) {
-          const float r2 = fmaxf(v[k] + sc[sc_cb2 + k], 0.f);
+          v[k] = fmaxf(v[k] + sc[sc_cb2 + k], 0.f);
 #pragma unroll
-          for (int i = 0; i < 3; ++i) pre[i] = fmaf(sc[sc_cW3 + 32 * i + k], r2, pre[i]);
+          for (int i = 0; i < 3; ++i) pre[i] = fmaf(sc[sc_cW3 + 32 * i + k], v[k], pre[i]);
         }
+        if (put) put_fields<kQr2, 32>(sp, ss, v);
 #pragma unroll
         for (int i = 0; i < 3; ++i) c3[i] = sigmoidf_(pre[i]);
+        if (put) {
+          cfs[6] = phi;
+          cfs[7] = 0.f;
+          put_fields<kQu, 8>(sp, ss, cfs);
+          const float c4[4] = {c3[0], c3[1], c3[2], 0.f};
+          put_fields<kQc, 4>(sp, ss, c4);
+        }
       }
 #pragma unroll
       for (int q = 0; q < NCH; ++q)
@@ -548,7 +592,7 @@ __global__ void __launch_bounds__(kPThreads, 1) paper_tc_kernel(const __grid_con
       dphi[j] = d;
     }
 
-    // ================= reverse, chunk by chunk: F1, F2 again, then B1, B2 and the scatter =================
+    // ================= reverse, chunk by chunk: the stored activations (or F1, F2 again), B1, B2, scatter =================
 #pragma unroll 1
     for (int j = 0; j < NCH && alive; ++j) {
       const int si = 32 * j + lane;
@@ -556,76 +600,104 @@ __global__ void __launch_bounds__(kPThreads, 1) paper_tc_kernel(const __grid_con
       const float t = pick_tc(tt, j);
       float x[3];
       sample_pos(o, r, t, x);
+      const float4* spr = a.store != nullptr ? reinterpret_cast<const float4*>(a.store) + (size_t)rr * N + si : nullptr;
       float z[kZ], u[16];
-      if (valid) {
-        gather(a, x, z, u);
-      } else {
+      uint32_t m1 = 0, mr1 = 0, m2 = 0, mr2 = 0;
+      // output layers on CUDA cores: [dpre | dphi | a2 | r2] staged per lane in the A tiles
+      float* ost = reinterpret_cast<float*>(Ag) + warp_g * (32 * kOr);
+      float* orow = ost + lane * kOr;
+      if (spr != nullptr) {  // stored by the forward pass: no gather and no forward phases
+        const long long ss = a.store_stride;
+        dw_wait(G);  // the previous chunk's weight-gradient products have read the tiles
+        get_fields<kQz, 16>(spr, ss, valid, z);
+        {
+          float c8[8];
+          get_fields<kQu, 8>(spr, ss, valid, c8);
 #pragma unroll
-        for (int k = 0; k < kZ; ++k) z[k] = 0.f;
-#pragma unroll
-        for (int k = 0; k < kC; ++k) u[k] = 0.f;
-      }
-#pragma unroll
-      for (int q = 0; q < 3; ++q) u[kC + q] = dvw[q];
-#pragma unroll
-      for (int k = kU; k < 16; ++k) u[k] = 0.f;
-      dw_wait(G);
-      store_row_planes<3, 16, kAP>(Ag, row, z);
-      store_row_planes<3, 16, kAP>(Ac, row, u);
-      phase2(G, [&] {
-        mma3<32, 16>(G.tcol + cG, Ag, wt + tOff(0));
-        mma3<32, 16>(G.tcol + cC, Ac, wt + tOff(1));
-      }, [] {}, false);
-      if (!(alive = mma_phase_wait(G))) break;
-      uint32_t m1 = 0, mr1 = 0;
-      {
+          for (int k = 0; k < kC; ++k) u[k] = c8[k];
+        }
         float v[32], pb[40];
-        tc::tmem_ld32(lane_addr(G, cG, warp_g), v);
-        tc::tmem_ld_wait();
+        get_fields<kQa1, 32>(spr, ss, valid, v);
 #pragma unroll
         for (int k = 0; k < 32; ++k) {
-          v[k] = fmaxf(v[k] + sc[sc_gb1 + k], 0.f);
           m1 |= (v[k] > 0.f ? 1u : 0u) << k;
           pb[k] = v[k];
         }
         pb[32] = 1.f;  // ones column: the bias gradient lands in row 32
 #pragma unroll
         for (int k = 33; k < 40; ++k) pb[k] = 0.f;
-        store_row_planes<3, 32, kAP>(Ag, row, v);
         store_row_planes<2, 40, kBP>(Bg, row, pb);
-        tc::tmem_ld32(lane_addr(G, cC, warp_g), v);
-        tc::tmem_ld_wait();
+        get_fields<kQr1, 32>(spr, ss, valid, v);
 #pragma unroll
         for (int k = 0; k < 32; ++k) {
-          v[k] = fmaxf(v[k] + sc[sc_cb1 + k], 0.f);
           mr1 |= (v[k] > 0.f ? 1u : 0u) << k;
           pb[k] = v[k];
         }
-        store_row_planes<3, 32, kAP>(Ac, row, v);
         store_row_planes<2, 40, kBP>(Bc, row, pb);
-      }
-      phase2(G, [&] {
-        mma3<32, 32>(G.tcol + cG, Ag, wt + tOff(2));
-        mma3<32, 32>(G.tcol + cC, Ac, wt + tOff(3));
-      }, [] {}, false);
-      if (!(alive = mma_phase_wait(G))) break;
-      // output layers on CUDA cores: stage [dpre | dphi | a2 | r2] per lane in the A tiles
-      float* ost = reinterpret_cast<float*>(Ag) + warp_g * (32 * kOr);
-      float* orow = ost + lane * kOr;
-      uint32_t m2 = 0, mr2 = 0;
-      float dpre[3];
-      const float dph = valid ? pick_tc(dphi, j) : 0.f;
-      {
-        const float wj = pick_tc(w, j);
-        float cj[3];
+        get_fields<kQa2, 32>(spr, ss, valid, v);
 #pragma unroll
-        for (int i = 0; i < 3; ++i) {
-          cj[i] = col[0][i];
+        for (int k = 0; k < 32; ++k) m2 |= (v[k] > 0.f ? 1u : 0u) << k;
 #pragma unroll
-          for (int q = 1; q < NCH; ++q)
-            if (q == j) cj[i] = col[q][i];
-          dpre[i] = valid ? wj * gc[i] * cj[i] * (1.0f - cj[i]) : 0.f;
+        for (int q = 0; q < 8; ++q)
+          *reinterpret_cast<float4*>(orow + 4 + 4 * q) = make_float4(v[4 * q], v[4 * q + 1], v[4 * q + 2], v[4 * q + 3]);
+        get_fields<kQr2, 32>(spr, ss, valid, v);
+#pragma unroll
+        for (int k = 0; k < 32; ++k) mr2 |= (v[k] > 0.f ? 1u : 0u) << k;
+#pragma unroll
+        for (int q = 0; q < 8; ++q)
+          *reinterpret_cast<float4*>(orow + 36 + 4 * q) = make_float4(v[4 * q], v[4 * q + 1], v[4 * q + 2], v[4 * q + 3]);
+      } else {
+        if (valid) {
+          gather(a, x, z, u);
+        } else {
+#pragma unroll
+          for (int k = 0; k < kZ; ++k) z[k] = 0.f;
+#pragma unroll
+          for (int k = 0; k < kC; ++k) u[k] = 0.f;
         }
+#pragma unroll
+        for (int q = 0; q < 3; ++q) u[kC + q] = dvw[q];
+#pragma unroll
+        for (int k = kU; k < 16; ++k) u[k] = 0.f;
+        dw_wait(G);
+        store_row_planes<3, 16, kAP>(Ag, row, z);
+        store_row_planes<3, 16, kAP>(Ac, row, u);
+        phase2(G, [&] {
+          mma3<32, 16>(G.tcol + cG, Ag, wt + tOff(0));
+          mma3<32, 16>(G.tcol + cC, Ac, wt + tOff(1));
+        }, [] {}, false);
+        if (!(alive = mma_phase_wait(G))) break;
+        {
+          float v[32], pb[40];
+          tc::tmem_ld32(lane_addr(G, cG, warp_g), v);
+          tc::tmem_ld_wait();
+#pragma unroll
+          for (int k = 0; k < 32; ++k) {
+            v[k] = fmaxf(v[k] + sc[sc_gb1 + k], 0.f);
+            m1 |= (v[k] > 0.f ? 1u : 0u) << k;
+            pb[k] = v[k];
+          }
+          pb[32] = 1.f;  // ones column: the bias gradient lands in row 32
+#pragma unroll
+          for (int k = 33; k < 40; ++k) pb[k] = 0.f;
+          store_row_planes<3, 32, kAP>(Ag, row, v);
+          store_row_planes<2, 40, kBP>(Bg, row, pb);
+          tc::tmem_ld32(lane_addr(G, cC, warp_g), v);
+          tc::tmem_ld_wait();
+#pragma unroll
+          for (int k = 0; k < 32; ++k) {
+            v[k] = fmaxf(v[k] + sc[sc_cb1 + k], 0.f);
+            mr1 |= (v[k] > 0.f ? 1u : 0u) << k;
+            pb[k] = v[k];
+          }
+          store_row_planes<3, 32, kAP>(Ac, row, v);
+          store_row_planes<2, 40, kBP>(Bc, row, pb);
+        }
+        phase2(G, [&] {
+          mma3<32, 32>(G.tcol + cG, Ag, wt + tOff(2));
+          mma3<32, 32>(G.tcol + cC, Ac, wt + tOff(3));
+        }, [] {}, false);
+        if (!(alive = mma_phase_wait(G))) break;
         float v[32];
         tc::tmem_ld32(lane_addr(G, cG, warp_g), v);
         tc::tmem_ld_wait();
@@ -634,7 +706,6 @@ __global__ void __launch_bounds__(kPThreads, 1) paper_tc_kernel(const __grid_con
           v[k] = fmaxf(v[k] + sc[sc_gb2 + k], 0.f);
           m2 |= (v[k] > 0.f ? 1u : 0u) << k;
         }
-        *reinterpret_cast<float4*>(orow) = make_float4(dpre[0], dpre[1], dpre[2], dph);
 #pragma unroll
         for (int q = 0; q < 8; ++q)
           *reinterpret_cast<float4*>(orow + 4 + 4 * q) = make_float4(v[4 * q], v[4 * q + 1], v[4 * q + 2], v[4 * q + 3]);
@@ -648,6 +719,24 @@ __global__ void __launch_bounds__(kPThreads, 1) paper_tc_kernel(const __grid_con
 #pragma unroll
         for (int q = 0; q < 8; ++q)
           *reinterpret_cast<float4*>(orow + 36 + 4 * q) = make_float4(v[4 * q], v[4 * q + 1], v[4 * q + 2], v[4 * q + 3]);
+      }
+#pragma unroll
+      for (int q = 0; q < 3; ++q) u[kC + q] = dvw[q];
+#pragma unroll
+      for (int k = kU; k < 16; ++k) u[k] = 0.f;
+      float dpre[3];
+      const float dph = valid ? pick_tc(dphi, j) : 0.f;
+      {
+        const float wj = pick_tc(w, j);
+#pragma unroll
+        for (int i = 0; i < 3; ++i) {
+          float cj = col[0][i];
+#pragma unroll
+          for (int q = 1; q < NCH; ++q)
+            if (q == j) cj = col[q][i];
+          dpre[i] = valid ? wj * gc[i] * cj * (1.0f - cj) : 0.f;
+        }
+        *reinterpret_cast<float4*>(orow) = make_float4(dpre[0], dpre[1], dpre[2], dph);
       }
       __syncwarp();
 #pragma unroll 4
