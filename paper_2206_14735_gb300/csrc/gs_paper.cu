@@ -818,6 +818,13 @@ gs_status gs_launch_paper(const gs_ctx* ctx, const float* theta, const gs_batch*
   int nparts = 0;
   float* first_loss = ctx->paper_loss_part;
   float* first_mlp = ctx->paper_part;
+  // The smoothness kernel is independent of the render kernel (its own partial rows, atomics
+  // into grad): on the side stream, forked before the render launch and joined before the
+  // combine, it runs on the SMs that the render kernel's last ray-quads leave idle.
+  const bool fork = b->R > 0 && b->P > 0;
+  if (fork && (cudaEventRecord(ctx->ev_fork, st) != cudaSuccess ||
+               cudaStreamWaitEvent(ctx->side, ctx->ev_fork, 0) != cudaSuccess))
+    return GS_ERR_CUDA;
   if (b->R > 0) {
     const gs_status s = gs_launch_paper_tc(ctx, theta, b, dloss, grad, rgb_hat, d_hat, wsum, mode,
                                            ctx->paper_loss_part, ctx->paper_part, render_ctas, st);
@@ -834,8 +841,11 @@ gs_status gs_launch_paper(const gs_ctx* ctx, const float* theta, const gs_batch*
     }
     a.loss_part = ctx->paper_loss_part + (size_t)render_ctas * kLossPad;
     a.mlp_part = ctx->paper_part + (size_t)render_ctas * kPart;
-    paper_smooth_kernel<<<kSmoothCtas, kThreads, kSmemBytes, st>>>(a);
+    paper_smooth_kernel<<<kSmoothCtas, kThreads, kSmemBytes, fork ? ctx->side : st>>>(a);
     if (cudaPeekAtLastError() != cudaSuccess) return GS_ERR_CUDA;
+    if (fork && (cudaEventRecord(ctx->ev_join, ctx->side) != cudaSuccess ||
+                 cudaStreamWaitEvent(st, ctx->ev_join, 0) != cudaSuccess))
+      return GS_ERR_CUDA;
     if (b->R == 0) {
       first_loss = a.loss_part;
       first_mlp = a.mlp_part;
