@@ -96,6 +96,8 @@ gs_status gs_launch_paper(const gs_ctx* ctx, const float* theta, const gs_batch*
 gs_status gs_launch_paper_tc(const gs_ctx* ctx, const float* theta, const gs_batch* b, const float* dloss, float* grad,
                              float* rgb_hat, float* d_hat, float* wsum, int mode, float* loss_part, float* mlp_part,
                              int ctas, cudaStream_t st);
+gs_status gs_launch_eikonal_paper_tc(const gs_ctx* ctx, const float* theta, const gs_batch* b, const float* dloss,
+                                     float* loss, float* grad, cudaStream_t st);
 gs_status gs_launch_paper_eikonal(const gs_ctx* ctx, const float* theta, const gs_batch* b, const float* dloss,
                                   float* loss, float* grad, cudaStream_t st);
 gs_status gs_launch_paper_query(const gs_ctx* ctx, const float* theta, const float* x, int P, float* sdf, float* grad,

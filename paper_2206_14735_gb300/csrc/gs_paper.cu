@@ -75,7 +75,6 @@ struct Args {
   int R, N, P, mode;
   float lam[5];
   float kappa_fs;
-  float4* eik;  // Eikonal call: deferred grid term, [5][R N] records of the free-space samples (or nullptr)
 };
 
 // lane j (row j of a 32-row matrix) sums delta_s[j] * act_s[k] over the warp's 32 staged
@@ -403,92 +402,6 @@ __global__ void __launch_bounds__(kThreads, 1) paper_smooth_kernel(Args a) {
   write_partials(a, sG, sL);
 }
 
-// Eikonal term (Sec. 3.3 Eq. eikonal_loss) on the batch's free-space samples, for the
-// two-hidden-layer geometry decoder: l = (1 - |g|)^2 with g = grad_x phi at x = o + d r, and
-// (grad != nullptr) its second-order adjoint a = dloss (-2 / |S_fs|) (1 - |g|) g / |g| (0 where
-// |g| = 0).  Each warp packs the free-space samples of its share of the batch into a queue
-// and evaluates 32 of them at a time, one per lane.  Loss sums go to this CTA's partial row.
-__global__ void __launch_bounds__(kThreads, 1) paper_eikonal_kernel(Args a) {
-  extern __shared__ __align__(16) float smem[];
-  float* sW = smem;
-  float* sG = sW + kSm;
-  float* sL = sG + kSm;
-  float* rows = sL + 8;
-  __shared__ long long queue[kWarps][64];
-  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-  float* wr = rows + wid * 32 * kRow;
-  float* my = wr + lane * kRow;
-  long long* q = queue[wid];
-  copy_decoder(a.theta + a.g.n_grid, sW);
-  for (int i = threadIdx.x; i < kSm; i += blockDim.x) sG[i] = 0.f;
-  if (threadIdx.x < 8) sL[threadIdx.x] = 0.f;
-  __syncthreads();
-  const bool bwd = a.grad != nullptr;
-  const int n_fs = a.counts[2];
-  const float k_eik = n_fs > 0 ? a.dloss[0] * -2.0f / (float)n_fs : 0.0f;
-  const long long S = (long long)a.R * a.N;
-  const long long stride = (long long)gridDim.x * kWarps * 32;
-  long long base = ((long long)blockIdx.x * kWarps + wid) * 32;
-  int queued = 0;
-  float lsum = 0.f;
-#pragma unroll 1
-  for (;;) {
-    while (queued < 32 && base < S) {  // warp-uniform: queued and base are the same in every lane
-      const long long sidx = base + lane;
-      const bool fs = sidx < S && a.cls[sidx] == CLS_FS;
-      const unsigned bal = __ballot_sync(0xffffffffu, fs);
-      if (fs) q[queued + __popc(bal & ((1u << lane) - 1u))] = sidx;
-      queued += __popc(bal);
-      base += stride;
-    }
-    __syncwarp();
-    if (queued == 0) break;
-    const int take = queued < 32 ? queued : 32;
-    const bool ok = lane < take;
-    const long long sidx = ok ? q[lane] : 0;
-    __syncwarp();
-    if (lane + 32 < queued) q[lane] = q[lane + 32];  // at most 31 left over
-    queued -= take;
-    float y[3] = {0.f, 0.f, 0.f};
-    if (ok) {
-      const long long ray = sidx / a.N;
-      float o[3], r[3];
-#pragma unroll
-      for (int c = 0; c < 3; ++c) {
-        o[c] = a.o[3 * ray + c];
-        r[c] = a.r[3 * ray + c];
-      }
-      sample_pos(o, r, a.t[sidx], y);
-    }
-    unsigned m1, m2;
-    float pz[kZ], g[3];
-    grad_phi_fwd(a, sW, my, y, m1, m2, pz, g);
-    const float nrm = sqrtf(g[0] * g[0] + g[1] * g[1] + g[2] * g[2]);
-    if (ok) lsum += (1.f - nrm) * (1.f - nrm);
-    float av[3] = {0.f, 0.f, 0.f};
-    if (bwd && ok && nrm > 0.f) {
-      const float sc = k_eik * (1.f - nrm) / nrm;
-#pragma unroll
-      for (int c = 0; c < 3; ++c) av[c] = sc * g[c];
-    }
-    if (a.eik != nullptr && ok) {
-      // the deferred grid term's record: q_l = p_l / v_l, then (a, 0) (zero adjoint without grad);
-      // the render kernel's backward scatter adds q_l (a . dw_c/df) to the corners it reduces
-      float4* rec = a.eik + sidx;
-#pragma unroll
-      for (int l = 0; l < kLevels; ++l)
-        rec[l * S] = f4scale(make_float4(pz[4 * l], pz[4 * l + 1], pz[4 * l + 2], pz[4 * l + 3]), a.g.inv_voxel[l]);
-      rec[4 * S] = make_float4(av[0], av[1], av[2], 0.f);
-    }
-    if (!bwd) continue;
-    grad_phi_adjoint(a, sW, sG, wr, my, lane, y, ok && a.eik == nullptr, av, m1, m2, pz);
-  }
-  const float v = warp_sum(lsum);
-  if (lane == 0) atomicAdd(sL, v);
-  __syncthreads();
-  write_partials(a, sG, sL);
-}
-
 // phi(x) and (grad != nullptr) grad_x phi(x) of the geometry decoder, one thread per point
 __global__ void __launch_bounds__(128) paper_query_kernel(GridDesc g, const float* __restrict__ theta,
                                                           const float* __restrict__ xq, int P, float* sdf,
@@ -701,11 +614,9 @@ __global__ void __launch_bounds__(kThreads, 1) paper_query_backward_kernel(Args 
       __syncwarp();
       outer_rows<kZ, true>(wr, fA1, fZ, sG + S_gW1, sG + S_gb1, lane);
       if (ok && dp != 0.f) {  // dz = gW1^T dy1 into the four levels
-        float dz[kZ], dcf[kC];
+        float dz[kZ];
 #pragma unroll
         for (int q = 0; q < kZ; ++q) dz[q] = 0.f;
-#pragma unroll
-        for (int q = 0; q < kC; ++q) dcf[q] = 0.f;
 #pragma unroll 4
         for (int j = 0; j < kH; ++j) {
 #pragma unroll
@@ -727,7 +638,6 @@ __global__ void __launch_bounds__(kThreads, 1) paper_query_backward_kernel(Args 
 #pragma unroll
           for (int k = 0; k < 8; ++k) atomicAdd(gl + c.vtx + corner_offset(a.g, l, k), f4scale(d4, wv[k]));
         }
-        (void)dcf;
       }
       __syncwarp();
     }
@@ -741,8 +651,7 @@ __global__ void __launch_bounds__(kThreads, 1) paper_query_backward_kernel(Args 
 // fs: |S_fs|, smooth: valid points) with the weighted total
 __global__ void __launch_bounds__(256) paper_combine_kernel(const float* loss_part, const float* mlp_part,
                                                             int nparts, const int* counts, int R, float l0, float l1,
-                                                            float l2, float l3, float l4, float* loss, float* gmlp,
-                                                            int eikonal) {
+                                                            float l2, float l3, float l4, float* loss, float* gmlp) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (gmlp && i < GS_PAPER_MLP_PARAMS) {
     float sacc = 0.f;
@@ -759,9 +668,7 @@ __global__ void __launch_bounds__(256) paper_combine_kernel(const float* loss_pa
     for (int k = 0; k < 5; ++k)
 #pragma unroll
       for (int off = 16; off > 0; off >>= 1) sk[k] += __shfl_xor_sync(0xffffffffu, sk[k], off);
-    if (lane == 0 && eikonal) {  // L_eik: the first entry of each row, over |S_fs|
-      loss[0] = counts[2] > 0 ? (float)(sk[0] / (double)counts[2]) : 0.f;
-    } else if (lane == 0) {
+    if (lane == 0) {
       const double den[5] = {(double)R, (double)counts[0], (double)counts[1], (double)counts[2], (double)counts[3]};
       const double lam[5] = {l0, l1, l2, l3, l4};
       double tot = 0.0;
@@ -862,48 +769,13 @@ gs_status gs_launch_paper(const gs_ctx* ctx, const float* theta, const gs_batch*
   const float* l = ctx->cfg.lam;
   paper_combine_kernel<<<(GS_PAPER_MLP_PARAMS + 255) / 256, 256, 0, st>>>(
       first_loss, first_mlp, nparts, b->counts, b->R, l[0], l[1], l[2], l[3], l[4], (mode & 1) ? loss : nullptr,
-      (mode & 2) ? grad + ctx->grid.n_grid : nullptr, 0);
+      (mode & 2) ? grad + ctx->grid.n_grid : nullptr);
   return cudaPeekAtLastError() == cudaSuccess ? GS_OK : GS_ERR_CUDA;
 }
 
 gs_status gs_launch_paper_eikonal(const gs_ctx* ctx, const float* theta, const gs_batch* b, const float* dloss,
                                   float* loss, float* grad, cudaStream_t st) {
-  using namespace paper;
-  if ((long long)b->R * b->N == 0) {
-    if (loss && cudaMemsetAsync(loss, 0, sizeof(float), st) != cudaSuccess) return GS_ERR_CUDA;
-    return GS_OK;
-  }
-  static bool attr = false;
-  if (!attr) {
-    if (cudaFuncSetAttribute(paper_eikonal_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmemBytes) !=
-        cudaSuccess)
-      return GS_ERR_CUDA;
-    attr = true;
-  }
-  Args a{};
-  a.g = ctx->grid;
-  a.colour_off = ctx->colour_off;
-  a.theta = theta;
-  a.grad = grad;
-  a.o = b->origin;
-  a.r = b->dir;
-  a.t = b->t;
-  a.cls = b->cls;
-  a.counts = b->counts;
-  a.dloss = dloss;
-  a.R = b->R;
-  a.N = b->N;
-  a.loss_part = ctx->paper_loss_part;
-  a.mlp_part = ctx->paper_part;
-  a.eik = reinterpret_cast<float4*>(b->eik);
-  const int ctas = kCtasPerSm * ctx->num_sms;  // the render kernel's partial rows (calls do not overlap)
-  paper_eikonal_kernel<<<ctas, kThreads, kSmemBytes, st>>>(a);
-  if (cudaPeekAtLastError() != cudaSuccess) return GS_ERR_CUDA;
-  const float* l = ctx->cfg.lam;
-  paper_combine_kernel<<<(GS_PAPER_MLP_PARAMS + 255) / 256, 256, 0, st>>>(
-      ctx->paper_loss_part, ctx->paper_part, ctas, b->counts, b->R, l[0], l[1], l[2], l[3], l[4], loss,
-      grad ? grad + ctx->grid.n_grid : nullptr, 1);
-  return cudaPeekAtLastError() == cudaSuccess ? GS_OK : GS_ERR_CUDA;
+  return gs_launch_eikonal_paper_tc(ctx, theta, b, dloss, loss, grad, st);  // csrc/gs_eikonal.cu
 }
 
 gs_status gs_launch_paper_query_backward(const gs_ctx* ctx, const float* theta, const float* x, int P,
@@ -931,7 +803,7 @@ gs_status gs_launch_paper_query_backward(const gs_ctx* ctx, const float* theta, 
   const float* l = ctx->cfg.lam;
   paper_combine_kernel<<<(GS_PAPER_MLP_PARAMS + 255) / 256, 256, 0, st>>>(
       ctx->paper_loss_part, ctx->paper_part, ctas, nullptr, 0, l[0], l[1], l[2], l[3], l[4], nullptr,
-      grad + ctx->grid.n_grid, 0);
+      grad + ctx->grid.n_grid);
   return cudaPeekAtLastError() == cudaSuccess ? GS_OK : GS_ERR_CUDA;
 }
 
