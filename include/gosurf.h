@@ -378,7 +378,10 @@ gs_status gs_voxel_index(gs_ctx* ctx, const float* x, int32_t P, int64_t* out, v
 gs_status gs_forward_backward_noalloc(const gs_config* cfg, const float* theta, const gs_batch* batch,
                                       const float* dloss, float* loss, float* grad, void* stream);
 
-/* Synchronises the context's last stream and reports device-side check failures. */
+/* Synchronises the context's last stream and reports device-side check failures: GS_ERR_DEVICE
+ * when a kernel's bounded wait for its tensor-core products ran out in an earlier call (the
+ * kernel then stopped early and that call's outputs are incomplete); gs_last_error names the
+ * kernel(s).  The status word is not cleared: the context stays in error. */
 gs_status gs_sync_status(gs_ctx* ctx);
 
 /* Host: message of the last error raised through this context ("" if none). */

@@ -505,7 +505,15 @@ gs_status gs_sync_status(gs_ctx* ctx) {
   int h = 0;
   if (cudaMemcpy(&h, ctx->status, sizeof(int), cudaMemcpyDeviceToHost) != cudaSuccess)
     return cuda_fail(ctx, "gs_sync_status");
-  if (h != 0) return fail(ctx, GS_ERR_DEVICE, "a device-side check failed");
+  if (h != 0) {
+    std::string m = "a bounded wait for tensor-core products ran out in:";
+    if (h & kStatusRender) m += " render";
+    if (h & kStatusProposal) m += " proposal";
+    if (h & kStatusEikonal) m += " eikonal";
+    if (h & kStatusPaperRender) m += " render (paper architecture)";
+    if (h & kStatusImportance) m += " importance sampler";
+    return fail(ctx, GS_ERR_DEVICE, m.c_str());
+  }
   return GS_OK;
 }
 

@@ -92,7 +92,7 @@ struct EikArgs {
   float* grad;         // nullptr: loss only
   float* part;         // [gridDim.x] per-CTA loss sums
   unsigned* ticket;    // 0 between calls
-  int* status;         // bit 8: a tensor-core phase did not complete
+  int* status;         // kStatusEikonal: a tensor-core phase did not complete
   float4* eik;         // deferred grid term: [5][S] records of the free-space samples; nullptr: scatter here
 };
 
@@ -429,7 +429,7 @@ __global__ void __launch_bounds__(kEtThreads, 1) eikonal_tc_kernel(EikArgs a) {
   }
 
   if (!alive && G.gt == 0) {
-    atomicOr(a.status, 8);
+    atomicOr(a.status, kStatusEikonal);
     tc::mbar_wait(G.mbar, G.phase ^ 1u, kMbarLimit);  // let an MMA in flight finish
   }
   dw_wait(G);
@@ -777,7 +777,7 @@ __global__ void __launch_bounds__(kEpThreads, 1) eikonal_paper_tc_kernel(EikArgs
   }
 
   if (!alive && G.gt == 0) {
-    atomicOr(a.status, 8);
+    atomicOr(a.status, kStatusEikonal);
     tc::mbar_wait(G.mbar, G.phase ^ 1u, kMbarLimit);  // let an MMA in flight finish
   }
   dw_wait(G);

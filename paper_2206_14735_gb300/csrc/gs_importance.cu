@@ -300,7 +300,7 @@ __global__ void __launch_bounds__(kItThreads, 1) importance_tc_kernel(ImpArgs a,
     __syncwarp();
   }
   if (!alive && G.gt == 0) {
-    atomicOr(status, 32);
+    atomicOr(status, kStatusImportance);
     tc::mbar_wait(G.mbar, G.phase ^ 1u, kItMbarLimit);  // let an MMA in flight finish
   }
   block_add_counts(a.counts, nd, ntr, nfs);

@@ -14,6 +14,10 @@ constexpr int kRenderCtasPerSm = 1;  // persistent render CTAs per SM
 constexpr int kStoreFloatsPerSample = 100;  // stored activations: z 16, a1 32, (phi, h) 16, a2 32, c 3 + 1 pad
 constexpr int kPaperStoreFloatsPerSample = 156;  // paper architecture: z 16, cf 6 + phi + pad, c 3 + pad, 4 x 32 hidden
 constexpr int kRenderGroups = 3;     // tile groups (4 warps, 128 tensor-memory columns each) per render CTA
+// Bits of the context's device status word: a kernel sets its bit when a bounded wait for its
+// tensor-core products ran out (it then stops early; that call's outputs are incomplete)
+constexpr int kStatusRender = 2, kStatusProposal = 4, kStatusEikonal = 8, kStatusPaperRender = 16,
+              kStatusImportance = 32;
 constexpr int kEikCtasPerSm = 4;     // CTAs of the Eikonal kernel per SM (one wave at 230 registers x 64 threads)
 
 struct gs_ctx {

@@ -88,7 +88,7 @@ struct PaperTcArgs {
   float* dz_out;                // [R][N][32] per-sample records for the pose gradient (may be nullptr)
   float *loss_part, *mlp_part;  // this kernel's partial rows, one per CTA
   int R, N;
-  int* status;  // bit 16: a tensor-core phase did not complete
+  int* status;  // kStatusPaperRender: a tensor-core phase did not complete
   // deferred Eikonal records ([5][R N] float4 planes) of the free-space samples, added to their
   // geometry scatter; nullptr: none
   const float4* eik;
@@ -864,7 +864,7 @@ __global__ void __launch_bounds__(kPThreads, 1) paper_tc_kernel(const __grid_con
     else if (lane == 3) atomicAdd(ga + ga_gb3, ob);
   }
   if (!alive && gt == 0) {
-    atomicOr(a.status, 16);
+    atomicOr(a.status, kStatusPaperRender);
     tc::mbar_wait(G.mbar, G.phase ^ 1u, kMbarLimit);  // let an MMA in flight finish
   }
   dw_wait(G);

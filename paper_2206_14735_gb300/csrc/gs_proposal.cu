@@ -531,7 +531,7 @@ __global__ void __launch_bounds__(128) prop_sample_tc_kernel(PropSampleArgs a, i
     prop_draw(a, i, pb, D, width, lane, ntr, nfs);
   }
   if (!alive && threadIdx.x == 0) {
-    atomicOr(status, 4);
+    atomicOr(status, kStatusProposal);
     tc::mbar_wait(mbar, phase ^ 1u, kPropMbarLimit);  // let an MMA in flight finish
   }
   block_add_counts(a.counts, nd, ntr, nfs);
@@ -678,7 +678,7 @@ __global__ void __launch_bounds__(128) prop_backward_tc_kernel(PropBwdArgs a, in
     __syncwarp();
   }
   if (!alive && threadIdx.x == 0) {
-    atomicOr(status, 4);
+    atomicOr(status, kStatusProposal);
     tc::mbar_wait(mbar, phase ^ 1u, kPropMbarLimit);  // let an MMA in flight finish
   }
   tc::fence_before_sync();

@@ -190,6 +190,8 @@ static bool encode_level_map(const gs_ctx* ctx, const float* theta, int l, CUten
             CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
 
+static_assert(kStatusRender == 2, "render_tc_kernel reports a bounded wait that ran out as bit 1 (value 2)");
+
 gs_status gs_launch_render(const gs_ctx* ctx, const float* theta, const uint16_t* theta_bf16, const gs_batch* b,
                            const float* dloss, float* grad, float* rgb_hat, float* d_hat, float* wsum, int mode,
                            cudaStream_t st) {
