@@ -92,3 +92,33 @@ def test_noalloc_rejects_bad_arguments():
     # forms this entry point does not run
     assert code(precision=gs.GS_PREC_BF16) == 6
     assert code(arch=gs.GS_ARCH_PAPER) == 6
+
+
+def test_noalloc_adds_deferred_eikonal_records():
+    """gs_forward_backward_noalloc reads batch->eik as gs_forward_backward does: after one
+    Eikonal call writes the records, both entry points give the same gradient."""
+    p = Problem(CUBE)
+    batch = p.gpu_sample(7, 4)
+    theta = torch.from_numpy(sdf_parity_params(CUBE, sg.cube_scene(), seed=21)).cuda()
+    batch.eik = torch.full((5, batch.R, batch.N, 4), float("nan"), device="cuda")
+    g_eik = torch.zeros_like(theta)
+    p.ctx.eikonal(theta, batch, grad=g_eik)  # decoder part into g_eik, grid part into the records
+    loss_ref = torch.empty(6, device="cuda")
+    grad_ref = g_eik.clone()
+    p.ctx.forward_backward(theta, batch, None, loss_ref, grad_ref)
+    torch.cuda.synchronize()
+    p.ctx.sync_status()
+    loss = torch.empty(6, device="cuda")
+    grad = g_eik.clone()
+    st = _noalloc(gs.make_config(CUBE), theta, batch.struct(), None, loss, grad)
+    assert st == 0, _lib.lib().gs_last_error(None)
+    torch.cuda.synchronize()
+    assert np.isfinite(loss.cpu().numpy()).all()
+    assert_grad_close(p, grad.cpu().numpy(), grad_ref.cpu().numpy())
+    # without the records the grid part is missing: the records do reach the scatter
+    batch.eik = None
+    grad_plain = g_eik.clone()
+    assert _noalloc(gs.make_config(CUBE), theta, batch.struct(), None, loss, grad_plain) == 0
+    torch.cuda.synchronize()
+    n = p.n_grid
+    assert np.abs(grad_plain.cpu().numpy()[:n] - grad.cpu().numpy()[:n]).max() > 0
