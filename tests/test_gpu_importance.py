@@ -130,3 +130,29 @@ def test_importance_sampler_room_scale():
         assert np.array_equal(got[k], ref[k]), k
     _check_depth_deviation(got["t"].astype(np.float64) - ref["t"], w.far - w.near, 96)
     assert (got["cls"] != ref["cls"]).mean() <= 1e-3
+
+
+def test_importance_sampler_ragged_configuration():
+    """N_c not a multiple of 32 and M not 12 (40 coarse samples in two rounds, the second with
+    8 busy rows per ray; 2 steps of 20): the tensor-core rounds with idle rows against the
+    oracle."""
+    w2 = CUBE.with_(name="cube-imp-ragged", imp_coarse=40, imp_steps=2, imp_per_step=20)
+    p = Problem(w2)
+    theta = sdf_parity_params(w2, sg.cube_scene(), seed=21)
+    R = 333
+    b = gs.Batch.allocate(R, w2.n_samples, 0)
+    assert w2.n_samples == 80
+    p.ctx.sample_importance(p.dfr, torch.from_numpy(theta).cuda(), SEED, 5, b)
+    torch.cuda.synchronize()
+    p.ctx.sync_status()
+    got = {k: getattr(b, a).cpu().numpy() for k, a in
+           (("pix", "pix"), ("o", "origin"), ("r", "dir"), ("rgb", "rgb"), ("D", "depth"), ("t", "t"), ("cls", "cls"))}
+    ref = oc.sample_importance(p.cfg, p.ofr, theta, SEED, 5, R, 40, 2, 20)
+    coarse = oc.sample_importance(p.cfg, p.ofr, theta, SEED, 5, R, 40, 0, 20)["t"]
+    for k in ("pix", "o", "r", "rgb", "D"):
+        assert np.array_equal(got[k], ref[k]), k
+    assert np.all(np.diff(got["t"].astype(np.float64), axis=1) >= 0)
+    for i in range(R):
+        assert np.isin(coarse[i], got["t"][i]).all(), i
+    _check_depth_deviation(got["t"].astype(np.float64) - ref["t"].astype(np.float64), w2.far - w2.near, 40)
+    assert (got["cls"] != ref["cls"]).mean() <= 1e-3
