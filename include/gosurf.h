@@ -348,7 +348,9 @@ gs_status gs_pose_backward(gs_ctx* ctx, const float* theta, const gs_frames* fra
  * sample's position gradient H_s a_s reaches the pose as in gs_pose_backward.  xi [F][6], the
  * frames (their poses the refined ones the batch was sampled with) and the batch (pix, origin,
  * dir, t, cls, counts) as for gs_pose_backward; dloss a device float [1] or NULL (1).  Either
- * architecture.  Accumulates with atomics. */
+ * architecture.  Accumulates with atomics.  With batch->eik set, each free-space sample's
+ * d phi / d z is read from the records that gs_eikonal wrote on this batch (that call must come
+ * first) instead of being evaluated here. */
 gs_status gs_eikonal_pose_backward(gs_ctx* ctx, const float* theta, const gs_frames* frames, const float* xi,
                                    const gs_batch* batch, const float* dloss, float* pose_grad, void* stream);
 

@@ -259,6 +259,10 @@ struct EikPoseArgs {
   const int* counts;   // counts[2] = |S_fs|
   const float* dloss;  // [1] or nullptr (1)
   float* pose_grad;    // [F][6] (+=)
+  // the batch's deferred Eikonal records (written by the Eikonal call on this batch): plane l of
+  // sample s holds p_l / v_l, so the sensitivity is read instead of computed; nullptr: computed
+  const float4* eik;
+  long long eik_stride;
 };
 
 // one warp per ray, lanes over its samples (free-space ones only), then lane 0 adds the
@@ -284,7 +288,11 @@ __global__ void __launch_bounds__(128) eikonal_pose_kernel(EikPoseArgs a) {
       const float tk = a.t[(size_t)i * a.N + k];
       float x[3];
       sample_pos(o, r, tk, x);
-      {
+      if (a.eik != nullptr) {  // q_l = p_l / v_l from the records
+        const float4* rec = a.eik + (size_t)i * a.N + k;
+#pragma unroll
+        for (int l = 0; l < kLevels; ++l) *reinterpret_cast<float4*>(myp + 4 * l) = __ldg(rec + l * a.eik_stride);
+      } else {
         float z[kZ], p[kZ];
 #pragma unroll
         for (int l = 0; l < kLevels; ++l) {
@@ -326,7 +334,9 @@ __global__ void __launch_bounds__(128) eikonal_pose_kernel(EikPoseArgs a) {
           f4fma(e02, sx * wy * sz, v);
           f4fma(e12, wx * sy * sz, v);
         }
-        const float iv = a.g.inv_voxel[l], iv2 = iv * iv;
+        // the records hold p_l already divided by v_l
+        const float iv = a.eik != nullptr ? 1.f : a.g.inv_voxel[l];
+        const float iv2 = a.eik != nullptr ? a.g.inv_voxel[l] : iv * iv;
         const bool cx = c.clamped & 1u, cy = c.clamped & 2u, cz = c.clamped & 4u;
         const float dot0 = d0.x * p4.x + d0.y * p4.y + d0.z * p4.z + d0.w * p4.w;
         const float dot1 = d1.x * p4.x + d1.y * p4.y + d1.z * p4.z + d1.w * p4.w;
@@ -413,6 +423,8 @@ gs_status gs_launch_eikonal_pose_backward(const gs_ctx* ctx, const float* theta,
   a.counts = b->counts;
   a.dloss = dloss;
   a.pose_grad = pose_grad;
+  a.eik = reinterpret_cast<const float4*>(b->eik);
+  a.eik_stride = (long long)b->R * b->N;
   const int blocks = (int)std::min<long long>(((long long)b->R * 32 + 127) / 128, 16LL * ctx->num_sms);
   if (ctx->cfg.arch == GS_ARCH_PAPER) eikonal_pose_kernel<true><<<blocks, 128, 0, st>>>(a);
   else eikonal_pose_kernel<false><<<blocks, 128, 0, st>>>(a);

@@ -457,9 +457,11 @@ def test_paper_pose_records_and_gradient_match_oracle():
     assert np.abs(g - g_ref).max() <= 1e-4 * np.abs(g_ref).max(), (g, g_ref)
 
 
-def test_paper_eikonal_pose_gradient_matches_oracle():
+@pytest.mark.parametrize("records", [False, True])
+def test_paper_eikonal_pose_gradient_matches_oracle(records):
     """The Eikonal term's pose gradient with the paper's two-hidden-layer geometry decoder,
-    against the oracle's (rays with a free-space sample at a ReLU kink left out)."""
+    against the oracle's (rays with a free-space sample at a ReLU kink left out); with records,
+    d phi / d z from the deferred Eikonal records of a preceding Eikonal call."""
     w = CUBE_P.with_(name="cube-paper-3frames", frames=3)
     p = Problem(w)
     rng = np.random.default_rng(5)
@@ -472,6 +474,9 @@ def test_paper_eikonal_pose_gradient_matches_oracle():
     assert dropped <= 0.05 * w.rays and int(bt["counts"][2]) > 1000
     g_ref = oc.eikonal_pose_grad(p.cfg, F, theta, c2w, xi, bt)
     batch = upload_oracle_batch(bt, None, 0)
+    if records:
+        batch.eik = torch.full((5, batch.R, batch.N, 4), float("nan"), device="cuda")
+        p.ctx.eikonal(_padded(theta), batch, loss=torch.empty(1, device="cuda"))
     dfr = p.dfr.with_poses(torch.from_numpy(c2w.astype(np.float32)).cuda())
     pg = torch.zeros(3, 6, device="cuda")
     p.ctx.eikonal_pose_backward(_padded(theta), dfr, torch.from_numpy(xi.astype(np.float32)).cuda(), batch, pg)

@@ -61,11 +61,13 @@ def test_dz_export_and_pose_gradient_match_oracle(posed):
     assert np.abs(g - g_ref).max() <= 1e-4 * np.abs(g_ref).max(), (g, g_ref)
 
 
-def test_eikonal_pose_gradient_matches_oracle(posed):
+@pytest.mark.parametrize("records", [False, True])
+def test_eikonal_pose_gradient_matches_oracle(posed, records):
     """The Eikonal term's pose gradient (x-Hessian of phi through the free-space samples'
     positions) against the oracle's, on hidden units that switch from sample to sample; rays
     holding a free-space sample within binary32 rounding of a ReLU kink are left out (the
-    term jumps there)."""
+    term jumps there).  With records, d phi / d z comes from the batch's deferred Eikonal
+    records, which an Eikonal call on the batch writes first."""
     from gpu_common import drop_kink_rays
     p, xi, c2w, F, theta = posed
     bt = oc.sample_rays(p.cfg, F, 9, 2, W3.rays)
@@ -75,6 +77,9 @@ def test_eikonal_pose_gradient_matches_oracle(posed):
     for dscale in (1.0, -0.75):
         g_ref = oc.eikonal_pose_grad(p.cfg, F, theta, c2w, xi, bt, dscale)
         batch = upload_oracle_batch(bt, None, 0)
+        if records:
+            batch.eik = torch.full((5, batch.R, batch.N, 4), float("nan"), device="cuda")
+            p.ctx.eikonal(torch.from_numpy(theta).cuda(), batch, loss=torch.empty(1, device="cuda"))
         dfr = p.dfr.with_poses(torch.from_numpy(c2w.astype(np.float32)).cuda())
         pg = torch.zeros(3, 6, device="cuda")
         dl = None if dscale == 1.0 else torch.tensor([dscale], dtype=torch.float32, device="cuda")
