@@ -46,6 +46,7 @@ gs_status gs_launch_paper_tc(const gs_ctx* ctx, const float* theta, const gs_bat
   a.eik_stride = (long long)b->R * b->N;
   a.store = ctx->store;
   a.store_stride = (long long)ctx->cfg.max_rays * ctx->max_n;
+  if (!gs_encode_level_map(ctx, theta, GS_LEVELS - 1, &a.tmap)) return GS_ERR_CUDA;
   switch ((b->N + 31) / 32) {
     case 1: return ptc::launch_paper_tc<1>(a, mode, ctas, st);
     case 2: return ptc::launch_paper_tc<2>(a, mode, ctas, st);

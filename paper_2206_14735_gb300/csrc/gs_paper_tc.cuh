@@ -74,6 +74,7 @@ static_assert(4u * 32u * kOr * 4u <= 2u * 3u * kAP, "output-layer staging fits i
 static_assert(4u * kScatterStage * 4u <= 3u * kAP, "scatter staging fits in Ag");
 
 struct PaperTcArgs {
+  CUtensorMap tmap;      // the finest geometry level for the forward pass's tile::gather4 loads
   GridDesc g;            // geometry levels; g.n_grid = decoder block offset (after the colour grid)
   long long colour_off;  // float offset of the colour grid (a multiple of 4)
   const float* theta;
@@ -108,52 +109,74 @@ __device__ __forceinline__ void red_add_f2(float* p, float a, float b) {
   asm volatile("red.global.add.v2.f32 [%0], {%1, %2};" ::"l"(p), "f"(a), "f"(b) : "memory");
 }
 
-// geometry features z (4 levels x 4) and colour features cf (finest cell, 6 per vertex) at x
-__device__ __forceinline__ void gather(const PaperTcArgs& a, const float x[3], float z[kZ], float cf[kC]) {
-  Cell cs[kLevels];
-#pragma unroll
-  for (int l = 0; l < kLevels; ++l) {  // every level's cell first, and an L2 prefetch of its corners
-    cs[l] = locate(a.g, l, x);
-    const float4* lv = reinterpret_cast<const float4*>(a.theta + a.g.off[l]);
-#pragma unroll
-    for (int k = 0; k < 4; ++k) asm volatile("prefetch.global.L2 [%0];" ::"l"(lv + cs[l].vtx + corner_offset(a.g, l, k)));
+// The gather of z (4 levels x 4) and the colour features cf (the finest cell, 6 per vertex) at
+// x.  The finest level's geometry corners come through the TMA: one tile::gather4 per sample
+// (rows (y,z), (y+1,z), (y,z+1), (y+1,z+1) of the level's 2D view, 2 vertices each: 128 B)
+// into a slot in the half of an A plane that the 16-column z and u tiles leave free, which
+// nothing else uses between the reverse pass of one chunk and the F1 epilogue of the next.
+// The colour corners (24 bytes each) and the coarse levels (a warp's samples share their cells)
+// come by plain loads meanwhile.  Every thread of the group takes part in every round (the
+// byte count is fixed); lanes without a sample get zeros.
+constexpr uint32_t kGatherBytes = 128u * 128u;  // per group and round
+__device__ __forceinline__ uint8_t* geo_slot(uint8_t* gmem, int gt) {  // warp w: the free half of A plane w
+  return gmem + (uint32_t)(gt >> 5) * kAP + kAP / 2 + (uint32_t)(gt & 31) * 128u;
+}
+
+__device__ __forceinline__ void gather_fwd(const PaperTcArgs& a, Group& G, uint8_t* gmem, const float x[3], bool valid,
+                                           float z[kZ], float cf[kC]) {
+  constexpr int l = kLevels - 1;
+  const Cell c = locate(a.g, l, x);
+  const int nx = a.g.dims[l][0], ny = a.g.dims[l][1];
+  uint8_t* gs = geo_slot(gmem, G.gt);
+  {
+    tc::fence_smem_async();  // earlier generic accesses to the slot before the asynchronous write
+    const int r0 = c.idx[2] * ny + c.idx[1];
+    tc::tma_gather4(tc::smem_u32(gs), &a.tmap, 4 * c.idx[0], r0, r0 + 1, r0 + ny, r0 + ny + 1, G.mbar_tma);
   }
+  const float f0 = c.f[0], f1 = c.f[1], f2 = c.f[2];
 #pragma unroll
-  for (int l = 0; l < kLevels; ++l) {
-    const Cell c = cs[l];
-    float w[8];
-    corner_weights(c.f, w);
-    const float4* lv = reinterpret_cast<const float4*>(a.theta + a.g.off[l]);
-    float4 acc = make_float4(0.f, 0.f, 0.f, 0.f);
+  for (int i = 0; i < kC; ++i) cf[i] = 0.f;
+  if (valid) {
+    const float* cg = a.theta + a.colour_off;
 #pragma unroll
-    for (int k = 0; k < 8; ++k) f4fma(acc, w[k], __ldg(lv + c.vtx + corner_offset(a.g, l, k)));
-    z[4 * l] = acc.x;
-    z[4 * l + 1] = acc.y;
-    z[4 * l + 2] = acc.z;
-    z[4 * l + 3] = acc.w;
-    if (l == kLevels - 1) {
+    for (int k = 0; k < 8; ++k) {  // corner k: vertex (x + (k & 1), y + (k >> 1 & 1), z + (k >> 2))
+      const long long v = c.vtx + (k & 1) + (long long)((k >> 1) & 1) * nx + (long long)(k >> 2) * nx * ny;
+      // its 24 bytes lie in the 16-byte aligned 32-byte window that starts at them (even v) or 8
+      // bytes before them (odd v): two loads and selects, no branch, so that the loads of all
+      // corners are in flight together (past the last vertex the window reads the decoder block)
+      const bool odd = (v & 1) != 0;
+      const float4* q = reinterpret_cast<const float4*>(cg + 6 * v - (odd ? 2 : 0));
+      const float4 A = __ldg(q), B = __ldg(q + 1);
+      const float e[6] = {odd ? A.z : A.x, odd ? A.w : A.y, odd ? B.x : A.z,
+                          odd ? B.y : A.w, odd ? B.z : B.x, odd ? B.w : B.y};
+      const float w = (((k & 1) ? f0 : 1.0f - f0) * ((k & 2) ? f1 : 1.0f - f1)) * ((k & 4) ? f2 : 1.0f - f2);
 #pragma unroll
-      for (int q = 0; q < kC; ++q) cf[q] = 0.f;
-      const float* cg = a.theta + a.colour_off;
-#pragma unroll
-      for (int k = 0; k < 8; ++k) {
-        const long long v = c.vtx + corner_offset(a.g, l, k);
-        const float* p = cg + 6 * v;  // 24 bytes: a float4 and a float2 on their own boundaries
-        float e[6];
-        if ((v & 1) == 0) {
-          const float4 q4 = __ldg(reinterpret_cast<const float4*>(p));
-          const float2 q2 = __ldg(reinterpret_cast<const float2*>(p + 4));
-          e[0] = q4.x, e[1] = q4.y, e[2] = q4.z, e[3] = q4.w, e[4] = q2.x, e[5] = q2.y;
-        } else {
-          const float2 q2 = __ldg(reinterpret_cast<const float2*>(p));
-          const float4 q4 = __ldg(reinterpret_cast<const float4*>(p + 2));
-          e[0] = q2.x, e[1] = q2.y, e[2] = q4.x, e[3] = q4.y, e[4] = q4.z, e[5] = q4.w;
-        }
-#pragma unroll
-        for (int q = 0; q < kC; ++q) cf[q] = fmaf(w[k], e[q], cf[q]);
-      }
+      for (int i = 0; i < kC; ++i) cf[i] = fmaf(w, e[i], cf[i]);
     }
+    coarse_gather(a.g, a.theta, x, z);
   }
+  if (!tc::mbar_wait(G.mbar_tma, G.phase_tma, kMbarLimit)) *reinterpret_cast<volatile int*>(G.abort) = 1;
+  G.phase_tma ^= 1u;
+  if (G.gt == 0) tc::mbar_arrive_expect_tx(G.mbar_tma, kGatherBytes);  // armed for the next round
+  if (!valid) {
+#pragma unroll
+    for (int k = 0; k < kZ; ++k) z[k] = 0.f;
+    return;
+  }
+  // geometry: 16-byte chunk c8 = vertex (x + (c8 & 1)) of row c8 >> 1, order rotated by lane
+  const int lane = G.gt & 31;
+  float4 s = make_float4(0.f, 0.f, 0.f, 0.f);
+#pragma unroll
+  for (int k = 0; k < 8; ++k) {
+    const int c8 = (k + lane) & 7;
+    const int bx = c8 & 1, by = (c8 >> 1) & 1, bz = c8 >> 2;
+    const float w = ((bx ? f0 : 1.0f - f0) * (by ? f1 : 1.0f - f1)) * (bz ? f2 : 1.0f - f2);
+    f4fma(s, w, *reinterpret_cast<const float4*>(gs + c8 * 16));
+  }
+  z[4 * l] = s.x;
+  z[4 * l + 1] = s.y;
+  z[4 * l + 2] = s.z;
+  z[4 * l + 3] = s.w;
 }
 
 // colour-grid gradient of one sample: corner k of the finest cell += w_k dcf
@@ -281,7 +304,9 @@ __global__ void __launch_bounds__(kPThreads, 1) paper_tc_kernel(const __grid_con
   if (gt == 0) {
     tc::mbar_init(G.mbar, 1);
     tc::mbar_init(G.mbar_dw, 1);
+    tc::mbar_init(G.mbar_tma, 1);
     tc::fence_mbar_init();
+    tc::mbar_arrive_expect_tx(G.mbar_tma, kGatherBytes);  // armed for the first round
     *G.abort = 0;
   }
   if (tid < 32) tc::tmem_alloc(tslot, kPTmem);
@@ -357,15 +382,10 @@ __global__ void __launch_bounds__(kPThreads, 1) paper_tc_kernel(const __grid_con
       float cfs[8];  // the colour features, phi and a zero: stored fields kQu..kQu + 7
       {
         float z[kZ], u[16];
-        if (valid) {
+        {
           float x[3];
           sample_pos(o, r, t, x);
-          gather(a, x, z, u);
-        } else {
-#pragma unroll
-          for (int k = 0; k < kZ; ++k) z[k] = 0.f;
-#pragma unroll
-          for (int k = 0; k < kC; ++k) u[k] = 0.f;
+          gather_fwd(a, G, gmem, x, valid, z, u);
         }
 #pragma unroll
         for (int q = 0; q < 3; ++q) u[kC + q] = dvw[q];
@@ -654,19 +674,12 @@ __global__ void __launch_bounds__(kPThreads, 1) paper_tc_kernel(const __grid_con
         for (int q = 0; q < 8; ++q)
           *reinterpret_cast<float4*>(orow + 36 + 4 * q) = make_float4(v[4 * q], v[4 * q + 1], v[4 * q + 2], v[4 * q + 3]);
       } else {
-        if (valid) {
-          gather(a, x, z, u);
-        } else {
-#pragma unroll
-          for (int k = 0; k < kZ; ++k) z[k] = 0.f;
-#pragma unroll
-          for (int k = 0; k < kC; ++k) u[k] = 0.f;
-        }
+        dw_wait(G);  // the previous chunk's weight-gradient products have read the tiles the gather lands in
+        gather_fwd(a, G, gmem, x, valid, z, u);
 #pragma unroll
         for (int q = 0; q < 3; ++q) u[kC + q] = dvw[q];
 #pragma unroll
         for (int k = kU; k < 16; ++k) u[k] = 0.f;
-        dw_wait(G);
         store_row_planes<3, 16, kAP>(Ag, row, z);
         store_row_planes<3, 16, kAP>(Ac, row, u);
         phase2(G, [&] {

@@ -177,7 +177,7 @@ static EncodeTiledFn encode_tiled() {
 }
 
 // 2D view [nz * ny][nx * 4] of grid level l with a box of 2 vertices x 4 features, one row high
-static bool encode_level_map(const gs_ctx* ctx, const float* theta, int l, CUtensorMap* m) {
+bool gs::gs_encode_level_map(const gs_ctx* ctx, const float* theta, int l, CUtensorMap* m) {
   EncodeTiledFn fn = encode_tiled();
   if (!fn) return false;
   const GridDesc& g = ctx->grid;
@@ -220,7 +220,7 @@ gs_status gs_launch_render(const gs_ctx* ctx, const float* theta, const uint16_t
   a.status = ctx->status;
   if (ctx->cfg.precision != GS_PREC_BF16)
     for (int q = 0; q < 2; ++q)
-      if (!encode_level_map(ctx, theta, 2 + q, &a.tmap[q])) return GS_ERR_CUDA;
+      if (!gs_encode_level_map(ctx, theta, 2 + q, &a.tmap[q])) return GS_ERR_CUDA;
   a.store = ctx->store;
   a.w_out = b->w;
   a.dz_out = b->dz;

@@ -332,6 +332,9 @@ __device__ __forceinline__ uint32_t fine_slot(uint8_t* ga, uint8_t* gb, int lvl,
   return tc::smem_u32(ga + 12288 + (gt - 96) * 128);
 }
 constexpr int kTmaLevels = 1;  // the finest levels that go through the TMA (the rest: plain loads)
+// host: the 2D view [nz ny][4 nx] of grid level l in theta, a box of 2 vertices x 4 features one
+// row high (the tile::gather4 source of the finest level); false if the driver refused it
+bool gs_encode_level_map(const gs_ctx* ctx, const float* theta, int l, CUtensorMap* m);
 constexpr uint32_t kFineTmaBytes = 128u * kTmaLevels * 128u;  // per group and round: 128 samples x levels x 128 B
 
 // issue both fine-level gathers of this thread's sample; returns the cells (for the weights)
