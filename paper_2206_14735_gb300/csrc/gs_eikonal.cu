@@ -319,13 +319,7 @@ __global__ void __launch_bounds__(kEtThreads, 1) eikonal_tc_kernel(EikArgs a) {
     {
       Cell cs[kLevels];
 #pragma unroll
-      for (int l = 0; l < kLevels; ++l) {  // every level's cell first, and an L2 prefetch of its corners
-        cs[l] = locate(a.g, l, y);
-        const float4* lv = reinterpret_cast<const float4*>(a.theta + a.g.off[l]);
-#pragma unroll
-        for (int k = 0; k < 4; ++k)  // corners k and k + 4 differ only in x
-          asm volatile("prefetch.global.L2 [%0];" ::"l"(lv + cs[l].vtx + corner_offset(a.g, l, k)));
-      }
+      for (int l = 0; l < kLevels; ++l) cs[l] = locate(a.g, l, y);
       float z[kZ];
 #pragma unroll
       for (int l = 0; l < kLevels; ++l) {
@@ -628,13 +622,7 @@ __global__ void __launch_bounds__(kEpThreads, 1) eikonal_paper_tc_kernel(EikArgs
       float z[kZ];
       Cell cs[kLevels];
 #pragma unroll
-      for (int l = 0; l < kLevels; ++l) {
-        cs[l] = locate(a.g, l, y);
-        const float4* lv = reinterpret_cast<const float4*>(a.theta + a.g.off[l]);
-#pragma unroll
-        for (int k = 0; k < 4; ++k)
-          asm volatile("prefetch.global.L2 [%0];" ::"l"(lv + cs[l].vtx + corner_offset(a.g, l, k)));
-      }
+      for (int l = 0; l < kLevels; ++l) cs[l] = locate(a.g, l, y);
 #pragma unroll
       for (int l = 0; l < kLevels; ++l) {
         const Cell c = cs[l];

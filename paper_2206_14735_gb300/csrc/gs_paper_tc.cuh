@@ -621,13 +621,6 @@ __global__ void __launch_bounds__(kPThreads, 1) paper_tc_kernel(const __grid_con
       float x[3];
       sample_pos(o, r, t, x);
       const float4* spr = a.store != nullptr ? reinterpret_cast<const float4*>(a.store) + (size_t)rr * N + si : nullptr;
-      if (spr != nullptr && has_ray && si + 32 < N) {
-        // the next chunk's stored lines into L2 while this chunk runs (a warp's 32 samples
-        // cover 512 bytes of each plane: lanes 0, 8, 16, 24 touch its four 128-byte lines)
-        if ((lane & 7) == 0)
-#pragma unroll 1
-          for (int f = 0; f < kQFields / 4; ++f) asm volatile("prefetch.global.L2 [%0];" ::"l"(spr + 32 + f * a.store_stride));
-      }
       float z[kZ], u[16];
       uint32_t m1 = 0, mr1 = 0, m2 = 0, mr2 = 0;
       // output layers on CUDA cores: [dpre | dphi | a2 | r2] staged per lane in the A tiles

@@ -278,22 +278,9 @@ __device__ __forceinline__ uint32_t lane_addr(const Group& G, uint32_t col, int 
 template <bool BF16GRID>
 __device__ __forceinline__ void gather_z(const GridDesc& g, const float* __restrict__ theta,
                                          const uint16_t* __restrict__ theta_bf16, const float x[3], float z[kZ]) {
-  // cells of every level first, and an L2 prefetch of each x-adjacent corner pair, so that the
-  // four levels' loads below overlap instead of taking four memory round trips in sequence
-  Cell cs[kLevels];
 #pragma unroll
   for (int l = 0; l < kLevels; ++l) {
-    cs[l] = locate(g, l, x);
-    const char* base = BF16GRID ? reinterpret_cast<const char*>(theta_bf16 + g.off[l])
-                                : reinterpret_cast<const char*>(theta + g.off[l]);
-    const int es = BF16GRID ? 8 : 16;  // bytes per vertex
-#pragma unroll
-    for (int k = 0; k < 4; ++k)  // corners k and k + 4 differ only in x
-      asm volatile("prefetch.global.L2 [%0];" ::"l"(base + (cs[l].vtx + corner_offset(g, l, k)) * es));
-  }
-#pragma unroll
-  for (int l = 0; l < kLevels; ++l) {
-    const Cell c = cs[l];
+    const Cell c = locate(g, l, x);
     float w[8];
     corner_weights(c.f, w);
     float4 v[8];
