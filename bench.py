@@ -387,7 +387,7 @@ def run_ours(args):
         "config": step_config(w, args, world, fr.depth.shape[0]),
         "samples_per_s": round(value * w.n_samples, 1), "frame_render_s": round(t_frames, 1),
         "kernels_ms": {k: round(vv, 4) for k, vv in avg.items()},
-        "roofline": {"kernel": ("render call: paper_render_kernel (fused gathers / CUDA-core decoders / compositing "
+        "roofline": {"kernel": ("render call: paper_tc_kernel (fused gathers / tcgen05 decoders / compositing "
                                 "/ backward / scatter) + paper_smooth_kernel + paper_combine_kernel" if paper else
                                 "render call: render_tc_kernel (fused gather / tcgen05 decoders / compositing / "
                                 "backward / scatter, 90 % of the call) + smooth_kernel + finalize_kernel")
