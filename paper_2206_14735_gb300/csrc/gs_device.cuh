@@ -104,6 +104,18 @@ __device__ __forceinline__ void f4fma(float4& acc, float s, float4 b) {
 }
 
 // trilinear weights of the 8 corners
+// Sum over the partial rows p = w, w + 8, ... < nparts of part[p stride + i] (a column of
+// per-CTA partial rows): eight loads in flight, four partial sums combined in a fixed order,
+// so the result does not depend on timing.
+__device__ __forceinline__ float column_sum8(const float* __restrict__ part, size_t stride, int i, int w,
+                                            int nparts) {
+  float s[4] = {0.f, 0.f, 0.f, 0.f};
+  int k = 0;
+#pragma unroll 8
+  for (int p = w; p < nparts; p += 8, ++k) s[k & 3] += part[(size_t)p * stride + i];
+  return (s[0] + s[1]) + (s[2] + s[3]);
+}
+
 __device__ __forceinline__ void corner_weights(const float f[3], float w[8]) {
   const float gx = 1.0f - f[0], gy = 1.0f - f[1], gz = 1.0f - f[2];
   const float w00 = gx * gy, w01 = gx * f[1], w10 = f[0] * gy, w11 = f[0] * f[1];

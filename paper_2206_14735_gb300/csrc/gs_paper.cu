@@ -652,14 +652,22 @@ __global__ void __launch_bounds__(kThreads, 1) paper_query_backward_kernel(Args 
 __global__ void __launch_bounds__(256) paper_combine_kernel(const float* loss_part, const float* mlp_part,
                                                             int nparts, const int* counts, int R, float l0, float l1,
                                                             float l2, float l3, float l4, float* loss, float* gmlp) {
-  const int i = blockIdx.x * blockDim.x + threadIdx.x;
-  if (gmlp && i < GS_PAPER_MLP_PARAMS) {
-    float sacc = 0.f;
-    for (int p = 0; p < nparts; ++p) sacc += mlp_part[(size_t)p * kPart + i];
-    gmlp[i] += sacc;
+  // decoder gradients: block b owns entries [32b, 32b + 32); warp w sums rows w, w + 8, ...,
+  // then warp 0 adds the 8 warps' sums in a fixed order
+  __shared__ float part[8][33];
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  const int i = blockIdx.x * 32 + lane;
+  if (gmlp) {
+    part[wid][lane] = i < GS_PAPER_MLP_PARAMS ? column_sum8(mlp_part, kPart, i, wid, nparts) : 0.f;
+    __syncthreads();
+    if (wid == 0 && i < GS_PAPER_MLP_PARAMS) {
+      float t = 0.f;
+#pragma unroll
+      for (int k = 0; k < 8; ++k) t += part[k][lane];
+      gmlp[i] += t;
+    }
   }
   if (loss && blockIdx.x == 0 && threadIdx.x < 32) {
-    const int lane = threadIdx.x;
     double sk[5] = {0.0, 0.0, 0.0, 0.0, 0.0};
     for (int p = lane; p < nparts; p += 32)
 #pragma unroll
@@ -767,7 +775,7 @@ gs_status gs_launch_paper(const gs_ctx* ctx, const float* theta, const gs_batch*
     return GS_OK;
   }
   const float* l = ctx->cfg.lam;
-  paper_combine_kernel<<<(GS_PAPER_MLP_PARAMS + 255) / 256, 256, 0, st>>>(
+  paper_combine_kernel<<<(GS_PAPER_MLP_PARAMS + 31) / 32, 256, 0, st>>>(
       first_loss, first_mlp, nparts, b->counts, b->R, l[0], l[1], l[2], l[3], l[4], (mode & 1) ? loss : nullptr,
       (mode & 2) ? grad + ctx->grid.n_grid : nullptr);
   return cudaPeekAtLastError() == cudaSuccess ? GS_OK : GS_ERR_CUDA;
@@ -801,7 +809,7 @@ gs_status gs_launch_paper_query_backward(const gs_ctx* ctx, const float* theta, 
   paper_query_backward_kernel<<<ctas, kThreads, kSmemBytes, st>>>(a, x, P, dsdf, dgrad);
   if (cudaPeekAtLastError() != cudaSuccess) return GS_ERR_CUDA;
   const float* l = ctx->cfg.lam;
-  paper_combine_kernel<<<(GS_PAPER_MLP_PARAMS + 255) / 256, 256, 0, st>>>(
+  paper_combine_kernel<<<(GS_PAPER_MLP_PARAMS + 31) / 32, 256, 0, st>>>(
       ctx->paper_loss_part, ctx->paper_part, ctas, nullptr, 0, l[0], l[1], l[2], l[3], l[4], nullptr,
       grad + ctx->grid.n_grid);
   return cudaPeekAtLastError() == cudaSuccess ? GS_OK : GS_ERR_CUDA;

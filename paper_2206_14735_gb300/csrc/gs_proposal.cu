@@ -344,14 +344,23 @@ __global__ void __launch_bounds__(kPropWarps * 32, 1) prop_backward_kernel(PropB
   }
 }
 
-// rows summed in block order; scaled by 1 / (rays used)
-__global__ void prop_finalize_kernel(const float* part, int rows, float* grad, float* ce) {
-  const int i = blockIdx.x * blockDim.x + threadIdx.x;
-  float n = 0.f;
-  for (int b = 0; b < rows; ++b) n += part[(size_t)b * kPropPart + GS_PROP_PARAMS + 1];
-  if (i < GS_PROP_PARAMS + 1) {
-    float s = 0.f;
-    for (int b = 0; b < rows; ++b) s += part[(size_t)b * kPropPart + i];
+// the partial rows summed in a fixed order (block b: entries [32 b, 32 b + 32), warp w rows
+// w, w + 8, ..., then the 8 warps' sums in order); scaled by 1 / (rays used)
+__global__ void __launch_bounds__(256) prop_finalize_kernel(const float* part, int rows, float* grad, float* ce) {
+  __shared__ float sp[8][33], sn[8];
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  const int i = blockIdx.x * 32 + lane;
+  sp[wid][lane] = i < GS_PROP_PARAMS + 1 ? column_sum8(part, kPropPart, i, wid, rows) : 0.f;
+  const float nw = column_sum8(part, kPropPart, GS_PROP_PARAMS + 1, wid, rows);  // rays used
+  if (lane == 0) sn[wid] = nw;
+  __syncthreads();
+  if (wid == 0 && i < GS_PROP_PARAMS + 1) {
+    float s = 0.f, n = 0.f;
+#pragma unroll
+    for (int k = 0; k < 8; ++k) {
+      s += sp[k][lane];
+      n += sn[k];
+    }
     if (i < GS_PROP_PARAMS) {
       if (n > 0.f) grad[i] += s / n;
     } else if (ce != nullptr) {
@@ -791,6 +800,6 @@ gs_status gs_launch_prop_backward(const gs_ctx* ctx, const float* theta, const f
       return GS_ERR_CUDA;
     prop_backward_kernel<<<blocks, kPropWarps * 32, smem, st>>>(a);
   }
-  prop_finalize_kernel<<<(GS_PROP_PARAMS + 1 + 255) / 256, 256, 0, st>>>(ctx->prop_part, blocks, grad, ce);
+  prop_finalize_kernel<<<(GS_PROP_PARAMS + 1 + 31) / 32, 256, 0, st>>>(ctx->prop_part, blocks, grad, ce);
   return cudaPeekAtLastError() == cudaSuccess ? GS_OK : GS_ERR_CUDA;
 }

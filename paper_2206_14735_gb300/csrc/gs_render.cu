@@ -21,22 +21,13 @@ extern template gs_status launch_tc_n<PrecBF16, 5>(const gs_ctx*, RenderTcArgs&,
 __global__ void __launch_bounds__(256) finalize_kernel(const float* loss_part, const float* mlp_part, int nparts,
                                                        const int* counts, int R, float l0, float l1, float l2,
                                                        float l3, float l4, float* loss, float* gmlp) {
-  // decoder gradients: block b owns entries [32b, 32b + 32); warp w sums rows w, w + 8, ...
-  // with four independent partial sums (the loads of a warp overlap), combined in a fixed order
+  // decoder gradients: block b owns entries [32b, 32b + 32); warp w sums rows w, w + 8, ...,
+  // then warp 0 adds the 8 warps' sums in a fixed order
   __shared__ float part[8][33];
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
   const int i = blockIdx.x * 32 + lane;
   if (gmlp) {
-    float s[4] = {0.f, 0.f, 0.f, 0.f};
-    if (i < GS_MLP_PARAMS) {
-      int p = wid;
-      for (; p + 24 < nparts; p += 32) {
-#pragma unroll
-        for (int q = 0; q < 4; ++q) s[q] += mlp_part[(size_t)(p + 8 * q) * kMlpPad + i];
-      }
-      for (int q = 0; p < nparts; p += 8, q = (q + 1) & 3) s[q] += mlp_part[(size_t)p * kMlpPad + i];
-    }
-    part[wid][lane] = (s[0] + s[1]) + (s[2] + s[3]);
+    part[wid][lane] = i < GS_MLP_PARAMS ? column_sum8(mlp_part, kMlpPad, i, wid, nparts) : 0.f;
     __syncthreads();
     if (wid == 0 && i < GS_MLP_PARAMS) {
       float t = 0.f;
