@@ -237,6 +237,9 @@ __device__ __forceinline__ void mma3(uint32_t d, const uint8_t* a0, const uint8_
   issue_mma<P3, N, K>(d, tc::smem_u32(a0), tc::smem_u32(b0), kTW);
 }
 
+// the forward-only instantiation ends each ray-quad before its reverse pass, which the front
+// end reports as unreachable code there
+#pragma nv_diag_suppress 128
 template <int NCH, bool FWD, bool BWD>
 __global__ void __launch_bounds__(kPThreads, 1) paper_tc_kernel(const __grid_constant__ PaperTcArgs a) {
   using namespace paper;
@@ -928,6 +931,7 @@ __global__ void __launch_bounds__(kPThreads, 1) paper_tc_kernel(const __grid_con
     tc::tmem_dealloc(*tslot, kPTmem);
   }
 }
+#pragma nv_diag_default 128
 
 inline size_t paper_tc_smem() {
   return 1024 + (size_t)kPGroups * kPGroupBytes + 3 * kTW + sizeof(float) * (kScal + kPGroups * kGAcc + 8) + 16;

@@ -580,6 +580,9 @@ __device__ __forceinline__ void gather_chunk(Group& G, const RenderTcArgs& a, co
   }
 }
 
+// the forward-only instantiation ends each ray-quad before its reverse pass, which the front
+// end reports as unreachable code there
+#pragma nv_diag_suppress 128
 template <class P, int NCH, int GR, bool FWD, bool BWD>
 __global__ void __launch_bounds__(GR * kGroupThreads, 1) render_tc_kernel(const __grid_constant__ RenderTcArgs a) {
   using L = TcLayout<P>;
@@ -1174,6 +1177,7 @@ __global__ void __launch_bounds__(GR * kGroupThreads, 1) render_tc_kernel(const 
     tc::tmem_dealloc(*tslot, tmem_cols(GR));
   }
 }
+#pragma nv_diag_default 128
 
 template <class P, int GR>
 size_t render_tc_smem() {
