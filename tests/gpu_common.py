@@ -200,3 +200,41 @@ def assert_grad_close(p: Problem, g_gpu, g_ref, tol=GRAD_TOL, elem_rtol=GRAD_ELE
         report[k] = (err, rel)
         assert err <= tol and rel <= elem_rtol, (k, err, rel, report)
     return report
+
+
+def _surface_through(w, theta, x, bias_name):
+    """theta with the SDF's output bias shifted so that phi(x) = 0: a surface through x, so
+    that rays crossing x carry real opacity there (far from the scene's surface they are
+    nearly transparent and every colour gradient is rounding noise)."""
+    cfg = oc.make_config(w)
+    s0 = oc.query_sdf(cfg, theta, np.asarray(x, np.float32)[None, :], want_grad=False)
+    s0 = float(np.asarray(s0[0] if isinstance(s0, tuple) else s0).ravel()[0])
+    o = w.layout()[1]
+    for name, shape in w.mlp_shapes:
+        if name == bias_name:
+            break
+        o += int(np.prod(shape))
+    th = theta.copy()
+    th[o] -= np.float32(s0)
+    return th
+
+
+def corner_case(p: Problem, theta, bias_name, corner, seed, step, R=256, max_drop=0.2):
+    """Rays moved so that their samples cross a corner of the grid (the middle sample a quarter
+    of a finest voxel inside it, the rest partly outside and clamped into the boundary cells),
+    with the surface through that point; returns (theta, batch subset, oracle step)."""
+    w = p.w
+    bt, _ = p.oracle_sample(seed, step, R, 0)
+    lo = np.array(w.extent_min, np.float64)
+    hi = lo + (np.array(w.dims[3], np.float64) - 1) * w.voxels[3]
+    target = hi - 0.25 * w.voxels[3] if corner == "max" else lo + 0.25 * w.voxels[3]
+    theta = _surface_through(w, theta, target, bias_name)
+    t_mid = np.median(bt["t"], axis=1)
+    bt = dict(bt)
+    bt["o"] = (target[None, :] - t_mid[:, None] * bt["r"].astype(np.float64)).astype(np.float32)
+    bt_s, ref, _ = prepare_parity_batch(p, theta, bt, None, max_drop=max_drop, label=f"{w.name}, {corner} corner")
+    x = sample_positions(bt_s).reshape(-1, 3)
+    outside = ((x > hi[None, :]) | (x < lo[None, :])).any(axis=1)
+    assert outside.mean() > 0.2 and (~outside).mean() > 0.05, outside.mean()
+    assert ref["rgb_hat"].max() > 0.1  # the rays render something: the colour path is conditioned
+    return theta, bt_s, ref

@@ -13,8 +13,8 @@ import torch
 import oracle as oc
 import paper_2206_14735_gb300 as gs
 import scenegen as sg
-from gpu_common import (LOSS_RTOL, Problem, assert_grad_close, drop_kink_points, drop_kink_rays, far_from_kinks,
-                        prepare_parity_batch, upload_oracle_batch)
+from gpu_common import (LOSS_RTOL, Problem, assert_grad_close, corner_case, drop_kink_points, drop_kink_rays,
+                        far_from_kinks, prepare_parity_batch, upload_oracle_batch)
 from helpers import paper_parity_params
 
 pytestmark = pytest.mark.gpu
@@ -524,3 +524,27 @@ def test_paper_autograd_step(cube_paper):
     _check_loss(loss.detach().cpu().numpy().astype(np.float64), c["ref"]["loss"])
     ref = oc.step(c["p"].cfg, c["theta"], c["bt"], c["sm"], dloss=seed.cpu().numpy().astype(np.float64))
     assert_grad_close(c["p"], th.grad.cpu().numpy()[:len(c["theta"])], ref["grad"])
+
+
+@pytest.mark.parametrize("corner", ["max", "min"])
+def test_paper_samples_at_the_grid_corners(corner):
+    """Samples crossing a corner of the grid where every level ends (the surface through the
+    corner, so that the colour path carries real gradients): the forward gather's TMA rows reach
+    the first or last (y, z) lines, and the colour corners' 32-byte windows the first or the
+    last vertex record (whose window extends into the decoder block that follows the colour
+    grid); loss and every gradient tensor against the FP64 oracle."""
+    w = CUBE_P
+    p = Problem(w, max_rays=256)
+    theta, bt_s, ref = corner_case(p, paper_parity_params(w, sg.cube_scene(), seed=23), "gb3", corner, SEED, STEP)
+    nx, ny, nz = w.dims[3]
+    g_ref = p.split_grad(ref["grad"])["colour_grid"]
+    rec = slice(6 * (nx * ny * nz - 1), 6 * nx * ny * nz) if corner == "max" else slice(0, 6)
+    assert np.abs(g_ref[rec]).max() > 1e-6 * np.abs(g_ref).max()  # the corner vertex's record is reached
+    batch = upload_oracle_batch(bt_s, None, 0)
+    th = _padded(theta)
+    loss = torch.empty(6, device="cuda")
+    grad = torch.zeros_like(th)
+    p.ctx.forward_backward(th, batch, None, loss, grad)
+    torch.cuda.synchronize()
+    _check_loss(loss.cpu().numpy().astype(np.float64), ref["loss"])
+    assert_grad_close(p, grad.cpu().numpy()[:len(theta)], ref["grad"])

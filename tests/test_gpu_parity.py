@@ -14,8 +14,8 @@ import torch
 import oracle as oc
 import paper_2206_14735_gb300 as gs
 import scenegen as sg
-from gpu_common import (GRAD_TOL, LOSS_RTOL, Problem, assert_grad_close, far_from_kinks, prepare_parity_batch,
-                        sample_positions, upload_oracle_batch)
+from gpu_common import (GRAD_TOL, LOSS_RTOL, Problem, assert_grad_close, corner_case, far_from_kinks,
+                        prepare_parity_batch, sample_positions, upload_oracle_batch)
 from helpers import CUBE, sdf_parity_params
 
 pytestmark = pytest.mark.gpu
@@ -273,4 +273,23 @@ def test_room_scale_parity(n_frames):
     got = loss.cpu().numpy().astype(np.float64)
     for k in range(6):
         assert abs(got[k] - ref["loss"][k]) <= LOSS_RTOL * abs(ref["loss"][k]), (k, got, ref["loss"])
+    assert_grad_close(p, grad.cpu().numpy(), ref["grad"])
+
+
+@pytest.mark.parametrize("corner", ["max", "min"])
+def test_samples_at_the_grid_corners(corner):
+    """Samples crossing a corner of the grid: the finest level's tile::gather4 rows reach the
+    first or last (y, z) lines and columns; loss and every gradient tensor against the FP64
+    oracle."""
+    p = Problem(CUBE, max_rays=256)
+    theta, bt_s, ref = corner_case(p, sdf_parity_params(CUBE, sg.cube_scene(), seed=21), "b2", corner, SEED, STEP)
+    batch = upload_oracle_batch(bt_s, None, 0)
+    th = torch.from_numpy(theta).cuda()
+    loss = torch.empty(6, device="cuda")
+    grad = torch.zeros_like(th)
+    p.ctx.forward_backward(th, batch, None, loss, grad)
+    torch.cuda.synchronize()
+    got = loss.cpu().numpy().astype(np.float64)
+    for k in range(6):
+        assert abs(got[k] - ref["loss"][k]) <= LOSS_RTOL * abs(ref["loss"][k]) + 1e-12, (k, got, ref["loss"])
     assert_grad_close(p, grad.cpu().numpy(), ref["grad"])
